@@ -1,0 +1,743 @@
+/*
+ * FP64 CPU oracle for the neural-constitutive hot path of COMMET
+ * (Alheit, Peirlinck & Kumar, "COMMET: orders-of-magnitude speed-up in finite
+ * element method via batch-vectorized neural constitutive updates").
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the product path may call, link or load
+ * this file: only the tests, the smoke check and the CPU-baseline leg of the
+ * benchmark use it. It shares no code, header, table or constant with the CUDA
+ * library; the two meet only through seeded inputs.
+ *
+ * Everything is plain double precision, one quadrature point (qp) or one
+ * element at a time, with fourth-order tensors written out as 81 entries.
+ * Index conventions:
+ *   F_iJ  -> F[3*i + J]                 (row = spatial i, column = material J)
+ *   A_iJkL = d2Psi/dF_iJ dF_kL -> A[(3*i+J)*9 + 3*k+L]      (App. A.1)
+ *   hex8 nodes lexicographic in (xi, eta, zeta), x fastest; 2x2x2 Gauss points
+ *   at +-1/sqrt(3), weight 1, same order; element dof 3*I + i (Sec. 2.1).
+ * Per-qp arrays are qp-major here (AoS: F[q][9], P[q][9], A[q][81]); element
+ * arrays are element-major (f_e[e][24], K_e[e][24][24]).
+ *
+ * Functions and the passages they follow:
+ *   kinematic layer K(F, A^i) and dK/dF, d2K/dF2 .... Eq. 454, App. A.2 (isochoric
+ *                                                     invariants), material form
+ *   MICNN value, gradient, Hessian (one pass) ........ Eq. icnn, Algorithm 4
+ *   closed-form inner functions (Gent-Thomas, HGO) ... Eq. gt (App. C); target model
+ *   P and A by the CGO chain rule .................... Eq. nncm-chain, App. A.1 (P, C^P)
+ *   F at a qp ........................................ Algorithm 1 (trial F)
+ *   f_int and K_e per element ........................ Eq. r-quad, k-quad (material form)
+ *   backward dL/dF, dL/dtheta ........................ chain rule on G : P(F; theta)
+ *
+ * Parity status: every function here is pinned by the CPU tests (closed forms,
+ * hyper-dual exact derivatives, finite differences, invariance, patch tests);
+ * none is "parity unpinned".
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ model */
+
+enum { OR_KIN_ISO_SHIFTED = 0, OR_KIN_RAW = 1 };
+enum { OR_INNER_MICNN = 0, OR_INNER_GENT_THOMAS = 1, OR_INNER_HGO = 2 };
+
+/*
+ * Strain-energy model Psi(F) = N(K(F)) + kappa (J-1)^2 [- n0 . (K - K0)].
+ * Kinematic layer (kin):
+ *   OR_KIN_ISO_SHIFTED: K = (Ibar1 - 3, Ibar2 - 3, J - 1),                  d = 3
+ *   OR_KIN_RAW:         K = (Ibar1, Ibar2, J, I4_11..I4_nn, I5_11..I5_nn),   d = 3 + 2 n_fib
+ * Inner function (inner):
+ *   OR_INNER_MICNN: eq. icnn with n-1 = L hidden layers. Layer 1 carries one
+ *     matrix W1 (A^(1) acting on z^(0) = K and B^(1) acting on K act on the
+ *     same vector, so they are one matrix); layers k = 2..L carry A_k (W x W),
+ *     B_k (W x d), c_k; the output is a . z^(L) + b . K (no output bias).
+ *   OR_INNER_GENT_THOMAS: N = 0.5 (K0 - 3) + log(K1 / 3) + (K2 - 1)^2 on raw
+ *     (Ibar1, Ibar2, J)  (eq. gt).
+ *   OR_INNER_HGO: N = mu/2 (K0 - 3) + sum_f k1/(2 k2) (exp(k2 (K_{3+f} - 1)^2) - 1)
+ *     on raw kinematics (Neo-Hookean plus exponential fibre terms).
+ * stress_free: subtract n0 . (K - K0), n0 = dN/dK at K0 = K(I), so that P(I) = 0.
+ */
+typedef struct {
+    int d, W, L;
+    int kin;
+    int n_fib;
+    const double *fib; /* [n_fib][3] reference structural vectors A^i */
+    int inner;
+    const double *W1; /* [W][d] */
+    const double *Ak; /* [L-1][W][W] */
+    const double *Bk; /* [L-1][W][d] */
+    const double *c;  /* [L][W] or NULL (= 0) */
+    const double *a;  /* [W] */
+    const double *b;  /* [d] */
+    double kappa;
+    int stress_free;
+    double mu, k1, k2;
+} oracle_model;
+
+#define OR_MAXD 16
+#define OR_MAXW 128
+
+/* ------------------------------------------------------- small tensor help */
+
+static int levi(int i, int j, int k) {
+    /* Levi-Civita symbol eps_ijk for i,j,k in {0,1,2}. */
+    if (i == j || j == k || i == k) return 0;
+    if ((i == 0 && j == 1 && k == 2) || (i == 1 && j == 2 && k == 0) || (i == 2 && j == 0 && k == 1)) return 1;
+    return -1;
+}
+
+static double kd(int i, int j) { return i == j ? 1.0 : 0.0; }
+
+/* cof F_iJ = 1/2 eps_ikl eps_JKL F_kK F_lL ; det F = 1/3 F_iJ cof F_iJ */
+static void cofactor(const double *F, double *cof, double *detF) {
+    for (int i = 0; i < 3; ++i)
+        for (int J = 0; J < 3; ++J) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k)
+                for (int l = 0; l < 3; ++l)
+                    for (int K = 0; K < 3; ++K)
+                        for (int L = 0; L < 3; ++L) {
+                            int e = levi(i, k, l) * levi(J, K, L);
+                            if (e) s += 0.5 * e * F[3 * k + K] * F[3 * l + L];
+                        }
+            cof[3 * i + J] = s;
+        }
+    double d = 0.0;
+    for (int i = 0; i < 9; ++i) d += F[i] * cof[i];
+    *detF = d / 3.0;
+}
+
+/* ------------------------------------------------------- kinematic layer */
+
+/*
+ * One invariant with its first (9) and second (81) derivatives w.r.t. F.
+ * Standard invariants (eq. 454): I1 = tr C, I2 = 1/2 (tr C^2... ), J = det F,
+ * I4 = A.CA, I5 = A.C^2 A, differentiated by hand in material form:
+ *   dI1/dF_iJ = 2 F_iJ ;            d2I1 = 2 d_ik d_JL
+ *   dI2/dF    = 2 (I1 F - F C) ;    d2I2 = 4 F_iJ F_kL + 2 I1 d_ik d_JL - 2 d_ik C_JL
+ *                                          - 2 F_iL F_kJ - 2 B_ik d_JL
+ *   dJ/dF     = cof F ;             d2J  = eps_ikm eps_JLM F_mM
+ *   dI4/dF_kL = 2 a_k A_L ;         d2I4 = 2 d_ik A_J A_L           (a = F A)
+ *   dI5/dF_kL = 2 (a_k v_L + (F v)_k A_L)                           (v = C A)
+ *   d2I5 = 2 [d_JL a_i a_k + F_iL A_J a_k + d_ik A_J v_L + d_ik v_J A_L
+ *             + F_kJ a_i A_L + B_ik A_J A_L]
+ */
+static void inv_I1(const double *F, double *v, double *g, double *h) {
+    double s = 0.0;
+    for (int i = 0; i < 9; ++i) s += F[i] * F[i];
+    *v = s;
+    for (int i = 0; i < 9; ++i) g[i] = 2.0 * F[i];
+    for (int i = 0; i < 3; ++i)
+        for (int J = 0; J < 3; ++J)
+            for (int k = 0; k < 3; ++k)
+                for (int L = 0; L < 3; ++L) h[(3 * i + J) * 9 + 3 * k + L] = 2.0 * kd(i, k) * kd(J, L);
+}
+
+static void right_cg(const double *F, double *C) {
+    for (int I = 0; I < 3; ++I)
+        for (int J = 0; J < 3; ++J) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += F[3 * k + I] * F[3 * k + J];
+            C[3 * I + J] = s;
+        }
+}
+
+static void left_cg(const double *F, double *B) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int K = 0; K < 3; ++K) s += F[3 * i + K] * F[3 * j + K];
+            B[3 * i + j] = s;
+        }
+}
+
+static void inv_I2(const double *F, double *v, double *g, double *h) {
+    double C[9], B[9], I1 = 0.0, trC2 = 0.0;
+    right_cg(F, C);
+    left_cg(F, B);
+    for (int I = 0; I < 3; ++I) I1 += C[4 * I];
+    for (int I = 0; I < 3; ++I)
+        for (int J = 0; J < 3; ++J) trC2 += C[3 * I + J] * C[3 * J + I];
+    *v = 0.5 * (I1 * I1 - trC2);
+    for (int i = 0; i < 3; ++i)
+        for (int J = 0; J < 3; ++J) {
+            double FC = 0.0;
+            for (int K = 0; K < 3; ++K) FC += F[3 * i + K] * C[3 * K + J];
+            g[3 * i + J] = 2.0 * (I1 * F[3 * i + J] - FC);
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int J = 0; J < 3; ++J)
+            for (int k = 0; k < 3; ++k)
+                for (int L = 0; L < 3; ++L)
+                    h[(3 * i + J) * 9 + 3 * k + L] = 4.0 * F[3 * i + J] * F[3 * k + L] + 2.0 * I1 * kd(i, k) * kd(J, L) -
+                                                     2.0 * kd(i, k) * C[3 * J + L] - 2.0 * F[3 * i + L] * F[3 * k + J] -
+                                                     2.0 * B[3 * i + k] * kd(J, L);
+}
+
+static void inv_J(const double *F, double *v, double *g, double *h) {
+    double cof[9], J;
+    cofactor(F, cof, &J);
+    *v = J;
+    for (int i = 0; i < 9; ++i) g[i] = cof[i];
+    for (int i = 0; i < 3; ++i)
+        for (int J_ = 0; J_ < 3; ++J_)
+            for (int k = 0; k < 3; ++k)
+                for (int L = 0; L < 3; ++L) {
+                    double s = 0.0;
+                    for (int m = 0; m < 3; ++m)
+                        for (int M = 0; M < 3; ++M) s += levi(i, k, m) * levi(J_, L, M) * F[3 * m + M];
+                    h[(3 * i + J_) * 9 + 3 * k + L] = s;
+                }
+}
+
+static void inv_I4(const double *F, const double *A0, double *v, double *g, double *h) {
+    double a[3];
+    for (int i = 0; i < 3; ++i) a[i] = F[3 * i] * A0[0] + F[3 * i + 1] * A0[1] + F[3 * i + 2] * A0[2];
+    *v = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+    for (int k = 0; k < 3; ++k)
+        for (int L = 0; L < 3; ++L) g[3 * k + L] = 2.0 * a[k] * A0[L];
+    for (int i = 0; i < 3; ++i)
+        for (int J = 0; J < 3; ++J)
+            for (int k = 0; k < 3; ++k)
+                for (int L = 0; L < 3; ++L) h[(3 * i + J) * 9 + 3 * k + L] = 2.0 * kd(i, k) * A0[J] * A0[L];
+}
+
+static void inv_I5(const double *F, const double *A0, double *v, double *g, double *h) {
+    double C[9], B[9], a[3], vv[3], Fv[3];
+    right_cg(F, C);
+    left_cg(F, B);
+    for (int i = 0; i < 3; ++i) a[i] = F[3 * i] * A0[0] + F[3 * i + 1] * A0[1] + F[3 * i + 2] * A0[2];
+    for (int I = 0; I < 3; ++I) vv[I] = C[3 * I] * A0[0] + C[3 * I + 1] * A0[1] + C[3 * I + 2] * A0[2];
+    for (int i = 0; i < 3; ++i) Fv[i] = F[3 * i] * vv[0] + F[3 * i + 1] * vv[1] + F[3 * i + 2] * vv[2];
+    *v = vv[0] * vv[0] + vv[1] * vv[1] + vv[2] * vv[2];
+    for (int k = 0; k < 3; ++k)
+        for (int L = 0; L < 3; ++L) g[3 * k + L] = 2.0 * (a[k] * vv[L] + Fv[k] * A0[L]);
+    for (int i = 0; i < 3; ++i)
+        for (int J = 0; J < 3; ++J)
+            for (int k = 0; k < 3; ++k)
+                for (int L = 0; L < 3; ++L)
+                    h[(3 * i + J) * 9 + 3 * k + L] =
+                        2.0 * (kd(J, L) * a[i] * a[k] + F[3 * i + L] * A0[J] * a[k] + kd(i, k) * A0[J] * vv[L] +
+                               kd(i, k) * vv[J] * A0[L] + F[3 * k + J] * a[i] * A0[L] + B[3 * i + k] * A0[J] * A0[L]);
+}
+
+/*
+ * Isochoric invariant Ibar = I * I3^alpha = J^q I with q = 2 alpha
+ * (alpha = -1/3 for I1, -2/3 for I2; App. A.2). With H = F^{-T} = dlnJ/dF and
+ * dH_iJ/dF_kL = -H_iL H_kJ:
+ *   dIbar   = J^q (dI + q I H)
+ *   d2Ibar  = J^q [d2I + q (dI (x) H + H (x) dI) + q^2 I H (x) H - q I H_iL H_kJ]
+ */
+static void isochoric(double q, const double *F, double I, const double *gI, const double *hI, double *v, double *g,
+                      double *h) {
+    double cof[9], J, H[9];
+    cofactor(F, cof, &J);
+    for (int i = 0; i < 9; ++i) H[i] = cof[i] / J;
+    double Jq = pow(J, q);
+    *v = Jq * I;
+    for (int i = 0; i < 9; ++i) g[i] = Jq * (gI[i] + q * I * H[i]);
+    for (int i = 0; i < 3; ++i)
+        for (int J_ = 0; J_ < 3; ++J_)
+            for (int k = 0; k < 3; ++k)
+                for (int L = 0; L < 3; ++L) {
+                    int a = 3 * i + J_, b = 3 * k + L;
+                    h[a * 9 + b] = Jq * (hI[a * 9 + b] + q * (gI[a] * H[b] + H[a] * gI[b]) + q * q * I * H[a] * H[b] -
+                                         q * I * H[3 * i + L] * H[3 * k + J_]);
+                }
+}
+
+/* K(F) with dK/dF [d][9] and d2K/dF2 [d][81]. Returns d. */
+static int oracle_kinematics(const oracle_model *m, const double *F, double *K, double *dK, double *d2K) {
+    double v, g[9], h[81];
+    double I1, g1[9], h1[81], I2, g2[9], h2[81];
+    inv_I1(F, &I1, g1, h1);
+    isochoric(-2.0 / 3.0, F, I1, g1, h1, &K[0], &dK[0], &d2K[0]);
+    inv_I2(F, &I2, g2, h2);
+    isochoric(-4.0 / 3.0, F, I2, g2, h2, &K[1], &dK[9], &d2K[81]);
+    inv_J(F, &v, g, h);
+    K[2] = v;
+    memcpy(&dK[18], g, sizeof g);
+    memcpy(&d2K[162], h, sizeof h);
+    if (m->kin == OR_KIN_ISO_SHIFTED) {
+        K[0] -= 3.0;
+        K[1] -= 3.0;
+        K[2] -= 1.0;
+        return 3;
+    }
+    int nf = m->n_fib;
+    for (int f = 0; f < nf; ++f) {
+        inv_I4(F, &m->fib[3 * f], &K[3 + f], &dK[9 * (3 + f)], &d2K[81 * (3 + f)]);
+        inv_I5(F, &m->fib[3 * f], &K[3 + nf + f], &dK[9 * (3 + nf + f)], &d2K[81 * (3 + nf + f)]);
+    }
+    return 3 + 2 * nf;
+}
+
+/* ------------------------------------------------------- inner functions */
+
+/* softplus (beta = 1) and its first two derivatives, in a form that does not overflow */
+static double softplus(double y) { return (y > 0.0 ? y : 0.0) + log1p(exp(-fabs(y))); }
+static double logistic(double y) {
+    if (y >= 0.0) return 1.0 / (1.0 + exp(-y));
+    double e = exp(y);
+    return e / (1.0 + e);
+}
+
+/*
+ * MICNN value, gradient and Hessian in one pass, following Algorithm 4:
+ *   z <- K, dz <- I, d2z <- 0
+ *   per hidden layer k: y = A z + B K + c ; dy = A dz + B ; d2y = A d2z ;
+ *     d2z = F'(y) * d2y + F''(y) * dy (x) dy ; dz = F'(y) * dy ; z = F(y)
+ *   N = A^(n) z + B^(n) K ; dN = A^(n) dz + B^(n) ; d2N = A^(n) d2z
+ * Layer 1 uses A = W1 (acting on z = K) and no B; the output layer uses a, b.
+ */
+static void micnn_alg4(const oracle_model *m, const double *K, double *N, double *dN, double *d2N) {
+    const int d = m->d, W = m->W, L = m->L;
+    int nin = d; /* current width of z */
+    double *z = (double *)calloc(OR_MAXW, sizeof(double));
+    double *dz = (double *)calloc((size_t)OR_MAXW * OR_MAXD, sizeof(double));
+    double *d2z = (double *)calloc((size_t)OR_MAXW * OR_MAXD * OR_MAXD, sizeof(double));
+    double *y = (double *)calloc(OR_MAXW, sizeof(double));
+    double *dy = (double *)calloc((size_t)OR_MAXW * OR_MAXD, sizeof(double));
+    double *d2y = (double *)calloc((size_t)OR_MAXW * OR_MAXD * OR_MAXD, sizeof(double));
+    for (int i = 0; i < d; ++i) {
+        z[i] = K[i];
+        for (int p = 0; p < d; ++p) dz[i * OR_MAXD + p] = kd(i, p);
+    }
+    for (int k = 1; k <= L; ++k) {
+        const double *A = (k == 1) ? m->W1 : &m->Ak[(size_t)(k - 2) * W * W];
+        const double *B = (k == 1) ? NULL : &m->Bk[(size_t)(k - 2) * W * d];
+        const double *c = m->c ? &m->c[(size_t)(k - 1) * W] : NULL;
+        for (int j = 0; j < W; ++j) {
+            double s = c ? c[j] : 0.0;
+            for (int i = 0; i < nin; ++i) s += A[j * nin + i] * z[i];
+            if (B)
+                for (int i = 0; i < d; ++i) s += B[j * d + i] * K[i];
+            y[j] = s;
+            for (int p = 0; p < d; ++p) {
+                double t = B ? B[j * d + p] : 0.0;
+                for (int i = 0; i < nin; ++i) t += A[j * nin + i] * dz[i * OR_MAXD + p];
+                dy[j * OR_MAXD + p] = t;
+                for (int q = 0; q < d; ++q) {
+                    double u = 0.0;
+                    for (int i = 0; i < nin; ++i) u += A[j * nin + i] * d2z[(i * OR_MAXD + p) * OR_MAXD + q];
+                    d2y[(j * OR_MAXD + p) * OR_MAXD + q] = u;
+                }
+            }
+        }
+        for (int j = 0; j < W; ++j) {
+            double s1 = logistic(y[j]);
+            double s2 = s1 * (1.0 - s1);
+            for (int p = 0; p < d; ++p)
+                for (int q = 0; q < d; ++q)
+                    d2z[(j * OR_MAXD + p) * OR_MAXD + q] =
+                        s1 * d2y[(j * OR_MAXD + p) * OR_MAXD + q] + s2 * dy[j * OR_MAXD + p] * dy[j * OR_MAXD + q];
+            for (int p = 0; p < d; ++p) dz[j * OR_MAXD + p] = s1 * dy[j * OR_MAXD + p];
+            z[j] = softplus(y[j]);
+        }
+        nin = W;
+    }
+    double s = 0.0;
+    for (int i = 0; i < W; ++i) s += m->a[i] * z[i];
+    for (int i = 0; i < d; ++i) s += m->b[i] * K[i];
+    *N = s;
+    for (int p = 0; p < d; ++p) {
+        double t = m->b[p];
+        for (int i = 0; i < W; ++i) t += m->a[i] * dz[i * OR_MAXD + p];
+        dN[p] = t;
+        for (int q = 0; q < d; ++q) {
+            double u = 0.0;
+            for (int i = 0; i < W; ++i) u += m->a[i] * d2z[(i * OR_MAXD + p) * OR_MAXD + q];
+            d2N[p * d + q] = u;
+        }
+    }
+    free(z);
+    free(dz);
+    free(d2z);
+    free(y);
+    free(dy);
+    free(d2y);
+}
+
+/* Gent-Thomas, eq. gt, on raw (Ibar1, Ibar2, J). */
+static void gent_thomas(const double *K, double *N, double *dN, double *d2N) {
+    *N = 0.5 * (K[0] - 3.0) + log(K[1] / 3.0) + (K[2] - 1.0) * (K[2] - 1.0);
+    dN[0] = 0.5;
+    dN[1] = 1.0 / K[1];
+    dN[2] = 2.0 * (K[2] - 1.0);
+    for (int i = 0; i < 9; ++i) d2N[i] = 0.0;
+    d2N[1 * 3 + 1] = -1.0 / (K[1] * K[1]);
+    d2N[2 * 3 + 2] = 2.0;
+}
+
+/* Neo-Hookean plus exponential fibre terms (HGO type, smooth) on raw kinematics. */
+static void hgo(const oracle_model *m, const double *K, double *N, double *dN, double *d2N) {
+    const int d = m->d, nf = m->n_fib;
+    for (int i = 0; i < d * d; ++i) d2N[i] = 0.0;
+    for (int i = 0; i < d; ++i) dN[i] = 0.0;
+    double s = 0.5 * m->mu * (K[0] - 3.0);
+    dN[0] = 0.5 * m->mu;
+    for (int f = 0; f < nf; ++f) {
+        double x = K[3 + f] - 1.0, e = exp(m->k2 * x * x);
+        s += m->k1 / (2.0 * m->k2) * (e - 1.0);
+        dN[3 + f] = m->k1 * x * e;
+        d2N[(3 + f) * d + 3 + f] = m->k1 * e * (1.0 + 2.0 * m->k2 * x * x);
+    }
+    *N = s;
+}
+
+static void inner_eval(const oracle_model *m, const double *K, double *N, double *dN, double *d2N) {
+    if (m->inner == OR_INNER_GENT_THOMAS)
+        gent_thomas(K, N, dN, d2N);
+    else if (m->inner == OR_INNER_HGO)
+        hgo(m, K, N, dN, d2N);
+    else
+        micnn_alg4(m, K, N, dN, d2N);
+}
+
+/* Network value/gradient/Hessian at a given K (exported for the Algorithm 4 pins). */
+void oracle_inner(const oracle_model *m, const double *K, double *N, double *dN, double *d2N) {
+    inner_eval(m, K, N, dN, d2N);
+}
+
+/* ---------------------------------------------------- constitutive update */
+
+/*
+ * One qp: Psi, P = dPsi/dF (9) and A = d2Psi/dF dF (81) by the chain rule of
+ * eq. nncm-chain plus the volumetric penalty kappa (J-1)^2:
+ *   P_iJ    = N_m dK_m/dF_iJ + 2 kappa (J-1) dJ/dF_iJ
+ *   A_iJkL  = N_mn dK_m/dF_iJ dK_n/dF_kL + N_m d2K_m/dF_iJ dF_kL
+ *             + 2 kappa dJ/dF_iJ dJ/dF_kL + 2 kappa (J-1) d2J/dF_iJ dF_kL
+ * n0 (or NULL) is dN/dK at K(I) for the stress-free shift.
+ */
+static void qp_update(const oracle_model *m, const double *n0, const double *F, double *psi, double *P, double *A) {
+    double K[OR_MAXD], dK[OR_MAXD * 9], d2K[OR_MAXD * 81];
+    double N, dN[OR_MAXD], d2N[OR_MAXD * OR_MAXD];
+    int d = oracle_kinematics(m, F, K, dK, d2K);
+    inner_eval(m, K, &N, dN, d2N);
+    double J, gJ[9], hJ[81];
+    inv_J(F, &J, gJ, hJ);
+    double Psi = N + m->kappa * (J - 1.0) * (J - 1.0);
+    if (n0) {
+        double K0[OR_MAXD], dK0[OR_MAXD * 9], d2K0[OR_MAXD * 81], I9[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+        oracle_kinematics(m, I9, K0, dK0, d2K0);
+        for (int i = 0; i < d; ++i) {
+            Psi -= n0[i] * (K[i] - K0[i]);
+            dN[i] -= n0[i];
+        }
+    }
+    if (psi) *psi = Psi;
+    for (int a = 0; a < 9; ++a) {
+        double s = 2.0 * m->kappa * (J - 1.0) * gJ[a];
+        for (int i = 0; i < d; ++i) s += dN[i] * dK[9 * i + a];
+        P[a] = s;
+    }
+    if (!A) return;
+    for (int a = 0; a < 9; ++a)
+        for (int b = 0; b < 9; ++b) {
+            double s = 2.0 * m->kappa * (gJ[a] * gJ[b] + (J - 1.0) * hJ[a * 9 + b]);
+            for (int i = 0; i < d; ++i) {
+                s += dN[i] * d2K[81 * i + a * 9 + b];
+                for (int j = 0; j < d; ++j) s += d2N[i * d + j] * dK[9 * i + a] * dK[9 * j + b];
+            }
+            A[a * 9 + b] = s;
+        }
+}
+
+static void stress_free_shift(const oracle_model *m, double *n0) {
+    double K0[OR_MAXD], dK0[OR_MAXD * 9], d2K0[OR_MAXD * 81], I9[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    double N, d2N[OR_MAXD * OR_MAXD];
+    oracle_kinematics(m, I9, K0, dK0, d2K0);
+    inner_eval(m, K0, &N, n0, d2N);
+}
+
+/* {Psi}, {P}, {A} <- model({F}) over n_qp points (Algorithm 2's constitutive call). psi, A may be NULL. */
+int oracle_const_update(const oracle_model *m, int64_t n_qp, const double *F, double *psi, double *P, double *A) {
+    double n0[OR_MAXD];
+    if (m->d > OR_MAXD || m->W > OR_MAXW) return -1;
+    if (m->stress_free) stress_free_shift(m, n0);
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < n_qp; ++q)
+        qp_update(m, m->stress_free ? n0 : NULL, &F[9 * q], psi ? &psi[q] : NULL, &P[9 * q], A ? &A[81 * q] : NULL);
+    return 0;
+}
+
+/* Kinematic scalars and their derivatives at one F (exported for the kinematics pins). */
+int oracle_kinematics_at(const oracle_model *m, const double *F, double *K, double *dK, double *d2K) {
+    return oracle_kinematics(m, F, K, dK, d2K);
+}
+
+/* ------------------------------------------------------------- hex8 element */
+
+static const double GP = 0.57735026918962576451; /* 1/sqrt(3) */
+
+/* Reference coordinates of node I (lexicographic, x fastest). */
+static double node_xi(int I, int a) { return ((I >> a) & 1) ? 1.0 : -1.0; }
+/* Gauss point q coordinates (lexicographic, x fastest). */
+static double gauss_xi(int q, int a) { return ((q >> a) & 1) ? GP : -GP; }
+
+/*
+ * Shape-function gradients of one element at its 8 Gauss points:
+ *   phi_I(xi) = 1/8 prod_a (1 + xi_I,a xi_a)
+ *   Je_ab = dX_a/dxi_b = sum_I X_I,a dphi_I/dxi_b ; grad_X phi = Je^{-T} grad_xi phi
+ *   w_q = det Je (Gauss weight 1): the "volume" of the qp (Sec. 2.1)
+ * dphi[q][I][a], w[q].
+ */
+void oracle_hex8_gradients(const double *Xe, double *dphi, double *w) {
+    for (int q = 0; q < 8; ++q) {
+        double gxi[8][3];
+        for (int I = 0; I < 8; ++I)
+            for (int b = 0; b < 3; ++b) {
+                double p = 0.125 * node_xi(I, b);
+                for (int c = 0; c < 3; ++c)
+                    if (c != b) p *= 1.0 + node_xi(I, c) * gauss_xi(q, c);
+                gxi[I][b] = p;
+            }
+        double Je[9] = {0}, cof[9], det;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                for (int I = 0; I < 8; ++I) Je[3 * a + b] += Xe[3 * I + a] * gxi[I][b];
+        cofactor(Je, cof, &det);
+        /* Je^{-T} = cof(Je) / det */
+        for (int I = 0; I < 8; ++I)
+            for (int a = 0; a < 3; ++a) {
+                double s = 0.0;
+                for (int b = 0; b < 3; ++b) s += cof[3 * a + b] / det * gxi[I][b];
+                dphi[(q * 8 + I) * 3 + a] = s;
+            }
+        w[q] = det;
+    }
+}
+
+static void gather_X(const double *X, const int32_t *conn, int64_t e, double *Xe) {
+    for (int I = 0; I < 8; ++I)
+        for (int a = 0; a < 3; ++a) Xe[3 * I + a] = X[3 * (int64_t)conn[8 * e + I] + a];
+}
+
+/* F = I + sum_I u^I (x) grad_X phi^I at every qp (Algorithm 1, trial F). u[n_nodes][3], F[n_el*8][9]. */
+void oracle_compute_F(int64_t n_el, const int32_t *conn, const double *X, const double *u, double *F) {
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < n_el; ++e) {
+        double Xe[24], dphi[192], w[8];
+        gather_X(X, conn, e, Xe);
+        oracle_hex8_gradients(Xe, dphi, w);
+        for (int q = 0; q < 8; ++q) {
+            double *Fq = &F[9 * (8 * e + q)];
+            for (int i = 0; i < 3; ++i)
+                for (int J = 0; J < 3; ++J) {
+                    double s = kd(i, J);
+                    for (int I = 0; I < 8; ++I) s += u[3 * (int64_t)conn[8 * e + I] + i] * dphi[(q * 8 + I) * 3 + J];
+                    Fq[3 * i + J] = s;
+                }
+        }
+    }
+}
+
+/*
+ * Element residual and stiffness from qp tables (Algorithm 2, second loop), in
+ * material form (App. A.1 relates it to the spatial eq. r-quad / k-quad):
+ *   f_e[3I+i]         = sum_q w_q P_iJ dphi_I/dX_J
+ *   K_e[3I+i][3K+k]   = sum_q w_q dphi_I/dX_J A_iJkL dphi_K/dX_L
+ * Element e owns qp 8e..8e+7. f_e or K_e may be NULL.
+ */
+void oracle_elem_assemble(int64_t n_el, const int32_t *conn, const double *X, const double *P, const double *A,
+                          double *f_e, double *K_e) {
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < n_el; ++e) {
+        double Xe[24], dphi[192], w[8];
+        gather_X(X, conn, e, Xe);
+        oracle_hex8_gradients(Xe, dphi, w);
+        if (f_e)
+            for (int r = 0; r < 24; ++r) f_e[24 * e + r] = 0.0;
+        if (K_e)
+            for (int r = 0; r < 576; ++r) K_e[576 * e + r] = 0.0;
+        for (int q = 0; q < 8; ++q) {
+            const double *Pq = &P[9 * (8 * e + q)];
+            const double *Aq = A ? &A[81 * (8 * e + q)] : NULL;
+            const double *g = &dphi[q * 24];
+            for (int I = 0; I < 8; ++I)
+                for (int i = 0; i < 3; ++i) {
+                    if (f_e) {
+                        double s = 0.0;
+                        for (int J = 0; J < 3; ++J) s += Pq[3 * i + J] * g[3 * I + J];
+                        f_e[24 * e + 3 * I + i] += w[q] * s;
+                    }
+                    if (K_e && Aq)
+                        for (int K = 0; K < 8; ++K)
+                            for (int k = 0; k < 3; ++k) {
+                                double s = 0.0;
+                                for (int J = 0; J < 3; ++J)
+                                    for (int L = 0; L < 3; ++L)
+                                        s += g[3 * I + J] * Aq[(3 * i + J) * 9 + 3 * k + L] * g[3 * K + L];
+                                K_e[576 * e + (3 * I + i) * 24 + 3 * K + k] += w[q] * s;
+                            }
+                }
+        }
+    }
+}
+
+/* Global residual r[3*n_nodes] = sum_e f_e scattered to dofs 3*node + i, elements in order. */
+void oracle_scatter_residual(int64_t n_el, const int32_t *conn, const double *f_e, int64_t n_nodes, double *r) {
+    for (int64_t i = 0; i < 3 * n_nodes; ++i) r[i] = 0.0;
+    for (int64_t e = 0; e < n_el; ++e)
+        for (int I = 0; I < 8; ++I)
+            for (int i = 0; i < 3; ++i) r[3 * (int64_t)conn[8 * e + I] + i] += f_e[24 * e + 3 * I + i];
+}
+
+/*
+ * Global K in CSR form (caller's pattern rowptr/col, columns sorted within a
+ * row): vals[p] = sum_e K_e entries landing on (row, col), elements in order.
+ * Returns the number of element entries that found no slot in the pattern.
+ */
+int64_t oracle_scatter_csr(int64_t n_el, const int32_t *conn, const double *K_e, int64_t n_rows, const int64_t *rowptr,
+                           const int32_t *col, double *vals) {
+    int64_t missing = 0;
+    for (int64_t p = 0; p < rowptr[n_rows]; ++p) vals[p] = 0.0;
+    for (int64_t e = 0; e < n_el; ++e)
+        for (int a = 0; a < 24; ++a)
+            for (int b = 0; b < 24; ++b) {
+                int64_t row = 3 * (int64_t)conn[8 * e + a / 3] + a % 3;
+                int32_t c = 3 * conn[8 * e + b / 3] + b % 3;
+                int64_t lo = rowptr[row], hi = rowptr[row + 1], found = -1;
+                for (int64_t p = lo; p < hi; ++p)
+                    if (col[p] == c) {
+                        found = p;
+                        break;
+                    }
+                if (found < 0)
+                    ++missing;
+                else
+                    vals[found] += K_e[576 * e + a * 24 + b];
+            }
+    return missing;
+}
+
+/* ---------------------------------------------------------------- backward */
+
+/*
+ * Parameter vector theta, in this order:
+ *   W1 [W][d], c1 [W], then for k = 2..L: A_k [W][W], B_k [W][d], c_k [W], then a [W], b [d].
+ */
+int64_t oracle_n_params(int d, int W, int L) {
+    return (int64_t)W * d + W + (int64_t)(L - 1) * ((int64_t)W * W + (int64_t)W * d + W) + W + d;
+}
+
+/*
+ * Backward of G : P(F; theta) summed over qp, for G = dL/dP given per qp:
+ *   dL/dF_kL   = sum_iJ G_iJ A_iJkL                        (A from qp_update)
+ *   dL/dtheta  = sum_q d/dtheta [ sum_m r_m dN/dK_m ],  r_m = G : dK_m/dF
+ * The inner term s = grad_K N . r is propagated forward as a tangent
+ * (zdot = F'(y) ydot, ydot = A zdot + B r) and then differentiated in reverse
+ * with respect to every weight; qp are summed in index order.
+ * The volumetric penalty does not depend on theta. MICNN inner only; the
+ * stress-free shift is not supported here (returns -2).
+ */
+int oracle_const_backward(const oracle_model *m, int64_t n_qp, const double *F, const double *G, double *dLdF,
+                          double *dLdtheta) {
+    const int d = m->d, W = m->W, L = m->L;
+    if (m->inner != OR_INNER_MICNN) return -1;
+    if (m->stress_free) return -2;
+    const int64_t np = oracle_n_params(d, W, L);
+    for (int64_t i = 0; i < np; ++i) dLdtheta[i] = 0.0;
+    /* offsets */
+    int64_t off_W1 = 0, off_c1 = (int64_t)W * d;
+    int64_t off_layer = off_c1 + W; /* start of layer 2 block */
+    int64_t layer_sz = (int64_t)W * W + (int64_t)W * d + W;
+    int64_t off_a = off_layer + (int64_t)(L - 1) * layer_sz, off_b = off_a + W;
+
+    double *y = (double *)malloc(sizeof(double) * L * W), *z = (double *)malloc(sizeof(double) * (L + 1) * OR_MAXW);
+    double *yd = (double *)malloc(sizeof(double) * L * W), *zd = (double *)malloc(sizeof(double) * (L + 1) * OR_MAXW);
+    double *zb = (double *)malloc(sizeof(double) * OR_MAXW), *zdb = (double *)malloc(sizeof(double) * OR_MAXW);
+    double *yb = (double *)malloc(sizeof(double) * OR_MAXW), *ydb = (double *)malloc(sizeof(double) * OR_MAXW);
+    for (int64_t q = 0; q < n_qp; ++q) {
+        const double *Fq = &F[9 * q], *Gq = &G[9 * q];
+        double psi, P[9], A[81];
+        qp_update(m, NULL, Fq, &psi, P, A);
+        if (dLdF)
+            for (int b = 0; b < 9; ++b) {
+                double s = 0.0;
+                for (int a = 0; a < 9; ++a) s += Gq[a] * A[a * 9 + b];
+                dLdF[9 * q + b] = s;
+            }
+        double K[OR_MAXD], dK[OR_MAXD * 9], d2K[OR_MAXD * 81], r[OR_MAXD];
+        oracle_kinematics(m, Fq, K, dK, d2K);
+        for (int i = 0; i < d; ++i) {
+            double s = 0.0;
+            for (int a = 0; a < 9; ++a) s += Gq[a] * dK[9 * i + a];
+            r[i] = s;
+        }
+        /* forward: values and tangents along r; z[0] = K, zd[0] = r */
+        for (int i = 0; i < d; ++i) {
+            z[i] = K[i];
+            zd[i] = r[i];
+        }
+        for (int k = 1; k <= L; ++k) {
+            int nin = (k == 1) ? d : W;
+            const double *A_ = (k == 1) ? m->W1 : &m->Ak[(size_t)(k - 2) * W * W];
+            const double *B_ = (k == 1) ? NULL : &m->Bk[(size_t)(k - 2) * W * d];
+            const double *c_ = m->c ? &m->c[(size_t)(k - 1) * W] : NULL;
+            const double *zin = &z[(k - 1) * OR_MAXW], *zdin = &zd[(k - 1) * OR_MAXW];
+            for (int j = 0; j < W; ++j) {
+                double s = c_ ? c_[j] : 0.0, t = 0.0;
+                for (int i = 0; i < nin; ++i) {
+                    s += A_[j * nin + i] * zin[i];
+                    t += A_[j * nin + i] * zdin[i];
+                }
+                if (B_)
+                    for (int i = 0; i < d; ++i) {
+                        s += B_[j * d + i] * K[i];
+                        t += B_[j * d + i] * r[i];
+                    }
+                y[(k - 1) * W + j] = s;
+                yd[(k - 1) * W + j] = t;
+                z[k * OR_MAXW + j] = softplus(s);
+                zd[k * OR_MAXW + j] = logistic(s) * t;
+            }
+        }
+        /* s = a . zd[L] + b . r ; reverse */
+        for (int j = 0; j < W; ++j) {
+            dLdtheta[off_a + j] += zd[L * OR_MAXW + j];
+            zb[j] = 0.0;
+            zdb[j] = m->a[j];
+        }
+        for (int i = 0; i < d; ++i) dLdtheta[off_b + i] += r[i];
+        for (int k = L; k >= 1; --k) {
+            int nin = (k == 1) ? d : W;
+            const double *A_ = (k == 1) ? m->W1 : &m->Ak[(size_t)(k - 2) * W * W];
+            const double *zin = &z[(k - 1) * OR_MAXW], *zdin = &zd[(k - 1) * OR_MAXW];
+            for (int j = 0; j < W; ++j) {
+                double yy = y[(k - 1) * W + j], s1 = logistic(yy), s2 = s1 * (1.0 - s1);
+                ydb[j] = s1 * zdb[j];
+                yb[j] = s1 * zb[j] + s2 * yd[(k - 1) * W + j] * zdb[j];
+            }
+            int64_t oA = (k == 1) ? off_W1 : off_layer + (int64_t)(k - 2) * layer_sz;
+            int64_t oB = oA + (int64_t)W * W, oc = (k == 1) ? off_c1 : oB + (int64_t)W * d;
+            for (int j = 0; j < W; ++j) {
+                for (int i = 0; i < nin; ++i) dLdtheta[oA + (int64_t)j * nin + i] += yb[j] * zin[i] + ydb[j] * zdin[i];
+                if (k > 1)
+                    for (int i = 0; i < d; ++i) dLdtheta[oB + (int64_t)j * d + i] += yb[j] * K[i] + ydb[j] * r[i];
+                dLdtheta[oc + j] += yb[j];
+            }
+            if (k > 1)
+                for (int i = 0; i < nin; ++i) {
+                    double s = 0.0, t = 0.0;
+                    for (int j = 0; j < W; ++j) {
+                        s += A_[j * nin + i] * yb[j];
+                        t += A_[j * nin + i] * ydb[j];
+                    }
+                    zb[i] = s;
+                    zdb[i] = t;
+                }
+        }
+    }
+    free(y);
+    free(z);
+    free(yd);
+    free(zd);
+    free(zb);
+    free(zdb);
+    free(yb);
+    free(ydb);
+    return 0;
+}

@@ -1,0 +1,308 @@
+"""Seeded synthetic inputs shared by the oracle tests, the CUDA tests and the benchmark.
+
+This module is the one thing both sides use. It holds input recipes only: random
+weights, meshes, displacement and deformation fields. It holds none of the method's
+arithmetic (no invariants, network evaluation, shape functions or assembly). The one
+computation on inputs is a determinant rejection test (``numpy.linalg.det``) that
+keeps the drawn deformation gradients orientation-preserving, as the workloads require.
+
+The workloads stand in for the paper's twisted cube and heart meshes with trained
+MICNNs (Sec. 4-5): structured unit-cube hex8 meshes and the paper's MICNN family
+(Appendix B, eq. icnn; sizes as in the hyper-parameter table and Appendix E), with
+random non-negative weights. No dataset is involved.
+
+Draw order for every workload, on one ``numpy.random.Generator(PCG64(seed))``:
+weights layer by layer (W1, c1, then A_k, B_k, c_k for k = 2..L, then a, b), then the
+displacement or deformation field, then any per-point scalars.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# Kinematic layers (input menus) of the strain energy.
+KIN_ISO_SHIFTED = 0  # K = (Ibar1 - 3, Ibar2 - 3, J - 1)
+KIN_RAW = 1          # K = (Ibar1, Ibar2, J, I4_11..I4_nn, I5_11..I5_nn)
+
+# Reference structural vectors at +-30 degrees from +x in the x-y plane.
+FIBRES_PM30 = np.array([[math.cos(math.pi / 6), math.sin(math.pi / 6), 0.0],
+                        [math.cos(math.pi / 6), -math.sin(math.pi / 6), 0.0]])
+
+
+@dataclass
+class ModelSpec:
+    """Weights and hyper-parameters of one MICNN strain energy (float64, row-major).
+
+    W1: [W][d]; Ak: [L-1][W][W]; Bk: [L-1][W][d]; c: [L][W]; a: [W]; b: [d].
+    """
+    d: int
+    W: int
+    L: int
+    kin: int
+    fibres: np.ndarray
+    W1: np.ndarray
+    Ak: np.ndarray
+    Bk: np.ndarray
+    c: np.ndarray
+    a: np.ndarray
+    b: np.ndarray
+    kappa: float = 0.0
+    stress_free: bool = False
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n_fib(self) -> int:
+        return int(self.fibres.shape[0])
+
+    def theta(self) -> np.ndarray:
+        """Flat parameter vector: W1, c1, then per k = 2..L: A_k, B_k, c_k, then a, b."""
+        parts = [self.W1.ravel(), self.c[0].ravel()]
+        for k in range(self.L - 1):
+            parts += [self.Ak[k].ravel(), self.Bk[k].ravel(), self.c[k + 1].ravel()]
+        parts += [self.a.ravel(), self.b.ravel()]
+        return np.concatenate(parts).astype(np.float64)
+
+    def with_theta(self, theta: np.ndarray) -> "ModelSpec":
+        """Copy of this model with the flat parameter vector replaced."""
+        d, W, L = self.d, self.W, self.L
+        t = np.asarray(theta, dtype=np.float64)
+        o = 0
+
+        def take(n, shape):
+            nonlocal o
+            v = t[o:o + n].reshape(shape).copy()
+            o += n
+            return v
+        W1 = take(W * d, (W, d))
+        c = np.zeros((L, W))
+        c[0] = take(W, (W,))
+        Ak = np.zeros((max(L - 1, 0), W, W))
+        Bk = np.zeros((max(L - 1, 0), W, d))
+        for k in range(L - 1):
+            Ak[k] = take(W * W, (W, W))
+            Bk[k] = take(W * d, (W, d))
+            c[k + 1] = take(W, (W,))
+        a = take(W, (W,))
+        b = take(d, (d,))
+        assert o == t.size
+        return ModelSpec(d, W, L, self.kin, self.fibres.copy(), W1, Ak, Bk, c, a, b, self.kappa,
+                         self.stress_free, dict(self.extra))
+
+
+def n_params(d: int, W: int, L: int, bias: bool = True) -> int:
+    """Number of learnable parameters of the MICNN (eq. icnn), with or without biases."""
+    n = W * d + (L - 1) * (W * W + W * d) + W + d
+    return n + (L * W if bias else 0)
+
+
+def micnn_weights(rng: np.random.Generator, d: int, W: int, L: int, std: float = 0.1,
+                  bias_std: float | None = None) -> dict:
+    """Non-negative weights |N(0, std)| layer by layer; biases N(0, bias_std) or zero."""
+    def nonneg(shape):
+        return np.abs(rng.normal(0.0, std, size=shape))
+
+    def bias(n):
+        return rng.normal(0.0, bias_std, size=n) if bias_std else np.zeros(n)
+    W1 = nonneg((W, d))
+    c = np.zeros((L, W))
+    c[0] = bias(W)
+    Ak = np.zeros((max(L - 1, 0), W, W))
+    Bk = np.zeros((max(L - 1, 0), W, d))
+    for k in range(L - 1):
+        Ak[k] = nonneg((W, W))
+        Bk[k] = nonneg((W, d))
+        c[k + 1] = bias(W)
+    a = nonneg(W)
+    b = nonneg(d)
+    return dict(W1=W1, Ak=Ak, Bk=Bk, c=c, a=a, b=b)
+
+
+def make_model(rng, kin: int, n_fib: int, W: int, L: int, kappa: float, std: float = 0.1,
+               bias_std: float | None = None, stress_free: bool = False) -> ModelSpec:
+    d = 3 if kin == KIN_ISO_SHIFTED else 3 + 2 * n_fib
+    fib = FIBRES_PM30[:n_fib].copy() if n_fib else np.zeros((0, 3))
+    w = micnn_weights(rng, d, W, L, std, bias_std)
+    return ModelSpec(d=d, W=W, L=L, kin=kin, fibres=fib, kappa=kappa, stress_free=stress_free, **w)
+
+
+# ----------------------------------------------------------------------- meshes
+
+@dataclass
+class Mesh:
+    """Hex8 mesh: X[n_nodes][3] (float64), conn[n_el][8] (int32), nodes lexicographic."""
+    X: np.ndarray
+    conn: np.ndarray
+    n: tuple
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.X.shape[0])
+
+    @property
+    def n_el(self) -> int:
+        return int(self.conn.shape[0])
+
+
+def structured_mesh(nx: int, ny: int | None = None, nz: int | None = None,
+                    lengths=(1.0, 1.0, 1.0)) -> Mesh:
+    """Box [0,Lx]x[0,Ly]x[0,Lz] split into nx*ny*nz hex8 elements.
+
+    Node (i, j, k) has index i + (nx+1) (j + (ny+1) k); element nodes follow the
+    lexicographic reference order (x fastest), element (i, j, k) has index
+    i + nx (j + ny k).
+    """
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    xs = np.linspace(0.0, lengths[0], nx + 1)
+    ys = np.linspace(0.0, lengths[1], ny + 1)
+    zs = np.linspace(0.0, lengths[2], nz + 1)
+    Z, Y, Xc = np.meshgrid(zs, ys, xs, indexing="ij")
+    X = np.stack([Xc.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    sx, sy = 1, nx + 1
+    sz = (nx + 1) * (ny + 1)
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    base = (i + sy * j + sz * k).ravel().astype(np.int64)
+    offs = np.array([0, sx, sy, sx + sy, sz, sz + sx, sz + sy, sz + sx + sy], dtype=np.int64)
+    conn = (base[:, None] + offs[None, :]).astype(np.int32)
+    return Mesh(X=X, conn=conn, n=(nx, ny, nz))
+
+
+def dof_count(nx: int, ny: int | None = None, nz: int | None = None) -> int:
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    return 3 * (nx + 1) * (ny + 1) * (nz + 1)
+
+
+# ------------------------------------------------------------ deformation inputs
+
+def random_F(rng: np.random.Generator, n_qp: int, scale: float) -> np.ndarray:
+    """F = I + scale*N(0,1) per entry per point, [n_qp][9]; points with det F <= 0 are
+    redrawn in index order from the same stream until every det F > 0."""
+    F = np.eye(3).ravel()[None, :] + scale * rng.normal(size=(n_qp, 9))
+    while True:
+        bad = np.nonzero(np.linalg.det(F.reshape(-1, 3, 3)) <= 0.0)[0]
+        if bad.size == 0:
+            return F
+        F[bad] = np.eye(3).ravel()[None, :] + scale * rng.normal(size=(bad.size, 9))
+
+
+def uniaxial_F(rng: np.random.Generator, n_qp: int, lo: float = 0.7, hi: float = 1.5,
+               noise: float = 0.02) -> np.ndarray:
+    """F = diag(lam, 1, 1) + noise*N(0,1), lam ~ U[lo, hi] per point, [n_qp][9]
+    (the uniaxial-tension family of App. C with a perturbation); det F > 0 by redraw."""
+    N = rng.normal(size=(n_qp, 9))
+    lam = rng.uniform(lo, hi, size=n_qp)
+    F = noise * N
+    F[:, 0] += lam
+    F[:, 4] += 1.0
+    F[:, 8] += 1.0
+    while True:
+        bad = np.nonzero(np.linalg.det(F.reshape(-1, 3, 3)) <= 0.0)[0]
+        if bad.size == 0:
+            return F
+        Nb = rng.normal(size=(bad.size, 9))
+        lb = rng.uniform(lo, hi, size=bad.size)
+        F[bad] = noise * Nb
+        F[bad, 0] += lb
+        F[bad, 4] += 1.0
+        F[bad, 8] += 1.0
+
+
+def nodal_noise(rng: np.random.Generator, mesh: Mesh, scale: float) -> np.ndarray:
+    """u = scale*N(0,1) per nodal component, [n_nodes][3]."""
+    return scale * rng.normal(size=(mesh.n_nodes, 3))
+
+
+def cantilever_u(mesh: Mesh, seed: int, delta: float = 0.1, noise_h: float = 0.1) -> np.ndarray:
+    """End-loaded cantilever along x on the unit cube, [n_nodes][3]:
+    u_z = delta x^2 (3 - x) / 2, u_x = -(z - 1/2) du_z/dx, plus noise_h*h*N(0,1) per
+    nodal component (h = element size along x) everywhere except the clamped face x = 0,
+    where u = 0."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x, z = mesh.X[:, 0], mesh.X[:, 2]
+    uz = delta * x * x * (3.0 - x) / 2.0
+    duz = delta * (6.0 * x - 3.0 * x * x) / 2.0
+    u = np.zeros_like(mesh.X)
+    u[:, 2] = uz
+    u[:, 0] = -(z - 0.5) * duz
+    h = 1.0 / mesh.n[0]
+    u += noise_h * h * rng.normal(size=u.shape)
+    u[x == 0.0] = 0.0
+    return u
+
+
+def loading_path(kind: str, gamma: float) -> np.ndarray:
+    """Deformation gradients of the six loading paths of App. C (UT, UC, BT, BC, SS, PS), [9]."""
+    g = gamma
+    F = np.eye(3)
+    if kind == "UT":
+        F[0, 0] = 1 + g
+    elif kind == "UC":
+        F[0, 0] = 1 / (1 + g)
+    elif kind == "BT":
+        F[0, 0] = F[1, 1] = 1 + g
+    elif kind == "BC":
+        F[0, 0] = F[1, 1] = 1 / (1 + g)
+    elif kind == "SS":
+        F[0, 1] = g
+    elif kind == "PS":
+        F[0, 0] = 1 + g
+        F[1, 1] = 1 / (1 + g)
+    else:
+        raise ValueError(kind)
+    return F.ravel()
+
+
+# ------------------------------------------------------------------- workloads
+
+def workload_c0():
+    """Plain FP64: 8^3 unit cube, 512 elements, 4096 qp; isotropic MICNN d3 W16 L2,
+    kappa 10; u = 0.05 h N(0,1) per nodal component (h = 1/8, the element edge), seed 0.
+    At this amplitude every Gauss point has det F > 0 (checked by the CPU tests)."""
+    rng = np.random.Generator(np.random.PCG64(0))
+    model = make_model(rng, KIN_ISO_SHIFTED, 0, W=16, L=2, kappa=10.0)
+    mesh = structured_mesh(8)
+    u = nodal_noise(rng, mesh, scale=0.05 / 8)
+    return dict(name="c0_cube8_iso_d3w16l2", model=model, mesh=mesh, u=u)
+
+
+def workload_c1(n: int = 64, seed: int = 1):
+    """Anisotropic: n^3 hex8 mesh, 8 qp per element (element e owns qp 8e..8e+7);
+    two fibres at +-30 deg; raw inputs (Ibar1, Ibar2, J, I4_11, I4_22, I5_11, I5_22);
+    MICNN W32 L3, kappa 0; F = I + 0.15 N(0,1) per point."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    model = make_model(rng, KIN_RAW, 2, W=32, L=3, kappa=0.0)
+    mesh = structured_mesh(n)
+    F = random_F(rng, 8 * mesh.n_el, 0.15)
+    return dict(name=f"c1_aniso_{n}cube_d7w32l3", model=model, mesh=mesh, F=F)
+
+
+def workload_c2(n: int = 128, seed: int = 2):
+    """Precision: n^3 mesh (8 n^3 qp); isotropic MICNN d3 W64 L3; uniaxial stretch
+    lam in [0.7, 1.5] plus 0.02 N(0,1)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    model = make_model(rng, KIN_ISO_SHIFTED, 0, W=64, L=3, kappa=10.0)
+    mesh = structured_mesh(n)
+    F = uniaxial_F(rng, 8 * mesh.n_el)
+    return dict(name=f"c2_uniaxial_{n}cube_d3w64l3", model=model, mesh=mesh, F=F)
+
+
+def workload_c3(n_qp: int = 1 << 20, seed: int = 3):
+    """Differentiation: the C1 network (seed 1 weights), n_qp points F = I + 0.15 N(0,1)
+    drawn from seed 3; target model Neo-Hookean plus fibres (mu 1, k1 2, k2 0.5, kappa 10)."""
+    model = workload_c1(n=1)["model"]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    F = random_F(rng, n_qp, 0.15)
+    target = dict(mu=1.0, k1=2.0, k2=0.5, kappa=10.0)
+    return dict(name=f"c3_backward_{n_qp}qp_d7w32l3", model=model, F=F, target=target)
+
+
+def workload_c4(n: int = 96, seed: int = 4):
+    """Newton hot path: n^3 cantilever, anisotropic d7 W32 L3 network (C1 weights),
+    end-load displacement field."""
+    model = workload_c1(n=1)["model"]
+    mesh = structured_mesh(n)
+    u = cantilever_u(mesh, seed)
+    return dict(name=f"c4_cantilever_{n}cube_d7w32l3", model=model, mesh=mesh, u=u)
