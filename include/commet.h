@@ -1,0 +1,192 @@
+/*
+ * commet.h -- C ABI of the GB300 (sm_103a) neural-constitutive hot path.
+ *
+ * The operation is the constitutive call of COMMET's batch-vectorised assembly
+ * (Algorithm 2/3: {Psi},{tau},{c} <- vectorized_constitutive_model({F})), written
+ * in material form (App. A.1: P = dPsi/dF, A = C^P = d2Psi/dF dF), followed by the
+ * element integrals of eq. r-quad / k-quad and their sum into the global residual
+ * and stiffness (Sec. 2.1, Algorithm 1).
+ *
+ * Conventions (all entry points):
+ *  - F_iJ at component 3*i + J; A_iJkL = dP_iJ/dF_kL at component (3*i+J)*9 + 3*k+L.
+ *  - Per-qp tables are structure-of-arrays, component-major: X[c * n_qp + q].
+ *    Per-element tables likewise: f_e[r * n_el + e], K_e[(24*r + s) * n_el + e].
+ *  - Element e owns quadrature points 8e..8e+7 (2x2x2 Gauss, lexicographic, x fastest);
+ *    hex8 nodes are lexicographic in the reference cube; element dof 3*I + i;
+ *    global dof 3*node + i (the node-major block layout of Sec. 2.1).
+ *  - Every pointer passed to a compute call is a DEVICE pointer owned by the caller,
+ *    except where a comment says "host". The library never frees caller memory and
+ *    allocates nothing in compute calls; model/mesh creation allocates device memory
+ *    owned by the returned handle.
+ *  - Compute calls are asynchronous on `stream` (a cudaStream_t, NULL = legacy default
+ *    stream). Arguments are checked on the host before any launch; a failed check
+ *    returns an error code and launches nothing.
+ *  - Element type of P/A/F/u/r/K buffers: double for COMMET_F64 handles, float for
+ *    COMMET_F32 and COMMET_BF16_MLP handles.
+ *  - Data errors (J <= 0 or a non-finite result at a qp) do not abort: the affected
+ *    outputs are set to NaN and, when `status` (device int32[2]) is given, status[0]
+ *    receives the number of such qp and status[1] the smallest such qp index
+ *    (INT32_MAX when none). The call resets `status` itself, in stream order.
+ */
+#ifndef COMMET_H
+#define COMMET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define COMMET_OK 0
+#define COMMET_ERR_INVALID_ARG 1 /* NULL where required, bad size, bad enum, misaligned pointer */
+#define COMMET_ERR_UNSUPPORTED 2 /* shape, precision or kinematics not built into this library */
+#define COMMET_ERR_CUDA 3        /* a CUDA runtime call or kernel launch failed */
+#define COMMET_ERR_NO_CSR 4      /* the mesh was created without the CSR pattern */
+
+/* ---- precisions ---- */
+#define COMMET_F64 0      /* everything in double */
+#define COMMET_F32 1      /* everything in float */
+#define COMMET_BF16_MLP 2 /* hidden W x W layers on bf16 tensor cores (fp32 accumulate), rest fp32 */
+
+/* ---- kinematic layers (Sec. 2.2 eq. comp-se; App. A.2) ---- */
+#define COMMET_KIN_ISO_SHIFTED 0 /* K = (Ibar1 - 3, Ibar2 - 3, J - 1), d = 3, no fibres */
+#define COMMET_KIN_RAW 1         /* K = (Ibar1, Ibar2, J, I4_11..I4_nn, I5_11..I5_nn), d = 3 + 2n */
+
+#define COMMET_ACT_SOFTPLUS 0 /* F(y) = log(1 + exp(y)), the only activation built */
+
+typedef struct commet_model commet_model;
+typedef struct commet_mesh commet_mesh;
+
+/*
+ * Strain energy Psi(F) = N(K(F, {A^i})) + kappa (J - 1)^2  [- n0 . (K - K(I)) if stress_free]
+ * with N the monotone input-convex network of App. B, eq. icnn:
+ *   y1 = W1 K + c1 ; z_k = softplus(y_k) ;
+ *   y_k = A_k z_{k-1} + B_k K + c_k (k = 2..L) ; N = a_out . z_L + b_out . K.
+ * (Layer 1's A^(1) z^(0) and B^(1) K act on the same vector K and are one matrix W1.)
+ * stress_free subtracts the linear term n0 = dN/dK at K(I) so that P(I) = 0.
+ * All arrays are HOST row-major double; they are copied at creation.
+ */
+typedef struct commet_model_desc {
+    int32_t kinematics;   /* COMMET_KIN_* */
+    int32_t n_fibres;     /* structural vectors, 0..2 (must be 0 for ISO_SHIFTED) */
+    const double *fibres; /* [n_fibres][3] reference vectors A^i */
+    int32_t d;            /* network inputs; must equal the kinematic layer's count */
+    int32_t W;            /* hidden width; built: 16, 32, 64 */
+    int32_t L;            /* hidden layers, >= 1 */
+    const double *W1;     /* [W][d] */
+    const double *A;      /* [L-1][W][W] (may be NULL when L == 1) */
+    const double *B;      /* [L-1][W][d] (may be NULL when L == 1) */
+    const double *c;      /* [L][W] biases, or NULL for zero biases */
+    const double *a_out;  /* [W] */
+    const double *b_out;  /* [d] */
+    int32_t activation;   /* COMMET_ACT_SOFTPLUS */
+    double kappa;         /* volumetric penalty; 0 = none */
+    int32_t stress_free;  /* 0 or 1 */
+} commet_model_desc;
+
+/*
+ * Create a model handle for one precision. Copies the weights to the current CUDA
+ * device in the layouts the kernels use. Synchronous. *out is set on success only.
+ * Errors: INVALID_ARG (NULL, d inconsistent with the kinematics, negative sizes),
+ * UNSUPPORTED (W or n_fibres not built, activation unknown), CUDA.
+ */
+int commet_model_create(const commet_model_desc *desc, int32_t precision, commet_model **out);
+int commet_model_destroy(commet_model *m);
+/* Number of parameters theta = [W1, c1, (A_k, B_k, c_k) for k = 2..L, a_out, b_out]. */
+int64_t commet_model_n_params(const commet_model *m);
+
+/*
+ * Constitutive update (Algorithm 2, "vectorized_constitutive_model", material form,
+ * chain rule of eq. nncm-chain): for every qp q < n_qp,
+ *   psi[q] = Psi(F_q), P[:, q] = dPsi/dF (9), A[:, q] = d2Psi/dF dF (81).
+ * F   [9][n_qp]  in.
+ * psi [n_qp]     out, or NULL.
+ * P   [9][n_qp]  out (required).
+ * A   [81][n_qp] out, or NULL (stress only).
+ * status: device int32[2] or NULL (see top of file).
+ * n_qp == 0 is a no-op returning COMMET_OK. Pointers must be 16-byte aligned.
+ */
+int commet_const_update(const commet_model *m, int64_t n_qp, const void *F, void *psi, void *P, void *A,
+                        int32_t *status, void *stream);
+
+/*
+ * Mesh of hex8 elements (App. -: deal.II-style Q1 bricks). X (host, double [n_nodes][3])
+ * and conn (host, int32 [n_el][8], lexicographic node order) are copied to the device.
+ * want_csr = 1 also builds, on the host, the CSR pattern of the global stiffness
+ * (rows 3*node+i; columns of every node sharing an element, 3 per node, sorted),
+ * an element -> CSR position map (one int32 per element node pair), and an element
+ * colouring in which no two elements of one colour share a node (greedy, in element
+ * order). Synchronous. Errors: INVALID_ARG (node index out of range, NULL, sizes),
+ * UNSUPPORTED (nnz >= 2^31), CUDA.
+ */
+int commet_mesh_create(int64_t n_nodes, const double *X, int64_t n_el, const int32_t *conn, int32_t want_csr,
+                       commet_mesh **out);
+int commet_mesh_destroy(commet_mesh *mesh);
+/* Sizes of the CSR pattern and colouring: n_rows = 3 n_nodes, nnz, n_colours. */
+int commet_mesh_info(const commet_mesh *mesh, int64_t *n_rows, int64_t *nnz, int32_t *n_colours);
+/* Copy the CSR pattern to HOST arrays rowptr[n_rows + 1] (int64) and col[nnz] (int32). */
+int commet_mesh_csr(const commet_mesh *mesh, int64_t *rowptr, int32_t *col);
+
+/*
+ * Deformation gradient at every qp (Algorithm 1, "trial F"):
+ *   F_q = I + sum_I u^I (x) grad_X phi^I(xi_q), grad_X phi = Je^{-T} grad_xi phi.
+ * u [3][n_nodes] in (precision of `precision`: COMMET_F64 -> double, else float);
+ * F [9][8 n_el] out.
+ */
+int commet_compute_F(const commet_mesh *mesh, int32_t precision, const void *u, void *F, void *stream);
+
+/*
+ * Element integrals (eq. r-quad, k-quad, in material form via App. A.1):
+ *   f_e[3I+i]       = sum_q w_q P_iJ dphi_I/dX_J
+ *   K_e[3I+i][3K+k] = sum_q w_q dphi_I/dX_J A_iJkL dphi_K/dX_L,  w_q = det Je (Gauss weight 1)
+ * and, optionally, their sums over elements into the global residual and CSR
+ * stiffness (Algorithm 1; race-free by element colouring, one launch per colour).
+ * P [9][8 n_el], A [81][8 n_el] in (A may be NULL only when K_e and K_vals are NULL).
+ * f_e [24][n_el], K_e [576][n_el] out or NULL.
+ * r [3 n_nodes], K_vals [nnz] out or NULL: OVERWRITTEN (zeroed first, in stream order).
+ * Errors: NO_CSR when r or K_vals is given for a mesh built without the CSR pattern.
+ */
+int commet_elem_assemble(const commet_mesh *mesh, int32_t precision, const void *P, const void *A, void *f_e,
+                         void *K_e, void *r, void *K_vals, void *stream);
+
+/*
+ * Fused Newton-iteration assembly: u -> F -> (Psi, P, A) -> f_e, K_e -> r, K_vals for
+ * every element in one pass per colour, with P and A kept on chip (Algorithm 3 with
+ * the constitutive call fused into the element loop). r [3 n_nodes], K_vals [nnz]
+ * OVERWRITTEN; u [3][n_nodes]; types follow the model's precision (F32 or F64).
+ */
+int commet_newton_assemble(const commet_model *m, const commet_mesh *mesh, const void *u, void *r, void *K_vals,
+                           int32_t *status, void *stream);
+
+/*
+ * Backward of the constitutive update for an upstream gradient G = dL/dP [9][n_qp]:
+ *   dL_dF[:, q]   = sum_iJ G_iJ A_iJkL            (A of the forward at F_q)
+ *   dL_dtheta[p]  = sum_q d/dtheta_p [ G_q : P_q ]  (all network parameters, order as
+ *                   commet_model_n_params), summed over q in a fixed order
+ * Recomputes the forward per qp; stores no activations. dL_dF may be NULL.
+ * workspace: device scratch of commet_const_backward_workspace() bytes, 256-byte aligned.
+ * Deterministic: the same inputs give bitwise the same dL_dtheta.
+ */
+size_t commet_const_backward_workspace(const commet_model *m, int64_t n_qp);
+int commet_const_backward(const commet_model *m, int64_t n_qp, const void *F, const void *dL_dP, void *dL_dF,
+                          void *dL_dtheta, void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * Target stress of a closed-form Neo-Hookean-plus-fibre model, used as synthetic
+ * training data for the backward:
+ *   Psi_t = mu/2 (Ibar1 - 3) + kappa (J - 1)^2 + sum_f k1/(2 k2) (exp(k2 (I4_ff - 1)^2) - 1)
+ * fibres: HOST double [n_fibres][3]; F [9][n_qp] in, P [9][n_qp] out (precision as given).
+ */
+int commet_target_stress(int32_t precision, int64_t n_qp, const void *F, int32_t n_fibres, const double *fibres,
+                         double mu, double k1, double k2, double kappa, void *P, void *stream);
+
+/* Human-readable text for a return code (static storage). */
+const char *commet_status_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COMMET_H */

@@ -1,0 +1,345 @@
+// extern "C" boundary of libcommet: argument checks, handle construction, dispatch.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+using namespace commet;
+
+namespace {
+
+bool aligned16(const void *p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+size_t elem_size(int precision) { return precision == COMMET_F64 ? sizeof(double) : sizeof(float); }
+
+int round4(int x) { return (x + 3) / 4 * 4; }
+
+// Build the packed-weight layout (offsets in elements, each block starting on a
+// multiple of 4 elements so that it is 16-byte aligned for float and double).
+NetLayout make_layout(int d, int W, int L) {
+    NetLayout l{};
+    l.d = d;
+    l.W = W;
+    l.L = L;
+    const int dp = (d + 3) / 4 * 4;
+    int o = 0;
+    l.W1t = o; o = round4(o + d * W);
+    l.W1r = o; o = round4(o + W * dp);
+    l.At = o; o = round4(o + (L - 1) * W * W);
+    l.Ar = o; o = round4(o + (L - 1) * W * W);
+    l.Bt = o; o = round4(o + (L - 1) * d * W);
+    l.c = o; o = round4(o + L * W);
+    l.a = o; o = round4(o + W);
+    l.b = o; o = round4(o + d);
+    l.n0 = o; o = round4(o + d);
+    l.K0 = o; o = round4(o + d);
+    l.total = o;
+    return l;
+}
+
+template <typename T>
+int upload(const std::vector<double> &h, void **dptr) {
+    const size_t bytes = (h.size() * sizeof(T) + 15) / 16 * 16;
+    std::vector<unsigned char> buf(bytes, 0);
+    T *t = reinterpret_cast<T *>(buf.data());
+    for (size_t i = 0; i < h.size(); ++i) t[i] = (T)h[i];
+    COMMET_CUDA_TRY(cudaMalloc(dptr, bytes));
+    COMMET_CUDA_TRY(cudaMemcpy(*dptr, buf.data(), bytes, cudaMemcpyHostToDevice));
+    return COMMET_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *commet_status_string(int code) {
+    switch (code) {
+        case COMMET_OK: return "ok";
+        case COMMET_ERR_INVALID_ARG: return "invalid argument";
+        case COMMET_ERR_UNSUPPORTED: return "unsupported shape, precision or kinematics";
+        case COMMET_ERR_CUDA: return "CUDA error";
+        case COMMET_ERR_NO_CSR: return "mesh has no CSR pattern";
+        default: return "unknown status code";
+    }
+}
+
+int commet_model_create(const commet_model_desc *desc, int32_t precision, commet_model **out) {
+    if (desc == nullptr || out == nullptr) return COMMET_ERR_INVALID_ARG;
+    if (precision != COMMET_F64 && precision != COMMET_F32 && precision != COMMET_BF16_MLP)
+        return COMMET_ERR_INVALID_ARG;
+    if (desc->kinematics != COMMET_KIN_ISO_SHIFTED && desc->kinematics != COMMET_KIN_RAW)
+        return COMMET_ERR_INVALID_ARG;
+    if (desc->n_fibres < 0 || desc->L < 1 || desc->W < 1 || desc->d < 1) return COMMET_ERR_INVALID_ARG;
+    if (desc->kinematics == COMMET_KIN_ISO_SHIFTED && desc->n_fibres != 0) return COMMET_ERR_INVALID_ARG;
+    if (desc->n_fibres > kMaxFibres) return COMMET_ERR_UNSUPPORTED;
+    const int d_expect = desc->kinematics == COMMET_KIN_ISO_SHIFTED ? 3 : 3 + 2 * desc->n_fibres;
+    if (desc->d != d_expect) return COMMET_ERR_INVALID_ARG;
+    if (desc->activation != COMMET_ACT_SOFTPLUS) return COMMET_ERR_UNSUPPORTED;
+    if (desc->W1 == nullptr || desc->a_out == nullptr || desc->b_out == nullptr) return COMMET_ERR_INVALID_ARG;
+    if (desc->L > 1 && (desc->A == nullptr || desc->B == nullptr)) return COMMET_ERR_INVALID_ARG;
+    if (desc->n_fibres > 0 && desc->fibres == nullptr) return COMMET_ERR_INVALID_ARG;
+    if (!(std::isfinite(desc->kappa))) return COMMET_ERR_INVALID_ARG;
+    const int W = desc->W, d = desc->d, L = desc->L;
+    if (W != 16 && W != 32 && W != 64) return COMMET_ERR_UNSUPPORTED;
+    if (L > 16) return COMMET_ERR_UNSUPPORTED;
+
+    commet_model *m = new (std::nothrow) commet_model();
+    if (!m) return COMMET_ERR_CUDA;
+    m->precision = precision;
+    m->d = d;
+    m->W = W;
+    m->L = L;
+    m->kp.kin = desc->kinematics;
+    m->kp.nf = desc->n_fibres;
+    for (int f = 0; f < desc->n_fibres; ++f)
+        for (int c = 0; c < 3; ++c) m->kp.fib[f][c] = desc->fibres[3 * f + c];
+    m->kp.kappa = desc->kappa;
+    m->kp.stress_free = desc->stress_free ? 1 : 0;
+    m->lay = make_layout(d, W, L);
+    m->n_params = (int64_t)W * d + W + (int64_t)(L - 1) * ((int64_t)W * W + (int64_t)W * d + W) + W + d;
+    cudaGetDevice(&m->device);
+
+    const NetLayout &l = m->lay;
+    const int dp = (d + 3) / 4 * 4;
+    std::vector<double> h(l.total, 0.0);
+    for (int j = 0; j < W; ++j)
+        for (int mm = 0; mm < d; ++mm) {
+            h[l.W1t + mm * W + j] = desc->W1[j * d + mm];
+            h[l.W1r + j * dp + mm] = desc->W1[j * d + mm];
+        }
+    for (int k = 0; k < L - 1; ++k) {
+        const double *Ak = desc->A + (size_t)k * W * W;
+        const double *Bk = desc->B + (size_t)k * W * d;
+        for (int j = 0; j < W; ++j) {
+            for (int i = 0; i < W; ++i) {
+                h[l.At + k * W * W + i * W + j] = Ak[j * W + i];
+                h[l.Ar + k * W * W + j * W + i] = Ak[j * W + i];
+            }
+            for (int mm = 0; mm < d; ++mm) h[l.Bt + k * d * W + mm * W + j] = Bk[j * d + mm];
+        }
+    }
+    for (int k = 0; k < L; ++k)
+        for (int j = 0; j < W; ++j) h[l.c + k * W + j] = desc->c ? desc->c[k * W + j] : 0.0;
+    for (int j = 0; j < W; ++j) h[l.a + j] = desc->a_out[j];
+    for (int mm = 0; mm < d; ++mm) h[l.b + mm] = desc->b_out[mm];
+
+    int rc;
+    if (precision == COMMET_F64)
+        rc = upload<double>(h, &m->d_weights);
+    else
+        rc = upload<float>(h, &m->d_weights);
+    if (rc != COMMET_OK) {
+        commet_model_destroy(m);
+        return rc;
+    }
+    if (m->kp.stress_free) {
+        // n0 = dN/dK and K0 = K at F = I, evaluated by the constitutive kernel itself
+        const size_t es = elem_size(precision == COMMET_F64 ? COMMET_F64 : COMMET_F32);
+        void *dF = nullptr, *dP = nullptr, *dN = nullptr;
+        const double I9[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+        unsigned char Fbuf[9 * sizeof(double)];
+        for (int c = 0; c < 9; ++c) {
+            if (es == 8)
+                reinterpret_cast<double *>(Fbuf)[c] = I9[c];
+            else
+                reinterpret_cast<float *>(Fbuf)[c] = (float)I9[c];
+        }
+        commet_model tmp = *m;
+        tmp.precision = (precision == COMMET_F64) ? COMMET_F64 : COMMET_F32;
+        rc = COMMET_ERR_CUDA;
+        if (cudaMalloc(&dF, 16 * es) == cudaSuccess && cudaMalloc(&dP, 16 * es) == cudaSuccess &&
+            cudaMalloc(&dN, 2 * kMaxD * es) == cudaSuccess &&
+            cudaMemcpy(dF, Fbuf, 9 * es, cudaMemcpyHostToDevice) == cudaSuccess) {
+            rc = launch_const_update(&tmp, 1, dF, nullptr, dP, nullptr, nullptr, 0, dN);
+            if (rc == COMMET_OK && cudaDeviceSynchronize() != cudaSuccess) rc = COMMET_ERR_CUDA;
+            if (rc == COMMET_OK) {
+                unsigned char *wb = reinterpret_cast<unsigned char *>(m->d_weights);
+                if (cudaMemcpy(wb + l.n0 * es, dN, d * es, cudaMemcpyDeviceToDevice) != cudaSuccess ||
+                    cudaMemcpy(wb + l.K0 * es, (unsigned char *)dN + d * es, d * es, cudaMemcpyDeviceToDevice) !=
+                        cudaSuccess)
+                    rc = COMMET_ERR_CUDA;
+            }
+        }
+        cudaFree(dF);
+        cudaFree(dP);
+        cudaFree(dN);
+        if (rc != COMMET_OK) {
+            commet_model_destroy(m);
+            return rc;
+        }
+    }
+    *out = m;
+    return COMMET_OK;
+}
+
+int commet_model_destroy(commet_model *m) {
+    if (m == nullptr) return COMMET_ERR_INVALID_ARG;
+    cudaFree(m->d_weights);
+    cudaFree(m->d_theta64);
+    cudaFree(m->d_bf16);
+    delete m;
+    return COMMET_OK;
+}
+
+int64_t commet_model_n_params(const commet_model *m) { return m ? m->n_params : -1; }
+
+int commet_const_update(const commet_model *m, int64_t n_qp, const void *F, void *psi, void *P, void *A,
+                        int32_t *status, void *stream) {
+    if (m == nullptr || n_qp < 0) return COMMET_ERR_INVALID_ARG;
+    if (n_qp > 0 && (F == nullptr || P == nullptr)) return COMMET_ERR_INVALID_ARG;
+    if (!aligned16(F) || !aligned16(P) || !aligned16(A) || !aligned16(psi) ||
+        (reinterpret_cast<uintptr_t>(status) & 7u) != 0)
+        return COMMET_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (m->precision == COMMET_BF16_MLP) {
+        if (status) {
+            int rc = launch_status_init(status, s);
+            if (rc != COMMET_OK) return rc;
+        }
+        if (n_qp == 0) return COMMET_OK;
+        return launch_const_update_bf16(m, n_qp, F, psi, P, A, status, s);
+    }
+    return launch_const_update(m, n_qp, F, psi, P, A, status, s, nullptr);
+}
+
+int commet_target_stress(int32_t precision, int64_t n_qp, const void *F, int32_t n_fibres, const double *fibres,
+                         double mu, double k1, double k2, double kappa, void *P, void *stream) {
+    if (precision != COMMET_F64 && precision != COMMET_F32) return COMMET_ERR_INVALID_ARG;
+    if (n_qp < 0 || n_fibres < 0 || n_fibres > kMaxFibres) return COMMET_ERR_INVALID_ARG;
+    if (n_fibres > 0 && fibres == nullptr) return COMMET_ERR_INVALID_ARG;
+    if (n_qp > 0 && (F == nullptr || P == nullptr)) return COMMET_ERR_INVALID_ARG;
+    if (!(k2 > 0.0) || !std::isfinite(mu) || !std::isfinite(k1) || !std::isfinite(kappa))
+        return COMMET_ERR_INVALID_ARG;
+    if (n_qp == 0) return COMMET_OK;
+    return launch_target_stress(precision, n_qp, F, n_fibres, fibres, mu, k1, k2, kappa, P,
+                                reinterpret_cast<cudaStream_t>(stream));
+}
+
+// ------------------------------------------------------------------------ mesh
+
+int commet_mesh_create(int64_t n_nodes, const double *X, int64_t n_el, const int32_t *conn, int32_t want_csr,
+                       commet_mesh **out) {
+    if (out == nullptr || n_nodes < 0 || n_el < 0) return COMMET_ERR_INVALID_ARG;
+    if ((n_nodes > 0 && X == nullptr) || (n_el > 0 && conn == nullptr)) return COMMET_ERR_INVALID_ARG;
+    if (n_nodes >= ((int64_t)1 << 31) / 3 || n_el >= ((int64_t)1 << 31) / 8) return COMMET_ERR_UNSUPPORTED;
+    for (int64_t i = 0; i < 8 * n_el; ++i)
+        if (conn[i] < 0 || conn[i] >= n_nodes) return COMMET_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < 3 * n_nodes; ++i)
+        if (!std::isfinite(X[i])) return COMMET_ERR_INVALID_ARG;
+    commet_mesh *mesh = new (std::nothrow) commet_mesh();
+    if (!mesh) return COMMET_ERR_CUDA;
+    mesh->n_nodes = n_nodes;
+    mesh->n_el = n_el;
+    cudaGetDevice(&mesh->device);
+    int rc = COMMET_OK;
+    if (cudaMalloc(&mesh->d_X, sizeof(double) * 3 * std::max<int64_t>(1, n_nodes)) != cudaSuccess ||
+        cudaMalloc(&mesh->d_conn, sizeof(int32_t) * 8 * std::max<int64_t>(1, n_el)) != cudaSuccess)
+        rc = COMMET_ERR_CUDA;
+    if (rc == COMMET_OK && n_nodes > 0 &&
+        cudaMemcpy(mesh->d_X, X, sizeof(double) * 3 * n_nodes, cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = COMMET_ERR_CUDA;
+    if (rc == COMMET_OK && n_el > 0 &&
+        cudaMemcpy(mesh->d_conn, conn, sizeof(int32_t) * 8 * n_el, cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = COMMET_ERR_CUDA;
+    if (rc == COMMET_OK && want_csr) rc = build_csr_and_colouring(n_nodes, n_el, conn, mesh);
+    if (rc != COMMET_OK) {
+        commet_mesh_destroy(mesh);
+        return rc;
+    }
+    *out = mesh;
+    return COMMET_OK;
+}
+
+int commet_mesh_destroy(commet_mesh *mesh) {
+    if (mesh == nullptr) return COMMET_ERR_INVALID_ARG;
+    cudaFree(mesh->d_X);
+    cudaFree(mesh->d_Xf);
+    cudaFree(mesh->d_conn);
+    cudaFree(mesh->d_rowptr);
+    cudaFree(mesh->d_col);
+    cudaFree(mesh->d_emap);
+    cudaFree(mesh->d_rowlen);
+    cudaFree(mesh->d_colour_el);
+    delete[] mesh->h_rowptr;
+    delete[] mesh->h_col;
+    delete mesh;
+    return COMMET_OK;
+}
+
+int commet_mesh_info(const commet_mesh *mesh, int64_t *n_rows, int64_t *nnz, int32_t *n_colours) {
+    if (mesh == nullptr) return COMMET_ERR_INVALID_ARG;
+    if (n_rows) *n_rows = 3 * mesh->n_nodes;
+    if (nnz) *nnz = mesh->nnz;
+    if (n_colours) *n_colours = mesh->n_colours;
+    return COMMET_OK;
+}
+
+int commet_mesh_csr(const commet_mesh *mesh, int64_t *rowptr, int32_t *col) {
+    if (mesh == nullptr || rowptr == nullptr || col == nullptr) return COMMET_ERR_INVALID_ARG;
+    if (mesh->h_rowptr == nullptr) return COMMET_ERR_NO_CSR;
+    std::memcpy(rowptr, mesh->h_rowptr, sizeof(int64_t) * (mesh->n_rows + 1));
+    std::memcpy(col, mesh->h_col, sizeof(int32_t) * mesh->nnz);
+    return COMMET_OK;
+}
+
+int commet_compute_F(const commet_mesh *mesh, int32_t precision, const void *u, void *F, void *stream) {
+    if (mesh == nullptr || (precision != COMMET_F64 && precision != COMMET_F32 && precision != COMMET_BF16_MLP))
+        return COMMET_ERR_INVALID_ARG;
+    if (mesh->n_el > 0 && (u == nullptr || F == nullptr)) return COMMET_ERR_INVALID_ARG;
+    if (!aligned16(u) || !aligned16(F)) return COMMET_ERR_INVALID_ARG;
+    return launch_compute_F(mesh, precision == COMMET_F64 ? COMMET_F64 : COMMET_F32, u, F,
+                            reinterpret_cast<cudaStream_t>(stream));
+}
+
+int commet_elem_assemble(const commet_mesh *mesh, int32_t precision, const void *P, const void *A, void *f_e,
+                         void *K_e, void *r, void *K_vals, void *stream) {
+    if (mesh == nullptr || (precision != COMMET_F64 && precision != COMMET_F32 && precision != COMMET_BF16_MLP))
+        return COMMET_ERR_INVALID_ARG;
+    if (mesh->n_el > 0 && P == nullptr) return COMMET_ERR_INVALID_ARG;
+    if (A == nullptr && (K_e != nullptr || K_vals != nullptr)) return COMMET_ERR_INVALID_ARG;
+    if ((r != nullptr || K_vals != nullptr) && mesh->h_rowptr == nullptr) return COMMET_ERR_NO_CSR;
+    if (!aligned16(P) || !aligned16(A) || !aligned16(f_e) || !aligned16(K_e) || !aligned16(r) || !aligned16(K_vals))
+        return COMMET_ERR_INVALID_ARG;
+    return launch_elem_assemble(mesh, precision == COMMET_F64 ? COMMET_F64 : COMMET_F32, P, A, f_e, K_e, r, K_vals,
+                                reinterpret_cast<cudaStream_t>(stream));
+}
+
+int commet_newton_assemble(const commet_model *m, const commet_mesh *mesh, const void *u, void *r, void *K_vals,
+                           int32_t *status, void *stream) {
+    if (m == nullptr || mesh == nullptr) return COMMET_ERR_INVALID_ARG;
+    if (mesh->h_rowptr == nullptr) return COMMET_ERR_NO_CSR;
+    if (mesh->n_el > 0 && (u == nullptr || r == nullptr || K_vals == nullptr)) return COMMET_ERR_INVALID_ARG;
+    if (!aligned16(u) || !aligned16(r) || !aligned16(K_vals) || (reinterpret_cast<uintptr_t>(status) & 7u) != 0)
+        return COMMET_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (status) {
+        int rc = launch_status_init(status, s);
+        if (rc != COMMET_OK) return rc;
+    }
+    return launch_newton_assemble(m, mesh, u, r, K_vals, status, s);
+}
+
+size_t commet_const_backward_workspace(const commet_model *m, int64_t n_qp) {
+    if (m == nullptr || n_qp < 0) return 0;
+    return backward_workspace_bytes(m, n_qp);
+}
+
+int commet_const_backward(const commet_model *m, int64_t n_qp, const void *F, const void *dL_dP, void *dL_dF,
+                          void *dL_dtheta, void *workspace, size_t ws_bytes, void *stream) {
+    if (m == nullptr || n_qp < 0 || dL_dtheta == nullptr) return COMMET_ERR_INVALID_ARG;
+    if (n_qp > 0 && (F == nullptr || dL_dP == nullptr)) return COMMET_ERR_INVALID_ARG;
+    if (!aligned16(F) || !aligned16(dL_dP) || !aligned16(dL_dF) || !aligned16(dL_dtheta)) return COMMET_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return COMMET_ERR_INVALID_ARG;
+    if (ws_bytes < backward_workspace_bytes(m, n_qp) || (workspace == nullptr && ws_bytes > 0))
+        return COMMET_ERR_INVALID_ARG;
+    if (m->kp.stress_free) return COMMET_ERR_UNSUPPORTED;
+    return launch_const_backward(m, n_qp, F, dL_dP, dL_dF, dL_dtheta, workspace, ws_bytes,
+                                 reinterpret_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

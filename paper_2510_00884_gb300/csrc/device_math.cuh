@@ -1,0 +1,339 @@
+// Device-side kinematics and activation helpers shared by the constitutive kernels.
+//
+// The kinematic layer (Sec. 2.2, eq. comp-se; invariants eq. 454; isochoric
+// invariants App. A.2) is evaluated in material form: K_m(F), g_m = dK_m/dF and the
+// second derivatives contracted with the network gradient, sum_m c_m d2K_m/dF dF,
+// which is written as a short sum of structured terms instead of d 81-entry tensors:
+//
+//   A_iJkL = sum_mn N_mn g_m[iJ] g_n[kL]
+//          + U_iJ H_kL + H_iJ U_kL + beta H_iJ H_kL + gamma F_iJ F_kL        (rank one)
+//          - eta H_iL H_kJ + zeta F_iL F_kJ
+//          + sum_f 2 c5f (F_iL a_k A_J + a_i A_L F_kJ)                        (index swap)
+//          + d_ik X_JL + Y_ik d_JL + sum_f 2 c5f B_ik A_J A_L                 (products)
+//
+// with H = F^{-T}, B = F F^T, a = F A, v = C A, and coefficients built from
+// c_m = dN/dK_m, J, I1, I2, kappa (see stage_kinematics below).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "../../include/commet.h"
+
+namespace commet {
+
+template <typename T>
+struct KinConst {
+    int kin;          // COMMET_KIN_*
+    int stress_free;  // shift by n0
+    T kappa;
+    T fib[2][3];
+};
+
+// ---------------------------------------------------------------- activation
+// softplus z = log(1 + e^y), s = z' = logistic(y), t = z'' = s (1 - s) = e/(1+e)^2
+// with e = exp(-|y|) so that nothing overflows.
+__device__ __forceinline__ void act(double y, double &z, double &s, double &t) {
+    const double e = exp(-fabs(y));
+    const double r = 1.0 / (1.0 + e);
+    z = fmax(y, 0.0) + log1p(e);
+    s = (y >= 0.0) ? r : e * r;
+    t = e * r * r;
+}
+__device__ __forceinline__ void act(float y, float &z, float &s, float &t) {
+    const float e = __expf(-fabsf(y));
+    const float r = __frcp_rn(1.0f + e);
+    z = fmaxf(y, 0.0f) + log1pf(e);
+    s = (y >= 0.0f) ? r : e * r;
+    t = e * r * r;
+}
+__device__ __forceinline__ void act_value_slope(double y, double &z, double &s) {
+    const double e = exp(-fabs(y));
+    const double r = 1.0 / (1.0 + e);
+    z = fmax(y, 0.0) + log1p(e);
+    s = (y >= 0.0) ? r : e * r;
+}
+__device__ __forceinline__ void act_value_slope(float y, float &z, float &s) {
+    const float e = __expf(-fabsf(y));
+    const float r = __frcp_rn(1.0f + e);
+    z = fmaxf(y, 0.0f) + log1pf(e);
+    s = (y >= 0.0f) ? r : e * r;
+}
+
+__device__ __forceinline__ double dev_rcbrt(double x) { return rcbrt(x); }
+__device__ __forceinline__ float dev_rcbrt(float x) { return rcbrtf(x); }
+__device__ __forceinline__ bool dev_finite(double x) { return isfinite(x); }
+__device__ __forceinline__ bool dev_finite(float x) { return isfinite(x); }
+
+// ------------------------------------------------------------ basic kinematics
+
+// cofactor of F (cof F = J F^{-T}) and J = det F
+template <typename T>
+__device__ __forceinline__ void cof_det(const T *F, T *cof, T &J) {
+    cof[0] = F[4] * F[8] - F[5] * F[7];
+    cof[1] = F[5] * F[6] - F[3] * F[8];
+    cof[2] = F[3] * F[7] - F[4] * F[6];
+    cof[3] = F[2] * F[7] - F[1] * F[8];
+    cof[4] = F[0] * F[8] - F[2] * F[6];
+    cof[5] = F[1] * F[6] - F[0] * F[7];
+    cof[6] = F[1] * F[5] - F[2] * F[4];
+    cof[7] = F[2] * F[3] - F[0] * F[5];
+    cof[8] = F[0] * F[4] - F[1] * F[3];
+    J = F[0] * cof[0] + F[1] * cof[1] + F[2] * cof[2];
+}
+
+// C = F^T F (full 3x3)
+template <typename T>
+__device__ __forceinline__ void right_cg(const T *F, T *C) {
+#pragma unroll
+    for (int I = 0; I < 3; ++I)
+#pragma unroll
+        for (int J = I; J < 3; ++J) {
+            T s = F[I] * F[J] + F[3 + I] * F[3 + J] + F[6 + I] * F[6 + J];
+            C[3 * I + J] = s;
+            C[3 * J + I] = s;
+        }
+}
+
+// B = F F^T (full 3x3)
+template <typename T>
+__device__ __forceinline__ void left_cg(const T *F, T *B) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+            T s = F[3 * i] * F[3 * j] + F[3 * i + 1] * F[3 * j + 1] + F[3 * i + 2] * F[3 * j + 2];
+            B[3 * i + j] = s;
+            B[3 * j + i] = s;
+        }
+}
+
+// J - 1 = det F - 1 in double precision. The volumetric penalty 2 kappa (J - 1) and
+// the J - 1 network input cancel to a small difference near J = 1, so the FP32 path
+// also evaluates this one quantity in FP64 (a few dozen DFMA per point).
+__device__ __forceinline__ double det_minus_one(const double *F) {
+    double cof[9], J;
+    cof_det(F, cof, J);
+    return J - 1.0;
+}
+__device__ __forceinline__ float det_minus_one(const float *F) {
+    double Fd[9], cof[9], J;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) Fd[a] = (double)F[a];
+    cof_det(Fd, cof, J);
+    return (float)(J - 1.0);
+}
+
+// Kinematic scalars K (D = 3 + 2 NF entries) and Jm1 = J - 1. Returns false if
+// J <= 0 or F is not finite.
+template <typename T, int NF>
+__device__ __forceinline__ bool kin_scalars(const T *F, const KinConst<T> &kc, T *K, T &Jm1) {
+    Jm1 = det_minus_one(F);
+    const T J = T(1) + Jm1;
+    T C[9];
+    right_cg(F, C);
+    const T I1 = C[0] + C[4] + C[8];
+    T trC2 = 0;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) trC2 += C[a] * C[a];
+    const T I2 = T(0.5) * (I1 * I1 - trC2);
+    const bool ok = (J > T(0)) && dev_finite(Jm1) && dev_finite(I1);
+    const T r3 = dev_rcbrt(ok ? J : T(1));
+    const T jm23 = r3 * r3;
+    K[0] = jm23 * I1;
+    K[1] = jm23 * jm23 * I2;
+    K[2] = J;
+    if (kc.kin == COMMET_KIN_ISO_SHIFTED) {
+        K[0] -= T(3);
+        K[1] -= T(3);
+        K[2] = Jm1;
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        T v[3];
+#pragma unroll
+        for (int I = 0; I < 3; ++I) v[I] = C[3 * I] * kc.fib[f][0] + C[3 * I + 1] * kc.fib[f][1] + C[3 * I + 2] * kc.fib[f][2];
+        K[3 + f] = v[0] * kc.fib[f][0] + v[1] * kc.fib[f][1] + v[2] * kc.fib[f][2];
+        K[3 + NF + f] = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    }
+    return ok;
+}
+
+// Layout of the per-qp staging area written by stage_kinematics (units of T).
+template <int D, int NF>
+struct Stage {
+    static constexpr int g = 0;             // [D][9] g_m = dK_m/dF
+    static constexpr int F = 9 * D;         // [9]
+    static constexpr int H = F + 9;         // [9] F^{-T}
+    static constexpr int U = H + 9;         // [9]
+    static constexpr int X = U + 9;         // [9] (J, L)
+    static constexpr int Y = X + 9;         // [9] (i, k)
+    static constexpr int Bm = Y + 9;        // [9] left Cauchy-Green
+    static constexpr int aA = Bm + 9;       // [NF][9] a_f (x) A_f, [3k+J] = a_k A_J
+    static constexpr int AA = aA + 9 * NF;  // [NF][9] A_f (x) A_f
+    static constexpr int sc = AA + 9 * NF;  // beta, gamma, eta, zeta, 2 c5f (NF), 2 kappa (J-1) J
+    static constexpr int size = sc + 5 + NF;
+};
+
+// Writes the quantities every row of A needs into the qp's staging area. The four
+// threads of a qp group split the work by `part` (0..3). c[] = dN/dK - n0;
+// Jm1 = J - 1 from det_minus_one.
+template <typename T, int NF>
+__device__ __forceinline__ void stage_kinematics(const T *F, const KinConst<T> &kc, const T *c, T Jm1, int part,
+                                                 T *st) {
+    constexpr int D = 3 + 2 * NF;
+    using S = Stage<D, NF>;
+    T cof[9], Jc, C[9];
+    cof_det(F, cof, Jc);
+    const T J = T(1) + Jm1;
+    right_cg(F, C);
+    const T I1 = C[0] + C[4] + C[8];
+    T trC2 = 0;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) trC2 += C[a] * C[a];
+    const T I2 = T(0.5) * (I1 * I1 - trC2);
+    const T r3 = dev_rcbrt(J);
+    const T jm23 = r3 * r3, jm43 = jm23 * jm23;
+    const T iJ = T(1) / J;
+    T H[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) H[a] = cof[a] * iJ;
+    // raw dI2/dF = 2 (I1 F - F C)
+    T gI2[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int L = 0; L < 3; ++L)
+            gI2[3 * i + L] = T(2) * (I1 * F[3 * i + L] - (F[3 * i] * C[L] + F[3 * i + 1] * C[3 + L] + F[3 * i + 2] * C[6 + L]));
+    const T p1 = T(-2) / T(3), p2 = T(-4) / T(3);
+    const T c1 = c[0], c2 = c[1], c3 = c[2];
+    const T k2 = T(2) * kc.kappa;
+    if (part == 0) {
+        T B[9];
+        left_cg(F, B);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            st[S::F + a] = F[a];
+            st[S::H + a] = H[a];
+            st[S::U + a] = c1 * jm23 * p1 * T(2) * F[a] + c2 * jm43 * p2 * gI2[a];
+            st[S::Bm + a] = B[a];
+        }
+        const T x0 = T(2) * c1 * jm23 + T(2) * I1 * c2 * jm43;
+        T X[9], Y[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            X[a] = ((a % 4) == 0 ? x0 : T(0)) - T(2) * c2 * jm43 * C[a];
+            Y[a] = -T(2) * c2 * jm43 * B[a];
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            const T *A0 = kc.fib[f];
+            const T c4 = c[3 + f], c5 = c[3 + NF + f];
+            T a[3], v[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                a[i] = F[3 * i] * A0[0] + F[3 * i + 1] * A0[1] + F[3 * i + 2] * A0[2];
+                v[i] = C[3 * i] * A0[0] + C[3 * i + 1] * A0[1] + C[3 * i + 2] * A0[2];
+            }
+#pragma unroll
+            for (int J_ = 0; J_ < 3; ++J_)
+#pragma unroll
+                for (int L = 0; L < 3; ++L) {
+                    X[3 * J_ + L] += T(2) * c4 * A0[J_] * A0[L] + T(2) * c5 * (A0[J_] * v[L] + v[J_] * A0[L]);
+                    Y[3 * J_ + L] += T(2) * c5 * a[J_] * a[L];
+                }
+            st[S::sc + 4 + f] = T(2) * c5;
+        }
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            st[S::X + a] = X[a];
+            st[S::Y + a] = Y[a];
+        }
+        st[S::sc + 0] = c1 * jm23 * p1 * p1 * I1 + c2 * jm43 * p2 * p2 * I2 + c3 * J + k2 * J * J + k2 * Jm1 * J;
+        st[S::sc + 1] = T(4) * c2 * jm43;
+        st[S::sc + 2] = c1 * jm23 * p1 * I1 + c2 * jm43 * p2 * I2 + c3 * J + k2 * Jm1 * J;
+        st[S::sc + 3] = -T(2) * c2 * jm43;
+        st[S::sc + 4 + NF] = k2 * Jm1 * J;
+    } else if (part == 1) {
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            st[S::g + a] = jm23 * (T(2) * F[a] + p1 * I1 * H[a]);
+            st[S::g + 9 + a] = jm43 * (gI2[a] + p2 * I2 * H[a]);
+            st[S::g + 18 + a] = cof[a];
+        }
+    } else if (part == 2) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            const T *A0 = kc.fib[f];
+            T a[3], v[3], Fv[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                a[i] = F[3 * i] * A0[0] + F[3 * i + 1] * A0[1] + F[3 * i + 2] * A0[2];
+                v[i] = C[3 * i] * A0[0] + C[3 * i + 1] * A0[1] + C[3 * i + 2] * A0[2];
+            }
+#pragma unroll
+            for (int i = 0; i < 3; ++i) Fv[i] = F[3 * i] * v[0] + F[3 * i + 1] * v[1] + F[3 * i + 2] * v[2];
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int L = 0; L < 3; ++L) {
+                    st[S::g + 9 * (3 + f) + 3 * k + L] = T(2) * a[k] * A0[L];
+                    st[S::g + 9 * (3 + NF + f) + 3 * k + L] = T(2) * (a[k] * v[L] + Fv[k] * A0[L]);
+                    st[S::aA + 9 * f + 3 * k + L] = a[k] * A0[L];
+                    st[S::AA + 9 * f + 3 * k + L] = A0[k] * A0[L];
+                }
+        }
+    }
+}
+
+// Row a = 3i + J of P and A from the staged quantities; Hs is the packed lower
+// triangle of d2N/dK2 (index m*(m+1)/2 + n, n <= m), c = dN/dK - n0.
+template <typename T, int NF>
+__device__ __forceinline__ void assemble_row(int a, const T *st, const T *Hs, const T *c, T &Pa, T *Arow) {
+    constexpr int D = 3 + 2 * NF;
+    using S = Stage<D, NF>;
+    const int i = a / 3, J_ = a % 3;
+    T u[D];
+#pragma unroll
+    for (int n = 0; n < D; ++n) u[n] = T(0);
+    T p = T(0);
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+        const T gma = st[S::g + 9 * m + a];
+        p += c[m] * gma;
+#pragma unroll
+        for (int n = 0; n < D; ++n) {
+            const int idx = (m >= n) ? (m * (m + 1) / 2 + n) : (n * (n + 1) / 2 + m);
+            u[n] += gma * Hs[idx];
+        }
+    }
+    const T Ha = st[S::H + a], Fa = st[S::F + a], Ua = st[S::U + a];
+    Pa = p + st[S::sc + 4 + NF] * Ha;
+    const T beta = st[S::sc + 0], gamma = st[S::sc + 1], eta = st[S::sc + 2], zeta = st[S::sc + 3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int L = 0; L < 3; ++L) {
+            const int b = 3 * k + L;
+            T s = T(0);
+#pragma unroll
+            for (int n = 0; n < D; ++n) s += u[n] * st[S::g + 9 * n + b];
+            const T Hb = st[S::H + b];
+            s += Ua * Hb + Ha * st[S::U + b] + beta * Ha * Hb + gamma * Fa * st[S::F + b];
+            const T FiL = st[S::F + 3 * i + L], FkJ = st[S::F + 3 * k + J_];
+            s += -eta * st[S::H + 3 * i + L] * st[S::H + 3 * k + J_] + zeta * FiL * FkJ;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const T c5x2 = st[S::sc + 4 + f];
+                s += c5x2 * (FiL * st[S::aA + 9 * f + 3 * k + J_] + st[S::aA + 9 * f + 3 * i + L] * FkJ +
+                             st[S::Bm + 3 * i + k] * st[S::AA + 9 * f + 3 * J_ + L]);
+            }
+            if (i == k) s += st[S::X + 3 * J_ + L];
+            if (J_ == L) s += st[S::Y + 3 * i + k];
+            Arow[b] = s;
+        }
+}
+
+}  // namespace commet

@@ -1,0 +1,271 @@
+// Hex8 element kernels: trial F at the Gauss points (Algorithm 1), the element
+// residual and stiffness integrals (eq. r-quad, k-quad in material form, App. A.1),
+// and their race-free sum into the global residual and CSR stiffness by element colour.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "internal.h"
+
+namespace commet {
+
+// Reference-cube data: node I at (+-1,+-1,+-1) lexicographic (x fastest), Gauss point q
+// at (+-1/sqrt3)^3 in the same order, weight 1.
+template <typename T>
+__device__ __forceinline__ void shape_grad_ref(int q, T g[8][3]) {
+    const T gp = T(0.57735026918962576451);
+#pragma unroll
+    for (int I = 0; I < 8; ++I) {
+        T xi[3], zq[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            xi[a] = ((I >> a) & 1) ? T(1) : T(-1);
+            zq[a] = ((q >> a) & 1) ? gp : -gp;
+        }
+        const T f0 = T(1) + xi[0] * zq[0], f1 = T(1) + xi[1] * zq[1], f2 = T(1) + xi[2] * zq[2];
+        g[I][0] = T(0.125) * xi[0] * f1 * f2;
+        g[I][1] = T(0.125) * xi[1] * f0 * f2;
+        g[I][2] = T(0.125) * xi[2] * f0 * f1;
+    }
+}
+
+// grad_X phi_I = Je^{-T} grad_xi phi_I and w = det Je for one element/Gauss point.
+template <typename T>
+__device__ __forceinline__ void physical_grads(const T Xe[8][3], int q, T gX[8][3], T &w) {
+    T g[8][3];
+    shape_grad_ref<T>(q, g);
+    T Je[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            T s = T(0);
+#pragma unroll
+            for (int I = 0; I < 8; ++I) s += Xe[I][a] * g[I][b];
+            Je[3 * a + b] = s;
+        }
+    T cof[9];
+    cof[0] = Je[4] * Je[8] - Je[5] * Je[7];
+    cof[1] = Je[5] * Je[6] - Je[3] * Je[8];
+    cof[2] = Je[3] * Je[7] - Je[4] * Je[6];
+    cof[3] = Je[2] * Je[7] - Je[1] * Je[8];
+    cof[4] = Je[0] * Je[8] - Je[2] * Je[6];
+    cof[5] = Je[1] * Je[6] - Je[0] * Je[7];
+    cof[6] = Je[1] * Je[5] - Je[2] * Je[4];
+    cof[7] = Je[2] * Je[3] - Je[0] * Je[5];
+    cof[8] = Je[0] * Je[4] - Je[1] * Je[3];
+    const T det = Je[0] * cof[0] + Je[1] * cof[1] + Je[2] * cof[2];
+    const T id = T(1) / det;
+#pragma unroll
+    for (int I = 0; I < 8; ++I)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            gX[I][a] = (cof[3 * a] * g[I][0] + cof[3 * a + 1] * g[I][1] + cof[3 * a + 2] * g[I][2]) * id;
+    w = det;
+}
+
+template <typename T>
+__device__ __forceinline__ T node_coord(const double *X, int64_t n, int a) {
+    return (T)X[3 * n + a];
+}
+
+// ------------------------------------------------------------------ compute_F
+template <typename T>
+__global__ void compute_F_kernel(int64_t n_el, int64_t n_nodes, const int32_t *__restrict__ conn,
+                                 const double *__restrict__ X, const T *__restrict__ u, T *__restrict__ F) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= 8 * n_el) return;
+    const int64_t e = gid >> 3;
+    const int q = (int)(gid & 7);
+    T Xe[8][3], ue[8][3];
+#pragma unroll
+    for (int I = 0; I < 8; ++I) {
+        const int64_t n = conn[8 * e + I];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            Xe[I][a] = node_coord<T>(X, n, a);
+            ue[I][a] = u[a * n_nodes + n];
+        }
+    }
+    T gX[8][3], w;
+    physical_grads<T>(Xe, q, gX, w);
+    const int64_t n_qp = 8 * n_el;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int J = 0; J < 3; ++J) {
+            T s = (i == J) ? T(1) : T(0);
+#pragma unroll
+            for (int I = 0; I < 8; ++I) s += ue[I][i] * gX[I][J];
+            F[(3 * i + J) * n_qp + gid] = s;
+        }
+}
+
+int launch_compute_F(const commet_mesh *mesh, int precision, const void *u, void *F, cudaStream_t s) {
+    const int64_t n = 8 * mesh->n_el;
+    if (n == 0) return COMMET_OK;
+    const int tpb = 256;
+    const int64_t blocks = (n + tpb - 1) / tpb;
+    if (precision == COMMET_F64)
+        compute_F_kernel<double><<<(unsigned)blocks, tpb, 0, s>>>(mesh->n_el, mesh->n_nodes, mesh->d_conn, mesh->d_X,
+                                                                   (const double *)u, (double *)F);
+    else
+        compute_F_kernel<float><<<(unsigned)blocks, tpb, 0, s>>>(mesh->n_el, mesh->n_nodes, mesh->d_conn, mesh->d_X,
+                                                                  (const float *)u, (float *)F);
+    return cudaGetLastError() == cudaSuccess ? COMMET_OK : COMMET_ERR_CUDA;
+}
+
+// -------------------------------------------------------------- elem_assemble
+// 8 lanes per element (lane I = element node I, which owns dof rows 3I..3I+2);
+// 16 elements per 128-thread CTA. Per Gauss point the element's P and A (90 values)
+// are staged in shared memory and read by its 8 lanes.
+constexpr int kElPerCta = 16;
+
+template <typename T, bool SCATTER>
+__global__ void __launch_bounds__(128)
+    elem_assemble_kernel(int64_t n_el, const int32_t *__restrict__ el_list, int64_t n_list,
+                         const int32_t *__restrict__ conn, const double *__restrict__ X, const T *__restrict__ P,
+                         const T *__restrict__ A, T *__restrict__ f_e, T *__restrict__ K_e, T *__restrict__ r,
+                         T *__restrict__ K_vals, const uint32_t *__restrict__ emap,
+                         const int32_t *__restrict__ rowlen) {
+    __shared__ T s_g[kElPerCta][8][8][3];  // [el][qp][node][dir]
+    __shared__ T s_w[kElPerCta][8];
+    __shared__ T s_pa[kElPerCta][90];      // P (9) then A (81) of the current qp
+    const int le = threadIdx.x >> 3, I = threadIdx.x & 7;
+    const int64_t li = (int64_t)blockIdx.x * kElPerCta + le;
+    const bool valid = li < n_list;
+    const int64_t e = valid ? (el_list ? (int64_t)el_list[li] : li) : 0;
+    const int64_t n_qp = 8 * n_el;
+    {
+        // lane I computes the gradients at Gauss point I
+        T Xe[8][3];
+#pragma unroll
+        for (int K = 0; K < 8; ++K) {
+            const int64_t n = conn[8 * e + K];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) Xe[K][a] = (T)X[3 * n + a];
+        }
+        T gX[8][3], w;
+        physical_grads<T>(Xe, I, gX, w);
+#pragma unroll
+        for (int K = 0; K < 8; ++K)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) s_g[le][I][K][a] = gX[K][a];
+        s_w[le][I] = w;
+    }
+    T f[3] = {T(0), T(0), T(0)};
+    T Kr[3][8][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int K = 0; K < 8; ++K)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) Kr[i][K][k] = T(0);
+    const bool want_K = (A != nullptr);
+    for (int q = 0; q < 8; ++q) {
+        __syncthreads();
+        const int64_t qq = 8 * e + q;
+        for (int c = I; c < 90; c += 8) {
+            T v = T(0);
+            if (c < 9)
+                v = P[c * n_qp + qq];
+            else if (want_K)
+                v = A[(c - 9) * n_qp + qq];
+            s_pa[le][c] = v;
+        }
+        __syncthreads();
+        const T w = s_w[le][q];
+        T wg[3];
+#pragma unroll
+        for (int J = 0; J < 3; ++J) wg[J] = w * s_g[le][q][I][J];
+        const T *Pq = &s_pa[le][0];
+        const T *Aq = &s_pa[le][9];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) f[i] += Pq[3 * i] * wg[0] + Pq[3 * i + 1] * wg[1] + Pq[3 * i + 2] * wg[2];
+        if (want_K) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                T T3[3][3];  // [k][L] = sum_J wg_J A_iJkL
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+#pragma unroll
+                    for (int L = 0; L < 3; ++L)
+                        T3[k][L] = wg[0] * Aq[(3 * i) * 9 + 3 * k + L] + wg[1] * Aq[(3 * i + 1) * 9 + 3 * k + L] +
+                                   wg[2] * Aq[(3 * i + 2) * 9 + 3 * k + L];
+#pragma unroll
+                for (int K = 0; K < 8; ++K) {
+                    const T g0 = s_g[le][q][K][0], g1 = s_g[le][q][K][1], g2 = s_g[le][q][K][2];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) Kr[i][K][k] += T3[k][0] * g0 + T3[k][1] * g1 + T3[k][2] * g2;
+                }
+            }
+        }
+    }
+    if (!valid) return;
+    if (f_e != nullptr) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) f_e[(3 * I + i) * n_el + e] = f[i];
+    }
+    if (K_e != nullptr && want_K) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int K = 0; K < 8; ++K)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) K_e[((3 * I + i) * 24 + 3 * K + k) * n_el + e] = Kr[i][K][k];
+    }
+    if (SCATTER) {
+        const int64_t gI = conn[8 * e + I];
+        if (r != nullptr) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) r[3 * gI + i] += f[i];
+        }
+        if (K_vals != nullptr && want_K) {
+            const int64_t rl = rowlen[gI];
+#pragma unroll
+            for (int K = 0; K < 8; ++K) {
+                const int64_t base = emap[(8 * e + I) * 8 + K];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) K_vals[base + i * rl + k] += Kr[i][K][k];
+            }
+        }
+    }
+}
+
+template <typename T>
+static int elem_typed(const commet_mesh *mesh, const void *P, const void *A, void *f_e, void *K_e, void *r,
+                      void *K_vals, cudaStream_t s) {
+    const int64_t n_el = mesh->n_el;
+    if (n_el == 0) return COMMET_OK;
+    const bool scatter = (r != nullptr) || (K_vals != nullptr);
+    if (!scatter) {
+        const int64_t blocks = (n_el + kElPerCta - 1) / kElPerCta;
+        elem_assemble_kernel<T, false><<<(unsigned)blocks, 128, 0, s>>>(
+            n_el, nullptr, n_el, mesh->d_conn, mesh->d_X, (const T *)P, (const T *)A, (T *)f_e, (T *)K_e, nullptr,
+            nullptr, nullptr, nullptr);
+        return cudaGetLastError() == cudaSuccess ? COMMET_OK : COMMET_ERR_CUDA;
+    }
+    if (r != nullptr) COMMET_CUDA_TRY(cudaMemsetAsync(r, 0, sizeof(T) * 3 * mesh->n_nodes, s));
+    if (K_vals != nullptr) COMMET_CUDA_TRY(cudaMemsetAsync(K_vals, 0, sizeof(T) * mesh->nnz, s));
+    for (int c = 0; c < mesh->n_colours; ++c) {
+        const int64_t off = mesh->colour_off[c], cnt = mesh->colour_off[c + 1] - off;
+        if (cnt == 0) continue;
+        const int64_t blocks = (cnt + kElPerCta - 1) / kElPerCta;
+        elem_assemble_kernel<T, true><<<(unsigned)blocks, 128, 0, s>>>(
+            n_el, mesh->d_colour_el + off, cnt, mesh->d_conn, mesh->d_X, (const T *)P, (const T *)A, (T *)f_e,
+            (T *)K_e, (T *)r, (T *)K_vals, mesh->d_emap, mesh->d_rowlen);
+        if (cudaGetLastError() != cudaSuccess) return COMMET_ERR_CUDA;
+    }
+    return COMMET_OK;
+}
+
+int launch_elem_assemble(const commet_mesh *mesh, int precision, const void *P, const void *A, void *f_e,
+                         void *K_e, void *r, void *K_vals, cudaStream_t s) {
+    if (precision == COMMET_F64) return elem_typed<double>(mesh, P, A, f_e, K_e, r, K_vals, s);
+    return elem_typed<float>(mesh, P, A, f_e, K_e, r, K_vals, s);
+}
+
+}  // namespace commet

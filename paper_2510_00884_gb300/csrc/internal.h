@@ -1,0 +1,108 @@
+// Internal declarations shared by the CUDA translation units of libcommet.
+// Not installed; the public boundary is include/commet.h.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/commet.h"
+
+namespace commet {
+
+constexpr int kMaxFibres = 2;
+constexpr int kMaxD = 3 + 2 * kMaxFibres;
+
+// Offsets (in elements of the path's scalar type) of the packed weight block that
+// every constitutive kernel copies into shared memory once per CTA.
+struct NetLayout {
+    int d, W, L;
+    int W1t;  // [d][W]       W1 transposed (forward: contiguous over neurons)
+    int W1r;  // [W][dp]      W1 row-major, rows padded to dp (tangent seed)
+    int At;   // [L-1][W][W]  A_k transposed: At[i][j] = A_k[j][i]
+    int Ar;   // [L-1][W][W]  A_k row-major (reverse pass)
+    int Bt;   // [L-1][d][W]  B_k transposed
+    int c;    // [L][W]
+    int a;    // [W]
+    int b;    // [d]
+    int n0;   // [d] stress-free shift (zeros when off)
+    int K0;   // [d] K at F = I
+    int total;
+};
+
+// Kinematic layer constants.
+struct KinParams {
+    int kin;       // COMMET_KIN_*
+    int nf;        // fibres
+    double fib[kMaxFibres][3];
+    double kappa;  // volumetric penalty
+    int stress_free;
+};
+
+}  // namespace commet
+
+struct commet_model {
+    int precision;
+    int d, W, L;
+    commet::KinParams kp;
+    commet::NetLayout lay;
+    int64_t n_params;
+    void *d_weights = nullptr;     // packed block, element type of the precision (float for BF16_MLP)
+    void *d_theta64 = nullptr;     // flat theta (double) for reference
+    void *d_bf16 = nullptr;        // hidden-layer weights in bf16 fragments (BF16_MLP only)
+    size_t bf16_bytes = 0;
+    int device = 0;
+};
+
+struct commet_mesh {
+    int64_t n_nodes = 0, n_el = 0;
+    double *d_X = nullptr;          // [n_nodes][3]
+    float *d_Xf = nullptr;          // [n_nodes][3] float copy
+    int32_t *d_conn = nullptr;      // [n_el][8]
+    // CSR pattern and colouring (want_csr)
+    int64_t n_rows = 0, nnz = 0;
+    int64_t *d_rowptr = nullptr;    // [n_rows + 1]
+    int32_t *d_col = nullptr;       // [nnz]
+    uint32_t *d_emap = nullptr;     // [n_el][8][8] CSR position of (3*gI, 3*gK)
+    int32_t *d_rowlen = nullptr;    // [n_nodes] entries per dof row of a node (3 * neighbours)
+    int32_t n_colours = 0;
+    int32_t *d_colour_el = nullptr; // elements sorted by colour
+    int64_t colour_off[65] = {0};   // offsets into d_colour_el
+    // host copies for commet_mesh_csr
+    int64_t *h_rowptr = nullptr;
+    int32_t *h_col = nullptr;
+    int device = 0;
+};
+
+namespace commet {
+
+// Launchers (return COMMET_* codes). Pointers already validated.
+int launch_const_update(const commet_model *m, int64_t n_qp, const void *F, void *psi, void *P, void *A,
+                        int32_t *status, cudaStream_t s, void *dN_out = nullptr);
+int launch_const_update_bf16(const commet_model *m, int64_t n_qp, const void *F, void *psi, void *P, void *A,
+                             int32_t *status, cudaStream_t s);
+int launch_status_init(int32_t *status, cudaStream_t s);
+int launch_target_stress(int precision, int64_t n_qp, const void *F, int nf, const double *fib, double mu,
+                         double k1, double k2, double kappa, void *P, cudaStream_t s);
+int launch_compute_F(const commet_mesh *mesh, int precision, const void *u, void *F, cudaStream_t s);
+int launch_elem_assemble(const commet_mesh *mesh, int precision, const void *P, const void *A, void *f_e,
+                         void *K_e, void *r, void *K_vals, cudaStream_t s);
+int launch_newton_assemble(const commet_model *m, const commet_mesh *mesh, const void *u, void *r, void *K_vals,
+                           int32_t *status, cudaStream_t s);
+size_t backward_workspace_bytes(const commet_model *m, int64_t n_qp);
+int launch_const_backward(const commet_model *m, int64_t n_qp, const void *F, const void *G, void *dF, void *dtheta,
+                          void *ws, size_t ws_bytes, cudaStream_t s);
+
+// Host-side mesh graph construction (mesh_host.cpp).
+int build_csr_and_colouring(int64_t n_nodes, int64_t n_el, const int32_t *conn, commet_mesh *mesh);
+
+int sm_count();
+
+}  // namespace commet
+
+#define COMMET_CUDA_TRY(expr)                                   \
+    do {                                                        \
+        cudaError_t _e = (expr);                                \
+        if (_e != cudaSuccess) return COMMET_ERR_CUDA;          \
+    } while (0)

@@ -1,0 +1,262 @@
+"""GPU parity: every CUDA output against the FP64 oracle on the same seeded inputs.
+
+All calls go through the C ABI (libcommet.so) via the package's thin binding.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workload as wl
+from tests.parity import TOL, assert_close, cm_to_pm, pm_to_cm
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DT = {"f64": torch.float64, "f32": torch.float32}
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2510_00884_gb300 as p
+    p.build()
+    return p
+
+
+def run_update(pkg, spec, F_pm, prec, want_A=True):
+    m = pkg.Model(spec, prec)
+    F = pm_to_cm(F_pm, DT[prec])
+    psi, P, A, st = m.const_update(F, want_A=want_A, status=True)
+    torch.cuda.synchronize()
+    return (psi.cpu().numpy(), cm_to_pm(P), cm_to_pm(A) if A is not None else None, st.cpu().numpy())
+
+
+def oracle_update(spec, F_pm, prec):
+    Fin = np.asarray(F_pm, dtype=np.float32 if prec == "f32" else np.float64).astype(np.float64)
+    return oracle.const_update(oracle.OracleModel(spec), Fin)
+
+
+def check_update(pkg, spec, F_pm, prec, what):
+    psi, P, A, st = run_update(pkg, spec, F_pm, prec)
+    psi_r, P_r, A_r = oracle_update(spec, F_pm, prec)
+    tol = TOL[prec]
+    assert st[0] == 0 and st[1] == np.iinfo(np.int32).max, f"{what}: status {st}"
+    scale = None
+    if spec.stress_free and prec != "f64":
+        # The stress-free shift subtracts n0 = dN/dK(K(I)) from dN/dK (Z8 reading of the
+        # stress-free reference state): P is the difference of two O(1) gradients, so the
+        # FP32 rounding scales with the unshifted stress, which is the scale used here.
+        unshifted = wl.ModelSpec(**{**spec.__dict__, "stress_free": False})
+        _, P_scale, _ = oracle_update(unshifted, F_pm, prec)
+        scale = P_scale
+    eP = assert_close(P, P_r, tol, what + " P", scale)
+    eA = assert_close(A, A_r, tol, what + " A")
+    epsi = assert_close(psi[:, None], psi_r[:, None], tol, what + " psi")
+    return eP, eA, epsi
+
+
+# ------------------------------------------------------------------ C0 (plain FP64)
+
+def test_c0_full_chain_fp64(pkg):
+    """8^3 cube: F from u, P/A/psi, f_e and K_e, all against the oracle at 1e-12."""
+    w = wl.workload_c0()
+    mesh, spec = w["mesh"], w["model"]
+    gm = pkg.Mesh(mesh.X, mesh.conn)
+    u = torch.from_numpy(np.ascontiguousarray(w["u"].T)).cuda()
+    F = gm.compute_F(u, "f64")
+    F_ref = oracle.compute_F(mesh, w["u"])
+    assert_close(cm_to_pm(F), F_ref, TOL["f64"], "C0 F")
+    m = pkg.Model(spec, "f64")
+    psi, P, A, st = m.const_update(F, status=True)
+    psi_r, P_r, A_r = oracle.const_update(oracle.OracleModel(spec), F_ref)
+    assert st.cpu().numpy()[0] == 0
+    assert_close(cm_to_pm(P), P_r, TOL["f64"], "C0 P")
+    assert_close(cm_to_pm(A), A_r, TOL["f64"], "C0 A")
+    assert_close(psi.cpu().numpy()[:, None], psi_r[:, None], TOL["f64"], "C0 psi")
+    f_e, K_e, _, _ = gm.elem_assemble(P, A, "f64")
+    f_r, K_r = oracle.elem_assemble(mesh, P_r, A_r)
+    assert_close(cm_to_pm(f_e), f_r, TOL["f64"], "C0 f_e")
+    assert_close(cm_to_pm(K_e), K_r.reshape(-1, 576), TOL["f64"], "C0 K_e")
+
+
+# --------------------------------------------------------- shapes, both precisions
+
+CASES = [
+    # (kin, n_fib, W, L, kappa, bias, stress_free, n_qp)
+    (wl.KIN_ISO_SHIFTED, 0, 16, 2, 10.0, False, False, 4099),
+    (wl.KIN_RAW, 2, 32, 3, 0.0, False, False, 5003),
+    (wl.KIN_ISO_SHIFTED, 0, 64, 3, 10.0, False, False, 2053),
+    (wl.KIN_RAW, 1, 16, 1, 2.0, True, False, 1031),
+    (wl.KIN_RAW, 2, 16, 4, 1.0, True, True, 1500),
+    (wl.KIN_ISO_SHIFTED, 0, 32, 5, 3.0, True, True, 777),
+    (wl.KIN_RAW, 1, 32, 2, 0.5, False, False, 7),
+]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("case", CASES, ids=[f"k{c[0]}f{c[1]}w{c[2]}l{c[3]}n{c[7]}" for c in CASES])
+def test_const_update_shapes(pkg, case, prec):
+    kin, nf, W, L, kappa, bias, sf, n = case
+    rng = np.random.Generator(np.random.PCG64(100 + W + L + nf))
+    spec = wl.make_model(rng, kin, nf, W=W, L=L, kappa=kappa, bias_std=0.1 if bias else None, stress_free=sf)
+    F = wl.random_F(rng, n, 0.15)
+    check_update(pkg, spec, F, prec, f"{case} {prec}")
+
+
+def test_stress_free_reference_state(pkg):
+    rng = np.random.Generator(np.random.PCG64(5))
+    spec = wl.make_model(rng, wl.KIN_RAW, 2, W=32, L=3, kappa=1.0, stress_free=True)
+    F = np.tile(np.eye(3).ravel(), (16, 1))
+    _, P, _, _ = run_update(pkg, spec, F, "f64")
+    assert np.abs(P).max() < 1e-14
+
+
+# ------------------------------------------------------------------- edge cases
+
+def test_empty_and_tiny(pkg):
+    rng = np.random.Generator(np.random.PCG64(6))
+    spec = wl.make_model(rng, wl.KIN_RAW, 2, W=32, L=3, kappa=0.0)
+    m = pkg.Model(spec, "f64")
+    F0 = torch.empty(9, 0, dtype=torch.float64, device="cuda")
+    psi, P, A = m.const_update(F0)
+    assert P.shape == (9, 0)
+    for n in (1, 2, 8, 9):
+        check_update(pkg, spec, wl.random_F(rng, n, 0.15), "f64", f"n={n}")
+
+
+def test_bad_points_are_reported(pkg):
+    """J <= 0 and non-finite F give NaN outputs at those points and a status count."""
+    rng = np.random.Generator(np.random.PCG64(7))
+    spec = wl.make_model(rng, wl.KIN_RAW, 2, W=32, L=3, kappa=0.0)
+    F = wl.random_F(rng, 100, 0.15)
+    F[17] = np.diag([1.0, 1.0, -1.0]).ravel()
+    F[42, 3] = np.nan
+    F[63] = 0.0
+    psi, P, A, st = run_update(pkg, spec, F, "f64")
+    assert st[0] == 3 and st[1] == 17
+    for q in (17, 42, 63):
+        assert np.all(np.isnan(P[q])) and np.all(np.isnan(A[q])) and np.isnan(psi[q])
+    good = np.setdiff1d(np.arange(100), [17, 42, 63])
+    _, P_r, A_r = oracle_update(spec, F[good], "f64")
+    assert_close(P[good], P_r, 1e-12, "good points P")
+    assert_close(A[good], A_r, 1e-12, "good points A")
+
+
+def test_invalid_arguments(pkg):
+    from paper_2510_00884_gb300 import _lib
+    lib = _lib.load()
+    rng = np.random.Generator(np.random.PCG64(8))
+    spec = wl.make_model(rng, wl.KIN_RAW, 2, W=32, L=3, kappa=0.0)
+    m = pkg.Model(spec, "f64")
+    F = torch.zeros(9, 10, dtype=torch.float64, device="cuda")
+    P = torch.zeros(9, 10, dtype=torch.float64, device="cuda")
+    import ctypes as C
+    s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.commet_const_update(m.handle, 10, None, None, C.c_void_p(P.data_ptr()), None, None, s) == \
+        _lib.ERR_INVALID_ARG
+    assert lib.commet_const_update(m.handle, -1, C.c_void_p(F.data_ptr()), None, C.c_void_p(P.data_ptr()),
+                                   None, None, s) == _lib.ERR_INVALID_ARG
+    assert lib.commet_const_update(m.handle, 10, C.c_void_p(F.data_ptr() + 8), None, C.c_void_p(P.data_ptr()),
+                                   None, None, s) == _lib.ERR_INVALID_ARG
+    spec8 = wl.make_model(rng, wl.KIN_RAW, 2, W=8, L=3, kappa=0.0)
+    with pytest.raises(_lib.CommetError) as ei:
+        pkg.Model(spec8, "f64")
+    assert ei.value.code == _lib.ERR_UNSUPPORTED
+    bad = wl.make_model(rng, wl.KIN_RAW, 2, W=32, L=3, kappa=0.0)
+    bad.d = 5
+    with pytest.raises(_lib.CommetError) as ei:
+        pkg.Model(bad, "f64")
+    assert ei.value.code == _lib.ERR_INVALID_ARG
+
+
+# ------------------------------------------------------------- element assembly
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_elem_assemble_and_csr_scatter(pkg, prec):
+    """Distorted 5x4x3 mesh: F, f_e, K_e, r and the CSR values against the oracle."""
+    mesh = wl.structured_mesh(5, 4, 3, lengths=(1.0, 0.8, 0.6))
+    rng = np.random.Generator(np.random.PCG64(9))
+    X = mesh.X + 0.02 * rng.uniform(-1, 1, size=mesh.X.shape)
+    mesh = wl.Mesh(X=X, conn=mesh.conn, n=mesh.n)
+    spec = wl.make_model(rng, wl.KIN_RAW, 2, W=32, L=3, kappa=1.0)
+    u_np = 0.01 * rng.normal(size=mesh.X.shape)
+    gm = pkg.Mesh(mesh.X, mesh.conn, want_csr=True)
+    assert gm.n_colours == 8
+    dt = DT[prec]
+    u = torch.from_numpy(np.ascontiguousarray(u_np.T)).to(dt).cuda()
+    F = gm.compute_F(u, prec)
+    u_in = u.double().cpu().numpy().T
+    F_r = oracle.compute_F(mesh, u_in)
+    assert_close(cm_to_pm(F), F_r, TOL[prec], "F")
+    m = pkg.Model(spec, prec)
+    _, P, A = m.const_update(F)
+    P_in, A_in = cm_to_pm(P).astype(np.float64), cm_to_pm(A).astype(np.float64)
+    f_e, K_e, r, Kv = gm.elem_assemble(P, A, prec, want_r=True, want_Kcsr=True)
+    f_r, K_r = oracle.elem_assemble(mesh, P_in, A_in)
+    assert_close(cm_to_pm(f_e), f_r, TOL[prec], "f_e")
+    assert_close(cm_to_pm(K_e), K_r.reshape(-1, 576), TOL[prec], "K_e")
+    r_r = oracle.scatter_residual(mesh, f_r)
+    rowptr, col = gm.csr()
+    Kv_r, missing = oracle.scatter_csr(mesh, K_r, rowptr, col)
+    assert missing == 0
+    tol = TOL[prec] * 10  # sums of up to 8 element contributions
+    rr = r.cpu().numpy().astype(np.float64)
+    assert np.abs(rr - r_r).max() <= tol * np.abs(r_r).max()
+    kk = Kv.cpu().numpy().astype(np.float64)
+    assert np.abs(kk - Kv_r).max() <= tol * np.abs(Kv_r).max()
+
+
+def test_target_stress(pkg):
+    rng = np.random.Generator(np.random.PCG64(10))
+    F = wl.random_F(rng, 3001, 0.15)
+    tgt = oracle.OracleModel(None, inner=oracle.INNER_HGO, kin=wl.KIN_RAW, fibres=wl.FIBRES_PM30,
+                             kappa=10.0, mu=1.0, k1=2.0, k2=0.5)
+    _, P_r, _ = oracle.const_update(tgt, F, want_A=False)
+    for prec in ("f64", "f32"):
+        Fd = pm_to_cm(F, DT[prec])
+        P = pkg.target_stress(Fd, wl.FIBRES_PM30, 1.0, 2.0, 0.5, 10.0)
+        Fin = cm_to_pm(Fd).astype(np.float64)
+        _, P_r2, _ = oracle.const_update(tgt, Fin, want_A=False)
+        assert_close(cm_to_pm(P), P_r2, TOL[prec], f"target {prec}")
+
+
+# ---------------------------------------------------- full-size sampled parity
+
+def sample_idx(n, F_pm, k=1500, seed=0):
+    """Strided sample plus every point with |J - 1| < 1e-3 or J < 0.8."""
+    idx = np.unique(np.linspace(0, n - 1, k).astype(np.int64))
+    J = np.linalg.det(F_pm.reshape(-1, 3, 3))
+    special = np.nonzero((np.abs(J - 1.0) < 1e-3) | (J < 0.8))[0]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if special.size > 500:
+        special = rng.choice(special, 500, replace=False)
+    return np.unique(np.concatenate([idx, special, [n - 1]]))
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_c1_full_size_sampled(pkg, prec):
+    """64^3 mesh, 2,097,152 points (the benchmark's launch): sampled points and elements."""
+    w = wl.workload_c1()
+    spec, mesh, F_pm = w["model"], w["mesh"], w["F"]
+    n = F_pm.shape[0]
+    m = pkg.Model(spec, prec)
+    F = pm_to_cm(F_pm, DT[prec])
+    psi, P, A, st = m.const_update(F, status=True)
+    gm = pkg.Mesh(mesh.X, mesh.conn)
+    f_e, K_e, _, _ = gm.elem_assemble(P, A, prec)
+    torch.cuda.synchronize()
+    assert st.cpu().numpy()[0] == 0
+    idx = sample_idx(n, F_pm)
+    Fin = F_pm[idx].astype(np.float32 if prec == "f32" else np.float64).astype(np.float64)
+    psi_r, P_r, A_r = oracle.const_update(oracle.OracleModel(spec), Fin)
+    it = torch.from_numpy(idx).cuda()
+    assert_close(P.index_select(1, it).cpu().numpy().T, P_r, TOL[prec], "C1 P")
+    assert_close(A.index_select(1, it).cpu().numpy().T, A_r, TOL[prec], "C1 A")
+    el = np.unique(np.linspace(0, mesh.n_el - 1, 300).astype(np.int64))
+    qp = (8 * el[:, None] + np.arange(8)[None, :]).ravel()
+    qt = torch.from_numpy(qp).cuda()
+    P_in = P.index_select(1, qt).cpu().numpy().T.astype(np.float64)
+    A_in = A.index_select(1, qt).cpu().numpy().T.astype(np.float64)
+    f_r, K_r = oracle.elem_assemble(mesh, P_in, A_in, el=el)
+    et = torch.from_numpy(el).cuda()
+    assert_close(f_e.index_select(1, et).cpu().numpy().T, f_r, TOL[prec], "C1 f_e")
+    assert_close(K_e.index_select(1, et).cpu().numpy().T, K_r.reshape(-1, 576), TOL[prec], "C1 K_e")
