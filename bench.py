@@ -71,18 +71,18 @@ def kernel_source_hash(files) -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str, workload: str, precision: str, src_hash: str):
-    """Per-launch DRAM bytes of the kernel from the committed ncu summary, if it was
-    taken on the current source; else None."""
+def ncu_traffic(kernel: str, network: str, precision: str, src_hash: str, n_qp: int):
+    """Per-launch DRAM bytes of the kernel from the committed ncu summary, scaled from the
+    captured case to n_qp points; None when the kernel source changed since the capture."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         tab = json.load(f)
-    e = tab.get(f"{kernel}|{workload}|{precision}")
+    e = tab.get(f"{kernel}|{network}|{precision}")
     if not e or e.get("src_hash") != src_hash:
         return None
-    return e.get("dram_bytes_per_launch")
+    return e["dram_bytes"] * n_qp / e["n_qp"]
 
 
 class ClockSampler:
@@ -299,7 +299,7 @@ def run_ours(args, rank, world, local_rank):
     peak = alu_peak_tflops(prec, n_sm, float(peaks.get("sm_max_mhz", 2070.0)))
     achieved = flops_qp * n_qp / (cu_ms * 1e-3) / 1e12
     src_hash = kernel_source_hash(["const_update.cu", "device_math.cuh"])
-    traffic = ncu_traffic("const_update_kernel", w["name"], prec, src_hash)
+    traffic = ncu_traffic("const_update_kernel", f"d{spec.d}w{spec.W}l{spec.L}", prec, src_hash, n_qp)
     roofline = {"bound": "alu", "kernel": "const_update_kernel", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "peak_source": f"derived: {n_sm} SMs x {'2 DFMA' if prec == 'f64' else '128 FFMA'}/clk x "

@@ -1,0 +1,481 @@
+// Backward (adjoint) of the constitutive update for an upstream G = dL/dP per point:
+//   dL/dF_q     = G_q : A_q
+//   dL/dtheta   = sum_q d/dtheta [ G_q : P_q(theta) ] = sum_q d/dtheta [ grad_K N . r_q ],
+//                 r_q,m = G_q : dK_m/dF
+// (the network's weights enter P only through grad_K N; the volumetric penalty does
+// not depend on theta). Nothing is stored between forward and backward: each point's
+// forward is recomputed here.
+//
+// Per point (a group of 4 lanes, as in the forward kernel): the network is evaluated
+// with a forward tangent along r (zdot_k = F'(y_k) ydot_k, ydot_k = A_k zdot_{k-1} + B_k r),
+// then differentiated in reverse:
+//   ydotbar_k = s_k zdotbar_k,  ybar_k = s_k zbar_k + t_k ydot_k zdotbar_k,
+//   zbar_{k-1} = A_k^T ybar_k,  zdotbar_{k-1} = A_k^T ydotbar_k,  zdotbar_L = a, zbar_L = 0,
+//   dA_k += ybar_k z_{k-1}^T + ydotbar_k zdot_{k-1}^T, dB_k += ybar_k K^T + ydotbar_k r^T,
+//   dc_k += ybar_k, da += zdot_L, db += r.
+// zdotbar follows the plain adjoint recursion, so ydotbar also gives dN/dK, and
+// sum_k B_k^T ybar_k is the Hessian-vector product (d2N/dK2) r; with them
+//   dL/dF = sum_n ((d2N/dK2) r)_n g_n + sum_a G_a S_ab,
+// S being the structured (non rank-one) part of A.
+//
+// The sums over points of the weight gradients are formed per CTA tile as small
+// outer-product GEMMs into shared-memory accumulators owned by fixed threads, written
+// once per CTA, and reduced over CTAs in index order by a second kernel: the result is
+// bitwise reproducible for a given device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "device_math.cuh"
+#include "internal.h"
+
+namespace commet {
+
+namespace {
+
+constexpr int kG = 4, kQPW = 8;
+
+template <typename T>
+struct BwConf {
+    static constexpr int warps = sizeof(T) == 8 ? 4 : 8;
+    static constexpr int Q = warps * kQPW;  // points per CTA tile
+};
+
+// Per-point slab (elements of T): K[d], r[d], z_k/zdot_k (k = 1..L-1), zdot_L, and per
+// layer s_k, t_k, ydot_k; then ybar, ydotbar of the current layer; padded.
+struct BwSlab {
+    int K, r, z, zd, zdL, s, t, yd, yb, ydb, size;
+};
+
+__host__ __device__ inline BwSlab bw_slab(int d, int W, int L, int NF, int tsize) {
+    BwSlab b{};
+    int o = 0;
+    b.K = o; o += d;
+    b.r = o; o += d;
+    b.z = o; o += (L - 1) * W;
+    b.zd = o; o += (L - 1) * W;
+    b.zdL = o; o += W;
+    b.s = o; o += L * W;
+    b.t = o; o += L * W;
+    b.yd = o; o += L * W;
+    b.yb = o; o += W;
+    b.ydb = o; o += W;
+    const int stage = 9 * d + 54 + 18 * NF + 5 + NF;
+    int raw = o > stage ? o : stage;
+    int words = raw * tsize / 4;
+    words = (words + 31) / 32 * 32 + 4;
+    b.size = words * 4 / tsize;
+    return b;
+}
+
+// sum_a G_a S_ab for the structured part S of A (see device_math.cuh), rows b given by
+// the caller; st = staged kinematics.
+template <typename T, int NF>
+__device__ __forceinline__ T contract_structured(int b, const T *st, const T *G) {
+    constexpr int D = 3 + 2 * NF;
+    using S = Stage<D, NF>;
+    const int k = b / 3, L = b % 3;
+    const T *F = st + S::F, *H = st + S::H, *U = st + S::U, *X = st + S::X, *Y = st + S::Y, *Bm = st + S::Bm;
+    T GU = 0, GH = 0, GF = 0;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        GU += G[a] * U[a];
+        GH += G[a] * H[a];
+        GF += G[a] * F[a];
+    }
+    const T beta = st[S::sc + 0], gamma = st[S::sc + 1], eta = st[S::sc + 2], zeta = st[S::sc + 3];
+    T v = GU * H[b] + GH * U[b] + beta * GH * H[b] + gamma * GF * F[b];
+    // - eta (H G^T H)_kL + zeta (F G^T F)_kL
+    T hgh = 0, fgf = 0;
+#pragma unroll
+    for (int J = 0; J < 3; ++J) {
+        T mh = 0, mf = 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            mh += G[3 * i + J] * H[3 * i + L];
+            mf += G[3 * i + J] * F[3 * i + L];
+        }
+        hgh += H[3 * k + J] * mh;
+        fgf += F[3 * k + J] * mf;
+    }
+    v += -eta * hgh + zeta * fgf;
+    // (G X)_kL + (Y G)_kL
+#pragma unroll
+    for (int J = 0; J < 3; ++J) v += G[3 * k + J] * X[3 * J + L];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) v += Y[3 * k + i] * G[3 * i + L];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const T c5x2 = st[S::sc + 4 + f];
+        const T *aA = st + S::aA + 9 * f, *AA = st + S::AA + 9 * f;
+        // recover a_f and A_f from a (x) A and A (x) A: A_J = sqrt(AA_JJ) signs from AA row
+        // (cheaper: sum over J of aA[kJ] A_J = a_k |A|^2)
+        // Terms: a_k (F^T G A)_L + A_L (F G^T a)_k + (B G A)_k A_L, written with aA and AA:
+        //   a_k (F^T G A)_L      = sum_iJ F_iL G_iJ aA[kJ]
+        //   A_L (F G^T a)_k      = sum_iJ aA[iL] G_iJ F_kJ
+        //   (B G A)_k A_L        = sum_iJ B_ik G_iJ AA[JL]
+        T t1 = 0, t2 = 0, t3 = 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int J = 0; J < 3; ++J) {
+                const T g = G[3 * i + J];
+                t1 += F[3 * i + L] * g * aA[3 * k + J];
+                t2 += aA[3 * i + L] * g * F[3 * k + J];
+                t3 += Bm[3 * i + k] * g * AA[3 * J + L];
+            }
+        v += c5x2 * (t1 + t2 + t3);
+    }
+    return v;
+}
+
+// acc[e] += sum_q U1[q][row(e)] V1[q][col(e)] + U2[q][row] V2[q][col] over the tile,
+// e = row * cols + col; entries owned by threads tid, tid + nthr, ...
+template <typename T>
+__device__ __forceinline__ void tile_outer(T *acc, int rows, int cols, const T *base, int qstride, int u1, int v1,
+                                           int u2, int v2, int Q) {
+    const int n = rows * cols;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int j = e / cols, i = e - j * cols;
+        T s = T(0);
+        for (int q = 0; q < Q; ++q) {
+            const T *p = base + (size_t)q * qstride;
+            s += p[u1 + j] * p[v1 + i];
+            if (u2 >= 0) s += p[u2 + j] * p[v2 + i];
+        }
+        acc[e] += s;
+    }
+}
+
+// acc[j] += sum_q U[q][j]
+template <typename T>
+__device__ __forceinline__ void tile_sum(T *acc, int n, const T *base, int qstride, int u, int Q) {
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        T s = T(0);
+        for (int q = 0; q < Q; ++q) s += base[(size_t)q * qstride + u + j];
+        acc[j] += s;
+    }
+}
+
+}  // namespace
+
+template <typename T, int NF, int W>
+__global__ void __launch_bounds__(BwConf<T>::warps * 32)
+    const_backward_kernel(const T *__restrict__ gw, NetLayout lay, KinConst<T> kc, int64_t n_qp,
+                          const T *__restrict__ Fg, const T *__restrict__ Gg, T *__restrict__ dFg,
+                          T *__restrict__ partial, int np_pad, BwSlab sl) {
+    constexpr int D = 3 + 2 * NF, NJ = W / kG;
+    constexpr int Q = BwConf<T>::Q;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sw = reinterpret_cast<T *>(smem_raw);
+    const int wbytes = (lay.total * (int)sizeof(T) + 15) / 16 * 16;
+    {
+        const int n16 = wbytes / 16;
+        const int4 *src = reinterpret_cast<const int4 *>(gw);
+        int4 *dst = reinterpret_cast<int4 *>(sw);
+        for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = src[i];
+    }
+    T *acc = sw + wbytes / (int)sizeof(T);  // [np_pad] parameter-gradient accumulators
+    T *slabs = acc + np_pad;
+    for (int i = threadIdx.x; i < np_pad; i += blockDim.x) acc[i] = T(0);
+    __syncthreads();
+
+    const int L = lay.L;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int qi = lane >> 2, jb = lane & 3;
+    const int ql = warp * kQPW + qi;  // point index within the tile
+    T *qs = slabs + (size_t)ql * sl.size;
+    const int j0 = jb * NJ;
+    // offsets of the parameter blocks (theta order)
+    const int oW1 = 0, oc1 = W * D, oL = oc1 + W;
+    const int lsz = W * W + W * D + W;
+    const int oa = oL + (L - 1) * lsz, ob = oa + W;
+
+    const int64_t n_tiles = (n_qp + Q - 1) / Q;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t q = tile * Q + ql;
+        const bool valid = q < n_qp;
+        T F[9], G[9];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+            F[c] = valid ? Fg[c * n_qp + q] : ((c % 4) == 0 ? T(1) : T(0));
+            G[c] = valid ? Gg[c * n_qp + q] : T(0);
+        }
+        T K[D], Jm1;
+        bool bad = !kin_scalars<T, NF>(F, kc, K, Jm1);
+#pragma unroll
+        for (int c = 0; c < 9; ++c) bad = bad || !dev_finite(G[c]);
+        if (bad) {
+#pragma unroll
+            for (int c = 0; c < 9; ++c) {
+                F[c] = (c % 4) == 0 ? T(1) : T(0);
+                G[c] = T(0);
+            }
+            kin_scalars<T, NF>(F, kc, K, Jm1);
+        }
+        // r_m = G : g_m; the 4 lanes stage g (part 1, 2) and read it back
+        {
+            T zero[D];
+#pragma unroll
+            for (int m = 0; m < D; ++m) zero[m] = T(0);
+            stage_kinematics<T, NF>(F, kc, zero, Jm1, jb == 0 ? 1 : (jb == 1 ? 2 : 3), qs);
+        }
+        __syncwarp();
+        T r[D];
+        {
+            using S = Stage<D, NF>;
+#pragma unroll
+            for (int m = 0; m < D; ++m) {
+                T s = T(0);
+#pragma unroll
+                for (int a = 0; a < 9; ++a) s += G[a] * qs[S::g + 9 * m + a];
+                r[m] = s;
+            }
+        }
+        __syncwarp();
+        if (jb == 0) {
+#pragma unroll
+            for (int m = 0; m < D; ++m) {
+                qs[sl.K + m] = K[m];
+                qs[sl.r + m] = r[m];
+            }
+        }
+        __syncwarp();
+
+        // ---- forward: values and tangents along r
+        for (int k = 1; k <= L; ++k) {
+            T y[NJ], yd[NJ];
+#pragma unroll
+            for (int jj = 0; jj < NJ; ++jj) {
+                y[jj] = sw[lay.c + (k - 1) * W + j0 + jj];
+                yd[jj] = T(0);
+            }
+            if (k == 1) {
+#pragma unroll
+                for (int m = 0; m < D; ++m) {
+                    const T *wr = sw + lay.W1t + m * W + j0;
+#pragma unroll
+                    for (int jj = 0; jj < NJ; ++jj) {
+                        y[jj] += wr[jj] * K[m];
+                        yd[jj] += wr[jj] * r[m];
+                    }
+                }
+            } else {
+                const T *zin = qs + sl.z + (k - 2) * W, *zdin = qs + sl.zd + (k - 2) * W;
+                const T *At = sw + lay.At + (k - 2) * W * W + j0;
+#pragma unroll 4
+                for (int i = 0; i < W; ++i) {
+                    const T zi = zin[i], zdi = zdin[i];
+#pragma unroll
+                    for (int jj = 0; jj < NJ; ++jj) {
+                        y[jj] += At[i * W + jj] * zi;
+                        yd[jj] += At[i * W + jj] * zdi;
+                    }
+                }
+                const T *Bt = sw + lay.Bt + (k - 2) * D * W + j0;
+#pragma unroll
+                for (int m = 0; m < D; ++m)
+#pragma unroll
+                    for (int jj = 0; jj < NJ; ++jj) {
+                        y[jj] += Bt[m * W + jj] * K[m];
+                        yd[jj] += Bt[m * W + jj] * r[m];
+                    }
+            }
+#pragma unroll
+            for (int jj = 0; jj < NJ; ++jj) {
+                const int j = j0 + jj;
+                T z, s, t;
+                act(y[jj], z, s, t);
+                qs[sl.s + (k - 1) * W + j] = s;
+                qs[sl.t + (k - 1) * W + j] = t;
+                qs[sl.yd + (k - 1) * W + j] = yd[jj];
+                if (k < L) {
+                    qs[sl.z + (k - 1) * W + j] = z;
+                    qs[sl.zd + (k - 1) * W + j] = s * yd[jj];
+                } else {
+                    qs[sl.zdL + j] = s * yd[jj];
+                }
+            }
+            __syncwarp();
+        }
+
+        // ---- reverse over the tangent computation
+        T zb[NJ], zdb[NJ];
+#pragma unroll
+        for (int jj = 0; jj < NJ; ++jj) {
+            zb[jj] = T(0);
+            zdb[jj] = sw[lay.a + j0 + jj];
+        }
+        T Hr[D], dN[D];
+#pragma unroll
+        for (int m = 0; m < D; ++m) {
+            Hr[m] = T(0);
+            dN[m] = (jb == 0) ? sw[lay.b + m] : T(0);
+        }
+        for (int k = L; k >= 1; --k) {
+            const T *Bt = (k == 1) ? (sw + lay.W1t + j0) : (sw + lay.Bt + (k - 2) * D * W + j0);
+#pragma unroll
+            for (int jj = 0; jj < NJ; ++jj) {
+                const int j = j0 + jj;
+                const T s = qs[sl.s + (k - 1) * W + j], t = qs[sl.t + (k - 1) * W + j];
+                const T ydb = s * zdb[jj];
+                const T yb = s * zb[jj] + t * qs[sl.yd + (k - 1) * W + j] * zdb[jj];
+                qs[sl.yb + j] = yb;
+                qs[sl.ydb + j] = ydb;
+#pragma unroll
+                for (int m = 0; m < D; ++m) {
+                    Hr[m] += Bt[m * W + jj] * yb;
+                    dN[m] += Bt[m * W + jj] * ydb;
+                }
+            }
+            __syncthreads();
+            // tile reductions of this layer's weight gradients
+            const T *base = slabs;
+            if (k == 1) {
+                tile_outer<T>(acc + oW1, W, D, base, sl.size, sl.yb, sl.K, sl.ydb, sl.r, Q);
+                tile_sum<T>(acc + oc1, W, base, sl.size, sl.yb, Q);
+            } else {
+                const int o = oL + (k - 2) * lsz;
+                tile_outer<T>(acc + o, W, W, base, sl.size, sl.yb, sl.z + (k - 2) * W, sl.ydb, sl.zd + (k - 2) * W, Q);
+                tile_outer<T>(acc + o + W * W, W, D, base, sl.size, sl.yb, sl.K, sl.ydb, sl.r, Q);
+                tile_sum<T>(acc + o + W * W + W * D, W, base, sl.size, sl.yb, Q);
+                // zbar_{k-1} = A_k^T ybar_k, zdotbar_{k-1} = A_k^T ydotbar_k for own neurons
+                const T *Ar = sw + lay.Ar + (k - 2) * W * W + j0;
+#pragma unroll
+                for (int ii = 0; ii < NJ; ++ii) {
+                    zb[ii] = T(0);
+                    zdb[ii] = T(0);
+                }
+#pragma unroll 4
+                for (int j = 0; j < W; ++j) {
+                    const T ybj = qs[sl.yb + j], ydbj = qs[sl.ydb + j];
+#pragma unroll
+                    for (int ii = 0; ii < NJ; ++ii) {
+                        zb[ii] += Ar[j * W + ii] * ybj;
+                        zdb[ii] += Ar[j * W + ii] * ydbj;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        tile_sum<T>(acc + oa, W, slabs, sl.size, sl.zdL, Q);
+        tile_sum<T>(acc + ob, D, slabs, sl.size, sl.r, Q);
+
+        // ---- dL/dF = sum_n (Hr)_n g_n + G : S (structured part)
+#pragma unroll
+        for (int msk = 1; msk <= 2; msk <<= 1)
+#pragma unroll
+            for (int m = 0; m < D; ++m) {
+                Hr[m] += __shfl_xor_sync(0xffffffffu, Hr[m], msk);
+                dN[m] += __shfl_xor_sync(0xffffffffu, dN[m], msk);
+            }
+        __syncthreads();  // slabs are reused as staging below
+        T cvec[D];
+#pragma unroll
+        for (int m = 0; m < D; ++m) cvec[m] = dN[m] - sw[lay.n0 + m];
+        stage_kinematics<T, NF>(F, kc, cvec, Jm1, jb, qs);
+        __syncwarp();
+        if (dFg != nullptr) {
+            using S = Stage<D, NF>;
+            for (int b = jb; b < 9; b += kG) {
+                T v = contract_structured<T, NF>(b, qs, G);
+#pragma unroll
+                for (int n = 0; n < D; ++n) v += Hr[n] * qs[S::g + 9 * n + b];
+                if (valid) dFg[b * n_qp + q] = bad ? T(NAN) : v;
+            }
+        }
+        __syncthreads();
+    }
+    // write this CTA's partial sums
+    T *dst = partial + (size_t)blockIdx.x * np_pad;
+    for (int i = threadIdx.x; i < np_pad; i += blockDim.x) dst[i] = acc[i];
+}
+
+template <typename T>
+__global__ void reduce_partials_kernel(const T *__restrict__ partial, int n_blocks, int np, int np_pad,
+                                       T *__restrict__ out) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    T s = T(0);
+    for (int b = 0; b < n_blocks; ++b) s += partial[(size_t)b * np_pad + p];
+    out[p] = s;
+}
+
+static int bw_grid(const commet_model *m, int64_t n_qp, int Q) {
+    const int64_t n_tiles = (n_qp + Q - 1) / Q;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(n_tiles, 2 * (int64_t)sm_count()));
+}
+
+static int np_padded(const commet_model *m) { return (int)((m->n_params + 3) / 4 * 4); }
+
+size_t backward_workspace_bytes(const commet_model *m, int64_t n_qp) {
+    if (m->precision != COMMET_F64 && m->precision != COMMET_F32) return 0;
+    const size_t es = m->precision == COMMET_F64 ? 8 : 4;
+    const int Q = m->precision == COMMET_F64 ? BwConf<double>::Q : BwConf<float>::Q;
+    const size_t bytes = (size_t)bw_grid(m, n_qp, Q) * np_padded(m) * es;
+    return (bytes + 255) / 256 * 256;
+}
+
+template <typename T, int NF, int W>
+static int bw_typed(const commet_model *m, int64_t n_qp, const void *F, const void *G, void *dF, void *dth,
+                    void *ws, cudaStream_t s) {
+    KinConst<T> kc{};
+    kc.kin = m->kp.kin;
+    kc.stress_free = m->kp.stress_free;
+    kc.kappa = (T)m->kp.kappa;
+    for (int f = 0; f < 2; ++f)
+        for (int c = 0; c < 3; ++c) kc.fib[f][c] = (T)m->kp.fib[f][c];
+    const int D = 3 + 2 * NF;
+    const BwSlab sl = bw_slab(D, W, m->L, NF, (int)sizeof(T));
+    const int Q = BwConf<T>::Q;
+    const int np_pad = np_padded(m);
+    const size_t wbytes = ((size_t)m->lay.total * sizeof(T) + 15) / 16 * 16;
+    const size_t smem = wbytes + (size_t)np_pad * sizeof(T) + (size_t)Q * sl.size * sizeof(T);
+    int dev = 0, smem_max = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (smem > (size_t)smem_max) return COMMET_ERR_UNSUPPORTED;
+    auto kern = const_backward_kernel<T, NF, W>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return COMMET_ERR_CUDA;
+    const int grid = bw_grid(m, n_qp, Q);
+    kern<<<grid, BwConf<T>::warps * 32, smem, s>>>((const T *)m->d_weights, m->lay, kc, n_qp, (const T *)F,
+                                                   (const T *)G, (T *)dF, (T *)ws, np_pad, sl);
+    if (cudaGetLastError() != cudaSuccess) return COMMET_ERR_CUDA;
+    const int np = (int)m->n_params;
+    reduce_partials_kernel<T><<<(np + 255) / 256, 256, 0, s>>>((const T *)ws, grid, np, np_pad, (T *)dth);
+    return cudaGetLastError() == cudaSuccess ? COMMET_OK : COMMET_ERR_CUDA;
+}
+
+template <typename T>
+static int bw_dispatch(const commet_model *m, int64_t n_qp, const void *F, const void *G, void *dF, void *dth,
+                       void *ws, cudaStream_t s) {
+    const int nf = m->kp.nf, W = m->W;
+#define COMMET_CASE(NF_, W_) \
+    if (nf == NF_ && W == W_) return bw_typed<T, NF_, W_>(m, n_qp, F, G, dF, dth, ws, s);
+    COMMET_CASE(0, 16)
+    COMMET_CASE(0, 32)
+    COMMET_CASE(0, 64)
+    COMMET_CASE(1, 16)
+    COMMET_CASE(1, 32)
+    COMMET_CASE(2, 16)
+    COMMET_CASE(2, 32)
+    COMMET_CASE(2, 64)
+#undef COMMET_CASE
+    return COMMET_ERR_UNSUPPORTED;
+}
+
+int launch_const_backward(const commet_model *m, int64_t n_qp, const void *F, const void *G, void *dF, void *dth,
+                          void *ws, size_t ws_bytes, cudaStream_t s) {
+    (void)ws_bytes;
+    if (n_qp == 0) {
+        const size_t es = m->precision == COMMET_F64 ? 8 : 4;
+        return cudaMemsetAsync(dth, 0, es * m->n_params, s) == cudaSuccess ? COMMET_OK : COMMET_ERR_CUDA;
+    }
+    if (m->precision == COMMET_F64) return bw_dispatch<double>(m, n_qp, F, G, dF, dth, ws, s);
+    if (m->precision == COMMET_F32) return bw_dispatch<float>(m, n_qp, F, G, dF, dth, ws, s);
+    return COMMET_ERR_UNSUPPORTED;
+}
+
+}  // namespace commet

@@ -11,10 +11,5 @@ int launch_newton_assemble(const commet_model *, const commet_mesh *, const void
                            cudaStream_t) {
     return COMMET_ERR_UNSUPPORTED;
 }
-size_t backward_workspace_bytes(const commet_model *, int64_t) { return 0; }
-int launch_const_backward(const commet_model *, int64_t, const void *, const void *, void *, void *, void *, size_t,
-                          cudaStream_t) {
-    return COMMET_ERR_UNSUPPORTED;
-}
 
 }  // namespace commet

@@ -1,0 +1,176 @@
+"""GPU parity of the backward (adjoint) kernel: dL/dF and dL/dtheta against the FP64
+oracle, central differences of the training loss, determinism and the autograd path."""
+import numpy as np
+import pytest
+
+import oracle
+import workload as wl
+from tests.parity import TOL, assert_close, cm_to_pm, pm_to_cm
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DT = {"f64": torch.float64, "f32": torch.float32}
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2510_00884_gb300 as p
+    p.build()
+    return p
+
+
+def blocks_rel(g, r, spec, scale=None):
+    """Relative error of each parameter block (W1, c1, A_k, B_k, c_k, a, b). dL/dtheta is
+    a sum over points, so the error is measured against the sum of the magnitudes of the
+    per-point terms (``scale`` = sum_q |dtheta_q|, the usual bound of a floating-point
+    sum) when it is given: a block whose terms cancel has a small result but no smaller
+    rounding error."""
+    d, W, L = spec.d, spec.W, spec.L
+    sizes = [W * d, W] + [W * W, W * d, W] * (L - 1) + [W, d]
+    sc = r if scale is None else scale
+    out, o = [], 0
+    for n in sizes:
+        a, b = g[o:o + n], r[o:o + n]
+        out.append(np.linalg.norm(a - b) / max(np.linalg.norm(sc[o:o + n]), 1e-300))
+        o += n
+    return np.array(out)
+
+
+def oracle_dtheta_abs(spec, F, G):
+    """sum_q |dL/dtheta of point q| from per-point oracle calls."""
+    m = oracle.OracleModel(spec)
+    tot = None
+    for q in range(F.shape[0]):
+        _, t = oracle.const_backward(m, F[q:q + 1], G[q:q + 1])
+        tot = np.abs(t) if tot is None else tot + np.abs(t)
+    return tot
+
+
+CASES = [(wl.KIN_RAW, 2, 32, 3, 0.0, 3001), (wl.KIN_ISO_SHIFTED, 0, 16, 2, 10.0, 2049),
+         (wl.KIN_RAW, 1, 16, 4, 1.0, 777), (wl.KIN_RAW, 2, 32, 1, 2.0, 513), (wl.KIN_ISO_SHIFTED, 0, 32, 3, 5.0, 5)]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("case", CASES, ids=[f"k{c[0]}f{c[1]}w{c[2]}l{c[3]}n{c[5]}" for c in CASES])
+def test_backward_vs_oracle(pkg, case, prec):
+    kin, nf, W, L, kappa, n = case
+    rng = np.random.Generator(np.random.PCG64(200 + W + L))
+    spec = wl.make_model(rng, kin, nf, W=W, L=L, kappa=kappa, bias_std=0.1)
+    F = wl.random_F(rng, n, 0.15)
+    G = rng.normal(size=F.shape)
+    m = pkg.Model(spec, prec)
+    Fd, Gd = pm_to_cm(F, DT[prec]), pm_to_cm(G, DT[prec])
+    dF, dth = m.backward(Fd, Gd)
+    Fin, Gin = cm_to_pm(Fd).astype(np.float64), cm_to_pm(Gd).astype(np.float64)
+    dF_r, dth_r = oracle.const_backward(oracle.OracleModel(spec), Fin, Gin)
+    # dL/dF per point is G : A, compared like A; dL/dtheta block by block
+    tol_F = TOL[prec]
+    assert_close(cm_to_pm(dF), dF_r, tol_F, f"dF {prec}")
+    tol_th = 1e-12 if prec == "f64" else 1e-4
+    e = blocks_rel(dth.cpu().numpy().astype(np.float64), dth_r, spec, oracle_dtheta_abs(spec, Fin, Gin))
+    assert e.max() < tol_th, e
+
+
+def test_backward_c3_loss_central_differences(pkg):
+    """C3 loss sum_q |P(F; theta) - P_target|^2 on 64 points: GPU dL/dtheta and dL/dF
+    against central differences (h = 1e-6) of the GPU FP64 forward."""
+    w = wl.workload_c3(n_qp=64)
+    spec, F = w["model"], w["F"]
+    t = w["target"]
+    Fd = pm_to_cm(F, torch.float64)
+    Pt = pkg.target_stress(Fd, spec.fibres, t["mu"], t["k1"], t["k2"], t["kappa"])
+    m = pkg.Model(spec, "f64")
+    _, P, _ = m.const_update(Fd, want_A=False)
+    G = 2.0 * (P - Pt)
+    dF, dth = m.backward(Fd, G)
+    dth = dth.cpu().numpy()
+
+    def loss(spec_, Fdev):
+        _, PP, _ = pkg.Model(spec_, "f64").const_update(Fdev, want_A=False)
+        return float(((PP - Pt) ** 2).sum().item())
+    theta = spec.theta()
+    h = 1e-6
+    idx = np.unique(np.concatenate([np.arange(0, theta.size, 11), np.arange(theta.size - spec.W - spec.d,
+                                                                               theta.size)]))
+    fd = np.empty(idx.size)
+    for t_i, i in enumerate(idx):
+        e = np.zeros_like(theta)
+        e[i] = h
+        fd[t_i] = (loss(spec.with_theta(theta + e), Fd) - loss(spec.with_theta(theta - e), Fd)) / (2 * h)
+    assert np.linalg.norm(dth[idx] - fd) / np.linalg.norm(fd) < 1e-6
+    # dL/dF on a few entries
+    dFn = dF.cpu().numpy()
+    for (c, q) in [(0, 0), (4, 17), (8, 63), (1, 5), (6, 40)]:
+        Fp, Fm = Fd.clone(), Fd.clone()
+        Fp[c, q] += h
+        Fm[c, q] -= h
+        _, Pp, _ = m.const_update(Fp, want_A=False)
+        _, Pm, _ = m.const_update(Fm, want_A=False)
+        # the kernel's dL/dF is G : dP/dF of the model; the target is held at its value
+        lp = float(((Pp - Pt) ** 2).sum().item())
+        lm = float(((Pm - Pt) ** 2).sum().item())
+        fdv = (lp - lm) / (2 * h)
+        assert abs(dFn[c, q] - fdv) <= 1e-6 * max(1.0, abs(fdv))
+    # and the oracle's gradient on the same points
+    _, dth_r = oracle.const_backward(oracle.OracleModel(spec), F, cm_to_pm(G))
+    assert np.linalg.norm(dth - dth_r) / np.linalg.norm(dth_r) < 1e-12
+
+
+def test_backward_deterministic_and_linear(pkg):
+    """Bitwise-identical results on repeat; the sum over two halves equals the whole."""
+    rng = np.random.Generator(np.random.PCG64(31))
+    spec = wl.workload_c1(n=1)["model"]
+    n = 50_000
+    F = wl.random_F(rng, n, 0.15)
+    G = rng.normal(size=F.shape)
+    m = pkg.Model(spec, "f64")
+    Fd, Gd = pm_to_cm(F, torch.float64), pm_to_cm(G, torch.float64)
+    _, t1 = m.backward(Fd, Gd)
+    _, t2 = m.backward(Fd, Gd)
+    assert torch.equal(t1, t2)
+    h = n // 2
+    _, ta = m.backward(Fd[:, :h].contiguous(), Gd[:, :h].contiguous())
+    _, tb = m.backward(Fd[:, h:].contiguous(), Gd[:, h:].contiguous())
+    assert torch.allclose(ta + tb, t1, rtol=1e-12, atol=1e-12 * t1.abs().max().item())
+
+
+def test_autograd_function(pkg):
+    """torch autograd through the forward (stress) and the adjoint kernel."""
+    rng = np.random.Generator(np.random.PCG64(32))
+    spec = wl.make_model(rng, wl.KIN_RAW, 2, W=32, L=3, kappa=0.0)
+    m = pkg.Model(spec, "f64")
+    F = pm_to_cm(wl.random_F(rng, 1000, 0.15), torch.float64).requires_grad_(True)
+    sink = torch.zeros(m.n_params, dtype=torch.float64, device="cuda", requires_grad=True)
+    P = pkg.ConstUpdateP.apply(F, sink, m)
+    loss = (P ** 2).sum()
+    loss.backward()
+    dF_ref, dth_ref = m.backward(F.detach(), 2.0 * P.detach())
+    assert torch.allclose(F.grad, dF_ref, rtol=0, atol=0)
+    assert torch.allclose(sink.grad, dth_ref, rtol=0, atol=0)
+
+
+def test_backward_c3_full_size_sampled(pkg):
+    """1,048,576 points of the two-fibre network (the benchmark's backward launch):
+    sampled dL/dF against the oracle; dL/dtheta on a 2^14-point prefix against the oracle."""
+    w = wl.workload_c3()
+    spec, F = w["model"], w["F"]
+    t = w["target"]
+    m = pkg.Model(spec, "f64")
+    Fd = pm_to_cm(F, torch.float64)
+    Pt = pkg.target_stress(Fd, spec.fibres, t["mu"], t["k1"], t["k2"], t["kappa"])
+    _, P, _ = m.const_update(Fd, want_A=False)
+    G = (2.0 * (P - Pt)).contiguous()
+    dF, dth = m.backward(Fd, G)
+    idx = np.unique(np.linspace(0, F.shape[0] - 1, 800).astype(np.int64))
+    it = torch.from_numpy(idx).cuda()
+    Gs = G.index_select(1, it).cpu().numpy().T
+    dF_r, _ = oracle.const_backward(oracle.OracleModel(spec), F[idx], Gs)
+    assert_close(dF.index_select(1, it).cpu().numpy().T, dF_r, 1e-12, "C3 dF")
+    npre = 1 << 14
+    _, dth_pre = m.backward(Fd[:, :npre].contiguous(), G[:, :npre].contiguous())
+    Gpre = G[:, :npre].cpu().numpy().T
+    _, dth_r = oracle.const_backward(oracle.OracleModel(spec), F[:npre], Gpre)
+    e = blocks_rel(dth_pre.cpu().numpy(), dth_r, spec, oracle_dtheta_abs(spec, F[:npre], Gpre))
+    assert e.max() < 1e-12, e
+    assert np.all(np.isfinite(dth.cpu().numpy()))
