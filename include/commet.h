@@ -174,6 +174,25 @@ int commet_const_backward(const commet_model *m, int64_t n_qp, const void *F, co
                           void *dL_dtheta, void *workspace, size_t ws_bytes, void *stream);
 
 /*
+ * Backward that allocates nothing (no counterpart in the paper; it exists for callers
+ * whose host application owns all device memory and cannot hand the library a
+ * workspace). Same computation and arguments as commet_const_backward, minus the
+ * workspace: the per-CTA partial sums go to a fixed array of
+ * COMMET_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU that loads the
+ * library holds until the process exits.
+ *  - The first call on a device looks up that array's device address
+ *    (cudaGetSymbolAddress) with the device current; make it before any stream capture.
+ *  - All calls share the array: calls whose kernels may overlap on the GPU race and must
+ *    be serialised by the caller. Nothing in it needs to be zero before a call.
+ *  - Returns COMMET_ERR_UNSUPPORTED, launching nothing, when the call would need more
+ *    scratch than COMMET_NOALLOC_SCRATCH_BYTES (commet_const_backward_workspace() tells
+ *    the need; FP64 d7 W32 L3 needs about 7 MB, W64 networks do not fit).
+ */
+#define COMMET_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)
+int commet_const_backward_noalloc(const commet_model *m, int64_t n_qp, const void *F, const void *dL_dP,
+                                  void *dL_dF, void *dL_dtheta, void *stream);
+
+/*
  * Target stress of a closed-form Neo-Hookean-plus-fibre model, used as synthetic
  * training data for the backward:
  *   Psi_t = mu/2 (Ibar1 - 3) + kappa (J - 1)^2 + sum_f k1/(2 k2) (exp(k2 (I4_ff - 1)^2) - 1)

@@ -20,7 +20,7 @@ EXPORTED = [
     "commet_model_create", "commet_model_destroy", "commet_model_n_params", "commet_const_update",
     "commet_mesh_create", "commet_mesh_destroy", "commet_mesh_info", "commet_mesh_csr", "commet_compute_F",
     "commet_elem_assemble", "commet_newton_assemble", "commet_const_backward_workspace",
-    "commet_const_backward", "commet_target_stress", "commet_status_string",
+    "commet_const_backward", "commet_target_stress", "commet_status_string", "commet_const_backward_noalloc",
 ]
 
 
@@ -70,6 +70,7 @@ def load() -> C.CDLL:
         "commet_target_stress": ([i32, i64, vp, i32, C.POINTER(C.c_double), C.c_double, C.c_double,
                                   C.c_double, C.c_double, vp, vp], C.c_int),
         "commet_status_string": ([C.c_int], C.c_char_p),
+        "commet_const_backward_noalloc": ([vp, i64, vp, vp, vp, vp, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
