@@ -1,10 +1,15 @@
 """Benchmark of the neural-constitutive hot path on one node (one rank per GPU).
 
-A step is one pass of the whole hot path over the workload's batch, with inputs
-resident in HBM: the fused constitutive update (F -> Psi, P, A for every quadrature
-point) followed by the hex8 element integrals (P, A -> f_int, K_e for every element).
-The default workload is the 64^3 anisotropic mesh (262,144 elements, 2,097,152 points,
-two-fibre MICNN d7 W32 L3) in FP64.
+A step is one pass of the hot path over one batch of the workload, with inputs resident
+in HBM. Default workload (no flags) is `c1`: the 64^3 anisotropic mesh (262,144
+elements, 2,097,152 points, two-fibre MICNN d7 W32 L3) in FP64, where a step is the
+fused constitutive update (F -> Psi, P, A at every point) followed by the hex8 element
+integrals (P, A -> f_int, K_e for every element). Other workloads:
+  c0  8^3 cube: F from u, update, element integrals (FP64)
+  c2  128^3 uniaxial points, d3 W64 L3: the update (FP32 or bf16 tensor-core MLP)
+  c3  2^20 points of the c1 network: stress, loss gradient and the adjoint kernel
+  c4  96^3 cantilever: fused Newton assembly u -> r, CSR K (FP32), with the unfused
+      FP64 GPU path timed beside it
 
 Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle on the
 host cores instead (a bounded sample of the same workload per step).
@@ -29,22 +34,39 @@ if ROOT not in sys.path:
 METRIC = "qp constitutive updates/sec (P+tangent) and element assemblies/sec; % roofline"
 
 
-# ------------------------------------------------------------------ helpers
+# ------------------------------------------------------------------ work models
 
-def algorithmic_flops_per_qp(d: int, W: int, L: int) -> int:
-    """Minimal exact work per point, in flops (2 per multiply-add), counted as stated in
-    the design doc: network values W d + (L-1)(W^2 + W d), reverse adjoints (L-1) W^2 plus the
-    gradient L W d, tangents (L-1) W^2 d, Hessian L W d(d+1)/2, and the rank-one part of A
-    (9 d^2 + 81 d). Kinematics, activations and the structured terms of A are not counted."""
+def update_macs(d: int, W: int, L: int) -> int:
+    """Minimal exact multiply-adds per point of the forward update: network values
+    W d + (L-1)(W^2 + W d), reverse adjoints (L-1) W^2 plus the gradient L W d,
+    tangents (L-1) W^2 d, Hessian L W d(d+1)/2, rank-one part of A 9 d^2 + 81 d.
+    Kinematics, activations and the structured terms of A are not counted."""
     macs = W * d + (L - 1) * (W * W + W * d)
     macs += (L - 1) * W * W + L * W * d
     macs += (L - 1) * W * W * d
     macs += L * W * d * (d + 1) // 2
     macs += 9 * d * d + 81 * d
+    return macs
+
+
+def algorithmic_flops_per_qp(d: int, W: int, L: int) -> int:
+    return 2 * update_macs(d, W, L)
+
+
+def backward_flops_per_qp(d: int, W: int, L: int) -> int:
+    """Minimal multiply-adds (x2) per point of the backward: values and tangents along r
+    2 [W d + (L-1)(W^2 + W d)], reverse of both 2 (L-1) W^2, weight-gradient outer
+    products 2 [(L-1)(W^2 + W d) + W d], Hessian-vector and gradient sums 2 L W d, and
+    r = G : dK/dF plus dL/dF's rank-one part 2 * 9 d."""
+    macs = 2 * (W * d + (L - 1) * (W * W + W * d))
+    macs += 2 * (L - 1) * W * W
+    macs += 2 * ((L - 1) * (W * W + W * d) + W * d)
+    macs += 2 * L * W * d
+    macs += 2 * 9 * d
     return 2 * macs
 
 
-ELEM_FLOPS = 2 * 8 * (3 * 27 * 3 + 3 * 8 * 3 * 3)  # per element: 8 qp x (T3 + row contractions), MACs x 2
+ELEM_MACS = 8 * (3 * 27 * 3 + 3 * 8 * 3 * 3)  # per element: 8 qp x (T3 + row contractions)
 
 
 def load_peaks():
@@ -71,9 +93,10 @@ def kernel_source_hash(files) -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str, network: str, precision: str, src_hash: str, n_qp: int):
+def ncu_traffic(kernel: str, network: str, precision: str, src_hash: str, units: int):
     """Per-launch DRAM bytes of the kernel from the committed ncu summary, scaled from the
-    captured case to n_qp points; None when the kernel source changed since the capture."""
+    captured case to `units` (points or elements); None when the kernel source changed
+    since the capture."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
@@ -82,7 +105,7 @@ def ncu_traffic(kernel: str, network: str, precision: str, src_hash: str, n_qp: 
     e = tab.get(f"{kernel}|{network}|{precision}")
     if not e or e.get("src_hash") != src_hash:
         return None
-    return e["dram_bytes"] * n_qp / e["n_qp"]
+    return e["dram_bytes"] * units / e["units"]
 
 
 class ClockSampler:
@@ -126,15 +149,14 @@ class ClockSampler:
             if len(parts) < 9:
                 continue
             try:
-                rows.append((float(parts[1]), float(parts[2]), float(parts[3]) if parts[3] not in ("", "[N/A]") else 0.0,
-                             parts[5], parts[6], parts[7], parts[8]))
+                pw = float(parts[3]) if parts[3] not in ("", "[N/A]") else 0.0
+                rows.append((float(parts[1]), float(parts[2]), pw, parts[5], parts[6], parts[7], parts[8]))
             except ValueError:
                 continue
         os.unlink(self.path)
         if not rows:
             return out
-        sm = np.array([r[0] for r in rows])
-        out["sm_mhz"] = float(np.median(sm))
+        out["sm_mhz"] = float(np.median([r[0] for r in rows]))
         out["sm_max_mhz"] = float(max(r[1] for r in rows))
         out["power_w_max"] = float(max(r[2] for r in rows))
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -152,33 +174,195 @@ class ClockSampler:
 
 def make_workload(name: str, n: int | None = None):
     import workload as wl
-    if name == "c1":
-        return wl.workload_c1() if n is None else wl.workload_c1(n=n)
-    if name == "c0":
-        w = wl.workload_c0()
-        return w
-    raise SystemExit(f"unknown workload {name}")
+    kw = {} if n is None else ({"n_qp": n} if name == "c3" else {"n": n})
+    return {"c0": wl.workload_c0, "c1": wl.workload_c1, "c2": wl.workload_c2, "c3": wl.workload_c3,
+            "c4": wl.workload_c4}[name](**kw)
 
 
-def cpu_sample_rate(w, n_el_sample: int, threads: int):
-    """Oracle throughput (qp/s through update + element assembly) on the first
-    n_el_sample elements and their 8 n_el_sample points."""
+def wl_sub(mesh, el):
+    import workload as wl
+    return wl.Mesh(X=mesh.X, conn=mesh.conn[el], n=mesh.n)
+
+
+def cpu_sample_rate(w, n_el_sample: int):
+    """Oracle throughput on the first n_el_sample elements (qp/s and elements/s through
+    update + element assembly), or on the first 8 n_el_sample points for point workloads."""
     import oracle
-    os.environ.setdefault("OMP_NUM_THREADS", str(threads))
     oracle.build()
-    mesh, spec = w["mesh"], w["model"]
-    el = np.arange(min(n_el_sample, mesh.n_el))
-    F = w["F"][: 8 * el.size] if "F" in w else oracle.compute_F(mesh, w["u"])[: 8 * el.size]
+    spec = w["model"]
     m = oracle.OracleModel(spec)
+    if "mesh" not in w:  # c3: the backward
+        n = min(8 * n_el_sample, w["F"].shape[0])
+        F = w["F"][:n]
+        tgt = oracle.OracleModel(None, inner=oracle.INNER_HGO, kin=1, fibres=spec.fibres, **w["target"])
+        t0 = time.perf_counter()
+        _, Pt, _ = oracle.const_update(tgt, F, want_A=False)
+        _, P, _ = oracle.const_update(m, F, want_A=False)
+        oracle.const_backward(m, F, 2.0 * (P - Pt))
+        secs = time.perf_counter() - t0
+        return n / secs, None, secs, f"first {n} points, FP64 stress + loss + backward"
+    mesh = w["mesh"]
+    el = np.arange(min(n_el_sample, mesh.n_el))
+    F = w["F"][: 8 * el.size] if "F" in w else oracle.compute_F(wl_sub(mesh, el), w["u"])
     t0 = time.perf_counter()
     _, P, A = oracle.const_update(m, F)
-    t1 = time.perf_counter()
     oracle.elem_assemble(mesh, P, A, el=el)
-    t2 = time.perf_counter()
-    return 8 * el.size / (t2 - t0), el.size / (t2 - t0), t2 - t0
+    secs = time.perf_counter() - t0
+    return 8 * el.size / secs, el.size / secs, secs, \
+        f"first {el.size} elements and their {8 * el.size} points, FP64 update + element assembly"
 
 
 # --------------------------------------------------------------- our kernels
+
+class Run:
+    """Device buffers and the phases of one step for a workload."""
+
+    def __init__(self, name, w, prec, dev, pkg, torch):
+        self.name, self.w, self.prec, self.dev = name, w, prec, dev
+        dt = torch.float64 if prec == "f64" else torch.float32
+        self.dt = dt
+        spec = w["model"]
+        self.spec = spec
+        self.model = pkg.Model(spec, prec)
+        self.mesh = w.get("mesh")
+        mp = "f64" if prec == "f64" else "f32"
+        if name in ("c1", "c2"):
+            F_host = np.ascontiguousarray(w["F"].T)
+            self.inputs_host = {"F": F_host}
+            n = F_host.shape[1]
+            self.n_qp, self.n_el = n, n // 8
+            self.F = torch.from_numpy(F_host).to(device=dev, dtype=dt).contiguous()
+            self.psi = torch.empty(n, dtype=dt, device=dev)
+            self.P = torch.empty(9, n, dtype=dt, device=dev)
+            self.A = torch.empty(81, n, dtype=dt, device=dev)
+            self.outputs = [self.psi, self.P, self.A]
+            self.phases = [("const_update_kernel",
+                            lambda: self.model.const_update(self.F, out=(self.psi, self.P, self.A)))]
+            if name == "c1":
+                self.gmesh = pkg.Mesh(self.mesh.X, self.mesh.conn)
+                self.f_e = torch.empty(24, self.n_el, dtype=dt, device=dev)
+                self.K_e = torch.empty(576, self.n_el, dtype=dt, device=dev)
+                self.outputs += [self.f_e, self.K_e]
+                self.phases.append(("elem_assemble_kernel", lambda: self.gmesh.elem_assemble(
+                    self.P, self.A, mp, out=(self.f_e, self.K_e, None, None))))
+            else:
+                self.n_el = 0
+            self.input_dev = {"F": self.F}
+        elif name == "c0":
+            self.gmesh = pkg.Mesh(self.mesh.X, self.mesh.conn)
+            u_host = np.ascontiguousarray(w["u"].T)
+            self.inputs_host = {"u": u_host}
+            self.u = torch.from_numpy(u_host).to(device=dev, dtype=dt).contiguous()
+            self.n_el = self.mesh.n_el
+            self.n_qp = 8 * self.n_el
+            n = self.n_qp
+            self.Fb = torch.empty(9, n, dtype=dt, device=dev)
+            self.psi = torch.empty(n, dtype=dt, device=dev)
+            self.P = torch.empty(9, n, dtype=dt, device=dev)
+            self.A = torch.empty(81, n, dtype=dt, device=dev)
+            self.f_e = torch.empty(24, self.n_el, dtype=dt, device=dev)
+            self.K_e = torch.empty(576, self.n_el, dtype=dt, device=dev)
+            self.outputs = [self.psi, self.P, self.A, self.f_e, self.K_e]
+            self.phases = [("compute_F_kernel", lambda: self.gmesh.compute_F(self.u, mp, out=self.Fb)),
+                           ("const_update_kernel",
+                            lambda: self.model.const_update(self.Fb, out=(self.psi, self.P, self.A))),
+                           ("elem_assemble_kernel", lambda: self.gmesh.elem_assemble(
+                               self.P, self.A, mp, out=(self.f_e, self.K_e, None, None)))]
+            self.input_dev = {"u": self.u}
+        elif name == "c3":
+            F_host = np.ascontiguousarray(w["F"].T)
+            n = F_host.shape[1]
+            self.n_qp, self.n_el = n, 0
+            self.F = torch.from_numpy(F_host).to(device=dev, dtype=dt).contiguous()
+            t = w["target"]
+            self.Pt = pkg.target_stress(self.F, spec.fibres, t["mu"], t["k1"], t["k2"], t["kappa"])
+            self.inputs_host = {"F": F_host, "Pt": self.Pt.cpu().numpy()}
+            self.P = torch.empty(9, n, dtype=dt, device=dev)
+            self.G = torch.empty(9, n, dtype=dt, device=dev)
+            nb = int(pkg._lib.load().commet_const_backward_workspace(self.model.handle, n))
+            self.ws = torch.empty(max(1, nb), dtype=torch.uint8, device=dev)
+            self.dF = torch.empty_like(self.F)
+            self.dth = torch.empty(self.model.n_params, dtype=dt, device=dev)
+
+            def bw():
+                self.model.backward(self.F, self.G, workspace=self.ws, out=(self.dF, self.dth))
+
+            def loss_grad():
+                torch.sub(self.P, self.Pt, out=self.G)
+                self.G.mul_(2.0)
+            self.phases = [("const_update_kernel", lambda: self.model.const_update(
+                               self.F, want_A=False, want_psi=False, out=(None, self.P, None))),
+                           ("loss_gradient (torch elementwise)", loss_grad),
+                           ("const_backward_kernel", bw)]
+            self.outputs = [self.dF]
+            self.input_dev = {"F": self.F, "Pt": self.Pt}
+        elif name == "c4":
+            self.gmesh = pkg.Mesh(self.mesh.X, self.mesh.conn, want_csr=True)
+            u_host = np.ascontiguousarray(w["u"].T)
+            self.inputs_host = {"u": u_host}
+            self.u = torch.from_numpy(u_host).to(device=dev, dtype=dt).contiguous()
+            self.n_el = self.mesh.n_el
+            self.n_qp = 8 * self.n_el
+            self.r = torch.empty(3 * self.mesh.n_nodes, dtype=dt, device=dev)
+            self.Kv = torch.empty(self.gmesh.nnz, dtype=dt, device=dev)
+            self.outputs = [self.r, self.Kv]
+            self.phases = [("newton_kernel", lambda: pkg.newton_assemble(self.model, self.gmesh, self.u,
+                                                                         out=(self.r, self.Kv)))]
+            self.input_dev = {"u": self.u}
+        else:
+            raise SystemExit(f"unknown workload {name}")
+
+    def step(self):
+        for _, fn in self.phases:
+            fn()
+
+    def step_outputs(self):
+        return [self.dF] if self.name == "c3" else self.outputs
+
+
+def fp64_unfused_baseline(run, pkg, torch, dev, reps=2):
+    """The unfused FP64 GPU path on the same mesh and field (compute_F, const_update,
+    elem_assemble with the colour scatter): ms per pass."""
+    spec, mesh = run.spec, run.mesh
+    m64 = pkg.Model(spec, "f64")
+    u = run.u.double()
+    n = run.n_qp
+    F = torch.empty(9, n, dtype=torch.float64, device=dev)
+    P = torch.empty(9, n, dtype=torch.float64, device=dev)
+    A = torch.empty(81, n, dtype=torch.float64, device=dev)
+    r = torch.empty(3 * mesh.n_nodes, dtype=torch.float64, device=dev)
+    Kv = torch.empty(run.gmesh.nnz, dtype=torch.float64, device=dev)
+
+    def once():
+        run.gmesh.compute_F(u, "f64", out=F)
+        m64.const_update(F, want_psi=False, out=(None, P, A))
+        run.gmesh.elem_assemble(P, A, "f64", want_f=False, want_K=False, out=(None, None, r, Kv))
+    once()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        once()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    del F, P, A, r, Kv
+    torch.cuda.empty_cache()
+    return ms
+
+
+def launches_per_step(run) -> int:
+    """Kernels of this library launched by one step (the torch elementwise op of c3 is not one)."""
+    n = 0
+    for name, _ in run.phases:
+        if name == "newton_kernel":
+            n += run.gmesh.n_colours
+        elif name == "const_backward_kernel":
+            n += 2
+        elif not name.startswith("loss_gradient"):
+            n += 1
+    return n
+
 
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -187,32 +371,11 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     pkg.build()
-    w = make_workload(args.workload, args.n)
-    prec = args.precision
-    dt = torch.float64 if prec == "f64" else torch.float32
-    spec, mesh = w["model"], w["mesh"]
-    model = pkg.Model(spec, prec)
-    gmesh = pkg.Mesh(mesh.X, mesh.conn)
-    n_el = mesh.n_el
-    if "F" in w:
-        F_host = np.ascontiguousarray(w["F"].T)
-    else:
-        import torch as _t
-        u = _t.from_numpy(np.ascontiguousarray(w["u"].T)).to(dev)
-        F_host = gmesh.compute_F(u, "f64").cpu().numpy()
-    n_qp = F_host.shape[1]
-    F = torch.from_numpy(F_host).to(device=dev, dtype=dt).contiguous()
-    psi = torch.empty(n_qp, dtype=dt, device=dev)
-    P = torch.empty(9, n_qp, dtype=dt, device=dev)
-    A = torch.empty(81, n_qp, dtype=dt, device=dev)
-    f_e = torch.empty(24, n_el, dtype=dt, device=dev)
-    K_e = torch.empty(576, n_el, dtype=dt, device=dev)
+    name = args.workload
+    prec = args.precision or ("f32" if name == "c4" else "f64")
+    w = make_workload(name, args.n)
+    run = Run(name, w, prec, dev, pkg, torch)
     stream = torch.cuda.current_stream()
-
-    def step(Fin):
-        model.const_update(Fin, out=(psi, P, A))
-        gmesh.elem_assemble(P, A, prec, out=(f_e, K_e, None, None))
-
     dist = world > 1
     if dist:
         import torch.distributed as tdist
@@ -222,11 +385,12 @@ def run_ours(args, rank, world, local_rank):
             tdist.barrier()
 
     for _ in range(args.warmup):
-        step(F)
+        run.step()
     torch.cuda.synchronize()
 
     n_steps = args.steps
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(n_steps)]
+    nph = len(run.phases)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(nph + 1)] for _ in range(n_steps)]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local_rank) as clk:
         barrier()
@@ -234,38 +398,37 @@ def run_ours(args, rank, world, local_rank):
         t_start.record(stream)
         for s in range(n_steps):
             ev[s][0].record(stream)
-            model.const_update(F, out=(psi, P, A))
-            ev[s][1].record(stream)
-            gmesh.elem_assemble(P, A, prec, out=(f_e, K_e, None, None))
-            ev[s][2].record(stream)
+            for p, (_, fn) in enumerate(run.phases):
+                fn()
+                ev[s][p + 1].record(stream)
         t_end.record(stream)
         torch.cuda.synchronize()
         barrier()
     total_ms = t_start.elapsed_time(t_end)
-    cu_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
-    el_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
+    phase_ms = [float(np.mean([e[p].elapsed_time(e[p + 1]) for e in ev])) for p in range(nph)]
     clocks = clk.summary()
     if dist:
         t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
         tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
         total_ms = float(t.item())
     ms_per_step = total_ms / n_steps
-    qps = world * n_qp * n_steps / (total_ms * 1e-3)
-    eps = world * n_el * n_steps / (total_ms * 1e-3)
+    qps = world * run.n_qp * n_steps / (total_ms * 1e-3)
+    eps = world * run.n_el * n_steps / (total_ms * 1e-3) if run.n_el else None
 
     # ---- end to end through the public API with pinned host buffers
     e2e = None
     if not args.no_e2e:
-        F_pin = torch.from_numpy(F_host).to(dt).pin_memory()
-        outs_h = [torch.empty(t.shape, dtype=dt).pin_memory() for t in (psi, P, A, f_e, K_e)]
-        h2d = F_pin.numel() * F_pin.element_size()
+        pin_in = {k: torch.from_numpy(v).to(run.dt).pin_memory() for k, v in run.inputs_host.items()}
+        outs = run.step_outputs()
+        outs_h = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in outs]
+        h2d = sum(t.numel() * t.element_size() for t in pin_in.values())
         d2h = sum(t.numel() * t.element_size() for t in outs_h)
-        Fd = torch.empty_like(F)
 
         def e2e_step():
-            Fd.copy_(F_pin, non_blocking=True)
-            step(Fd)
-            for src, dst in zip((psi, P, A, f_e, K_e), outs_h):
+            for k, t in pin_in.items():
+                run.input_dev[k].copy_(t, non_blocking=True)
+            run.step()
+            for src, dst in zip(run.step_outputs(), outs_h):
                 dst.copy_(src, non_blocking=True)
         for _ in range(max(1, args.warmup)):
             e2e_step()
@@ -284,56 +447,80 @@ def run_ours(args, rank, world, local_rank):
             t = torch.tensor([e_ms], device=dev, dtype=torch.float64)
             tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
             e_ms = float(t.item())
-        e2e = {"value": world * n_qp * n_e2e / (e_ms * 1e-3), "unit": "qp/s",
+        e2e = {"value": world * run.n_qp * n_e2e / (e_ms * 1e-3), "unit": "qp/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": n_e2e,
                "ms_per_step": e_ms / n_e2e}
+
+    fp64_base = None
+    if name == "c4" and not args.no_baseline and rank == 0:
+        b_ms = fp64_unfused_baseline(run, pkg, torch, dev)
+        fp64_base = {"what": "unfused FP64 GPU path (compute_F, const_update, elem_assemble + colour scatter)",
+                     "ms_per_step": b_ms, "qp_per_s": run.n_qp / (b_ms * 1e-3),
+                     "speedup_of_fused": b_ms / ms_per_step}
 
     if rank != 0:
         return None
 
-    # ---- roofline of the dominant kernel (the fused constitutive update)
+    # ---- roofline of the dominant kernel
     peaks, peak_src = load_peaks()
-    props = torch.cuda.get_device_properties(dev)
-    n_sm = props.multi_processor_count
-    flops_qp = algorithmic_flops_per_qp(spec.d, spec.W, spec.L)
-    peak = alu_peak_tflops(prec, n_sm, float(peaks.get("sm_max_mhz", 2070.0)))
-    achieved = flops_qp * n_qp / (cu_ms * 1e-3) / 1e12
-    src_hash = kernel_source_hash(["const_update.cu", "device_math.cuh"])
-    traffic = ncu_traffic("const_update_kernel", f"d{spec.d}w{spec.W}l{spec.L}", prec, src_hash, n_qp)
-    roofline = {"bound": "alu", "kernel": "const_update_kernel", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                "peak_source": f"derived: {n_sm} SMs x {'2 DFMA' if prec == 'f64' else '128 FFMA'}/clk x "
-                               f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz (max SM clock, {peak_src} peaks file)",
-                "algorithmic_flops_per_qp": flops_qp, "kernel_ms": cu_ms,
-                "frac_at_median_clock": (achieved / peak * float(peaks.get("sm_max_mhz", 2070.0)) /
-                                         clocks["sm_mhz"]) if clocks.get("sm_mhz") else None,
-                "elem_kernel": {"ms": el_ms, "bytes_per_el": (8 * 90 + 600) * (8 if prec == "f64" else 4),
-                                "achieved_gbs": n_el * (8 * 90 + 600) * (8 if prec == "f64" else 4) / (el_ms * 1e-3) / 1e9,
-                                "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)),
-                                "achieved_tflops": n_el * ELEM_FLOPS / (el_ms * 1e-3) / 1e12}}
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    spec = run.spec
+    net = f"d{spec.d}w{spec.W}l{spec.L}"
+    dom = int(np.argmax(phase_ms))
+    kname = run.phases[dom][0]
+    alu = "f64" if prec == "f64" else "f32"
+    if kname == "const_update_kernel":
+        flops = algorithmic_flops_per_qp(spec.d, spec.W, spec.L) * run.n_qp
+        units, src = run.n_qp, ["const_update.cu", "qp_body.cuh", "device_math.cuh"]
+    elif kname == "const_backward_kernel":
+        flops = backward_flops_per_qp(spec.d, spec.W, spec.L) * run.n_qp
+        units, src = run.n_qp, ["backward.cu", "device_math.cuh"]
+    elif kname == "newton_kernel":
+        flops = (algorithmic_flops_per_qp(spec.d, spec.W, spec.L) * 8 + 2 * ELEM_MACS) * run.n_el
+        units, src = run.n_el, ["newton.cu", "qp_body.cuh", "device_math.cuh"]
+    else:
+        flops = 2 * ELEM_MACS * run.n_el
+        units, src = run.n_el, ["elem.cu"]
+    peak = alu_peak_tflops(alu, n_sm, mhz)
+    achieved = flops / (phase_ms[dom] * 1e-3) / 1e12
+    src_hash = kernel_source_hash(src)
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak,
+                "traffic": ncu_traffic(kname, net, prec, src_hash, units),
+                "peak_source": f"derived: {n_sm} SMs x {'2 DFMA' if alu == 'f64' else '128 FFMA'}/clk x 2 flop x "
+                               f"{mhz:.0f} MHz (max SM clock; {peak_src} peaks file)",
+                "algorithmic_flops_per_launch": flops, "kernel_ms": phase_ms[dom],
+                "frac_at_median_clock": (achieved / peak * mhz / clocks["sm_mhz"]) if clocks.get("sm_mhz") else None,
+                "src_hash": src_hash}
+    phases = {n_: ms for (n_, _), ms in zip(run.phases, phase_ms)}
+    if "elem_assemble_kernel" in phases:
+        es = 8 if prec == "f64" else 4
+        el_ms = phases["elem_assemble_kernel"]
+        roofline["elem_kernel"] = {"ms": el_ms, "bytes_per_el": (8 * 90 + 600) * es,
+                                   "achieved_gbs": run.n_el * (8 * 90 + 600) * es / (el_ms * 1e-3) / 1e9,
+                                   "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)),
+                                   "achieved_tflops": run.n_el * 2 * ELEM_MACS / (el_ms * 1e-3) / 1e12}
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        threads = os.cpu_count() or 1
-        qps_cpu, eps_cpu, secs = cpu_sample_rate(w, args.cpu_sample_el, threads)
-        cpu = {"value": qps_cpu, "unit": "qp/s", "cores": threads, "kind": "oracle",
-               "sample": f"first {min(args.cpu_sample_el, n_el)} elements and their "
-                         f"{8 * min(args.cpu_sample_el, n_el)} points of the same workload, FP64, "
-                         f"update + element assembly, {secs:.1f} s",
-               "elements_per_s": eps_cpu}
+        qps_cpu, eps_cpu, secs, what = cpu_sample_rate(w, args.cpu_sample_el)
+        cpu = {"value": qps_cpu, "unit": "qp/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+               "sample": f"{what} of {w['name']}, {secs:.1f} s", "elements_per_s": eps_cpu}
 
-    return {
+    cfg = {"workload": w["name"], "n_qp": run.n_qp, "n_el": run.n_el, "network": f"d{spec.d} W{spec.W} L{spec.L}",
+           "precision": prec, "parallelism": f"replicas x{world} (independent meshes)",
+           "l2": "inputs/outputs larger than L2 (129 MB) every step"}
+    res = {
         "metric": METRIC, "value": qps, "unit": "qp/s", "n_gpus": world, "steps": n_steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": prec, "data": "synthetic (seeded; random non-negative MICNN weights)",
-        "elements_per_s": eps,
-        "config": {"workload": w["name"], "n_qp": n_qp, "n_el": n_el, "network": f"d{spec.d} W{spec.W} L{spec.L}",
-                   "precision": prec, "parallelism": f"replicas x{world} (independent meshes)",
-                   "l2": "inputs larger than L2: F %.0f MB, A %.0f MB per step" %
-                         (9 * n_qp * F.element_size() / 1e6, 81 * n_qp * F.element_size() / 1e6)},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * n_steps,
-        "clocks": clocks,
+        "elements_per_s": eps, "phases_ms": phases, "config": cfg, "roofline": roofline, "cpu_baseline": cpu,
+        "e2e": e2e, "gpu_launches": n_steps * launches_per_step(run), "clocks": clocks,
     }
+    if fp64_base is not None:
+        res["fp64_unfused_gpu"] = fp64_base
+    return res
 
 
 # ----------------------------------------------------------- reference arm
@@ -341,34 +528,47 @@ def run_ours(args, rank, world, local_rank):
 def run_reference(args):
     """The FP64 oracle on the host cores; each step is a bounded sample of the workload."""
     import oracle
-    threads = os.cpu_count() or 1
-    os.environ.setdefault("OMP_NUM_THREADS", str(threads))
     oracle.build()
-    w = make_workload(args.workload, args.n)
-    mesh, spec = w["mesh"], w["model"]
-    n_el_s = min(args.ref_sample_el, mesh.n_el)
-    el = np.arange(n_el_s)
-    F = w["F"][: 8 * n_el_s] if "F" in w else oracle.compute_F(mesh, w["u"])[: 8 * n_el_s]
+    name = args.workload
+    w = make_workload(name, args.n)
+    spec = w["model"]
     m = oracle.OracleModel(spec)
+    if "mesh" in w:
+        mesh = w["mesh"]
+        n_el_s = min(args.ref_sample_el, mesh.n_el)
+        el = np.arange(n_el_s)
+        F = w["F"][: 8 * n_el_s] if "F" in w else oracle.compute_F(wl_sub(mesh, el), w["u"])
+        n_qp_s = 8 * n_el_s
 
-    def step():
-        _, P, A = oracle.const_update(m, F)
-        oracle.elem_assemble(mesh, P, A, el=el)
+        def step():
+            _, P, A = oracle.const_update(m, F)
+            oracle.elem_assemble(mesh, P, A, el=el)
+        sample = f"first {n_el_s} elements / {n_qp_s} points of {w['name']} per step, FP64 update + assembly"
+    else:
+        n_qp_s = min(8 * args.ref_sample_el, w["F"].shape[0])
+        n_el_s = 0
+        F = w["F"][:n_qp_s]
+        tgt = oracle.OracleModel(None, inner=oracle.INNER_HGO, kin=1, fibres=spec.fibres, **w["target"])
+        _, Pt, _ = oracle.const_update(tgt, F, want_A=False)
+
+        def step():
+            _, P, _ = oracle.const_update(m, F, want_A=False)
+            oracle.const_backward(m, F, 2.0 * (P - Pt))
+        sample = f"first {n_qp_s} points of {w['name']} per step, FP64 stress + backward"
     for _ in range(args.warmup):
         step()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         step()
     secs = time.perf_counter() - t0
-    qps = 8 * n_el_s * args.steps / secs
-    sample = f"first {n_el_s} elements / {8 * n_el_s} points of {w['name']} per step, FP64"
+    qps = n_qp_s * args.steps / secs
+    threads = os.cpu_count() or 1
     return {
         "impl": "reference", "metric": METRIC, "value": qps, "unit": "qp/s", "n_gpus": 0, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "elements_per_s": n_el_s * args.steps / secs,
-        "config": {"workload": w["name"], "n_qp": 8 * mesh.n_el, "n_el": mesh.n_el, "precision": "f64",
-                   "sample_el": n_el_s},
+        "elements_per_s": (n_el_s * args.steps / secs) if n_el_s else None,
+        "config": {"workload": w["name"], "precision": "f64", "sample_qp": n_qp_s},
         "cpu_baseline": {"value": qps, "unit": "qp/s", "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": qps, "unit": "qp/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -380,11 +580,13 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="c1")
-    ap.add_argument("--n", type=int, default=None, help="mesh size per side (default: the workload's)")
-    ap.add_argument("--precision", choices=["f64", "f32"], default="f64")
+    ap.add_argument("--workload", choices=["c0", "c1", "c2", "c3", "c4"], default="c1")
+    ap.add_argument("--n", type=int, default=None, help="mesh size per side (points for c3)")
+    ap.add_argument("--precision", choices=["f64", "f32", "bf16"], default=None,
+                    help="default: f64 (f32 for c4)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-baseline", action="store_true", help="c4: skip the unfused FP64 GPU timing")
     ap.add_argument("--cpu-sample-el", type=int, default=65536)
     ap.add_argument("--ref-sample-el", type=int, default=4096)
     args = ap.parse_args()

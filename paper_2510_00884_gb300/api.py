@@ -91,14 +91,17 @@ class Model:
             self.handle, n, _ptr(F), _ptr(psi), _ptr(P), _ptr(A), _ptr(st), _stream()))
         return (psi, P, A, st) if status else (psi, P, A)
 
-    def backward(self, F: torch.Tensor, G: torch.Tensor, want_dF: bool = True, workspace=None):
+    def backward(self, F: torch.Tensor, G: torch.Tensor, want_dF: bool = True, workspace=None, out=None):
         """dL/dF[9, n] (or None) and dL/dtheta[n_params] for upstream G = dL/dP [9, n]."""
         _check_dev(F, self.dtype, name="F")
         _check_dev(G, self.dtype, shape=F.shape, name="G")
         lib = _lib.load()
         n = F.shape[1]
-        dF = torch.empty_like(F) if want_dF else None
-        dth = torch.empty(self.n_params, dtype=self.dtype, device=F.device)
+        if out is None:
+            dF = torch.empty_like(F) if want_dF else None
+            dth = torch.empty(self.n_params, dtype=self.dtype, device=F.device)
+        else:
+            dF, dth = out
         ws_bytes = int(lib.commet_const_backward_workspace(self.handle, n))
         if workspace is None or workspace.numel() < ws_bytes:
             workspace = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=F.device)

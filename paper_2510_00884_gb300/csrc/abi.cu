@@ -173,6 +173,13 @@ int commet_model_create(const commet_model_desc *desc, int32_t precision, commet
             return rc;
         }
     }
+    if (precision == COMMET_BF16_MLP) {
+        rc = prepare_bf16_weights(m);
+        if (rc != COMMET_OK) {
+            commet_model_destroy(m);
+            return rc;
+        }
+    }
     *out = m;
     return COMMET_OK;
 }

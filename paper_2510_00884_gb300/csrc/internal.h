@@ -90,6 +90,7 @@ int launch_elem_assemble(const commet_mesh *mesh, int precision, const void *P, 
                          void *K_e, void *r, void *K_vals, cudaStream_t s);
 int launch_newton_assemble(const commet_model *m, const commet_mesh *mesh, const void *u, void *r, void *K_vals,
                            int32_t *status, cudaStream_t s);
+int prepare_bf16_weights(commet_model *m);
 size_t backward_workspace_bytes(const commet_model *m, int64_t n_qp);
 int launch_const_backward(const commet_model *m, int64_t n_qp, const void *F, const void *G, void *dF, void *dtheta,
                           void *ws, size_t ws_bytes, cudaStream_t s);
