@@ -191,8 +191,8 @@ def cpu_sample_rate(w, n_el_sample: int):
     oracle.build()
     spec = w["model"]
     m = oracle.OracleModel(spec)
-    if "mesh" not in w:  # c3: the backward
-        n = min(8 * n_el_sample, w["F"].shape[0])
+    if "mesh" not in w:  # c3: the backward (the oracle's backward runs on one core)
+        n = min(2 * n_el_sample, w["F"].shape[0])
         F = w["F"][:n]
         tgt = oracle.OracleModel(None, inner=oracle.INNER_HGO, kin=1, fibres=spec.fibres, **w["target"])
         t0 = time.perf_counter()

@@ -268,9 +268,10 @@ __global__ void __launch_bounds__(192)
         for (int h = 0; h < 2; ++h)
 #pragma unroll
             for (int i = 0; i < NH; ++i) Hs[h][i] = 0.f;
+        const bool want_A = (A != nullptr);  // P alone needs dN/dK, not the Hessian
         // layer 1: J_1 = W1
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt)
+        for (int nt = 0; nt < NT && want_A; ++nt)
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int j = 8 * nt + 2 * t + (e & 1), h = e >> 1;
@@ -283,7 +284,7 @@ __global__ void __launch_bounds__(192)
                     for (int n = 0; n <= m; ++n) Hs[h][m * (m + 1) / 2 + n] += dm * w1[n];
                 }
             }
-        if (L >= 2) {
+        if (L >= 2 && want_A) {
             // A fragments of s_1 (x) W1[:, m] for every input m
             uint32_t tf[D][KT][4];
 #pragma unroll
@@ -383,7 +384,13 @@ __global__ void __launch_bounds__(192)
             bool nonfinite = false;
             for (int a = t; a < 9; a += 4) {
                 float Pa, Arow[9];
-                assemble_row<float, NF>(a, st, Hs[h], cvec, Pa, Arow);
+                if (want_A) {
+                    assemble_row<float, NF>(a, st, Hs[h], cvec, Pa, Arow);
+                } else {
+                    Pa = assemble_P<float, NF>(a, st, cvec);
+#pragma unroll
+                    for (int b = 0; b < 9; ++b) Arow[b] = 0.f;
+                }
                 bool fin = isfinite(Pa);
 #pragma unroll
                 for (int b = 0; b < 9; ++b) fin = fin && isfinite(Arow[b]);

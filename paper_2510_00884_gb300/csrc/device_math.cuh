@@ -288,6 +288,17 @@ __device__ __forceinline__ void stage_kinematics(const T *F, const KinConst<T> &
     }
 }
 
+// P_a alone (no tangent): sum_m c_m g_m[a] + 2 kappa (J - 1) J H_a.
+template <typename T, int NF>
+__device__ __forceinline__ T assemble_P(int a, const T *st, const T *c) {
+    constexpr int D = 3 + 2 * NF;
+    using S = Stage<D, NF>;
+    T p = T(0);
+#pragma unroll
+    for (int m = 0; m < D; ++m) p += c[m] * st[S::g + 9 * m + a];
+    return p + st[S::sc + 4 + NF] * st[S::H + a];
+}
+
 // Row a = 3i + J of P and A from the staged quantities; Hs is the packed lower
 // triangle of d2N/dK2 (index m*(m+1)/2 + n, n <= m), c = dN/dK - n0.
 template <typename T, int NF>

@@ -179,10 +179,12 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
         __syncwarp();
     }
 
-    // ---- forward tangents and Hessian
+    // ---- forward tangents and Hessian (only when A is wanted: P needs dN/dK alone)
+    const bool want_A = (Aq != nullptr);
     T Hs[NH];
 #pragma unroll
     for (int h = 0; h < NH; ++h) Hs[h] = T(0);
+    if (want_A) {
 #pragma unroll
     for (int jj = 0; jj < NJ; ++jj) {
         const int j = j0 + jj;
@@ -258,6 +260,8 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
         __syncwarp();
     }
 
+    }  // want_A
+
     // ---- reduce the group's partial sums
 #pragma unroll
     for (int msk = 1; msk <= 2; msk <<= 1) {
@@ -284,7 +288,13 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
     bool nonfinite = false;
     for (int a = jb; a < 9; a += kG) {
         T Pa, Arow[9];
-        assemble_row<T, NF>(a, qs, Hs, cvec, Pa, Arow);
+        if (want_A) {
+            assemble_row<T, NF>(a, qs, Hs, cvec, Pa, Arow);
+        } else {
+            Pa = assemble_P<T, NF>(a, qs, cvec);
+#pragma unroll
+            for (int b = 0; b < 9; ++b) Arow[b] = T(0);
+        }
         bool fin = dev_finite(Pa);
 #pragma unroll
         for (int b = 0; b < 9; ++b) fin = fin && dev_finite(Arow[b]);

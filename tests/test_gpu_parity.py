@@ -260,3 +260,21 @@ def test_c1_full_size_sampled(pkg, prec):
     et = torch.from_numpy(el).cuda()
     assert_close(f_e.index_select(1, et).cpu().numpy().T, f_r, TOL[prec], "C1 f_e")
     assert_close(K_e.index_select(1, et).cpu().numpy().T, K_r.reshape(-1, 576), TOL[prec], "C1 K_e")
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+def test_stress_only_path(pkg, prec):
+    """Without A the kernels skip the tangent pass; P and psi must not change."""
+    rng = np.random.Generator(np.random.PCG64(51))
+    spec = wl.make_model(rng, wl.KIN_RAW, 2, W=32, L=3, kappa=1.0)
+    F = wl.random_F(rng, 3001, 0.15)
+    m = pkg.Model(spec, prec)
+    Fd = pm_to_cm(F, torch.float64 if prec == "f64" else torch.float32)
+    psi1, P1, A1 = m.const_update(Fd)
+    psi2, P2, A2 = m.const_update(Fd, want_A=False)
+    assert A2 is None
+    torch.cuda.synchronize()
+    assert torch.equal(P1, P2) or (P1 - P2).abs().max().item() <= 1e-14 * P1.abs().max().item()
+    assert torch.equal(psi1, psi2)
+    _, P_r, _ = oracle.const_update(oracle.OracleModel(spec), cm_to_pm(Fd).astype(np.float64))
+    assert_close(cm_to_pm(P2), P_r, TOL[prec], f"stress only {prec}")
