@@ -14,7 +14,7 @@
 namespace commet {
 
 template <typename T, int NF, int W>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512)
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 384)
     const_update_kernel(const T *__restrict__ gw, NetLayout lay, KinConst<T> kc, int64_t n_qp,
                         const T *__restrict__ Fg, T *__restrict__ psi, T *__restrict__ P, T *__restrict__ A,
                         int32_t *__restrict__ status, T *__restrict__ dN_out, int qstride) {
@@ -94,7 +94,7 @@ static int launch_typed(const commet_model *m, int64_t n_qp, const void *F, void
     cudaGetDevice(&dev);
     int smem_max = 0;
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const int max_threads = sizeof(T) == 8 ? 256 : 512;
+    const int max_threads = sizeof(T) == 8 ? 256 : 384;
     int warps = (int)std::min<size_t>((size_t)max_threads / 32, (smem_max - wbytes) / per_warp);
     if (smem_max < (int)wbytes || warps < 1) return COMMET_ERR_UNSUPPORTED;
     const size_t smem = wbytes + warps * per_warp;

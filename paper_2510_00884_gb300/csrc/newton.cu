@@ -68,7 +68,7 @@ __device__ __forceinline__ void gauss_grads(const T *Xe, int q, T *gX, T &w) {
 }  // namespace
 
 template <typename T, int NF, int W>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512)
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 384)
     newton_kernel(const T *__restrict__ gw, NetLayout lay, KinConst<T> kc, const int32_t *__restrict__ el_list,
                   int64_t n_list, const int32_t *__restrict__ conn, const double *__restrict__ X,
                   const T *__restrict__ u, int64_t n_nodes, T *__restrict__ r, T *__restrict__ K_vals,
@@ -201,7 +201,7 @@ static int newton_typed(const commet_model *m, const commet_mesh *mesh, const vo
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if ((size_t)smem_max < wbytes + per_warp) return COMMET_ERR_UNSUPPORTED;
-    const int max_threads = sizeof(T) == 8 ? 256 : 512;
+    const int max_threads = sizeof(T) == 8 ? 256 : 384;
     const int warps = (int)std::min<size_t>((size_t)max_threads / 32, (smem_max - wbytes) / per_warp);
     const size_t smem = wbytes + warps * per_warp;
     auto kern = newton_kernel<T, NF, W>;

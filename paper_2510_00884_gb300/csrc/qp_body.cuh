@@ -59,6 +59,42 @@ __device__ __forceinline__ T shfl_xor(T v, int m) {
     return __shfl_xor_sync(0xffffffffu, v, m);
 }
 
+// 128-bit shared-memory loads/stores of N consecutive elements (p 16-byte aligned,
+// N a multiple of 16 / sizeof(T)).
+template <int N, typename T>
+__device__ __forceinline__ void ldv(const T *p, T *r) {
+    if constexpr (sizeof(T) == 8) {
+        static_assert(N % 2 == 0, "ldv<double>: N must be even");
+#pragma unroll
+        for (int v = 0; v < N / 2; ++v) {
+            const double2 x = reinterpret_cast<const double2 *>(p)[v];
+            r[2 * v] = x.x;
+            r[2 * v + 1] = x.y;
+        }
+    } else {
+        static_assert(N % 4 == 0, "ldv<float>: N must be a multiple of 4");
+#pragma unroll
+        for (int v = 0; v < N / 4; ++v) {
+            const float4 x = reinterpret_cast<const float4 *>(p)[v];
+            r[4 * v] = x.x;
+            r[4 * v + 1] = x.y;
+            r[4 * v + 2] = x.z;
+            r[4 * v + 3] = x.w;
+        }
+    }
+}
+template <int N, typename T>
+__device__ __forceinline__ void stv(T *p, const T *r) {
+    if constexpr (sizeof(T) == 8) {
+#pragma unroll
+        for (int v = 0; v < N / 2; ++v) reinterpret_cast<double2 *>(p)[v] = make_double2(r[2 * v], r[2 * v + 1]);
+    } else {
+#pragma unroll
+        for (int v = 0; v < N / 4; ++v)
+            reinterpret_cast<float4 *>(p)[v] = make_float4(r[4 * v], r[4 * v + 1], r[4 * v + 2], r[4 * v + 3]);
+    }
+}
+
 // One point on its 4-lane group (all 32 lanes of the warp call this together).
 //  F      the point's deformation gradient (replaced by I when it is not admissible)
 //  valid  false for padding points: computed on F = I, nothing written
@@ -87,46 +123,55 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
     }
 
     // ---- forward values
+    constexpr int V = 16 / (int)sizeof(T);  // elements per 128-bit shared load
     T npart = T(0);
     for (int k = 1; k <= L; ++k) {
         T y[NJ];
-#pragma unroll
-        for (int jj = 0; jj < NJ; ++jj) y[jj] = sw[lay.c + (k - 1) * W + j0 + jj];
+        ldv<NJ>(sw + lay.c + (k - 1) * W + j0, y);
         if (k == 1) {
 #pragma unroll
             for (int m = 0; m < D; ++m) {
-                const T *wr = sw + lay.W1t + m * W + j0;
+                T w[NJ];
+                ldv<NJ>(sw + lay.W1t + m * W + j0, w);
 #pragma unroll
-                for (int jj = 0; jj < NJ; ++jj) y[jj] += wr[jj] * K[m];
+                for (int jj = 0; jj < NJ; ++jj) y[jj] += w[jj] * K[m];
             }
         } else {
             const T *zin = wk + ((k - 1) & 1) * W;
             const T *At = sw + lay.At + (k - 2) * W * W + j0;
-#pragma unroll 4
-            for (int i = 0; i < W; ++i) {
-                const T zi = zin[i];
+#pragma unroll 2
+            for (int i = 0; i < W; i += V) {
+                T zv[V];
+                ldv<V>(zin + i, zv);
 #pragma unroll
-                for (int jj = 0; jj < NJ; ++jj) y[jj] += At[i * W + jj] * zi;
+                for (int u = 0; u < V; ++u) {
+                    T w[NJ];
+                    ldv<NJ>(At + (i + u) * W, w);
+#pragma unroll
+                    for (int jj = 0; jj < NJ; ++jj) y[jj] += w[jj] * zv[u];
+                }
             }
             const T *Bt = sw + lay.Bt + (k - 2) * D * W + j0;
 #pragma unroll
-            for (int m = 0; m < D; ++m)
+            for (int m = 0; m < D; ++m) {
+                T w[NJ];
+                ldv<NJ>(Bt + m * W, w);
 #pragma unroll
-                for (int jj = 0; jj < NJ; ++jj) y[jj] += Bt[m * W + jj] * K[m];
+                for (int jj = 0; jj < NJ; ++jj) y[jj] += w[jj] * K[m];
+            }
         }
-        T *sk = sd + (k - 1) * W + j0;
-        T *tk = sd + (L + k - 1) * W + j0;
-        T *zout = wk + (k & 1) * W + j0;
+        T sv[NJ], tv[NJ], zv[NJ];
 #pragma unroll
-        for (int jj = 0; jj < NJ; ++jj) {
-            T z, s, t;
-            act(y[jj], z, s, t);
-            sk[jj] = s;
-            tk[jj] = t;
-            if (k < L)
-                zout[jj] = z;
-            else
-                npart += sw[lay.a + j0 + jj] * z;
+        for (int jj = 0; jj < NJ; ++jj) act(y[jj], zv[jj], sv[jj], tv[jj]);
+        stv<NJ>(sd + (k - 1) * W + j0, sv);
+        stv<NJ>(sd + (L + k - 1) * W + j0, tv);
+        if (k < L) {
+            stv<NJ>(wk + (k & 1) * W + j0, zv);
+        } else {
+            T av[NJ];
+            ldv<NJ>(sw + lay.a + j0, av);
+#pragma unroll
+            for (int jj = 0; jj < NJ; ++jj) npart += av[jj] * zv[jj];
         }
         __syncwarp();
     }
@@ -142,15 +187,23 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
     T *yb = wk;
     {
         const T *Bt = (L == 1) ? (sw + lay.W1t + j0) : (sw + lay.Bt + (L - 2) * D * W + j0);
+        T av[NJ], sv[NJ], tv[NJ], ybar[NJ];
+        ldv<NJ>(sw + lay.a + j0, av);
+        ldv<NJ>(sd + (L - 1) * W + j0, sv);
+        ldv<NJ>(sd + (2 * L - 1) * W + j0, tv);
 #pragma unroll
         for (int jj = 0; jj < NJ; ++jj) {
-            const int j = j0 + jj;
-            const T aj = sw[lay.a + j];
-            const T ybar = sd[(L - 1) * W + j] * aj;
-            sd[(2 * L - 1) * W + j] *= aj;
-            yb[j] = ybar;
+            ybar[jj] = sv[jj] * av[jj];
+            tv[jj] *= av[jj];
+        }
+        stv<NJ>(sd + (2 * L - 1) * W + j0, tv);
+        stv<NJ>(yb + j0, ybar);
 #pragma unroll
-            for (int m = 0; m < D; ++m) dN[m] += Bt[m * W + jj] * ybar;
+        for (int m = 0; m < D; ++m) {
+            T w[NJ];
+            ldv<NJ>(Bt + m * W, w);
+#pragma unroll
+            for (int jj = 0; jj < NJ; ++jj) dN[m] += w[jj] * ybar[jj];
         }
         __syncwarp();
     }
@@ -159,22 +212,36 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
 #pragma unroll
         for (int ii = 0; ii < NJ; ++ii) zb[ii] = T(0);
         const T *Ar = sw + lay.Ar + (k - 2) * W * W + j0;
-#pragma unroll 4
-        for (int j = 0; j < W; ++j) {
-            const T ybj = yb[j];
+#pragma unroll 2
+        for (int j = 0; j < W; j += V) {
+            T yv[V];
+            ldv<V>(yb + j, yv);
 #pragma unroll
-            for (int ii = 0; ii < NJ; ++ii) zb[ii] += Ar[j * W + ii] * ybj;
+            for (int u = 0; u < V; ++u) {
+                T w[NJ];
+                ldv<NJ>(Ar + (j + u) * W, w);
+#pragma unroll
+                for (int ii = 0; ii < NJ; ++ii) zb[ii] += w[ii] * yv[u];
+            }
         }
         __syncwarp();
         const T *Bt = (k - 1 == 1) ? (sw + lay.W1t + j0) : (sw + lay.Bt + (k - 3) * D * W + j0);
+        T sv[NJ], tv[NJ], ybar[NJ];
+        ldv<NJ>(sd + (k - 2) * W + j0, sv);
+        ldv<NJ>(sd + (L + k - 2) * W + j0, tv);
 #pragma unroll
         for (int ii = 0; ii < NJ; ++ii) {
-            const int i = j0 + ii;
-            const T ybar = sd[(k - 2) * W + i] * zb[ii];
-            sd[(L + k - 2) * W + i] *= zb[ii];
-            yb[i] = ybar;
+            ybar[ii] = sv[ii] * zb[ii];
+            tv[ii] *= zb[ii];
+        }
+        stv<NJ>(sd + (L + k - 2) * W + j0, tv);
+        stv<NJ>(yb + j0, ybar);
 #pragma unroll
-            for (int m = 0; m < D; ++m) dN[m] += Bt[m * W + ii] * ybar;
+        for (int m = 0; m < D; ++m) {
+            T w[NJ];
+            ldv<NJ>(Bt + m * W, w);
+#pragma unroll
+            for (int ii = 0; ii < NJ; ++ii) dN[m] += w[ii] * ybar[ii];
         }
         __syncwarp();
     }
@@ -185,81 +252,88 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
 #pragma unroll
     for (int h = 0; h < NH; ++h) Hs[h] = T(0);
     if (want_A) {
+        {
+            T Dv[NJ];
+            ldv<NJ>(sd + L * W + j0, Dv);
 #pragma unroll
-    for (int jj = 0; jj < NJ; ++jj) {
-        const int j = j0 + jj;
-        const T *w1 = sw + lay.W1r + j * DP;
-        const T Dj = sd[L * W + j];
-#pragma unroll
-        for (int m = 0; m < D; ++m) {
-            const T dm = Dj * w1[m];
-#pragma unroll
-            for (int n = 0; n <= m; ++n) Hs[m * (m + 1) / 2 + n] += dm * w1[n];
-        }
-    }
-    for (int k = 2; k <= L; ++k) {
-        const T *At = sw + lay.At + (k - 2) * W * W + j0;
-        const T *Bt = sw + lay.Bt + (k - 2) * D * W + j0;
-        const T *sin = wk + ((k - 1) & 1) * W * DP;
-        T *sout = wk + (k & 1) * W * DP;
-#pragma unroll 1
-        for (int c0 = 0; c0 < NJ; c0 += NC) {
-            T acc[NC][D];
-#pragma unroll
-            for (int cc = 0; cc < NC; ++cc)
-#pragma unroll
-                for (int m = 0; m < D; ++m) acc[cc][m] = Bt[m * W + c0 + cc];
-            if (k == 2) {
-#pragma unroll 2
-                for (int i = 0; i < W; ++i) {
-                    const T si = sd[i];
-                    const T *w1 = sw + lay.W1r + i * DP;
-                    T sv[D];
-#pragma unroll
-                    for (int m = 0; m < D; ++m) sv[m] = si * w1[m];
-#pragma unroll
-                    for (int cc = 0; cc < NC; ++cc) {
-                        const T wv = At[i * W + c0 + cc];
-#pragma unroll
-                        for (int m = 0; m < D; ++m) acc[cc][m] += wv * sv[m];
-                    }
-                }
-            } else {
-#pragma unroll 2
-                for (int i = 0; i < W; ++i) {
-                    const T *p = sin + i * DP;
-                    T sv[D];
-#pragma unroll
-                    for (int m = 0; m < D; ++m) sv[m] = p[m];
-#pragma unroll
-                    for (int cc = 0; cc < NC; ++cc) {
-                        const T wv = At[i * W + c0 + cc];
-#pragma unroll
-                        for (int m = 0; m < D; ++m) acc[cc][m] += wv * sv[m];
-                    }
-                }
-            }
-#pragma unroll
-            for (int cc = 0; cc < NC; ++cc) {
-                const int j = j0 + c0 + cc;
-                const T Dj = sd[(L + k - 1) * W + j];
+            for (int jj = 0; jj < NJ; ++jj) {
+                T w1[DP];
+                ldv<DP>(sw + lay.W1r + (j0 + jj) * DP, w1);
 #pragma unroll
                 for (int m = 0; m < D; ++m) {
-                    const T dm = Dj * acc[cc][m];
+                    const T dm = Dv[jj] * w1[m];
 #pragma unroll
-                    for (int n = 0; n <= m; ++n) Hs[m * (m + 1) / 2 + n] += dm * acc[cc][n];
-                }
-                if (k < L) {
-                    const T sj = sd[(k - 1) * W + j];
-                    T *o = sout + j * DP;
-#pragma unroll
-                    for (int m = 0; m < D; ++m) o[m] = sj * acc[cc][m];
+                    for (int n = 0; n <= m; ++n) Hs[m * (m + 1) / 2 + n] += dm * w1[n];
                 }
             }
         }
-        __syncwarp();
-    }
-
+        for (int k = 2; k <= L; ++k) {
+            const T *At = sw + lay.At + (k - 2) * W * W + j0;
+            const T *Bt = sw + lay.Bt + (k - 2) * D * W + j0;
+            const T *sin = wk + ((k - 1) & 1) * W * DP;
+            T *sout = wk + (k & 1) * W * DP;
+#pragma unroll 1
+            for (int c0 = 0; c0 < NJ; c0 += NC) {
+                T acc[NC][D];
+#pragma unroll
+                for (int m = 0; m < D; ++m) {
+                    T w[NC];
+                    ldv<NC>(Bt + m * W + c0, w);
+#pragma unroll
+                    for (int cc = 0; cc < NC; ++cc) acc[cc][m] = w[cc];
+                }
+                if (k == 2) {
+#pragma unroll 1
+                    for (int i = 0; i < W; i += V) {
+                        T s1[V];
+                        ldv<V>(sd + i, s1);
+#pragma unroll
+                        for (int u = 0; u < V; ++u) {
+                            T w1[DP], w[NC];
+                            ldv<DP>(sw + lay.W1r + (i + u) * DP, w1);
+                            ldv<NC>(At + (i + u) * W + c0, w);
+                            T sv[D];
+#pragma unroll
+                            for (int m = 0; m < D; ++m) sv[m] = s1[u] * w1[m];
+#pragma unroll
+                            for (int cc = 0; cc < NC; ++cc)
+#pragma unroll
+                                for (int m = 0; m < D; ++m) acc[cc][m] += w[cc] * sv[m];
+                        }
+                    }
+                } else {
+#pragma unroll 2
+                    for (int i = 0; i < W; ++i) {
+                        T sv[DP], w[NC];
+                        ldv<DP>(sin + i * DP, sv);
+                        ldv<NC>(At + i * W + c0, w);
+#pragma unroll
+                        for (int cc = 0; cc < NC; ++cc)
+#pragma unroll
+                            for (int m = 0; m < D; ++m) acc[cc][m] += w[cc] * sv[m];
+                    }
+                }
+                T Dv[NC], sjv[NC];
+                ldv<NC>(sd + (L + k - 1) * W + j0 + c0, Dv);
+                ldv<NC>(sd + (k - 1) * W + j0 + c0, sjv);
+#pragma unroll
+                for (int cc = 0; cc < NC; ++cc) {
+#pragma unroll
+                    for (int m = 0; m < D; ++m) {
+                        const T dm = Dv[cc] * acc[cc][m];
+#pragma unroll
+                        for (int n = 0; n <= m; ++n) Hs[m * (m + 1) / 2 + n] += dm * acc[cc][n];
+                    }
+                    if (k < L) {
+                        T o[DP];
+#pragma unroll
+                        for (int m = 0; m < DP; ++m) o[m] = (m < D) ? sjv[cc] * acc[cc][m] : T(0);
+                        stv<DP>(sout + (j0 + c0 + cc) * DP, o);
+                    }
+                }
+            }
+            __syncwarp();
+        }
     }  // want_A
 
     // ---- reduce the group's partial sums
