@@ -170,6 +170,25 @@ class ClockSampler:
         return out
 
 
+# ------------------------------------------------------------ multi-rank timing
+
+def max_over_ranks(ms: float, dist=None, device=None) -> float:
+    """The largest of the ranks' times (the job ends with its slowest rank); identity
+    without a process group. ``device`` is where the reduction tensor lives (a CUDA device
+    for NCCL, the CPU for gloo)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_rate(units_per_rank: int, world: int, steps: int, max_ms: float) -> float:
+    """Whole-job throughput: every rank processes its own batch of units each step."""
+    return world * units_per_rank * steps / (max_ms * 1e-3)
+
+
 # ----------------------------------------------------------------- workloads
 
 def make_workload(name: str, n: int | None = None):
@@ -408,12 +427,10 @@ def run_ours(args, rank, world, local_rank):
     phase_ms = [float(np.mean([e[p].elapsed_time(e[p + 1]) for e in ev])) for p in range(nph)]
     clocks = clk.summary()
     if dist:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, tdist, dev)
     ms_per_step = total_ms / n_steps
-    qps = world * run.n_qp * n_steps / (total_ms * 1e-3)
-    eps = world * run.n_el * n_steps / (total_ms * 1e-3) if run.n_el else None
+    qps = weak_scaling_rate(run.n_qp, world, n_steps, total_ms)
+    eps = weak_scaling_rate(run.n_el, world, n_steps, total_ms) if run.n_el else None
 
     # ---- end to end through the public API with pinned host buffers
     e2e = None
@@ -444,10 +461,8 @@ def run_ours(args, rank, world, local_rank):
         barrier()
         e_ms = t0.elapsed_time(t1)
         if dist:
-            t = torch.tensor([e_ms], device=dev, dtype=torch.float64)
-            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": world * run.n_qp * n_e2e / (e_ms * 1e-3), "unit": "qp/s",
+            e_ms = max_over_ranks(e_ms, tdist, dev)
+        e2e = {"value": weak_scaling_rate(run.n_qp, world, n_e2e, e_ms), "unit": "qp/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": n_e2e,
                "ms_per_step": e_ms / n_e2e}
 

@@ -7,6 +7,7 @@
 #include <new>
 #include <vector>
 
+#include "device_math.cuh"
 #include "internal.h"
 
 using namespace commet;
@@ -21,7 +22,7 @@ int round4(int x) { return (x + 3) / 4 * 4; }
 
 // Build the packed-weight layout (offsets in elements, each block starting on a
 // multiple of 4 elements so that it is 16-byte aligned for float and double).
-NetLayout make_layout(int d, int W, int L) {
+NetLayout make_layout(int d, int W, int L, bool with_tab) {
     NetLayout l{};
     l.d = d;
     l.W = W;
@@ -38,6 +39,11 @@ NetLayout make_layout(int d, int W, int L) {
     l.b = o; o = round4(o + d);
     l.n0 = o; o = round4(o + d);
     l.K0 = o; o = round4(o + d);
+    l.tab = 0;
+    if (with_tab) {
+        l.tab = o;
+        o = round4(o + kActTab);
+    }
     l.total = o;
     return l;
 }
@@ -100,7 +106,7 @@ int commet_model_create(const commet_model_desc *desc, int32_t precision, commet
         for (int c = 0; c < 3; ++c) m->kp.fib[f][c] = desc->fibres[3 * f + c];
     m->kp.kappa = desc->kappa;
     m->kp.stress_free = desc->stress_free ? 1 : 0;
-    m->lay = make_layout(d, W, L);
+    m->lay = make_layout(d, W, L, precision == COMMET_F64);
     m->n_params = (int64_t)W * d + W + (int64_t)(L - 1) * ((int64_t)W * W + (int64_t)W * d + W) + W + d;
     cudaGetDevice(&m->device);
 
@@ -127,6 +133,24 @@ int commet_model_create(const commet_model_desc *desc, int32_t precision, commet
         for (int j = 0; j < W; ++j) h[l.c + k * W + j] = desc->c ? desc->c[k * W + j] : 0.0;
     for (int j = 0; j < W; ++j) h[l.a + j] = desc->a_out[j];
     for (int mm = 0; mm < d; ++mm) h[l.b + mm] = desc->b_out[mm];
+    if (l.tab > 0) {
+        // tables of the FP64 activation (device_math.cuh act_tab): 2^(j/64) and
+        // log(1 + k/128) as double-double pairs, 1/(1 + k/128), from extended precision
+        for (int j = 0; j < 64; ++j) {
+            const long double v = exp2l((long double)j / 64.0L);
+            const double hi = (double)v;
+            h[l.tab + 2 * j] = hi;
+            h[l.tab + 2 * j + 1] = (double)(v - (long double)hi);
+        }
+        for (int k = 0; k <= 128; ++k) {
+            const long double F = 1.0L + (long double)k / 128.0L;
+            const long double v = logl(F);
+            const double hi = (double)v;
+            h[l.tab + 128 + 3 * k] = hi;
+            h[l.tab + 128 + 3 * k + 1] = (double)(v - (long double)hi);
+            h[l.tab + 128 + 3 * k + 2] = (double)(1.0L / F);
+        }
+    }
 
     int rc;
     if (precision == COMMET_F64)

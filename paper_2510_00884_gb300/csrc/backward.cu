@@ -286,7 +286,10 @@ __global__ void __launch_bounds__(BwConf<T>::warps * 32)
             for (int jj = 0; jj < NJ; ++jj) {
                 const int j = j0 + jj;
                 T z, s, t;
-                act(y[jj], z, s, t);
+                if constexpr (sizeof(T) == 8)
+                    act_tab(y[jj], z, s, t, sw + lay.tab);
+                else
+                    act(y[jj], z, s, t);
                 qs[sl.s + (k - 1) * W + j] = s;
                 qs[sl.t + (k - 1) * W + j] = t;
                 qs[sl.yd + (k - 1) * W + j] = yd[jj];

@@ -62,6 +62,68 @@ __device__ __forceinline__ void act_value_slope(float y, float &z, float &s) {
     s = (y >= 0.0f) ? r : e * r;
 }
 
+// FP64 softplus triple from tables in shared memory, after the table-driven methods
+// of P. T. P. Tang (exp: ACM TOMS 15(2) 1989; log: ACM TOMS 16(4) 1990). GB300 runs
+// FP64 at 1/64 of FP32 and charges every warp-level FP64 instruction in full, so the
+// libm exp/log1p/division sequence (about 68 FP64 slots per neuron) dominated the
+// FP64 update; this form needs about 38.
+//  e = exp(-|y|):  -|y| = (64 m + j) ln2/64 + r, |r| <= ln2/128,
+//                  e = 2^m (T_j + T_j p(r)), p(r) = expm1(r) to degree 6, T_j = 2^(j/64)
+//  u = 1 + e rounded, c = e - (u - 1) its exact error (u in [1, 2])
+//  log1p(e) = log F_k + log1p(rr) + c / u,  F_k = 1 + k/128 nearest u, rr = (u - F_k)/F_k,
+//             |rr| <= 1/256, log1p(rr) to degree 6
+//  1/(1+e)  = (1/F_k) (1 - rr + rr^2 - ... + rr^6) (1 - c/u)
+// Table layout (doubles): [0, 128) = (T_hi, T_lo) for j = 0..63;
+// [128, 128 + 3*129) = (logF_hi, logF_lo, 1/F) for k = 0..128.
+constexpr int kActTab = 128 + 3 * 129;
+
+__device__ __forceinline__ void act_tab(double y, double &z, double &s, double &t, const double *tab) {
+    const double x = fmax(-fabs(y), -700.0);
+    const double SH = 6755399441055744.0;  // 1.5 * 2^52: rounds to an integer in the low bits
+    const double tt = fma(x, 92.33248261689366, SH);  // x * 64 / ln2
+    const double kd = tt - SH;
+    const int k = __double2loint(tt);
+    const int j = k & 63, m = k >> 6;
+    double r = fma(-kd, 0.010830424696249145, x);
+    r = fma(-kd, 3.623510646634843e-19, r);
+    double q = fma(r, 1.0 / 720.0, 1.0 / 120.0);
+    q = fma(r, q, 1.0 / 24.0);
+    q = fma(r, q, 1.0 / 6.0);
+    q = fma(r, q, 0.5);
+    const double p = fma(r * r, q, r);
+    const double Thi = tab[2 * j], Tlo = tab[2 * j + 1];
+    double e = fma(Thi, p, Tlo) + Thi;
+    e = __hiloint2double(__double2hiint(e) + (m << 20), __double2loint(e));
+    // log1p(e) and 1/(1+e)
+    const double u = 1.0 + e;
+    const double c = e - (u - 1.0);
+    const int hw = __double2hiint(u);
+    const int kk = (hw >= 0x40000000) ? 128 : (((hw & 0xFFFFF) + (1 << 12)) >> 13);
+    const double *lt = tab + 128 + 3 * kk;
+    const double F = 1.0 + kk * 0.0078125;
+    const double invF = lt[2];
+    const double rr = (u - F) * invF;
+    double g = fma(rr, -1.0 / 6.0, 0.2);
+    g = fma(rr, g, -0.25);
+    g = fma(rr, g, 1.0 / 3.0);
+    g = fma(rr, g, -0.5);
+    g = fma(rr, g, 1.0);
+    const double lrr = rr * g;                       // log1p(rr)
+    const double cu = c * invF;                      // c / u to first order
+    const double lg = lt[0] + (lt[1] + (lrr + cu));  // log1p(e)
+    double h = fma(rr, 1.0, -1.0);                   // series 1 - rr + rr^2 - ... + rr^6
+    h = fma(rr, h, 1.0);
+    h = fma(rr, h, -1.0);
+    h = fma(rr, h, 1.0);
+    h = fma(rr, h, -1.0);
+    h = fma(rr, h, 1.0);
+    const double inv_u = invF * h;
+    const double rinv = fma(-cu, inv_u, inv_u);      // 1/(u + c)
+    z = fmax(y, 0.0) + lg;
+    s = (y >= 0.0) ? rinv : e * rinv;
+    t = e * rinv * rinv;
+}
+
 __device__ __forceinline__ double dev_rcbrt(double x) { return rcbrt(x); }
 __device__ __forceinline__ float dev_rcbrt(float x) { return rcbrtf(x); }
 __device__ __forceinline__ bool dev_finite(double x) { return isfinite(x); }
@@ -345,6 +407,46 @@ __device__ __forceinline__ void assemble_row(int a, const T *st, const T *Hs, co
             if (J_ == L) s += st[S::Y + 3 * i + k];
             Arow[b] = s;
         }
+}
+
+
+// Entry (a, b) of A: the rank-one network part from the row vectors
+// u_a = sum_m g_m[a] d2N/dK_m dK (staged at ust[a * DP ...]) plus the structured part.
+template <typename T, int NF, int DP>
+__device__ __forceinline__ T assemble_entry(int a, int b, const T *st, const T *ust) {
+    constexpr int D = 3 + 2 * NF;
+    using S = Stage<D, NF>;
+    const int i = a / 3, J_ = a - 3 * i, k = b / 3, L = b - 3 * k;
+    T s = T(0);
+#pragma unroll
+    for (int n = 0; n < D; ++n) s += ust[a * DP + n] * st[S::g + 9 * n + b];
+    const T Ha = st[S::H + a], Hb = st[S::H + b], Fa = st[S::F + a], Fb = st[S::F + b];
+    const T beta = st[S::sc + 0], gamma = st[S::sc + 1], eta = st[S::sc + 2], zeta = st[S::sc + 3];
+    s += st[S::U + a] * Hb + Ha * st[S::U + b] + beta * Ha * Hb + gamma * Fa * Fb;
+    const T FiL = st[S::F + 3 * i + L], FkJ = st[S::F + 3 * k + J_];
+    s += -eta * st[S::H + 3 * i + L] * st[S::H + 3 * k + J_] + zeta * FiL * FkJ;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const T c5x2 = st[S::sc + 4 + f];
+        s += c5x2 * (FiL * st[S::aA + 9 * f + 3 * k + J_] + st[S::aA + 9 * f + 3 * i + L] * FkJ +
+                     st[S::Bm + 3 * i + k] * st[S::AA + 9 * f + 3 * J_ + L]);
+    }
+    s += (i == k) ? st[S::X + 3 * J_ + L] : T(0);
+    s += (J_ == L) ? st[S::Y + 3 * i + k] : T(0);
+    return s;
+}
+
+// The e-th (0 <= e < 45) entry of the upper triangle of a symmetric 9 x 9 matrix, row by row.
+__device__ __forceinline__ void upper_index(int e, int &a, int &b) {
+    int r = 0;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const bool step = e >= 9 - r;
+        e -= step ? 9 - r : 0;
+        r += step ? 1 : 0;
+    }
+    a = r;
+    b = r + e;
 }
 
 }  // namespace commet

@@ -28,6 +28,7 @@ struct NetLayout {
     int b;    // [d]
     int n0;   // [d] stress-free shift (zeros when off)
     int K0;   // [d] K at F = I
+    int tab;  // FP64 models: activation tables (kActTab doubles); 0 otherwise
     int total;
 };
 

@@ -47,7 +47,8 @@ __host__ __device__ inline int qp_slab_elems(int D, int W, int L, int NF) {
     int work = 2 * W;
     if (nbuf * W * DP > work) work = nbuf * W * DP;
     int raw = 2 * L * W + work;
-    const int stage = 9 * D + 54 + 18 * NF + 5 + NF;
+    // staged kinematics, then u[9][DP] and d2N/dK2 [D][DP] (see qp_group_update)
+    const int stage = (9 * D + 54 + 18 * NF + 5 + NF + 3) / 4 * 4 + 9 * DP + D * DP;
     if (stage > raw) raw = stage;
     int words = raw * (int)sizeof(T) / 4;
     words = (words + 31) / 32 * 32 + 4;
@@ -162,7 +163,12 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
         }
         T sv[NJ], tv[NJ], zv[NJ];
 #pragma unroll
-        for (int jj = 0; jj < NJ; ++jj) act(y[jj], zv[jj], sv[jj], tv[jj]);
+        for (int jj = 0; jj < NJ; ++jj) {
+            if constexpr (sizeof(T) == 8)
+                act_tab(y[jj], zv[jj], sv[jj], tv[jj], sw + lay.tab);
+            else
+                act(y[jj], zv[jj], sv[jj], tv[jj]);
+        }
         stv<NJ>(sd + (k - 1) * W + j0, sv);
         stv<NJ>(sd + (L + k - 1) * W + j0, tv);
         if (k < L) {
@@ -358,34 +364,120 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
 #pragma unroll
     for (int m = 0; m < D; ++m) cvec[m] = dN[m] - sw[lay.n0 + m];
     stage_kinematics<T, NF>(F, kc, cvec, Jm1, jb, qs);
+    using S = Stage<D, NF>;
+    constexpr int UOFF = (S::size + 3) / 4 * 4;  // u_a = sum_m g_m[a] N_mn : [9][DP]
+    constexpr int HOFF = UOFF + 9 * DP;          // d2N/dK2, full: [D][DP]
+    constexpr int NPL = (D + kG - 1) / kG;       // u columns per lane
+    if (want_A && jb == 0) {
+#pragma unroll
+        for (int m = 0; m < D; ++m)
+#pragma unroll
+            for (int n = 0; n < D; ++n)
+                qs[HOFF + m * DP + n] = Hs[(m >= n) ? (m * (m + 1) / 2 + n) : (n * (n + 1) / 2 + m)];
+    }
     __syncwarp();
-    bool nonfinite = false;
-    for (int a = jb; a < 9; a += kG) {
-        T Pa, Arow[9];
-        if (want_A) {
-            assemble_row<T, NF>(a, qs, Hs, cvec, Pa, Arow);
-        } else {
-            Pa = assemble_P<T, NF>(a, qs, cvec);
+    bool group_nonfinite = false;
+    if constexpr (sizeof(T) != 8) {
+        // FP32: each lane forms whole rows a = jb, jb + 4, jb + 8 (fewer live registers)
+        bool nonfinite = false;
+        for (int a = jb; a < 9; a += kG) {
+            T Pa, Arow[9];
+            if (want_A) {
+                assemble_row<T, NF>(a, qs, Hs, cvec, Pa, Arow);
+            } else {
+                Pa = assemble_P<T, NF>(a, qs, cvec);
 #pragma unroll
-            for (int b = 0; b < 9; ++b) Arow[b] = T(0);
+                for (int b = 0; b < 9; ++b) Arow[b] = T(0);
+            }
+            bool fin = dev_finite(Pa);
+#pragma unroll
+            for (int b = 0; b < 9; ++b) fin = fin && dev_finite(Arow[b]);
+            nonfinite |= !fin;
+            const bool nan_out = bad || !fin;
+            if (valid) {
+                const T nanv = T(NAN);
+                Pq[a * pst] = nan_out ? nanv : Pa;
+                if (want_A) {
+#pragma unroll
+                    for (int b = 0; b < 9; ++b) Aq[(9 * a + b) * ast] = nan_out ? nanv : Arow[b];
+                }
+            }
         }
-        bool fin = dev_finite(Pa);
+        const unsigned m0 = __ballot_sync(0xffffffffu, nonfinite);
+        group_nonfinite = ((m0 >> (qi * 4)) & 0xFu) != 0u;
+    } else {
+        // FP64: the FP64 pipe is charged per warp instruction, so the work is spread evenly:
+        // P rows a = jb, jb + 4, jb + 8 and, with A, the 45 upper entries round-robin over the
+        // group's four lanes; every value is formed before any is stored so that a point with
+        // a non-finite entry is written as NaN throughout.
+        T Pv[3];
 #pragma unroll
-        for (int b = 0; b < 9; ++b) fin = fin && dev_finite(Arow[b]);
-        nonfinite |= !fin;
-        const bool nan_out = bad || !fin;
+        for (int t = 0; t < 3; ++t) {
+            const int a = jb + kG * t;
+            Pv[t] = (a < 9) ? assemble_P<T, NF>(a, qs, cvec) : T(0);
+        }
+        T Av[12];
+#pragma unroll
+        for (int t = 0; t < 12; ++t) Av[t] = T(0);
+        if (want_A) {
+#pragma unroll 1
+            for (int a = 0; a < 9; ++a) {
+#pragma unroll
+                for (int nn = 0; nn < NPL; ++nn) {
+                    const int n = jb * NPL + nn;
+                    const int nc = n < D ? n : D - 1;
+                    T acc = T(0);
+#pragma unroll
+                    for (int m = 0; m < D; ++m) acc += qs[S::g + 9 * m + a] * qs[HOFF + m * DP + nc];
+                    if (n < D) qs[UOFF + a * DP + n] = acc;
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int t = 0; t < 12; ++t) {
+                const int e = jb + kG * t;
+                if (e < 45) {
+                    int a, b;
+                    upper_index(e, a, b);
+                    Av[t] = assemble_entry<T, NF, DP>(a, b, qs, qs + UOFF);
+                }
+            }
+        }
+        bool nonfinite = false;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) nonfinite |= !dev_finite(Pv[t]);
+#pragma unroll
+        for (int t = 0; t < 12; ++t) nonfinite |= !dev_finite(Av[t]);
+        {
+            const unsigned m0 = __ballot_sync(0xffffffffu, nonfinite);
+            nonfinite = ((m0 >> (qi * 4)) & 0xFu) != 0u;
+            group_nonfinite = nonfinite;
+        }
         if (valid) {
+            const bool nan_out = bad || nonfinite;
             const T nanv = T(NAN);
-            Pq[a * pst] = nan_out ? nanv : Pa;
-            if (Aq != nullptr) {
 #pragma unroll
-                for (int b = 0; b < 9; ++b) Aq[(9 * a + b) * ast] = nan_out ? nanv : Arow[b];
+            for (int t = 0; t < 3; ++t) {
+                const int a = jb + kG * t;
+                if (a < 9) Pq[a * pst] = nan_out ? nanv : Pv[t];
+            }
+            if (want_A) {
+#pragma unroll
+                for (int t = 0; t < 12; ++t) {
+                    const int e = jb + kG * t;
+                    if (e < 45) {
+                        int a, b;
+                        upper_index(e, a, b);
+                        const T v = nan_out ? nanv : Av[t];
+                        Aq[(9 * a + b) * ast] = v;
+                        if (a != b) Aq[(9 * b + a) * ast] = v;
+                    }
+                }
             }
         }
     }
-    // a point is reported if J <= 0 / bad input, or any of its rows was not finite
-    const unsigned nf_mask = __ballot_sync(0xffffffffu, nonfinite);
-    const bool grp_nonfinite = ((nf_mask >> (qi * 4)) & 0xFu) != 0u;
+    // a point is reported if J <= 0 / bad input, or any of its values was not finite
+    const bool grp_nonfinite = group_nonfinite;
     {
         T Psi = npart + kc.kappa * Jm1 * Jm1;
 #pragma unroll

@@ -278,3 +278,15 @@ def test_stress_only_path(pkg, prec):
     assert torch.equal(psi1, psi2)
     _, P_r, _ = oracle.const_update(oracle.OracleModel(spec), cm_to_pm(Fd).astype(np.float64))
     assert_close(cm_to_pm(P2), P_r, TOL[prec], f"stress only {prec}")
+
+
+@pytest.mark.parametrize("bias_std", [0.0, 3.0, 40.0])
+def test_fp64_activation_range(pkg, bias_std):
+    """Pre-activations from about -120 to 120 (biases ~ N(0, bias_std)) exercise every
+    branch of the FP64 softplus evaluation; FP64 parity at 1e-12 against libm in the oracle."""
+    rng = np.random.Generator(np.random.PCG64(61 + int(bias_std)))
+    spec = wl.make_model(rng, wl.KIN_RAW, 2, W=32, L=3, kappa=1.0, bias_std=bias_std if bias_std else None)
+    if bias_std == 0.0:
+        spec.c[:] = 0.0
+        spec.W1[:] *= 1e-8  # pre-activations near 0: e = exp(-|y|) near 1
+    check_update(pkg, spec, wl.random_F(rng, 2000, 0.15), "f64", f"activation range {bias_std}")
