@@ -498,13 +498,23 @@ def run_ours(args, rank, world, local_rank):
         flops = 2 * ELEM_MACS * run.n_el
         units, src = run.n_el, ["elem.cu"]
     peak = alu_peak_tflops(alu, n_sm, mhz)
+    bound = "alu"
+    peak_source = (f"derived: {n_sm} SMs x {'2 DFMA' if alu == 'f64' else '128 FFMA'}/clk x 2 flop x "
+                   f"{mhz:.0f} MHz (max SM clock; {peak_src} peaks file)")
+    if prec == "bf16" and kname == "const_update_kernel":
+        # the hidden W x W products run on the tensor cores: values, adjoints and the d
+        # tangent channels of every hidden layer, 2 (L-1) W^2 (2 + d) flops per point
+        flops = 2 * (spec.L - 1) * spec.W * spec.W * (2 + spec.d) * run.n_qp
+        bound = "tensor"
+        peak = float(peaks.get("bf16_tflops", 1900.0))
+        peak_source = f"bf16 dense matmul burst ({peak_src} peaks file); mma.sync m16n8k16 bf16, fp32 accumulate"
+        src = ["bf16_update.cu", "device_math.cuh"]
     achieved = flops / (phase_ms[dom] * 1e-3) / 1e12
     src_hash = kernel_source_hash(src)
-    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+    roofline = {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "traffic": ncu_traffic(kname, net, prec, src_hash, units),
-                "peak_source": f"derived: {n_sm} SMs x {'2 DFMA' if alu == 'f64' else '128 FFMA'}/clk x 2 flop x "
-                               f"{mhz:.0f} MHz (max SM clock; {peak_src} peaks file)",
+                "peak_source": peak_source,
                 "algorithmic_flops_per_launch": flops, "kernel_ms": phase_ms[dom],
                 "frac_at_median_clock": (achieved / peak * mhz / clocks["sm_mhz"]) if clocks.get("sm_mhz") else None,
                 "src_hash": src_hash}

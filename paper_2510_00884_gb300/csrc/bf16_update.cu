@@ -11,6 +11,7 @@
 // weights (D_k) go to shared memory. Layer 1 (d inputs), the output layer, the
 // activations, the Hessian sums and the kinematics/P/A assembly are fp32.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -93,10 +94,11 @@ constexpr int kPW = 16;  // points per warp (the MMA's M)
 
 }  // namespace
 
-// Per-warp shared memory (floats): s_k and t_k/D_k for 16 points x W neurons x L layers,
-// point-major with a pad, reused at the end as the 16 points' staging areas.
+// Per-warp shared memory: s_k and t_k/D_k in fp16 for 16 points x W neurons x L layers,
+// point-major with a pad (pstride halves per point), reused at the end as the 16
+// points' fp32 staging areas. fp16 keeps 11 bits, finer than the bf16 MMA inputs.
 template <int NF, int W>
-__global__ void __launch_bounds__(192)
+__global__ void __launch_bounds__(256)
     bf16_update_kernel(const float *__restrict__ gw32, const __nv_bfloat16 *__restrict__ gw16, B16Layout lay,
                        KinConst<float> kc, int64_t n_qp, const float *__restrict__ Fg, float *__restrict__ psi,
                        float *__restrict__ P, float *__restrict__ A, int32_t *__restrict__ status, int pstride) {
@@ -120,7 +122,7 @@ __global__ void __launch_bounds__(192)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, t = lane & 3;
     const int L = lay.L;
-    float *ws = reinterpret_cast<float *>(smem_raw + f32_bytes + b16_bytes) + (size_t)warp * kPW * pstride;
+    __half *ws = reinterpret_cast<__half *>(smem_raw + f32_bytes + b16_bytes) + (size_t)warp * kPW * pstride;
     // s_k of point p, neuron j: ws[p * pstride + (k-1) * W + j]; t_k / D_k at (L + k - 1) * W
     const int64_t n_tiles = (n_qp + kPW - 1) / kPW;
     const int64_t n_gwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -143,7 +145,7 @@ __global__ void __launch_bounds__(192)
                 kin_scalars_f32<NF>(F[h], kc, K[h], Jm1[h]);
             }
         }
-        float* wrow[2] = {ws + g * pstride, ws + (g + 8) * pstride};
+        __half *wrow[2] = {ws + g * pstride, ws + (g + 8) * pstride};
 
         // ---- forward values
         float acc[NT][4];
@@ -191,8 +193,8 @@ __global__ void __launch_bounds__(192)
                     const int j = 8 * nt + 2 * t + (e & 1), h = e >> 1;
                     float z, s, tt;
                     act(acc[nt][e], z, s, tt);
-                    wrow[h][(k - 1) * W + j] = s;
-                    wrow[h][(L + k - 1) * W + j] = tt;
+                    wrow[h][(k - 1) * W + j] = __float2half_rn(s);
+                    wrow[h][(L + k - 1) * W + j] = __float2half_rn(tt);
                     if (k == L) npart[h] += s32[lay.a + j] * z;
                     acc[nt][e] = z;
                 }
@@ -231,8 +233,9 @@ __global__ void __launch_bounds__(192)
                 for (int e = 0; e < 4; ++e) {
                     const int j = 8 * nt + 2 * t + (e & 1), h = e >> 1;
                     const float zb = acc[nt][e];
-                    const float yb = wrow[h][(k - 1) * W + j] * zb;
-                    wrow[h][(L + k - 1) * W + j] *= zb;  // D_k = t_k zbar_k
+                    const float yb = __half2float(wrow[h][(k - 1) * W + j]) * zb;
+                    wrow[h][(L + k - 1) * W + j] =
+                        __float2half_rn(__half2float(wrow[h][(L + k - 1) * W + j]) * zb);  // D_k = t_k zbar_k
 #pragma unroll
                     for (int m = 0; m < D; ++m) dN[h][m] += Bm[j * lay.dp + m] * yb;
                     acc[nt][e] = yb;
@@ -275,7 +278,7 @@ __global__ void __launch_bounds__(192)
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int j = 8 * nt + 2 * t + (e & 1), h = e >> 1;
-                const float Dj = wrow[h][L * W + j];
+                const float Dj = __half2float(wrow[h][L * W + j]);
                 const float *w1 = s32 + lay.W1 + j * lay.dp;
 #pragma unroll
                 for (int m = 0; m < D; ++m) {
@@ -297,7 +300,7 @@ __global__ void __launch_bounds__(192)
                         // element e: nt = 2kt + (e >> 2), (e & 3) as in the C layout
                         const int nt = 2 * kt + (e >> 2), ee = e & 3;
                         const int j = 8 * nt + 2 * t + (ee & 1), h = ee >> 1;
-                        v[e] = wrow[h][j] * s32[lay.W1 + j * lay.dp + m];
+                        v[e] = __half2float(wrow[h][j]) * s32[lay.W1 + j * lay.dp + m];
                     }
                     tf[m][kt][0] = pack_bf16(v[0], v[1]);
                     tf[m][kt][1] = pack_bf16(v[2], v[3]);
@@ -329,7 +332,7 @@ __global__ void __launch_bounds__(192)
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const int j = 8 * nt + 2 * t + (e & 1), h = e >> 1;
-                        const float Dj = wrow[h][(L + k - 1) * W + j];
+                        const float Dj = __half2float(wrow[h][(L + k - 1) * W + j]);
 #pragma unroll
                         for (int m = 0; m < D; ++m) {
                             const float dm = Dj * jac[m][nt][e];
@@ -347,7 +350,7 @@ __global__ void __launch_bounds__(192)
                             for (int e = 0; e < 8; ++e) {
                                 const int nt = 2 * kt + (e >> 2), ee = e & 3;
                                 const int j = 8 * nt + 2 * t + (ee & 1), h = ee >> 1;
-                                v[e] = wrow[h][(k - 1) * W + j] * jac[m][nt][ee];
+                                v[e] = __half2float(wrow[h][(k - 1) * W + j]) * jac[m][nt][ee];
                             }
                             tf[m][kt][0] = pack_bf16(v[0], v[1]);
                             tf[m][kt][1] = pack_bf16(v[2], v[3]);
@@ -374,7 +377,7 @@ __global__ void __launch_bounds__(192)
         // ---- P, A, Psi: the 4 lanes (t) of row g act as the point's group, twice
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            float *st = ws + (g + 8 * h) * pstride;  // staging reuses this point's s/D area
+            float *st = reinterpret_cast<float *>(ws + (g + 8 * h) * pstride);  // reuses the s/D area
             float cvec[D];
 #pragma unroll
             for (int m = 0; m < D; ++m) cvec[m] = dN[h][m] - s32[lay.n0 + m];
@@ -508,14 +511,15 @@ static int bf16_typed(const commet_model *m, int64_t n_qp, const void *F, void *
     const size_t b16_bytes = ((size_t)bl.b16_total * 2 + 15) / 16 * 16;
     const int D = 3 + 2 * NF;
     const int stage = 9 * D + 54 + 18 * NF + 5 + NF;
-    int raw = std::max(2 * m->L * W, stage);
-    const int pstride = (raw + 31) / 32 * 32 + 4;  // floats per point
-    const size_t per_warp = (size_t)kPW * pstride * 4;
+    const int raw_halves = std::max(2 * m->L * W, 2 * stage);
+    const int words = ((raw_halves + 1) / 2 + 31) / 32 * 32 + 4;  // 4-byte words per point
+    const int pstride = 2 * words;                                // halves per point
+    const size_t per_warp = (size_t)kPW * pstride * 2;
     int dev = 0, smem_max = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if ((size_t)smem_max < f32_bytes + b16_bytes + per_warp) return COMMET_ERR_UNSUPPORTED;
-    const int warps = (int)std::min<size_t>(6, (smem_max - f32_bytes - b16_bytes) / per_warp);
+    const int warps = (int)std::min<size_t>(8, (smem_max - f32_bytes - b16_bytes) / per_warp);
     const size_t smem = f32_bytes + b16_bytes + warps * per_warp;
     auto kern = bf16_update_kernel<NF, W>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
