@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(BwConf<T>::warps * 32)
             T zero[D];
 #pragma unroll
             for (int m = 0; m < D; ++m) zero[m] = T(0);
-            stage_kinematics<T, NF>(F, kc, zero, Jm1, jb == 0 ? 1 : (jb == 1 ? 2 : 3), qs);
+            stage_kinematics<T, NF, true>(F, kc, zero, Jm1, jb, qs);
         }
         __syncwarp();
         T r[D];

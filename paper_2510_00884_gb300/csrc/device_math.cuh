@@ -239,18 +239,22 @@ struct Stage {
     static constexpr int size = sc + 5 + NF;
 };
 
-// Writes the quantities every row of A needs into the qp's staging area. The four
-// threads of a qp group split the work by `part` (0..3). c[] = dN/dK - n0;
-// Jm1 = J - 1 from det_minus_one.
-template <typename T, int NF>
-__device__ __forceinline__ void stage_kinematics(const T *F, const KinConst<T> &kc, const T *c, T Jm1, int part,
+// Writes the quantities every entry of P and A needs into the point's staging area.
+// The four lanes of a point's group call it together; lane `lane4` (0..3) writes the
+// components a = lane4, lane4 + 4, lane4 + 8 of every 9-component quantity, so that all
+// lanes run the same instructions (GB300 bills a divergent branch's FP64 instructions to
+// every lane of the warp). Scalars and the fibre vectors a = F A, v = C A, F v are formed
+// in every lane. c[] = dN/dK - n0; Jm1 = J - 1 from det_minus_one. With G_ONLY, only the
+// kinematic gradients g_m are staged.
+template <typename T, int NF, bool G_ONLY = false>
+__device__ __forceinline__ void stage_kinematics(const T *F, const KinConst<T> &kc, const T *c, T Jm1, int lane4,
                                                  T *st) {
     constexpr int D = 3 + 2 * NF;
     using S = Stage<D, NF>;
     T cof[9], Jc, C[9];
     cof_det(F, cof, Jc);
-    const T J = T(1) + Jm1;
     right_cg(F, C);
+    const T J = T(1) + Jm1;
     const T I1 = C[0] + C[4] + C[8];
     T trC2 = 0;
 #pragma unroll
@@ -259,94 +263,69 @@ __device__ __forceinline__ void stage_kinematics(const T *F, const KinConst<T> &
     const T r3 = dev_rcbrt(J);
     const T jm23 = r3 * r3, jm43 = jm23 * jm23;
     const T iJ = T(1) / J;
-    T H[9];
-#pragma unroll
-    for (int a = 0; a < 9; ++a) H[a] = cof[a] * iJ;
-    // raw dI2/dF = 2 (I1 F - F C)
-    T gI2[9];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int L = 0; L < 3; ++L)
-            gI2[3 * i + L] = T(2) * (I1 * F[3 * i + L] - (F[3 * i] * C[L] + F[3 * i + 1] * C[3 + L] + F[3 * i + 2] * C[6 + L]));
     const T p1 = T(-2) / T(3), p2 = T(-4) / T(3);
     const T c1 = c[0], c2 = c[1], c3 = c[2];
     const T k2 = T(2) * kc.kappa;
-    if (part == 0) {
-        T B[9];
-        left_cg(F, B);
+    T af[NF > 0 ? NF : 1][3], vf[NF > 0 ? NF : 1][3], Fvf[NF > 0 ? NF : 1][3];
 #pragma unroll
-        for (int a = 0; a < 9; ++a) {
-            st[S::F + a] = F[a];
-            st[S::H + a] = H[a];
-            st[S::U + a] = c1 * jm23 * p1 * T(2) * F[a] + c2 * jm43 * p2 * gI2[a];
-            st[S::Bm + a] = B[a];
-        }
-        const T x0 = T(2) * c1 * jm23 + T(2) * I1 * c2 * jm43;
-        T X[9], Y[9];
+    for (int f = 0; f < NF; ++f) {
+        const T *A0 = kc.fib[f];
 #pragma unroll
-        for (int a = 0; a < 9; ++a) {
-            X[a] = ((a % 4) == 0 ? x0 : T(0)) - T(2) * c2 * jm43 * C[a];
-            Y[a] = -T(2) * c2 * jm43 * B[a];
+        for (int i = 0; i < 3; ++i) {
+            af[f][i] = F[3 * i] * A0[0] + F[3 * i + 1] * A0[1] + F[3 * i + 2] * A0[2];
+            vf[f][i] = C[3 * i] * A0[0] + C[3 * i + 1] * A0[1] + C[3 * i + 2] * A0[2];
         }
 #pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            const T *A0 = kc.fib[f];
-            const T c4 = c[3 + f], c5 = c[3 + NF + f];
-            T a[3], v[3];
+        for (int i = 0; i < 3; ++i) Fvf[f][i] = F[3 * i] * vf[f][0] + F[3 * i + 1] * vf[f][1] + F[3 * i + 2] * vf[f][2];
+    }
+    const T x0 = T(2) * c1 * jm23 + T(2) * I1 * c2 * jm43;
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                a[i] = F[3 * i] * A0[0] + F[3 * i + 1] * A0[1] + F[3 * i + 2] * A0[2];
-                v[i] = C[3 * i] * A0[0] + C[3 * i + 1] * A0[1] + C[3 * i + 2] * A0[2];
+    for (int t = 0; t < 3; ++t) {
+        const int a = lane4 + 4 * t;
+        if (a < 9) {
+            const int p = a / 3, q = a - 3 * p;  // a = 3 p + q
+            const T Fa = F[a], Ha = cof[a] * iJ;
+            const T FC = F[3 * p] * C[q] + F[3 * p + 1] * C[3 + q] + F[3 * p + 2] * C[6 + q];
+            const T gI2 = T(2) * (I1 * Fa - FC);  // raw dI2/dF = 2 (I1 F - F C)
+            st[S::g + a] = jm23 * (T(2) * Fa + p1 * I1 * Ha);
+            st[S::g + 9 + a] = jm43 * (gI2 + p2 * I2 * Ha);
+            st[S::g + 18 + a] = cof[a];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const T *A0 = kc.fib[f];
+                st[S::g + 9 * (3 + f) + a] = T(2) * af[f][p] * A0[q];
+                st[S::g + 9 * (3 + NF + f) + a] = T(2) * (af[f][p] * vf[f][q] + Fvf[f][p] * A0[q]);
             }
+            if (!G_ONLY) {
+                const T Bpq = F[3 * p] * F[3 * q] + F[3 * p + 1] * F[3 * q + 1] + F[3 * p + 2] * F[3 * q + 2];
+                st[S::F + a] = Fa;
+                st[S::H + a] = Ha;
+                st[S::U + a] = c1 * jm23 * p1 * T(2) * Fa + c2 * jm43 * p2 * gI2;
+                st[S::Bm + a] = Bpq;
+                T X = (p == q ? x0 : T(0)) - T(2) * c2 * jm43 * C[a];
+                T Y = -T(2) * c2 * jm43 * Bpq;
 #pragma unroll
-            for (int J_ = 0; J_ < 3; ++J_)
-#pragma unroll
-                for (int L = 0; L < 3; ++L) {
-                    X[3 * J_ + L] += T(2) * c4 * A0[J_] * A0[L] + T(2) * c5 * (A0[J_] * v[L] + v[J_] * A0[L]);
-                    Y[3 * J_ + L] += T(2) * c5 * a[J_] * a[L];
+                for (int f = 0; f < NF; ++f) {
+                    const T *A0 = kc.fib[f];
+                    const T c4 = c[3 + f], c5 = c[3 + NF + f];
+                    X += T(2) * c4 * A0[p] * A0[q] + T(2) * c5 * (A0[p] * vf[f][q] + vf[f][p] * A0[q]);
+                    Y += T(2) * c5 * af[f][p] * af[f][q];
+                    st[S::aA + 9 * f + a] = af[f][p] * A0[q];
+                    st[S::AA + 9 * f + a] = A0[p] * A0[q];
                 }
-            st[S::sc + 4 + f] = T(2) * c5;
+                st[S::X + a] = X;
+                st[S::Y + a] = Y;
+            }
         }
-#pragma unroll
-        for (int a = 0; a < 9; ++a) {
-            st[S::X + a] = X[a];
-            st[S::Y + a] = Y[a];
-        }
+    }
+    if (!G_ONLY && lane4 == 0) {
         st[S::sc + 0] = c1 * jm23 * p1 * p1 * I1 + c2 * jm43 * p2 * p2 * I2 + c3 * J + k2 * J * J + k2 * Jm1 * J;
         st[S::sc + 1] = T(4) * c2 * jm43;
         st[S::sc + 2] = c1 * jm23 * p1 * I1 + c2 * jm43 * p2 * I2 + c3 * J + k2 * Jm1 * J;
         st[S::sc + 3] = -T(2) * c2 * jm43;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) st[S::sc + 4 + f] = T(2) * c[3 + NF + f];
         st[S::sc + 4 + NF] = k2 * Jm1 * J;
-    } else if (part == 1) {
-#pragma unroll
-        for (int a = 0; a < 9; ++a) {
-            st[S::g + a] = jm23 * (T(2) * F[a] + p1 * I1 * H[a]);
-            st[S::g + 9 + a] = jm43 * (gI2[a] + p2 * I2 * H[a]);
-            st[S::g + 18 + a] = cof[a];
-        }
-    } else if (part == 2) {
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            const T *A0 = kc.fib[f];
-            T a[3], v[3], Fv[3];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                a[i] = F[3 * i] * A0[0] + F[3 * i + 1] * A0[1] + F[3 * i + 2] * A0[2];
-                v[i] = C[3 * i] * A0[0] + C[3 * i + 1] * A0[1] + C[3 * i + 2] * A0[2];
-            }
-#pragma unroll
-            for (int i = 0; i < 3; ++i) Fv[i] = F[3 * i] * v[0] + F[3 * i + 1] * v[1] + F[3 * i + 2] * v[2];
-#pragma unroll
-            for (int k = 0; k < 3; ++k)
-#pragma unroll
-                for (int L = 0; L < 3; ++L) {
-                    st[S::g + 9 * (3 + f) + 3 * k + L] = T(2) * a[k] * A0[L];
-                    st[S::g + 9 * (3 + NF + f) + 3 * k + L] = T(2) * (a[k] * v[L] + Fv[k] * A0[L]);
-                    st[S::aA + 9 * f + 3 * k + L] = a[k] * A0[L];
-                    st[S::AA + 9 * f + 3 * k + L] = A0[k] * A0[L];
-                }
-        }
     }
 }
 

@@ -295,16 +295,16 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
                         ldv<V>(sd + i, s1);
 #pragma unroll
                         for (int u = 0; u < V; ++u) {
+                            // s_1 folded into the weight: NC multiplies instead of D
                             T w1[DP], w[NC];
                             ldv<DP>(sw + lay.W1r + (i + u) * DP, w1);
                             ldv<NC>(At + (i + u) * W + c0, w);
-                            T sv[D];
 #pragma unroll
-                            for (int m = 0; m < D; ++m) sv[m] = s1[u] * w1[m];
+                            for (int cc = 0; cc < NC; ++cc) {
+                                const T ws = w[cc] * s1[u];
 #pragma unroll
-                            for (int cc = 0; cc < NC; ++cc)
-#pragma unroll
-                                for (int m = 0; m < D; ++m) acc[cc][m] += w[cc] * sv[m];
+                                for (int m = 0; m < D; ++m) acc[cc][m] += ws * w1[m];
+                            }
                         }
                     }
                 } else {
