@@ -40,7 +40,7 @@
 
 /* ------------------------------------------------------------------ model */
 
-enum { OR_KIN_ISO_SHIFTED = 0, OR_KIN_RAW = 1 };
+enum { OR_KIN_ISO_SHIFTED = 0, OR_KIN_RAW = 1, OR_KIN_POLYCONVEX = 2 };
 enum { OR_INNER_MICNN = 0, OR_INNER_GENT_THOMAS = 1, OR_INNER_HGO = 2 };
 
 /*
@@ -48,6 +48,8 @@ enum { OR_INNER_MICNN = 0, OR_INNER_GENT_THOMAS = 1, OR_INNER_HGO = 2 };
  * Kinematic layer (kin):
  *   OR_KIN_ISO_SHIFTED: K = (Ibar1 - 3, Ibar2 - 3, J - 1),                  d = 3
  *   OR_KIN_RAW:         K = (Ibar1, Ibar2, J, I4_11..I4_nn, I5_11..I5_nn),   d = 3 + 2 n_fib
+ *   OR_KIN_POLYCONVEX:  K = (Ibar1 - 3, Ibar2^{3/2} - 3^{3/2}, (J - 1)^2),     d = 3
+ *                       (the kinematic layer of the paper's trained NCMs, App. C)
  * Inner function (inner):
  *   OR_INNER_MICNN: eq. icnn with n-1 = L hidden layers. Layer 1 carries one
  *     matrix W1 (A^(1) acting on z^(0) = K and B^(1) acting on K act on the
@@ -264,6 +266,22 @@ static int oracle_kinematics(const oracle_model *m, const double *F, double *K, 
         K[0] -= 3.0;
         K[1] -= 3.0;
         K[2] -= 1.0;
+        return 3;
+    }
+    if (m->kin == OR_KIN_POLYCONVEX) {
+        /* K_m = phi_m(I_m) of an invariant: dK = phi' dI, d2K = phi'' dI (x) dI + phi' d2I */
+        const double Ib2 = K[1], Jv = K[2];
+        const double d1[3] = {1.0, 1.5 * sqrt(Ib2), 2.0 * (Jv - 1.0)};
+        const double d2[3] = {0.0, 0.75 / sqrt(Ib2), 2.0};
+        for (int m2 = 0; m2 < 3; ++m2) {
+            for (int a = 0; a < 9; ++a)
+                for (int b = 0; b < 9; ++b)
+                    d2K[81 * m2 + a * 9 + b] = d2[m2] * dK[9 * m2 + a] * dK[9 * m2 + b] + d1[m2] * d2K[81 * m2 + a * 9 + b];
+            for (int a = 0; a < 9; ++a) dK[9 * m2 + a] *= d1[m2];
+        }
+        K[0] -= 3.0;
+        K[1] = Ib2 * sqrt(Ib2) - 3.0 * sqrt(3.0);
+        K[2] = (Jv - 1.0) * (Jv - 1.0);
         return 3;
     }
     int nf = m->n_fib;

@@ -124,6 +124,8 @@ def kinematic_scalars(F9, kin: int, fibres) -> list:
     Ib2 = I2 * I3 ** (-2.0 / 3.0)
     if kin == 0:
         return [Ib1 - 3.0, Ib2 - 3.0, J - 1.0], J
+    if kin == 2:
+        return [Ib1 - 3.0, Ib2 ** 1.5 - 3.0 ** 1.5, (J - 1.0) * (J - 1.0)], J
     K = [Ib1, Ib2, J]
     I4s, I5s = [], []
     for A0 in fibres:

@@ -559,3 +559,42 @@ def test_c0_workload_is_orientation_preserving():
     F = oracle.compute_F(w["mesh"], w["u"])
     assert F.shape == (4096, 9)
     assert np.linalg.det(F.reshape(-1, 3, 3)).min() > 0.5
+
+
+# ------------------------------------------- the paper's polyconvex kinematic layer
+
+@pytest.fixture(scope="module")
+def poly_spec():
+    rng = np.random.Generator(np.random.PCG64(16))
+    return wl.make_model(rng, wl.KIN_POLYCONVEX, 0, W=8, L=3, kappa=0.0, bias_std=0.1)
+
+
+def test_polyconvex_layer_exact_derivatives(poly_spec):
+    """K = (Ibar1 - 3, Ibar2^{3/2} - 3^{3/2}, (J - 1)^2) (App. C) against hyper-dual Psi(F)."""
+    m = oracle.OracleModel(poly_spec)
+    rng = np.random.Generator(np.random.PCG64(17))
+    F = rand_F(rng, 3, 0.25)
+    psi, P, A = oracle.const_update(m, F)
+    for q in range(F.shape[0]):
+        psi_h, P_h, A_h = hdm.exact_P_A(poly_spec, F[q])
+        assert abs(psi[q] - psi_h) < 1e-13 * max(1, abs(psi_h))
+        assert rel(P[q], P_h) < 1e-12
+        assert rel(A[q], A_h) < 1e-12
+
+
+def test_polyconvex_layer_is_stress_free_for_any_weights(poly_spec):
+    """Every input of this layer has zero F-gradient at F = I, so P(I) = 0 without any
+    shift (the reason the paper chose it), while A(I) is not zero."""
+    m = oracle.OracleModel(poly_spec)
+    _, P, A = oracle.const_update(m, np.eye(3).ravel()[None])
+    assert np.abs(P).max() < 1e-15
+    assert np.abs(A).max() > 1e-3
+
+
+def test_paper_ncm_has_675_parameters():
+    w = wl.workload_paper_ncm(n=1)
+    spec = w["model"]
+    assert (spec.d, spec.W, spec.L) == (3, 16, 3)
+    g = json.load(open(os.path.join(GOLD, "paper_sizes.json")))
+    assert wl.n_params(spec.d, spec.W, spec.L, bias=False) == g["micnn_params_d3_w16_l3"]["value"]
+    assert np.all(spec.c == 0)

@@ -25,6 +25,7 @@ import numpy as np
 # Kinematic layers (input menus) of the strain energy.
 KIN_ISO_SHIFTED = 0  # K = (Ibar1 - 3, Ibar2 - 3, J - 1)
 KIN_RAW = 1          # K = (Ibar1, Ibar2, J, I4_11..I4_nn, I5_11..I5_nn)
+KIN_POLYCONVEX = 2   # K = (Ibar1 - 3, Ibar2^{3/2} - 3^{3/2}, (J - 1)^2), the paper's NCM inputs (App. C)
 
 # Reference structural vectors at +-30 degrees from +x in the x-y plane.
 FIBRES_PM30 = np.array([[math.cos(math.pi / 6), math.sin(math.pi / 6), 0.0],
@@ -121,7 +122,7 @@ def micnn_weights(rng: np.random.Generator, d: int, W: int, L: int, std: float =
 
 def make_model(rng, kin: int, n_fib: int, W: int, L: int, kappa: float, std: float = 0.1,
                bias_std: float | None = None, stress_free: bool = False) -> ModelSpec:
-    d = 3 if kin == KIN_ISO_SHIFTED else 3 + 2 * n_fib
+    d = 3 + 2 * n_fib if kin == KIN_RAW else 3
     fib = FIBRES_PM30[:n_fib].copy() if n_fib else np.zeros((0, 3))
     w = micnn_weights(rng, d, W, L, std, bias_std)
     return ModelSpec(d=d, W=W, L=L, kin=kin, fibres=fib, kappa=kappa, stress_free=stress_free, **w)
@@ -266,6 +267,18 @@ def workload_c0():
     mesh = structured_mesh(8)
     u = nodal_noise(rng, mesh, scale=0.05 / 8)
     return dict(name="c0_cube8_iso_d3w16l2", model=model, mesh=mesh, u=u)
+
+
+def workload_paper_ncm(n: int = 64, seed: int = 5):
+    """The paper's NCM architecture (App. C, hyper-parameter table): MICNN with 3 hidden
+    layers of 16 neurons, no biases (675 parameters), on the polyconvex kinematic layer
+    K = (Ibar1 - 3, Ibar2^{3/2} - 3^{3/2}, (J - 1)^2); random non-negative weights (the
+    trained weights do not ship); F = I + 0.15 N(0,1) per point on an n^3 mesh."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    model = make_model(rng, KIN_POLYCONVEX, 0, W=16, L=3, kappa=0.0)
+    mesh = structured_mesh(n)
+    F = random_F(rng, 8 * mesh.n_el, 0.15)
+    return dict(name=f"ncm_polyconvex_{n}cube_d3w16l3", model=model, mesh=mesh, F=F)
 
 
 def workload_c1(n: int = 64, seed: int = 1):
