@@ -59,6 +59,8 @@ def _load():
         _lib.oracle_compute_F.argtypes = [i64, i32, d, d, d]
         _lib.oracle_elem_assemble.argtypes = [i64, i32, d, d, d, d, d]
         _lib.oracle_scatter_residual.argtypes = [i64, i32, d, i64, d]
+        _lib.oracle_push_forward.argtypes = [d, d, d, d, d]
+        _lib.oracle_elem_assemble_spatial.argtypes = [i64, i32, d, d, d, d, d, d]
         _lib.oracle_scatter_csr.argtypes = [i64, i32, d, i64, P(C.c_int64), i32, d]
         _lib.oracle_scatter_csr.restype = C.c_int64
         _lib.oracle_n_params.argtypes = [C.c_int, C.c_int, C.c_int]
@@ -180,6 +182,38 @@ def elem_assemble(mesh, P: np.ndarray, A: np.ndarray | None, want_K: bool = True
     f = np.empty((n, 24))
     K = np.empty((n, 24, 24)) if (want_K and A is not None) else None
     lib.oracle_elem_assemble(n, _ip(conn), _dp(X), _dp(P), _dp(A), _dp(f), _dp(K))
+    return f, K
+
+
+VOIGT = ((0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1))
+
+
+def push_forward(F: np.ndarray, P: np.ndarray, A: np.ndarray | None):
+    """Kirchhoff stress tau[n][6] (Voigt 11 22 33 23 13 12) and spatial stiffness c[n][21]
+    (upper triangle of the 6 x 6 Voigt matrix, row-major) per point (App. A.1)."""
+    lib = _load()
+    F, P = _c64(F).reshape(-1, 9), _c64(P).reshape(-1, 9)
+    n = F.shape[0]
+    A = _c64(A).reshape(n, 81) if A is not None else None
+    tau = np.empty((n, 6))
+    c = np.empty((n, 21)) if A is not None else None
+    for q in range(n):
+        lib.oracle_push_forward(_dp(F[q]), _dp(P[q]), _dp(A[q]) if A is not None else None, _dp(tau[q]),
+                                _dp(c[q]) if c is not None else None)
+    return tau, c
+
+
+def elem_assemble_spatial(mesh, F: np.ndarray, tau: np.ndarray, c: np.ndarray | None, el=None):
+    """f_e[n][24], K_e[n][24][24] from F, tau, c by the spatial eq. r-quad / k-quad."""
+    lib = _load()
+    conn = np.ascontiguousarray(mesh.conn if el is None else mesh.conn[el], dtype=np.int32)
+    X = _c64(mesh.X)
+    n = conn.shape[0]
+    F, tau = _c64(F), _c64(tau)
+    c = _c64(c) if c is not None else None
+    f = np.empty((n, 24))
+    K = np.empty((n, 24, 24)) if c is not None else None
+    lib.oracle_elem_assemble_spatial(n, _ip(conn), _dp(X), _dp(F), _dp(tau), _dp(c), _dp(f), _dp(K))
     return f, K
 
 

@@ -26,6 +26,8 @@
  *   P and A by the CGO chain rule .................... Eq. nncm-chain, App. A.1 (P, C^P)
  *   F at a qp ........................................ Algorithm 1 (trial F)
  *   f_int and K_e per element ........................ Eq. r-quad, k-quad (material form)
+ *   Kirchhoff stress, spatial stiffness (Voigt) ...... App. A.1 (push-forward of P, A)
+ *   f_int and K_e from tau, c ........................ Eq. r-quad, k-quad (spatial form)
  *   backward dL/dF, dL/dtheta ........................ chain rule on G : P(F; theta)
  *
  * Parity status: every function here is pinned by the CPU tests (closed forms,
@@ -588,6 +590,112 @@ void oracle_elem_assemble(int64_t n_el, const int32_t *conn, const double *X, co
                                 for (int J = 0; J < 3; ++J)
                                     for (int L = 0; L < 3; ++L)
                                         s += g[3 * I + J] * Aq[(3 * i + J) * 9 + 3 * k + L] * g[3 * K + L];
+                                K_e[576 * e + (3 * I + i) * 24 + 3 * K + k] += w[q] * s;
+                            }
+                }
+        }
+    }
+}
+
+/* ------------------------------------------------------------ spatial form */
+
+/* Voigt pairs in the order (11, 22, 33, 23, 13, 12). */
+static const int VOIGT_I[6] = {0, 1, 2, 1, 0, 0};
+static const int VOIGT_J[6] = {0, 1, 2, 2, 2, 1};
+
+/*
+ * Kirchhoff stress and spatial stiffness from P and A by the push-forward of App. A.1:
+ *   tau_ij    = P_iJ F_jJ
+ *   c_ijkl    = F_jJ A_iJkL F_lL - delta_ik tau_jl
+ * tau[6] in Voigt order; c[21] the upper triangle (row-major, I <= J) of the 6 x 6
+ * Voigt matrix C_IJ = c_{ij kl}, (i, j) the pair of I and (k, l) the pair of J.
+ * F, P, A are one point's; c may be NULL.
+ */
+void oracle_push_forward(const double *F, const double *P, const double *A, double *tau, double *c) {
+    double t[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int J = 0; J < 3; ++J) s += P[3 * i + J] * F[3 * j + J];
+            t[3 * i + j] = s;
+        }
+    for (int v = 0; v < 6; ++v) tau[v] = t[3 * VOIGT_I[v] + VOIGT_J[v]];
+    if (!c) return;
+    int e = 0;
+    for (int I = 0; I < 6; ++I)
+        for (int Jv = I; Jv < 6; ++Jv) {
+            const int i = VOIGT_I[I], j = VOIGT_J[I], k = VOIGT_I[Jv], l = VOIGT_J[Jv];
+            double s = 0.0;
+            for (int J = 0; J < 3; ++J)
+                for (int L = 0; L < 3; ++L) s += F[3 * j + J] * A[(3 * i + J) * 9 + 3 * k + L] * F[3 * l + L];
+            c[e++] = s - kd(i, k) * t[3 * j + l];
+        }
+}
+
+/* Voigt slot of the symmetric pair (i, j). */
+static int voigt_of(int i, int j) {
+    if (i == j) return i;
+    if (i > j) { int x = i; i = j; j = x; }
+    return (i == 1) ? 3 : (j == 2 ? 4 : 5);
+}
+
+/* c_{ijkl} from the 21 stored values. */
+static double voigt_c(const double *c, int i, int j, int k, int l) {
+    int I = voigt_of(i, j), J = voigt_of(k, l);
+    if (I > J) { int x = I; I = J; J = x; }
+    /* row I of the upper triangle starts at I*6 - I(I-1)/2 */
+    return c[I * 6 - I * (I - 1) / 2 + (J - I)];
+}
+
+/*
+ * Element residual and stiffness in the spatial form of eq. r-quad and k-quad:
+ *   f_e[3I+i]       = sum_q w_q tau_ij grad phi_I,j
+ *   K_e[3I+i][3K+k] = sum_q w_q grad phi_I,m (delta_ik tau_ml + c_imkl) grad phi_K,l
+ * with the spatial gradients grad phi_I,m = dphi_I/dX_M (F^{-1})_Mm and w_q the qp's
+ * reference volume. F[q][9], tau[q][6], c[q][21] (c may be NULL).
+ */
+void oracle_elem_assemble_spatial(int64_t n_el, const int32_t *conn, const double *X, const double *F,
+                                  const double *tau, const double *c, double *f_e, double *K_e) {
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < n_el; ++e) {
+        double Xe[24], dphi[192], w[8];
+        gather_X(X, conn, e, Xe);
+        oracle_hex8_gradients(Xe, dphi, w);
+        if (f_e)
+            for (int r = 0; r < 24; ++r) f_e[24 * e + r] = 0.0;
+        if (K_e)
+            for (int r = 0; r < 576; ++r) K_e[576 * e + r] = 0.0;
+        for (int q = 0; q < 8; ++q) {
+            const int64_t qq = 8 * e + q;
+            const double *Fq = &F[9 * qq], *tq = &tau[6 * qq];
+            const double *cq = c ? &c[21 * qq] : NULL;
+            double cof[9], det, Finv[9];
+            cofactor(Fq, cof, &det);
+            /* F^{-1}_Mm = cof(F)_mM / det F */
+            for (int M = 0; M < 3; ++M)
+                for (int m = 0; m < 3; ++m) Finv[3 * M + m] = cof[3 * m + M] / det;
+            double g[8][3];
+            for (int I = 0; I < 8; ++I)
+                for (int m = 0; m < 3; ++m) {
+                    double s = 0.0;
+                    for (int M = 0; M < 3; ++M) s += dphi[(q * 8 + I) * 3 + M] * Finv[3 * M + m];
+                    g[I][m] = s;
+                }
+            for (int I = 0; I < 8; ++I)
+                for (int i = 0; i < 3; ++i) {
+                    if (f_e) {
+                        double s = 0.0;
+                        for (int j = 0; j < 3; ++j) s += tq[voigt_of(i, j)] * g[I][j];
+                        f_e[24 * e + 3 * I + i] += w[q] * s;
+                    }
+                    if (K_e && cq)
+                        for (int K = 0; K < 8; ++K)
+                            for (int k = 0; k < 3; ++k) {
+                                double s = 0.0;
+                                for (int m = 0; m < 3; ++m)
+                                    for (int l = 0; l < 3; ++l)
+                                        s += g[I][m] * (kd(i, k) * tq[voigt_of(m, l)] + voigt_c(cq, i, m, k, l)) *
+                                             g[K][l];
                                 K_e[576 * e + (3 * I + i) * 24 + 3 * K + k] += w[q] * s;
                             }
                 }

@@ -598,3 +598,86 @@ def test_paper_ncm_has_675_parameters():
     g = json.load(open(os.path.join(GOLD, "paper_sizes.json")))
     assert wl.n_params(spec.d, spec.W, spec.L, bias=False) == g["micnn_params_d3_w16_l3"]["value"]
     assert np.all(spec.c == 0)
+
+
+# ------------------------------------------------- spatial (Voigt) outputs, App. A.1
+
+def _voigt_full(c21):
+    """Full c_ijkl from the 21 stored values (upper triangle of the 6 x 6 Voigt matrix)."""
+    V = np.zeros((6, 6))
+    V[np.triu_indices(6)] = c21
+    V = V + np.triu(V, 1).T
+    slot = np.zeros((3, 3), dtype=int)
+    for v, (i, j) in enumerate(oracle.VOIGT):
+        slot[i, j] = slot[j, i] = v
+    return V[slot[:, :, None, None], slot[None, None, :, :]]
+
+
+@pytest.mark.parametrize("which", ["iso", "aniso"])
+def test_spatial_voigt_outputs_against_the_paper_route(which, iso_spec, aniso_spec):
+    """tau[6], c[21] from the oracle's push-forward (App. A.1) against tau = 2 N_m G^m,
+    c = 4 N_mn G^m G^n + 4 N_m GG^m (App. A.2) with exact hyper-dual network derivatives;
+    the 21 values rebuild the whole c_ijkl, so c has both minor and the major symmetry."""
+    spec = iso_spec if which == "iso" else aniso_spec
+    m = oracle.OracleModel(spec)
+    rng = np.random.Generator(np.random.PCG64(21))
+    F = rand_F(rng, 4, 0.25)
+    _, P, A = oracle.const_update(m, F)
+    tau6, c21 = oracle.push_forward(F, P, A)
+    for q in range(F.shape[0]):
+        Fq = F[q].reshape(3, 3)
+        Gs, GGs = spatial_G(Fq, spec.kin, spec.fibres)
+        C = Fq.T @ Fq
+        J = np.linalg.det(Fq)
+        I1, I2 = np.trace(C), 0.5 * (np.trace(C) ** 2 - np.trace(C @ C))
+        K = [J ** (-2 / 3) * I1, J ** (-4 / 3) * I2, J]
+        if spec.kin == wl.KIN_ISO_SHIFTED:
+            K = [K[0] - 3, K[1] - 3, J - 1]
+        for A0 in spec.fibres:
+            K.append(A0 @ C @ A0)
+        for A0 in spec.fibres:
+            K.append(A0 @ C @ C @ A0)
+        _, dN, d2N = hdm.exact_inner(spec, np.array(K))
+        dN[2] += 2 * spec.kappa * (J - 1.0)
+        d2N[2, 2] += 2 * spec.kappa
+        n = len(Gs)
+        tau = 2 * sum(dN[i] * Gs[i] for i in range(n))
+        c = 4 * sum(d2N[i, j] * _otimes(Gs[i], Gs[j]) for i in range(n) for j in range(n))
+        c = c + 4 * sum(dN[i] * GGs[i] for i in range(n))
+        assert rel([tau[i, j] for i, j in oracle.VOIGT], tau6[q]) < 1e-12
+        assert rel(_voigt_full(c21[q]), c) < 1e-12
+        assert rel(tau, tau.T) < 1e-13
+
+
+def test_spatial_neo_hookean_closed_form():
+    """Neo-Hookean: tau = mu J^{-2/3} dev(B) + 2 kappa (J - 1) J I."""
+    mu, kappa = 1.3, 7.0
+    m = oracle.OracleModel(neo_hookean_spec(mu, kappa))
+    rng = np.random.Generator(np.random.PCG64(22))
+    F = rand_F(rng, 5)
+    _, P, A = oracle.const_update(m, F)
+    tau6, _ = oracle.push_forward(F, P, None)
+    for q in range(F.shape[0]):
+        Fq = F[q].reshape(3, 3)
+        J = np.linalg.det(Fq)
+        B = Fq @ Fq.T
+        tau = mu * J ** (-2 / 3) * (B - np.trace(B) / 3 * np.eye(3)) + 2 * kappa * (J - 1) * J * np.eye(3)
+        assert rel([tau[i, j] for i, j in oracle.VOIGT], tau6[q]) < 1e-13
+
+
+def test_spatial_assembly_equals_material_assembly(aniso_spec):
+    """eq. k-quad in spatial form with grad phi = Grad phi F^{-1} gives the material-form
+    K_e and f_e (App. A.1: grad phi_k c_ikjl grad phi_l + delta tau terms = Grad phi A Grad phi)
+    for any F, compatible with a displacement or not."""
+    mesh = distorted_mesh(2, 23)
+    m = oracle.OracleModel(aniso_spec)
+    rng = np.random.Generator(np.random.PCG64(24))
+    F = rand_F(rng, 8 * mesh.n_el, 0.2)
+    _, P, A = oracle.const_update(m, F)
+    tau6, c21 = oracle.push_forward(F, P, A)
+    f_m, K_m = oracle.elem_assemble(mesh, P, A)
+    f_s, K_s = oracle.elem_assemble_spatial(mesh, F, tau6, c21)
+    assert rel(f_s, f_m) < 1e-12
+    assert rel(K_s, K_m) < 1e-12
+    f_s2, K_s2 = oracle.elem_assemble_spatial(mesh, F, tau6, None)
+    assert K_s2 is None and rel(f_s2, f_m) < 1e-12
