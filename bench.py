@@ -10,6 +10,8 @@ integrals (P, A -> f_int, K_e for every element). Other workloads:
   c3  2^20 points of the c1 network: stress, loss gradient and the adjoint kernel
   c4  96^3 cantilever: fused Newton assembly u -> r, CSR K (FP32), with the unfused
       FP64 GPU path timed beside it
+  ncm the paper's NCM (App. C): MICNN d3 W16 L3 without biases (675 parameters) on the
+      polyconvex inputs (Ibar1 - 3, Ibar2^{3/2} - 3^{3/2}, (J - 1)^2), 64^3 mesh, c1's step
 
 Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle on the
 host cores instead (a bounded sample of the same workload per step).
@@ -195,7 +197,7 @@ def make_workload(name: str, n: int | None = None):
     import workload as wl
     kw = {} if n is None else ({"n_qp": n} if name == "c3" else {"n": n})
     return {"c0": wl.workload_c0, "c1": wl.workload_c1, "c2": wl.workload_c2, "c3": wl.workload_c3,
-            "c4": wl.workload_c4}[name](**kw)
+            "c4": wl.workload_c4, "ncm": wl.workload_paper_ncm}[name](**kw)
 
 
 def wl_sub(mesh, el):
@@ -245,7 +247,7 @@ class Run:
         self.model = pkg.Model(spec, prec)
         self.mesh = w.get("mesh")
         mp = "f64" if prec == "f64" else "f32"
-        if name in ("c1", "c2"):
+        if name in ("c1", "c2", "ncm"):
             F_host = np.ascontiguousarray(w["F"].T)
             self.inputs_host = {"F": F_host}
             n = F_host.shape[1]
@@ -257,7 +259,7 @@ class Run:
             self.outputs = [self.psi, self.P, self.A]
             self.phases = [("const_update_kernel",
                             lambda: self.model.const_update(self.F, out=(self.psi, self.P, self.A)))]
-            if name == "c1":
+            if name in ("c1", "ncm"):
                 self.gmesh = pkg.Mesh(self.mesh.X, self.mesh.conn)
                 self.f_e = torch.empty(24, self.n_el, dtype=dt, device=dev)
                 self.K_e = torch.empty(576, self.n_el, dtype=dt, device=dev)
@@ -337,6 +339,21 @@ class Run:
 
     def step_outputs(self):
         return [self.dF] if self.name == "c3" else self.outputs
+
+
+def time_steps(run, torch, warmup: int, steps: int) -> float:
+    """Mean ms per step of a Run on the current stream (CUDA events)."""
+    for _ in range(warmup):
+        run.step()
+    stream = torch.cuda.current_stream()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(steps):
+        run.step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1) / steps
 
 
 def fp64_unfused_baseline(run, pkg, torch, dev, reps=2):
@@ -467,6 +484,14 @@ def run_ours(args, rank, world, local_rank):
                "ms_per_step": e_ms / n_e2e}
 
     fp64_base = None
+    if name in ("c1", "c2", "c3", "ncm") and prec != "f64" and not args.no_baseline and rank == 0:
+        # the same step through the plain FP64 path of the same kernels
+        run64 = Run(name, w, "f64", dev, pkg, torch)
+        b_ms = time_steps(run64, torch, 2, 3)
+        fp64_base = {"what": "same step, FP64 path", "ms_per_step": b_ms, "qp_per_s": run.n_qp / (b_ms * 1e-3),
+                     "speedup_of_" + prec: b_ms / ms_per_step}
+        del run64
+        torch.cuda.empty_cache()
     if name == "c4" and not args.no_baseline and rank == 0:
         b_ms = fp64_unfused_baseline(run, pkg, torch, dev)
         fp64_base = {"what": "unfused FP64 GPU path (compute_F, const_update, elem_assemble + colour scatter)",
@@ -544,7 +569,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": e2e, "gpu_launches": n_steps * launches_per_step(run), "clocks": clocks,
     }
     if fp64_base is not None:
-        res["fp64_unfused_gpu"] = fp64_base
+        res["fp64_unfused_gpu" if name == "c4" else "fp64_gpu"] = fp64_base
     return res
 
 
@@ -605,13 +630,13 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["c0", "c1", "c2", "c3", "c4"], default="c1")
+    ap.add_argument("--workload", choices=["c0", "c1", "c2", "c3", "c4", "ncm"], default="c1")
     ap.add_argument("--n", type=int, default=None, help="mesh size per side (points for c3)")
     ap.add_argument("--precision", choices=["f64", "f32", "bf16"], default=None,
                     help="default: f64 (f32 for c4)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-baseline", action="store_true", help="c4: skip the unfused FP64 GPU timing")
+    ap.add_argument("--no-baseline", action="store_true", help="skip the FP64 GPU timing beside a reduced-precision step (c4: the unfused FP64 path)")
     ap.add_argument("--cpu-sample-el", type=int, default=65536)
     ap.add_argument("--ref-sample-el", type=int, default=4096)
     args = ap.parse_args()

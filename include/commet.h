@@ -53,6 +53,9 @@ extern "C" {
 /* ---- kinematic layers (Sec. 2.2 eq. comp-se; App. A.2) ---- */
 #define COMMET_KIN_ISO_SHIFTED 0 /* K = (Ibar1 - 3, Ibar2 - 3, J - 1), d = 3, no fibres */
 #define COMMET_KIN_RAW 1         /* K = (Ibar1, Ibar2, J, I4_11..I4_nn, I5_11..I5_nn), d = 3 + 2n */
+#define COMMET_KIN_POLYCONVEX 2  /* K = (Ibar1 - 3, Ibar2^{3/2} - 3^{3/2}, (J - 1)^2), d = 3, no fibres:
+                                    the polyconvex inputs of the paper's trained NCMs (App. C);
+                                    every input has zero F-gradient at F = I, so P(I) = 0 */
 
 #define COMMET_ACT_SOFTPLUS 0 /* F(y) = log(1 + exp(y)), the only activation built */
 

@@ -78,12 +78,13 @@ int commet_model_create(const commet_model_desc *desc, int32_t precision, commet
     if (desc == nullptr || out == nullptr) return COMMET_ERR_INVALID_ARG;
     if (precision != COMMET_F64 && precision != COMMET_F32 && precision != COMMET_BF16_MLP)
         return COMMET_ERR_INVALID_ARG;
-    if (desc->kinematics != COMMET_KIN_ISO_SHIFTED && desc->kinematics != COMMET_KIN_RAW)
+    if (desc->kinematics != COMMET_KIN_ISO_SHIFTED && desc->kinematics != COMMET_KIN_RAW &&
+        desc->kinematics != COMMET_KIN_POLYCONVEX)
         return COMMET_ERR_INVALID_ARG;
     if (desc->n_fibres < 0 || desc->L < 1 || desc->W < 1 || desc->d < 1) return COMMET_ERR_INVALID_ARG;
-    if (desc->kinematics == COMMET_KIN_ISO_SHIFTED && desc->n_fibres != 0) return COMMET_ERR_INVALID_ARG;
+    if (desc->kinematics != COMMET_KIN_RAW && desc->n_fibres != 0) return COMMET_ERR_INVALID_ARG;
     if (desc->n_fibres > kMaxFibres) return COMMET_ERR_UNSUPPORTED;
-    const int d_expect = desc->kinematics == COMMET_KIN_ISO_SHIFTED ? 3 : 3 + 2 * desc->n_fibres;
+    const int d_expect = desc->kinematics == COMMET_KIN_RAW ? 3 + 2 * desc->n_fibres : 3;
     if (desc->d != d_expect) return COMMET_ERR_INVALID_ARG;
     if (desc->activation != COMMET_ACT_SOFTPLUS) return COMMET_ERR_UNSUPPORTED;
     if (desc->W1 == nullptr || desc->a_out == nullptr || desc->b_out == nullptr) return COMMET_ERR_INVALID_ARG;

@@ -203,7 +203,8 @@ __global__ void __launch_bounds__(BwConf<T>::warps * 32)
             G[c] = valid ? Gg[c * n_qp + q] : T(0);
         }
         T K[D], Jm1;
-        bool bad = !kin_scalars<T, NF>(F, kc, K, Jm1);
+        PolyChain<T> ch;
+        bool bad = !kin_scalars<T, NF>(F, kc, K, Jm1, &ch);
 #pragma unroll
         for (int c = 0; c < 9; ++c) bad = bad || !dev_finite(G[c]);
         if (bad) {
@@ -212,8 +213,9 @@ __global__ void __launch_bounds__(BwConf<T>::warps * 32)
                 F[c] = (c % 4) == 0 ? T(1) : T(0);
                 G[c] = T(0);
             }
-            kin_scalars<T, NF>(F, kc, K, Jm1);
+            kin_scalars<T, NF>(F, kc, K, Jm1, &ch);
         }
+        const bool poly = NF == 0 && kc.kin == COMMET_KIN_POLYCONVEX;
         // r_m = G : g_m; the 4 lanes stage g (part 1, 2) and read it back
         {
             T zero[D];
@@ -232,6 +234,15 @@ __global__ void __launch_bounds__(BwConf<T>::warps * 32)
                 for (int a = 0; a < 9; ++a) s += G[a] * qs[S::g + 9 * m + a];
                 r[m] = s;
             }
+        }
+        // polyconvex layer: g_m above are invariant derivatives; the network sees
+        // r_K = phi' r_I, and r_I is kept for the chain rule's second-order term
+        T rI[D];
+#pragma unroll
+        for (int m = 0; m < D; ++m) rI[m] = r[m];
+        if (poly) {
+#pragma unroll
+            for (int m = 0; m < 3; ++m) r[m] *= ch.d1[m];
         }
         __syncwarp();
         if (jb == 0) {
@@ -377,6 +388,14 @@ __global__ void __launch_bounds__(BwConf<T>::warps * 32)
         T cvec[D];
 #pragma unroll
         for (int m = 0; m < D; ++m) cvec[m] = dN[m] - sw[lay.n0 + m];
+        if (poly) {
+            // (d2Psi/dI2) r_I = phi' (N r_K) + phi'' c r_I;  dPsi/dI = phi' c
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                Hr[m] = ch.d1[m] * Hr[m] + ch.d2[m] * cvec[m] * rI[m];
+                cvec[m] *= ch.d1[m];
+            }
+        }
         stage_kinematics<T, NF>(F, kc, cvec, Jm1, jb, qs);
         __syncwarp();
         if (dFg != nullptr) {

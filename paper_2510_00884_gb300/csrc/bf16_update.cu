@@ -57,7 +57,8 @@ __device__ __forceinline__ float det_minus_one_f32(const float *F) {
 }
 
 template <int NF>
-__device__ __forceinline__ bool kin_scalars_f32(const float *F, const KinConst<float> &kc, float *K, float &Jm1) {
+__device__ __forceinline__ bool kin_scalars_f32(const float *F, const KinConst<float> &kc, float *K, float &Jm1,
+                                                PolyChain<float> *ch) {
     Jm1 = det_minus_one_f32(F);
     const float J = 1.f + Jm1;
     float C[9];
@@ -77,6 +78,8 @@ __device__ __forceinline__ bool kin_scalars_f32(const float *F, const KinConst<f
         K[0] -= 3.f;
         K[1] -= 3.f;
         K[2] = Jm1;
+    } else if (NF == 0 && kc.kin == COMMET_KIN_POLYCONVEX) {
+        poly_inputs<float>(K, Jm1, ch);
     }
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
@@ -131,6 +134,7 @@ __global__ void __launch_bounds__(256)
         // ---- kinematics of the two points this lane holds (rows g and g + 8)
         float F[2][9], K[2][D], Jm1[2];
         bool bad[2], valid[2];
+        PolyChain<float> ch[2];
         int64_t q[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -138,11 +142,11 @@ __global__ void __launch_bounds__(256)
             valid[h] = q[h] < n_qp;
 #pragma unroll
             for (int c = 0; c < 9; ++c) F[h][c] = valid[h] ? Fg[c * n_qp + q[h]] : ((c % 4) == 0 ? 1.f : 0.f);
-            bad[h] = !kin_scalars_f32<NF>(F[h], kc, K[h], Jm1[h]);
+            bad[h] = !kin_scalars_f32<NF>(F[h], kc, K[h], Jm1[h], &ch[h]);
             if (bad[h]) {
 #pragma unroll
                 for (int c = 0; c < 9; ++c) F[h][c] = (c % 4) == 0 ? 1.f : 0.f;
-                kin_scalars_f32<NF>(F[h], kc, K[h], Jm1[h]);
+                kin_scalars_f32<NF>(F[h], kc, K[h], Jm1[h], &ch[h]);
             }
         }
         __half *wrow[2] = {ws + g * pstride, ws + (g + 8) * pstride};
@@ -381,6 +385,9 @@ __global__ void __launch_bounds__(256)
             float cvec[D];
 #pragma unroll
             for (int m = 0; m < D; ++m) cvec[m] = dN[h][m] - s32[lay.n0 + m];
+            if constexpr (NF == 0) {
+                if (kc.kin == COMMET_KIN_POLYCONVEX) poly_to_invariants<float>(ch[h], cvec, Hs[h]);
+            }
             __syncwarp();
             stage_kinematics<float, NF>(F[h], kc, cvec, Jm1[h], t, st);
             __syncwarp();

@@ -188,10 +188,52 @@ __device__ __forceinline__ float det_minus_one(const float *F) {
     return (float)(J - 1.0);
 }
 
+// Polyconvex kinematic layer (App. C): K_m = phi_m(I_m) of the invariants
+// I = (Ibar1, Ibar2, J), phi = (I - 3, I^{3/2} - 3^{3/2}, (I - 1)^2). The staged kinematic
+// derivatives are those of I_m, so the network's gradient c and Hessian N are carried over
+// to invariant space by the chain rule:
+//   dPsi/dI_m = phi'_m c_m,   d2Psi/dI_m dI_n = phi'_m phi'_n N_mn + delta_mn phi''_m c_m.
+template <typename T>
+struct PolyChain {
+    T d1[3], d2[3];  // phi'_m, phi''_m at the point
+};
+
+template <typename T>
+__device__ __forceinline__ void poly_inputs(T *K, T Jm1, PolyChain<T> *ch) {
+    const T Ib2 = K[1];
+    const T sq = sqrt(Ib2);  // Ibar2 >= 3 for every admissible F
+    K[0] -= T(3);
+    K[1] = Ib2 * sq - T(5.196152422706632);  // 3^{3/2}
+    K[2] = Jm1 * Jm1;
+    if (ch != nullptr) {
+        ch->d1[0] = T(1);
+        ch->d1[1] = T(1.5) * sq;
+        ch->d1[2] = T(2) * Jm1;
+        ch->d2[0] = T(0);
+        ch->d2[1] = T(0.75) / sq;
+        ch->d2[2] = T(2);
+    }
+}
+
+// c <- phi' c and the packed lower triangle Hs (Hs[m (m + 1) / 2 + n], n <= m) <- the
+// invariant-space Hessian, both in place (D = 3).
+template <typename T>
+__device__ __forceinline__ void poly_to_invariants(const PolyChain<T> &ch, T *c, T *Hs) {
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+#pragma unroll
+        for (int n = 0; n <= m; ++n) Hs[m * (m + 1) / 2 + n] *= ch.d1[m] * ch.d1[n];
+        Hs[m * (m + 1) / 2 + m] += ch.d2[m] * c[m];
+    }
+#pragma unroll
+    for (int m = 0; m < 3; ++m) c[m] *= ch.d1[m];
+}
+
 // Kinematic scalars K (D = 3 + 2 NF entries) and Jm1 = J - 1. Returns false if
-// J <= 0 or F is not finite.
+// J <= 0 or F is not finite. With the polyconvex layer, ch (if given) receives phi', phi''.
 template <typename T, int NF>
-__device__ __forceinline__ bool kin_scalars(const T *F, const KinConst<T> &kc, T *K, T &Jm1) {
+__device__ __forceinline__ bool kin_scalars(const T *F, const KinConst<T> &kc, T *K, T &Jm1,
+                                            PolyChain<T> *ch = nullptr) {
     Jm1 = det_minus_one(F);
     const T J = T(1) + Jm1;
     T C[9];
@@ -211,6 +253,8 @@ __device__ __forceinline__ bool kin_scalars(const T *F, const KinConst<T> &kc, T
         K[0] -= T(3);
         K[1] -= T(3);
         K[2] = Jm1;
+    } else if (NF == 0 && kc.kin == COMMET_KIN_POLYCONVEX) {
+        poly_inputs<T>(K, Jm1, ch);
     }
 #pragma unroll
     for (int f = 0; f < NF; ++f) {

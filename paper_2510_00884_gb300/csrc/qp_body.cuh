@@ -116,11 +116,12 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
     T *wk = qs + 2 * L * W;  // work area
     const int j0 = jb * NJ;
     T K[D], Jm1;
-    bool bad = !kin_scalars<T, NF>(F, kc, K, Jm1);
+    PolyChain<T> ch;
+    bool bad = !kin_scalars<T, NF>(F, kc, K, Jm1, &ch);
     if (bad) {
 #pragma unroll
         for (int cpt = 0; cpt < 9; ++cpt) F[cpt] = (cpt % 4) == 0 ? T(1) : T(0);
-        kin_scalars<T, NF>(F, kc, K, Jm1);
+        kin_scalars<T, NF>(F, kc, K, Jm1, &ch);
     }
 
     // ---- forward values
@@ -363,6 +364,9 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
     T cvec[D];
 #pragma unroll
     for (int m = 0; m < D; ++m) cvec[m] = dN[m] - sw[lay.n0 + m];
+    if constexpr (NF == 0) {
+        if (kc.kin == COMMET_KIN_POLYCONVEX) poly_to_invariants<T>(ch, cvec, Hs);
+    }
     stage_kinematics<T, NF>(F, kc, cvec, Jm1, jb, qs);
     using S = Stage<D, NF>;
     constexpr int UOFF = (S::size + 3) / 4 * 4;  // u_a = sum_m g_m[a] N_mn : [9][DP]

@@ -56,6 +56,10 @@ def test_host_side_argument_checks(lib):
     assert lib.commet_model_create(C.byref(desc), 0, C.byref(out)) == _lib.ERR_INVALID_ARG
     desc = _lib.ModelDesc(kinematics=0, d=3, W=16, L=2)
     assert lib.commet_model_create(C.byref(desc), 9, C.byref(out)) == _lib.ERR_INVALID_ARG
+    desc = _lib.ModelDesc(kinematics=2, n_fibres=1, d=5, W=16, L=2)  # polyconvex takes no fibres
+    assert lib.commet_model_create(C.byref(desc), 0, C.byref(out)) == _lib.ERR_INVALID_ARG
+    desc = _lib.ModelDesc(kinematics=2, d=5, W=16, L=2)                # and d = 3
+    assert lib.commet_model_create(C.byref(desc), 0, C.byref(out)) == _lib.ERR_INVALID_ARG
     assert lib.commet_const_update(None, 1, None, None, None, None, None, None) == _lib.ERR_INVALID_ARG
     assert lib.commet_mesh_create(-1, None, 0, None, 0, C.byref(out)) == _lib.ERR_INVALID_ARG
     X = (C.c_double * 24)(*([0.0] * 24))

@@ -24,6 +24,7 @@ CASES = [
     (wl.KIN_ISO_SHIFTED, 0, 32, 2, 10.0, 1003),
     (wl.KIN_RAW, 2, 32, 3, 0.0, 2011),
     (wl.KIN_ISO_SHIFTED, 0, 64, 4, 3.0, 33),
+    (wl.KIN_POLYCONVEX, 0, 32, 3, 0.0, 3001),
 ]
 
 

@@ -35,14 +35,16 @@ def distorted(nx, ny, nz, seed):
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-@pytest.mark.parametrize("net", ["aniso_w32", "iso_w16"])
+@pytest.mark.parametrize("net", ["aniso_w32", "iso_w16", "poly_w16"])
 def test_newton_small_mesh(pkg, prec, net):
     mesh = distorted(6, 5, 4, 3)
     rng = np.random.Generator(np.random.PCG64(41))
     if net == "aniso_w32":
         spec = wl.make_model(rng, wl.KIN_RAW, 2, W=32, L=3, kappa=1.0)
-    else:
+    elif net == "iso_w16":
         spec = wl.make_model(rng, wl.KIN_ISO_SHIFTED, 0, W=16, L=2, kappa=10.0)
+    else:
+        spec = wl.make_model(rng, wl.KIN_POLYCONVEX, 0, W=16, L=3, kappa=0.0)
     u_np = 0.02 * rng.normal(size=mesh.X.shape)
     gm = pkg.Mesh(mesh.X, mesh.conn, want_csr=True)
     m = pkg.Model(spec, prec)

@@ -89,6 +89,10 @@ CASES = [
     (wl.KIN_RAW, 2, 16, 4, 1.0, True, True, 1500),
     (wl.KIN_ISO_SHIFTED, 0, 32, 5, 3.0, True, True, 777),
     (wl.KIN_RAW, 1, 32, 2, 0.5, False, False, 7),
+    # the polyconvex layer of the paper's NCMs (App. C): the 3x16 network itself, and
+    # a biased, shifted variant with a volumetric penalty
+    (wl.KIN_POLYCONVEX, 0, 16, 3, 0.0, False, False, 3001),
+    (wl.KIN_POLYCONVEX, 0, 32, 2, 5.0, True, True, 1025),
 ]
 
 
@@ -290,3 +294,28 @@ def test_fp64_activation_range(pkg, bias_std):
         spec.c[:] = 0.0
         spec.W1[:] *= 1e-8  # pre-activations near 0: e = exp(-|y|) near 1
     check_update(pkg, spec, wl.random_F(rng, 2000, 0.15), "f64", f"activation range {bias_std}")
+
+
+# ---------------------------------------------------- the paper's polyconvex NCM
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_polyconvex_ncm(pkg, prec):
+    """MICNN 3x16 without biases on K = (Ibar1 - 3, Ibar2^{3/2} - 3^{3/2}, (J - 1)^2):
+    parity on a 16^3 mesh of random F, and P(I) = 0 with A(I) != 0 (App. C)."""
+    w = wl.workload_paper_ncm(n=16)
+    spec = w["model"]
+    check_update(pkg, spec, w["F"], prec, f"paper NCM {prec}")
+    _, P, A, st = run_update(pkg, spec, np.tile(np.eye(3).ravel(), (37, 1)), prec)
+    assert st[0] == 0
+    assert np.abs(P).max() < (1e-14 if prec == "f64" else 1e-6)
+    assert np.abs(A).max() > 1e-3
+
+
+def test_polyconvex_rejects_fibres(pkg):
+    from paper_2510_00884_gb300 import _lib
+    rng = np.random.Generator(np.random.PCG64(9))
+    spec = wl.make_model(rng, wl.KIN_RAW, 2, W=16, L=3, kappa=0.0)
+    spec.kin = wl.KIN_POLYCONVEX
+    with pytest.raises(_lib.CommetError) as ei:
+        pkg.Model(spec, "f64")
+    assert ei.value.code == _lib.ERR_INVALID_ARG
