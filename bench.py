@@ -69,6 +69,7 @@ def backward_flops_per_qp(d: int, W: int, L: int) -> int:
 
 
 ELEM_MACS = 8 * (3 * 27 * 3 + 3 * 8 * 3 * 3)  # per element: 8 qp x (T3 + row contractions)
+PUSH_FORWARD_MACS = 21 * 15 + 6 * 3  # per point: c = F A F - delta tau (21 entries), tau = P F^T (6)
 
 
 def load_peaks():
@@ -238,8 +239,9 @@ def cpu_sample_rate(w, n_el_sample: int):
 class Run:
     """Device buffers and the phases of one step for a workload."""
 
-    def __init__(self, name, w, prec, dev, pkg, torch):
+    def __init__(self, name, w, prec, dev, pkg, torch, spatial=False):
         self.name, self.w, self.prec, self.dev = name, w, prec, dev
+        self.spatial = spatial
         dt = torch.float64 if prec == "f64" else torch.float32
         self.dt = dt
         spec = w["model"]
@@ -254,18 +256,29 @@ class Run:
             self.n_qp, self.n_el = n, n // 8
             self.F = torch.from_numpy(F_host).to(device=dev, dtype=dt).contiguous()
             self.psi = torch.empty(n, dtype=dt, device=dev)
-            self.P = torch.empty(9, n, dtype=dt, device=dev)
-            self.A = torch.empty(81, n, dtype=dt, device=dev)
+            if spatial:
+                # Kirchhoff stress and spatial stiffness in Voigt form (6 + 21 values per point)
+                self.P = torch.empty(6, n, dtype=dt, device=dev)
+                self.A = torch.empty(21, n, dtype=dt, device=dev)
+                self.phases = [("const_update_kernel", lambda: self.model.const_update_spatial(
+                    self.F, out=(self.psi, self.P, self.A)))]
+            else:
+                self.P = torch.empty(9, n, dtype=dt, device=dev)
+                self.A = torch.empty(81, n, dtype=dt, device=dev)
+                self.phases = [("const_update_kernel",
+                                lambda: self.model.const_update(self.F, out=(self.psi, self.P, self.A)))]
             self.outputs = [self.psi, self.P, self.A]
-            self.phases = [("const_update_kernel",
-                            lambda: self.model.const_update(self.F, out=(self.psi, self.P, self.A)))]
             if name in ("c1", "ncm"):
                 self.gmesh = pkg.Mesh(self.mesh.X, self.mesh.conn)
                 self.f_e = torch.empty(24, self.n_el, dtype=dt, device=dev)
                 self.K_e = torch.empty(576, self.n_el, dtype=dt, device=dev)
                 self.outputs += [self.f_e, self.K_e]
-                self.phases.append(("elem_assemble_kernel", lambda: self.gmesh.elem_assemble(
-                    self.P, self.A, mp, out=(self.f_e, self.K_e, None, None))))
+                if spatial:
+                    self.phases.append(("elem_spatial_kernel", lambda: self.gmesh.elem_assemble_spatial(
+                        self.F, self.P, self.A, mp, out=(self.f_e, self.K_e, None, None))))
+                else:
+                    self.phases.append(("elem_assemble_kernel", lambda: self.gmesh.elem_assemble(
+                        self.P, self.A, mp, out=(self.f_e, self.K_e, None, None))))
             else:
                 self.n_el = 0
             self.input_dev = {"F": self.F}
@@ -410,7 +423,9 @@ def run_ours(args, rank, world, local_rank):
     name = args.workload
     prec = args.precision or ("f32" if name == "c4" else "f64")
     w = make_workload(name, args.n)
-    run = Run(name, w, prec, dev, pkg, torch)
+    if args.spatial and name not in ("c1", "c2", "ncm"):
+        raise SystemExit("--spatial applies to the c1, c2 and ncm workloads")
+    run = Run(name, w, prec, dev, pkg, torch, spatial=args.spatial)
     stream = torch.cuda.current_stream()
     dist = world > 1
     if dist:
@@ -486,7 +501,7 @@ def run_ours(args, rank, world, local_rank):
     fp64_base = None
     if name in ("c1", "c2", "c3", "ncm") and prec != "f64" and not args.no_baseline and rank == 0:
         # the same step through the plain FP64 path of the same kernels
-        run64 = Run(name, w, "f64", dev, pkg, torch)
+        run64 = Run(name, w, "f64", dev, pkg, torch, spatial=args.spatial)
         b_ms = time_steps(run64, torch, 2, 3)
         fp64_base = {"what": "same step, FP64 path", "ms_per_step": b_ms, "qp_per_s": run.n_qp / (b_ms * 1e-3),
                      "speedup_of_" + prec: b_ms / ms_per_step}
@@ -511,8 +526,11 @@ def run_ours(args, rank, world, local_rank):
     kname = run.phases[dom][0]
     alu = "f64" if prec == "f64" else "f32"
     if kname == "const_update_kernel":
-        flops = algorithmic_flops_per_qp(spec.d, spec.W, spec.L) * run.n_qp
-        units, src = run.n_qp, ["const_update.cu", "qp_body.cuh", "device_math.cuh"]
+        per_qp = algorithmic_flops_per_qp(spec.d, spec.W, spec.L) + (2 * PUSH_FORWARD_MACS if args.spatial else 0)
+        flops = per_qp * run.n_qp
+        units = run.n_qp
+        src = ["spatial.cu" if args.spatial else "const_update.cu", "update_kernel.cuh", "qp_body.cuh",
+               "device_math.cuh"]
     elif kname == "const_backward_kernel":
         flops = backward_flops_per_qp(spec.d, spec.W, spec.L) * run.n_qp
         units, src = run.n_qp, ["backward.cu", "device_math.cuh"]
@@ -521,7 +539,7 @@ def run_ours(args, rank, world, local_rank):
         units, src = run.n_el, ["newton.cu", "qp_body.cuh", "device_math.cuh"]
     else:
         flops = 2 * ELEM_MACS * run.n_el
-        units, src = run.n_el, ["elem.cu"]
+        units, src = run.n_el, ["spatial.cu" if kname == "elem_spatial_kernel" else "elem.cu", "hex8.cuh"]
     peak = alu_peak_tflops(alu, n_sm, mhz)
     bound = "alu"
     peak_source = (f"derived: {n_sm} SMs x {'2 DFMA' if alu == 'f64' else '128 FFMA'}/clk x 2 flop x "
@@ -544,11 +562,13 @@ def run_ours(args, rank, world, local_rank):
                 "frac_at_median_clock": (achieved / peak * mhz / clocks["sm_mhz"]) if clocks.get("sm_mhz") else None,
                 "src_hash": src_hash}
     phases = {n_: ms for (n_, _), ms in zip(run.phases, phase_ms)}
-    if "elem_assemble_kernel" in phases:
+    ek = "elem_spatial_kernel" if args.spatial else "elem_assemble_kernel"
+    if ek in phases:
         es = 8 if prec == "f64" else 4
-        el_ms = phases["elem_assemble_kernel"]
-        roofline["elem_kernel"] = {"ms": el_ms, "bytes_per_el": (8 * 90 + 600) * es,
-                                   "achieved_gbs": run.n_el * (8 * 90 + 600) * es / (el_ms * 1e-3) / 1e9,
+        el_ms = phases[ek]
+        per_qp = 36 if args.spatial else 90  # F, tau, c  or  P, A
+        roofline["elem_kernel"] = {"kernel": ek, "ms": el_ms, "bytes_per_el": (8 * per_qp + 600) * es,
+                                   "achieved_gbs": run.n_el * (8 * per_qp + 600) * es / (el_ms * 1e-3) / 1e9,
                                    "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)),
                                    "achieved_tflops": run.n_el * 2 * ELEM_MACS / (el_ms * 1e-3) / 1e12}
 
@@ -559,7 +579,7 @@ def run_ours(args, rank, world, local_rank):
                "sample": f"{what} of {w['name']}, {secs:.1f} s", "elements_per_s": eps_cpu}
 
     cfg = {"workload": w["name"], "n_qp": run.n_qp, "n_el": run.n_el, "network": f"d{spec.d} W{spec.W} L{spec.L}",
-           "precision": prec, "parallelism": f"replicas x{world} (independent meshes)",
+           "precision": prec, "outputs": "tau, c (Voigt, spatial)" if args.spatial else "P, A (material)", "parallelism": f"replicas x{world} (independent meshes)",
            "l2": "inputs/outputs larger than L2 (129 MB) every step"}
     res = {
         "metric": METRIC, "value": qps, "unit": "qp/s", "n_gpus": world, "steps": n_steps,
@@ -636,6 +656,8 @@ def main():
                     help="default: f64 (f32 for c4)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--spatial", action="store_true",
+                    help="c1/c2/ncm: spatial Voigt outputs tau, c and the spatial element kernel")
     ap.add_argument("--no-baseline", action="store_true", help="skip the FP64 GPU timing beside a reduced-precision step (c4: the unfused FP64 path)")
     ap.add_argument("--cpu-sample-el", type=int, default=65536)
     ap.add_argument("--ref-sample-el", type=int, default=4096)

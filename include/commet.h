@@ -115,6 +115,20 @@ int commet_const_update(const commet_model *m, int64_t n_qp, const void *F, void
                         int32_t *status, void *stream);
 
 /*
+ * Constitutive update in spatial form (App. A.1, the paper's own storage): for every qp
+ *   tau[:, q] = Kirchhoff stress tau_ij = P_iJ F_jJ in Voigt order (11, 22, 33, 23, 13, 12),
+ *   c[:, q]   = spatial stiffness c_ijkl = F_jJ A_iJkL F_lL - delta_ik tau_jl as the 21
+ *               entries C_IJ (I <= J, row-major upper triangle) of the 6 x 6 Voigt matrix,
+ *               C_IJ = c_{ij kl} with (i, j) the pair of slot I and (k, l) that of slot J,
+ * both symmetric, so 27 values per point leave the GPU instead of P and A's 90.
+ * F [9][n_qp] in; psi [n_qp] out or NULL; tau [6][n_qp] out (required); c [21][n_qp] out
+ * or NULL (stress only). Every precision of the model; status, alignment and errors as
+ * commet_const_update.
+ */
+int commet_const_update_spatial(const commet_model *m, int64_t n_qp, const void *F, void *psi, void *tau, void *c,
+                                int32_t *status, void *stream);
+
+/*
  * Mesh of hex8 elements (App. -: deal.II-style Q1 bricks). X (host, double [n_nodes][3])
  * and conn (host, int32 [n_el][8], lexicographic node order) are copied to the device.
  * want_csr = 1 also builds, on the host, the CSR pattern of the global stiffness
@@ -153,6 +167,19 @@ int commet_compute_F(const commet_mesh *mesh, int32_t precision, const void *u, 
  */
 int commet_elem_assemble(const commet_mesh *mesh, int32_t precision, const void *P, const void *A, void *f_e,
                          void *K_e, void *r, void *K_vals, void *stream);
+
+/*
+ * Element integrals in the spatial form of eq. r-quad and k-quad:
+ *   f_e[3I+i]       = sum_q w_q tau_ij grad phi_I,j
+ *   K_e[3I+i][3K+k] = sum_q w_q grad phi_I,m (delta_ik tau_ml + c_imkl) grad phi_K,l
+ * with grad phi_I,m = dphi_I/dX_M (F^{-1})_Mm (spatial gradients) and w_q = det Je; equal
+ * to the material form of commet_elem_assemble for the same point (App. A.1).
+ * F [9][8 n_el], tau [6][8 n_el], c [21][8 n_el] in (layouts of
+ * commet_const_update_spatial; c may be NULL only when K_e and K_vals are NULL);
+ * outputs, scatter and errors as commet_elem_assemble.
+ */
+int commet_elem_assemble_spatial(const commet_mesh *mesh, int32_t precision, const void *F, const void *tau,
+                                 const void *c, void *f_e, void *K_e, void *r, void *K_vals, void *stream);
 
 /*
  * Fused Newton-iteration assembly: u -> F -> (Psi, P, A) -> f_e, K_e -> r, K_vals for

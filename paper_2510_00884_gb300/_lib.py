@@ -18,6 +18,7 @@ ACT_SOFTPLUS = 0
 
 EXPORTED = [
     "commet_model_create", "commet_model_destroy", "commet_model_n_params", "commet_const_update",
+    "commet_const_update_spatial", "commet_elem_assemble_spatial",
     "commet_mesh_create", "commet_mesh_destroy", "commet_mesh_info", "commet_mesh_csr", "commet_compute_F",
     "commet_elem_assemble", "commet_newton_assemble", "commet_const_backward_workspace",
     "commet_const_backward", "commet_target_stress", "commet_status_string", "commet_const_backward_noalloc",
@@ -64,6 +65,8 @@ def load() -> C.CDLL:
         "commet_mesh_csr": ([vp, C.POINTER(i64), C.POINTER(i32)], C.c_int),
         "commet_compute_F": ([vp, i32, vp, vp, vp], C.c_int),
         "commet_elem_assemble": ([vp, i32, vp, vp, vp, vp, vp, vp, vp], C.c_int),
+        "commet_const_update_spatial": ([vp, i64, vp, vp, vp, vp, vp, vp], C.c_int),
+        "commet_elem_assemble_spatial": ([vp, i32, vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
         "commet_newton_assemble": ([vp, vp, vp, vp, vp, vp, vp], C.c_int),
         "commet_const_backward_workspace": ([vp, i64], C.c_size_t),
         "commet_const_backward": ([vp, i64, vp, vp, vp, vp, vp, C.c_size_t, vp], C.c_int),

@@ -91,6 +91,24 @@ class Model:
             self.handle, n, _ptr(F), _ptr(psi), _ptr(P), _ptr(A), _ptr(st), _stream()))
         return (psi, P, A, st) if status else (psi, P, A)
 
+    def const_update_spatial(self, F: torch.Tensor, want_c: bool = True, want_psi: bool = True,
+                             status: bool = False, out=None):
+        """psi[n], tau[6, n], c[21, n] (or None) for F[9, n]: Kirchhoff stress and spatial
+        stiffness in Voigt form (11, 22, 33, 23, 13, 12; c as the row-major upper triangle
+        of the 6 x 6 matrix)."""
+        _check_dev(F, self.dtype, name="F")
+        n = F.shape[1]
+        if out is None:
+            psi = torch.empty(n, dtype=self.dtype, device=F.device) if want_psi else None
+            tau = torch.empty(6, n, dtype=self.dtype, device=F.device)
+            c = torch.empty(21, n, dtype=self.dtype, device=F.device) if want_c else None
+        else:
+            psi, tau, c = out
+        st = torch.empty(2, dtype=torch.int32, device=F.device) if status else None
+        _lib.check("commet_const_update_spatial", _lib.load().commet_const_update_spatial(
+            self.handle, n, _ptr(F), _ptr(psi), _ptr(tau), _ptr(c), _ptr(st), _stream()))
+        return (psi, tau, c, st) if status else (psi, tau, c)
+
     def backward(self, F: torch.Tensor, G: torch.Tensor, want_dF: bool = True, workspace=None, out=None):
         """dL/dF[9, n] (or None) and dL/dtheta[n_params] for upstream G = dL/dP [9, n]."""
         _check_dev(F, self.dtype, name="F")
@@ -170,6 +188,31 @@ class Mesh:
             f_e, K_e, r, Kv = out
         _lib.check("commet_elem_assemble", _lib.load().commet_elem_assemble(
             self.handle, _PREC[precision], _ptr(P), _ptr(A), _ptr(f_e), _ptr(K_e), _ptr(r), _ptr(Kv), _stream()))
+        return f_e, K_e, r, Kv
+
+
+    def elem_assemble_spatial(self, F: torch.Tensor, tau: torch.Tensor, c: torch.Tensor | None,
+                              precision: str = "f64", want_f: bool = True, want_K: bool = True,
+                              want_r: bool = False, want_Kcsr: bool = False, out=None):
+        """Spatial-form element integrals from F[9, n_qp], tau[6, n_qp], c[21, n_qp]:
+        (f_e[24, n_el], K_e[576, n_el], r[3 n_nodes], K_vals[nnz]); entries not wanted are None."""
+        dt = _DTYPE[precision]
+        n_qp = 8 * self.n_el
+        _check_dev(F, dt, shape=(9, n_qp), name="F")
+        _check_dev(tau, dt, shape=(6, n_qp), name="tau")
+        if c is not None:
+            _check_dev(c, dt, shape=(21, n_qp), name="c")
+        dev = F.device
+        if out is None:
+            f_e = torch.empty(24, self.n_el, dtype=dt, device=dev) if want_f else None
+            K_e = torch.empty(576, self.n_el, dtype=dt, device=dev) if (want_K and c is not None) else None
+            r = torch.empty(3 * self.n_nodes, dtype=dt, device=dev) if want_r else None
+            Kv = torch.empty(self.nnz, dtype=dt, device=dev) if want_Kcsr else None
+        else:
+            f_e, K_e, r, Kv = out
+        _lib.check("commet_elem_assemble_spatial", _lib.load().commet_elem_assemble_spatial(
+            self.handle, _PREC[precision], _ptr(F), _ptr(tau), _ptr(c), _ptr(f_e), _ptr(K_e), _ptr(r), _ptr(Kv),
+            _stream()))
         return f_e, K_e, r, Kv
 
 

@@ -239,6 +239,16 @@ int commet_const_update(const commet_model *m, int64_t n_qp, const void *F, void
     return launch_const_update(m, n_qp, F, psi, P, A, status, s, nullptr);
 }
 
+int commet_const_update_spatial(const commet_model *m, int64_t n_qp, const void *F, void *psi, void *tau, void *c,
+                                int32_t *status, void *stream) {
+    if (m == nullptr || n_qp < 0) return COMMET_ERR_INVALID_ARG;
+    if (n_qp > 0 && (F == nullptr || tau == nullptr)) return COMMET_ERR_INVALID_ARG;
+    if (!aligned16(F) || !aligned16(tau) || !aligned16(c) || !aligned16(psi) ||
+        (reinterpret_cast<uintptr_t>(status) & 7u) != 0)
+        return COMMET_ERR_INVALID_ARG;
+    return launch_const_update_spatial(m, n_qp, F, psi, tau, c, status, reinterpret_cast<cudaStream_t>(stream));
+}
+
 int commet_target_stress(int32_t precision, int64_t n_qp, const void *F, int32_t n_fibres, const double *fibres,
                          double mu, double k1, double k2, double kappa, void *P, void *stream) {
     if (precision != COMMET_F64 && precision != COMMET_F32) return COMMET_ERR_INVALID_ARG;
@@ -339,6 +349,20 @@ int commet_elem_assemble(const commet_mesh *mesh, int32_t precision, const void 
         return COMMET_ERR_INVALID_ARG;
     return launch_elem_assemble(mesh, precision == COMMET_F64 ? COMMET_F64 : COMMET_F32, P, A, f_e, K_e, r, K_vals,
                                 reinterpret_cast<cudaStream_t>(stream));
+}
+
+int commet_elem_assemble_spatial(const commet_mesh *mesh, int32_t precision, const void *F, const void *tau,
+                                 const void *c, void *f_e, void *K_e, void *r, void *K_vals, void *stream) {
+    if (mesh == nullptr || (precision != COMMET_F64 && precision != COMMET_F32 && precision != COMMET_BF16_MLP))
+        return COMMET_ERR_INVALID_ARG;
+    if (mesh->n_el > 0 && (F == nullptr || tau == nullptr)) return COMMET_ERR_INVALID_ARG;
+    if (c == nullptr && (K_e != nullptr || K_vals != nullptr)) return COMMET_ERR_INVALID_ARG;
+    if ((r != nullptr || K_vals != nullptr) && mesh->h_rowptr == nullptr) return COMMET_ERR_NO_CSR;
+    if (!aligned16(F) || !aligned16(tau) || !aligned16(c) || !aligned16(f_e) || !aligned16(K_e) || !aligned16(r) ||
+        !aligned16(K_vals))
+        return COMMET_ERR_INVALID_ARG;
+    return launch_elem_assemble_spatial(mesh, precision == COMMET_F64 ? COMMET_F64 : COMMET_F32, F, tau, c, f_e, K_e,
+                                        r, K_vals, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int commet_newton_assemble(const commet_model *m, const commet_mesh *mesh, const void *u, void *r, void *K_vals,

@@ -100,7 +100,7 @@ constexpr int kPW = 16;  // points per warp (the MMA's M)
 // Per-warp shared memory: s_k and t_k/D_k in fp16 for 16 points x W neurons x L layers,
 // point-major with a pad (pstride halves per point), reused at the end as the 16
 // points' fp32 staging areas. fp16 keeps 11 bits, finer than the bf16 MMA inputs.
-template <int NF, int W>
+template <int NF, int W, bool SPATIAL>
 __global__ void __launch_bounds__(256)
     bf16_update_kernel(const float *__restrict__ gw32, const __nv_bfloat16 *__restrict__ gw16, B16Layout lay,
                        KinConst<float> kc, int64_t n_qp, const float *__restrict__ Fg, float *__restrict__ psi,
@@ -392,6 +392,10 @@ __global__ void __launch_bounds__(256)
             stage_kinematics<float, NF>(F[h], kc, cvec, Jm1[h], t, st);
             __syncwarp();
             bool nonfinite = false;
+            // spatial form: P and A go to the point's area after its staging, then are
+            // pushed forward to tau (written through P) and c (through A)
+            constexpr int kStageF = (9 * D + 54 + 18 * NF + 5 + NF + 3) / 4 * 4;
+            float *pa = st + kStageF;
             for (int a = t; a < 9; a += 4) {
                 float Pa, Arow[9];
                 if (want_A) {
@@ -406,13 +410,25 @@ __global__ void __launch_bounds__(256)
                 for (int b = 0; b < 9; ++b) fin = fin && isfinite(Arow[b]);
                 nonfinite |= !fin;
                 const bool nan_out = bad[h] || !fin;
-                if (valid[h]) {
+                if constexpr (SPATIAL) {
+                    pa[a] = nan_out ? NAN : Pa;
+                    if (A != nullptr) {
+#pragma unroll
+                        for (int b = 0; b < 9; ++b) pa[9 + 9 * a + b] = nan_out ? NAN : Arow[b];
+                    }
+                } else if (valid[h]) {
                     P[a * n_qp + q[h]] = nan_out ? NAN : Pa;
                     if (A != nullptr) {
 #pragma unroll
                         for (int b = 0; b < 9; ++b) A[(9 * a + b) * n_qp + q[h]] = nan_out ? NAN : Arow[b];
                     }
                 }
+            }
+            if constexpr (SPATIAL) {
+                __syncwarp();
+                const int64_t qo = valid[h] ? q[h] : 0;
+                push_forward_group<float>(st + Stage<D, NF>::F, pa, pa + 9, t, valid[h], P + qo,
+                                          A != nullptr ? A + qo : nullptr, n_qp);
             }
             const unsigned nf_mask = __ballot_sync(0xffffffffu, nonfinite);
             const bool grp_nonfinite = ((nf_mask >> (g * 4)) & 0xFu) != 0u;
@@ -504,7 +520,7 @@ int prepare_bf16_weights(commet_model *m) {
     return rc;
 }
 
-template <int NF, int W>
+template <int NF, int W, bool SPATIAL>
 static int bf16_typed(const commet_model *m, int64_t n_qp, const void *F, void *psi, void *P, void *A,
                       int32_t *status, cudaStream_t s) {
     KinConst<float> kc{};
@@ -517,7 +533,7 @@ static int bf16_typed(const commet_model *m, int64_t n_qp, const void *F, void *
     const size_t f32_bytes = ((size_t)bl.f32_total * 4 + 15) / 16 * 16;
     const size_t b16_bytes = ((size_t)bl.b16_total * 2 + 15) / 16 * 16;
     const int D = 3 + 2 * NF;
-    const int stage = 9 * D + 54 + 18 * NF + 5 + NF;
+    const int stage = (9 * D + 54 + 18 * NF + 5 + NF + 3) / 4 * 4 + (SPATIAL ? 90 : 0);
     const int raw_halves = std::max(2 * m->L * W, 2 * stage);
     const int words = ((raw_halves + 1) / 2 + 31) / 32 * 32 + 4;  // 4-byte words per point
     const int pstride = 2 * words;                                // halves per point
@@ -528,7 +544,7 @@ static int bf16_typed(const commet_model *m, int64_t n_qp, const void *F, void *
     if ((size_t)smem_max < f32_bytes + b16_bytes + per_warp) return COMMET_ERR_UNSUPPORTED;
     const int warps = (int)std::min<size_t>(8, (smem_max - f32_bytes - b16_bytes) / per_warp);
     const size_t smem = f32_bytes + b16_bytes + warps * per_warp;
-    auto kern = bf16_update_kernel<NF, W>;
+    auto kern = bf16_update_kernel<NF, W, SPATIAL>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return COMMET_ERR_CUDA;
     int per_sm = 0;
@@ -544,14 +560,21 @@ static int bf16_typed(const commet_model *m, int64_t n_qp, const void *F, void *
     return cudaGetLastError() == cudaSuccess ? COMMET_OK : COMMET_ERR_CUDA;
 }
 
-int launch_const_update_bf16(const commet_model *m, int64_t n_qp, const void *F, void *psi, void *P, void *A,
-                             int32_t *status, cudaStream_t s) {
-    if (m->d_bf16 == nullptr) return COMMET_ERR_UNSUPPORTED;
+template <bool SPATIAL>
+static int bf16_dispatch(const commet_model *m, int64_t n_qp, const void *F, void *psi, void *P, void *A,
+                         int32_t *status, cudaStream_t s) {
     const int nf = m->kp.nf, W = m->W;
-    if (nf == 0 && W == 64) return bf16_typed<0, 64>(m, n_qp, F, psi, P, A, status, s);
-    if (nf == 0 && W == 32) return bf16_typed<0, 32>(m, n_qp, F, psi, P, A, status, s);
-    if (nf == 2 && W == 32) return bf16_typed<2, 32>(m, n_qp, F, psi, P, A, status, s);
+    if (nf == 0 && W == 64) return bf16_typed<0, 64, SPATIAL>(m, n_qp, F, psi, P, A, status, s);
+    if (nf == 0 && W == 32) return bf16_typed<0, 32, SPATIAL>(m, n_qp, F, psi, P, A, status, s);
+    if (nf == 2 && W == 32) return bf16_typed<2, 32, SPATIAL>(m, n_qp, F, psi, P, A, status, s);
     return COMMET_ERR_UNSUPPORTED;
+}
+
+int launch_const_update_bf16(const commet_model *m, int64_t n_qp, const void *F, void *psi, void *P, void *A,
+                             int32_t *status, cudaStream_t s, bool spatial) {
+    if (m->d_bf16 == nullptr) return COMMET_ERR_UNSUPPORTED;
+    return spatial ? bf16_dispatch<true>(m, n_qp, F, psi, P, A, status, s)
+                   : bf16_dispatch<false>(m, n_qp, F, psi, P, A, status, s);
 }
 
 }  // namespace commet

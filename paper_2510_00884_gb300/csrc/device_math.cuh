@@ -373,6 +373,78 @@ __device__ __forceinline__ void stage_kinematics(const T *F, const KinConst<T> &
     }
 }
 
+// ------------------------------------------------------------ spatial form
+// Voigt pairs in the order (11, 22, 33, 23, 13, 12).
+__host__ __device__ constexpr int voigt_i(int v) { return v < 3 ? v : (v == 3 ? 1 : 0); }
+__host__ __device__ constexpr int voigt_j(int v) { return v < 3 ? v : (v == 5 ? 1 : 2); }
+// Voigt slot of the symmetric index pair (i, j).
+__host__ __device__ constexpr int voigt_of(int i, int j) {
+    return i == j ? i : ((i + j) == 3 ? 3 : ((i + j) == 2 ? 4 : 5));
+}
+// Position of the Voigt pair (I, J) in the row-major upper triangle of the 6 x 6 matrix.
+__host__ __device__ constexpr int voigt_upper_pos(int I, int J) {
+    return I <= J ? I * 6 - I * (I - 1) / 2 + (J - I) : J * 6 - J * (J - 1) / 2 + (I - J);
+}
+// Inverse of voigt_upper_pos for e in [0, 21).
+__device__ __forceinline__ void voigt_upper_pair(int e, int &I, int &J) {
+    I = 0;
+    int rem = e;
+#pragma unroll
+    for (int r = 0; r < 5; ++r)
+        if (rem >= 6 - I) {
+            rem -= 6 - I;
+            ++I;
+        }
+    J = I + rem;
+}
+
+// Push-forward of one point's P (9) and A (81) to the Kirchhoff stress and the spatial
+// stiffness in Voigt form (App. A.1):
+//   tau_ij = P_iJ F_jJ,   c_ijkl = F_jJ A_iJkL F_lL - delta_ik tau_jl,
+// tau[v] for the 6 Voigt pairs, c[e] for the 21 upper-triangle pairs (I, J) of the 6 x 6
+// Voigt matrix. Fs, Ps, As are in shared memory; the 4 lanes of the point's group share
+// the 27 outputs (lane4 takes o = lane4 + 4 t) and write them at tau[o * stride],
+// c[(o - 6) * stride] (c may be null: stress only).
+template <typename T>
+__device__ __forceinline__ void push_forward_group(const T *Fs, const T *Ps, const T *As, int lane4, bool valid,
+                                                   T *tau, T *c, int64_t stride) {
+#pragma unroll
+    for (int t = 0; t < 7; ++t) {
+        const int o = lane4 + 4 * t;
+        if (o >= 27 || (o >= 6 && c == nullptr)) continue;
+        int i, j, k = 0, l = 0;
+        if (o < 6) {
+            i = voigt_i(o);
+            j = voigt_j(o);
+        } else {
+            int I, J;
+            voigt_upper_pair(o - 6, I, J);
+            i = voigt_i(I);
+            j = voigt_j(I);
+            k = voigt_i(J);
+            l = voigt_j(J);
+        }
+        T v;
+        if (o < 6) {
+            v = Ps[3 * i] * Fs[3 * j] + Ps[3 * i + 1] * Fs[3 * j + 1] + Ps[3 * i + 2] * Fs[3 * j + 2];
+        } else {
+            v = T(0);
+#pragma unroll
+            for (int Jc = 0; Jc < 3; ++Jc) {
+                const T *Ar = As + (3 * i + Jc) * 9 + 3 * k;
+                v += Fs[3 * j + Jc] * (Ar[0] * Fs[3 * l] + Ar[1] * Fs[3 * l + 1] + Ar[2] * Fs[3 * l + 2]);
+            }
+            if (i == k) v -= Ps[3 * j] * Fs[3 * l] + Ps[3 * j + 1] * Fs[3 * l + 1] + Ps[3 * j + 2] * Fs[3 * l + 2];
+        }
+        if (valid) {
+            if (o < 6)
+                tau[o * stride] = v;
+            else
+                c[(o - 6) * stride] = v;
+        }
+    }
+}
+
 // P_a alone (no tangent): sum_m c_m g_m[a] + 2 kappa (J - 1) J H_a.
 template <typename T, int NF>
 __device__ __forceinline__ T assemble_P(int a, const T *st, const T *c) {

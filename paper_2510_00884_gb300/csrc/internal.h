@@ -82,7 +82,12 @@ namespace commet {
 int launch_const_update(const commet_model *m, int64_t n_qp, const void *F, void *psi, void *P, void *A,
                         int32_t *status, cudaStream_t s, void *dN_out = nullptr);
 int launch_const_update_bf16(const commet_model *m, int64_t n_qp, const void *F, void *psi, void *P, void *A,
-                             int32_t *status, cudaStream_t s);
+                             int32_t *status, cudaStream_t s, bool spatial = false);
+// Spatial form (App. A.1): tau [6][n], c [21][n] (Voigt) instead of P, A; all precisions.
+int launch_const_update_spatial(const commet_model *m, int64_t n_qp, const void *F, void *psi, void *tau, void *c,
+                                int32_t *status, cudaStream_t s);
+int launch_elem_assemble_spatial(const commet_mesh *mesh, int precision, const void *F, const void *tau,
+                                 const void *c, void *f_e, void *K_e, void *r, void *K_vals, cudaStream_t s);
 int launch_status_init(int32_t *status, cudaStream_t s);
 int launch_target_stress(int precision, int64_t n_qp, const void *F, int nf, const double *fib, double mu,
                          double k1, double k2, double kappa, void *P, cudaStream_t s);

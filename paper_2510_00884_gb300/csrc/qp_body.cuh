@@ -39,16 +39,24 @@ struct CUConf {
     static constexpr int NC = NC0 < NJ ? NC0 : NJ;
 };
 
-// Per-qp slab size in elements of T for the given network (host and device agree).
+// End of the staging area in a point's slab (elements of T): staged kinematics, then
+// u[9][DP] and d2N/dK2 [D][DP] (see qp_group_update). The spatial-output kernels put the
+// point's P (9) and A (81) right after it.
+__host__ __device__ inline int qp_stage_end(int D, int NF) {
+    const int DP = (D + 3) / 4 * 4;
+    return (9 * D + 54 + 18 * NF + 5 + NF + 3) / 4 * 4 + 9 * DP + D * DP;
+}
+
+// Per-qp slab size in elements of T for the given network (host and device agree);
+// with `spatial`, room for P and A after the staging area.
 template <typename T>
-__host__ __device__ inline int qp_slab_elems(int D, int W, int L, int NF) {
+__host__ __device__ inline int qp_slab_elems(int D, int W, int L, int NF, bool spatial = false) {
     const int DP = (D + 3) / 4 * 4;
     const int nbuf = L >= 4 ? 2 : (L == 3 ? 1 : 0);
     int work = 2 * W;
     if (nbuf * W * DP > work) work = nbuf * W * DP;
     int raw = 2 * L * W + work;
-    // staged kinematics, then u[9][DP] and d2N/dK2 [D][DP] (see qp_group_update)
-    const int stage = (9 * D + 54 + 18 * NF + 5 + NF + 3) / 4 * 4 + 9 * DP + D * DP;
+    const int stage = qp_stage_end(D, NF) + (spatial ? 90 : 0);
     if (stage > raw) raw = stage;
     int words = raw * (int)sizeof(T) / 4;
     words = (words + 31) / 32 * 32 + 4;

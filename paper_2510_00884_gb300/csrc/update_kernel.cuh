@@ -1,0 +1,129 @@
+// The fused constitutive-update kernel and its launcher, shared by the material-form
+// entry (const_update.cu: P, A) and the spatial-form entry (spatial.cu: tau, c in Voigt
+// form, App. A.1); each translation unit instantiates one form.
+//
+// Fused constitutive update (Algorithm 2's constitutive call): F -> kinematic scalars K ->
+// MICNN value, gradient and Hessian -> P, A, Psi, one persistent kernel over all points.
+// The per-point work is qp_group_update (qp_body.cuh): a group of 4 lanes per point,
+// 8 points per warp, the whole network in shared memory.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdint>
+
+#include "qp_body.cuh"
+
+namespace commet {
+
+int sm_count();
+
+template <typename T, int NF, int W, bool SPATIAL>
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 384)
+    const_update_kernel(const T *__restrict__ gw, NetLayout lay, KinConst<T> kc, int64_t n_qp,
+                        const T *__restrict__ Fg, T *__restrict__ psi, T *__restrict__ P, T *__restrict__ A,
+                        int32_t *__restrict__ status, T *__restrict__ dN_out, int qstride) {
+    using Cf = CUConf<T, NF, W>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sw = reinterpret_cast<T *>(smem_raw);
+    const int wbytes = (lay.total * (int)sizeof(T) + 15) / 16 * 16;
+    {
+        const int n16 = wbytes / 16;
+        const int4 *src = reinterpret_cast<const int4 *>(gw);
+        int4 *dst = reinterpret_cast<int4 *>(sw);
+        for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int qi = lane >> 2, jb = lane & 3;
+    T *qs = sw + wbytes / (int)sizeof(T) + (size_t)(warp * kQPW + qi) * qstride;
+    const int64_t n_tiles = (n_qp + kQPW - 1) / kQPW;
+    const int64_t n_gwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+
+    for (int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; tile < n_tiles; tile += n_gwarps) {
+        const int64_t q = tile * kQPW + qi;
+        const bool valid = q < n_qp;
+        T F[9];
+#pragma unroll
+        for (int cpt = 0; cpt < 9; ++cpt) F[cpt] = valid ? Fg[cpt * n_qp + q] : ((cpt % 4) == 0 ? T(1) : T(0));
+        const int64_t qo = valid ? q : 0;
+        T psi_val;
+        bool report;
+        if constexpr (SPATIAL) {
+            // P and A of the point go to its slab, then are pushed forward to tau (P) and c (A)
+            T *pa = qs + qp_stage_end(Cf::D, NF);
+            qp_group_update<T, NF, W>(sw, lay, kc, qs, qi, jb, F, valid, pa, 1, A ? pa + 9 : nullptr, 1, nullptr, 0,
+                                      psi_val, report);
+            __syncwarp();
+            push_forward_group<T>(qs + Stage<Cf::D, NF>::F, pa, pa + 9, jb, valid, P + qo, A ? A + qo : nullptr, n_qp);
+        } else {
+            qp_group_update<T, NF, W>(sw, lay, kc, qs, qi, jb, F, valid, P + qo, n_qp, A ? A + qo : nullptr, n_qp,
+                                      dN_out ? dN_out + qo : nullptr, n_qp, psi_val, report);
+        }
+        if (valid && jb == 0) {
+            if (psi != nullptr) psi[q] = psi_val;
+            if (report && status != nullptr) {
+                atomicAdd(&status[0], 1);
+                atomicMin(&status[1], (int32_t)(q < INT32_MAX ? q : INT32_MAX));
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <typename T, int NF, int W, bool SPATIAL>
+static int launch_typed(const commet_model *m, int64_t n_qp, const void *F, void *psi, void *P, void *A,
+                        int32_t *status, cudaStream_t s, void *dN_out) {
+    using Cf = CUConf<T, NF, W>;
+    KinConst<T> kc{};
+    kc.kin = m->kp.kin;
+    kc.stress_free = m->kp.stress_free;
+    kc.kappa = (T)m->kp.kappa;
+    for (int f = 0; f < 2; ++f)
+        for (int c = 0; c < 3; ++c) kc.fib[f][c] = (T)m->kp.fib[f][c];
+    const int qstride = qp_slab_elems<T>(Cf::D, W, m->L, NF, SPATIAL);
+    const size_t wbytes = ((size_t)m->lay.total * sizeof(T) + 15) / 16 * 16;
+    const size_t per_warp = (size_t)kQPW * qstride * sizeof(T);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int smem_max = 0;
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int max_threads = sizeof(T) == 8 ? 256 : 384;
+    int warps = (int)std::min<size_t>((size_t)max_threads / 32, (smem_max - wbytes) / per_warp);
+    if (smem_max < (int)wbytes || warps < 1) return COMMET_ERR_UNSUPPORTED;
+    const size_t smem = wbytes + warps * per_warp;
+    auto kern = const_update_kernel<T, NF, W, SPATIAL>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return COMMET_ERR_CUDA;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t n_tiles = (n_qp + kQPW - 1) / kQPW;
+    const int64_t want = (n_tiles + warps - 1) / warps;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count() * per_sm));
+    kern<<<grid, warps * 32, smem, s>>>((const T *)m->d_weights, m->lay, kc, n_qp, (const T *)F, (T *)psi, (T *)P,
+                                        (T *)A, status, (T *)dN_out, qstride);
+    return cudaGetLastError() == cudaSuccess ? COMMET_OK : COMMET_ERR_CUDA;
+}
+
+template <typename T, bool SPATIAL>
+static int dispatch(const commet_model *m, int64_t n_qp, const void *F, void *psi, void *P, void *A,
+                    int32_t *status, cudaStream_t s, void *dN_out) {
+    const int nf = m->kp.nf, W = m->W;
+#define COMMET_CASE(NF_, W_) \
+    if (nf == NF_ && W == W_) return launch_typed<T, NF_, W_, SPATIAL>(m, n_qp, F, psi, P, A, status, s, dN_out);
+    COMMET_CASE(0, 16)
+    COMMET_CASE(0, 32)
+    COMMET_CASE(0, 64)
+    COMMET_CASE(1, 16)
+    COMMET_CASE(1, 32)
+    COMMET_CASE(2, 16)
+    COMMET_CASE(2, 32)
+    COMMET_CASE(2, 64)
+#undef COMMET_CASE
+    return COMMET_ERR_UNSUPPORTED;
+}
+
+}  // namespace commet
