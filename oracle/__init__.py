@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "commet_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-INNER_MICNN, INNER_GENT_THOMAS, INNER_HGO = 0, 1, 2
+INNER_MICNN, INNER_GENT_THOMAS, INNER_HGO, INNER_CANN = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -38,7 +38,8 @@ class _Model(C.Structure):
                 ("Bk", C.POINTER(C.c_double)), ("c", C.POINTER(C.c_double)),
                 ("a", C.POINTER(C.c_double)), ("b", C.POINTER(C.c_double)),
                 ("kappa", C.c_double), ("stress_free", C.c_int),
-                ("mu", C.c_double), ("k1", C.c_double), ("k2", C.c_double)]
+                ("mu", C.c_double), ("k1", C.c_double), ("k2", C.c_double),
+                ("cann_n", C.c_int), ("cann_kind", C.POINTER(C.c_int)), ("cann_w", C.POINTER(C.c_double))]
 
 
 _lib = None
@@ -84,7 +85,23 @@ class OracleModel:
     def __init__(self, spec=None, inner: int = INNER_MICNN, kin: int | None = None,
                  fibres=None, kappa: float | None = None, mu=1.0, k1=2.0, k2=0.5,
                  stress_free: bool | None = None):
-        if spec is not None:
+        self.kind = self.cw = None
+        cann_n = 0
+        if spec is not None and getattr(spec, "inner_name", "micnn") != "micnn":
+            # closed-form and CANN inner functions: no network arrays
+            inner = {"cann": INNER_CANN, "gent_thomas": INNER_GENT_THOMAS}[spec.inner_name]
+            kin = spec.kin if kin is None else kin
+            fibres = spec.fibres if fibres is None else fibres
+            kappa = spec.kappa if kappa is None else kappa
+            stress_free = spec.stress_free if stress_free is None else stress_free
+            d, W, L = spec.d, 1, 1
+            self.arrs = {"W1": np.zeros((1, d)), "Ak": np.zeros(1), "Bk": np.zeros(1),
+                         "c": np.zeros((1, 1)), "a": np.zeros(1), "b": np.zeros(d)}
+            if spec.inner_name == "cann":
+                cann_n = int(spec.n)
+                self.kind = np.ascontiguousarray(spec.kinds, dtype=np.int32).reshape(cann_n, 3)
+                self.cw = _c64(spec.w).reshape(d, cann_n, 2)
+        elif spec is not None:
             d, W, L = spec.d, spec.W, spec.L
             kin = spec.kin if kin is None else kin
             fibres = spec.fibres if fibres is None else fibres
@@ -105,7 +122,9 @@ class OracleModel:
                         inner=int(inner), W1=_dp(self.arrs["W1"]), Ak=_dp(self.arrs["Ak"]),
                         Bk=_dp(self.arrs["Bk"]), c=_dp(self.arrs["c"]), a=_dp(self.arrs["a"]),
                         b=_dp(self.arrs["b"]), kappa=float(kappa), stress_free=int(bool(stress_free)),
-                        mu=float(mu), k1=float(k1), k2=float(k2))
+                        mu=float(mu), k1=float(k1), k2=float(k2), cann_n=cann_n,
+                        cann_kind=self.kind.ctypes.data_as(C.POINTER(C.c_int)) if self.kind is not None else None,
+                        cann_w=_dp(self.cw))
 
 
 def const_update(model: OracleModel, F: np.ndarray, want_A: bool = True):

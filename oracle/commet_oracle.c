@@ -43,7 +43,9 @@
 /* ------------------------------------------------------------------ model */
 
 enum { OR_KIN_ISO_SHIFTED = 0, OR_KIN_RAW = 1, OR_KIN_POLYCONVEX = 2 };
-enum { OR_INNER_MICNN = 0, OR_INNER_GENT_THOMAS = 1, OR_INNER_HGO = 2 };
+enum { OR_INNER_MICNN = 0, OR_INNER_GENT_THOMAS = 1, OR_INNER_HGO = 2, OR_INNER_CANN = 3 };
+enum { OR_F0_ID = 0, OR_F0_MACAULAY = 1, OR_F0_ABS = 2 };
+enum { OR_F2_LINEAR = 0, OR_F2_EXP = 1, OR_F2_LOG = 2 };
 
 /*
  * Strain-energy model Psi(F) = N(K(F)) + kappa (J-1)^2 [- n0 . (K - K0)].
@@ -61,6 +63,9 @@ enum { OR_INNER_MICNN = 0, OR_INNER_GENT_THOMAS = 1, OR_INNER_HGO = 2 };
  *     (Ibar1, Ibar2, J)  (eq. gt).
  *   OR_INNER_HGO: N = mu/2 (K0 - 3) + sum_f k1/(2 k2) (exp(k2 (K_{3+f} - 1)^2) - 1)
  *     on raw kinematics (Neo-Hookean plus exponential fibre terms).
+ *   OR_INNER_CANN: eq. cann-def, N = sum_m sum_k w2_mk f2_k(f1_k(f0_k(K_m)); w1_mk) with
+ *     term k's functions from the menus of eq. cann-fs: f0 in {x, <x>, |x|}, f1 = x^p
+ *     (p = 1, 2, 3), f2 in {w1 y, exp(w1 y) - 1, -ln(1 - w1 y)}.
  * stress_free: subtract n0 . (K - K0), n0 = dN/dK at K0 = K(I), so that P(I) = 0.
  */
 typedef struct {
@@ -78,6 +83,9 @@ typedef struct {
     double kappa;
     int stress_free;
     double mu, k1, k2;
+    int cann_n;             /* CANN: terms per input */
+    const int *cann_kind;   /* CANN: [n][3] (f0, p, f2) */
+    const double *cann_w;   /* CANN: [d][n][2] (w1, w2) */
 } oracle_model;
 
 #define OR_MAXD 16
@@ -407,8 +415,68 @@ static void hgo(const oracle_model *m, const double *K, double *N, double *dN, d
     *N = s;
 }
 
+/*
+ * CANN (eq. cann-def) and its derivatives by the chain rule of eq. cann-chain-rule:
+ *   dN/dK_m   = sum_k w2 f2' f1' f0'
+ *   d2N/dK_m2 = sum_k w2 [(f2'' f1'^2 + f2' f1'') f0'^2 + f2' f1' f0'']
+ * and d2N/dK_m dK_n = 0 for m != n. The menus' derivatives are written from their
+ * definitions: d/dy (-ln(1 - w1 y)) = w1 / (1 - w1 y), second derivative
+ * + w1^2 / (1 - w1 y)^2 (the printed table has a minus sign here); <x>' = (1 + sign x)/2,
+ * |x|' = sign x, both with zero second derivative away from 0.
+ */
+static void cann(const oracle_model *m, const double *K, double *N, double *dN, double *d2N) {
+    const int d = m->d, n = m->cann_n;
+    for (int i = 0; i < d * d; ++i) d2N[i] = 0.0;
+    double s = 0.0;
+    for (int mm = 0; mm < d; ++mm) {
+        double g = 0.0, h = 0.0;
+        for (int k = 0; k < n; ++k) {
+            const int *kind = &m->cann_kind[3 * k];
+            const double w1 = m->cann_w[(mm * n + k) * 2], w2 = m->cann_w[(mm * n + k) * 2 + 1];
+            const double x = K[mm];
+            double f0, f0d, f0dd = 0.0;
+            if (kind[0] == OR_F0_MACAULAY) {
+                f0 = x > 0.0 ? x : 0.0;
+                f0d = 0.5 * (1.0 + (x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0)));
+            } else if (kind[0] == OR_F0_ABS) {
+                f0 = fabs(x);
+                f0d = x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0);
+            } else {
+                f0 = x;
+                f0d = 1.0;
+            }
+            const int p = kind[1];
+            const double f1 = pow(f0, p), f1d = p * pow(f0, p - 1), f1dd = p * (p - 1) * (p >= 2 ? pow(f0, p - 2) : 0.0);
+            double f2, f2d, f2dd;
+            if (kind[2] == OR_F2_EXP) {
+                const double e = exp(w1 * f1);
+                f2 = e - 1.0;
+                f2d = w1 * e;
+                f2dd = w1 * w1 * e;
+            } else if (kind[2] == OR_F2_LOG) {
+                const double q = 1.0 - w1 * f1;
+                f2 = -log(q);
+                f2d = w1 / q;
+                f2dd = w1 * w1 / (q * q);
+            } else {
+                f2 = w1 * f1;
+                f2d = w1;
+                f2dd = 0.0;
+            }
+            s += w2 * f2;
+            g += w2 * f2d * f1d * f0d;
+            h += w2 * ((f2dd * f1d * f1d + f2d * f1dd) * f0d * f0d + f2d * f1d * f0dd);
+        }
+        dN[mm] = g;
+        d2N[mm * d + mm] = h;
+    }
+    *N = s;
+}
+
 static void inner_eval(const oracle_model *m, const double *K, double *N, double *dN, double *d2N) {
-    if (m->inner == OR_INNER_GENT_THOMAS)
+    if (m->inner == OR_INNER_CANN)
+        cann(m, K, N, dN, d2N);
+    else if (m->inner == OR_INNER_GENT_THOMAS)
         gent_thomas(K, N, dN, d2N);
     else if (m->inner == OR_INNER_HGO)
         hgo(m, K, N, dN, d2N);

@@ -145,11 +145,45 @@ def micnn_forward(spec, K: HD) -> HD:
     return out[0]
 
 
+def _sign(x):
+    return np.sign(x)
+
+
+def cann_forward(spec, K: list) -> HD:
+    """eq. cann-def from the menus of eq. cann-fs, value only, on a list of HD inputs."""
+    out = HD(0.0)
+    for m in range(spec.d):
+        for k in range(spec.n):
+            f0k, p, f2k = (int(v) for v in spec.kinds[k])
+            w1, w2 = float(spec.w[m, k, 0]), float(spec.w[m, k, 1])
+            x = K[m]
+            if f0k == 1:    # Macaulay bracket
+                x = x.apply(np.maximum(x.r, 0.0), 0.5 * (1.0 + _sign(x.r)), 0.0)
+            elif f0k == 2:  # absolute value
+                x = x.apply(np.abs(x.r), _sign(x.r), 0.0)
+            y = x
+            for _ in range(p - 1):
+                y = y * x
+            if f2k == 1:
+                f = hd_exp(w1 * y) - 1.0
+            elif f2k == 2:
+                f = -1.0 * hd_log(1.0 - w1 * y)
+            else:
+                f = w1 * y
+            out = out + w2 * f
+    return out
+
+
 def psi_hd(spec, F9: list, inner=None) -> HD:
     """Psi(F) = N(K(F)) + kappa (J - 1)^2 (stress-free shift not included).
-    inner(K_list) -> HD replaces the MICNN when given."""
+    inner(K_list) -> HD replaces the MICNN when given; CANN specs use eq. cann-def."""
     K, J = kinematic_scalars(F9, spec.kin if inner is None else 1, spec.fibres)
-    N = micnn_forward(spec, hd_stack(K)) if inner is None else inner(K)
+    if inner is not None:
+        N = inner(K)
+    elif getattr(spec, "inner_name", "micnn") == "cann":
+        N = cann_forward(spec, K)
+    else:
+        N = micnn_forward(spec, hd_stack(K))
     return N + spec.kappa * (J - 1.0) * (J - 1.0)
 
 

@@ -681,3 +681,72 @@ def test_spatial_assembly_equals_material_assembly(aniso_spec):
     assert rel(K_s, K_m) < 1e-12
     f_s2, K_s2 = oracle.elem_assemble_spatial(mesh, F, tau6, None)
     assert K_s2 is None and rel(f_s2, f_m) < 1e-12
+
+
+# ----------------------------------------------------------- CANN (eq. cann-def)
+
+ALL_KINDS = np.array([[wl.CANN_F0_ID, 1, wl.CANN_F2_LINEAR], [wl.CANN_F0_ID, 2, wl.CANN_F2_EXP],
+                      [wl.CANN_F0_MACAULAY, 3, wl.CANN_F2_LINEAR], [wl.CANN_F0_ABS, 2, wl.CANN_F2_LOG],
+                      [wl.CANN_F0_ABS, 1, wl.CANN_F2_EXP], [wl.CANN_F0_MACAULAY, 2, wl.CANN_F2_LOG]],
+                     dtype=np.int32)
+
+
+@pytest.mark.parametrize("kin,nf", [(wl.KIN_POLYCONVEX, 0), (wl.KIN_RAW, 2), (wl.KIN_ISO_SHIFTED, 0)])
+def test_cann_exact_derivatives(kin, nf):
+    """Every menu entry of eq. cann-fs through the oracle's chain rule (eq. cann-chain-rule)
+    against hyper-dual derivatives of the value-only CANN; the f2 = -ln(1 - w1 y) term fixes
+    the sign of its second derivative (+w1^2 / (1 - w1 y)^2)."""
+    rng = np.random.Generator(np.random.PCG64(40 + kin))
+    # raw inputs are O(3): smaller weights keep 1 - w1 y > 0 for the logarithmic term
+    spec = wl.make_cann(rng, kin, nf, kinds=ALL_KINDS, kappa=2.0, std=0.02 if kin == wl.KIN_RAW else 0.2)
+    m = oracle.OracleModel(spec)
+    F = rand_F(rng, 4, 0.25)
+    psi, P, A = oracle.const_update(m, F)
+    for q in range(F.shape[0]):
+        psi_h, P_h, A_h = hdm.exact_P_A(spec, F[q])
+        assert abs(psi[q] - psi_h) < 1e-13 * max(1, abs(psi_h))
+        assert rel(P[q], P_h) < 1e-12
+        assert rel(A[q], A_h) < 1e-12
+
+
+def test_cann_reduces_to_neo_hookean():
+    """One linear term w2 w1 (Ibar1 - 3) with w1 w2 = mu / 2 is the textbook Neo-Hookean."""
+    mu, kappa = 1.7, 10.0
+    w = np.zeros((3, 1, 2))
+    w[0, 0] = (0.5, mu)  # w1 = 0.5, w2 = mu
+    spec = wl.CannSpec(d=3, kin=wl.KIN_ISO_SHIFTED, fibres=np.zeros((0, 3)), n=1,
+                       kinds=np.array([[wl.CANN_F0_ID, 1, wl.CANN_F2_LINEAR]], dtype=np.int32), w=w, kappa=kappa)
+    m = oracle.OracleModel(spec)
+    rng = np.random.Generator(np.random.PCG64(41))
+    F = rand_F(rng, 8)
+    psi, P, _ = oracle.const_update(m, F)
+    for q in range(F.shape[0]):
+        psi_c, P_c = nh_closed_form(F[q], mu, kappa)
+        assert abs(psi[q] - psi_c) < 1e-13 * max(1, abs(psi_c))
+        assert rel(P[q], P_c) < 1e-13
+
+
+def test_cann_hessian_is_diagonal_and_paper_cann_is_stress_free():
+    rng = np.random.Generator(np.random.PCG64(42))
+    spec = wl.make_cann(rng)
+    m = oracle.OracleModel(spec)
+    _, dN, d2N = oracle.inner(m, np.array([0.3, 0.2, 0.1]))
+    assert np.all(d2N[~np.eye(3, dtype=bool)] == 0.0) and np.all(np.diag(d2N) > 0)
+    _, P, _ = oracle.const_update(m, np.eye(3).ravel()[None])
+    assert np.abs(P).max() < 1e-15
+    assert spec.theta().size == 24
+
+
+def test_gent_thomas_spec_is_eq_gt():
+    """The Gent-Thomas spec (no parameters) is eq. gt, against hyper-dual derivatives."""
+    m = oracle.OracleModel(wl.GentThomasSpec())
+    spec = neo_hookean_spec(1.0, 0.0)
+
+    def gt(K):
+        return 0.5 * (K[0] - 3.0) + hdm.hd_log(K[1] / 3.0) + (K[2] - 1.0) * (K[2] - 1.0)
+    rng = np.random.Generator(np.random.PCG64(43))
+    F = rand_F(rng, 3)
+    psi, P, A = oracle.const_update(m, F)
+    for q in range(3):
+        psi_h, P_h, A_h = hdm.exact_P_A(spec, F[q], inner=gt)
+        assert rel(P[q], P_h) < 1e-12 and rel(A[q], A_h) < 1e-12

@@ -269,6 +269,73 @@ def workload_c0():
     return dict(name="c0_cube8_iso_d3w16l2", model=model, mesh=mesh, u=u)
 
 
+# CANN term menus (eq. cann-fs): f0 in {x, <x>, |x|}, f1 = x^p, f2 in {w1 y, exp(w1 y) - 1, -ln(1 - w1 y)}
+CANN_F0_ID, CANN_F0_MACAULAY, CANN_F0_ABS = 0, 1, 2
+CANN_F2_LINEAR, CANN_F2_EXP, CANN_F2_LOG = 0, 1, 2
+# the paper's CANN (App. C table): exponents {1, 2} x functions {x, exp(x)}
+CANN_PAPER_KINDS = np.array([[CANN_F0_ID, 1, CANN_F2_LINEAR], [CANN_F0_ID, 1, CANN_F2_EXP],
+                             [CANN_F0_ID, 2, CANN_F2_LINEAR], [CANN_F0_ID, 2, CANN_F2_EXP]], dtype=np.int32)
+
+
+@dataclass
+class CannSpec:
+    """A CANN strain energy (eq. cann-def): n terms per input, kinds[n][3] = (f0, p, f2)
+    shared by the inputs, weights w[d][n][2] = (w1, w2) per input and term."""
+    d: int
+    kin: int
+    fibres: np.ndarray
+    n: int
+    kinds: np.ndarray
+    w: np.ndarray
+    kappa: float = 0.0
+    stress_free: bool = False
+    inner_name: str = "cann"
+
+    def theta(self) -> np.ndarray:
+        return np.asarray(self.w, dtype=np.float64).ravel().copy()
+
+
+@dataclass
+class GentThomasSpec:
+    """The closed-form Gent-Thomas energy of eq. gt on raw (Ibar1, Ibar2, J); no parameters."""
+    d: int = 3
+    kin: int = KIN_RAW
+    fibres: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
+    kappa: float = 0.0
+    stress_free: bool = False
+    inner_name: str = "gent_thomas"
+
+
+def make_cann(rng, kin: int = KIN_POLYCONVEX, n_fib: int = 0, kinds=None, kappa: float = 0.0,
+              std: float = 0.1, stress_free: bool = False) -> CannSpec:
+    """CANN with |N(0, std)| weights drawn input by input, term by term (w1 then w2)."""
+    kinds = CANN_PAPER_KINDS if kinds is None else np.asarray(kinds, dtype=np.int32)
+    d = 3 + 2 * n_fib if kin == KIN_RAW else 3
+    fib = FIBRES_PM30[:n_fib].copy() if n_fib else np.zeros((0, 3))
+    w = np.abs(rng.normal(0.0, std, size=(d, kinds.shape[0], 2)))
+    return CannSpec(d=d, kin=kin, fibres=fib, n=int(kinds.shape[0]), kinds=kinds, w=w, kappa=kappa,
+                    stress_free=stress_free)
+
+
+def workload_cann(n: int = 64, seed: int = 6):
+    """The paper's CANN (App. C): exponents {1, 2} x {x, exp(x)} on the polyconvex inputs,
+    24 weights; F = I + 0.15 N(0,1) on an n^3 mesh."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    model = make_cann(rng)
+    mesh = structured_mesh(n)
+    F = random_F(rng, 8 * mesh.n_el, 0.15)
+    return dict(name=f"cann_polyconvex_{n}cube_4terms", model=model, mesh=mesh, F=F)
+
+
+def workload_gent_thomas(n: int = 64, seed: int = 7):
+    """The closed-form Gent-Thomas model of eq. gt (the paper's traditional-law comparison
+    in its model-size study); F = I + 0.15 N(0,1) on an n^3 mesh."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    mesh = structured_mesh(n)
+    F = random_F(rng, 8 * mesh.n_el, 0.15)
+    return dict(name=f"gent_thomas_{n}cube", model=GentThomasSpec(), mesh=mesh, F=F)
+
+
 def workload_paper_ncm(n: int = 64, seed: int = 5):
     """The paper's NCM architecture (App. C, hyper-parameter table): MICNN with 3 hidden
     layers of 16 neurons, no biases (675 parameters), on the polyconvex kinematic layer
