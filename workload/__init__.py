@@ -336,6 +336,27 @@ def workload_gent_thomas(n: int = 64, seed: int = 7):
     return dict(name=f"gent_thomas_{n}cube", model=GentThomasSpec(), mesh=mesh, F=F)
 
 
+def twist_dirichlet(mesh, frac: float, stretch: float = 1.0, turns: float = 0.5):
+    """Prescribed displacements of the twisting-cube benchmark (Sec. 4.3) at load fraction
+    frac: the x = 0 face clamped; the x = Lx face moved frac * stretch along x and rotated by
+    frac * turns * 2 pi about its centre line (y, z) = (Ly / 2, Lz / 2). Returns the fixed
+    dofs (3 node + i, int64, sorted) and their displacement values."""
+    X = np.asarray(mesh.X, dtype=np.float64)
+    x0, x1 = X[:, 0].min(), X[:, 0].max()
+    cy, cz = 0.5 * (X[:, 1].min() + X[:, 1].max()), 0.5 * (X[:, 2].min() + X[:, 2].max())
+    left = np.nonzero(np.isclose(X[:, 0], x0))[0]
+    right = np.nonzero(np.isclose(X[:, 0], x1))[0]
+    th = frac * turns * 2.0 * math.pi
+    c, s_ = math.cos(th), math.sin(th)
+    yr, zr = X[right, 1] - cy, X[right, 2] - cz
+    ur = np.stack([np.full(right.size, frac * stretch), c * yr - s_ * zr - yr, s_ * yr + c * zr - zr], axis=1)
+    nodes = np.concatenate([left, right])
+    vals = np.concatenate([np.zeros((left.size, 3)), ur])
+    dofs = (3 * nodes[:, None] + np.arange(3)[None, :]).ravel()
+    order = np.argsort(dofs, kind="stable")
+    return dofs[order].astype(np.int64), vals.ravel()[order]
+
+
 def workload_paper_ncm(n: int = 64, seed: int = 5):
     """The paper's NCM architecture (App. C, hyper-parameter table): MICNN with 3 hidden
     layers of 16 neurons, no biases (675 parameters), on the polyconvex kinematic layer
