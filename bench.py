@@ -12,6 +12,8 @@ integrals (P, A -> f_int, K_e for every element). Other workloads:
       FP64 GPU path timed beside it
   ncm the paper's NCM (App. C): MICNN d3 W16 L3 without biases (675 parameters) on the
       polyconvex inputs (Ibar1 - 3, Ibar2^{3/2} - 3^{3/2}, (J - 1)^2), 64^3 mesh, c1's step
+  cann the paper's CANN (exponents {1, 2} x {x, exp x}) on the same inputs, c1's step
+  gt  the closed-form Gent-Thomas law (eq. gt), c1's step
 
 Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle on the
 host cores instead (a bounded sample of the same workload per step).
@@ -198,7 +200,8 @@ def make_workload(name: str, n: int | None = None):
     import workload as wl
     kw = {} if n is None else ({"n_qp": n} if name == "c3" else {"n": n})
     return {"c0": wl.workload_c0, "c1": wl.workload_c1, "c2": wl.workload_c2, "c3": wl.workload_c3,
-            "c4": wl.workload_c4, "ncm": wl.workload_paper_ncm}[name](**kw)
+            "c4": wl.workload_c4, "ncm": wl.workload_paper_ncm, "cann": wl.workload_cann,
+            "gt": wl.workload_gent_thomas}[name](**kw)
 
 
 def wl_sub(mesh, el):
@@ -249,7 +252,7 @@ class Run:
         self.model = pkg.Model(spec, prec)
         self.mesh = w.get("mesh")
         mp = "f64" if prec == "f64" else "f32"
-        if name in ("c1", "c2", "ncm"):
+        if name in ("c1", "c2", "ncm", "cann", "gt"):
             F_host = np.ascontiguousarray(w["F"].T)
             self.inputs_host = {"F": F_host}
             n = F_host.shape[1]
@@ -268,7 +271,7 @@ class Run:
                 self.phases = [("const_update_kernel",
                                 lambda: self.model.const_update(self.F, out=(self.psi, self.P, self.A)))]
             self.outputs = [self.psi, self.P, self.A]
-            if name in ("c1", "ncm"):
+            if name in ("c1", "ncm", "cann", "gt"):
                 self.gmesh = pkg.Mesh(self.mesh.X, self.mesh.conn)
                 self.f_e = torch.empty(24, self.n_el, dtype=dt, device=dev)
                 self.K_e = torch.empty(576, self.n_el, dtype=dt, device=dev)
@@ -423,8 +426,8 @@ def run_ours(args, rank, world, local_rank):
     name = args.workload
     prec = args.precision or ("f32" if name == "c4" else "f64")
     w = make_workload(name, args.n)
-    if args.spatial and name not in ("c1", "c2", "ncm"):
-        raise SystemExit("--spatial applies to the c1, c2 and ncm workloads")
+    if args.spatial and name not in ("c1", "c2", "ncm", "cann", "gt"):
+        raise SystemExit("--spatial applies to the c1, c2, ncm, cann and gt workloads")
     run = Run(name, w, prec, dev, pkg, torch, spatial=args.spatial)
     stream = torch.cuda.current_stream()
     dist = world > 1
@@ -499,7 +502,7 @@ def run_ours(args, rank, world, local_rank):
                "ms_per_step": e_ms / n_e2e}
 
     fp64_base = None
-    if name in ("c1", "c2", "c3", "ncm") and prec != "f64" and not args.no_baseline and rank == 0:
+    if name in ("c1", "c2", "c3", "ncm", "cann", "gt") and prec != "f64" and not args.no_baseline and rank == 0:
         # the same step through the plain FP64 path of the same kernels
         run64 = Run(name, w, "f64", dev, pkg, torch, spatial=args.spatial)
         b_ms = time_steps(run64, torch, 2, 3)
@@ -521,21 +524,22 @@ def run_ours(args, rank, world, local_rank):
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
     spec = run.spec
-    net = f"d{spec.d}w{spec.W}l{spec.L}"
+    sW, sL = getattr(spec, "W", 0), getattr(spec, "L", 0)
+    net = f"d{spec.d}w{sW}l{sL}"
     dom = int(np.argmax(phase_ms))
     kname = run.phases[dom][0]
     alu = "f64" if prec == "f64" else "f32"
     if kname == "const_update_kernel":
-        per_qp = algorithmic_flops_per_qp(spec.d, spec.W, spec.L) + (2 * PUSH_FORWARD_MACS if args.spatial else 0)
+        per_qp = algorithmic_flops_per_qp(spec.d, sW, sL) + (2 * PUSH_FORWARD_MACS if args.spatial else 0)
         flops = per_qp * run.n_qp
         units = run.n_qp
         src = ["spatial.cu" if args.spatial else "const_update.cu", "update_kernel.cuh", "qp_body.cuh",
                "device_math.cuh"]
     elif kname == "const_backward_kernel":
-        flops = backward_flops_per_qp(spec.d, spec.W, spec.L) * run.n_qp
+        flops = backward_flops_per_qp(spec.d, sW, sL) * run.n_qp
         units, src = run.n_qp, ["backward.cu", "device_math.cuh"]
     elif kname == "newton_kernel":
-        flops = (algorithmic_flops_per_qp(spec.d, spec.W, spec.L) * 8 + 2 * ELEM_MACS) * run.n_el
+        flops = (algorithmic_flops_per_qp(spec.d, sW, sL) * 8 + 2 * ELEM_MACS) * run.n_el
         units, src = run.n_el, ["newton.cu", "qp_body.cuh", "device_math.cuh"]
     else:
         flops = 2 * ELEM_MACS * run.n_el
@@ -547,7 +551,7 @@ def run_ours(args, rank, world, local_rank):
     if prec == "bf16" and kname == "const_update_kernel":
         # the hidden W x W products run on the tensor cores: values, adjoints and the d
         # tangent channels of every hidden layer, 2 (L-1) W^2 (2 + d) flops per point
-        flops = 2 * (spec.L - 1) * spec.W * spec.W * (2 + spec.d) * run.n_qp
+        flops = 2 * (sL - 1) * sW * sW * (2 + spec.d) * run.n_qp
         bound = "tensor"
         peak = float(peaks.get("bf16_tflops", 1900.0))
         peak_source = f"bf16 dense matmul burst ({peak_src} peaks file); mma.sync m16n8k16 bf16, fp32 accumulate"
@@ -561,6 +565,16 @@ def run_ours(args, rank, world, local_rank):
                 "algorithmic_flops_per_launch": flops, "kernel_ms": phase_ms[dom],
                 "frac_at_median_clock": (achieved / peak * mhz / clocks["sm_mhz"]) if clocks.get("sm_mhz") else None,
                 "src_hash": src_hash}
+    if kname == "const_update_kernel" and getattr(spec, "inner_name", "micnn") != "micnn":
+        # no network: the algorithmic work is the output stream (9 in, 1 + 9 + 81 or
+        # 1 + 6 + 21 out per point), so the roofline is HBM
+        es = 8 if prec == "f64" else 4
+        per_qp = (9 + 1 + (6 + 21 if args.spatial else 9 + 81)) * es
+        bts = per_qp * run.n_qp / (phase_ms[dom] * 1e-3) / 1e9
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        roofline = {"bound": "hbm", "kernel": kname, "achieved": bts, "peak": hbm, "unit": "GB/s",
+                    "frac": bts / hbm, "traffic": None, "bytes_per_qp": per_qp,
+                    "peak_source": f"measured HBM copy ({peak_src} peaks file)", "kernel_ms": phase_ms[dom]}
     phases = {n_: ms for (n_, _), ms in zip(run.phases, phase_ms)}
     ek = "elem_spatial_kernel" if args.spatial else "elem_assemble_kernel"
     if ek in phases:
@@ -578,7 +592,8 @@ def run_ours(args, rank, world, local_rank):
         cpu = {"value": qps_cpu, "unit": "qp/s", "cores": os.cpu_count() or 1, "kind": "oracle",
                "sample": f"{what} of {w['name']}, {secs:.1f} s", "elements_per_s": eps_cpu}
 
-    cfg = {"workload": w["name"], "n_qp": run.n_qp, "n_el": run.n_el, "network": f"d{spec.d} W{spec.W} L{spec.L}",
+    cfg = {"workload": w["name"], "n_qp": run.n_qp, "n_el": run.n_el, "network": (f"d{spec.d} W{sW} L{sL}" if getattr(spec, "inner_name", "micnn") == "micnn"
+                                           else f"{spec.inner_name} d{spec.d}"),
            "precision": prec, "outputs": "tau, c (Voigt, spatial)" if args.spatial else "P, A (material)", "parallelism": f"replicas x{world} (independent meshes)",
            "l2": "inputs/outputs larger than L2 (129 MB) every step"}
     res = {
@@ -644,13 +659,170 @@ def run_reference(args):
     }
 
 
+# --------------------------------------------------------- twisting cube
+
+def run_twist(args):
+    """The FE benchmark of Sec. 4.3 on the GPU: a unit cube of n^3 hex8 elements (the paper's
+    largest is 128^3, 6,440,067 dofs) clamped at x = 0; the x = 1 face is stretched by 1 and
+    turned by half a turn in `--twist-steps` load steps. A timed step is the first load step
+    solved from u = 0: a predictor that moves the fixed dofs through the system, then Newton
+    iterations of fused FP64 assembly (u -> r, K), Dirichlet rows and columns, Jacobi-CG
+    (rtol 1e-8) and the update, until |r_free| <= 1e-8 max(1, |r_free| after the predictor).
+    Reports assembly and solve time separately, as the paper compares them."""
+    import torch
+    import workload as wl
+    import paper_2510_00884_gb300 as pkg
+    pkg.build()
+    dev = torch.device("cuda", 0)
+    n = args.n or 32
+    mesh = wl.structured_mesh(n)
+    spec = wl.workload_paper_ncm(n=1)["model"]
+    gm = pkg.Mesh(mesh.X, mesh.conn, want_csr=True)
+    model = pkg.Model(spec, "f64")
+    dofs, vals = wl.twist_dirichlet(mesh, 1.0 / args.twist_steps)
+    gm.set_dirichlet(dofs)
+    u = torch.zeros(3, mesh.n_nodes, dtype=torch.float64, device=dev)
+    r = torch.empty(3 * mesh.n_nodes, dtype=torch.float64, device=dev)
+    Kv = torch.empty(gm.nnz, dtype=torch.float64, device=dev)
+    du = torch.empty_like(r)
+    ws = torch.empty(int(pkg._lib.load().commet_cg_workspace(gm.handle, 0)), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def load_step(times):
+        # predictor (fixed dofs moved by their increment through the system), then Newton
+        u.zero_()
+        r0, newton, cg_its = None, 0, 0
+        for it in range(30):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            pkg.newton_assemble(model, gm, u, out=(r, Kv))
+            gm.apply_dirichlet(r, Kv, delta=vals if it == 0 else None)
+            e1.record(stream)
+            if it > 0:
+                rn = gm.norm2(r)
+                r0 = rn if r0 is None else r0
+                if rn <= 1e-8 * max(1.0, r0):
+                    times["assembly"].append((e0, e1, None))
+                    break
+            _, n_cg, _ = gm.cg_solve(Kv, r, "f64", 1e-8, 50000, x=du, workspace=ws)
+            gm.add_increment(du, -1.0, u)
+            if it == 0:
+                gm.set_dirichlet_values(vals, u)
+            e2.record(stream)
+            times["assembly"].append((e0, e1, e2))
+            newton += 1
+            cg_its += n_cg
+        return newton, cg_its
+
+    for _ in range(max(1, args.warmup)):
+        load_step({"assembly": []})
+    torch.cuda.synchronize()
+    times = {"assembly": []}
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    its = [load_step(times) for _ in range(args.steps)]
+    t1.record(stream)
+    torch.cuda.synchronize()
+    total = t0.elapsed_time(t1) / args.steps
+    asm = sum(a.elapsed_time(b) for a, b, _ in times["assembly"]) / args.steps
+    sol = sum(b.elapsed_time(c) for a, b, c in times["assembly"] if c is not None) / args.steps
+    newton = its[0][0]
+    res = {"metric": "twisting-cube load step (Sec. 4.3): Newton with fused assembly and Jacobi-CG",
+           "value": newton * 8 * mesh.n_el / (total * 1e-3), "unit": "assembled qp/s over the load step",
+           "ms_per_load_step": total, "assembly_ms": asm, "solve_ms": sol, "newton_iterations": newton,
+           "cg_iterations": its[0][1], "dofs": 3 * mesh.n_nodes, "n_el": mesh.n_el, "nnz": gm.nnz,
+           "steps": args.steps, "warmup": args.warmup, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"twist_{n}cube", "network": "paper NCM d3 W16 L3 (675 parameters)",
+                      "load": f"1/{args.twist_steps} of a unit stretch and a half turn", "cg_rtol": 1e-8}}
+    print(json.dumps(res), flush=True)
+
+
+# ------------------------------------------------------------------ sweeps
+
+def run_sweep(args):
+    """GPU analogues of the paper's material-point studies (one JSON line per case):
+      size   model size (App. D): MICNN on the polyconvex inputs with L in {2, 3, 4} hidden
+             layers and W in {4, 8, 16, 32, 64}, plus the CANN and Gent-Thomas laws, at
+             2^21 points per launch, P and A in FP64 and FP32
+      batch  points per launch (the paper's batch size, Sec. 4.1) from 2^8 to 2^24 for the
+             paper's NCM (3 x 16, 675 parameters), FP64 and FP32
+    Each case: 3 warm-up launches, then the mean of `steps` launches timed with CUDA events."""
+    import torch
+    import workload as wl
+    import paper_2510_00884_gb300 as pkg
+    pkg.build()
+    dev = torch.device("cuda", 0)
+    peaks, _ = load_peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    rng = np.random.Generator(np.random.PCG64(11))
+
+    def timed(model, F, out):
+        for _ in range(3):
+            model.const_update(F, out=out)
+        s = torch.cuda.current_stream()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record(s)
+        for _ in range(args.steps):
+            model.const_update(F, out=out)
+        t1.record(s)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / args.steps
+
+    def case(spec, label, n, prec, F_host):
+        dt = torch.float64 if prec == "f64" else torch.float32
+        F = torch.from_numpy(np.ascontiguousarray(F_host[:n].T)).to(device=dev, dtype=dt).contiguous()
+        out = (torch.empty(n, dtype=dt, device=dev), torch.empty(9, n, dtype=dt, device=dev),
+               torch.empty(81, n, dtype=dt, device=dev))
+        try:
+            m = pkg.Model(spec, prec)
+            ms = timed(m, F, out)
+        except pkg._lib.CommetError as e:
+            print(json.dumps({"sweep": args.sweep, "case": label, "precision": prec, "n_qp": n, "error": str(e)}),
+                  flush=True)
+            return
+        rec = {"sweep": args.sweep, "case": label, "precision": prec, "n_qp": n, "ms": ms,
+               "qp_per_s": n / (ms * 1e-3), "n_params": m.n_params}
+        if getattr(spec, "inner_name", "micnn") == "micnn":
+            fl = algorithmic_flops_per_qp(spec.d, spec.W, spec.L) * n / (ms * 1e-3) / 1e12
+            pk = alu_peak_tflops("f64" if prec == "f64" else "f32", n_sm, mhz)
+            rec.update({"bound": "alu", "achieved_tflops": fl, "frac": fl / pk})
+        else:
+            es = 8 if prec == "f64" else 4
+            gbs = 100 * es * n / (ms * 1e-3) / 1e9
+            rec.update({"bound": "hbm", "achieved_gbs": gbs, "frac": gbs / float(peaks.get("hbm_gbs", 6800.0))})
+        del F, out, m
+        torch.cuda.empty_cache()
+        print(json.dumps(rec), flush=True)
+
+    n_max = 1 << (24 if args.sweep == "batch" else 21)
+    F_host = wl.random_F(rng, n_max, 0.15)
+    if args.sweep == "size":
+        for L in (2, 3, 4):
+            for W in (4, 8, 16, 32, 64):
+                spec = wl.make_model(np.random.Generator(np.random.PCG64(100 * L + W)), wl.KIN_POLYCONVEX, 0,
+                                     W=W, L=L, kappa=0.0)
+                for prec in ("f64", "f32"):
+                    case(spec, f"micnn L{L} W{W}", n_max, prec, F_host)
+        for label, spec in (("cann (paper, 4 terms)", wl.make_cann(np.random.Generator(np.random.PCG64(9)))),
+                            ("gent-thomas", wl.GentThomasSpec())):
+            for prec in ("f64", "f32"):
+                case(spec, label, n_max, prec, F_host)
+    else:
+        spec = wl.workload_paper_ncm(n=1)["model"]
+        for prec in ("f64", "f32"):
+            for e in range(8, 25, 2):
+                case(spec, "paper NCM 3x16", 1 << e, prec, F_host)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["c0", "c1", "c2", "c3", "c4", "ncm"], default="c1")
+    ap.add_argument("--workload", choices=["c0", "c1", "c2", "c3", "c4", "ncm", "cann", "gt"], default="c1")
     ap.add_argument("--n", type=int, default=None, help="mesh size per side (points for c3)")
     ap.add_argument("--precision", choices=["f64", "f32", "bf16"], default=None,
                     help="default: f64 (f32 for c4)")
@@ -659,6 +831,11 @@ def main():
     ap.add_argument("--spatial", action="store_true",
                     help="c1/c2/ncm: spatial Voigt outputs tau, c and the spatial element kernel")
     ap.add_argument("--no-baseline", action="store_true", help="skip the FP64 GPU timing beside a reduced-precision step (c4: the unfused FP64 path)")
+    ap.add_argument("--twist", action="store_true",
+                    help="the twisting-cube Newton benchmark of Sec. 4.3 (--n elements per side)")
+    ap.add_argument("--twist-steps", type=int, default=20)
+    ap.add_argument("--sweep", choices=["size", "batch"], default=None,
+                    help="model-size or batch-size sweep of the update (one JSON line per case)")
     ap.add_argument("--cpu-sample-el", type=int, default=65536)
     ap.add_argument("--ref-sample-el", type=int, default=4096)
     args = ap.parse_args()
@@ -667,6 +844,12 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.sweep is not None:
+        run_sweep(args)
+        return
+    if args.twist:
+        run_twist(args)
+        return
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)))

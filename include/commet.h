@@ -59,6 +59,20 @@ extern "C" {
 
 #define COMMET_ACT_SOFTPLUS 0 /* F(y) = log(1 + exp(y)), the only activation built */
 
+/* ---- inner functions N(K) (App. B; eq. gt) ---- */
+#define COMMET_INNER_MICNN 0        /* eq. icnn (default; the fields W .. activation) */
+#define COMMET_INNER_CANN 1         /* eq. cann-def (the cann_* fields) */
+#define COMMET_INNER_GENT_THOMAS 2  /* eq. gt, 0.5 (K0 - 3) + log(K1 / 3) + (K2 - 1)^2 on COMMET_KIN_RAW
+                                       without fibres; no parameters */
+/* CANN term menus of eq. cann-fs: f0 (applied to K_m), f1 = x^p, f2 (with weight w1) */
+#define COMMET_CANN_F0_ID 0       /* x */
+#define COMMET_CANN_F0_MACAULAY 1 /* <x> = max(x, 0) */
+#define COMMET_CANN_F0_ABS 2      /* |x| */
+#define COMMET_CANN_F2_LINEAR 0   /* w1 y */
+#define COMMET_CANN_F2_EXP 1      /* exp(w1 y) - 1 */
+#define COMMET_CANN_F2_LOG 2      /* -ln(1 - w1 y); points with w1 y >= 1 are reported */
+#define COMMET_CANN_MAX_TERMS 8
+
 typedef struct commet_model commet_model;
 typedef struct commet_mesh commet_mesh;
 
@@ -76,7 +90,7 @@ typedef struct commet_model_desc {
     int32_t n_fibres;     /* structural vectors, 0..2 (must be 0 for ISO_SHIFTED) */
     const double *fibres; /* [n_fibres][3] reference vectors A^i */
     int32_t d;            /* network inputs; must equal the kinematic layer's count */
-    int32_t W;            /* hidden width; built: 16, 32, 64 */
+    int32_t W;            /* hidden width; built: 16, 32, 64, and 4, 8 without fibres (BF16: 32, 64) */
     int32_t L;            /* hidden layers, >= 1 */
     const double *W1;     /* [W][d] */
     const double *A;      /* [L-1][W][W] (may be NULL when L == 1) */
@@ -87,13 +101,22 @@ typedef struct commet_model_desc {
     int32_t activation;   /* COMMET_ACT_SOFTPLUS */
     double kappa;         /* volumetric penalty; 0 = none */
     int32_t stress_free;  /* 0 or 1 */
+    /* inner function; a zero-initialised tail selects the MICNN above */
+    int32_t inner;            /* COMMET_INNER_* */
+    int32_t cann_terms;       /* CANN: terms n per input, 1..COMMET_CANN_MAX_TERMS */
+    const int32_t *cann_kind; /* CANN: [n][3] per term (f0, p in 1..3, f2), shared by the inputs */
+    const double *cann_w;     /* CANN: [d][n][2] per input m and term k: (w1, w2) of
+                                 N = sum_m sum_k w2 f2(f1(f0(K_m)); w1)  (eq. cann-def) */
 } commet_model_desc;
 
 /*
  * Create a model handle for one precision. Copies the weights to the current CUDA
  * device in the layouts the kernels use. Synchronous. *out is set on success only.
- * Errors: INVALID_ARG (NULL, d inconsistent with the kinematics, negative sizes),
- * UNSUPPORTED (W or n_fibres not built, activation unknown), CUDA.
+ * Errors: INVALID_ARG (NULL, d inconsistent with the kinematics, negative sizes,
+ * bad CANN kinds), UNSUPPORTED (W or n_fibres not built, activation unknown, a CANN or
+ * Gent-Thomas model in COMMET_BF16_MLP), CUDA. CANN and Gent-Thomas models serve the
+ * constitutive updates (both forms) and the element integrals; the backward and the
+ * fused Newton assembly return UNSUPPORTED for them.
  */
 int commet_model_create(const commet_model_desc *desc, int32_t precision, commet_model **out);
 int commet_model_destroy(commet_model *m);
@@ -189,6 +212,47 @@ int commet_elem_assemble_spatial(const commet_mesh *mesh, int32_t precision, con
  */
 int commet_newton_assemble(const commet_model *m, const commet_mesh *mesh, const void *u, void *r, void *K_vals,
                            int32_t *status, void *stream);
+
+/*
+ * ---- The Newton step after assembly (Sec. 4.3: CG with a Jacobi preconditioner) ----
+ * These calls act on a mesh built with want_csr. Each mesh holds one small FP64
+ * reduction array that the solver calls below share: calls on one mesh must not overlap
+ * on the GPU (use one stream per mesh). Dofs are numbered 3 node + i (the CSR rows).
+ */
+/* Fixed (Dirichlet) dofs: a strictly increasing HOST list of n_fixed dofs, copied; 0
+ * clears them. Synchronous. Errors: INVALID_ARG (out of range, not increasing). */
+int commet_mesh_set_dirichlet(commet_mesh *mesh, int64_t n_fixed, const int64_t *dofs);
+/* u[i][node] = values[j] for fixed dof j = 3 node + i; u [3][n_nodes] on the device,
+ * values a HOST double array [n_fixed] read before the call returns. */
+int commet_set_dirichlet_values(const commet_mesh *mesh, int32_t precision, const double *values, void *u,
+                                void *stream);
+/* Dirichlet conditions on the system K du = r of the update u <- u - du: rows and columns
+ * of the fixed dofs in K_vals zeroed with 1 on their diagonal (the matrix stays symmetric).
+ * delta NULL: r of the fixed dofs zeroed, so they keep their values (r or K_vals may be NULL).
+ * delta a HOST double array [n_fixed] (prescribed increments, in the order of the fixed
+ * dofs, read before the call returns): r_c = -delta_c and every free row adds the coupling
+ * it loses, r_f += K_fc delta_c, so the update moves the fixed dofs by delta (the predictor
+ * of a load step); r and K_vals are then required. Errors: NO_CSR, INVALID_ARG. */
+int commet_apply_dirichlet(const commet_mesh *mesh, int32_t precision, void *r, void *K_vals, const double *delta,
+                           void *stream);
+/*
+ * x = K^{-1} b by conjugate gradients (Hestenes-Stiefel) preconditioned by the inverse
+ * diagonal of K, from x = 0, until |b - K x| <= rtol |b| (recursively updated residual)
+ * or max_iter iterations. K_vals [nnz] (symmetric positive definite, e.g. after
+ * commet_apply_dirichlet), b, x [3 n_nodes] in the precision; dot products in FP64.
+ * workspace: device scratch of commet_cg_workspace() bytes, 256-byte aligned.
+ * Synchronous: returns after the solve with *iters and *rel_res (HOST, may be NULL); a
+ * breakdown (p.Kp = 0) ends the solve with a NaN rel_res. Deterministic for a device.
+ */
+size_t commet_cg_workspace(const commet_mesh *mesh, int32_t precision);
+int commet_cg_solve(const commet_mesh *mesh, int32_t precision, const void *K_vals, const void *b, void *x,
+                    double rtol, int32_t max_iter, void *workspace, size_t ws_bytes, int32_t *iters, double *rel_res,
+                    void *stream);
+/* u[i][node] += alpha du[3 node + i]: a dof-ordered increment into the [3][n_nodes] field. */
+int commet_add_increment(const commet_mesh *mesh, int32_t precision, const void *du, double alpha, void *u,
+                         void *stream);
+/* *out (HOST) = |x|_2 of a device vector of n entries, summed in FP64 in a fixed order. */
+int commet_norm2(const commet_mesh *mesh, int32_t precision, int64_t n, const void *x, double *out, void *stream);
 
 /*
  * Backward of the constitutive update for an upstream gradient G = dL/dP [9][n_qp]:

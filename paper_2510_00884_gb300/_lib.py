@@ -22,6 +22,8 @@ EXPORTED = [
     "commet_mesh_create", "commet_mesh_destroy", "commet_mesh_info", "commet_mesh_csr", "commet_compute_F",
     "commet_elem_assemble", "commet_newton_assemble", "commet_const_backward_workspace",
     "commet_const_backward", "commet_target_stress", "commet_status_string", "commet_const_backward_noalloc",
+    "commet_mesh_set_dirichlet", "commet_set_dirichlet_values", "commet_apply_dirichlet", "commet_cg_workspace",
+    "commet_cg_solve", "commet_add_increment", "commet_norm2",
 ]
 
 
@@ -31,7 +33,10 @@ class ModelDesc(C.Structure):
                 ("W1", C.POINTER(C.c_double)), ("A", C.POINTER(C.c_double)), ("B", C.POINTER(C.c_double)),
                 ("c", C.POINTER(C.c_double)), ("a_out", C.POINTER(C.c_double)),
                 ("b_out", C.POINTER(C.c_double)), ("activation", C.c_int32), ("kappa", C.c_double),
-                ("stress_free", C.c_int32)]
+                ("stress_free", C.c_int32), ("inner", C.c_int32), ("cann_terms", C.c_int32),
+                ("cann_kind", C.POINTER(C.c_int32)), ("cann_w", C.POINTER(C.c_double))]
+
+INNER_MICNN, INNER_CANN, INNER_GENT_THOMAS = 0, 1, 2
 
 
 class CommetError(RuntimeError):
@@ -74,6 +79,14 @@ def load() -> C.CDLL:
                                   C.c_double, C.c_double, vp, vp], C.c_int),
         "commet_status_string": ([C.c_int], C.c_char_p),
         "commet_const_backward_noalloc": ([vp, i64, vp, vp, vp, vp, vp], C.c_int),
+        "commet_mesh_set_dirichlet": ([vp, i64, C.POINTER(i64)], C.c_int),
+        "commet_set_dirichlet_values": ([vp, i32, C.POINTER(C.c_double), vp, vp], C.c_int),
+        "commet_apply_dirichlet": ([vp, i32, vp, vp, C.POINTER(C.c_double), vp], C.c_int),
+        "commet_cg_workspace": ([vp, i32], C.c_size_t),
+        "commet_cg_solve": ([vp, i32, vp, vp, vp, C.c_double, i32, vp, C.c_size_t, C.POINTER(i32),
+                             C.POINTER(C.c_double), vp], C.c_int),
+        "commet_add_increment": ([vp, i32, vp, C.c_double, vp, vp], C.c_int),
+        "commet_norm2": ([vp, i32, i64, vp, C.POINTER(C.c_double), vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

@@ -39,19 +39,45 @@ def _check_dev(t, dtype, shape=None, name="tensor"):
 
 
 class Model:
-    """A MICNN strain energy on the GPU (one precision per handle).
+    """A strain energy on the GPU (one precision per handle).
 
-    ``spec`` is any object with the attributes d, W, L, kin, fibres, W1, Ak, Bk, c, a, b,
-    kappa and stress_free (row-major float64 arrays, see workload.ModelSpec).
+    ``spec`` is any object with the attributes d, kin, fibres, kappa and stress_free and,
+    by its ``inner_name`` (default "micnn"):
+      micnn        W, L, W1, Ak, Bk, c, a, b (row-major float64 arrays, see workload.ModelSpec)
+      cann         n, kinds[n][3], w[d][n][2] (see workload.CannSpec)
+      gent_thomas  nothing more (eq. gt on raw kinematics)
     """
 
     def __init__(self, spec, precision: str = "f64"):
         lib = _lib.load()
         self.precision = precision
         self.dtype = _DTYPE[precision]
-        self.d, self.W, self.L = int(spec.d), int(spec.W), int(spec.L)
         self._keep = []
         fib, pfib = _dbl(np.asarray(spec.fibres).reshape(-1, 3) if len(spec.fibres) else np.zeros((1, 3)))
+        inner = getattr(spec, "inner_name", "micnn")
+        if inner != "micnn":
+            self.d, self.W, self.L = int(spec.d), 0, 0
+            desc = _lib.ModelDesc(kinematics=int(spec.kin), n_fibres=int(len(spec.fibres)), fibres=pfib,
+                                  d=self.d, kappa=float(spec.kappa), stress_free=int(bool(spec.stress_free)))
+            if inner == "cann":
+                kinds = np.ascontiguousarray(spec.kinds, dtype=np.int32)
+                w, pw = _dbl(spec.w)
+                self._keep += [kinds, w]
+                desc.inner = _lib.INNER_CANN
+                desc.cann_terms = int(spec.n)
+                desc.cann_kind = kinds.ctypes.data_as(C.POINTER(C.c_int32))
+                desc.cann_w = pw
+            elif inner == "gent_thomas":
+                desc.inner = _lib.INNER_GENT_THOMAS
+            else:
+                raise ValueError(f"unknown inner function {inner!r}")
+            self._keep.append(fib)
+            h = C.c_void_p()
+            _lib.check("commet_model_create", lib.commet_model_create(C.byref(desc), _PREC[precision], C.byref(h)))
+            self.handle = h
+            self.n_params = int(lib.commet_model_n_params(h))
+            return
+        self.d, self.W, self.L = int(spec.d), int(spec.W), int(spec.L)
         W1, pW1 = _dbl(spec.W1)
         Ak, pA = _dbl(spec.Ak if self.L > 1 else np.zeros(1))
         Bk, pB = _dbl(spec.Bk if self.L > 1 else np.zeros(1))
@@ -214,6 +240,104 @@ class Mesh:
             self.handle, _PREC[precision], _ptr(F), _ptr(tau), _ptr(c), _ptr(f_e), _ptr(K_e), _ptr(r), _ptr(Kv),
             _stream()))
         return f_e, K_e, r, Kv
+
+
+    # ---- the Newton step after assembly (Sec. 4.3)
+    def set_dirichlet(self, dofs):
+        """Fixed dofs (3 node + i), a strictly increasing integer list; empty clears them."""
+        d = np.ascontiguousarray(np.asarray(dofs, dtype=np.int64))
+        self.n_fixed = int(d.size)
+        _lib.check("commet_mesh_set_dirichlet", _lib.load().commet_mesh_set_dirichlet(
+            self.handle, d.size, d.ctypes.data_as(C.POINTER(C.c_int64)) if d.size else None))
+
+    def set_dirichlet_values(self, values, u: torch.Tensor, precision: str = "f64"):
+        """u[:, node] <- the prescribed values of the fixed dofs (host array in dof order)."""
+        _check_dev(u, _DTYPE[precision], shape=(3, self.n_nodes), name="u")
+        v = np.ascontiguousarray(np.asarray(values, dtype=np.float64))
+        if v.size != getattr(self, "n_fixed", 0):
+            raise ValueError("one value per fixed dof is required")
+        _lib.check("commet_set_dirichlet_values", _lib.load().commet_set_dirichlet_values(
+            self.handle, _PREC[precision], v.ctypes.data_as(C.POINTER(C.c_double)), _ptr(u), _stream()))
+
+    def apply_dirichlet(self, r: torch.Tensor | None, K_vals: torch.Tensor | None, precision: str = "f64",
+                        delta=None):
+        """Dirichlet rows and columns; ``delta`` (host, one value per fixed dof) makes the next
+        update u <- u - du move the fixed dofs by delta."""
+        d = None if delta is None else np.ascontiguousarray(np.asarray(delta, dtype=np.float64))
+        if d is not None and d.size != getattr(self, "n_fixed", 0):
+            raise ValueError("one increment per fixed dof is required")
+        _lib.check("commet_apply_dirichlet", _lib.load().commet_apply_dirichlet(
+            self.handle, _PREC[precision], _ptr(r), _ptr(K_vals),
+            d.ctypes.data_as(C.POINTER(C.c_double)) if d is not None else None, _stream()))
+
+    def cg_solve(self, K_vals: torch.Tensor, b: torch.Tensor, precision: str = "f64", rtol: float = 1e-10,
+                 max_iter: int = 10000, x=None, workspace=None):
+        """Jacobi-preconditioned CG: (x, iterations, |b - K x| / |b|)."""
+        lib = _lib.load()
+        dt = _DTYPE[precision]
+        _check_dev(K_vals, dt, shape=(self.nnz,), name="K_vals")
+        _check_dev(b, dt, shape=(3 * self.n_nodes,), name="b")
+        x = torch.empty_like(b) if x is None else x
+        nb = int(lib.commet_cg_workspace(self.handle, _PREC[precision]))
+        if workspace is None or workspace.numel() < nb:
+            workspace = torch.empty(max(nb, 1), dtype=torch.uint8, device=b.device)
+        it, res = C.c_int32(0), C.c_double(0.0)
+        _lib.check("commet_cg_solve", lib.commet_cg_solve(
+            self.handle, _PREC[precision], _ptr(K_vals), _ptr(b), _ptr(x), float(rtol), int(max_iter),
+            _ptr(workspace), nb, C.byref(it), C.byref(res), _stream()))
+        return x, int(it.value), float(res.value)
+
+    def add_increment(self, du: torch.Tensor, alpha: float, u: torch.Tensor, precision: str = "f64"):
+        _lib.check("commet_add_increment", _lib.load().commet_add_increment(
+            self.handle, _PREC[precision], _ptr(du), float(alpha), _ptr(u), _stream()))
+
+    def norm2(self, x: torch.Tensor, precision: str = "f64") -> float:
+        out = C.c_double(0.0)
+        _lib.check("commet_norm2", _lib.load().commet_norm2(
+            self.handle, _PREC[precision], x.numel(), _ptr(x), C.byref(out), _stream()))
+        return float(out.value)
+
+
+def newton_solve(model: Model, mesh: Mesh, u: torch.Tensor, steps, tol: float = 1e-10, max_newton: int = 25,
+                 cg_rtol: float = 1e-10, cg_max_iter: int = 20000):
+    """Load-stepped Newton-Raphson on the GPU (the solve of Sec. 4.3). ``steps`` is a list of
+    (fixed dofs, prescribed values) per load step, the same dofs in every step. Each iteration
+    assembles r and K (fused kernel), applies the Dirichlet rows and columns, solves K du = r
+    by Jacobi-CG and updates u <- u - du. The first iteration of a step is the predictor: it
+    moves the fixed dofs by their prescribed increment through the system (apply_dirichlet
+    with delta), after which they are set to their values exactly; the step ends when
+    |r_free| <= tol max(1, |r_free| after the predictor). u [3][n_nodes], updated in place,
+    must hold the first step's starting state (fixed dofs included). Returns per step the
+    list of (|r_free|, CG iterations of the solve that followed)."""
+    prec = model.precision
+    hist = []
+    r = Kv = du = ws = None
+    prev = None
+    for dofs, vals in steps:
+        vals = np.asarray(vals, dtype=np.float64)
+        if prev is None:
+            mesh.set_dirichlet(dofs)
+            prev = np.zeros_like(vals)
+        h = []
+        for it in range(max_newton):
+            r, Kv = newton_assemble(model, mesh, u, out=None if r is None else (r, Kv))
+            if it == 0:
+                mesh.apply_dirichlet(r, Kv, prec, delta=vals - prev)
+            else:
+                mesh.apply_dirichlet(r, Kv, prec)
+                rn = mesh.norm2(r, prec)
+                if rn <= tol * max(1.0, h[0][0] if h else rn):
+                    h.append((rn, 0))
+                    break
+            du, n_cg, _ = mesh.cg_solve(Kv, r, prec, cg_rtol, cg_max_iter, x=du, workspace=ws)
+            mesh.add_increment(du, -1.0, u, prec)
+            if it == 0:
+                mesh.set_dirichlet_values(vals, u, prec)
+            else:
+                h.append((rn, n_cg))
+        prev = vals
+        hist.append(h)
+    return hist
 
 
 def newton_assemble(model: Model, mesh: Mesh, u: torch.Tensor, status: bool = False, out=None):

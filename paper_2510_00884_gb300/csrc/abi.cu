@@ -32,7 +32,6 @@ NetLayout make_layout(int d, int W, int L, bool with_tab) {
     l.W1t = o; o = round4(o + d * W);
     l.W1r = o; o = round4(o + W * dp);
     l.At = o; o = round4(o + (L - 1) * W * W);
-    l.Ar = o; o = round4(o + (L - 1) * W * W);
     l.Bt = o; o = round4(o + (L - 1) * d * W);
     l.c = o; o = round4(o + L * W);
     l.a = o; o = round4(o + W);
@@ -44,6 +43,9 @@ NetLayout make_layout(int d, int W, int L, bool with_tab) {
         l.tab = o;
         o = round4(o + kActTab);
     }
+    // the reverse pass's row-major copy of A_k comes last: networks whose block does not
+    // fit in shared memory beside the point slabs read it from global memory (L1) instead
+    l.Ar = o; o = round4(o + (L - 1) * W * W);
     l.total = o;
     return l;
 }
@@ -56,6 +58,119 @@ int upload(const std::vector<double> &h, void **dptr) {
     for (size_t i = 0; i < h.size(); ++i) t[i] = (T)h[i];
     COMMET_CUDA_TRY(cudaMalloc(dptr, bytes));
     COMMET_CUDA_TRY(cudaMemcpy(*dptr, buf.data(), bytes, cudaMemcpyHostToDevice));
+    return COMMET_OK;
+}
+
+// n0 = dN/dK and K0 = K at F = I for the stress-free shift, evaluated by the
+// constitutive kernel itself and written into the model's packed block.
+int stress_free_shift(commet_model *m) {
+    const int precision = m->precision, d = m->d;
+    const NetLayout &l = m->lay;
+    int rc;
+    if (!m->kp.stress_free) return COMMET_OK;
+    {
+        // n0 = dN/dK and K0 = K at F = I, evaluated by the constitutive kernel itself
+        const size_t es = elem_size(precision == COMMET_F64 ? COMMET_F64 : COMMET_F32);
+        void *dF = nullptr, *dP = nullptr, *dN = nullptr;
+        const double I9[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+        unsigned char Fbuf[9 * sizeof(double)];
+        for (int c = 0; c < 9; ++c) {
+            if (es == 8)
+                reinterpret_cast<double *>(Fbuf)[c] = I9[c];
+            else
+                reinterpret_cast<float *>(Fbuf)[c] = (float)I9[c];
+        }
+        commet_model tmp = *m;
+        tmp.precision = (precision == COMMET_F64) ? COMMET_F64 : COMMET_F32;
+        rc = COMMET_ERR_CUDA;
+        if (cudaMalloc(&dF, 16 * es) == cudaSuccess && cudaMalloc(&dP, 16 * es) == cudaSuccess &&
+            cudaMalloc(&dN, 2 * kMaxD * es) == cudaSuccess &&
+            cudaMemcpy(dF, Fbuf, 9 * es, cudaMemcpyHostToDevice) == cudaSuccess) {
+            rc = launch_const_update(&tmp, 1, dF, nullptr, dP, nullptr, nullptr, 0, dN);
+            if (rc == COMMET_OK && cudaDeviceSynchronize() != cudaSuccess) rc = COMMET_ERR_CUDA;
+            if (rc == COMMET_OK) {
+                unsigned char *wb = reinterpret_cast<unsigned char *>(m->d_weights);
+                if (cudaMemcpy(wb + l.n0 * es, dN, d * es, cudaMemcpyDeviceToDevice) != cudaSuccess ||
+                    cudaMemcpy(wb + l.K0 * es, (unsigned char *)dN + d * es, d * es, cudaMemcpyDeviceToDevice) !=
+                        cudaSuccess)
+                    rc = COMMET_ERR_CUDA;
+            }
+        }
+        cudaFree(dF);
+        cudaFree(dP);
+        cudaFree(dN);
+    }
+    return rc;
+}
+
+// CANN (eq. cann-def) and Gent-Thomas (eq. gt) models: no network; the packed block holds
+// the CANN weights [d][n][2], its kinds [n][3] (as numbers) and n0, K0.
+int create_closed_form(const commet_model_desc *desc, int32_t precision, commet_model **out) {
+    const int inner = desc->inner;
+    if (desc->kinematics != COMMET_KIN_ISO_SHIFTED && desc->kinematics != COMMET_KIN_RAW &&
+        desc->kinematics != COMMET_KIN_POLYCONVEX)
+        return COMMET_ERR_INVALID_ARG;
+    if (desc->n_fibres < 0 || desc->d < 1) return COMMET_ERR_INVALID_ARG;
+    if (desc->kinematics != COMMET_KIN_RAW && desc->n_fibres != 0) return COMMET_ERR_INVALID_ARG;
+    if (desc->n_fibres > kMaxFibres) return COMMET_ERR_UNSUPPORTED;
+    if (desc->n_fibres > 0 && desc->fibres == nullptr) return COMMET_ERR_INVALID_ARG;
+    const int d = desc->d;
+    if (d != (desc->kinematics == COMMET_KIN_RAW ? 3 + 2 * desc->n_fibres : 3)) return COMMET_ERR_INVALID_ARG;
+    if (!std::isfinite(desc->kappa)) return COMMET_ERR_INVALID_ARG;
+    int n = 0;
+    if (inner == COMMET_INNER_CANN) {
+        n = desc->cann_terms;
+        if (n < 1 || n > COMMET_CANN_MAX_TERMS || desc->cann_kind == nullptr || desc->cann_w == nullptr)
+            return COMMET_ERR_INVALID_ARG;
+        for (int k = 0; k < n; ++k) {
+            const int f0 = desc->cann_kind[3 * k], p = desc->cann_kind[3 * k + 1], f2 = desc->cann_kind[3 * k + 2];
+            if (f0 < COMMET_CANN_F0_ID || f0 > COMMET_CANN_F0_ABS || p < 1 || p > 3 || f2 < COMMET_CANN_F2_LINEAR ||
+                f2 > COMMET_CANN_F2_LOG)
+                return COMMET_ERR_INVALID_ARG;
+        }
+        for (int i = 0; i < 2 * d * n; ++i)
+            if (!std::isfinite(desc->cann_w[i])) return COMMET_ERR_INVALID_ARG;
+    } else if (desc->kinematics != COMMET_KIN_RAW || desc->n_fibres != 0) {
+        return COMMET_ERR_INVALID_ARG;  // eq. gt is written on raw (Ibar1, Ibar2, J)
+    }
+    if (precision == COMMET_BF16_MLP) return COMMET_ERR_UNSUPPORTED;
+
+    commet_model *m = new (std::nothrow) commet_model();
+    if (!m) return COMMET_ERR_CUDA;
+    m->precision = precision;
+    m->inner = inner;
+    m->d = d;
+    m->W = 0;
+    m->L = 0;
+    m->kp.kin = desc->kinematics;
+    m->kp.nf = desc->n_fibres;
+    for (int f = 0; f < desc->n_fibres; ++f)
+        for (int c = 0; c < 3; ++c) m->kp.fib[f][c] = desc->fibres[3 * f + c];
+    m->kp.kappa = desc->kappa;
+    m->kp.stress_free = desc->stress_free ? 1 : 0;
+    NetLayout l{};
+    l.d = d;
+    l.inner = inner;
+    l.cn = n;
+    int o = 0;
+    l.cw = o; o = round4(o + 2 * d * n);
+    l.ck = o; o = round4(o + 3 * n);
+    l.n0 = o; o = round4(o + d);
+    l.K0 = o; o = round4(o + d);
+    l.total = o;
+    m->lay = l;
+    m->n_params = (int64_t)2 * d * n;
+    cudaGetDevice(&m->device);
+    std::vector<double> h(l.total, 0.0);
+    for (int i = 0; i < 2 * d * n; ++i) h[l.cw + i] = desc->cann_w[i];
+    for (int i = 0; i < 3 * n; ++i) h[l.ck + i] = (double)desc->cann_kind[i];
+    int rc = (precision == COMMET_F64) ? upload<double>(h, &m->d_weights) : upload<float>(h, &m->d_weights);
+    if (rc == COMMET_OK) rc = stress_free_shift(m);
+    if (rc != COMMET_OK) {
+        commet_model_destroy(m);
+        return rc;
+    }
+    *out = m;
     return COMMET_OK;
 }
 
@@ -78,6 +193,10 @@ int commet_model_create(const commet_model_desc *desc, int32_t precision, commet
     if (desc == nullptr || out == nullptr) return COMMET_ERR_INVALID_ARG;
     if (precision != COMMET_F64 && precision != COMMET_F32 && precision != COMMET_BF16_MLP)
         return COMMET_ERR_INVALID_ARG;
+    const int inner = desc->inner;
+    if (inner != COMMET_INNER_MICNN && inner != COMMET_INNER_CANN && inner != COMMET_INNER_GENT_THOMAS)
+        return COMMET_ERR_INVALID_ARG;
+    if (inner != COMMET_INNER_MICNN) return create_closed_form(desc, precision, out);
     if (desc->kinematics != COMMET_KIN_ISO_SHIFTED && desc->kinematics != COMMET_KIN_RAW &&
         desc->kinematics != COMMET_KIN_POLYCONVEX)
         return COMMET_ERR_INVALID_ARG;
@@ -92,7 +211,8 @@ int commet_model_create(const commet_model_desc *desc, int32_t precision, commet
     if (desc->n_fibres > 0 && desc->fibres == nullptr) return COMMET_ERR_INVALID_ARG;
     if (!(std::isfinite(desc->kappa))) return COMMET_ERR_INVALID_ARG;
     const int W = desc->W, d = desc->d, L = desc->L;
-    if (W != 16 && W != 32 && W != 64) return COMMET_ERR_UNSUPPORTED;
+    if (W != 4 && W != 8 && W != 16 && W != 32 && W != 64) return COMMET_ERR_UNSUPPORTED;
+    if (W < 16 && desc->n_fibres != 0) return COMMET_ERR_UNSUPPORTED;  // narrow networks: d = 3 only
     if (L > 16) return COMMET_ERR_UNSUPPORTED;
 
     commet_model *m = new (std::nothrow) commet_model();
@@ -108,6 +228,7 @@ int commet_model_create(const commet_model_desc *desc, int32_t precision, commet
     m->kp.kappa = desc->kappa;
     m->kp.stress_free = desc->stress_free ? 1 : 0;
     m->lay = make_layout(d, W, L, precision == COMMET_F64);
+    m->lay.inner = COMMET_INNER_MICNN;
     m->n_params = (int64_t)W * d + W + (int64_t)(L - 1) * ((int64_t)W * W + (int64_t)W * d + W) + W + d;
     cudaGetDevice(&m->device);
 
@@ -162,41 +283,10 @@ int commet_model_create(const commet_model_desc *desc, int32_t precision, commet
         commet_model_destroy(m);
         return rc;
     }
-    if (m->kp.stress_free) {
-        // n0 = dN/dK and K0 = K at F = I, evaluated by the constitutive kernel itself
-        const size_t es = elem_size(precision == COMMET_F64 ? COMMET_F64 : COMMET_F32);
-        void *dF = nullptr, *dP = nullptr, *dN = nullptr;
-        const double I9[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
-        unsigned char Fbuf[9 * sizeof(double)];
-        for (int c = 0; c < 9; ++c) {
-            if (es == 8)
-                reinterpret_cast<double *>(Fbuf)[c] = I9[c];
-            else
-                reinterpret_cast<float *>(Fbuf)[c] = (float)I9[c];
-        }
-        commet_model tmp = *m;
-        tmp.precision = (precision == COMMET_F64) ? COMMET_F64 : COMMET_F32;
-        rc = COMMET_ERR_CUDA;
-        if (cudaMalloc(&dF, 16 * es) == cudaSuccess && cudaMalloc(&dP, 16 * es) == cudaSuccess &&
-            cudaMalloc(&dN, 2 * kMaxD * es) == cudaSuccess &&
-            cudaMemcpy(dF, Fbuf, 9 * es, cudaMemcpyHostToDevice) == cudaSuccess) {
-            rc = launch_const_update(&tmp, 1, dF, nullptr, dP, nullptr, nullptr, 0, dN);
-            if (rc == COMMET_OK && cudaDeviceSynchronize() != cudaSuccess) rc = COMMET_ERR_CUDA;
-            if (rc == COMMET_OK) {
-                unsigned char *wb = reinterpret_cast<unsigned char *>(m->d_weights);
-                if (cudaMemcpy(wb + l.n0 * es, dN, d * es, cudaMemcpyDeviceToDevice) != cudaSuccess ||
-                    cudaMemcpy(wb + l.K0 * es, (unsigned char *)dN + d * es, d * es, cudaMemcpyDeviceToDevice) !=
-                        cudaSuccess)
-                    rc = COMMET_ERR_CUDA;
-            }
-        }
-        cudaFree(dF);
-        cudaFree(dP);
-        cudaFree(dN);
-        if (rc != COMMET_OK) {
-            commet_model_destroy(m);
-            return rc;
-        }
+    rc = stress_free_shift(m);
+    if (rc != COMMET_OK) {
+        commet_model_destroy(m);
+        return rc;
     }
     if (precision == COMMET_BF16_MLP) {
         rc = prepare_bf16_weights(m);
@@ -289,6 +379,7 @@ int commet_mesh_create(int64_t n_nodes, const double *X, int64_t n_el, const int
         cudaMemcpy(mesh->d_conn, conn, sizeof(int32_t) * 8 * n_el, cudaMemcpyHostToDevice) != cudaSuccess)
         rc = COMMET_ERR_CUDA;
     if (rc == COMMET_OK && want_csr) rc = build_csr_and_colouring(n_nodes, n_el, conn, mesh);
+    if (rc == COMMET_OK && cudaMalloc(&mesh->d_red, sizeof(double) * kRedDoubles) != cudaSuccess) rc = COMMET_ERR_CUDA;
     if (rc != COMMET_OK) {
         commet_mesh_destroy(mesh);
         return rc;
@@ -307,10 +398,109 @@ int commet_mesh_destroy(commet_mesh *mesh) {
     cudaFree(mesh->d_emap);
     cudaFree(mesh->d_rowlen);
     cudaFree(mesh->d_colour_el);
+    cudaFree(mesh->d_fixed);
+    cudaFree(mesh->d_fixed_dofs);
+    cudaFree(mesh->d_fixed_vals);
+    cudaFree(mesh->d_delta);
+    cudaFree(mesh->d_red);
     delete[] mesh->h_rowptr;
     delete[] mesh->h_col;
     delete mesh;
     return COMMET_OK;
+}
+
+int commet_mesh_set_dirichlet(commet_mesh *mesh, int64_t n_fixed, const int64_t *dofs) {
+    if (mesh == nullptr || n_fixed < 0 || (n_fixed > 0 && dofs == nullptr)) return COMMET_ERR_INVALID_ARG;
+    const int64_t n = 3 * mesh->n_nodes;
+    for (int64_t i = 0; i < n_fixed; ++i)
+        if (dofs[i] < 0 || dofs[i] >= n || (i > 0 && dofs[i] <= dofs[i - 1])) return COMMET_ERR_INVALID_ARG;
+    cudaFree(mesh->d_fixed);
+    cudaFree(mesh->d_fixed_dofs);
+    cudaFree(mesh->d_fixed_vals);
+    cudaFree(mesh->d_delta);
+    mesh->d_fixed = nullptr;
+    mesh->d_fixed_dofs = nullptr;
+    mesh->d_fixed_vals = nullptr;
+    mesh->d_delta = nullptr;
+    mesh->n_fixed = 0;
+    if (n_fixed == 0) return COMMET_OK;
+    std::vector<uint8_t> mask(n, 0);
+    for (int64_t i = 0; i < n_fixed; ++i) mask[dofs[i]] = 1;
+    COMMET_CUDA_TRY(cudaMalloc(&mesh->d_fixed, n));
+    COMMET_CUDA_TRY(cudaMalloc(&mesh->d_fixed_dofs, sizeof(int64_t) * n_fixed));
+    COMMET_CUDA_TRY(cudaMalloc(&mesh->d_fixed_vals, sizeof(double) * n_fixed));
+    COMMET_CUDA_TRY(cudaMalloc(&mesh->d_delta, sizeof(double) * n));
+    COMMET_CUDA_TRY(cudaMemcpy(mesh->d_fixed, mask.data(), n, cudaMemcpyHostToDevice));
+    COMMET_CUDA_TRY(cudaMemcpy(mesh->d_fixed_dofs, dofs, sizeof(int64_t) * n_fixed, cudaMemcpyHostToDevice));
+    mesh->n_fixed = n_fixed;
+    return COMMET_OK;
+}
+
+int commet_set_dirichlet_values(const commet_mesh *mesh, int32_t precision, const double *values, void *u,
+                                void *stream) {
+    if (mesh == nullptr || (precision != COMMET_F64 && precision != COMMET_F32)) return COMMET_ERR_INVALID_ARG;
+    if (mesh->n_fixed > 0 && (values == nullptr || u == nullptr)) return COMMET_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < mesh->n_fixed; ++i)
+        if (!std::isfinite(values[i])) return COMMET_ERR_INVALID_ARG;
+    if (!aligned16(u)) return COMMET_ERR_INVALID_ARG;
+    return launch_set_dirichlet_values(mesh, precision, values, u, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int commet_apply_dirichlet(const commet_mesh *mesh, int32_t precision, void *r, void *K_vals, const double *delta,
+                           void *stream) {
+    if (mesh == nullptr || (precision != COMMET_F64 && precision != COMMET_F32)) return COMMET_ERR_INVALID_ARG;
+    if (mesh->h_rowptr == nullptr) return COMMET_ERR_NO_CSR;
+    if (!aligned16(r) || !aligned16(K_vals)) return COMMET_ERR_INVALID_ARG;
+    if (delta != nullptr) {
+        if (r == nullptr || K_vals == nullptr) return COMMET_ERR_INVALID_ARG;
+        for (int64_t i = 0; i < mesh->n_fixed; ++i)
+            if (!std::isfinite(delta[i])) return COMMET_ERR_INVALID_ARG;
+    }
+    return launch_apply_dirichlet(mesh, precision, r, K_vals, delta, reinterpret_cast<cudaStream_t>(stream));
+}
+
+size_t commet_cg_workspace(const commet_mesh *mesh, int32_t precision) {
+    if (mesh == nullptr || (precision != COMMET_F64 && precision != COMMET_F32)) return 0;
+    return cg_workspace_bytes(mesh, precision);
+}
+
+int commet_cg_solve(const commet_mesh *mesh, int32_t precision, const void *K_vals, const void *b, void *x,
+                    double rtol, int32_t max_iter, void *workspace, size_t ws_bytes, int32_t *iters, double *rel_res,
+                    void *stream) {
+    if (mesh == nullptr || (precision != COMMET_F64 && precision != COMMET_F32)) return COMMET_ERR_INVALID_ARG;
+    if (mesh->h_rowptr == nullptr) return COMMET_ERR_NO_CSR;
+    if (!(rtol >= 0.0) || max_iter < 1) return COMMET_ERR_INVALID_ARG;
+    if (mesh->n_rows > 0 && (K_vals == nullptr || b == nullptr || x == nullptr || workspace == nullptr))
+        return COMMET_ERR_INVALID_ARG;
+    if (ws_bytes < cg_workspace_bytes(mesh, precision)) return COMMET_ERR_INVALID_ARG;
+    if (!aligned16(K_vals) || !aligned16(b) || !aligned16(x) || (reinterpret_cast<uintptr_t>(workspace) & 255u) != 0)
+        return COMMET_ERR_INVALID_ARG;
+    if (mesh->n_rows == 0) {
+        if (iters) *iters = 0;
+        if (rel_res) *rel_res = 0.0;
+        return COMMET_OK;
+    }
+    return launch_cg_solve(mesh, precision, K_vals, b, x, rtol, max_iter, workspace, iters, rel_res,
+                           reinterpret_cast<cudaStream_t>(stream));
+}
+
+int commet_add_increment(const commet_mesh *mesh, int32_t precision, const void *du, double alpha, void *u,
+                         void *stream) {
+    if (mesh == nullptr || (precision != COMMET_F64 && precision != COMMET_F32)) return COMMET_ERR_INVALID_ARG;
+    if (mesh->n_nodes > 0 && (du == nullptr || u == nullptr)) return COMMET_ERR_INVALID_ARG;
+    if (!std::isfinite(alpha) || !aligned16(du) || !aligned16(u)) return COMMET_ERR_INVALID_ARG;
+    return launch_add_increment(mesh, precision, du, alpha, u, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int commet_norm2(const commet_mesh *mesh, int32_t precision, int64_t n, const void *x, double *out, void *stream) {
+    if (mesh == nullptr || out == nullptr || n < 0 || (precision != COMMET_F64 && precision != COMMET_F32))
+        return COMMET_ERR_INVALID_ARG;
+    if (n > 0 && x == nullptr) return COMMET_ERR_INVALID_ARG;
+    if (n == 0) {
+        *out = 0.0;
+        return COMMET_OK;
+    }
+    return launch_norm2(mesh, precision, n, x, out, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int commet_mesh_info(const commet_mesh *mesh, int64_t *n_rows, int64_t *nnz, int32_t *n_colours) {
@@ -388,6 +578,7 @@ size_t commet_const_backward_workspace(const commet_model *m, int64_t n_qp) {
 int commet_const_backward(const commet_model *m, int64_t n_qp, const void *F, const void *dL_dP, void *dL_dF,
                           void *dL_dtheta, void *workspace, size_t ws_bytes, void *stream) {
     if (m == nullptr || n_qp < 0 || dL_dtheta == nullptr) return COMMET_ERR_INVALID_ARG;
+    if (m->inner != COMMET_INNER_MICNN) return COMMET_ERR_UNSUPPORTED;
     if (n_qp > 0 && (F == nullptr || dL_dP == nullptr)) return COMMET_ERR_INVALID_ARG;
     if (!aligned16(F) || !aligned16(dL_dP) || !aligned16(dL_dF) || !aligned16(dL_dtheta)) return COMMET_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return COMMET_ERR_INVALID_ARG;

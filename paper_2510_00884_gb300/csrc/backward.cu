@@ -433,6 +433,7 @@ static int np_padded(const commet_model *m) { return (int)((m->n_params + 3) / 4
 
 size_t backward_workspace_bytes(const commet_model *m, int64_t n_qp) {
     if (m->precision != COMMET_F64 && m->precision != COMMET_F32) return 0;
+    if (m->inner != COMMET_INNER_MICNN) return 0;
     const size_t es = m->precision == COMMET_F64 ? 8 : 4;
     const int Q = m->precision == COMMET_F64 ? BwConf<double>::Q : BwConf<float>::Q;
     const size_t bytes = (size_t)bw_grid(m, n_qp, Q) * np_padded(m) * es;
@@ -476,6 +477,8 @@ static int bw_dispatch(const commet_model *m, int64_t n_qp, const void *F, const
     const int nf = m->kp.nf, W = m->W;
 #define COMMET_CASE(NF_, W_) \
     if (nf == NF_ && W == W_) return bw_typed<T, NF_, W_>(m, n_qp, F, G, dF, dth, ws, s);
+    COMMET_CASE(0, 4)
+    COMMET_CASE(0, 8)
     COMMET_CASE(0, 16)
     COMMET_CASE(0, 32)
     COMMET_CASE(0, 64)
@@ -491,6 +494,7 @@ static int bw_dispatch(const commet_model *m, int64_t n_qp, const void *F, const
 int launch_const_backward(const commet_model *m, int64_t n_qp, const void *F, const void *G, void *dF, void *dth,
                           void *ws, size_t ws_bytes, cudaStream_t s) {
     (void)ws_bytes;
+    if (m->inner != COMMET_INNER_MICNN) return COMMET_ERR_UNSUPPORTED;
     if (n_qp == 0) {
         const size_t es = m->precision == COMMET_F64 ? 8 : 4;
         return cudaMemsetAsync(dth, 0, es * m->n_params, s) == cudaSuccess ? COMMET_OK : COMMET_ERR_CUDA;

@@ -1,0 +1,254 @@
+// Constitutive update for the inner functions that are not networks: the CANN of
+// eq. cann-def and the closed-form Gent-Thomas energy of eq. gt. The point's inner
+// value, gradient and (diagonal) Hessian are formed by its 4-lane group; everything
+// after that (polyconvex chain rule, kinematic staging, P and A, Psi) is the shared
+// qp_group_finish of the network kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdint>
+
+#include "qp_body.cuh"
+
+namespace commet {
+
+int sm_count();
+
+__device__ __forceinline__ double dev_exp(double x) { return exp(x); }
+__device__ __forceinline__ float dev_exp(float x) { return expf(x); }
+__device__ __forceinline__ double dev_log(double x) { return log(x); }
+__device__ __forceinline__ float dev_log(float x) { return logf(x); }
+
+// One CANN term of eq. cann-def at input value x, with its first and second derivative
+// by the chain rule of eq. cann-chain-rule: v = w2 f2(f1(f0(x))), g = dv/dx, h = d2v/dx2.
+// f0'' = 0 for every f0 of the menu; the second derivative of -ln(1 - w1 y) is
+// +(w1 / (1 - w1 y))^2.
+template <typename T>
+__device__ __forceinline__ void cann_term(T x, int f0, int p, int f2, T w1, T w2, T &v, T &g, T &h) {
+    T a, ad;
+    if (f0 == COMMET_CANN_F0_MACAULAY) {
+        a = x > T(0) ? x : T(0);
+        ad = x > T(0) ? T(1) : (x < T(0) ? T(0) : T(0.5));
+    } else if (f0 == COMMET_CANN_F0_ABS) {
+        a = x < T(0) ? -x : x;
+        ad = x > T(0) ? T(1) : (x < T(0) ? T(-1) : T(0));
+    } else {
+        a = x;
+        ad = T(1);
+    }
+    T y, yd, ydd;
+    if (p == 1) {
+        y = a;
+        yd = T(1);
+        ydd = T(0);
+    } else if (p == 2) {
+        y = a * a;
+        yd = T(2) * a;
+        ydd = T(2);
+    } else {
+        y = a * a * a;
+        yd = T(3) * a * a;
+        ydd = T(6) * a;
+    }
+    T f, fd, fdd;
+    if (f2 == COMMET_CANN_F2_EXP) {
+        const T e = dev_exp(w1 * y);
+        f = e - T(1);
+        fd = w1 * e;
+        fdd = w1 * w1 * e;
+    } else if (f2 == COMMET_CANN_F2_LOG) {
+        const T q = T(1) - w1 * y;  // q <= 0 gives a non-finite value: the point is reported
+        f = -dev_log(q);
+        fd = w1 / q;
+        fdd = fd * fd;
+    } else {
+        f = w1 * y;
+        fd = w1;
+        fdd = T(0);
+    }
+    v = w2 * f;
+    g = w2 * fd * yd * ad;
+    h = w2 * (fdd * yd * yd + fd * ydd) * ad * ad;
+}
+
+// K in FP64 whatever T is. The CANN's polynomial terms make dN/dK proportional to K,
+// and a shifted invariant such as Ibar2 - 3 formed in FP32 carries an absolute error of
+// a few ulp(3) ~ 1e-6, a large relative error when K is small; with FP64 kinematic
+// scalars the FP32 path keeps its 1e-5 bound. (A network's dN/dK varies slowly with K,
+// so the network kernels form K in T.)
+template <typename T, int NF>
+__device__ __forceinline__ bool kin_scalars_k64(const T (&F)[9], const KinConst<T> &kc, T *K, T &Jm1,
+                                                PolyChain<T> &ch) {
+    if constexpr (sizeof(T) == 8) {
+        return kin_scalars<T, NF>(F, kc, K, Jm1, &ch);
+    } else {
+        constexpr int D = 3 + 2 * NF;
+        KinConst<double> kd{};
+        kd.kin = kc.kin;
+        kd.stress_free = kc.stress_free;
+        kd.kappa = (double)kc.kappa;
+        for (int f = 0; f < 2; ++f)
+            for (int c = 0; c < 3; ++c) kd.fib[f][c] = (double)kc.fib[f][c];
+        double Fd[9], Kd[D], Jd;
+        PolyChain<double> chd;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) Fd[c] = (double)F[c];
+        const bool ok = kin_scalars<double, NF>(Fd, kd, Kd, Jd, &chd);
+#pragma unroll
+        for (int m = 0; m < D; ++m) K[m] = (T)Kd[m];
+        Jm1 = (T)Jd;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            ch.d1[m] = (T)chd.d1[m];
+            ch.d2[m] = (T)chd.d2[m];
+        }
+        return ok;
+    }
+}
+
+template <typename T, int NF, int INNER, bool SPATIAL>
+__global__ void __launch_bounds__(256)
+    closed_update_kernel(const T *__restrict__ gw, NetLayout lay, KinConst<T> kc, int64_t n_qp,
+                         const T *__restrict__ Fg, T *__restrict__ psi, T *__restrict__ P, T *__restrict__ A,
+                         int32_t *__restrict__ status, T *__restrict__ dN_out, int qstride) {
+    constexpr int D = 3 + 2 * NF, NH = D * (D + 1) / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sw = reinterpret_cast<T *>(smem_raw);
+    const int wbytes = (lay.total * (int)sizeof(T) + 15) / 16 * 16;
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(gw);
+        int4 *dst = reinterpret_cast<int4 *>(sw);
+        for (int i = threadIdx.x; i < wbytes / 16; i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int qi = lane >> 2, jb = lane & 3;
+    T *qs = sw + wbytes / (int)sizeof(T) + (size_t)(warp * kQPW + qi) * qstride;
+    const int64_t n_tiles = (n_qp + kQPW - 1) / kQPW;
+    const int64_t n_gwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const bool want_A = (A != nullptr);
+
+    for (int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; tile < n_tiles; tile += n_gwarps) {
+        const int64_t q = tile * kQPW + qi;
+        const bool valid = q < n_qp;
+        const int64_t qo = valid ? q : 0;
+        T F[9];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) F[c] = valid ? Fg[c * n_qp + q] : ((c % 4) == 0 ? T(1) : T(0));
+        T K[D], Jm1;
+        PolyChain<T> ch;
+        const bool bad = !kin_scalars_k64<T, NF>(F, kc, K, Jm1, ch);
+        if (bad) {
+#pragma unroll
+            for (int c = 0; c < 9; ++c) F[c] = (c % 4) == 0 ? T(1) : T(0);
+            kin_scalars_k64<T, NF>(F, kc, K, Jm1, ch);
+        }
+        T npart = T(0), dN[D], Hs[NH];
+#pragma unroll
+        for (int m = 0; m < D; ++m) dN[m] = T(0);
+#pragma unroll
+        for (int h = 0; h < NH; ++h) Hs[h] = T(0);
+        if constexpr (INNER == COMMET_INNER_CANN) {
+            // the D n terms (input m, term k) go round-robin over the group's 4 lanes
+            const int n = lay.cn, nt = D * n;
+            for (int t0 = 0; t0 < nt; t0 += kG) {
+                const int t = t0 + jb;
+                if (t < nt) {
+                    const int m = t / n, k = t - m * n;
+                    T x = T(0);
+#pragma unroll
+                    for (int mm = 0; mm < D; ++mm) x = (mm == m) ? K[mm] : x;
+                    T v, g, h;
+                    cann_term<T>(x, (int)sw[lay.ck + 3 * k], (int)sw[lay.ck + 3 * k + 1], (int)sw[lay.ck + 3 * k + 2],
+                                 sw[lay.cw + 2 * t], sw[lay.cw + 2 * t + 1], v, g, h);
+                    npart += v;
+#pragma unroll
+                    for (int mm = 0; mm < D; ++mm) {
+                        dN[mm] += (mm == m) ? g : T(0);
+                        Hs[mm * (mm + 1) / 2 + mm] += (mm == m) ? h : T(0);
+                    }
+                }
+            }
+        } else {
+            // eq. gt on raw (Ibar1, Ibar2, J); J - 1 from det_minus_one
+            if (jb == 0) {
+                const T r2 = T(1) / K[1];
+                npart = T(0.5) * (K[0] - T(3)) + dev_log(K[1] * T(1.0 / 3.0)) + Jm1 * Jm1;
+                dN[0] = T(0.5);
+                dN[1] = r2;
+                dN[2] = T(2) * Jm1;
+                Hs[2] = -r2 * r2;
+                Hs[5] = T(2);
+            }
+        }
+        T psi_val;
+        bool report;
+        if constexpr (SPATIAL) {
+            T *pa = qs + qp_stage_end(D, NF);
+            qp_group_finish<T, NF>(sw + lay.n0, sw + lay.K0, kc, qs, qi, jb, F, K, Jm1, ch, bad, valid, npart, dN, Hs,
+                                   want_A, pa, 1, want_A ? pa + 9 : nullptr, 1, nullptr, 0, psi_val, report);
+            __syncwarp();
+            push_forward_group<T>(qs + Stage<D, NF>::F, pa, pa + 9, jb, valid, P + qo, want_A ? A + qo : nullptr,
+                                  n_qp);
+        } else {
+            qp_group_finish<T, NF>(sw + lay.n0, sw + lay.K0, kc, qs, qi, jb, F, K, Jm1, ch, bad, valid, npart, dN, Hs,
+                                   want_A, P + qo, n_qp, want_A ? A + qo : nullptr, n_qp,
+                                   dN_out ? dN_out + qo : nullptr, n_qp, psi_val, report);
+        }
+        if (valid && jb == 0) {
+            if (psi != nullptr) psi[q] = psi_val;
+            if (report && status != nullptr) {
+                atomicAdd(&status[0], 1);
+                atomicMin(&status[1], (int32_t)(q < INT32_MAX ? q : INT32_MAX));
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <typename T, int NF, int INNER, bool SPATIAL>
+static int launch_closed(const commet_model *m, int64_t n_qp, const void *F, void *psi, void *P, void *A,
+                         int32_t *status, cudaStream_t s, void *dN_out) {
+    constexpr int D = 3 + 2 * NF;
+    KinConst<T> kc{};
+    kc.kin = m->kp.kin;
+    kc.stress_free = m->kp.stress_free;
+    kc.kappa = (T)m->kp.kappa;
+    for (int f = 0; f < 2; ++f)
+        for (int c = 0; c < 3; ++c) kc.fib[f][c] = (T)m->kp.fib[f][c];
+    const int qstride = qp_slab_elems<T>(D, 0, 0, NF, SPATIAL);
+    const size_t wbytes = ((size_t)m->lay.total * sizeof(T) + 15) / 16 * 16;
+    const int warps = 8;
+    const size_t smem = wbytes + (size_t)warps * kQPW * qstride * sizeof(T);
+    auto kern = closed_update_kernel<T, NF, INNER, SPATIAL>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return COMMET_ERR_CUDA;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t n_tiles = (n_qp + kQPW - 1) / kQPW;
+    const int64_t want = (n_tiles + warps - 1) / warps;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count() * per_sm));
+    kern<<<grid, warps * 32, smem, s>>>((const T *)m->d_weights, m->lay, kc, n_qp, (const T *)F, (T *)psi, (T *)P,
+                                        (T *)A, status, (T *)dN_out, qstride);
+    return cudaGetLastError() == cudaSuccess ? COMMET_OK : COMMET_ERR_CUDA;
+}
+
+template <typename T, bool SPATIAL>
+static int dispatch_closed(const commet_model *m, int64_t n_qp, const void *F, void *psi, void *P, void *A,
+                           int32_t *status, cudaStream_t s, void *dN_out) {
+    const int nf = m->kp.nf;
+    if (m->inner == COMMET_INNER_GENT_THOMAS && nf == 0)
+        return launch_closed<T, 0, COMMET_INNER_GENT_THOMAS, SPATIAL>(m, n_qp, F, psi, P, A, status, s, dN_out);
+    if (m->inner == COMMET_INNER_CANN) {
+        if (nf == 0) return launch_closed<T, 0, COMMET_INNER_CANN, SPATIAL>(m, n_qp, F, psi, P, A, status, s, dN_out);
+        if (nf == 1) return launch_closed<T, 1, COMMET_INNER_CANN, SPATIAL>(m, n_qp, F, psi, P, A, status, s, dN_out);
+        if (nf == 2) return launch_closed<T, 2, COMMET_INNER_CANN, SPATIAL>(m, n_qp, F, psi, P, A, status, s, dN_out);
+    }
+    return COMMET_ERR_UNSUPPORTED;
+}
+
+}  // namespace commet

@@ -12,6 +12,8 @@
 namespace commet {
 
 constexpr int kMaxFibres = 2;
+constexpr int kRedBlocks = 1024;  // partial sums per reduction slot of the solver
+constexpr int kRedDoubles = 16 + 2 * kRedBlocks;
 constexpr int kMaxD = 3 + 2 * kMaxFibres;
 
 // Offsets (in elements of the path's scalar type) of the packed weight block that
@@ -21,7 +23,7 @@ struct NetLayout {
     int W1t;  // [d][W]       W1 transposed (forward: contiguous over neurons)
     int W1r;  // [W][dp]      W1 row-major, rows padded to dp (tangent seed)
     int At;   // [L-1][W][W]  A_k transposed: At[i][j] = A_k[j][i]
-    int Ar;   // [L-1][W][W]  A_k row-major (reverse pass)
+    int Ar;   // [L-1][W][W]  A_k row-major (reverse pass); the last block
     int Bt;   // [L-1][d][W]  B_k transposed
     int c;    // [L][W]
     int a;    // [W]
@@ -29,6 +31,8 @@ struct NetLayout {
     int n0;   // [d] stress-free shift (zeros when off)
     int K0;   // [d] K at F = I
     int tab;  // FP64 models: activation tables (kActTab doubles); 0 otherwise
+    // CANN (inner == COMMET_INNER_CANN): cn terms, weights cw [d][cn][2], kinds ck [cn][3]
+    int inner, cn, cw, ck;
     int total;
 };
 
@@ -45,6 +49,7 @@ struct KinParams {
 
 struct commet_model {
     int precision;
+    int inner = COMMET_INNER_MICNN;
     int d, W, L;
     commet::KinParams kp;
     commet::NetLayout lay;
@@ -73,6 +78,14 @@ struct commet_mesh {
     // host copies for commet_mesh_csr
     int64_t *h_rowptr = nullptr;
     int32_t *h_col = nullptr;
+    // solver state: Dirichlet dofs (mask over the 3 n_nodes dofs, the sorted list and a
+    // value buffer) and the FP64 reduction array of the CG scalars and partial sums
+    int64_t n_fixed = 0;
+    uint8_t *d_fixed = nullptr;
+    int64_t *d_fixed_dofs = nullptr;
+    double *d_fixed_vals = nullptr;
+    double *d_delta = nullptr;  // [n_rows] prescribed increments, dense
+    double *d_red = nullptr;
     int device = 0;
 };
 
@@ -86,6 +99,17 @@ int launch_const_update_bf16(const commet_model *m, int64_t n_qp, const void *F,
 // Spatial form (App. A.1): tau [6][n], c [21][n] (Voigt) instead of P, A; all precisions.
 int launch_const_update_spatial(const commet_model *m, int64_t n_qp, const void *F, void *psi, void *tau, void *c,
                                 int32_t *status, cudaStream_t s);
+// Newton step after assembly (solver.cu)
+size_t cg_workspace_bytes(const commet_mesh *mesh, int precision);
+int launch_cg_solve(const commet_mesh *mesh, int precision, const void *K_vals, const void *b, void *x, double rtol,
+                    int max_iter, void *ws, int32_t *iters, double *rel_res, cudaStream_t s);
+int launch_apply_dirichlet(const commet_mesh *mesh, int precision, void *r, void *K_vals, const double *delta_host,
+                           cudaStream_t s);
+int launch_set_dirichlet_values(const commet_mesh *mesh, int precision, const double *vals_host, void *u,
+                                cudaStream_t s);
+int launch_add_increment(const commet_mesh *mesh, int precision, const void *du, double alpha, void *u,
+                         cudaStream_t s);
+int launch_norm2(const commet_mesh *mesh, int precision, int64_t n, const void *x, double *out, cudaStream_t s);
 int launch_elem_assemble_spatial(const commet_mesh *mesh, int precision, const void *F, const void *tau,
                                  const void *c, void *f_e, void *K_e, void *r, void *K_vals, cudaStream_t s);
 int launch_status_init(int32_t *status, cudaStream_t s);

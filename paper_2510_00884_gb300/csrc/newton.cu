@@ -122,7 +122,8 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 384)
         T psi_val;
         bool report;
         T *pa = ea + kEPA + 90 * qi;
-        qp_group_update<T, NF, W>(sw, lay, kc, qs, qi, jb, F, true, pa, 1, pa + 9, 1, nullptr, 0, psi_val, report);
+        qp_group_update<T, NF, W>(sw, lay, sw + lay.Ar, kc, qs, qi, jb, F, true, pa, 1, pa + 9, 1, nullptr, 0, psi_val,
+                                  report);
         if (report && jb == 0 && status != nullptr) {
             const int64_t q = 8 * e + qi;
             atomicAdd(&status[0], 1);
@@ -240,6 +241,7 @@ static int newton_dispatch(const commet_model *m, const commet_mesh *mesh, const
 
 int launch_newton_assemble(const commet_model *m, const commet_mesh *mesh, const void *u, void *r, void *K_vals,
                            int32_t *status, cudaStream_t s) {
+    if (m->inner != COMMET_INNER_MICNN) return COMMET_ERR_UNSUPPORTED;
     if (mesh->n_el == 0) {
         const size_t es = m->precision == COMMET_F64 ? 8 : 4;
         if (mesh->n_nodes > 0) COMMET_CUDA_TRY(cudaMemsetAsync(r, 0, es * 3 * mesh->n_nodes, s));

@@ -54,6 +54,7 @@ bool aligned16(const void *p) { return p == nullptr || (reinterpret_cast<uintptr
 extern "C" int commet_const_backward_noalloc(const commet_model *m, int64_t n_qp, const void *F, const void *dL_dP,
                                              void *dL_dF, void *dL_dtheta, void *stream) {
     if (m == nullptr || n_qp < 0 || dL_dtheta == nullptr) return COMMET_ERR_INVALID_ARG;
+    if (m->inner != COMMET_INNER_MICNN) return COMMET_ERR_UNSUPPORTED;
     if (n_qp > 0 && (F == nullptr || dL_dP == nullptr)) return COMMET_ERR_INVALID_ARG;
     if (!aligned16(F) || !aligned16(dL_dP) || !aligned16(dL_dF) || !aligned16(dL_dtheta)) return COMMET_ERR_INVALID_ARG;
     if (m->kp.stress_free) return COMMET_ERR_UNSUPPORTED;

@@ -68,20 +68,19 @@ __device__ __forceinline__ T shfl_xor(T v, int m) {
     return __shfl_xor_sync(0xffffffffu, v, m);
 }
 
-// 128-bit shared-memory loads/stores of N consecutive elements (p 16-byte aligned,
-// N a multiple of 16 / sizeof(T)).
+// Vector shared-memory loads/stores of N consecutive elements: 128-bit when N is a
+// multiple of 16 / sizeof(T) (p 16-byte aligned), 64-bit float pairs when N is even
+// (p 8-byte aligned), scalar otherwise (the narrow networks, W = 4 and 8).
 template <int N, typename T>
 __device__ __forceinline__ void ldv(const T *p, T *r) {
-    if constexpr (sizeof(T) == 8) {
-        static_assert(N % 2 == 0, "ldv<double>: N must be even");
+    if constexpr (sizeof(T) == 8 && N % 2 == 0) {
 #pragma unroll
         for (int v = 0; v < N / 2; ++v) {
             const double2 x = reinterpret_cast<const double2 *>(p)[v];
             r[2 * v] = x.x;
             r[2 * v + 1] = x.y;
         }
-    } else {
-        static_assert(N % 4 == 0, "ldv<float>: N must be a multiple of 4");
+    } else if constexpr (sizeof(T) == 4 && N % 4 == 0) {
 #pragma unroll
         for (int v = 0; v < N / 4; ++v) {
             const float4 x = reinterpret_cast<const float4 *>(p)[v];
@@ -90,21 +89,203 @@ __device__ __forceinline__ void ldv(const T *p, T *r) {
             r[4 * v + 2] = x.z;
             r[4 * v + 3] = x.w;
         }
+    } else if constexpr (sizeof(T) == 4 && N % 2 == 0) {
+#pragma unroll
+        for (int v = 0; v < N / 2; ++v) {
+            const float2 x = reinterpret_cast<const float2 *>(p)[v];
+            r[2 * v] = x.x;
+            r[2 * v + 1] = x.y;
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < N; ++v) r[v] = p[v];
     }
 }
 template <int N, typename T>
 __device__ __forceinline__ void stv(T *p, const T *r) {
-    if constexpr (sizeof(T) == 8) {
+    if constexpr (sizeof(T) == 8 && N % 2 == 0) {
 #pragma unroll
         for (int v = 0; v < N / 2; ++v) reinterpret_cast<double2 *>(p)[v] = make_double2(r[2 * v], r[2 * v + 1]);
-    } else {
+    } else if constexpr (sizeof(T) == 4 && N % 4 == 0) {
 #pragma unroll
         for (int v = 0; v < N / 4; ++v)
             reinterpret_cast<float4 *>(p)[v] = make_float4(r[4 * v], r[4 * v + 1], r[4 * v + 2], r[4 * v + 3]);
+    } else if constexpr (sizeof(T) == 4 && N % 2 == 0) {
+#pragma unroll
+        for (int v = 0; v < N / 2; ++v) reinterpret_cast<float2 *>(p)[v] = make_float2(r[2 * v], r[2 * v + 1]);
+    } else {
+#pragma unroll
+        for (int v = 0; v < N; ++v) p[v] = r[v];
     }
 }
 
+// Second half of a point's update, shared by every inner function: the 4-lane group
+// reduction of the partial sums (npart, dN, Hs: N, dN/dK and the packed lower triangle
+// of d2N/dK2, each lane holding its share), the polyconvex chain rule, the kinematic
+// staging and the assembly of P and A (eq. nncm-chain, material form), and Psi.
+//  n0s, K0s  the stress-free shift n0 and K(I) (zeros when off)
+//  K, Jm1, ch, bad   from kin_scalars at the (possibly replaced) F
+// Outputs as qp_group_update.
+template <typename T, int NF>
+__device__ __forceinline__ void qp_group_finish(const T *n0s, const T *K0s, const KinConst<T> &kc, T *qs, int qi,
+                                                int jb, const T (&F)[9], const T *K, T Jm1,
+                                                const PolyChain<T> &ch, bool bad, bool valid, T npart, T *dN,
+                                                T *Hs, bool want_A, T *Pq, int64_t pst, T *Aq, int64_t ast,
+                                                T *dNq, int64_t dst, T &psi_val, bool &report) {
+    constexpr int D = 3 + 2 * NF, DP = (D + 3) / 4 * 4, NH = D * (D + 1) / 2;
+    // ---- reduce the group's partial sums
+#pragma unroll
+    for (int msk = 1; msk <= 2; msk <<= 1) {
+        npart += shfl_xor(npart, msk);
+#pragma unroll
+        for (int m = 0; m < D; ++m) dN[m] += shfl_xor(dN[m], msk);
+#pragma unroll
+        for (int h = 0; h < NH; ++h) Hs[h] += shfl_xor(Hs[h], msk);
+    }
+    if (dNq != nullptr && valid && jb == 0) {
+#pragma unroll
+        for (int m = 0; m < D; ++m) {
+            dNq[m * dst] = dN[m];
+            dNq[(D + m) * dst] = K[m];
+        }
+    }
+
+    // ---- Psi first: a point whose energy is not finite (an inner function outside its
+    // domain) is reported with all of its outputs NaN, like an inadmissible F
+    T Psi = npart + kc.kappa * Jm1 * Jm1;
+#pragma unroll
+    for (int m = 0; m < D; ++m) Psi -= n0s[m] * (K[m] - K0s[m]);
+    bad = bad || !dev_finite(Psi);
+
+    // ---- kinematic derivatives, P, A
+    T cvec[D];
+#pragma unroll
+    for (int m = 0; m < D; ++m) cvec[m] = dN[m] - n0s[m];
+    if constexpr (NF == 0) {
+        if (kc.kin == COMMET_KIN_POLYCONVEX) poly_to_invariants<T>(ch, cvec, Hs);
+    }
+    stage_kinematics<T, NF>(F, kc, cvec, Jm1, jb, qs);
+    using S = Stage<D, NF>;
+    constexpr int UOFF = (S::size + 3) / 4 * 4;  // u_a = sum_m g_m[a] N_mn : [9][DP]
+    constexpr int HOFF = UOFF + 9 * DP;          // d2N/dK2, full: [D][DP]
+    constexpr int NPL = (D + kG - 1) / kG;       // u columns per lane
+    if (want_A && jb == 0) {
+#pragma unroll
+        for (int m = 0; m < D; ++m)
+#pragma unroll
+            for (int n = 0; n < D; ++n)
+                qs[HOFF + m * DP + n] = Hs[(m >= n) ? (m * (m + 1) / 2 + n) : (n * (n + 1) / 2 + m)];
+    }
+    __syncwarp();
+    bool group_nonfinite = false;
+    if constexpr (sizeof(T) != 8) {
+        // FP32: each lane forms whole rows a = jb, jb + 4, jb + 8 (fewer live registers)
+        bool nonfinite = false;
+        for (int a = jb; a < 9; a += kG) {
+            T Pa, Arow[9];
+            if (want_A) {
+                assemble_row<T, NF>(a, qs, Hs, cvec, Pa, Arow);
+            } else {
+                Pa = assemble_P<T, NF>(a, qs, cvec);
+#pragma unroll
+                for (int b = 0; b < 9; ++b) Arow[b] = T(0);
+            }
+            bool fin = dev_finite(Pa);
+#pragma unroll
+            for (int b = 0; b < 9; ++b) fin = fin && dev_finite(Arow[b]);
+            nonfinite |= !fin;
+            const bool nan_out = bad || !fin;
+            if (valid) {
+                const T nanv = T(NAN);
+                Pq[a * pst] = nan_out ? nanv : Pa;
+                if (want_A) {
+#pragma unroll
+                    for (int b = 0; b < 9; ++b) Aq[(9 * a + b) * ast] = nan_out ? nanv : Arow[b];
+                }
+            }
+        }
+        const unsigned m0 = __ballot_sync(0xffffffffu, nonfinite);
+        group_nonfinite = ((m0 >> (qi * 4)) & 0xFu) != 0u;
+    } else {
+        // FP64: the FP64 pipe is charged per warp instruction, so the work is spread evenly:
+        // P rows a = jb, jb + 4, jb + 8 and, with A, the 45 upper entries round-robin over the
+        // group's four lanes; every value is formed before any is stored so that a point with
+        // a non-finite entry is written as NaN throughout.
+        T Pv[3];
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const int a = jb + kG * t;
+            Pv[t] = (a < 9) ? assemble_P<T, NF>(a, qs, cvec) : T(0);
+        }
+        T Av[12];
+#pragma unroll
+        for (int t = 0; t < 12; ++t) Av[t] = T(0);
+        if (want_A) {
+#pragma unroll 1
+            for (int a = 0; a < 9; ++a) {
+#pragma unroll
+                for (int nn = 0; nn < NPL; ++nn) {
+                    const int n = jb * NPL + nn;
+                    const int nc = n < D ? n : D - 1;
+                    T acc = T(0);
+#pragma unroll
+                    for (int m = 0; m < D; ++m) acc += qs[S::g + 9 * m + a] * qs[HOFF + m * DP + nc];
+                    if (n < D) qs[UOFF + a * DP + n] = acc;
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int t = 0; t < 12; ++t) {
+                const int e = jb + kG * t;
+                if (e < 45) {
+                    int a, b;
+                    upper_index(e, a, b);
+                    Av[t] = assemble_entry<T, NF, DP>(a, b, qs, qs + UOFF);
+                }
+            }
+        }
+        bool nonfinite = false;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) nonfinite |= !dev_finite(Pv[t]);
+#pragma unroll
+        for (int t = 0; t < 12; ++t) nonfinite |= !dev_finite(Av[t]);
+        {
+            const unsigned m0 = __ballot_sync(0xffffffffu, nonfinite);
+            nonfinite = ((m0 >> (qi * 4)) & 0xFu) != 0u;
+            group_nonfinite = nonfinite;
+        }
+        if (valid) {
+            const bool nan_out = bad || nonfinite;
+            const T nanv = T(NAN);
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                const int a = jb + kG * t;
+                if (a < 9) Pq[a * pst] = nan_out ? nanv : Pv[t];
+            }
+            if (want_A) {
+#pragma unroll
+                for (int t = 0; t < 12; ++t) {
+                    const int e = jb + kG * t;
+                    if (e < 45) {
+                        int a, b;
+                        upper_index(e, a, b);
+                        const T v = nan_out ? nanv : Av[t];
+                        Aq[(9 * a + b) * ast] = v;
+                        if (a != b) Aq[(9 * b + a) * ast] = v;
+                    }
+                }
+            }
+        }
+    }
+    // a point is reported if J <= 0 / bad input, or any of its values was not finite
+    const bool grp_nonfinite = group_nonfinite;
+    report = bad || grp_nonfinite;
+    psi_val = report ? T(NAN) : Psi;
+}
+
 // One point on its 4-lane group (all 32 lanes of the warp call this together).
+//  ar     the row-major A_k block (lay.Ar of the packed weights), in shared memory or,
+//         for networks too large for it, in global memory
 //  F      the point's deformation gradient (replaced by I when it is not admissible)
 //  valid  false for padding points: computed on F = I, nothing written
 //  Pq, pst / Aq, ast   where row a of P and entry (a, b) of A go: Pq[a*pst], Aq[(9a+b)*ast]
@@ -114,7 +295,7 @@ __device__ __forceinline__ void stv(T *p, const T *r) {
 //                      (J <= 0, non-finite input or result); valid in every lane
 template <typename T, int NF, int W>
 __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const NetLayout &lay,
-                                                const KinConst<T> &kc, T *qs, int qi, int jb, T (&F)[9],
+                                                const T *__restrict__ ar, const KinConst<T> &kc, T *qs, int qi, int jb, T (&F)[9],
                                                 bool valid, T *Pq, int64_t pst, T *Aq, int64_t ast, T *dNq,
                                                 int64_t dst, T &psi_val, bool &report) {
     using Cf = CUConf<T, NF, W>;
@@ -226,7 +407,7 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
         T zb[NJ];
 #pragma unroll
         for (int ii = 0; ii < NJ; ++ii) zb[ii] = T(0);
-        const T *Ar = sw + lay.Ar + (k - 2) * W * W + j0;
+        const T *Ar = ar + (k - 2) * W * W + j0;
 #pragma unroll 2
         for (int j = 0; j < W; j += V) {
             T yv[V];
@@ -351,152 +532,8 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
         }
     }  // want_A
 
-    // ---- reduce the group's partial sums
-#pragma unroll
-    for (int msk = 1; msk <= 2; msk <<= 1) {
-        npart += shfl_xor(npart, msk);
-#pragma unroll
-        for (int m = 0; m < D; ++m) dN[m] += shfl_xor(dN[m], msk);
-#pragma unroll
-        for (int h = 0; h < NH; ++h) Hs[h] += shfl_xor(Hs[h], msk);
-    }
-    if (dNq != nullptr && valid && jb == 0) {
-#pragma unroll
-        for (int m = 0; m < D; ++m) {
-            dNq[m * dst] = dN[m];
-            dNq[(D + m) * dst] = K[m];
-        }
-    }
-
-    // ---- kinematic derivatives, P, A, Psi
-    T cvec[D];
-#pragma unroll
-    for (int m = 0; m < D; ++m) cvec[m] = dN[m] - sw[lay.n0 + m];
-    if constexpr (NF == 0) {
-        if (kc.kin == COMMET_KIN_POLYCONVEX) poly_to_invariants<T>(ch, cvec, Hs);
-    }
-    stage_kinematics<T, NF>(F, kc, cvec, Jm1, jb, qs);
-    using S = Stage<D, NF>;
-    constexpr int UOFF = (S::size + 3) / 4 * 4;  // u_a = sum_m g_m[a] N_mn : [9][DP]
-    constexpr int HOFF = UOFF + 9 * DP;          // d2N/dK2, full: [D][DP]
-    constexpr int NPL = (D + kG - 1) / kG;       // u columns per lane
-    if (want_A && jb == 0) {
-#pragma unroll
-        for (int m = 0; m < D; ++m)
-#pragma unroll
-            for (int n = 0; n < D; ++n)
-                qs[HOFF + m * DP + n] = Hs[(m >= n) ? (m * (m + 1) / 2 + n) : (n * (n + 1) / 2 + m)];
-    }
-    __syncwarp();
-    bool group_nonfinite = false;
-    if constexpr (sizeof(T) != 8) {
-        // FP32: each lane forms whole rows a = jb, jb + 4, jb + 8 (fewer live registers)
-        bool nonfinite = false;
-        for (int a = jb; a < 9; a += kG) {
-            T Pa, Arow[9];
-            if (want_A) {
-                assemble_row<T, NF>(a, qs, Hs, cvec, Pa, Arow);
-            } else {
-                Pa = assemble_P<T, NF>(a, qs, cvec);
-#pragma unroll
-                for (int b = 0; b < 9; ++b) Arow[b] = T(0);
-            }
-            bool fin = dev_finite(Pa);
-#pragma unroll
-            for (int b = 0; b < 9; ++b) fin = fin && dev_finite(Arow[b]);
-            nonfinite |= !fin;
-            const bool nan_out = bad || !fin;
-            if (valid) {
-                const T nanv = T(NAN);
-                Pq[a * pst] = nan_out ? nanv : Pa;
-                if (want_A) {
-#pragma unroll
-                    for (int b = 0; b < 9; ++b) Aq[(9 * a + b) * ast] = nan_out ? nanv : Arow[b];
-                }
-            }
-        }
-        const unsigned m0 = __ballot_sync(0xffffffffu, nonfinite);
-        group_nonfinite = ((m0 >> (qi * 4)) & 0xFu) != 0u;
-    } else {
-        // FP64: the FP64 pipe is charged per warp instruction, so the work is spread evenly:
-        // P rows a = jb, jb + 4, jb + 8 and, with A, the 45 upper entries round-robin over the
-        // group's four lanes; every value is formed before any is stored so that a point with
-        // a non-finite entry is written as NaN throughout.
-        T Pv[3];
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            const int a = jb + kG * t;
-            Pv[t] = (a < 9) ? assemble_P<T, NF>(a, qs, cvec) : T(0);
-        }
-        T Av[12];
-#pragma unroll
-        for (int t = 0; t < 12; ++t) Av[t] = T(0);
-        if (want_A) {
-#pragma unroll 1
-            for (int a = 0; a < 9; ++a) {
-#pragma unroll
-                for (int nn = 0; nn < NPL; ++nn) {
-                    const int n = jb * NPL + nn;
-                    const int nc = n < D ? n : D - 1;
-                    T acc = T(0);
-#pragma unroll
-                    for (int m = 0; m < D; ++m) acc += qs[S::g + 9 * m + a] * qs[HOFF + m * DP + nc];
-                    if (n < D) qs[UOFF + a * DP + n] = acc;
-                }
-            }
-            __syncwarp();
-#pragma unroll
-            for (int t = 0; t < 12; ++t) {
-                const int e = jb + kG * t;
-                if (e < 45) {
-                    int a, b;
-                    upper_index(e, a, b);
-                    Av[t] = assemble_entry<T, NF, DP>(a, b, qs, qs + UOFF);
-                }
-            }
-        }
-        bool nonfinite = false;
-#pragma unroll
-        for (int t = 0; t < 3; ++t) nonfinite |= !dev_finite(Pv[t]);
-#pragma unroll
-        for (int t = 0; t < 12; ++t) nonfinite |= !dev_finite(Av[t]);
-        {
-            const unsigned m0 = __ballot_sync(0xffffffffu, nonfinite);
-            nonfinite = ((m0 >> (qi * 4)) & 0xFu) != 0u;
-            group_nonfinite = nonfinite;
-        }
-        if (valid) {
-            const bool nan_out = bad || nonfinite;
-            const T nanv = T(NAN);
-#pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                const int a = jb + kG * t;
-                if (a < 9) Pq[a * pst] = nan_out ? nanv : Pv[t];
-            }
-            if (want_A) {
-#pragma unroll
-                for (int t = 0; t < 12; ++t) {
-                    const int e = jb + kG * t;
-                    if (e < 45) {
-                        int a, b;
-                        upper_index(e, a, b);
-                        const T v = nan_out ? nanv : Av[t];
-                        Aq[(9 * a + b) * ast] = v;
-                        if (a != b) Aq[(9 * b + a) * ast] = v;
-                    }
-                }
-            }
-        }
-    }
-    // a point is reported if J <= 0 / bad input, or any of its values was not finite
-    const bool grp_nonfinite = group_nonfinite;
-    {
-        T Psi = npart + kc.kappa * Jm1 * Jm1;
-#pragma unroll
-        for (int m = 0; m < D; ++m) Psi -= sw[lay.n0 + m] * (K[m] - sw[lay.K0 + m]);
-        report = bad || grp_nonfinite || !dev_finite(Psi);
-        psi_val = report ? T(NAN) : Psi;
-    }
+    qp_group_finish<T, NF>(sw + lay.n0, sw + lay.K0, kc, qs, qi, jb, F, K, Jm1, ch, bad, valid, npart, dN, Hs,
+                           want_A, Pq, pst, Aq, ast, dNq, dst, psi_val, report);
 }
 
 }  // namespace commet

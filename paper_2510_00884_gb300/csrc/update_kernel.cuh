@@ -14,6 +14,7 @@
 #include <climits>
 #include <cstdint>
 
+#include "closed_form.cuh"
 #include "qp_body.cuh"
 
 namespace commet {
@@ -24,11 +25,14 @@ template <typename T, int NF, int W, bool SPATIAL>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 384)
     const_update_kernel(const T *__restrict__ gw, NetLayout lay, KinConst<T> kc, int64_t n_qp,
                         const T *__restrict__ Fg, T *__restrict__ psi, T *__restrict__ P, T *__restrict__ A,
-                        int32_t *__restrict__ status, T *__restrict__ dN_out, int qstride) {
+                        int32_t *__restrict__ status, T *__restrict__ dN_out, int qstride, int wcount) {
     using Cf = CUConf<T, NF, W>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sw = reinterpret_cast<T *>(smem_raw);
-    const int wbytes = (lay.total * (int)sizeof(T) + 15) / 16 * 16;
+    // the packed weights up to wcount elements go to shared memory; A_k row-major (the
+    // last block) is read from global memory when wcount stops before it
+    const int wbytes = (wcount * (int)sizeof(T) + 15) / 16 * 16;
+    const T *ar = (wcount >= lay.total) ? sw + lay.Ar : gw + lay.Ar;
     {
         const int n16 = wbytes / 16;
         const int4 *src = reinterpret_cast<const int4 *>(gw);
@@ -54,12 +58,12 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 384)
         if constexpr (SPATIAL) {
             // P and A of the point go to its slab, then are pushed forward to tau (P) and c (A)
             T *pa = qs + qp_stage_end(Cf::D, NF);
-            qp_group_update<T, NF, W>(sw, lay, kc, qs, qi, jb, F, valid, pa, 1, A ? pa + 9 : nullptr, 1, nullptr, 0,
+            qp_group_update<T, NF, W>(sw, lay, ar, kc, qs, qi, jb, F, valid, pa, 1, A ? pa + 9 : nullptr, 1, nullptr, 0,
                                       psi_val, report);
             __syncwarp();
             push_forward_group<T>(qs + Stage<Cf::D, NF>::F, pa, pa + 9, jb, valid, P + qo, A ? A + qo : nullptr, n_qp);
         } else {
-            qp_group_update<T, NF, W>(sw, lay, kc, qs, qi, jb, F, valid, P + qo, n_qp, A ? A + qo : nullptr, n_qp,
+            qp_group_update<T, NF, W>(sw, lay, ar, kc, qs, qi, jb, F, valid, P + qo, n_qp, A ? A + qo : nullptr, n_qp,
                                       dN_out ? dN_out + qo : nullptr, n_qp, psi_val, report);
         }
         if (valid && jb == 0) {
@@ -84,15 +88,26 @@ static int launch_typed(const commet_model *m, int64_t n_qp, const void *F, void
     for (int f = 0; f < 2; ++f)
         for (int c = 0; c < 3; ++c) kc.fib[f][c] = (T)m->kp.fib[f][c];
     const int qstride = qp_slab_elems<T>(Cf::D, W, m->L, NF, SPATIAL);
-    const size_t wbytes = ((size_t)m->lay.total * sizeof(T) + 15) / 16 * 16;
     const size_t per_warp = (size_t)kQPW * qstride * sizeof(T);
     int dev = 0;
     cudaGetDevice(&dev);
     int smem_max = 0;
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int max_threads = sizeof(T) == 8 ? 256 : 384;
-    int warps = (int)std::min<size_t>((size_t)max_threads / 32, (smem_max - wbytes) / per_warp);
-    if (smem_max < (int)wbytes || warps < 1) return COMMET_ERR_UNSUPPORTED;
+    // all weights in shared memory, unless leaving A_k row-major (the last block) in global
+    // memory lets more warps fit beside the point slabs
+    auto fit = [&](size_t wb) -> int {
+        return wb + per_warp > (size_t)smem_max
+                   ? 0
+                   : (int)std::min<size_t>((size_t)max_threads / 32, (smem_max - wb) / per_warp);
+    };
+    const size_t wb_all = ((size_t)m->lay.total * sizeof(T) + 15) / 16 * 16;
+    const size_t wb_noar = ((size_t)m->lay.Ar * sizeof(T) + 15) / 16 * 16;
+    const bool ar_global = fit(wb_noar) > fit(wb_all);
+    const int wcount = ar_global ? m->lay.Ar : m->lay.total;
+    const size_t wbytes = ar_global ? wb_noar : wb_all;
+    const int warps = fit(wbytes);
+    if (warps < 1) return COMMET_ERR_UNSUPPORTED;
     const size_t smem = wbytes + warps * per_warp;
     auto kern = const_update_kernel<T, NF, W, SPATIAL>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -104,16 +119,19 @@ static int launch_typed(const commet_model *m, int64_t n_qp, const void *F, void
     const int64_t want = (n_tiles + warps - 1) / warps;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count() * per_sm));
     kern<<<grid, warps * 32, smem, s>>>((const T *)m->d_weights, m->lay, kc, n_qp, (const T *)F, (T *)psi, (T *)P,
-                                        (T *)A, status, (T *)dN_out, qstride);
+                                        (T *)A, status, (T *)dN_out, qstride, wcount);
     return cudaGetLastError() == cudaSuccess ? COMMET_OK : COMMET_ERR_CUDA;
 }
 
 template <typename T, bool SPATIAL>
 static int dispatch(const commet_model *m, int64_t n_qp, const void *F, void *psi, void *P, void *A,
                     int32_t *status, cudaStream_t s, void *dN_out) {
+    if (m->inner != COMMET_INNER_MICNN) return dispatch_closed<T, SPATIAL>(m, n_qp, F, psi, P, A, status, s, dN_out);
     const int nf = m->kp.nf, W = m->W;
 #define COMMET_CASE(NF_, W_) \
     if (nf == NF_ && W == W_) return launch_typed<T, NF_, W_, SPATIAL>(m, n_qp, F, psi, P, A, status, s, dN_out);
+    COMMET_CASE(0, 4)
+    COMMET_CASE(0, 8)
     COMMET_CASE(0, 16)
     COMMET_CASE(0, 32)
     COMMET_CASE(0, 64)

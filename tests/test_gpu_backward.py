@@ -49,7 +49,8 @@ def oracle_dtheta_abs(spec, F, G):
 
 CASES = [(wl.KIN_RAW, 2, 32, 3, 0.0, 3001), (wl.KIN_ISO_SHIFTED, 0, 16, 2, 10.0, 2049),
          (wl.KIN_RAW, 1, 16, 4, 1.0, 777), (wl.KIN_RAW, 2, 32, 1, 2.0, 513), (wl.KIN_ISO_SHIFTED, 0, 32, 3, 5.0, 5),
-         (wl.KIN_POLYCONVEX, 0, 16, 3, 0.0, 2500), (wl.KIN_POLYCONVEX, 0, 32, 2, 4.0, 301)]
+         (wl.KIN_POLYCONVEX, 0, 16, 3, 0.0, 2500), (wl.KIN_POLYCONVEX, 0, 32, 2, 4.0, 301),
+         (wl.KIN_POLYCONVEX, 0, 4, 3, 0.0, 777), (wl.KIN_ISO_SHIFTED, 0, 8, 2, 3.0, 1500)]
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])

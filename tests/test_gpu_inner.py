@@ -1,0 +1,146 @@
+"""GPU parity of the inner functions other than the MICNN: the CANN of eq. cann-def and
+the closed-form Gent-Thomas energy of eq. gt, in both output forms, against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import workload as wl
+from tests.parity import TOL, assert_close, cm_to_pm, pm_to_cm
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DT = {"f64": torch.float64, "f32": torch.float32}
+
+ALL_KINDS = np.array([[wl.CANN_F0_ID, 1, wl.CANN_F2_LINEAR], [wl.CANN_F0_ID, 2, wl.CANN_F2_EXP],
+                      [wl.CANN_F0_MACAULAY, 3, wl.CANN_F2_LINEAR], [wl.CANN_F0_ABS, 2, wl.CANN_F2_LOG],
+                      [wl.CANN_F0_ABS, 1, wl.CANN_F2_EXP], [wl.CANN_F0_MACAULAY, 2, wl.CANN_F2_LOG]],
+                     dtype=np.int32)
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2510_00884_gb300 as p
+    p.build()
+    return p
+
+
+def specs():
+    rng = np.random.Generator(np.random.PCG64(600))
+    return {
+        "cann_paper_poly": wl.make_cann(rng),
+        "cann_all_raw2": wl.make_cann(rng, wl.KIN_RAW, 2, kinds=ALL_KINDS, kappa=1.0, std=0.005),
+        "cann_all_iso_shift": wl.make_cann(rng, wl.KIN_ISO_SHIFTED, 0, kinds=ALL_KINDS, kappa=5.0, std=0.2,
+                                           stress_free=True),
+        "cann_all_raw1": wl.make_cann(rng, wl.KIN_RAW, 1, kinds=ALL_KINDS[:5], kappa=0.0, std=0.005),
+        "gent_thomas": wl.GentThomasSpec(),
+    }
+
+
+SPECS = specs()
+
+
+def check(pkg, spec, F, prec, what):
+    Fd = pm_to_cm(F, DT[prec])
+    Fin = cm_to_pm(Fd).astype(np.float64)
+    m = pkg.Model(spec, prec)
+    psi, P, A, st = m.const_update(Fd, status=True)
+    psi_s, tau, c, st_s = m.const_update_spatial(Fd, status=True)
+    torch.cuda.synchronize()
+    assert int(st[0]) == 0 and int(st_s[0]) == 0
+    psi_r, P_r, A_r = oracle.const_update(oracle.OracleModel(spec), Fin)
+    scale = None
+    if spec.stress_free and prec != "f64":
+        import dataclasses
+        _, scale, _ = oracle.const_update(oracle.OracleModel(dataclasses.replace(spec, stress_free=False)), Fin)
+    assert_close(cm_to_pm(P), P_r, TOL[prec], f"{what} P", scale)
+    assert_close(cm_to_pm(A), A_r, TOL[prec], f"{what} A")
+    assert_close(psi.cpu().numpy()[:, None], psi_r[:, None], TOL[prec], f"{what} psi")
+    tau_r, c_r = oracle.push_forward(Fin, P_r, A_r)
+    tscale = None if scale is None else oracle.push_forward(Fin, scale, None)[0]
+    assert_close(cm_to_pm(tau), tau_r, TOL[prec], f"{what} tau", tscale)
+    assert_close(cm_to_pm(c), c_r, TOL[prec], f"{what} c")
+    assert torch.equal(psi, psi_s)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("name", list(SPECS))
+def test_inner_vs_oracle(pkg, name, prec):
+    rng = np.random.Generator(np.random.PCG64(610))
+    F = wl.random_F(rng, 2053, 0.15)
+    check(pkg, SPECS[name], F, prec, f"{name} {prec}")
+
+
+def test_cann_parameter_count_and_stress_free(pkg):
+    spec = SPECS["cann_paper_poly"]
+    m = pkg.Model(spec, "f64")
+    assert m.n_params == 24
+    F = torch.eye(3, dtype=torch.float64).reshape(9, 1).repeat(1, 17).cuda().contiguous()
+    _, P, _ = m.const_update(F)
+    assert P.abs().max().item() < 1e-15
+
+
+def test_cann_log_domain_is_reported(pkg):
+    """-ln(1 - w1 y) with w1 y >= 1 has no value: such points are reported and NaN."""
+    w = np.zeros((3, 1, 2))
+    w[0, 0] = (2.0, 1.0)
+    spec = wl.CannSpec(d=3, kin=wl.KIN_ISO_SHIFTED, fibres=np.zeros((0, 3)), n=1,
+                       kinds=np.array([[wl.CANN_F0_ID, 1, wl.CANN_F2_LOG]], dtype=np.int32), w=w)
+    F = np.tile(np.eye(3).ravel(), (8, 1))
+    F[3] = np.diag([2.0, 1.0, 1.0]).ravel()  # Ibar1 - 3 ~ 0.78: w1 y > 1
+    m = pkg.Model(spec, "f64")
+    psi, P, A, st = m.const_update(pm_to_cm(F, torch.float64), status=True)
+    torch.cuda.synchronize()
+    assert int(st[0]) == 1 and int(st[1]) == 3
+    assert torch.isnan(P[:, 3]).all() and torch.isnan(psi[3])
+    good = [q for q in range(8) if q != 3]
+    assert torch.isfinite(P[:, good]).all()
+
+
+def test_unsupported_paths(pkg):
+    from paper_2510_00884_gb300 import _lib
+    spec = SPECS["cann_paper_poly"]
+    with pytest.raises(_lib.CommetError) as ei:
+        pkg.Model(spec, "bf16")
+    assert ei.value.code == _lib.ERR_UNSUPPORTED
+    m = pkg.Model(spec, "f64")
+    F = torch.eye(3, dtype=torch.float64).reshape(9, 1).repeat(1, 8).cuda().contiguous()
+    with pytest.raises(_lib.CommetError) as ei:
+        m.backward(F, torch.zeros_like(F))
+    assert ei.value.code == _lib.ERR_UNSUPPORTED
+    mesh = wl.structured_mesh(1)
+    gm = pkg.Mesh(mesh.X, mesh.conn, want_csr=True)
+    u = torch.zeros(3, mesh.n_nodes, dtype=torch.float64, device="cuda")
+    with pytest.raises(_lib.CommetError) as ei:
+        pkg.newton_assemble(m, gm, u)
+    assert ei.value.code == _lib.ERR_UNSUPPORTED
+    bad = wl.GentThomasSpec(kin=wl.KIN_ISO_SHIFTED)
+    with pytest.raises(_lib.CommetError) as ei:
+        pkg.Model(bad, "f64")
+    assert ei.value.code == _lib.ERR_INVALID_ARG
+    kinds = np.array([[0, 4, 0]], dtype=np.int32)  # exponent 4 is not in the menu
+    with pytest.raises(_lib.CommetError) as ei:
+        pkg.Model(wl.CannSpec(d=3, kin=wl.KIN_POLYCONVEX, fibres=np.zeros((0, 3)), n=1, kinds=kinds,
+                              w=np.ones((3, 1, 2))), "f64")
+    assert ei.value.code == _lib.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("name", ["cann_polyconvex", "gent_thomas"])
+def test_full_size_sampled(pkg, name):
+    """The 64^3 CANN and Gent-Thomas workloads in FP64 as the bench launches them; sampled
+    points (including the last) against the oracle."""
+    w = wl.workload_cann() if name == "cann_polyconvex" else wl.workload_gent_thomas()
+    spec = w["model"]
+    m = pkg.Model(spec, "f64")
+    F = pm_to_cm(w["F"], torch.float64)
+    _, P, A, st = m.const_update(F, status=True)
+    torch.cuda.synchronize()
+    assert int(st[0]) == 0
+    n = w["F"].shape[0]
+    rng = np.random.Generator(np.random.PCG64(620))
+    qp = np.sort(rng.choice(n, 512, replace=False))
+    qp[-1] = n - 1
+    _, P_r, A_r = oracle.const_update(oracle.OracleModel(spec), w["F"][qp])
+    idx = torch.from_numpy(qp).cuda()
+    assert_close(cm_to_pm(P[:, idx]), P_r, 1e-12, f"{name} P")
+    assert_close(cm_to_pm(A[:, idx]), A_r, 1e-12, f"{name} A")

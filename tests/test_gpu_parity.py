@@ -93,6 +93,9 @@ CASES = [
     # a biased, shifted variant with a volumetric penalty
     (wl.KIN_POLYCONVEX, 0, 16, 3, 0.0, False, False, 3001),
     (wl.KIN_POLYCONVEX, 0, 32, 2, 5.0, True, True, 1025),
+    # the narrow networks of the paper's model-size study (App. D)
+    (wl.KIN_POLYCONVEX, 0, 4, 2, 0.0, False, False, 1001),
+    (wl.KIN_ISO_SHIFTED, 0, 8, 4, 5.0, True, False, 2049),
 ]
 
 

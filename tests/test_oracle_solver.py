@@ -50,6 +50,23 @@ def test_dirichlet_system_equals_the_reduced_system():
     assert np.abs(x[free] - xr).max() <= 1e-12 * np.abs(xr).max()
 
 
+def test_prescribed_increment_moves_the_fixed_dofs():
+    """With delta, the solution of the modified system is the solution of K du = r over the
+    free dofs with du_c = -delta_c substituted (the affine constraint)."""
+    mesh, r, K = small_system(3)
+    dofs, vals = wl.twist_dirichlet(mesh, 0.05)
+    fixed = np.zeros(r.size, dtype=bool)
+    fixed[dofs] = True
+    delta = np.zeros(r.size)
+    delta[dofs] = vals
+    Kv, rb = solver.apply_dirichlet(K.indptr, K.indices, K.data, r, fixed, delta=delta)
+    du = spla.spsolve(sp.csr_matrix((Kv, K.indices, K.indptr), shape=K.shape).tocsc(), rb)
+    assert np.abs(du[fixed] + delta[fixed]).max() <= 1e-15 * np.abs(delta).max()
+    free = ~fixed
+    ref = spla.spsolve(K[free][:, free].tocsc(), r[free] - K[free][:, fixed] @ (-delta[fixed]))
+    assert np.abs(du[free] - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
 def test_pcg_matches_the_direct_solve():
     mesh, r, K = small_system(2)
     dofs, _ = wl.twist_dirichlet(mesh, 0.1)
