@@ -12,7 +12,7 @@
 namespace commet {
 
 constexpr int kMaxFibres = 2;
-constexpr int kRedBlocks = 1024;  // partial sums per reduction slot of the solver
+constexpr int kRedBlocks = 4096;  // partial sums per reduction slot of the solver
 constexpr int kRedDoubles = 16 + 2 * kRedBlocks;
 constexpr int kMaxD = 3 + 2 * kMaxFibres;
 

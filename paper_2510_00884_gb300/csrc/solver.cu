@@ -29,7 +29,7 @@ constexpr int kChunk = 16;  // iterations between host checks of the stopping wo
 // reduction array layout (doubles): scalars, then partial sums [2][kRedBlocks]
 enum { S_RZ = 0, S_PAP, S_RR, S_BB, S_ALPHA, S_BETA, S_DONE, S_ITERS, S_RTOL2, S_COUNT = 16 };
 
-int red_blocks() { return std::min(kRedBlocks, 4 * sm_count()); }
+int red_blocks() { return std::min(kRedBlocks, 16 * sm_count()); }
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -202,33 +202,32 @@ __global__ void cg_start_kernel(double *__restrict__ red, int nb, double rtol) {
     }
 }
 
-// Ap = K p, one warp per node (its 3 rows share one column pattern); partials of p.Ap
+// Ap = K p with 4 lanes per row (8 rows per warp). GB300 charges every FP64 warp
+// instruction in full, so the row sums are split where they cost fewest FP64 instructions:
+// about nnz / 32 DFMAs plus two shuffle additions per 8 rows (a warp per row would spend
+// 5 shuffle additions per row on its reduction). The 4 lanes of a row read 4 consecutive
+// values (one 32-byte sector). Partial sums of p.Ap per block.
 template <typename T>
-__global__ void cg_spmv_kernel(int64_t n_nodes, const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+__global__ void cg_spmv_kernel(int64_t n_rows, const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                                const T *__restrict__ K_vals, const T *__restrict__ p, T *__restrict__ Ap,
                                double *__restrict__ red) {
     if (red[S_DONE] != 0.0) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31, sub = lane & 3;
+    const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 2;  // rows per grid pass
     double pap = 0.0;
-    for (int64_t nd = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; nd < n_nodes; nd += warps) {
-        const int64_t r0 = rowptr[3 * nd], len = rowptr[3 * nd + 1] - r0;
-        const int64_t r1 = rowptr[3 * nd + 1], r2 = rowptr[3 * nd + 2];
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-        for (int64_t k = lane; k < len; k += 32) {
-            const double pc = (double)p[col[r0 + k]];
-            a0 += (double)K_vals[r0 + k] * pc;
-            a1 += (double)K_vals[r1 + k] * pc;
-            a2 += (double)K_vals[r2 + k] * pc;
+    // base is uniform over the warp, so every lane reaches the shuffles together
+    for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 8; base < n_rows; base += stride) {
+        const int64_t row = base + (lane >> 2);
+        double a = 0.0;
+        if (row < n_rows) {
+            const int64_t e = rowptr[row + 1];
+            for (int64_t k = rowptr[row] + sub; k < e; k += 4) a += (double)K_vals[k] * (double)p[col[k]];
         }
-        a0 = warp_sum(a0);
-        a1 = warp_sum(a1);
-        a2 = warp_sum(a2);
-        if (lane == 0) {
-            Ap[3 * nd] = (T)a0;
-            Ap[3 * nd + 1] = (T)a1;
-            Ap[3 * nd + 2] = (T)a2;
-            pap += a0 * (double)p[3 * nd] + a1 * (double)p[3 * nd + 1] + a2 * (double)p[3 * nd + 2];
+        a += __shfl_xor_sync(0xffffffffu, a, 1);
+        a += __shfl_xor_sync(0xffffffffu, a, 2);
+        if (sub == 0 && row < n_rows) {
+            Ap[row] = (T)a;
+            pap += a * (double)p[row];
         }
     }
     block_sum2(pap, 0.0, red + S_COUNT);
@@ -295,7 +294,7 @@ int cg_typed(const commet_mesh *mesh, const void *K_vals_v, const void *b_v, voi
     T *r = (T *)ws, *z = r + n, *p = z + n, *Ap = p + n, *dinv = Ap + n;
     double *red = mesh->d_red;
     const int nb = red_blocks();
-    const int spmv_blocks = (int)std::min<int64_t>(nb, (mesh->n_nodes * 32 + kSolveThreads - 1) / kSolveThreads);
+    const int spmv_blocks = (int)std::min<int64_t>(nb, (n * 4 + kSolveThreads - 1) / kSolveThreads);
     const int vec_blocks = (int)std::min<int64_t>(nb, (n + kSolveThreads - 1) / kSolveThreads);
     cg_init_kernel<T><<<vec_blocks, kSolveThreads, 0, s>>>(n, mesh->d_rowptr, mesh->d_col, K_vals, b, x, r, z, p,
                                                            dinv, red);
@@ -306,8 +305,8 @@ int cg_typed(const commet_mesh *mesh, const void *K_vals_v, const void *b_v, voi
     for (int it0 = 0; it0 < max_iter; it0 += kChunk) {
         const int m = std::min(kChunk, max_iter - it0);
         for (int k = 0; k < m; ++k) {
-            cg_spmv_kernel<T><<<spmv_blocks, kSolveThreads, 0, s>>>(mesh->n_nodes, mesh->d_rowptr, mesh->d_col,
-                                                                    K_vals, p, Ap, red);
+            cg_spmv_kernel<T><<<spmv_blocks, kSolveThreads, 0, s>>>(n, mesh->d_rowptr, mesh->d_col, K_vals, p, Ap,
+                                                                    red);
             cg_alpha_kernel<<<1, kSolveThreads, 0, s>>>(red, spmv_blocks);
             cg_update_kernel<T><<<vec_blocks, kSolveThreads, 0, s>>>(n, x, r, z, p, Ap, dinv, red);
             cg_beta_kernel<<<1, kSolveThreads, 0, s>>>(red, vec_blocks);
