@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "commet_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-INNER_MICNN, INNER_GENT_THOMAS, INNER_HGO, INNER_CANN = 0, 1, 2, 3
+INNER_MICNN, INNER_GENT_THOMAS, INNER_HGO, INNER_CANN, INNER_ICKAN = 0, 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:
@@ -39,7 +39,10 @@ class _Model(C.Structure):
                 ("a", C.POINTER(C.c_double)), ("b", C.POINTER(C.c_double)),
                 ("kappa", C.c_double), ("stress_free", C.c_int),
                 ("mu", C.c_double), ("k1", C.c_double), ("k2", C.c_double),
-                ("cann_n", C.c_int), ("cann_kind", C.POINTER(C.c_int)), ("cann_w", C.POINTER(C.c_double))]
+                ("cann_n", C.c_int), ("cann_kind", C.POINTER(C.c_int)), ("cann_w", C.POINTER(C.c_double)),
+                ("kan_R", C.c_int), ("kan_deg", C.c_int), ("kan_G", C.c_int), ("kan_w", C.POINTER(C.c_int)),
+                ("kan_lo", C.POINTER(C.c_double)), ("kan_hi", C.POINTER(C.c_double)),
+                ("kan_par", C.POINTER(C.c_double))]
 
 
 _lib = None
@@ -60,6 +63,8 @@ def _load():
         _lib.oracle_compute_F.argtypes = [i64, i32, d, d, d]
         _lib.oracle_elem_assemble.argtypes = [i64, i32, d, d, d, d, d]
         _lib.oracle_scatter_residual.argtypes = [i64, i32, d, i64, d]
+        _lib.oracle_kan_basis.argtypes = [P(_Model), C.c_int, C.c_double, d, d, d]
+        _lib.oracle_kan_basis.restype = C.c_int
         _lib.oracle_push_forward.argtypes = [d, d, d, d, d]
         _lib.oracle_elem_assemble_spatial.argtypes = [i64, i32, d, d, d, d, d, d]
         _lib.oracle_scatter_csr.argtypes = [i64, i32, d, i64, P(C.c_int64), i32, d]
@@ -86,10 +91,11 @@ class OracleModel:
                  fibres=None, kappa: float | None = None, mu=1.0, k1=2.0, k2=0.5,
                  stress_free: bool | None = None):
         self.kind = self.cw = None
+        self.kan = None
         cann_n = 0
         if spec is not None and getattr(spec, "inner_name", "micnn") != "micnn":
             # closed-form and CANN inner functions: no network arrays
-            inner = {"cann": INNER_CANN, "gent_thomas": INNER_GENT_THOMAS}[spec.inner_name]
+            inner = {"cann": INNER_CANN, "gent_thomas": INNER_GENT_THOMAS, "ickan": INNER_ICKAN}[spec.inner_name]
             kin = spec.kin if kin is None else kin
             fibres = spec.fibres if fibres is None else fibres
             kappa = spec.kappa if kappa is None else kappa
@@ -101,6 +107,10 @@ class OracleModel:
                 cann_n = int(spec.n)
                 self.kind = np.ascontiguousarray(spec.kinds, dtype=np.int32).reshape(cann_n, 3)
                 self.cw = _c64(spec.w).reshape(d, cann_n, 2)
+            if spec.inner_name == "ickan":
+                self.kan = {"w": np.ascontiguousarray(spec.widths, dtype=np.int32), "lo": _c64(spec.lo),
+                            "hi": _c64(spec.hi), "par": _c64(spec.params)}
+                self.kan_meta = (len(spec.widths) - 1, int(spec.degree), int(spec.G))
         elif spec is not None:
             d, W, L = spec.d, spec.W, spec.L
             kin = spec.kin if kin is None else kin
@@ -125,6 +135,11 @@ class OracleModel:
                         mu=float(mu), k1=float(k1), k2=float(k2), cann_n=cann_n,
                         cann_kind=self.kind.ctypes.data_as(C.POINTER(C.c_int)) if self.kind is not None else None,
                         cann_w=_dp(self.cw))
+        if self.kan is not None:
+            R, k, G = self.kan_meta
+            self.s.kan_R, self.s.kan_deg, self.s.kan_G = R, k, G
+            self.s.kan_w = self.kan["w"].ctypes.data_as(C.POINTER(C.c_int))
+            self.s.kan_lo, self.s.kan_hi, self.s.kan_par = _dp(self.kan["lo"]), _dp(self.kan["hi"]), _dp(self.kan["par"])
 
 
 def const_update(model: OracleModel, F: np.ndarray, want_A: bool = True):
@@ -162,6 +177,15 @@ def inner(model: OracleModel, K: np.ndarray):
     d2N = np.zeros((d, d))
     lib.oracle_inner(C.byref(model.s), _dp(K), _dp(N), _dp(dN), _dp(d2N))
     return N[0], dN, d2N
+
+
+def kan_basis(model: OracleModel, r: int, x: float):
+    """B-spline basis functions of ICKAN layer r at x and their first and second derivatives."""
+    lib = _load()
+    nb = model.kan_meta[2] + model.kan_meta[1]
+    B, dB, d2B = np.zeros(nb + 8), np.zeros(nb + 8), np.zeros(nb + 8)
+    n = lib.oracle_kan_basis(C.byref(model.s), r, float(x), _dp(B), _dp(dB), _dp(d2B))
+    return B[:n], dB[:n], d2B[:n]
 
 
 def hex8_gradients(Xe: np.ndarray):

@@ -43,7 +43,7 @@
 /* ------------------------------------------------------------------ model */
 
 enum { OR_KIN_ISO_SHIFTED = 0, OR_KIN_RAW = 1, OR_KIN_POLYCONVEX = 2 };
-enum { OR_INNER_MICNN = 0, OR_INNER_GENT_THOMAS = 1, OR_INNER_HGO = 2, OR_INNER_CANN = 3 };
+enum { OR_INNER_MICNN = 0, OR_INNER_GENT_THOMAS = 1, OR_INNER_HGO = 2, OR_INNER_CANN = 3, OR_INNER_ICKAN = 4 };
 enum { OR_F0_ID = 0, OR_F0_MACAULAY = 1, OR_F0_ABS = 2 };
 enum { OR_F2_LINEAR = 0, OR_F2_EXP = 1, OR_F2_LOG = 2 };
 
@@ -63,6 +63,8 @@ enum { OR_F2_LINEAR = 0, OR_F2_EXP = 1, OR_F2_LOG = 2 };
  *     (Ibar1, Ibar2, J)  (eq. gt).
  *   OR_INNER_HGO: N = mu/2 (K0 - 3) + sum_f k1/(2 k2) (exp(k2 (K_{3+f} - 1)^2) - 1)
  *     on raw kinematics (Neo-Hookean plus exponential fibre terms).
+ *   OR_INNER_ICKAN: the KAN of App. B, z^(r)_i = sum_j phi_rij(z^(r-1)_j), N = z^(R),
+ *     phi = w_s psi, psi = sum_l c_l B_l,k (B-splines by the recursion of App. B).
  *   OR_INNER_CANN: eq. cann-def, N = sum_m sum_k w2_mk f2_k(f1_k(f0_k(K_m)); w1_mk) with
  *     term k's functions from the menus of eq. cann-fs: f0 in {x, <x>, |x|}, f1 = x^p
  *     (p = 1, 2, 3), f2 in {w1 y, exp(w1 y) - 1, -ln(1 - w1 y)}.
@@ -86,6 +88,13 @@ typedef struct {
     int cann_n;             /* CANN: terms per input */
     const int *cann_kind;   /* CANN: [n][3] (f0, p, f2) */
     const double *cann_w;   /* CANN: [d][n][2] (w1, w2) */
+    /* ICKAN: R spline layers of widths kw[0] = d, kw[1..R-1], kw[R] = 1; B-splines of degree
+     * kdeg on G uniform intervals of [lo_r, hi_r] per layer (knots extended by kdeg on each
+     * side, nb = G + kdeg basis functions); per spline (layer r, output i, input j, in that
+     * order) the weight w_s then the nb control points. */
+    int kan_R, kan_deg, kan_G;
+    const int *kan_w;
+    const double *kan_lo, *kan_hi, *kan_par;
 } oracle_model;
 
 #define OR_MAXD 16
@@ -473,8 +482,122 @@ static void cann(const oracle_model *m, const double *K, double *N, double *dN, 
     *N = s;
 }
 
+/*
+ * B-spline basis of degree k on the knots t[0..nk-1] at x by the recursion of App. B: the
+ * zero-degree indicators of [t_l, t_l+1), then
+ *   B_l,q(x) = (x - t_l) / (t_l+q - t_l) B_l,q-1(x) + (t_l+q+1 - x) / (t_l+q+1 - t_l+1) B_l+1,q-1(x),
+ * with the first and second x-derivatives of the same recursion by the product rule:
+ *   B'_l,q  = [B_l,q-1 + (x - t_l) B'_l,q-1] / (t_l+q - t_l) + [-B_l+1,q-1 + (t_l+q+1 - x) B'_l+1,q-1] / (t_l+q+1 - t_l+1)
+ *   B''_l,q = [2 B'_l,q-1 + (x - t_l) B''_l,q-1] / (.)     + [-2 B'_l+1,q-1 + (t_l+q+1 - x) B''_l+1,q-1] / (.)
+ * B, dB, d2B receive the nk - 1 - k basis functions of degree k.
+ */
+#define OR_MAXKNOTS 160
+static void bspline_basis(int k, const double *t, int nk, double x, double *B, double *dB, double *d2B) {
+    double b[OR_MAXKNOTS], db[OR_MAXKNOTS], d2b[OR_MAXKNOTS];
+    for (int l = 0; l + 1 < nk; ++l) {
+        b[l] = (t[l] <= x && x < t[l + 1]) ? 1.0 : 0.0;
+        db[l] = 0.0;
+        d2b[l] = 0.0;
+    }
+    for (int q = 1; q <= k; ++q)
+        for (int l = 0; l + q + 1 < nk; ++l) {
+            const double a1 = 1.0 / (t[l + q] - t[l]), a2 = 1.0 / (t[l + q + 1] - t[l + 1]);
+            const double u1 = (x - t[l]) * a1, u2 = (t[l + q + 1] - x) * a2;
+            const double nb = u1 * b[l] + u2 * b[l + 1];
+            const double ndb = a1 * b[l] + u1 * db[l] - a2 * b[l + 1] + u2 * db[l + 1];
+            const double nd2b = 2.0 * a1 * db[l] + u1 * d2b[l] - 2.0 * a2 * db[l + 1] + u2 * d2b[l + 1];
+            b[l] = nb;
+            db[l] = ndb;
+            d2b[l] = nd2b;
+        }
+    for (int l = 0; l + 1 + k < nk; ++l) {
+        B[l] = b[l];
+        dB[l] = db[l];
+        d2B[l] = d2b[l];
+    }
+}
+
+/* Knots of ICKAN layer r: t_m = lo + (m - k) h, h = (hi - lo) / G, m = 0 .. G + 2k. */
+static int kan_knots(const oracle_model *m, int r, double *t) {
+    const int k = m->kan_deg, G = m->kan_G;
+    const double h = (m->kan_hi[r] - m->kan_lo[r]) / G;
+    for (int q = 0; q <= G + 2 * k; ++q) t[q] = m->kan_lo[r] + (q - k) * h;
+    return G + 2 * k + 1;
+}
+
+/* ICKAN value, gradient and Hessian by forward propagation of (z, dz/dK, d2z/dK2) through the
+ * spline layers (App. B): z_i = sum_j phi_ij(z_j), dz_i = sum_j phi'_ij dz_j,
+ * d2z_i = sum_j [phi''_ij dz_j (x) dz_j + phi'_ij d2z_j]. */
+static void ickan(const oracle_model *m, const double *K, double *N, double *dN, double *d2N) {
+    const int d = m->d, R = m->kan_R, k = m->kan_deg, nb = m->kan_G + k;
+    int wmax = d;
+    for (int r = 0; r <= R; ++r) wmax = m->kan_w[r] > wmax ? m->kan_w[r] : wmax;
+    double *z = calloc((size_t)wmax, sizeof(double)), *dz = calloc((size_t)wmax * d, sizeof(double));
+    double *d2z = calloc((size_t)wmax * d * d, sizeof(double));
+    double *zn = calloc((size_t)wmax, sizeof(double)), *dzn = calloc((size_t)wmax * d, sizeof(double));
+    double *d2zn = calloc((size_t)wmax * d * d, sizeof(double));
+    double t[OR_MAXKNOTS], B[OR_MAXKNOTS], dB[OR_MAXKNOTS], d2B[OR_MAXKNOTS];
+    for (int j = 0; j < d; ++j) {
+        z[j] = K[j];
+        dz[j * d + j] = 1.0;
+    }
+    const double *par = m->kan_par;
+    for (int r = 0; r < R; ++r) {
+        const int nin = m->kan_w[r], nout = m->kan_w[r + 1];
+        const int nk = kan_knots(m, r, t);
+        for (int i = 0; i < nout; ++i) {
+            zn[i] = 0.0;
+            for (int a = 0; a < d; ++a) dzn[i * d + a] = 0.0;
+            for (int a = 0; a < d * d; ++a) d2zn[i * d * d + a] = 0.0;
+            for (int j = 0; j < nin; ++j) {
+                const double ws = par[0], *c = par + 1;
+                par += 1 + nb;
+                bspline_basis(k, t, nk, z[j], B, dB, d2B);
+                double f = 0.0, f1 = 0.0, f2 = 0.0;
+                for (int l = 0; l < nb; ++l) {
+                    f += c[l] * B[l];
+                    f1 += c[l] * dB[l];
+                    f2 += c[l] * d2B[l];
+                }
+                f *= ws;
+                f1 *= ws;
+                f2 *= ws;
+                zn[i] += f;
+                for (int a = 0; a < d; ++a) dzn[i * d + a] += f1 * dz[j * d + a];
+                for (int a = 0; a < d; ++a)
+                    for (int b = 0; b < d; ++b)
+                        d2zn[i * d * d + a * d + b] += f2 * dz[j * d + a] * dz[j * d + b] + f1 * d2z[j * d * d + a * d + b];
+            }
+        }
+        for (int i = 0; i < nout; ++i) {
+            z[i] = zn[i];
+            for (int a = 0; a < d; ++a) dz[i * d + a] = dzn[i * d + a];
+            for (int a = 0; a < d * d; ++a) d2z[i * d * d + a] = d2zn[i * d * d + a];
+        }
+    }
+    *N = z[0];
+    for (int a = 0; a < d; ++a) dN[a] = dz[a];
+    for (int a = 0; a < d * d; ++a) d2N[a] = d2z[a];
+    free(z);
+    free(dz);
+    free(d2z);
+    free(zn);
+    free(dzn);
+    free(d2zn);
+}
+
+/* Exported for the spline pins: basis functions of ICKAN layer r at x. */
+int oracle_kan_basis(const oracle_model *m, int r, double x, double *B, double *dB, double *d2B) {
+    double t[OR_MAXKNOTS];
+    const int nk = kan_knots(m, r, t);
+    bspline_basis(m->kan_deg, t, nk, x, B, dB, d2B);
+    return nk - 1 - m->kan_deg;
+}
+
 static void inner_eval(const oracle_model *m, const double *K, double *N, double *dN, double *d2N) {
-    if (m->inner == OR_INNER_CANN)
+    if (m->inner == OR_INNER_ICKAN)
+        ickan(m, K, N, dN, d2N);
+    else if (m->inner == OR_INNER_CANN)
         cann(m, K, N, dN, d2N);
     else if (m->inner == OR_INNER_GENT_THOMAS)
         gent_thomas(K, N, dN, d2N);

@@ -174,6 +174,42 @@ def cann_forward(spec, K: list) -> HD:
     return out
 
 
+def _bspline_hd(k, t, x: HD):
+    """Value-only B-spline basis of degree k on knots t at a hyper-dual x (recursion of App. B);
+    the indicators are evaluated at the real part (piecewise polynomial)."""
+    nk = len(t)
+    b = [HD(np.where((t[l] <= x.r) & (x.r < t[l + 1]), 1.0, 0.0)) for l in range(nk - 1)]
+    for q in range(1, k + 1):
+        b = [(x - t[l]) * (1.0 / (t[l + q] - t[l])) * b[l] + (t[l + q + 1] - x) * (1.0 / (t[l + q + 1] - t[l + 1])) * b[l + 1]
+             for l in range(nk - q - 1)]
+    return b
+
+
+def ickan_forward(spec, K: list) -> HD:
+    """The KAN of App. B, value only: z_i = sum_j w_s sum_l c_l B_l,k(z_j)."""
+    R, k, G = len(spec.widths) - 1, spec.degree, spec.G
+    nb = G + k
+    z = list(K)
+    off = 0
+    for r in range(R):
+        h = (spec.hi[r] - spec.lo[r]) / G
+        t = [spec.lo[r] + (m - k) * h for m in range(G + 2 * k + 1)]
+        zn = []
+        for i in range(spec.widths[r + 1]):
+            acc = HD(0.0)
+            for j in range(spec.widths[r]):
+                ws, c = spec.params[off], spec.params[off + 1: off + 1 + nb]
+                off += 1 + nb
+                B = _bspline_hd(k, t, z[j])
+                psi = HD(0.0)
+                for l in range(nb):
+                    psi = psi + float(c[l]) * B[l]
+                acc = acc + float(ws) * psi
+            zn.append(acc)
+        z = zn
+    return z[0]
+
+
 def psi_hd(spec, F9: list, inner=None) -> HD:
     """Psi(F) = N(K(F)) + kappa (J - 1)^2 (stress-free shift not included).
     inner(K_list) -> HD replaces the MICNN when given; CANN specs use eq. cann-def."""
@@ -182,6 +218,8 @@ def psi_hd(spec, F9: list, inner=None) -> HD:
         N = inner(K)
     elif getattr(spec, "inner_name", "micnn") == "cann":
         N = cann_forward(spec, K)
+    elif getattr(spec, "inner_name", "micnn") == "ickan":
+        N = ickan_forward(spec, K)
     else:
         N = micnn_forward(spec, hd_stack(K))
     return N + spec.kappa * (J - 1.0) * (J - 1.0)

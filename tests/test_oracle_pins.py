@@ -750,3 +750,68 @@ def test_gent_thomas_spec_is_eq_gt():
     for q in range(3):
         psi_h, P_h, A_h = hdm.exact_P_A(spec, F[q], inner=gt)
         assert rel(P[q], P_h) < 1e-12 and rel(A[q], A_h) < 1e-12
+
+
+# ------------------------------------------------------------------ ICKAN (App. B)
+
+@pytest.fixture(scope="module")
+def kan_spec():
+    rng = np.random.Generator(np.random.PCG64(50))
+    return wl.make_ickan(rng, widths=(3, 3, 2, 1), degree=4, G=12)
+
+
+def test_bspline_partition_of_unity_and_linear_reproduction(kan_spec):
+    """On [lo, hi] the basis sums to 1 and, with the Greville abscissae as control points,
+    reproduces x itself (psi = x, psi' = 1, psi'' = 0): properties of the recursion of App. B."""
+    m = oracle.OracleModel(kan_spec)
+    k, G = kan_spec.degree, kan_spec.G
+    lo, hi = kan_spec.lo[0], kan_spec.hi[0]
+    h = (hi - lo) / G
+    t = lo + (np.arange(G + 2 * k + 1) - k) * h
+    grev = np.array([t[l + 1: l + k + 1].mean() for l in range(G + k)])
+    for x in np.linspace(lo, hi - 1e-9, 37):
+        B, dB, d2B = oracle.kan_basis(m, 0, x)
+        assert abs(B.sum() - 1.0) < 1e-14 and abs(dB.sum()) < 1e-11 and abs(d2B.sum()) < 1e-9
+        assert abs(grev @ B - x) < 1e-14
+        assert abs(grev @ dB - 1.0) < 1e-12 and abs(grev @ d2B) < 1e-9
+
+
+def test_bspline_derivatives_against_hyperdual(kan_spec):
+    m = oracle.OracleModel(kan_spec)
+    k, G = kan_spec.degree, kan_spec.G
+    lo, hi = kan_spec.lo[1], kan_spec.hi[1]
+    h = (hi - lo) / G
+    t = list(lo + (np.arange(G + 2 * k + 1) - k) * h)
+    for x in (lo - 0.7 * k * h, lo + 0.31 * h, 0.5 * (lo + hi), hi - 0.17 * h, hi + 0.5 * h):
+        B, dB, d2B = oracle.kan_basis(m, 1, x)
+        Bh = hdm._bspline_hd(k, t, hdm.HD(x, 1.0, 1.0, 0.0))
+        for l in range(B.size):
+            assert abs(B[l] - float(Bh[l].r)) < 1e-14
+            assert abs(dB[l] - float(Bh[l].e1)) < 1e-10 * max(1.0, abs(dB[l]))
+            assert abs(d2B[l] - float(Bh[l].e12)) < 1e-8 * max(1.0, abs(d2B[l]))
+
+
+@pytest.mark.parametrize("kin", [wl.KIN_POLYCONVEX, wl.KIN_ISO_SHIFTED])
+def test_ickan_exact_derivatives(kin):
+    rng = np.random.Generator(np.random.PCG64(51 + kin))
+    spec = wl.make_ickan(rng, kin=kin, widths=(3, 3, 2, 1), degree=3, G=10, lo0=-0.6, hi0=1.5, kappa=1.5)
+    m = oracle.OracleModel(spec)
+    F = rand_F(rng, 4, 0.2)
+    psi, P, A = oracle.const_update(m, F)
+    for q in range(F.shape[0]):
+        psi_h, P_h, A_h = hdm.exact_P_A(spec, F[q])
+        assert abs(psi[q] - psi_h) < 1e-13 * max(1, abs(psi_h))
+        assert rel(P[q], P_h) < 1e-12
+        assert rel(A[q], A_h) < 1e-12
+
+
+def test_ickan_is_convex_and_monotone(kan_spec):
+    """Positive weights and convex non-decreasing splines (App. B) make N convex and
+    non-decreasing in K on the grids: d2N is positive semi-definite, dN >= 0."""
+    m = oracle.OracleModel(kan_spec)
+    rng = np.random.Generator(np.random.PCG64(52))
+    for _ in range(20):
+        K = rng.uniform(kan_spec.lo[0] + 0.1, kan_spec.hi[0] - 0.1, size=3)
+        _, dN, d2N = oracle.inner(m, K)
+        assert np.all(dN >= -1e-14)
+        assert np.linalg.eigvalsh(d2N).min() >= -1e-12 * max(1.0, np.abs(d2N).max())

@@ -306,6 +306,70 @@ class GentThomasSpec:
     inner_name: str = "gent_thomas"
 
 
+@dataclass
+class IckanSpec:
+    """An input-convex KAN (App. B): widths [d, n_1, .., n_{R-1}, 1]; per layer r a uniform grid
+    of G intervals on [lo[r], hi[r]] with B-splines of degree `degree` (knots extended by
+    `degree` on each side, G + degree basis functions); params = per spline (layer, output i,
+    input j order) the weight w_s then the control points."""
+    d: int
+    kin: int
+    fibres: np.ndarray
+    widths: list
+    degree: int
+    G: int
+    lo: np.ndarray
+    hi: np.ndarray
+    params: np.ndarray
+    kappa: float = 0.0
+    stress_free: bool = False
+    inner_name: str = "ickan"
+
+    def theta(self) -> np.ndarray:
+        return np.asarray(self.params, dtype=np.float64).copy()
+
+
+def make_ickan(rng, kin: int = KIN_POLYCONVEX, widths=(3, 4, 4, 1), degree: int = 4, G: int = 30,
+               lo0: float = -0.25, hi0: float = 1.5, kappa: float = 0.0) -> IckanSpec:
+    """ICKAN with convex, non-decreasing splines (App. B condition c_{l+2} - c_{l+1} >=
+    c_{l+1} - c_l >= 0: control points are cumulative sums of non-decreasing increments) and
+    positive weights. Layer 0's grid is [lo0, hi0]; each later layer's grid is the range its
+    inputs can take (on its grid a spline lies between its first and last control point), with
+    a 5 % margin."""
+    widths = list(widths)
+    d = widths[0]
+    nb = G + degree
+    lo, hi, params = [lo0], [hi0], []
+    for r in range(len(widths) - 1):
+        nin, nout = widths[r], widths[r + 1]
+        zmin, zmax = np.zeros(nout), np.zeros(nout)
+        for i in range(nout):
+            for j in range(nin):
+                w = 0.1 + abs(rng.normal(0.0, 0.5))
+                inc = np.cumsum(np.abs(rng.normal(0.0, 0.1, size=nb - 1)))   # non-decreasing increments
+                c = np.concatenate([[0.0], np.cumsum(inc)]) * (1.0 / max(1e-12, inc.sum()))
+                params.append(np.concatenate([[w], c]))
+                zmin[i] += w * c[0]
+                zmax[i] += w * c[-1]
+        if r + 1 < len(widths) - 1:
+            span = zmax.max() - zmin.min()
+            lo.append(zmin.min() - 0.05 * span)
+            hi.append(zmax.max() + 0.05 * span)
+    fib = np.zeros((0, 3))
+    return IckanSpec(d=d, kin=kin, fibres=fib, widths=widths, degree=degree, G=G, lo=np.array(lo),
+                     hi=np.array(hi), params=np.concatenate(params), kappa=kappa)
+
+
+def workload_ickan(n: int = 64, seed: int = 8):
+    """An ICKAN with the paper's spline settings (App. C: 2 hidden layers, order 4, 30 grid
+    points; widths 3 -> 4 -> 4 -> 1) on the polyconvex inputs; F = I + 0.15 N(0,1), n^3 mesh."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    model = make_ickan(rng)
+    mesh = structured_mesh(n)
+    F = random_F(rng, 8 * mesh.n_el, 0.15)
+    return dict(name=f"ickan_polyconvex_{n}cube_3x4x4x1_k4_g30", model=model, mesh=mesh, F=F)
+
+
 def make_cann(rng, kin: int = KIN_POLYCONVEX, n_fib: int = 0, kinds=None, kappa: float = 0.0,
               std: float = 0.1, stress_free: bool = False) -> CannSpec:
     """CANN with |N(0, std)| weights drawn input by input, term by term (w1 then w2)."""
