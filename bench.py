@@ -14,6 +14,7 @@ integrals (P, A -> f_int, K_e for every element). Other workloads:
       polyconvex inputs (Ibar1 - 3, Ibar2^{3/2} - 3^{3/2}, (J - 1)^2), 64^3 mesh, c1's step
   cann the paper's CANN (exponents {1, 2} x {x, exp x}) on the same inputs, c1's step
   gt  the closed-form Gent-Thomas law (eq. gt), c1's step
+  ickan an input-convex KAN (App. B; 3 -> 4 -> 4 -> 1, degree 4, 30 intervals), c1's step
 
 Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle on the
 host cores instead (a bounded sample of the same workload per step).
@@ -201,7 +202,7 @@ def make_workload(name: str, n: int | None = None):
     kw = {} if n is None else ({"n_qp": n} if name == "c3" else {"n": n})
     return {"c0": wl.workload_c0, "c1": wl.workload_c1, "c2": wl.workload_c2, "c3": wl.workload_c3,
             "c4": wl.workload_c4, "ncm": wl.workload_paper_ncm, "cann": wl.workload_cann,
-            "gt": wl.workload_gent_thomas}[name](**kw)
+            "gt": wl.workload_gent_thomas, "ickan": wl.workload_ickan}[name](**kw)
 
 
 def wl_sub(mesh, el):
@@ -252,7 +253,7 @@ class Run:
         self.model = pkg.Model(spec, prec)
         self.mesh = w.get("mesh")
         mp = "f64" if prec == "f64" else "f32"
-        if name in ("c1", "c2", "ncm", "cann", "gt"):
+        if name in ("c1", "c2", "ncm", "cann", "gt", "ickan"):
             F_host = np.ascontiguousarray(w["F"].T)
             self.inputs_host = {"F": F_host}
             n = F_host.shape[1]
@@ -271,7 +272,7 @@ class Run:
                 self.phases = [("const_update_kernel",
                                 lambda: self.model.const_update(self.F, out=(self.psi, self.P, self.A)))]
             self.outputs = [self.psi, self.P, self.A]
-            if name in ("c1", "ncm", "cann", "gt"):
+            if name in ("c1", "ncm", "cann", "gt", "ickan"):
                 self.gmesh = pkg.Mesh(self.mesh.X, self.mesh.conn)
                 self.f_e = torch.empty(24, self.n_el, dtype=dt, device=dev)
                 self.K_e = torch.empty(576, self.n_el, dtype=dt, device=dev)
@@ -426,8 +427,8 @@ def run_ours(args, rank, world, local_rank):
     name = args.workload
     prec = args.precision or ("f32" if name == "c4" else "f64")
     w = make_workload(name, args.n)
-    if args.spatial and name not in ("c1", "c2", "ncm", "cann", "gt"):
-        raise SystemExit("--spatial applies to the c1, c2, ncm, cann and gt workloads")
+    if args.spatial and name not in ("c1", "c2", "ncm", "cann", "gt", "ickan"):
+        raise SystemExit("--spatial applies to the c1, c2, ncm, cann, gt and ickan workloads")
     run = Run(name, w, prec, dev, pkg, torch, spatial=args.spatial)
     stream = torch.cuda.current_stream()
     dist = world > 1
@@ -502,7 +503,7 @@ def run_ours(args, rank, world, local_rank):
                "ms_per_step": e_ms / n_e2e}
 
     fp64_base = None
-    if name in ("c1", "c2", "c3", "ncm", "cann", "gt") and prec != "f64" and not args.no_baseline and rank == 0:
+    if name in ("c1", "c2", "c3", "ncm", "cann", "gt", "ickan") and prec != "f64" and not args.no_baseline and rank == 0:
         # the same step through the plain FP64 path of the same kernels
         run64 = Run(name, w, "f64", dev, pkg, torch, spatial=args.spatial)
         b_ms = time_steps(run64, torch, 2, 3)
@@ -822,7 +823,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["c0", "c1", "c2", "c3", "c4", "ncm", "cann", "gt"], default="c1")
+    ap.add_argument("--workload", choices=["c0", "c1", "c2", "c3", "c4", "ncm", "cann", "gt", "ickan"],
+                    default="c1")
     ap.add_argument("--n", type=int, default=None, help="mesh size per side (points for c3)")
     ap.add_argument("--precision", choices=["f64", "f32", "bf16"], default=None,
                     help="default: f64 (f32 for c4)")

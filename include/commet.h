@@ -64,6 +64,9 @@ extern "C" {
 #define COMMET_INNER_CANN 1         /* eq. cann-def (the cann_* fields) */
 #define COMMET_INNER_GENT_THOMAS 2  /* eq. gt, 0.5 (K0 - 3) + log(K1 / 3) + (K2 - 1)^2 on COMMET_KIN_RAW
                                        without fibres; no parameters */
+#define COMMET_INNER_ICKAN 3        /* the input-convex KAN of App. B (the kan_* fields), d = 3 */
+#define COMMET_KAN_MAX_LAYERS 8
+#define COMMET_KAN_MAX_WIDTH 8
 /* CANN term menus of eq. cann-fs: f0 (applied to K_m), f1 = x^p, f2 (with weight w1) */
 #define COMMET_CANN_F0_ID 0       /* x */
 #define COMMET_CANN_F0_MACAULAY 1 /* <x> = max(x, 0) */
@@ -107,6 +110,16 @@ typedef struct commet_model_desc {
     const int32_t *cann_kind; /* CANN: [n][3] per term (f0, p in 1..3, f2), shared by the inputs */
     const double *cann_w;     /* CANN: [d][n][2] per input m and term k: (w1, w2) of
                                  N = sum_m sum_k w2 f2(f1(f0(K_m)); w1)  (eq. cann-def) */
+    /* ICKAN (App. B): z^(r)_i = sum_j w_s,rij sum_l c_rij,l B_l,k(z^(r-1)_j), z^(0) = K, N = z^(R);
+       B-splines of degree k (the recursion of App. B) on G uniform intervals of [lo_r, hi_r],
+       knots extended by k on each side: G + k control points per spline */
+    int32_t kan_layers;        /* R, 1..COMMET_KAN_MAX_LAYERS */
+    const int32_t *kan_widths; /* [R + 1]: widths[0] = d, widths[R] = 1, each <= COMMET_KAN_MAX_WIDTH */
+    int32_t kan_degree;        /* k, 2..4 */
+    int32_t kan_grid;          /* G, 1..128 */
+    const double *kan_lo;      /* [R] */
+    const double *kan_hi;      /* [R], > lo */
+    const double *kan_params;  /* per spline (layer r, output i, input j, in that order): w_s, then c[G + k] */
 } commet_model_desc;
 
 /*

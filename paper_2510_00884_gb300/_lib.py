@@ -34,9 +34,12 @@ class ModelDesc(C.Structure):
                 ("c", C.POINTER(C.c_double)), ("a_out", C.POINTER(C.c_double)),
                 ("b_out", C.POINTER(C.c_double)), ("activation", C.c_int32), ("kappa", C.c_double),
                 ("stress_free", C.c_int32), ("inner", C.c_int32), ("cann_terms", C.c_int32),
-                ("cann_kind", C.POINTER(C.c_int32)), ("cann_w", C.POINTER(C.c_double))]
+                ("cann_kind", C.POINTER(C.c_int32)), ("cann_w", C.POINTER(C.c_double)),
+                ("kan_layers", C.c_int32), ("kan_widths", C.POINTER(C.c_int32)), ("kan_degree", C.c_int32),
+                ("kan_grid", C.c_int32), ("kan_lo", C.POINTER(C.c_double)), ("kan_hi", C.POINTER(C.c_double)),
+                ("kan_params", C.POINTER(C.c_double))]
 
-INNER_MICNN, INNER_CANN, INNER_GENT_THOMAS = 0, 1, 2
+INNER_MICNN, INNER_CANN, INNER_GENT_THOMAS, INNER_ICKAN = 0, 1, 2, 3
 
 
 class CommetError(RuntimeError):

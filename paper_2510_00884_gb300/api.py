@@ -46,6 +46,7 @@ class Model:
       micnn        W, L, W1, Ak, Bk, c, a, b (row-major float64 arrays, see workload.ModelSpec)
       cann         n, kinds[n][3], w[d][n][2] (see workload.CannSpec)
       gent_thomas  nothing more (eq. gt on raw kinematics)
+      ickan        widths, degree, G, lo, hi, params (see workload.IckanSpec)
     """
 
     def __init__(self, spec, precision: str = "f64"):
@@ -69,6 +70,18 @@ class Model:
                 desc.cann_w = pw
             elif inner == "gent_thomas":
                 desc.inner = _lib.INNER_GENT_THOMAS
+            elif inner == "ickan":
+                widths = np.ascontiguousarray(spec.widths, dtype=np.int32)
+                lo, plo = _dbl(spec.lo)
+                hi, phi = _dbl(spec.hi)
+                par, ppar = _dbl(spec.params)
+                self._keep += [widths, lo, hi, par]
+                desc.inner = _lib.INNER_ICKAN
+                desc.kan_layers = int(widths.size - 1)
+                desc.kan_widths = widths.ctypes.data_as(C.POINTER(C.c_int32))
+                desc.kan_degree = int(spec.degree)
+                desc.kan_grid = int(spec.G)
+                desc.kan_lo, desc.kan_hi, desc.kan_params = plo, phi, ppar
             else:
                 raise ValueError(f"unknown inner function {inner!r}")
             self._keep.append(fib)

@@ -1,6 +1,7 @@
 // extern "C" boundary of libcommet: argument checks, handle construction, dispatch.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -130,6 +131,19 @@ int create_closed_form(const commet_model_desc *desc, int32_t precision, commet_
         }
         for (int i = 0; i < 2 * d * n; ++i)
             if (!std::isfinite(desc->cann_w[i])) return COMMET_ERR_INVALID_ARG;
+    } else if (inner == COMMET_INNER_ICKAN) {
+        const int R = desc->kan_layers, k = desc->kan_degree, G = desc->kan_grid;
+        if (R < 1 || R > COMMET_KAN_MAX_LAYERS || desc->kan_widths == nullptr || desc->kan_lo == nullptr ||
+            desc->kan_hi == nullptr || desc->kan_params == nullptr || G < 1 || G > 128)
+            return COMMET_ERR_INVALID_ARG;
+        if (k < 2 || k > 4) return COMMET_ERR_UNSUPPORTED;
+        if (desc->kan_widths[0] != d || desc->kan_widths[R] != 1 || desc->n_fibres != 0)
+            return COMMET_ERR_INVALID_ARG;
+        for (int r = 0; r <= R; ++r)
+            if (desc->kan_widths[r] < 1 || desc->kan_widths[r] > COMMET_KAN_MAX_WIDTH) return COMMET_ERR_INVALID_ARG;
+        for (int r = 0; r < R; ++r)
+            if (!std::isfinite(desc->kan_lo[r]) || !std::isfinite(desc->kan_hi[r]) || !(desc->kan_hi[r] > desc->kan_lo[r]))
+                return COMMET_ERR_INVALID_ARG;
     } else if (desc->kinematics != COMMET_KIN_RAW || desc->n_fibres != 0) {
         return COMMET_ERR_INVALID_ARG;  // eq. gt is written on raw (Ibar1, Ibar2, J)
     }
@@ -152,18 +166,46 @@ int create_closed_form(const commet_model_desc *desc, int32_t precision, commet_
     l.d = d;
     l.inner = inner;
     l.cn = n;
+    int64_t n_kan = 0;  // ICKAN parameters
+    if (inner == COMMET_INNER_ICKAN) {
+        l.kR = desc->kan_layers;
+        l.kdeg = desc->kan_degree;
+        l.kG = desc->kan_grid;
+        l.kwmax = 1;
+        for (int r = 0; r <= l.kR; ++r) l.kwmax = std::max(l.kwmax, (int)desc->kan_widths[r]);
+        for (int r = 0; r < l.kR; ++r) n_kan += (int64_t)desc->kan_widths[r] * desc->kan_widths[r + 1];
+        n_kan *= 1 + l.kG + l.kdeg;
+    }
     int o = 0;
     l.cw = o; o = round4(o + 2 * d * n);
     l.ck = o; o = round4(o + 3 * n);
+    l.kwid = o; o = round4(o + (inner == COMMET_INNER_ICKAN ? l.kR + 1 : 0));
+    l.klo = o; o = round4(o + l.kR);
+    l.khi = o; o = round4(o + l.kR);
+    l.kpar = o; o = round4(o + (int)n_kan);
     l.n0 = o; o = round4(o + d);
     l.K0 = o; o = round4(o + d);
     l.total = o;
     m->lay = l;
-    m->n_params = (int64_t)2 * d * n;
+    m->n_params = inner == COMMET_INNER_ICKAN ? n_kan : (int64_t)2 * d * n;
     cudaGetDevice(&m->device);
     std::vector<double> h(l.total, 0.0);
     for (int i = 0; i < 2 * d * n; ++i) h[l.cw + i] = desc->cann_w[i];
     for (int i = 0; i < 3 * n; ++i) h[l.ck + i] = (double)desc->cann_kind[i];
+    if (inner == COMMET_INNER_ICKAN) {
+        for (int r = 0; r <= l.kR; ++r) h[l.kwid + r] = (double)desc->kan_widths[r];
+        for (int r = 0; r < l.kR; ++r) {
+            h[l.klo + r] = desc->kan_lo[r];
+            h[l.khi + r] = desc->kan_hi[r];
+        }
+        for (int64_t i = 0; i < n_kan; ++i) {
+            if (!std::isfinite(desc->kan_params[i])) {
+                delete m;
+                return COMMET_ERR_INVALID_ARG;
+            }
+            h[l.kpar + i] = desc->kan_params[i];
+        }
+    }
     int rc = (precision == COMMET_F64) ? upload<double>(h, &m->d_weights) : upload<float>(h, &m->d_weights);
     if (rc == COMMET_OK) rc = stress_free_shift(m);
     if (rc != COMMET_OK) {
@@ -194,7 +236,8 @@ int commet_model_create(const commet_model_desc *desc, int32_t precision, commet
     if (precision != COMMET_F64 && precision != COMMET_F32 && precision != COMMET_BF16_MLP)
         return COMMET_ERR_INVALID_ARG;
     const int inner = desc->inner;
-    if (inner != COMMET_INNER_MICNN && inner != COMMET_INNER_CANN && inner != COMMET_INNER_GENT_THOMAS)
+    if (inner != COMMET_INNER_MICNN && inner != COMMET_INNER_CANN && inner != COMMET_INNER_GENT_THOMAS &&
+        inner != COMMET_INNER_ICKAN)
         return COMMET_ERR_INVALID_ARG;
     if (inner != COMMET_INNER_MICNN) return create_closed_form(desc, precision, out);
     if (desc->kinematics != COMMET_KIN_ISO_SHIFTED && desc->kinematics != COMMET_KIN_RAW &&

@@ -109,7 +109,144 @@ __device__ __forceinline__ bool kin_scalars_k64(const T (&F)[9], const KinConst<
     }
 }
 
-template <typename T, int NF, int INNER, bool SPATIAL>
+// One weighted B-spline phi = w psi of an ICKAN layer (App. B) at x, with phi' and phi'':
+// degree KD on uniform knots t_m = lo + (m - KD) h. In knot units x sits in span m with
+// offset u; the KD + 1 non-zero basis functions follow from de Boor's triangle on uniform
+// knots (every denominator of the recursion is the stage number j), and the derivatives
+// from the lower-degree stages of the same triangle:
+//   psi'  = (1/h)   sum_l (c_l - c_{l-1}) B_l,KD-1
+//   psi'' = (1/h^2) sum_l (c_l - 2 c_{l-1} + c_{l-2}) B_l,KD-2
+// (control points outside 0 .. nb - 1 are zero; outside the knots everything is zero).
+template <typename T, int KD>
+__device__ __forceinline__ void kan_spline(T x, T lo, T inv_h, int G, const T *__restrict__ wc, T &f, T &f1,
+                                           T &f2) {
+    const int nb = G + KD;
+    const T s = (x - lo) * inv_h + T(KD);
+    f = f1 = f2 = T(0);
+    if (!(s >= T(0)) || !(s < T(G + 2 * KD))) return;
+    const int m = (int)floor(s);
+    const T u = s - T(m);
+    T N[KD + 1], N1[KD], N2[KD - 1];
+    N[0] = T(1);
+    if constexpr (KD == 2) N2[0] = T(1);  // the degree-0 stage is the single indicator
+#pragma unroll
+    for (int j = 1; j <= KD; ++j) {
+        T saved = T(0);
+#pragma unroll
+        for (int r = 0; r < j; ++r) {
+            const T temp = N[r] * (T(1) / T(j));
+            N[r] = saved + (T(r + 1) - u) * temp;
+            saved = (u + T(j - r - 1)) * temp;
+        }
+        N[j] = saved;
+        if (j == KD - 2) {
+#pragma unroll
+            for (int r = 0; r <= KD - 2; ++r) N2[r] = N[r];
+        }
+        if (j == KD - 1) {
+#pragma unroll
+            for (int r = 0; r <= KD - 1; ++r) N1[r] = N[r];
+        }
+    }
+    const T ws = wc[0];
+    const T *c = wc + 1;
+    auto cp = [&](int l) -> T { return (l >= 0 && l < nb) ? c[l] : T(0); };
+    T v = T(0), d1 = T(0), d2 = T(0);
+#pragma unroll
+    for (int r = 0; r <= KD; ++r) v += cp(m - KD + r) * N[r];
+#pragma unroll
+    for (int r = 0; r < KD; ++r) {
+        const int l = m - KD + 1 + r;
+        d1 += (cp(l) - cp(l - 1)) * N1[r];
+    }
+#pragma unroll
+    for (int r = 0; r < KD - 1; ++r) {
+        const int l = m - KD + 2 + r;
+        d2 += (cp(l) - T(2) * cp(l - 1) + cp(l - 2)) * N2[r];
+    }
+    f = ws * v;
+    f1 = ws * inv_h * d1;
+    f2 = ws * inv_h * inv_h * d2;
+}
+
+// ICKAN value, gradient and packed Hessian of one point on its 4-lane group: the outputs
+// of a hidden layer go round-robin over the lanes (each propagates z, dz/dK, d2z/dK2 of its
+// outputs by the chain rule and writes them to the point's slab); the last layer's single
+// output is split over its inputs, leaving per-lane partial sums for qp_group_finish.
+template <typename T, int D, int KD>
+__device__ __forceinline__ void kan_point(const T *__restrict__ sw, const NetLayout &lay, const T *K, T *qs, int jb,
+                                          T &npart, T *dN, T *Hs) {
+    constexpr int NH = D * (D + 1) / 2, S = 1 + D + NH;  // z, dz, d2z per neuron
+    const int R = lay.kR, G = lay.kG, nb = G + KD;
+    const int stride = lay.kwmax * S;
+    const T *par = sw + lay.kpar;
+    for (int r = 0; r < R; ++r) {
+        const int nin = (int)sw[lay.kwid + r], nout = (int)sw[lay.kwid + r + 1];
+        const T lo = sw[lay.klo + r], inv_h = T(G) / (sw[lay.khi + r] - lo);
+        const T *zin = qs + ((r + 1) & 1) * stride;  // layer r - 1's outputs
+        T *zout = qs + (r & 1) * stride;
+        const bool last = (r == R - 1);
+        // outputs (hidden layers) or inputs (last layer) of this lane
+        for (int t = jb; t < (last ? nin : nout); t += kG) {
+            T z = T(0), dz[D], d2z[NH];
+#pragma unroll
+            for (int a = 0; a < D; ++a) dz[a] = T(0);
+#pragma unroll
+            for (int h = 0; h < NH; ++h) d2z[h] = T(0);
+            const int i = last ? 0 : t;
+            const int j0 = last ? t : 0, j1 = last ? t + 1 : nin;
+            for (int j = j0; j < j1; ++j) {
+                const T *wc = par + (size_t)(i * nin + j) * (1 + nb);
+                if (r == 0) {
+                    // inputs are K itself: dz_j = e_j, d2z_j = 0
+                    T x = T(0);
+#pragma unroll
+                    for (int a = 0; a < D; ++a) x = (a == j) ? K[a] : x;
+                    T f, f1, f2;
+                    kan_spline<T, KD>(x, lo, inv_h, G, wc, f, f1, f2);
+                    z += f;
+#pragma unroll
+                    for (int a = 0; a < D; ++a) {
+                        dz[a] += (a == j) ? f1 : T(0);
+                        d2z[a * (a + 1) / 2 + a] += (a == j) ? f2 : T(0);
+                    }
+                } else {
+                    const T *in = zin + j * S;
+                    T f, f1, f2;
+                    kan_spline<T, KD>(in[0], lo, inv_h, G, wc, f, f1, f2);
+                    z += f;
+#pragma unroll
+                    for (int a = 0; a < D; ++a) {
+                        const T da = in[1 + a];
+                        dz[a] += f1 * da;
+#pragma unroll
+                        for (int b = 0; b <= a; ++b) d2z[a * (a + 1) / 2 + b] += f2 * da * in[1 + b];
+                    }
+#pragma unroll
+                    for (int h = 0; h < NH; ++h) d2z[h] += f1 * in[1 + D + h];
+                }
+            }
+            if (last) {
+                npart += z;
+#pragma unroll
+                for (int a = 0; a < D; ++a) dN[a] += dz[a];
+#pragma unroll
+                for (int h = 0; h < NH; ++h) Hs[h] += d2z[h];
+            } else {
+                T *out = zout + t * S;
+                out[0] = z;
+#pragma unroll
+                for (int a = 0; a < D; ++a) out[1 + a] = dz[a];
+#pragma unroll
+                for (int h = 0; h < NH; ++h) out[1 + D + h] = d2z[h];
+            }
+        }
+        par += (size_t)nin * nout * (1 + nb);
+        __syncwarp();
+    }
+}
+
+template <typename T, int NF, int INNER, bool SPATIAL, int KD = 3>
 __global__ void __launch_bounds__(256)
     closed_update_kernel(const T *__restrict__ gw, NetLayout lay, KinConst<T> kc, int64_t n_qp,
                          const T *__restrict__ Fg, T *__restrict__ psi, T *__restrict__ P, T *__restrict__ A,
@@ -151,7 +288,9 @@ __global__ void __launch_bounds__(256)
         for (int m = 0; m < D; ++m) dN[m] = T(0);
 #pragma unroll
         for (int h = 0; h < NH; ++h) Hs[h] = T(0);
-        if constexpr (INNER == COMMET_INNER_CANN) {
+        if constexpr (INNER == COMMET_INNER_ICKAN) {
+            kan_point<T, 3 + 2 * NF, KD>(sw, lay, K, qs, jb, npart, dN, Hs);
+        } else if constexpr (INNER == COMMET_INNER_CANN) {
             // the D n terms (input m, term k) go round-robin over the group's 4 lanes
             const int n = lay.cn, nt = D * n;
             for (int t0 = 0; t0 < nt; t0 += kG) {
@@ -209,7 +348,7 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-template <typename T, int NF, int INNER, bool SPATIAL>
+template <typename T, int NF, int INNER, bool SPATIAL, int KD = 3>
 static int launch_closed(const commet_model *m, int64_t n_qp, const void *F, void *psi, void *P, void *A,
                          int32_t *status, cudaStream_t s, void *dN_out) {
     constexpr int D = 3 + 2 * NF;
@@ -219,11 +358,12 @@ static int launch_closed(const commet_model *m, int64_t n_qp, const void *F, voi
     kc.kappa = (T)m->kp.kappa;
     for (int f = 0; f < 2; ++f)
         for (int c = 0; c < 3; ++c) kc.fib[f][c] = (T)m->kp.fib[f][c];
-    const int qstride = qp_slab_elems<T>(D, 0, 0, NF, SPATIAL);
+    const int net = (INNER == COMMET_INNER_ICKAN) ? 2 * m->lay.kwmax * (1 + D + D * (D + 1) / 2) : 0;
+    const int qstride = qp_slab_elems<T>(D, 0, 0, NF, SPATIAL, net);
     const size_t wbytes = ((size_t)m->lay.total * sizeof(T) + 15) / 16 * 16;
     const int warps = 8;
     const size_t smem = wbytes + (size_t)warps * kQPW * qstride * sizeof(T);
-    auto kern = closed_update_kernel<T, NF, INNER, SPATIAL>;
+    auto kern = closed_update_kernel<T, NF, INNER, SPATIAL, KD>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return COMMET_ERR_CUDA;
     int per_sm = 0;
@@ -241,6 +381,15 @@ template <typename T, bool SPATIAL>
 static int dispatch_closed(const commet_model *m, int64_t n_qp, const void *F, void *psi, void *P, void *A,
                            int32_t *status, cudaStream_t s, void *dN_out) {
     const int nf = m->kp.nf;
+    if (m->inner == COMMET_INNER_ICKAN && nf == 0) {
+        if (m->lay.kdeg == 2)
+            return launch_closed<T, 0, COMMET_INNER_ICKAN, SPATIAL, 2>(m, n_qp, F, psi, P, A, status, s, dN_out);
+        if (m->lay.kdeg == 3)
+            return launch_closed<T, 0, COMMET_INNER_ICKAN, SPATIAL, 3>(m, n_qp, F, psi, P, A, status, s, dN_out);
+        if (m->lay.kdeg == 4)
+            return launch_closed<T, 0, COMMET_INNER_ICKAN, SPATIAL, 4>(m, n_qp, F, psi, P, A, status, s, dN_out);
+        return COMMET_ERR_UNSUPPORTED;
+    }
     if (m->inner == COMMET_INNER_GENT_THOMAS && nf == 0)
         return launch_closed<T, 0, COMMET_INNER_GENT_THOMAS, SPATIAL>(m, n_qp, F, psi, P, A, status, s, dN_out);
     if (m->inner == COMMET_INNER_CANN) {

@@ -33,6 +33,9 @@ struct NetLayout {
     int tab;  // FP64 models: activation tables (kActTab doubles); 0 otherwise
     // CANN (inner == COMMET_INNER_CANN): cn terms, weights cw [d][cn][2], kinds ck [cn][3]
     int inner, cn, cw, ck;
+    // ICKAN: kR layers, B-spline degree kdeg, kG intervals; offsets of the widths [kR + 1]
+    // (as numbers), grid ranges lo/hi [kR] and the spline parameters
+    int kR, kdeg, kG, kwid, klo, khi, kpar, kwmax;
     int total;
 };
 

@@ -48,9 +48,9 @@ __host__ __device__ inline int qp_stage_end(int D, int NF) {
 }
 
 // Per-qp slab size in elements of T for the given network (host and device agree);
-// with `spatial`, room for P and A after the staging area.
+// with `spatial`, room for P and A after the staging area; `net` elements at least.
 template <typename T>
-__host__ __device__ inline int qp_slab_elems(int D, int W, int L, int NF, bool spatial = false) {
+__host__ __device__ inline int qp_slab_elems(int D, int W, int L, int NF, bool spatial = false, int net = 0) {
     const int DP = (D + 3) / 4 * 4;
     const int nbuf = L >= 4 ? 2 : (L == 3 ? 1 : 0);
     int work = 2 * W;
@@ -58,6 +58,7 @@ __host__ __device__ inline int qp_slab_elems(int D, int W, int L, int NF, bool s
     int raw = 2 * L * W + work;
     const int stage = qp_stage_end(D, NF) + (spatial ? 90 : 0);
     if (stage > raw) raw = stage;
+    if (net > raw) raw = net;  // per-point network area of the non-MLP inner functions
     int words = raw * (int)sizeof(T) / 4;
     words = (words + 31) / 32 * 32 + 4;
     return words * 4 / (int)sizeof(T);

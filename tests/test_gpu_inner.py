@@ -1,5 +1,7 @@
 """GPU parity of the inner functions other than the MICNN: the CANN of eq. cann-def and
 the closed-form Gent-Thomas energy of eq. gt, in both output forms, against the oracle."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -34,6 +36,12 @@ def specs():
                                            stress_free=True),
         "cann_all_raw1": wl.make_cann(rng, wl.KIN_RAW, 1, kinds=ALL_KINDS[:5], kappa=0.0, std=0.005),
         "gent_thomas": wl.GentThomasSpec(),
+        "ickan_k4_poly": wl.make_ickan(rng),
+        "ickan_k2_iso": wl.make_ickan(rng, kin=wl.KIN_ISO_SHIFTED, widths=(3, 5, 1), degree=2, G=16, lo0=-0.8,
+                                      kappa=3.0),
+        "ickan_k3_iso_shift": dataclasses.replace(
+            wl.make_ickan(rng, kin=wl.KIN_ISO_SHIFTED, widths=(3, 8, 3, 2, 1), degree=3, G=20, lo0=-0.8, kappa=1.0),
+            stress_free=True),
     }
 
 
@@ -51,7 +59,6 @@ def check(pkg, spec, F, prec, what):
     psi_r, P_r, A_r = oracle.const_update(oracle.OracleModel(spec), Fin)
     scale = None
     if spec.stress_free and prec != "f64":
-        import dataclasses
         _, scale, _ = oracle.const_update(oracle.OracleModel(dataclasses.replace(spec, stress_free=False)), Fin)
     assert_close(cm_to_pm(P), P_r, TOL[prec], f"{what} P", scale)
     assert_close(cm_to_pm(A), A_r, TOL[prec], f"{what} A")
@@ -125,11 +132,18 @@ def test_unsupported_paths(pkg):
     assert ei.value.code == _lib.ERR_INVALID_ARG
 
 
-@pytest.mark.parametrize("name", ["cann_polyconvex", "gent_thomas"])
+def test_ickan_parameter_count(pkg):
+    spec = SPECS["ickan_k4_poly"]
+    m = pkg.Model(spec, "f64")
+    assert m.n_params == spec.params.size == (12 + 16 + 4) * (1 + 30 + 4)
+
+
+@pytest.mark.parametrize("name", ["cann_polyconvex", "gent_thomas", "ickan"])
 def test_full_size_sampled(pkg, name):
     """The 64^3 CANN and Gent-Thomas workloads in FP64 as the bench launches them; sampled
     points (including the last) against the oracle."""
-    w = wl.workload_cann() if name == "cann_polyconvex" else wl.workload_gent_thomas()
+    w = {"cann_polyconvex": wl.workload_cann, "gent_thomas": wl.workload_gent_thomas,
+         "ickan": wl.workload_ickan}[name]()
     spec = w["model"]
     m = pkg.Model(spec, "f64")
     F = pm_to_cm(w["F"], torch.float64)

@@ -330,12 +330,13 @@ class IckanSpec:
 
 
 def make_ickan(rng, kin: int = KIN_POLYCONVEX, widths=(3, 4, 4, 1), degree: int = 4, G: int = 30,
-               lo0: float = -0.25, hi0: float = 1.5, kappa: float = 0.0) -> IckanSpec:
+               lo0: float = -0.5, hi0: float = 12.0, kappa: float = 0.0) -> IckanSpec:
     """ICKAN with convex, non-decreasing splines (App. B condition c_{l+2} - c_{l+1} >=
     c_{l+1} - c_l >= 0: control points are cumulative sums of non-decreasing increments) and
-    positive weights. Layer 0's grid is [lo0, hi0]; each later layer's grid is the range its
-    inputs can take (on its grid a spline lies between its first and last control point), with
-    a 5 % margin."""
+    positive weights. Layer 0's grid is [lo0, hi0], wide enough for the kinematic scalars of
+    F = I + 0.15 N(0,1) (outside its grid a KAN is neither monotone nor convex); each later
+    layer's grid is the range its inputs can take (on its grid a spline lies between its first
+    and last control point), with a 5 % margin."""
     widths = list(widths)
     d = widths[0]
     nb = G + degree
