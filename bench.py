@@ -71,7 +71,10 @@ def backward_flops_per_qp(d: int, W: int, L: int) -> int:
     return 2 * macs
 
 
-ELEM_MACS = 8 * (3 * 27 * 3 + 3 * 8 * 3 * 3)  # per element: 8 qp x (T3 + row contractions)
+# Multiply-adds per hex8 element of eq. r-quad / k-quad: per Gauss point and per row (I, i)
+# of K_e, A contracted with the node's gradient (9 entries x 3) and then with every
+# column's gradient (24 entries x 3), plus 3 for f_e: 24 x (27 + 72 + 3) per point, 8 points.
+ELEM_MACS = 8 * 24 * (27 + 72 + 3)
 PUSH_FORWARD_MACS = 21 * 15 + 6 * 3  # per point: c = F A F - delta tau (21 entries), tau = P F^T (6)
 
 

@@ -8,6 +8,7 @@
 
 #include "hex8.cuh"
 #include "internal.h"
+#include "tma.cuh"
 
 namespace commet {
 
@@ -181,6 +182,172 @@ __global__ void __launch_bounds__(128)
     }
 }
 
+// ------------------------------------------------- TMA-fed element integrals
+// The same integrals with the P and A of a tile of 16 consecutive elements (128 points)
+// brought into shared memory by two 2D tensor copies ([9][128] and [81][128] boxes of the
+// component-major tables) instead of per-lane strided loads: the copies overlap the
+// gradient computation and arrive as whole 512-byte rows. Used for FP32, where the kernel
+// is bound by HBM; FP64 is bound by its FP64 pipe and keeps the kernel above.
+constexpr int kTmaQP = kElPerCta * 8;
+constexpr int kTmaTries = 1 << 20;
+
+template <typename T>
+__global__ void __launch_bounds__(128)
+    elem_tma_kernel(int64_t n_el, const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmA,
+                    int want_K, const int32_t *__restrict__ conn, const double *__restrict__ X, T *__restrict__ f_e,
+                    T *__restrict__ K_e, unsigned int *__restrict__ err) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    T *s_p = reinterpret_cast<T *>(dsm);  // [9][128]
+    T *s_a = s_p + 9 * kTmaQP;            // [81][128]
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ T s_g[kElPerCta][8][8][3];
+    __shared__ T s_w[kElPerCta][8];
+    const int le = threadIdx.x >> 3, I = threadIdx.x & 7;
+    const int64_t el0 = (int64_t)blockIdx.x * kElPerCta;
+    const int64_t e = el0 + le;
+    const bool valid = e < n_el;
+    const int64_t ec = valid ? e : n_el - 1;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t bytes = (uint32_t)((9 + (want_K ? 81 : 0)) * kTmaQP * sizeof(T));
+        mbar_expect_tx(&bar, bytes);
+        tma_load_2d(s_p, &tmP, (int)(el0 * 8), 0, &bar);
+        if (want_K) tma_load_2d(s_a, &tmA, (int)(el0 * 8), 0, &bar);
+    }
+    {
+        // lane I: the gradients at Gauss point I, while the copies are in flight
+        T Xe[8][3];
+#pragma unroll
+        for (int K = 0; K < 8; ++K) {
+            const int64_t n = conn[8 * ec + K];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) Xe[K][a] = (T)X[3 * n + a];
+        }
+        T gX[8][3], w;
+        physical_grads<T>(Xe, I, gX, w);
+#pragma unroll
+        for (int K = 0; K < 8; ++K)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) s_g[le][I][K][a] = gX[K][a];
+        s_w[le][I] = w;
+    }
+    __syncthreads();
+    if (!mbar_wait_bounded(&bar, 0, kTmaTries)) {
+        // cannot happen in a correct run; flag it, let the copies land, and mark the tile
+        if (threadIdx.x == 0) atomicAdd(err, 1u);
+        mbar_wait_bounded(&bar, 0, kTmaTries);
+        if (valid) {
+            const T nanv = T(NAN);
+            if (f_e != nullptr)
+                for (int i = 0; i < 3; ++i) f_e[(3 * I + i) * n_el + e] = nanv;
+            if (K_e != nullptr && want_K)
+                for (int c = 0; c < 72; ++c) K_e[((3 * I + c / 24) * 24 + c % 24) * n_el + e] = nanv;
+        }
+        return;
+    }
+    T f[3] = {T(0), T(0), T(0)};
+    T Kr[3][8][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int K = 0; K < 8; ++K)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) Kr[i][K][k] = T(0);
+    for (int q = 0; q < 8; ++q) {
+        const int col = le * 8 + q;
+        const T w = s_w[le][q];
+        T wg[3];
+#pragma unroll
+        for (int J = 0; J < 3; ++J) wg[J] = w * s_g[le][q][I][J];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            f[i] += s_p[(3 * i) * kTmaQP + col] * wg[0] + s_p[(3 * i + 1) * kTmaQP + col] * wg[1] +
+                    s_p[(3 * i + 2) * kTmaQP + col] * wg[2];
+        if (want_K) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                T T3[3][3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+#pragma unroll
+                    for (int L = 0; L < 3; ++L)
+                        T3[k][L] = wg[0] * s_a[((3 * i) * 9 + 3 * k + L) * kTmaQP + col] +
+                                   wg[1] * s_a[((3 * i + 1) * 9 + 3 * k + L) * kTmaQP + col] +
+                                   wg[2] * s_a[((3 * i + 2) * 9 + 3 * k + L) * kTmaQP + col];
+#pragma unroll
+                for (int K = 0; K < 8; ++K) {
+                    const T g0 = s_g[le][q][K][0], g1 = s_g[le][q][K][1], g2 = s_g[le][q][K][2];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) Kr[i][K][k] += T3[k][0] * g0 + T3[k][1] * g1 + T3[k][2] * g2;
+                }
+            }
+        }
+    }
+    if (!valid) return;
+    if (f_e != nullptr) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) f_e[(3 * I + i) * n_el + e] = f[i];
+    }
+    if (K_e != nullptr && want_K) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int K = 0; K < 8; ++K)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) K_e[((3 * I + i) * 24 + 3 * K + k) * n_el + e] = Kr[i][K][k];
+    }
+}
+
+bool encode_tensor_map_2d(CUtensorMap *map, const void *base, int elem_bytes, uint64_t rows, uint64_t cols,
+                          uint32_t box_rows, uint32_t box_cols) {
+    using encode_fn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static encode_fn fn = nullptr;
+    if (fn == nullptr) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || p == nullptr)
+            return false;
+        fn = reinterpret_cast<encode_fn>(p);
+    }
+    if ((reinterpret_cast<uintptr_t>(base) & 15u) != 0 || (cols * elem_bytes) % 16 != 0 ||
+        (box_cols * (uint32_t)elem_bytes) % 16 != 0)
+        return false;
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {cols * (uint64_t)elem_bytes};
+    const cuuint32_t box[2] = {box_cols, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, elem_bytes == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+              const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Launches the TMA-fed kernel; COMMET_ERR_UNSUPPORTED when a tensor map cannot be encoded
+// (the caller then uses the per-lane kernel).
+template <typename T>
+static int launch_elem_tma(const commet_mesh *mesh, const void *P, const void *A, void *f_e, void *K_e,
+                           cudaStream_t s) {
+    const int64_t n_el = mesh->n_el, n_qp = 8 * n_el;
+    if (n_qp > 0x7fffffffLL) return COMMET_ERR_UNSUPPORTED;
+    CUtensorMap tmP{}, tmA{};
+    const bool want_K = (A != nullptr);
+    if (!encode_tensor_map_2d(&tmP, P, (int)sizeof(T), 9, (uint64_t)n_qp, 9, kTmaQP)) return COMMET_ERR_UNSUPPORTED;
+    if (want_K && !encode_tensor_map_2d(&tmA, A, (int)sizeof(T), 81, (uint64_t)n_qp, 81, kTmaQP))
+        return COMMET_ERR_UNSUPPORTED;
+    const size_t dyn = (size_t)(9 + 81) * kTmaQP * sizeof(T);
+    if (cudaFuncSetAttribute(elem_tma_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
+        return COMMET_ERR_CUDA;
+    const int64_t blocks = (n_el + kElPerCta - 1) / kElPerCta;
+    elem_tma_kernel<T><<<(unsigned)blocks, 128, dyn, s>>>(n_el, tmP, tmA, want_K ? 1 : 0, mesh->d_conn, mesh->d_X,
+                                                          (T *)f_e, (T *)K_e, mesh->d_err);
+    return cudaGetLastError() == cudaSuccess ? COMMET_OK : COMMET_ERR_CUDA;
+}
+
 template <typename T>
 static int elem_typed(const commet_mesh *mesh, const void *P, const void *A, void *f_e, void *K_e, void *r,
                       void *K_vals, cudaStream_t s) {
@@ -188,6 +355,10 @@ static int elem_typed(const commet_mesh *mesh, const void *P, const void *A, voi
     if (n_el == 0) return COMMET_OK;
     const bool scatter = (r != nullptr) || (K_vals != nullptr);
     if (!scatter) {
+        if constexpr (sizeof(T) == 4) {
+            const int rc = launch_elem_tma<T>(mesh, P, A, f_e, K_e, s);
+            if (rc != COMMET_ERR_UNSUPPORTED) return rc;
+        }
         const int64_t blocks = (n_el + kElPerCta - 1) / kElPerCta;
         elem_assemble_kernel<T, false><<<(unsigned)blocks, 128, 0, s>>>(
             n_el, nullptr, n_el, mesh->d_conn, mesh->d_X, (const T *)P, (const T *)A, (T *)f_e, (T *)K_e, nullptr,

@@ -89,6 +89,7 @@ struct commet_mesh {
     double *d_fixed_vals = nullptr;
     double *d_delta = nullptr;  // [n_rows] prescribed increments, dense
     double *d_red = nullptr;
+    unsigned int *d_err = nullptr;  // count of tiles whose bulk copies did not complete in time
     int device = 0;
 };
 

@@ -322,3 +322,27 @@ def test_polyconvex_rejects_fibres(pkg):
     with pytest.raises(_lib.CommetError) as ei:
         pkg.Model(spec, "f64")
     assert ei.value.code == _lib.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("n", [(5, 4, 3), (7, 3, 1)])
+def test_elem_assemble_tiles_fp32(pkg, n):
+    """Element integrals without scatter in FP32 (the kernel fed by 2D tensor copies of
+    16-element tiles): ragged last tiles (60 and 21 elements), with and without K_e, against
+    the oracle on the same P, A."""
+    mesh = wl.structured_mesh(*n, lengths=(1.0, 0.8, 0.6))
+    rng = np.random.Generator(np.random.PCG64(90 + n[2]))
+    X = mesh.X + 0.02 * rng.uniform(-1, 1, size=mesh.X.shape)
+    mesh = wl.Mesh(X=X, conn=mesh.conn, n=mesh.n)
+    spec = wl.make_model(rng, wl.KIN_RAW, 2, W=32, L=3, kappa=1.0)
+    F = wl.random_F(rng, 8 * mesh.n_el, 0.15)
+    m = pkg.Model(spec, "f32")
+    gm = pkg.Mesh(mesh.X, mesh.conn)
+    _, P, A = m.const_update(pm_to_cm(F, torch.float32))
+    f_e, K_e, _, _ = gm.elem_assemble(P, A, "f32")
+    P_in, A_in = cm_to_pm(P).astype(np.float64), cm_to_pm(A).astype(np.float64)
+    f_r, K_r = oracle.elem_assemble(mesh, P_in, A_in)
+    assert_close(cm_to_pm(f_e), f_r, TOL["f32"], "f_e")
+    assert_close(cm_to_pm(K_e), K_r.reshape(-1, 576), TOL["f32"], "K_e")
+    f2, K2, _, _ = gm.elem_assemble(P, None, "f32")
+    assert K2 is None
+    assert_close(cm_to_pm(f2), f_r, TOL["f32"], "f_e without K")
