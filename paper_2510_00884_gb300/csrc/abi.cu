@@ -423,7 +423,7 @@ int commet_mesh_create(int64_t n_nodes, const double *X, int64_t n_el, const int
         rc = COMMET_ERR_CUDA;
     if (rc == COMMET_OK && want_csr) rc = build_csr_and_colouring(n_nodes, n_el, conn, mesh);
     if (rc == COMMET_OK && cudaMalloc(&mesh->d_red, sizeof(double) * kRedDoubles) != cudaSuccess) rc = COMMET_ERR_CUDA;
-    if (rc == COMMET_OK && (cudaMalloc(&mesh->d_err, 16) != cudaSuccess || cudaMemset(mesh->d_err, 0, 16) != cudaSuccess))
+    if (rc == COMMET_OK && (cudaMalloc(&mesh->d_err, 64) != cudaSuccess || cudaMemset(mesh->d_err, 0, 64) != cudaSuccess))
         rc = COMMET_ERR_CUDA;
     if (rc != COMMET_OK) {
         commet_mesh_destroy(mesh);

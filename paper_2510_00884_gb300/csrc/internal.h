@@ -13,7 +13,7 @@ namespace commet {
 
 constexpr int kMaxFibres = 2;
 constexpr int kRedBlocks = 4096;  // partial sums per reduction slot of the solver
-constexpr int kRedDoubles = 16 + 2 * kRedBlocks;
+constexpr int kRedDoubles = 16 + 4 * kRedBlocks;
 constexpr int kMaxD = 3 + 2 * kMaxFibres;
 
 // Offsets (in elements of the path's scalar type) of the packed weight block that
@@ -89,7 +89,8 @@ struct commet_mesh {
     double *d_fixed_vals = nullptr;
     double *d_delta = nullptr;  // [n_rows] prescribed increments, dense
     double *d_red = nullptr;
-    unsigned int *d_err = nullptr;  // count of tiles whose bulk copies did not complete in time
+    unsigned int *d_err = nullptr;  // [16]: [0] tiles whose bulk copies did not complete in time,
+                                    // [1..2] last-block counters of the CG kernels (zero between launches)
     int device = 0;
 };
 

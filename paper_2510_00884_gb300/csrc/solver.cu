@@ -3,13 +3,14 @@
 // Jacobi relaxation as the preconditioner), and the displacement update.
 //
 // CG layout: every vector lives in the workspace ([5][n] of the precision's type) and the
-// scalars of the recurrence in the mesh's reduction array, so that an iteration is six
-// launches with no host round trip: SpMV with the p.Ap partial sums, a one-block reduction
-// that forms alpha, the x / r / z update with the r.z and r.r partial sums, a reduction that
-// forms beta and the stopping test, and the p update. Every kernel first reads the `done`
-// word and returns at once after convergence, so the host reads that word only once per
-// chunk of iterations. Dot products are summed in FP64 in a fixed order (per-block partials,
-// then one block): a solve is bitwise reproducible for a given device and grid.
+// scalars of the recurrence in the mesh's reduction array, so that an iteration is three
+// launches with no host round trip: SpMV with the p.Ap partial sums, whose last block to
+// finish forms alpha; the x / r / z update with the r.z and r.r partial sums, whose last
+// block forms beta and the stopping test; and the p update. Every kernel first reads the
+// `done` word and returns at once after convergence, so the host reads that word only once
+// per chunk of iterations. Dot products are summed in FP64 in a fixed order (per-block
+// partials, then one tree in index order): a solve is bitwise reproducible for a given
+// device and grid.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,7 +28,22 @@ constexpr int kSolveThreads = 256;
 constexpr int kChunk = 16;  // iterations between host checks of the stopping word
 
 // reduction array layout (doubles): scalars, then partial sums [2][kRedBlocks]
-enum { S_RZ = 0, S_PAP, S_RR, S_BB, S_ALPHA, S_BETA, S_DONE, S_ITERS, S_RTOL2, S_COUNT = 16 };
+// PART_A / PART_B are two partial-sum regions (2 x kRedBlocks each).
+enum { S_RZ = 0, S_RR, S_BB, S_ALPHA, S_BETA, S_DONE, S_ITERS, S_RTOL2, S_COUNT = 16 };
+constexpr int PART_A = S_COUNT, PART_B = S_COUNT + 2 * kRedBlocks;
+
+// True in the block that finishes last: every block publishes its partial sums, then
+// counts itself in; the last one sums all partials (in index order, so the result does not
+// depend on which block it is) and resets the counter for the next launch. No block waits.
+__device__ __forceinline__ bool last_block(unsigned int *counter) {
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (is_last) __threadfence();
+    return is_last;
+}
 
 int red_blocks() { return std::min(kRedBlocks, 16 * sm_count()); }
 
@@ -186,12 +202,12 @@ __global__ void cg_init_kernel(int64_t n, const int64_t *__restrict__ rowptr, co
         rz += (double)bi * (double)(di * bi);
         bb += (double)bi * (double)bi;
     }
-    block_sum2(rz, bb, red + S_COUNT);
+    block_sum2(rz, bb, red + PART_A);
 }
 
 __global__ void cg_start_kernel(double *__restrict__ red, int nb, double rtol) {
     double rz, bb;
-    sum_partials(red + S_COUNT, nb, rz, bb);
+    sum_partials(red + PART_A, nb, rz, bb);
     if (threadIdx.x == 0) {
         red[S_RZ] = rz;
         red[S_BB] = bb;
@@ -210,7 +226,7 @@ __global__ void cg_start_kernel(double *__restrict__ red, int nb, double rtol) {
 template <typename T>
 __global__ void cg_spmv_kernel(int64_t n_rows, const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                                const T *__restrict__ K_vals, const T *__restrict__ p, T *__restrict__ Ap,
-                               double *__restrict__ red) {
+                               double *__restrict__ red, unsigned int *__restrict__ counter) {
     if (red[S_DONE] != 0.0) return;
     const int lane = threadIdx.x & 31, sub = lane & 3;
     const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 2;  // rows per grid pass
@@ -230,24 +246,23 @@ __global__ void cg_spmv_kernel(int64_t n_rows, const int64_t *__restrict__ rowpt
             pap += a * (double)p[row];
         }
     }
-    block_sum2(pap, 0.0, red + S_COUNT);
-}
-
-__global__ void cg_alpha_kernel(double *__restrict__ red, int nb) {
-    if (red[S_DONE] != 0.0) return;
-    double pap, unused;
-    sum_partials(red + S_COUNT, nb, pap, unused);
-    if (threadIdx.x == 0) {
-        red[S_PAP] = pap;
-        red[S_ALPHA] = red[S_RZ] / pap;
+    block_sum2(pap, 0.0, red + PART_A);
+    if (last_block(counter)) {
+        double s_pap, unused;
+        sum_partials(red + PART_A, gridDim.x, s_pap, unused);
+        if (threadIdx.x == 0) {
+            red[S_ALPHA] = red[S_RZ] / s_pap;
+            *counter = 0u;
+        }
     }
 }
 
-// x += alpha p, r -= alpha Ap, z = dinv r; partials of r.z and r.r
+// x += alpha p, r -= alpha Ap, z = dinv r; partials of the new r.z and r.r, from which the
+// last block forms beta and the stopping test.
 template <typename T>
 __global__ void cg_update_kernel(int64_t n, T *__restrict__ x, T *__restrict__ r, T *__restrict__ z,
                                  const T *__restrict__ p, const T *__restrict__ Ap, const T *__restrict__ dinv,
-                                 double *__restrict__ red) {
+                                 double *__restrict__ red, unsigned int *__restrict__ counter) {
     if (red[S_DONE] != 0.0) return;
     const T alpha = (T)red[S_ALPHA];
     double rz = 0.0, rr = 0.0;
@@ -260,19 +275,18 @@ __global__ void cg_update_kernel(int64_t n, T *__restrict__ x, T *__restrict__ r
         rz += (double)ri * (double)zi;
         rr += (double)ri * (double)ri;
     }
-    block_sum2(rz, rr, red + S_COUNT);
-}
-
-__global__ void cg_beta_kernel(double *__restrict__ red, int nb) {
-    if (red[S_DONE] != 0.0) return;
-    double rz, rr;
-    sum_partials(red + S_COUNT, nb, rz, rr);
-    if (threadIdx.x == 0) {
-        red[S_BETA] = rz / red[S_RZ];
-        red[S_RZ] = rz;
-        red[S_RR] = rr;
-        red[S_ITERS] += 1.0;
-        if (rr <= red[S_RTOL2] * red[S_BB] || !(rr == rr)) red[S_DONE] = 1.0;
+    block_sum2(rz, rr, red + PART_B);
+    if (last_block(counter)) {
+        double rz_new, s_rr;
+        sum_partials(red + PART_B, gridDim.x, rz_new, s_rr);
+        if (threadIdx.x == 0) {
+            red[S_BETA] = rz_new / red[S_RZ];
+            red[S_RZ] = rz_new;
+            red[S_RR] = s_rr;
+            red[S_ITERS] += 1.0;
+            if (s_rr <= red[S_RTOL2] * red[S_BB] || !(s_rr == s_rr)) red[S_DONE] = 1.0;
+            *counter = 0u;
+        }
     }
 }
 
@@ -293,6 +307,7 @@ int cg_typed(const commet_mesh *mesh, const void *K_vals_v, const void *b_v, voi
     T *x = (T *)x_v;
     T *r = (T *)ws, *z = r + n, *p = z + n, *Ap = p + n, *dinv = Ap + n;
     double *red = mesh->d_red;
+    unsigned int *counters = mesh->d_err + 1;  // [2], zero between launches
     const int nb = red_blocks();
     const int spmv_blocks = (int)std::min<int64_t>(nb, (n * 4 + kSolveThreads - 1) / kSolveThreads);
     const int vec_blocks = (int)std::min<int64_t>(nb, (n + kSolveThreads - 1) / kSolveThreads);
@@ -306,10 +321,8 @@ int cg_typed(const commet_mesh *mesh, const void *K_vals_v, const void *b_v, voi
         const int m = std::min(kChunk, max_iter - it0);
         for (int k = 0; k < m; ++k) {
             cg_spmv_kernel<T><<<spmv_blocks, kSolveThreads, 0, s>>>(n, mesh->d_rowptr, mesh->d_col, K_vals, p, Ap,
-                                                                    red);
-            cg_alpha_kernel<<<1, kSolveThreads, 0, s>>>(red, spmv_blocks);
-            cg_update_kernel<T><<<vec_blocks, kSolveThreads, 0, s>>>(n, x, r, z, p, Ap, dinv, red);
-            cg_beta_kernel<<<1, kSolveThreads, 0, s>>>(red, vec_blocks);
+                                                                    red, counters);
+            cg_update_kernel<T><<<vec_blocks, kSolveThreads, 0, s>>>(n, x, r, z, p, Ap, dinv, red, counters + 1);
             cg_p_kernel<T><<<vec_blocks, kSolveThreads, 0, s>>>(n, z, p, red);
         }
         COMMET_CUDA_TRY(cudaGetLastError());
@@ -400,10 +413,10 @@ int launch_norm2(const commet_mesh *mesh, int precision, int64_t n, const void *
     double *red = mesh->d_red;
     const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(red_blocks(), (n + kSolveThreads - 1) / kSolveThreads));
     if (precision == COMMET_F64)
-        norm2_partial_kernel<double><<<nb, kSolveThreads, 0, s>>>(n, (const double *)x, red + S_COUNT);
+        norm2_partial_kernel<double><<<nb, kSolveThreads, 0, s>>>(n, (const double *)x, red + PART_A);
     else
-        norm2_partial_kernel<float><<<nb, kSolveThreads, 0, s>>>(n, (const float *)x, red + S_COUNT);
-    norm2_final_kernel<<<1, kSolveThreads, 0, s>>>(red + S_COUNT, nb, red + S_COUNT - 1);
+        norm2_partial_kernel<float><<<nb, kSolveThreads, 0, s>>>(n, (const float *)x, red + PART_A);
+    norm2_final_kernel<<<1, kSolveThreads, 0, s>>>(red + PART_A, nb, red + S_COUNT - 1);
     COMMET_CUDA_TRY(cudaGetLastError());
     COMMET_CUDA_TRY(cudaMemcpyAsync(out, red + S_COUNT - 1, sizeof(double), cudaMemcpyDeviceToHost, s));
     COMMET_CUDA_TRY(cudaStreamSynchronize(s));
