@@ -215,13 +215,14 @@ def wl_sub(mesh, el):
 
 def cpu_sample_rate(w, n_el_sample: int):
     """Oracle throughput on the first n_el_sample elements (qp/s and elements/s through
-    update + element assembly), or on the first 8 n_el_sample points for point workloads."""
+    update + element assembly), or on the first n_el_sample / 2 points of the backward
+    workload (its oracle runs on one core)."""
     import oracle
     oracle.build()
     spec = w["model"]
     m = oracle.OracleModel(spec)
     if "mesh" not in w:  # c3: the backward (the oracle's backward runs on one core)
-        n = min(2 * n_el_sample, w["F"].shape[0])
+        n = min(n_el_sample // 2, w["F"].shape[0])
         F = w["F"][:n]
         tgt = oracle.OracleModel(None, inner=oracle.INNER_HGO, kin=1, fibres=spec.fibres, **w["target"])
         t0 = time.perf_counter()
@@ -653,7 +654,7 @@ def run_reference(args):
     qps = n_qp_s * args.steps / secs
     threads = os.cpu_count() or 1
     return {
-        "impl": "reference", "metric": METRIC, "value": qps, "unit": "qp/s", "n_gpus": 0, "steps": args.steps,
+        "impl": "reference", "metric": METRIC, "value": qps, "unit": "qp/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "elements_per_s": (n_el_s * args.steps / secs) if n_el_s else None,
@@ -841,7 +842,8 @@ def main():
     ap.add_argument("--twist-steps", type=int, default=20)
     ap.add_argument("--sweep", choices=["size", "batch"], default=None,
                     help="model-size or batch-size sweep of the update (one JSON line per case)")
-    ap.add_argument("--cpu-sample-el", type=int, default=65536)
+    ap.add_argument("--cpu-sample-el", type=int, default=262144,
+                    help="elements (c3: half the points) of the workload the CPU baseline runs on")
     ap.add_argument("--ref-sample-el", type=int, default=4096)
     args = ap.parse_args()
     if args.warmup < 3:
