@@ -311,8 +311,40 @@ class Mesh:
         return float(out.value)
 
 
+class Assembler:
+    """u -> (r, K_vals) of a mesh: the fused Newton kernel, or compute_F + const_update +
+    element integrals with the colour scatter, whichever is faster for the precision (in FP64
+    the separate kernels are: the element integrals of one element per warp in the fused
+    kernel cost more FP64 instructions than the element kernel's four per warp)."""
+
+    def __init__(self, model: Model, mesh: "Mesh", fused: bool | None = None):
+        self.model, self.mesh = model, mesh
+        self.fused = (model.precision != "f64") if fused is None else fused
+        self.r = self.Kv = None
+        if not self.fused:
+            n_qp, dt, dev = 8 * mesh.n_el, model.dtype, torch.device("cuda", torch.cuda.current_device())
+            self.F = torch.empty(9, n_qp, dtype=dt, device=dev)
+            self.P = torch.empty(9, n_qp, dtype=dt, device=dev)
+            self.A = torch.empty(81, n_qp, dtype=dt, device=dev)
+            self.psi = torch.empty(n_qp, dtype=dt, device=dev)
+
+    def __call__(self, u: torch.Tensor):
+        m, g = self.model, self.mesh
+        if self.r is None:
+            self.r = torch.empty(3 * g.n_nodes, dtype=m.dtype, device=u.device)
+            self.Kv = torch.empty(g.nnz, dtype=m.dtype, device=u.device)
+        if self.fused:
+            newton_assemble(m, g, u, out=(self.r, self.Kv))
+        else:
+            g.compute_F(u, m.precision, out=self.F)
+            m.const_update(self.F, out=(self.psi, self.P, self.A))
+            g.elem_assemble(self.P, self.A, m.precision, want_f=False, want_K=False, want_r=True, want_Kcsr=True,
+                            out=(None, None, self.r, self.Kv))
+        return self.r, self.Kv
+
+
 def newton_solve(model: Model, mesh: Mesh, u: torch.Tensor, steps, tol: float = 1e-10, max_newton: int = 25,
-                 cg_rtol: float = 1e-10, cg_max_iter: int = 20000):
+                 cg_rtol: float = 1e-10, cg_max_iter: int = 20000, fused: bool | None = None):
     """Load-stepped Newton-Raphson on the GPU (the solve of Sec. 4.3). ``steps`` is a list of
     (fixed dofs, prescribed values) per load step, the same dofs in every step. Each iteration
     assembles r and K (fused kernel), applies the Dirichlet rows and columns, solves K du = r
@@ -324,7 +356,8 @@ def newton_solve(model: Model, mesh: Mesh, u: torch.Tensor, steps, tol: float = 
     list of (|r_free|, CG iterations of the solve that followed)."""
     prec = model.precision
     hist = []
-    r = Kv = du = ws = None
+    assemble = Assembler(model, mesh, fused)
+    du = ws = None
     prev = None
     for dofs, vals in steps:
         vals = np.asarray(vals, dtype=np.float64)
@@ -333,7 +366,7 @@ def newton_solve(model: Model, mesh: Mesh, u: torch.Tensor, steps, tol: float = 
             prev = np.zeros_like(vals)
         h = []
         for it in range(max_newton):
-            r, Kv = newton_assemble(model, mesh, u, out=None if r is None else (r, Kv))
+            r, Kv = assemble(u)
             if it == 0:
                 mesh.apply_dirichlet(r, Kv, prec, delta=vals - prev)
             else:
