@@ -746,7 +746,8 @@ def run_twist(args):
 def run_sweep(args):
     """GPU analogues of the paper's material-point studies (one JSON line per case):
       size   model size (App. D): MICNN on the polyconvex inputs with L in {2, 3, 4} hidden
-             layers and W in {4, 8, 16, 32, 64}, plus the CANN and Gent-Thomas laws, at
+             layers and W in {2, 4, 8, 16, 32, 64} (W = 2 runs zero-padded to 4), plus the CANN
+             and Gent-Thomas laws, at
              2^21 points per launch, P and A in FP64 and FP32
       batch  points per launch (the paper's batch size, Sec. 4.1) from 2^8 to 2^24 for the
              paper's NCM (3 x 16, 675 parameters), FP64 and FP32
@@ -804,7 +805,7 @@ def run_sweep(args):
     F_host = wl.random_F(rng, n_max, 0.15)
     if args.sweep == "size":
         for L in (2, 3, 4):
-            for W in (4, 8, 16, 32, 64):
+            for W in (2, 4, 8, 16, 32, 64):
                 spec = wl.make_model(np.random.Generator(np.random.PCG64(100 * L + W)), wl.KIN_POLYCONVEX, 0,
                                      W=W, L=L, kappa=0.0)
                 for prec in ("f64", "f32"):

@@ -93,7 +93,9 @@ typedef struct commet_model_desc {
     int32_t n_fibres;     /* structural vectors, 0..2 (must be 0 for ISO_SHIFTED) */
     const double *fibres; /* [n_fibres][3] reference vectors A^i */
     int32_t d;            /* network inputs; must equal the kinematic layer's count */
-    int32_t W;            /* hidden width; built: 16, 32, 64, and 4, 8 without fibres (BF16: 32, 64) */
+    int32_t W;            /* hidden width 1..64; the kernels are built for 16, 32, 64, and 4, 8 without
+                             fibres (BF16: 32, 64); other widths run as the next built one with zero
+                             rows and columns (exact), and theta stays the caller's */
     int32_t L;            /* hidden layers, >= 1 */
     const double *W1;     /* [W][d] */
     const double *A;      /* [L-1][W][W] (may be NULL when L == 1) */

@@ -253,10 +253,57 @@ int commet_model_create(const commet_model_desc *desc, int32_t precision, commet
     if (desc->L > 1 && (desc->A == nullptr || desc->B == nullptr)) return COMMET_ERR_INVALID_ARG;
     if (desc->n_fibres > 0 && desc->fibres == nullptr) return COMMET_ERR_INVALID_ARG;
     if (!(std::isfinite(desc->kappa))) return COMMET_ERR_INVALID_ARG;
-    const int W = desc->W, d = desc->d, L = desc->L;
-    if (W != 4 && W != 8 && W != 16 && W != 32 && W != 64) return COMMET_ERR_UNSUPPORTED;
-    if (W < 16 && desc->n_fibres != 0) return COMMET_ERR_UNSUPPORTED;  // narrow networks: d = 3 only
-    if (L > 16) return COMMET_ERR_UNSUPPORTED;
+    const int Wu = desc->W, d = desc->d, L = desc->L;
+    if (Wu > 64 || L > 16) return COMMET_ERR_UNSUPPORTED;
+    // Widths the kernels are built for: 4, 8 (no fibres), 16, 32, 64. Another width runs as the
+    // next built one with zero rows and columns, an exact padding: a padded neuron gets no input
+    // weight and no bias and feeds nothing, so N and all its derivatives are unchanged.
+    int W = Wu <= 4 ? 4 : (Wu <= 8 ? 8 : (Wu <= 16 ? 16 : (Wu <= 32 ? 32 : 64)));
+    if (W < 16 && desc->n_fibres != 0) W = 16;  // the narrow kernels take no fibres
+    std::vector<double> pW1, pA, pB, pc, pa;
+    std::vector<int32_t> theta_map;
+    commet_model_desc padded;
+    if (W != Wu) {
+        pW1.assign((size_t)W * d, 0.0);
+        pA.assign((size_t)(L - 1) * W * W, 0.0);
+        pB.assign((size_t)(L - 1) * W * d, 0.0);
+        pc.assign((size_t)L * W, 0.0);
+        pa.assign(W, 0.0);
+        for (int i = 0; i < Wu; ++i) {
+            for (int mm = 0; mm < d; ++mm) pW1[i * d + mm] = desc->W1[i * d + mm];
+            pa[i] = desc->a_out[i];
+            for (int k = 0; k < L; ++k) pc[k * W + i] = desc->c ? desc->c[k * Wu + i] : 0.0;
+            for (int k = 0; k < L - 1; ++k) {
+                for (int j = 0; j < Wu; ++j) pA[((size_t)k * W + i) * W + j] = desc->A[((size_t)k * Wu + i) * Wu + j];
+                for (int mm = 0; mm < d; ++mm) pB[((size_t)k * W + i) * d + mm] = desc->B[((size_t)k * Wu + i) * d + mm];
+            }
+        }
+        padded = *desc;
+        padded.W = W;
+        padded.W1 = pW1.data();
+        padded.A = L > 1 ? pA.data() : nullptr;
+        padded.B = L > 1 ? pB.data() : nullptr;
+        padded.c = pc.data();
+        padded.a_out = pa.data();
+        // padded theta [W1, c1, (A_k, B_k, c_k), a, b] -> the caller's theta index (or -1)
+        int64_t ou = 0;
+        auto block = [&](int rows, int cols, int urows, int ucols) {
+            for (int i = 0; i < rows; ++i)
+                for (int j = 0; j < cols; ++j)
+                    theta_map.push_back((i < urows && j < ucols) ? (int32_t)(ou + (int64_t)i * ucols + j) : -1);
+            ou += (int64_t)urows * ucols;
+        };
+        block(W, d, Wu, d);
+        block(1, W, 1, Wu);
+        for (int k = 0; k < L - 1; ++k) {
+            block(W, W, Wu, Wu);
+            block(W, d, Wu, d);
+            block(1, W, 1, Wu);
+        }
+        block(1, W, 1, Wu);
+        block(1, d, 1, d);
+        desc = &padded;
+    }
 
     commet_model *m = new (std::nothrow) commet_model();
     if (!m) return COMMET_ERR_CUDA;
@@ -272,8 +319,18 @@ int commet_model_create(const commet_model_desc *desc, int32_t precision, commet
     m->kp.stress_free = desc->stress_free ? 1 : 0;
     m->lay = make_layout(d, W, L, precision == COMMET_F64);
     m->lay.inner = COMMET_INNER_MICNN;
-    m->n_params = (int64_t)W * d + W + (int64_t)(L - 1) * ((int64_t)W * W + (int64_t)W * d + W) + W + d;
+    m->W_user = Wu;
+    m->n_params_net = (int64_t)W * d + W + (int64_t)(L - 1) * ((int64_t)W * W + (int64_t)W * d + W) + W + d;
+    m->n_params = (int64_t)Wu * d + Wu + (int64_t)(L - 1) * ((int64_t)Wu * Wu + (int64_t)Wu * d + Wu) + Wu + d;
     cudaGetDevice(&m->device);
+    if (!theta_map.empty()) {
+        if (cudaMalloc(&m->d_theta_map, sizeof(int32_t) * theta_map.size()) != cudaSuccess ||
+            cudaMemcpy(m->d_theta_map, theta_map.data(), sizeof(int32_t) * theta_map.size(), cudaMemcpyHostToDevice) !=
+                cudaSuccess) {
+            commet_model_destroy(m);
+            return COMMET_ERR_CUDA;
+        }
+    }
 
     const NetLayout &l = m->lay;
     const int dp = (d + 3) / 4 * 4;
@@ -347,6 +404,7 @@ int commet_model_destroy(commet_model *m) {
     cudaFree(m->d_weights);
     cudaFree(m->d_theta64);
     cudaFree(m->d_bf16);
+    cudaFree(m->d_theta_map);
     delete m;
     return COMMET_OK;
 }

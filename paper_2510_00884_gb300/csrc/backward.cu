@@ -36,10 +36,12 @@ namespace {
 
 constexpr int kG = 4, kQPW = 8;
 
+// Warps per CTA (8 points each: the CTA tile): 4 in FP64, 8 in FP32; 64-wide networks,
+// whose weights, accumulators and slabs would not fit, run half as many.
 template <typename T>
 struct BwConf {
     static constexpr int warps = sizeof(T) == 8 ? 4 : 8;
-    static constexpr int Q = warps * kQPW;  // points per CTA tile
+    static constexpr int min_warps = warps / 2;
 };
 
 // Per-point slab (elements of T): K[d], r[d], z_k/zdot_k (k = 1..L-1), zdot_L, and per
@@ -160,13 +162,13 @@ __device__ __forceinline__ void tile_sum(T *acc, int n, const T *base, int qstri
 
 }  // namespace
 
-template <typename T, int NF, int W>
-__global__ void __launch_bounds__(BwConf<T>::warps * 32)
+template <typename T, int NF, int W, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
     const_backward_kernel(const T *__restrict__ gw, NetLayout lay, KinConst<T> kc, int64_t n_qp,
                           const T *__restrict__ Fg, const T *__restrict__ Gg, T *__restrict__ dFg,
                           T *__restrict__ partial, int np_pad, BwSlab sl) {
     constexpr int D = 3 + 2 * NF, NJ = W / kG;
-    constexpr int Q = BwConf<T>::Q;
+    constexpr int Q = WARPS * kQPW;  // points per CTA tile
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sw = reinterpret_cast<T *>(smem_raw);
     const int wbytes = (lay.total * (int)sizeof(T) + 15) / 16 * 16;
@@ -414,14 +416,18 @@ __global__ void __launch_bounds__(BwConf<T>::warps * 32)
     for (int i = threadIdx.x; i < np_pad; i += blockDim.x) dst[i] = acc[i];
 }
 
+// Sums the per-CTA partials of parameter p in CTA order; with a map (padded networks) the
+// sum goes to the caller's theta index map[p], and padding parameters (map -1) are dropped.
 template <typename T>
 __global__ void reduce_partials_kernel(const T *__restrict__ partial, int n_blocks, int np, int np_pad,
-                                       T *__restrict__ out) {
+                                       T *__restrict__ out, const int32_t *__restrict__ map) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np) return;
+    const int dst = map ? map[p] : p;
+    if (dst < 0) return;
     T s = T(0);
     for (int b = 0; b < n_blocks; ++b) s += partial[(size_t)b * np_pad + p];
-    out[p] = s;
+    out[dst] = s;
 }
 
 static int bw_grid(const commet_model *m, int64_t n_qp, int Q) {
@@ -429,20 +435,22 @@ static int bw_grid(const commet_model *m, int64_t n_qp, int Q) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(n_tiles, 2 * (int64_t)sm_count()));
 }
 
-static int np_padded(const commet_model *m) { return (int)((m->n_params + 3) / 4 * 4); }
+static int64_t np_net(const commet_model *m) { return m->n_params_net > 0 ? m->n_params_net : m->n_params; }
+static int np_padded(const commet_model *m) { return (int)((np_net(m) + 3) / 4 * 4); }
 
 size_t backward_workspace_bytes(const commet_model *m, int64_t n_qp) {
     if (m->precision != COMMET_F64 && m->precision != COMMET_F32) return 0;
     if (m->inner != COMMET_INNER_MICNN) return 0;
     const size_t es = m->precision == COMMET_F64 ? 8 : 4;
-    const int Q = m->precision == COMMET_F64 ? BwConf<double>::Q : BwConf<float>::Q;
+    // sized for the smallest tile any launch may use (the largest grid)
+    const int Q = (m->precision == COMMET_F64 ? BwConf<double>::min_warps : BwConf<float>::min_warps) * kQPW;
     const size_t bytes = (size_t)bw_grid(m, n_qp, Q) * np_padded(m) * es;
     return (bytes + 255) / 256 * 256;
 }
 
-template <typename T, int NF, int W>
-static int bw_typed(const commet_model *m, int64_t n_qp, const void *F, const void *G, void *dF, void *dth,
-                    void *ws, cudaStream_t s) {
+template <typename T, int NF, int W, int WARPS>
+static int bw_launch(const commet_model *m, int64_t n_qp, const void *F, const void *G, void *dF, void *dth,
+                     void *ws, cudaStream_t s) {
     KinConst<T> kc{};
     kc.kin = m->kp.kin;
     kc.stress_free = m->kp.stress_free;
@@ -451,7 +459,7 @@ static int bw_typed(const commet_model *m, int64_t n_qp, const void *F, const vo
         for (int c = 0; c < 3; ++c) kc.fib[f][c] = (T)m->kp.fib[f][c];
     const int D = 3 + 2 * NF;
     const BwSlab sl = bw_slab(D, W, m->L, NF, (int)sizeof(T));
-    const int Q = BwConf<T>::Q;
+    const int Q = WARPS * kQPW;
     const int np_pad = np_padded(m);
     const size_t wbytes = ((size_t)m->lay.total * sizeof(T) + 15) / 16 * 16;
     const size_t smem = wbytes + (size_t)np_pad * sizeof(T) + (size_t)Q * sl.size * sizeof(T);
@@ -459,16 +467,27 @@ static int bw_typed(const commet_model *m, int64_t n_qp, const void *F, const vo
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (smem > (size_t)smem_max) return COMMET_ERR_UNSUPPORTED;
-    auto kern = const_backward_kernel<T, NF, W>;
+    auto kern = const_backward_kernel<T, NF, W, WARPS>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return COMMET_ERR_CUDA;
     const int grid = bw_grid(m, n_qp, Q);
-    kern<<<grid, BwConf<T>::warps * 32, smem, s>>>((const T *)m->d_weights, m->lay, kc, n_qp, (const T *)F,
+    kern<<<grid, WARPS * 32, smem, s>>>((const T *)m->d_weights, m->lay, kc, n_qp, (const T *)F,
                                                    (const T *)G, (T *)dF, (T *)ws, np_pad, sl);
     if (cudaGetLastError() != cudaSuccess) return COMMET_ERR_CUDA;
-    const int np = (int)m->n_params;
-    reduce_partials_kernel<T><<<(np + 255) / 256, 256, 0, s>>>((const T *)ws, grid, np, np_pad, (T *)dth);
+    const int np = (int)np_net(m);
+    reduce_partials_kernel<T><<<(np + 255) / 256, 256, 0, s>>>((const T *)ws, grid, np, np_pad, (T *)dth,
+                                                               m->d_theta_map);
     return cudaGetLastError() == cudaSuccess ? COMMET_OK : COMMET_ERR_CUDA;
+}
+
+template <typename T, int NF, int W>
+static int bw_typed(const commet_model *m, int64_t n_qp, const void *F, const void *G, void *dF, void *dth,
+                    void *ws, cudaStream_t s) {
+    const int rc = bw_launch<T, NF, W, BwConf<T>::warps>(m, n_qp, F, G, dF, dth, ws, s);
+    if constexpr (W == 64) {
+        if (rc == COMMET_ERR_UNSUPPORTED) return bw_launch<T, NF, W, BwConf<T>::min_warps>(m, n_qp, F, G, dF, dth, ws, s);
+    }
+    return rc;
 }
 
 template <typename T>

@@ -56,7 +56,10 @@ struct commet_model {
     int d, W, L;
     commet::KinParams kp;
     commet::NetLayout lay;
-    int64_t n_params;
+    int64_t n_params;      // parameters of the caller's network (theta of commet_model_n_params)
+    int64_t n_params_net = 0;  // parameters of the network the kernels run (padded width)
+    int W_user = 0;            // the caller's width; W is the padded one the kernels run
+    int32_t *d_theta_map = nullptr;  // [n_params_net] padded -> caller theta index, -1 for padding
     void *d_weights = nullptr;     // packed block, element type of the precision (float for BF16_MLP)
     void *d_theta64 = nullptr;     // flat theta (double) for reference
     void *d_bf16 = nullptr;        // hidden-layer weights in bf16 fragments (BF16_MLP only)

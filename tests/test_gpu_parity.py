@@ -164,9 +164,9 @@ def test_invalid_arguments(pkg):
                                    None, None, s) == _lib.ERR_INVALID_ARG
     assert lib.commet_const_update(m.handle, 10, C.c_void_p(F.data_ptr() + 8), None, C.c_void_p(P.data_ptr()),
                                    None, None, s) == _lib.ERR_INVALID_ARG
-    spec8 = wl.make_model(rng, wl.KIN_RAW, 2, W=8, L=3, kappa=0.0)
+    spec65 = wl.make_model(rng, wl.KIN_RAW, 2, W=65, L=2, kappa=0.0)
     with pytest.raises(_lib.CommetError) as ei:
-        pkg.Model(spec8, "f64")
+        pkg.Model(spec65, "f64")
     assert ei.value.code == _lib.ERR_UNSUPPORTED
     bad = wl.make_model(rng, wl.KIN_RAW, 2, W=32, L=3, kappa=0.0)
     bad.d = 5
@@ -346,3 +346,38 @@ def test_elem_assemble_tiles_fp32(pkg, n):
     f2, K2, _, _ = gm.elem_assemble(P, None, "f32")
     assert K2 is None
     assert_close(cm_to_pm(f2), f_r, TOL["f32"], "f_e without K")
+
+
+# ------------------------------------------------ widths run zero-padded (exact)
+
+PAD_CASES = [(wl.KIN_POLYCONVEX, 0, 2, 3), (wl.KIN_ISO_SHIFTED, 0, 5, 2), (wl.KIN_RAW, 2, 8, 2),
+             (wl.KIN_RAW, 1, 24, 3), (wl.KIN_ISO_SHIFTED, 0, 40, 2)]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("case", PAD_CASES, ids=[f"k{c[0]}f{c[1]}w{c[2]}l{c[3]}" for c in PAD_CASES])
+def test_padded_widths(pkg, case, prec):
+    """Widths the kernels are not built for (2, 5, 24, 40, and 8 with fibres) run as the next
+    built width with zero rows and columns: the update and the backward match the oracle on
+    the caller's network, and dL/dtheta comes back in the caller's theta layout."""
+    kin, nf, W, L = case
+    rng = np.random.Generator(np.random.PCG64(700 + W))
+    spec = wl.make_model(rng, kin, nf, W=W, L=L, kappa=2.0, bias_std=0.1)
+    F = wl.random_F(rng, 1003, 0.15)
+    check_update(pkg, spec, F, prec, f"padded {case} {prec}")
+    m = pkg.Model(spec, prec)
+    assert m.n_params == spec.theta().size
+    G = rng.normal(size=F.shape)
+    Fd, Gd = pm_to_cm(F, DT[prec]), pm_to_cm(G, DT[prec])
+    from paper_2510_00884_gb300 import _lib
+    try:
+        dF, dth = m.backward(Fd, Gd)
+    except _lib.CommetError as e:
+        # a 64-wide network whose backward does not fit in shared memory
+        assert W > 32 and e.code == _lib.ERR_UNSUPPORTED
+        return
+    Fin, Gin = cm_to_pm(Fd).astype(np.float64), cm_to_pm(Gd).astype(np.float64)
+    dF_r, dth_r = oracle.const_backward(oracle.OracleModel(spec), Fin, Gin)
+    assert_close(cm_to_pm(dF), dF_r, TOL[prec], "padded dF")
+    scale = np.abs(dth_r).max()
+    assert np.abs(dth.cpu().numpy() - dth_r).max() <= (1e-11 if prec == "f64" else 1e-4) * scale
