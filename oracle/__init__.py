@@ -63,6 +63,8 @@ def _load():
         _lib.oracle_compute_F.argtypes = [i64, i32, d, d, d]
         _lib.oracle_elem_assemble.argtypes = [i64, i32, d, d, d, d, d]
         _lib.oracle_scatter_residual.argtypes = [i64, i32, d, i64, d]
+        _lib.oracle_residual_adjoint.argtypes = [i64, i32, d, d, d]
+        _lib.oracle_compute_F_adjoint.argtypes = [i64, i32, d, d, i64, d]
         _lib.oracle_kan_basis.argtypes = [P(_Model), C.c_int, C.c_double, d, d, d]
         _lib.oracle_kan_basis.restype = C.c_int
         _lib.oracle_push_forward.argtypes = [d, d, d, d, d]
@@ -258,6 +260,24 @@ def elem_assemble_spatial(mesh, F: np.ndarray, tau: np.ndarray, c: np.ndarray | 
     K = np.empty((n, 24, 24)) if c is not None else None
     lib.oracle_elem_assemble_spatial(n, _ip(conn), _dp(X), _dp(F), _dp(tau), _dp(c), _dp(f), _dp(K))
     return f, K
+
+
+def residual_adjoint(mesh, lam: np.ndarray) -> np.ndarray:
+    """dL/dP [n_qp][9] for dL/dr = lam [n_nodes][3] (transpose of eq. r-quad and the scatter)."""
+    lib = _load()
+    conn = np.ascontiguousarray(mesh.conn, dtype=np.int32)
+    G = np.empty((8 * conn.shape[0], 9))
+    lib.oracle_residual_adjoint(conn.shape[0], _ip(conn), _dp(_c64(mesh.X)), _dp(_c64(lam)), _dp(G))
+    return G
+
+
+def compute_F_adjoint(mesh, dF: np.ndarray) -> np.ndarray:
+    """dL/du [n_nodes][3] for dL/dF = dF [n_qp][9] (transpose of the trial F)."""
+    lib = _load()
+    conn = np.ascontiguousarray(mesh.conn, dtype=np.int32)
+    du = np.empty((mesh.n_nodes, 3))
+    lib.oracle_compute_F_adjoint(conn.shape[0], _ip(conn), _dp(_c64(mesh.X)), _dp(_c64(dF)), mesh.n_nodes, _dp(du))
+    return du
 
 
 def scatter_residual(mesh, f_e: np.ndarray) -> np.ndarray:

@@ -29,6 +29,7 @@
  *   Kirchhoff stress, spatial stiffness (Voigt) ...... App. A.1 (push-forward of P, A)
  *   f_int and K_e from tau, c ........................ Eq. r-quad, k-quad (spatial form)
  *   backward dL/dF, dL/dtheta ........................ chain rule on G : P(F; theta)
+ *   adjoints of r-quad and of the trial F ............. transposes for a residual loss (eq. loss)
  *
  * Parity status: every function here is pinned by the CPU tests (closed forms,
  * hyper-dual exact derivatives, finite differences, invariance, patch tests);
@@ -891,6 +892,47 @@ void oracle_elem_assemble_spatial(int64_t n_el, const int32_t *conn, const doubl
                             }
                 }
         }
+    }
+}
+
+/*
+ * Adjoints of the assembly chain for a residual-based loss (eq. loss of App. C, the NN-EUCLID
+ * objective, is a function of the global residual r):
+ *   r = sum_e sum_q w_q P_q grad phi  (eq. r-quad)  =>  dL/dP_q,iJ = w_q sum_I lam_I,i dphi_I/dX_J
+ *   F_q = I + sum_I u_I (x) grad phi  (Algorithm 1) =>  dL/du_I,i = sum_{e,q} dL/dF_q,iJ dphi_I/dX_J
+ * with lam = dL/dr. lam[n_nodes][3] -> G[n_qp][9]; dF[n_qp][9] -> du[n_nodes][3] (summed over
+ * elements in order).
+ */
+void oracle_residual_adjoint(int64_t n_el, const int32_t *conn, const double *X, const double *lam, double *G) {
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < n_el; ++e) {
+        double Xe[24], dphi[192], w[8];
+        gather_X(X, conn, e, Xe);
+        oracle_hex8_gradients(Xe, dphi, w);
+        for (int q = 0; q < 8; ++q)
+            for (int i = 0; i < 3; ++i)
+                for (int J = 0; J < 3; ++J) {
+                    double s = 0.0;
+                    for (int I = 0; I < 8; ++I) s += lam[3 * (int64_t)conn[8 * e + I] + i] * dphi[(q * 8 + I) * 3 + J];
+                    G[9 * (8 * e + q) + 3 * i + J] = w[q] * s;
+                }
+    }
+}
+
+void oracle_compute_F_adjoint(int64_t n_el, const int32_t *conn, const double *X, const double *dF, int64_t n_nodes,
+                              double *du) {
+    for (int64_t i = 0; i < 3 * n_nodes; ++i) du[i] = 0.0;
+    for (int64_t e = 0; e < n_el; ++e) {
+        double Xe[24], dphi[192], w[8];
+        gather_X(X, conn, e, Xe);
+        oracle_hex8_gradients(Xe, dphi, w);
+        for (int q = 0; q < 8; ++q)
+            for (int I = 0; I < 8; ++I)
+                for (int i = 0; i < 3; ++i) {
+                    double s = 0.0;
+                    for (int J = 0; J < 3; ++J) s += dF[9 * (8 * e + q) + 3 * i + J] * dphi[(q * 8 + I) * 3 + J];
+                    du[3 * (int64_t)conn[8 * e + I] + i] += s;
+                }
     }
 }
 

@@ -815,3 +815,61 @@ def test_ickan_is_convex_and_monotone(kan_spec):
         _, dN, d2N = oracle.inner(m, K)
         assert np.all(dN >= -1e-14)
         assert np.linalg.eigvalsh(d2N).min() >= -1e-12 * max(1.0, np.abs(d2N).max())
+
+
+# --------------------------------------- adjoints of the assembly (residual-based loss)
+
+def test_residual_adjoint_is_the_transpose_of_assembly():
+    """<lam, r(P)> = <G(lam), P> for the linear map P -> r of eq. r-quad plus the scatter,
+    and <dF, F(u) - I> = <u_adj(dF), u> for the linear part of the trial F."""
+    mesh = distorted_mesh(3, 30)
+    rng = np.random.Generator(np.random.PCG64(31))
+    P = rng.normal(size=(8 * mesh.n_el, 9))
+    lam = rng.normal(size=(mesh.n_nodes, 3))
+    f_e, _ = oracle.elem_assemble(mesh, P, None, want_K=False)
+    r = oracle.scatter_residual(mesh, f_e)
+    G = oracle.residual_adjoint(mesh, lam)
+    assert abs(lam.ravel() @ r - (G * P).sum()) <= 1e-13 * np.abs(lam.ravel()).sum() * np.abs(r).max()
+    u = rng.normal(size=(mesh.n_nodes, 3))
+    dF = rng.normal(size=(8 * mesh.n_el, 9))
+    F = oracle.compute_F(mesh, u) - np.eye(3).ravel()
+    du = oracle.compute_F_adjoint(mesh, dF)
+    assert abs((dF * F).sum() - (du * u).sum()) <= 1e-12 * np.abs(dF * F).sum()
+
+
+def test_residual_loss_gradient_central_differences():
+    """L = 1/2 |r_free(u; theta)|^2 on a 2^3 mesh: dL/dtheta (backward through G = residual
+    adjoint of lam = r_free) and dL/du (through the backward's dL/dF and the F adjoint) against
+    central differences of the whole oracle chain."""
+    mesh = distorted_mesh(2, 32)
+    rng = np.random.Generator(np.random.PCG64(33))
+    spec = wl.make_model(rng, wl.KIN_ISO_SHIFTED, 0, W=4, L=2, kappa=2.0, bias_std=0.1)
+    u = 0.03 * rng.normal(size=(mesh.n_nodes, 3))
+    fixed = np.zeros((mesh.n_nodes, 3), dtype=bool)
+    fixed[np.isclose(mesh.X[:, 0], 0.0)] = True
+
+    def loss(spec_, u_):
+        _, P, _ = oracle.const_update(oracle.OracleModel(spec_), oracle.compute_F(mesh, u_), want_A=False)
+        f_e, _ = oracle.elem_assemble(mesh, P, None, want_K=False)
+        r = oracle.scatter_residual(mesh, f_e).reshape(-1, 3)
+        r[fixed] = 0.0
+        return 0.5 * (r * r).sum(), r
+    L0, r = loss(spec, u)
+    G = oracle.residual_adjoint(mesh, r)
+    F = oracle.compute_F(mesh, u)
+    dF, dth = oracle.const_backward(oracle.OracleModel(spec), F, G)
+    du = oracle.compute_F_adjoint(mesh, dF)
+    theta = spec.theta()
+    h = 1e-6
+    for p in rng.choice(theta.size, 12, replace=False):
+        tp, tm = theta.copy(), theta.copy()
+        tp[p] += h
+        tm[p] -= h
+        fd = (loss(spec.with_theta(tp), u)[0] - loss(spec.with_theta(tm), u)[0]) / (2 * h)
+        assert abs(fd - dth[p]) <= 1e-6 * max(1.0, abs(fd))
+    for k in rng.choice(u.size, 12, replace=False):
+        up, um = u.copy(), u.copy()
+        up.ravel()[k] += h
+        um.ravel()[k] -= h
+        fd = (loss(spec, up)[0] - loss(spec, um)[0]) / (2 * h)
+        assert abs(fd - du.ravel()[k]) <= 1e-6 * max(1.0, abs(fd))
