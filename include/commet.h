@@ -220,6 +220,20 @@ int commet_elem_assemble_spatial(const commet_mesh *mesh, int32_t precision, con
                                  const void *c, void *f_e, void *K_e, void *r, void *K_vals, void *stream);
 
 /*
+ * Adjoints of the assembly chain, for gradients of a loss of the global residual (eq. loss of
+ * App. C, the NN-EUCLID objective) through commet_const_backward:
+ *   commet_residual_adjoint:   G[:, q] = dL/dP_q = w_q sum_I lam_I (x) grad_X phi_I(xi_q), the
+ *                              transpose of eq. r-quad and the scatter; lam = dL/dr [3 n_nodes]
+ *                              (dof 3 node + i), G [9][8 n_el] out.
+ *   commet_compute_F_adjoint:  du[i][node] = dL/du = sum over the node's elements and points of
+ *                              dL/dF_iJ dphi/dX_J, the transpose of the trial F; dF [9][8 n_el]
+ *                              in, du [3][n_nodes] OVERWRITTEN. Summed by element colour
+ *                              (deterministic): needs a mesh built with want_csr (else NO_CSR).
+ */
+int commet_residual_adjoint(const commet_mesh *mesh, int32_t precision, const void *lam, void *G, void *stream);
+int commet_compute_F_adjoint(const commet_mesh *mesh, int32_t precision, const void *dF, void *du, void *stream);
+
+/*
  * Fused Newton-iteration assembly: u -> F -> (Psi, P, A) -> f_e, K_e -> r, K_vals for
  * every element in one pass per colour, with P and A kept on chip (Algorithm 3 with
  * the constitutive call fused into the element loop). r [3 n_nodes], K_vals [nnz]

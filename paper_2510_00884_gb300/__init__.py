@@ -11,7 +11,8 @@ from . import _lib  # noqa: F401
 
 def __getattr__(name):
     # torch-facing API is imported lazily so that ``build`` works without a GPU
-    if name in ("Model", "Mesh", "Assembler", "newton_assemble", "newton_solve", "target_stress", "ConstUpdateP"):
+    if name in ("Model", "Mesh", "Assembler", "newton_assemble", "newton_solve", "target_stress", "ConstUpdateP",
+                "ComputeF", "AssembleResidual"):
         from . import api
         return getattr(api, name)
     raise AttributeError(name)

@@ -23,7 +23,7 @@ EXPORTED = [
     "commet_elem_assemble", "commet_newton_assemble", "commet_const_backward_workspace",
     "commet_const_backward", "commet_target_stress", "commet_status_string", "commet_const_backward_noalloc",
     "commet_mesh_set_dirichlet", "commet_set_dirichlet_values", "commet_apply_dirichlet", "commet_cg_workspace",
-    "commet_cg_solve", "commet_add_increment", "commet_norm2",
+    "commet_cg_solve", "commet_add_increment", "commet_norm2", "commet_residual_adjoint", "commet_compute_F_adjoint",
 ]
 
 
@@ -90,6 +90,8 @@ def load() -> C.CDLL:
                              C.POINTER(C.c_double), vp], C.c_int),
         "commet_add_increment": ([vp, i32, vp, C.c_double, vp, vp], C.c_int),
         "commet_norm2": ([vp, i32, i64, vp, C.POINTER(C.c_double), vp], C.c_int),
+        "commet_residual_adjoint": ([vp, i32, vp, vp, vp], C.c_int),
+        "commet_compute_F_adjoint": ([vp, i32, vp, vp, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

@@ -255,6 +255,25 @@ class Mesh:
         return f_e, K_e, r, Kv
 
 
+    # ---- adjoints of the assembly chain (residual-based losses)
+    def residual_adjoint(self, lam: torch.Tensor, precision: str = "f64", out=None):
+        """dL/dP [9, 8 n_el] for dL/dr = lam [3 n_nodes] (dof 3 node + i)."""
+        dt = _DTYPE[precision]
+        _check_dev(lam, dt, shape=(3 * self.n_nodes,), name="lam")
+        G = torch.empty(9, 8 * self.n_el, dtype=dt, device=lam.device) if out is None else out
+        _lib.check("commet_residual_adjoint", _lib.load().commet_residual_adjoint(
+            self.handle, _PREC[precision], _ptr(lam), _ptr(G), _stream()))
+        return G
+
+    def compute_F_adjoint(self, dF: torch.Tensor, precision: str = "f64", out=None):
+        """dL/du [3, n_nodes] for dL/dF = dF [9, 8 n_el]."""
+        dt = _DTYPE[precision]
+        _check_dev(dF, dt, shape=(9, 8 * self.n_el), name="dF")
+        du = torch.empty(3, self.n_nodes, dtype=dt, device=dF.device) if out is None else out
+        _lib.check("commet_compute_F_adjoint", _lib.load().commet_compute_F_adjoint(
+            self.handle, _PREC[precision], _ptr(dF), _ptr(du), _stream()))
+        return du
+
     # ---- the Newton step after assembly (Sec. 4.3)
     def set_dirichlet(self, dofs):
         """Fixed dofs (3 node + i), a strictly increasing integer list; empty clears them."""
@@ -428,3 +447,33 @@ class ConstUpdateP(torch.autograd.Function):
         (F,) = ctx.saved_tensors
         dF, dth = ctx.model.backward(F.contiguous(), G.contiguous())
         return dF, dth, None
+
+
+class ComputeF(torch.autograd.Function):
+    """F(u) at every Gauss point as an autograd node (Algorithm 1's trial F); backward is the
+    transposed kernel. Call as ComputeF.apply(u [3, n_nodes], mesh, precision)."""
+
+    @staticmethod
+    def forward(ctx, u, mesh, precision):
+        ctx.mesh, ctx.precision = mesh, precision
+        return mesh.compute_F(u.contiguous(), precision)
+
+    @staticmethod
+    def backward(ctx, dF):
+        return ctx.mesh.compute_F_adjoint(dF.contiguous(), ctx.precision), None, None
+
+
+class AssembleResidual(torch.autograd.Function):
+    """The global residual r [3 n_nodes] of eq. r-quad from P [9, 8 n_el] as an autograd node
+    (element integrals and the colour scatter); backward is the transposed kernel. The mesh
+    needs the CSR pattern. Call as AssembleResidual.apply(P, mesh, precision)."""
+
+    @staticmethod
+    def forward(ctx, P, mesh, precision):
+        ctx.mesh, ctx.precision = mesh, precision
+        _, _, r, _ = mesh.elem_assemble(P.contiguous(), None, precision, want_f=False, want_K=False, want_r=True)
+        return r
+
+    @staticmethod
+    def backward(ctx, lam):
+        return ctx.mesh.residual_adjoint(lam.contiguous(), ctx.precision), None, None

@@ -659,6 +659,21 @@ int commet_elem_assemble_spatial(const commet_mesh *mesh, int32_t precision, con
                                         r, K_vals, reinterpret_cast<cudaStream_t>(stream));
 }
 
+int commet_residual_adjoint(const commet_mesh *mesh, int32_t precision, const void *lam, void *G, void *stream) {
+    if (mesh == nullptr || (precision != COMMET_F64 && precision != COMMET_F32)) return COMMET_ERR_INVALID_ARG;
+    if (mesh->n_el > 0 && (lam == nullptr || G == nullptr)) return COMMET_ERR_INVALID_ARG;
+    if (!aligned16(lam) || !aligned16(G)) return COMMET_ERR_INVALID_ARG;
+    return launch_assembly_adjoints(mesh, precision, lam, G, nullptr, nullptr, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int commet_compute_F_adjoint(const commet_mesh *mesh, int32_t precision, const void *dF, void *du, void *stream) {
+    if (mesh == nullptr || (precision != COMMET_F64 && precision != COMMET_F32)) return COMMET_ERR_INVALID_ARG;
+    if (mesh->h_rowptr == nullptr) return COMMET_ERR_NO_CSR;
+    if ((mesh->n_el > 0 && dF == nullptr) || (mesh->n_nodes > 0 && du == nullptr)) return COMMET_ERR_INVALID_ARG;
+    if (!aligned16(dF) || !aligned16(du)) return COMMET_ERR_INVALID_ARG;
+    return launch_assembly_adjoints(mesh, precision, nullptr, nullptr, dF, du, reinterpret_cast<cudaStream_t>(stream));
+}
+
 int commet_newton_assemble(const commet_model *m, const commet_mesh *mesh, const void *u, void *r, void *K_vals,
                            int32_t *status, void *stream) {
     if (m == nullptr || mesh == nullptr) return COMMET_ERR_INVALID_ARG;

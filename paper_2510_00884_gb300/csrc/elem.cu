@@ -379,6 +379,113 @@ static int elem_typed(const commet_mesh *mesh, const void *P, const void *A, voi
     return COMMET_OK;
 }
 
+// ------------------------------------------------------------------ adjoints
+// For a loss of the global residual (eq. loss): G = dL/dP from lam = dL/dr, the transpose of
+// eq. r-quad and of the scatter (a gather of lam at the element's nodes): one thread per
+// (element, Gauss point), as compute_F.
+template <typename T>
+__global__ void residual_adjoint_kernel(int64_t n_el, const int32_t *__restrict__ conn, const double *__restrict__ X,
+                                        const T *__restrict__ lam, T *__restrict__ G) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= 8 * n_el) return;
+    const int64_t e = gid >> 3;
+    const int q = (int)(gid & 7);
+    T Xe[8][3], le[8][3];
+#pragma unroll
+    for (int I = 0; I < 8; ++I) {
+        const int64_t n = conn[8 * e + I];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            Xe[I][a] = (T)X[3 * n + a];
+            le[I][a] = lam[3 * n + a];
+        }
+    }
+    T gX[8][3], w;
+    physical_grads<T>(Xe, q, gX, w);
+    const int64_t n_qp = 8 * n_el;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int J = 0; J < 3; ++J) {
+            T s = T(0);
+#pragma unroll
+            for (int I = 0; I < 8; ++I) s += le[I][i] * gX[I][J];
+            G[(3 * i + J) * n_qp + gid] = w * s;
+        }
+}
+
+// du = dL/du from dF = dL/dF, the transpose of the trial F: element e adds
+// sum_q dF_q,iJ dphi_I/dX_J to node I. 8 lanes per element (lane I: node I), 16 elements
+// per CTA, one launch per element colour so that no two lanes add to one node.
+template <typename T>
+__global__ void __launch_bounds__(128)
+    compute_F_adjoint_kernel(int64_t n_el, int64_t n_nodes, const int32_t *__restrict__ el_list, int64_t n_list,
+                             const int32_t *__restrict__ conn, const double *__restrict__ X,
+                             const T *__restrict__ dF, T *__restrict__ du) {
+    __shared__ T s_g[kElPerCta][8][8][3];
+    const int le = threadIdx.x >> 3, I = threadIdx.x & 7;
+    const int64_t li = (int64_t)blockIdx.x * kElPerCta + le;
+    const bool valid = li < n_list;
+    const int64_t e = valid ? (int64_t)el_list[li] : 0;
+    {
+        T Xe[8][3];
+#pragma unroll
+        for (int K = 0; K < 8; ++K) {
+            const int64_t n = conn[8 * e + K];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) Xe[K][a] = (T)X[3 * n + a];
+        }
+        T gX[8][3], w;
+        physical_grads<T>(Xe, I, gX, w);
+#pragma unroll
+        for (int K = 0; K < 8; ++K)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) s_g[le][I][K][a] = gX[K][a];
+    }
+    __syncthreads();
+    if (!valid) return;
+    const int64_t n_qp = 8 * n_el;
+    T acc[3] = {T(0), T(0), T(0)};
+    for (int q = 0; q < 8; ++q) {
+        const int64_t qq = 8 * e + q;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int J = 0; J < 3; ++J) acc[i] += dF[(3 * i + J) * n_qp + qq] * s_g[le][q][I][J];
+    }
+    const int64_t gI = conn[8 * e + I];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) du[i * n_nodes + gI] += acc[i];
+}
+
+template <typename T>
+static int adjoints_typed(const commet_mesh *mesh, const void *lam, void *G, const void *dF, void *du, cudaStream_t s) {
+    const int64_t n_el = mesh->n_el;
+    if (lam != nullptr && n_el > 0) {
+        const int tpb = 256;
+        residual_adjoint_kernel<T><<<(unsigned)((8 * n_el + tpb - 1) / tpb), tpb, 0, s>>>(
+            n_el, mesh->d_conn, mesh->d_X, (const T *)lam, (T *)G);
+        COMMET_CUDA_TRY(cudaGetLastError());
+    }
+    if (dF != nullptr) {
+        COMMET_CUDA_TRY(cudaMemsetAsync(du, 0, sizeof(T) * 3 * mesh->n_nodes, s));
+        for (int c = 0; c < mesh->n_colours; ++c) {
+            const int64_t off = mesh->colour_off[c], cnt = mesh->colour_off[c + 1] - off;
+            if (cnt == 0) continue;
+            compute_F_adjoint_kernel<T><<<(unsigned)((cnt + kElPerCta - 1) / kElPerCta), 128, 0, s>>>(
+                n_el, mesh->n_nodes, mesh->d_colour_el + off, cnt, mesh->d_conn, mesh->d_X, (const T *)dF, (T *)du);
+            COMMET_CUDA_TRY(cudaGetLastError());
+        }
+    }
+    return COMMET_OK;
+}
+
+int launch_assembly_adjoints(const commet_mesh *mesh, int precision, const void *lam, void *G, const void *dF,
+                             void *du, cudaStream_t s) {
+    if (precision == COMMET_F64) return adjoints_typed<double>(mesh, lam, G, dF, du, s);
+    return adjoints_typed<float>(mesh, lam, G, dF, du, s);
+}
+
 int launch_elem_assemble(const commet_mesh *mesh, int precision, const void *P, const void *A, void *f_e,
                          void *K_e, void *r, void *K_vals, cudaStream_t s) {
     if (precision == COMMET_F64) return elem_typed<double>(mesh, P, A, f_e, K_e, r, K_vals, s);

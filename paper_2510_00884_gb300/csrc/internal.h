@@ -107,6 +107,10 @@ int launch_const_update_bf16(const commet_model *m, int64_t n_qp, const void *F,
 // Spatial form (App. A.1): tau [6][n], c [21][n] (Voigt) instead of P, A; all precisions.
 int launch_const_update_spatial(const commet_model *m, int64_t n_qp, const void *F, void *psi, void *tau, void *c,
                                 int32_t *status, cudaStream_t s);
+// Adjoints of the residual assembly and of the trial F (elem.cu): G = dL/dP from lam = dL/dr
+// (lam may be null), du = dL/du from dF = dL/dF (dF may be null; needs the colouring).
+int launch_assembly_adjoints(const commet_mesh *mesh, int precision, const void *lam, void *G, const void *dF,
+                             void *du, cudaStream_t s);
 // Newton step after assembly (solver.cu)
 size_t cg_workspace_bytes(const commet_mesh *mesh, int precision);
 int launch_cg_solve(const commet_mesh *mesh, int precision, const void *K_vals, const void *b, void *x, double rtol,

@@ -1,0 +1,86 @@
+"""GPU parity of the adjoints of the assembly chain and of the autograd graph of a
+residual-based loss (eq. loss of App. C) against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import workload as wl
+from tests.parity import TOL, assert_close, cm_to_pm, pm_to_cm
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DT = {"f64": torch.float64, "f32": torch.float32}
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2510_00884_gb300 as p
+    p.build()
+    return p
+
+
+def distorted(nx, ny, nz, seed):
+    mesh = wl.structured_mesh(nx, ny, nz, lengths=(1.0, 0.8, 0.6))
+    rng = np.random.Generator(np.random.PCG64(seed))
+    X = mesh.X + 0.02 * rng.uniform(-1, 1, size=mesh.X.shape)
+    return wl.Mesh(X=X, conn=mesh.conn, n=mesh.n)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_adjoint_kernels(pkg, prec):
+    mesh = distorted(5, 4, 3, 800)
+    rng = np.random.Generator(np.random.PCG64(801))
+    gm = pkg.Mesh(mesh.X, mesh.conn, want_csr=True)
+    dt = DT[prec]
+    lam = torch.from_numpy(rng.normal(size=3 * mesh.n_nodes)).to(dt).cuda()
+    G = gm.residual_adjoint(lam, prec)
+    G_r = oracle.residual_adjoint(mesh, lam.double().cpu().numpy().reshape(-1, 3))
+    assert_close(cm_to_pm(G), G_r, TOL[prec], "dL/dP")
+    dF = pm_to_cm(rng.normal(size=(8 * mesh.n_el, 9)), dt)
+    du = gm.compute_F_adjoint(dF, prec)
+    du_r = oracle.compute_F_adjoint(mesh, cm_to_pm(dF).astype(np.float64))
+    assert_close(du.double().cpu().numpy().T, du_r, TOL[prec] * 10, "dL/du")
+    # deterministic (colour scatter)
+    du2 = gm.compute_F_adjoint(dF, prec)
+    assert torch.equal(du, du2)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_residual_loss_autograd(pkg, prec):
+    """L = 1/2 |r_free(u; theta)|^2 through ComputeF -> ConstUpdateP -> AssembleResidual:
+    torch autograd over the library's kernels gives dL/du and dL/dtheta equal to the oracle's
+    adjoint chain (pinned by central differences)."""
+    mesh = distorted(4, 3, 3, 802)
+    rng = np.random.Generator(np.random.PCG64(803))
+    spec = wl.make_model(rng, wl.KIN_RAW, 2, W=16, L=3, kappa=1.0, bias_std=0.1)
+    gm = pkg.Mesh(mesh.X, mesh.conn, want_csr=True)
+    m = pkg.Model(spec, prec)
+    dt = DT[prec]
+    u_np = 0.02 * rng.normal(size=mesh.X.shape)
+    fixed = np.zeros((mesh.n_nodes, 3), dtype=bool)
+    fixed[np.isclose(mesh.X[:, 0], mesh.X[:, 0].min())] = True
+    mask = torch.from_numpy((~fixed).ravel().astype(np.float64)).to(dt).cuda()
+    u = torch.from_numpy(np.ascontiguousarray(u_np.T)).to(dt).cuda().requires_grad_(True)
+    sink = torch.zeros(m.n_params, dtype=dt, device="cuda", requires_grad=True)
+    F = pkg.ComputeF.apply(u, gm, prec)
+    P = pkg.ConstUpdateP.apply(F, sink, m)
+    r = pkg.AssembleResidual.apply(P, gm, prec) * mask
+    loss = 0.5 * (r * r).sum()
+    loss.backward()
+    # oracle chain at the same (rounded) inputs
+    u_in = u.detach().double().cpu().numpy().T
+    F_r = oracle.compute_F(mesh, u_in)
+    _, P_r, _ = oracle.const_update(oracle.OracleModel(spec), F_r, want_A=False)
+    f_e, _ = oracle.elem_assemble(mesh, P_r, None, want_K=False)
+    r_r = oracle.scatter_residual(mesh, f_e).reshape(-1, 3)
+    r_r[fixed] = 0.0
+    assert abs(loss.item() - 0.5 * (r_r * r_r).sum()) <= (1e-11 if prec == "f64" else 1e-4) * max(1.0, loss.item())
+    G_r = oracle.residual_adjoint(mesh, r_r)
+    dF_r, dth_r = oracle.const_backward(oracle.OracleModel(spec), F_r, G_r)
+    du_r = oracle.compute_F_adjoint(mesh, dF_r)
+    tol = 1e-10 if prec == "f64" else 2e-3
+    gu = u.grad.double().cpu().numpy().T
+    assert np.abs(gu - du_r).max() <= tol * np.abs(du_r).max()
+    gth = sink.grad.double().cpu().numpy()
+    assert np.abs(gth - dth_r).max() <= tol * np.abs(dth_r).max()
