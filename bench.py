@@ -15,6 +15,8 @@ integrals (P, A -> f_int, K_e for every element). Other workloads:
   cann the paper's CANN (exponents {1, 2} x {x, exp x}) on the same inputs, c1's step
   gt  the closed-form Gent-Thomas law (eq. gt), c1's step
   ickan an input-convex KAN (App. B; 3 -> 4 -> 4 -> 1, degree 4, 30 intervals), c1's step
+  resid the gradient of a residual-based loss 1/2 |r_free|^2 (eq. loss) on a 64^3 cantilever:
+      u -> F -> P -> r, then the adjoint chain to dL/dtheta and dL/du
 
 Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle on the
 host cores instead (a bounded sample of the same workload per step).
@@ -205,12 +207,24 @@ def make_workload(name: str, n: int | None = None):
     kw = {} if n is None else ({"n_qp": n} if name == "c3" else {"n": n})
     return {"c0": wl.workload_c0, "c1": wl.workload_c1, "c2": wl.workload_c2, "c3": wl.workload_c3,
             "c4": wl.workload_c4, "ncm": wl.workload_paper_ncm, "cann": wl.workload_cann,
-            "gt": wl.workload_gent_thomas, "ickan": wl.workload_ickan}[name](**kw)
+            "gt": wl.workload_gent_thomas, "ickan": wl.workload_ickan, "resid": wl.workload_residual}[name](**kw)
 
 
 def wl_sub(mesh, el):
     import workload as wl
     return wl.Mesh(X=mesh.X, conn=mesh.conn[el], n=mesh.n)
+
+
+def oracle_residual_loss_gradient(oracle, m, sub, u, free):
+    """The residual-loss gradient chain of the oracle on a (sub)mesh: u -> F -> P -> r,
+    lam = free * r, then dL/dP, (dL/dF, dL/dtheta) and dL/du."""
+    F = oracle.compute_F(sub, u)
+    _, P, _ = oracle.const_update(m, F, want_A=False)
+    f_e, _ = oracle.elem_assemble(sub, P, None, want_K=False)
+    lam = free * oracle.scatter_residual(sub, f_e)
+    G = oracle.residual_adjoint(sub, lam.reshape(-1, 3))
+    dF, dth = oracle.const_backward(m, F, G)
+    return oracle.compute_F_adjoint(sub, dF), dth
 
 
 def cpu_sample_rate(w, n_el_sample: int):
@@ -232,6 +246,14 @@ def cpu_sample_rate(w, n_el_sample: int):
         secs = time.perf_counter() - t0
         return n / secs, None, secs, f"first {n} points, FP64 stress + loss + backward"
     mesh = w["mesh"]
+    if "free" in w:  # the residual-loss gradient (its backward runs on one core)
+        el = np.arange(min(n_el_sample // 16, mesh.n_el))
+        sub = wl_sub(mesh, el)
+        t0 = time.perf_counter()
+        oracle_residual_loss_gradient(oracle, m, sub, w["u"], w["free"])
+        secs = time.perf_counter() - t0
+        return 8 * el.size / secs, el.size / secs, secs, \
+            f"first {el.size} elements and their {8 * el.size} points, FP64 residual-loss gradient chain"
     el = np.arange(min(n_el_sample, mesh.n_el))
     F = w["F"][: 8 * el.size] if "F" in w else oracle.compute_F(wl_sub(mesh, el), w["u"])
     t0 = time.perf_counter()
@@ -338,6 +360,40 @@ class Run:
                            ("const_backward_kernel", bw)]
             self.outputs = [self.dF]
             self.input_dev = {"F": self.F, "Pt": self.Pt}
+        elif name == "resid":
+            # u -> F -> P (stress) -> r, then dL/dr -> dL/dP -> (dL/dF, dL/dtheta) -> dL/du
+            self.gmesh = g = pkg.Mesh(self.mesh.X, self.mesh.conn, want_csr=True)
+            u_host = np.ascontiguousarray(w["u"].T)
+            self.inputs_host = {"u": u_host}
+            self.u = torch.from_numpy(u_host).to(device=dev, dtype=dt).contiguous()
+            self.free = torch.from_numpy(w["free"]).to(device=dev, dtype=dt)
+            self.n_el = self.mesh.n_el
+            self.n_qp = n = 8 * self.n_el
+            self.Fb = torch.empty(9, n, dtype=dt, device=dev)
+            self.P = torch.empty(9, n, dtype=dt, device=dev)
+            self.r = torch.empty(3 * self.mesh.n_nodes, dtype=dt, device=dev)
+            self.lam = torch.empty_like(self.r)
+            self.G = torch.empty(9, n, dtype=dt, device=dev)
+            self.dF = torch.empty_like(self.Fb)
+            self.dth = torch.empty(self.model.n_params, dtype=dt, device=dev)
+            self.du = torch.empty_like(self.u)
+            nb = int(pkg._lib.load().commet_const_backward_workspace(self.model.handle, n))
+            self.ws = torch.empty(max(1, nb), dtype=torch.uint8, device=dev)
+
+            def lam_of_r():
+                torch.mul(self.r, self.free, out=self.lam)
+            self.phases = [("compute_F_kernel", lambda: g.compute_F(self.u, mp, out=self.Fb)),
+                           ("const_update_kernel", lambda: self.model.const_update(
+                               self.Fb, want_A=False, want_psi=False, out=(None, self.P, None))),
+                           ("elem_assemble_kernel", lambda: g.elem_assemble(
+                               self.P, None, mp, want_f=False, want_K=False, want_r=True, out=(None, None, self.r, None))),
+                           ("loss_gradient (torch elementwise)", lam_of_r),
+                           ("residual_adjoint_kernel", lambda: g.residual_adjoint(self.lam, mp, out=self.G)),
+                           ("const_backward_kernel", lambda: self.model.backward(
+                               self.Fb, self.G, workspace=self.ws, out=(self.dF, self.dth))),
+                           ("compute_F_adjoint_kernel", lambda: g.compute_F_adjoint(self.dF, mp, out=self.du))]
+            self.outputs = [self.du, self.dth]
+            self.input_dev = {"u": self.u}
         elif name == "c4":
             self.gmesh = pkg.Mesh(self.mesh.X, self.mesh.conn, want_csr=True)
             u_host = np.ascontiguousarray(w["u"].T)
@@ -416,6 +472,10 @@ def launches_per_step(run) -> int:
             n += run.gmesh.n_colours
         elif name == "const_backward_kernel":
             n += 2
+        elif name == "elem_assemble_kernel" and run.name == "resid":
+            n += run.gmesh.n_colours
+        elif name == "compute_F_adjoint_kernel":
+            n += run.gmesh.n_colours
         elif not name.startswith("loss_gradient"):
             n += 1
     return n
@@ -507,7 +567,8 @@ def run_ours(args, rank, world, local_rank):
                "ms_per_step": e_ms / n_e2e}
 
     fp64_base = None
-    if name in ("c1", "c2", "c3", "ncm", "cann", "gt", "ickan") and prec != "f64" and not args.no_baseline and rank == 0:
+    if name in ("c1", "c2", "c3", "ncm", "cann", "gt", "ickan", "resid") and prec != "f64" and not args.no_baseline \
+            and rank == 0:
         # the same step through the plain FP64 path of the same kernels
         run64 = Run(name, w, "f64", dev, pkg, torch, spatial=args.spatial)
         b_ms = time_steps(run64, torch, 2, 3)
@@ -623,7 +684,16 @@ def run_reference(args):
     w = make_workload(name, args.n)
     spec = w["model"]
     m = oracle.OracleModel(spec)
-    if "mesh" in w:
+    if "free" in w:
+        mesh = w["mesh"]
+        n_el_s = min(args.ref_sample_el // 16, mesh.n_el)
+        sub = wl_sub(mesh, np.arange(n_el_s))
+        n_qp_s = 8 * n_el_s
+
+        def step():
+            oracle_residual_loss_gradient(oracle, m, sub, w["u"], w["free"])
+        sample = f"first {n_el_s} elements / {n_qp_s} points of {w['name']} per step, FP64 residual-loss gradient"
+    elif "mesh" in w:
         mesh = w["mesh"]
         n_el_s = min(args.ref_sample_el, mesh.n_el)
         el = np.arange(n_el_s)
@@ -827,7 +897,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["c0", "c1", "c2", "c3", "c4", "ncm", "cann", "gt", "ickan"],
+    ap.add_argument("--workload", choices=["c0", "c1", "c2", "c3", "c4", "ncm", "cann", "gt", "ickan", "resid"],
                     default="c1")
     ap.add_argument("--n", type=int, default=None, help="mesh size per side (points for c3)")
     ap.add_argument("--precision", choices=["f64", "f32", "bf16"], default=None,

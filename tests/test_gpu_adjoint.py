@@ -84,3 +84,40 @@ def test_residual_loss_autograd(pkg, prec):
     assert np.abs(gu - du_r).max() <= tol * np.abs(du_r).max()
     gth = sink.grad.double().cpu().numpy()
     assert np.abs(gth - dth_r).max() <= tol * np.abs(dth_r).max()
+
+
+def test_residual_loss_full_size_sampled(pkg):
+    """The residual-loss gradient step on the 64^3 cantilever in FP64, launched as the
+    benchmark launches it; dL/du at sampled nodes (corners, faces, the clamped face,
+    interior) against the oracle chain on the elements within two rings of each node (the
+    only ones dL/du there depends on: r at the nodes of the node's elements is complete
+    over those)."""
+    import bench
+    w = wl.workload_residual()
+    run = bench.Run("resid", w, "f64", torch.device("cuda", 0), pkg, torch)
+    run.step()
+    torch.cuda.synchronize()
+    du = run.du.cpu().numpy().T
+    assert np.isfinite(du).all() and np.isfinite(run.dth.cpu().numpy()).all()
+    n = w["mesh"].n[0]
+    m = oracle.OracleModel(w["model"])
+    rng = np.random.Generator(np.random.PCG64(804))
+    picks = [(0, 0, 0), (n, n, n), (0, 17, 30), (n, 5, 0), (1, 1, 1), (33, 0, 12)]
+    picks += [tuple(int(v) for v in rng.integers(0, n + 1, size=3)) for _ in range(6)]
+    got, ref = [], []
+    for (i, j, k) in picks:
+        rg = [np.arange(max(0, c - 2), min(n - 1, c + 1) + 1) for c in (i, j, k)]
+        ez, ey, ex = np.meshgrid(rg[2], rg[1], rg[0], indexing="ij")
+        el = (ex + n * (ey + n * ez)).ravel()
+        sub = wl.Mesh(X=w["mesh"].X, conn=w["mesh"].conn[el], n=w["mesh"].n)
+        F = oracle.compute_F(sub, w["u"])
+        _, P, _ = oracle.const_update(m, F, want_A=False)
+        f_e, _ = oracle.elem_assemble(sub, P, None, want_K=False)
+        lam = w["free"] * oracle.scatter_residual(sub, f_e)
+        G = oracle.residual_adjoint(sub, lam.reshape(-1, 3))
+        dF, _ = oracle.const_backward(m, F, G)
+        node = i + (n + 1) * (j + (n + 1) * k)
+        ref.append(oracle.compute_F_adjoint(sub, dF)[node])
+        got.append(du[node])
+    got, ref = np.array(got), np.array(ref)
+    assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()

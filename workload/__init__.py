@@ -465,6 +465,18 @@ def workload_c3(n_qp: int = 1 << 20, seed: int = 3):
     return dict(name=f"c3_backward_{n_qp}qp_d7w32l3", model=model, F=F, target=target)
 
 
+def workload_residual(n: int = 64, seed: int = 9):
+    """Gradient of a residual-based loss (eq. loss without reaction terms): the C1 network on an
+    n^3 cantilever (the displacement field of c4, clamped at x = 0); L = 1/2 |r_free|^2, with
+    the x = 0 dofs fixed."""
+    model = workload_c1(n=1)["model"]
+    mesh = structured_mesh(n)
+    u = cantilever_u(mesh, seed)
+    free = np.ones((mesh.n_nodes, 3))
+    free[np.isclose(mesh.X[:, 0], 0.0)] = 0.0
+    return dict(name=f"residual_loss_{n}cube_d7w32l3", model=model, mesh=mesh, u=u, free=free.ravel())
+
+
 def workload_c4(n: int = 96, seed: int = 4):
     """Newton hot path: n^3 cantilever, anisotropic d7 W32 L3 network (C1 weights),
     end-load displacement field."""
