@@ -1,15 +1,28 @@
-// Constitutive update with the hidden W x W layers on bf16 tensor cores (fp32
-// accumulate): the COMMET_BF16_MLP precision. The network derivatives follow the same
-// scheme as the FP64/FP32 kernel (forward values, reverse adjoints, forward tangents
-// consumed into the Hessian); here every hidden-layer product
-//     values    Y_k   = Z_{k-1} A_k^T       [16 points x W] = [16 x W][W x W]
-//     adjoints  Zb_{k-1} = Yb_k A_k         [16 x W]
-//     tangents  J_k^(m) = (s_{k-1} J_{k-1}^(m)) A_k^T   for each input m
-// is a warp-level bf16 MMA (m16n8k16) with the 16 points of a warp along M. The fp32
-// accumulator fragment of one layer is, element for element, the A-operand fragment of
-// the next, so activations stay in registers; only F', F'' (s_k) and the adjoint
-// weights (D_k) go to shared memory. Layer 1 (d inputs), the output layer, the
-// activations, the Hessian sums and the kinematics/P/A assembly are fp32.
+// Constitutive update with the hidden W x W layers on the fifth-generation tensor cores
+// (tcgen05: bf16 operands in shared memory, fp32 accumulators in tensor memory): the
+// COMMET_BF16_MLP precision. The network derivatives follow the scheme of the FP64/FP32
+// kernel (forward values, reverse adjoints, forward tangents consumed into the Hessian).
+//
+// One CTA of 256 threads takes a tile of 128 points: point i is lane i of tensor memory
+// and row i of every MMA (M = 128), held by threads i and 128 + i (warps w and w + 4 reach
+// the same TMEM lanes), each taking half of every layer's neurons. Per tile and hidden
+// layer k:
+//     values    Y_k      = Z_{k-1} A_k^T                [128 x W] = [128 x W][W x W]
+//     adjoints  Zb_{k-1} = Yb_k A_k                     [128 x W]
+//     tangents  J_k^(m)  = T_{k-1}^(m) A_k^T, m < d,    T = F'(y) (.) J
+// are tcgen05.mma kind::f16 instructions issued by one thread from operand tiles that
+// the threads write row by row (bf16, K-major core-matrix layout) and from the weights,
+// staged once per CTA in the same layout; the accumulators are read back with
+// tcgen05.ld. F'(y) and F''(y) of every layer are kept in the point's TMEM lane as fp16
+// pairs (tcgen05.st), F'' later replaced by the adjoint weight D_k = F''(y) zbar_k. Layer
+// 1 (d inputs), biases and skip terms, activations, the output layer and the Hessian sums
+// run in fp32 in the point's two threads, whose partial sums meet in shared memory. The
+// kinematics (fp32, J - 1 without cancellation) and the P/A assembly run in groups of 4
+// lanes as in the other kernels, each warp taking 2 rounds of 8 of its 32 points, their
+// data passed by warp shuffles.
+//
+// Tensor memory per CTA: d W columns of accumulators (values and adjoints use the first
+// W) plus L W columns of (F', F''/D) pairs: (d + L) W <= 512.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -20,31 +33,25 @@
 
 #include "device_math.cuh"
 #include "internal.h"
+#include "tma.cuh"
+#include "umma.cuh"
 
 namespace commet {
 
 namespace {
 
+constexpr int kTile = 128;           // points per CTA tile = MMA M = TMEM lanes
+constexpr int kThreads = 256;        // two threads per point
+constexpr int kWaitTries = 1 << 22;  // bounded mbarrier polls per MMA batch
+
 // Offsets of the bf16-path weight block: an fp32 part (units of float) followed by a
-// bf16 part (units of bf16) holding A_k row-major and A_k^T row-major with padded rows.
-struct B16Layout {
-    int d, dp, W, L, ld;
+// bf16 part (bytes) holding, per hidden layer k >= 2, A_k (rows j, K = i) and A_k^T
+// (rows i, K = j) in the core-matrix layout, W * W * 2 bytes each.
+struct TcLayout {
+    int d, dp, W, L;
     int W1, Bk, c, a, b, n0, K0, f32_total;  // float offsets
-    int Ab, Atb, b16_total;                   // bf16 offsets (from the start of the bf16 part)
+    int Ab, Atb, b16_bytes;                   // byte offsets from the start of the bf16 part
 };
-
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t *>(&v);
-}
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
 
 // J - 1 = det(I + H) - 1 = tr H + (principal 2x2 minors of H) + det H, H = F - I:
 // free of the cancellation of det F - 1 near J = 1 (accurate to a few ulp of |H|).
@@ -93,315 +100,398 @@ __device__ __forceinline__ bool kin_scalars_f32(const float *F, const KinConst<f
     return ok;
 }
 
-constexpr int kPW = 16;  // points per warp (the MMA's M)
+__device__ __forceinline__ uint32_t pack_half2(float lo, float hi) {
+    __half2 v = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+__device__ __forceinline__ float2 unpack_half2(uint32_t u) {
+    return __half22float2(*reinterpret_cast<__half2 *>(&u));
+}
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+// 8 consecutive columns j0..j0+7 (j0 % 8 == 0) of row r of an operand tile with K = W.
+template <int W>
+__device__ __forceinline__ void store_row8(unsigned char *op, int r, int j0, const float *v) {
+    uint4 u;
+    u.x = pack_bf16x2(v[0], v[1]);
+    u.y = pack_bf16x2(v[2], v[3]);
+    u.z = pack_bf16x2(v[4], v[5]);
+    u.w = pack_bf16x2(v[6], v[7]);
+    *reinterpret_cast<uint4 *>(op + cm_byte(r, j0, W)) = u;
+}
+
+// sum_m w[m] K[m] with w 16-byte aligned in shared memory (broadcast loads).
+template <int D>
+__device__ __forceinline__ float dot_w(const float *w, const float *K) {
+    float s = 0.f;
+#pragma unroll
+    for (int m0 = 0; m0 < D; m0 += 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(w + m0);
+        s += v.x * K[m0];
+        if (m0 + 1 < D) s += v.y * K[m0 + 1];
+        if (m0 + 2 < D) s += v.z * K[m0 + 2];
+        if (m0 + 3 < D) s += v.w * K[m0 + 3];
+    }
+    return s;
+}
+template <int D>
+__device__ __forceinline__ void load_w(const float *w, float *o) {
+#pragma unroll
+    for (int m0 = 0; m0 < D; m0 += 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(w + m0);
+        o[m0] = v.x;
+        if (m0 + 1 < D) o[m0 + 1] = v.y;
+        if (m0 + 2 < D) o[m0 + 2] = v.z;
+        if (m0 + 3 < D) o[m0 + 3] = v.w;
+    }
+}
+
+// One GEMM D[128 x W] = Op[128 x W] * Bw[W x W]^T (Bw rows = output columns), K = W.
+template <int W>
+__device__ __forceinline__ void issue_gemm(uint32_t d_tmem, uint32_t op_saddr, uint32_t w_saddr) {
+    constexpr uint32_t idesc = umma_idesc_bf16(kTile, W);
+#pragma unroll
+    for (int s = 0; s < W / 16; ++s)
+        umma_bf16(d_tmem, umma_desc(op_saddr + 256u * s, 128u, 16u * W), umma_desc(w_saddr + 256u * s, 128u, 16u * W),
+                  idesc, s > 0);
+}
+
+// Makes this tile's operand rows and TMEM stores visible, lets thread 0 issue the batch
+// (issue() runs on thread 0 only), and waits for its completion. False on timeout (every
+// thread returns the same answer).
+template <typename Issue>
+__device__ __forceinline__ bool mma_round(uint64_t *bar, uint32_t &phase, Issue issue) {
+    fence_async_smem();
+    tmem_wait_st();
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tc_fence_after();
+        issue();
+        umma_commit(bar);
+    }
+    const bool ok = mbar_wait_bounded(bar, phase, kWaitTries);
+    phase ^= 1u;
+    const bool any_fail = __syncthreads_or(!ok) != 0;
+    tc_fence_after();
+    return !any_fail;
+}
 
 }  // namespace
 
-// Per-warp shared memory: s_k and t_k/D_k in fp16 for 16 points x W neurons x L layers,
-// point-major with a pad (pstride halves per point), reused at the end as the 16
-// points' fp32 staging areas. fp16 keeps 11 bits, finer than the bf16 MMA inputs.
 template <int NF, int W, bool SPATIAL>
-__global__ void __launch_bounds__(256)
-    bf16_update_kernel(const float *__restrict__ gw32, const __nv_bfloat16 *__restrict__ gw16, B16Layout lay,
-                       KinConst<float> kc, int64_t n_qp, const float *__restrict__ Fg, float *__restrict__ psi,
-                       float *__restrict__ P, float *__restrict__ A, int32_t *__restrict__ status, int pstride) {
+__global__ void __launch_bounds__(kThreads)
+    bf16_tc_kernel(const float *__restrict__ gw32, const unsigned char *__restrict__ gw16, TcLayout lay,
+                   KinConst<float> kc, int64_t n_qp, const float *__restrict__ Fg, float *__restrict__ psi,
+                   float *__restrict__ P, float *__restrict__ A, int32_t *__restrict__ status, int *__restrict__ err,
+                   uint32_t tmem_cols, int stage_stride) {
     constexpr int D = 3 + 2 * NF, NH = D * (D + 1) / 2;
-    constexpr int NT = W / 8;   // n-tiles (8 neurons)
-    constexpr int KT = W / 16;  // k-tiles (16 neurons)
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *s32 = reinterpret_cast<float *>(smem_raw);
+    constexpr int WH = W / 2;           // neurons per thread
+    constexpr int CH = (D > 3 || WH < 16) ? 8 : 16;  // TMEM columns per load / store
+    constexpr int NCH = WH / CH;
+    constexpr int NRED = 1 + D + NH;    // partial sums a thread hands to its partner
+    constexpr int OPB = kTile * W * 2;  // bytes of one operand tile
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_bar;
+
+    // shared memory: [bf16 weights][operand Z][operands T^(0..D-1)][fp32 weights]
+    //                [partial sums NRED x 256][stage areas 64 x stage_stride]
+    unsigned char *w16 = smem_raw;
+    unsigned char *opZ = w16 + lay.b16_bytes;
+    unsigned char *opT = opZ + OPB;
+    float *s32 = reinterpret_cast<float *>(opT + D * OPB);
     const int f32_bytes = (lay.f32_total * 4 + 15) / 16 * 16;
-    __nv_bfloat16 *s16 = reinterpret_cast<__nv_bfloat16 *>(smem_raw + f32_bytes);
-    const int b16_bytes = (lay.b16_total * 2 + 15) / 16 * 16;
+    float *red = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(s32) + f32_bytes);
+    float *stage_base = red + kThreads * NRED;
     {
-        const int4 *src = reinterpret_cast<const int4 *>(gw32);
-        int4 *dst = reinterpret_cast<int4 *>(smem_raw);
-        for (int i = threadIdx.x; i < f32_bytes / 16; i += blockDim.x) dst[i] = src[i];
-        const int4 *src16 = reinterpret_cast<const int4 *>(gw16);
-        int4 *dst16 = reinterpret_cast<int4 *>(smem_raw + f32_bytes);
-        for (int i = threadIdx.x; i < b16_bytes / 16; i += blockDim.x) dst16[i] = src16[i];
+        const int4 *src = reinterpret_cast<const int4 *>(gw16);
+        int4 *dst = reinterpret_cast<int4 *>(w16);
+        for (int i = threadIdx.x; i < lay.b16_bytes / 16; i += blockDim.x) dst[i] = src[i];
+        const int4 *src32 = reinterpret_cast<const int4 *>(gw32);
+        int4 *dst32 = reinterpret_cast<int4 *>(s32);
+        for (int i = threadIdx.x; i < f32_bytes / 16; i += blockDim.x) dst32[i] = src32[i];
     }
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row = tid & (kTile - 1), half = tid >> 7;  // point in the tile, neuron half
+    const int j0 = half * WH;
+    if (warp == 0) {
+        tmem_alloc(&s_tmem, tmem_cols);
+        tmem_relinquish();
+    }
+    if (tid == 0) mbar_init(&s_bar, 1);
+    fence_async_smem();
+    tc_fence_before();
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, t = lane & 3;
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);  // this thread's lane, column 0
+    const uint32_t col_st = (uint32_t)(D * W);                  // (F', F''/D) pairs of layer k at col_st + (k-1) W
+    const uint32_t sa_opZ = smem_addr(opZ), sa_opT = smem_addr(opT), sa_w = smem_addr(w16);
     const int L = lay.L;
-    __half *ws = reinterpret_cast<__half *>(smem_raw + f32_bytes + b16_bytes) + (size_t)warp * kPW * pstride;
-    // s_k of point p, neuron j: ws[p * pstride + (k-1) * W + j]; t_k / D_k at (L + k - 1) * W
-    const int64_t n_tiles = (n_qp + kPW - 1) / kPW;
-    const int64_t n_gwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const bool want_A = A != nullptr;
+    const int g = lane >> 2, t4 = lane & 3;
+    float *st = stage_base + (size_t)(warp * 8 + g) * stage_stride;
+    uint32_t phase = 0;
+    bool aborted = false;
 
-    for (int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; tile < n_tiles; tile += n_gwarps) {
-        // ---- kinematics of the two points this lane holds (rows g and g + 8)
-        float F[2][9], K[2][D], Jm1[2];
-        bool bad[2], valid[2];
-        PolyChain<float> ch[2];
-        int64_t q[2];
+    const int64_t n_tiles = (n_qp + kTile - 1) / kTile;
+    int64_t tile = blockIdx.x;
+    for (; tile < n_tiles; tile += gridDim.x) {
+        const int64_t q = tile * kTile + row;
+        const bool valid = q < n_qp;
+        float F[9], K[D], Jm1;
+        PolyChain<float> ch;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            q[h] = tile * kPW + g + 8 * h;
-            valid[h] = q[h] < n_qp;
+        for (int c = 0; c < 9; ++c) F[c] = valid ? Fg[c * n_qp + q] : ((c % 4) == 0 ? 1.f : 0.f);
+        bool bad = !kin_scalars_f32<NF>(F, kc, K, Jm1, &ch);
+        if (bad) {
 #pragma unroll
-            for (int c = 0; c < 9; ++c) F[h][c] = valid[h] ? Fg[c * n_qp + q[h]] : ((c % 4) == 0 ? 1.f : 0.f);
-            bad[h] = !kin_scalars_f32<NF>(F[h], kc, K[h], Jm1[h], &ch[h]);
-            if (bad[h]) {
+            for (int c = 0; c < 9; ++c) F[c] = (c % 4) == 0 ? 1.f : 0.f;
+            kin_scalars_f32<NF>(F, kc, K, Jm1, &ch);
+        }
+
+        // ---- forward values; layer 1 in fp32
+        float npart = 0.f;
+#pragma unroll 1
+        for (int c = 0; c < NCH; ++c) {
+            float zz[CH];
+            uint32_t sv[CH];
 #pragma unroll
-                for (int c = 0; c < 9; ++c) F[h][c] = (c % 4) == 0 ? 1.f : 0.f;
-                kin_scalars_f32<NF>(F[h], kc, K[h], Jm1[h], &ch[h]);
+            for (int u = 0; u < CH; ++u) {
+                const int j = j0 + c * CH + u;
+                const float y = s32[lay.c + j] + dot_w<D>(s32 + lay.W1 + j * lay.dp, K);
+                float z, s, tt;
+                act(y, z, s, tt);
+                sv[u] = pack_half2(s, tt);
+                zz[u] = z;
+                if (L == 1) npart += s32[lay.a + j] * z;
+            }
+            tmem_st<CH>(tl + col_st + j0 + c * CH, sv);
+            if (L > 1) {
+#pragma unroll
+                for (int u = 0; u < CH; u += 8) store_row8<W>(opZ, row, j0 + c * CH + u, zz + u);
             }
         }
-        __half *wrow[2] = {ws + g * pstride, ws + (g + 8) * pstride};
-
-        // ---- forward values
-        float acc[NT][4];
-        uint32_t af[KT][4];
-        float npart[2] = {0.f, 0.f};
-        for (int k = 1; k <= L; ++k) {
-            if (k == 1) {
-#pragma unroll
-                for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int j = 8 * nt + 2 * t + (e & 1), h = e >> 1;
-                        float y = s32[lay.c + j];
-#pragma unroll
-                        for (int m = 0; m < D; ++m) y += s32[lay.W1 + j * lay.dp + m] * K[h][m];
-                        acc[nt][e] = y;
-                    }
-            } else {
-                const __nv_bfloat16 *Ab = s16 + lay.Ab + (k - 2) * W * lay.ld;
-#pragma unroll
-                for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int j = 8 * nt + 2 * t + (e & 1), h = e >> 1;
-                        float y = s32[lay.c + (k - 1) * W + j];
-#pragma unroll
-                        for (int m = 0; m < D; ++m) y += s32[lay.Bk + ((k - 2) * W + j) * lay.dp + m] * K[h][m];
-                        acc[nt][e] = y;
-                    }
-#pragma unroll
-                for (int kt = 0; kt < KT; ++kt)
-#pragma unroll
-                    for (int nt = 0; nt < NT; ++nt) {
-                        const __nv_bfloat16 *bp = Ab + (8 * nt + g) * lay.ld + 16 * kt + 2 * t;
-                        const uint32_t b0 = *reinterpret_cast<const uint32_t *>(bp);
-                        const uint32_t b1 = *reinterpret_cast<const uint32_t *>(bp + 8);
-                        mma_bf16(acc[nt], af[kt], b0, b1);
-                    }
+        for (int k = 2; k <= L; ++k) {
+            const uint32_t wk = sa_w + (uint32_t)(lay.Ab + (k - 2) * W * W * 2);
+            if (!mma_round(&s_bar, phase, [&] { issue_gemm<W>(tmem, sa_opZ, wk); })) {
+                aborted = true;
+                break;
             }
-            // activation; s_k, t_k to shared memory; z to the next layer's A fragments
+            const float *ck = s32 + lay.c + (k - 1) * W;
+            const float *Bk = s32 + lay.Bk + (k - 2) * W * lay.dp;
+#pragma unroll 1
+            for (int c = 0; c < NCH; ++c) {
+                uint32_t acc[CH], sv[CH];
+                float zz[CH];
+                tmem_ld<CH>(tl + j0 + c * CH, acc);
+                tmem_wait_ld();
 #pragma unroll
-            for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int j = 8 * nt + 2 * t + (e & 1), h = e >> 1;
+                for (int u = 0; u < CH; ++u) {
+                    const int j = j0 + c * CH + u;
+                    const float y = __uint_as_float(acc[u]) + ck[j] + dot_w<D>(Bk + j * lay.dp, K);
                     float z, s, tt;
-                    act(acc[nt][e], z, s, tt);
-                    wrow[h][(k - 1) * W + j] = __float2half_rn(s);
-                    wrow[h][(L + k - 1) * W + j] = __float2half_rn(tt);
-                    if (k == L) npart[h] += s32[lay.a + j] * z;
-                    acc[nt][e] = z;
+                    act(y, z, s, tt);
+                    sv[u] = pack_half2(s, tt);
+                    zz[u] = z;
+                    if (k == L) npart += s32[lay.a + j] * z;
                 }
-            if (k < L) {
-#pragma unroll
-                for (int kt = 0; kt < KT; ++kt) {
-                    af[kt][0] = pack_bf16(acc[2 * kt][0], acc[2 * kt][1]);
-                    af[kt][1] = pack_bf16(acc[2 * kt][2], acc[2 * kt][3]);
-                    af[kt][2] = pack_bf16(acc[2 * kt + 1][0], acc[2 * kt + 1][1]);
-                    af[kt][3] = pack_bf16(acc[2 * kt + 1][2], acc[2 * kt + 1][3]);
-                }
-            }
-        }
-        if (t == 0) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-                for (int m = 0; m < D; ++m) npart[h] += s32[lay.b + m] * K[h][m];
-        }
-
-        // ---- reverse adjoints: zbar_L = a; ybar = s zbar; D = t zbar; zbar_{k-1} = ybar_k A_k
-        float dN[2][D];
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-            for (int m = 0; m < D; ++m) dN[h][m] = (t == 0) ? s32[lay.b + m] : 0.f;
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[nt][e] = s32[lay.a + 8 * nt + 2 * t + (e & 1)];  // zbar_L
-        for (int k = L; k >= 1; --k) {
-            const float *Bm = (k == 1) ? (s32 + lay.W1) : (s32 + lay.Bk + (k - 2) * W * lay.dp);
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int j = 8 * nt + 2 * t + (e & 1), h = e >> 1;
-                    const float zb = acc[nt][e];
-                    const float yb = __half2float(wrow[h][(k - 1) * W + j]) * zb;
-                    wrow[h][(L + k - 1) * W + j] =
-                        __float2half_rn(__half2float(wrow[h][(L + k - 1) * W + j]) * zb);  // D_k = t_k zbar_k
-#pragma unroll
-                    for (int m = 0; m < D; ++m) dN[h][m] += Bm[j * lay.dp + m] * yb;
-                    acc[nt][e] = yb;
-                }
-            if (k == 1) break;
-#pragma unroll
-            for (int kt = 0; kt < KT; ++kt) {
-                af[kt][0] = pack_bf16(acc[2 * kt][0], acc[2 * kt][1]);
-                af[kt][1] = pack_bf16(acc[2 * kt][2], acc[2 * kt][3]);
-                af[kt][2] = pack_bf16(acc[2 * kt + 1][0], acc[2 * kt + 1][1]);
-                af[kt][3] = pack_bf16(acc[2 * kt + 1][2], acc[2 * kt + 1][3]);
-            }
-            const __nv_bfloat16 *Atb = s16 + lay.Atb + (k - 2) * W * lay.ld;
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) acc[nt][e] = 0.f;
-#pragma unroll
-            for (int kt = 0; kt < KT; ++kt)
-#pragma unroll
-                for (int nt = 0; nt < NT; ++nt) {
-                    const __nv_bfloat16 *bp = Atb + (8 * nt + g) * lay.ld + 16 * kt + 2 * t;
-                    const uint32_t b0 = *reinterpret_cast<const uint32_t *>(bp);
-                    const uint32_t b1 = *reinterpret_cast<const uint32_t *>(bp + 8);
-                    mma_bf16(acc[nt], af[kt], b0, b1);
-                }
-        }
-        __syncwarp();
-
-        // ---- forward tangents and Hessian: H = sum_k J_k^T diag(D_k) J_k
-        float Hs[2][NH];
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-            for (int i = 0; i < NH; ++i) Hs[h][i] = 0.f;
-        const bool want_A = (A != nullptr);  // P alone needs dN/dK, not the Hessian
-        // layer 1: J_1 = W1
-#pragma unroll
-        for (int nt = 0; nt < NT && want_A; ++nt)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int j = 8 * nt + 2 * t + (e & 1), h = e >> 1;
-                const float Dj = __half2float(wrow[h][L * W + j]);
-                const float *w1 = s32 + lay.W1 + j * lay.dp;
-#pragma unroll
-                for (int m = 0; m < D; ++m) {
-                    const float dm = Dj * w1[m];
-#pragma unroll
-                    for (int n = 0; n <= m; ++n) Hs[h][m * (m + 1) / 2 + n] += dm * w1[n];
-                }
-            }
-        if (L >= 2 && want_A) {
-            // A fragments of s_1 (x) W1[:, m] for every input m
-            uint32_t tf[D][KT][4];
-#pragma unroll
-            for (int m = 0; m < D; ++m)
-#pragma unroll
-                for (int kt = 0; kt < KT; ++kt) {
-                    float v[8];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        // element e: nt = 2kt + (e >> 2), (e & 3) as in the C layout
-                        const int nt = 2 * kt + (e >> 2), ee = e & 3;
-                        const int j = 8 * nt + 2 * t + (ee & 1), h = ee >> 1;
-                        v[e] = __half2float(wrow[h][j]) * s32[lay.W1 + j * lay.dp + m];
-                    }
-                    tf[m][kt][0] = pack_bf16(v[0], v[1]);
-                    tf[m][kt][1] = pack_bf16(v[2], v[3]);
-                    tf[m][kt][2] = pack_bf16(v[4], v[5]);
-                    tf[m][kt][3] = pack_bf16(v[6], v[7]);
-                }
-            for (int k = 2; k <= L; ++k) {
-                const __nv_bfloat16 *Ab = s16 + lay.Ab + (k - 2) * W * lay.ld;
-                float jac[D][NT][4];
-#pragma unroll
-                for (int m = 0; m < D; ++m)
-#pragma unroll
-                    for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            jac[m][nt][e] = s32[lay.Bk + ((k - 2) * W + 8 * nt + 2 * t + (e & 1)) * lay.dp + m];
-#pragma unroll
-                for (int kt = 0; kt < KT; ++kt)
-#pragma unroll
-                    for (int nt = 0; nt < NT; ++nt) {
-                        const __nv_bfloat16 *bp = Ab + (8 * nt + g) * lay.ld + 16 * kt + 2 * t;
-                        const uint32_t b0 = *reinterpret_cast<const uint32_t *>(bp);
-                        const uint32_t b1 = *reinterpret_cast<const uint32_t *>(bp + 8);
-#pragma unroll
-                        for (int m = 0; m < D; ++m) mma_bf16(jac[m][nt], tf[m][kt], b0, b1);
-                    }
-#pragma unroll
-                for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int j = 8 * nt + 2 * t + (e & 1), h = e >> 1;
-                        const float Dj = __half2float(wrow[h][(L + k - 1) * W + j]);
-#pragma unroll
-                        for (int m = 0; m < D; ++m) {
-                            const float dm = Dj * jac[m][nt][e];
-#pragma unroll
-                            for (int n = 0; n <= m; ++n) Hs[h][m * (m + 1) / 2 + n] += dm * jac[n][nt][e];
-                        }
-                    }
+                tmem_st<CH>(tl + col_st + (k - 1) * W + j0 + c * CH, sv);
                 if (k < L) {
+#pragma unroll
+                    for (int u = 0; u < CH; u += 8) store_row8<W>(opZ, row, j0 + c * CH + u, zz + u);
+                }
+            }
+        }
+        if (aborted) break;
+        if (half == 0) npart += dot_w<D>(s32 + lay.b, K);
+
+        // ---- reverse adjoints: zbar_L = a; ybar = F' zbar; D = F'' zbar; zbar_{k-1} = ybar_k A_k
+        float dN[D];
+        load_w<D>(s32 + lay.b, dN);
+        if (half != 0) {
+#pragma unroll
+            for (int m = 0; m < D; ++m) dN[m] = 0.f;
+        }
+        tmem_wait_st();  // layer L's (F', F'') pairs are read back below
+        for (int k = L; k >= 1; --k) {
+            if (k < L) {
+                const uint32_t wt = sa_w + (uint32_t)(lay.Atb + (k - 1) * W * W * 2);  // A_{k+1}^T
+                if (!mma_round(&s_bar, phase, [&] { issue_gemm<W>(tmem, sa_opZ, wt); })) {
+                    aborted = true;
+                    break;
+                }
+            }
+            const float *Bw = (k == 1) ? (s32 + lay.W1) : (s32 + lay.Bk + (k - 2) * W * lay.dp);
+#pragma unroll 1
+            for (int c = 0; c < NCH; ++c) {
+                uint32_t sv[CH], acc[CH];
+                float yv[CH];
+                tmem_ld<CH>(tl + col_st + (k - 1) * W + j0 + c * CH, sv);
+                if (k < L) tmem_ld<CH>(tl + j0 + c * CH, acc);
+                tmem_wait_ld();
+#pragma unroll
+                for (int u = 0; u < CH; ++u) {
+                    const int j = j0 + c * CH + u;
+                    const float zb = (k < L) ? __uint_as_float(acc[u]) : s32[lay.a + j];
+                    const float2 s_t = unpack_half2(sv[u]);
+                    const float yb = s_t.x * zb;
+                    sv[u] = pack_half2(s_t.x, s_t.y * zb);
+                    float w[D];
+                    load_w<D>(Bw + j * lay.dp, w);
+#pragma unroll
+                    for (int m = 0; m < D; ++m) dN[m] += w[m] * yb;
+                    yv[u] = yb;
+                }
+                tmem_st<CH>(tl + col_st + (k - 1) * W + j0 + c * CH, sv);
+                if (k >= 2) {
+#pragma unroll
+                    for (int u = 0; u < CH; u += 8) store_row8<W>(opZ, row, j0 + c * CH + u, yv + u);
+                }
+            }
+        }
+        if (aborted) break;
+
+        // ---- forward tangents and the Hessian H = sum_k J_k^T diag(D_k) J_k
+        float Hs[NH];
+#pragma unroll
+        for (int i = 0; i < NH; ++i) Hs[i] = 0.f;
+        if (want_A) {
+            tmem_wait_st();
+#pragma unroll 1
+            for (int c = 0; c < NCH; ++c) {
+                uint32_t sv[CH];
+                float tv[D][CH];
+                tmem_ld<CH>(tl + col_st + j0 + c * CH, sv);
+                tmem_wait_ld();
+#pragma unroll
+                for (int u = 0; u < CH; ++u) {
+                    const int j = j0 + c * CH + u;
+                    const float2 s_d = unpack_half2(sv[u]);
+                    float w[D];
+                    load_w<D>(s32 + lay.W1 + j * lay.dp, w);
+#pragma unroll
+                    for (int m = 0; m < D; ++m) {
+                        const float dm = s_d.y * w[m];
+#pragma unroll
+                        for (int n = 0; n <= m; ++n) Hs[m * (m + 1) / 2 + n] += dm * w[n];
+                        tv[m][u] = s_d.x * w[m];
+                    }
+                }
+                if (L > 1) {
 #pragma unroll
                     for (int m = 0; m < D; ++m)
 #pragma unroll
-                        for (int kt = 0; kt < KT; ++kt) {
-                            float v[8];
-#pragma unroll
-                            for (int e = 0; e < 8; ++e) {
-                                const int nt = 2 * kt + (e >> 2), ee = e & 3;
-                                const int j = 8 * nt + 2 * t + (ee & 1), h = ee >> 1;
-                                v[e] = __half2float(wrow[h][(k - 1) * W + j]) * jac[m][nt][ee];
-                            }
-                            tf[m][kt][0] = pack_bf16(v[0], v[1]);
-                            tf[m][kt][1] = pack_bf16(v[2], v[3]);
-                            tf[m][kt][2] = pack_bf16(v[4], v[5]);
-                            tf[m][kt][3] = pack_bf16(v[6], v[7]);
-                        }
+                        for (int u = 0; u < CH; u += 8) store_row8<W>(opT + m * OPB, row, j0 + c * CH + u, tv[m] + u);
                 }
             }
+            for (int k = 2; k <= L; ++k) {
+                const uint32_t wk = sa_w + (uint32_t)(lay.Ab + (k - 2) * W * W * 2);
+                if (!mma_round(&s_bar, phase, [&] {
+#pragma unroll
+                        for (int m = 0; m < D; ++m)
+                            issue_gemm<W>(tmem + (uint32_t)(m * W), sa_opT + (uint32_t)(m * OPB), wk);
+                    })) {
+                    aborted = true;
+                    break;
+                }
+                const float *Bk = s32 + lay.Bk + (k - 2) * W * lay.dp;
+#pragma unroll 1
+                for (int c = 0; c < NCH; ++c) {
+                    uint32_t jv[D][CH], sv[CH];
+#pragma unroll
+                    for (int m = 0; m < D; ++m) tmem_ld<CH>(tl + m * W + j0 + c * CH, jv[m]);
+                    tmem_ld<CH>(tl + col_st + (k - 1) * W + j0 + c * CH, sv);
+                    tmem_wait_ld();
+                    float tv[D][CH];
+#pragma unroll
+                    for (int u = 0; u < CH; ++u) {
+                        const int j = j0 + c * CH + u;
+                        const float2 s_d = unpack_half2(sv[u]);
+                        float Jm[D];
+                        load_w<D>(Bk + j * lay.dp, Jm);
+#pragma unroll
+                        for (int m = 0; m < D; ++m) Jm[m] += __uint_as_float(jv[m][u]);
+#pragma unroll
+                        for (int m = 0; m < D; ++m) {
+                            const float dm = s_d.y * Jm[m];
+#pragma unroll
+                            for (int n = 0; n <= m; ++n) Hs[m * (m + 1) / 2 + n] += dm * Jm[n];
+                            tv[m][u] = s_d.x * Jm[m];
+                        }
+                    }
+                    if (k < L) {
+#pragma unroll
+                        for (int m = 0; m < D; ++m)
+#pragma unroll
+                            for (int u = 0; u < CH; u += 8) store_row8<W>(opT + m * OPB, row, j0 + c * CH + u, tv[m] + u);
+                    }
+                }
+            }
+            if (aborted) break;
         }
 
-        // ---- reduce over the 4 lanes that share rows g, g + 8
+        // ---- the two halves' partial sums: npart, dN, Hs
+        {
+            float *mine = red + tid;  // entry i at mine[i * kThreads]
+            mine[0] = npart;
 #pragma unroll
-        for (int msk = 1; msk <= 2; msk <<= 1)
+            for (int m = 0; m < D; ++m) mine[(1 + m) * kThreads] = dN[m];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                npart[h] += __shfl_xor_sync(0xffffffffu, npart[h], msk);
+            for (int i = 0; i < NH; ++i) mine[(1 + D + i) * kThreads] = Hs[i];
+            __syncthreads();
+            const float *other = red + (tid ^ kTile);
+            npart += other[0];
 #pragma unroll
-                for (int m = 0; m < D; ++m) dN[h][m] += __shfl_xor_sync(0xffffffffu, dN[h][m], msk);
+            for (int m = 0; m < D; ++m) dN[m] += other[(1 + m) * kThreads];
 #pragma unroll
-                for (int i = 0; i < NH; ++i) Hs[h][i] += __shfl_xor_sync(0xffffffffu, Hs[h][i], msk);
-            }
-        __syncwarp();
+            for (int i = 0; i < NH; ++i) Hs[i] += other[(1 + D + i) * kThreads];
+            __syncthreads();
+        }
 
-        // ---- P, A, Psi: the 4 lanes (t) of row g act as the point's group, twice
+        // ---- P, A, Psi: the warp's 32 points in 4 rounds of 8 groups of 4 lanes
+        float cvec[D];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            float *st = reinterpret_cast<float *>(ws + (g + 8 * h) * pstride);  // reuses the s/D area
-            float cvec[D];
+        for (int m = 0; m < D; ++m) cvec[m] = dN[m] - s32[lay.n0 + m];
+        if constexpr (NF == 0) {
+            if (kc.kin == COMMET_KIN_POLYCONVEX) poly_to_invariants<float>(ch, cvec, Hs);
+        }
+#pragma unroll 1
+        for (int r = 2 * half; r < 2 * half + 2; ++r) {
+            const int src = 8 * r + g;
+            float Fr[9], cr[D], Hr[NH], Kr[D];
 #pragma unroll
-            for (int m = 0; m < D; ++m) cvec[m] = dN[h][m] - s32[lay.n0 + m];
-            if constexpr (NF == 0) {
-                if (kc.kin == COMMET_KIN_POLYCONVEX) poly_to_invariants<float>(ch[h], cvec, Hs[h]);
+            for (int c = 0; c < 9; ++c) Fr[c] = __shfl_sync(0xffffffffu, F[c], src);
+#pragma unroll
+            for (int m = 0; m < D; ++m) {
+                cr[m] = __shfl_sync(0xffffffffu, cvec[m], src);
+                Kr[m] = __shfl_sync(0xffffffffu, K[m], src);
             }
+#pragma unroll
+            for (int i = 0; i < NH; ++i) Hr[i] = want_A ? __shfl_sync(0xffffffffu, Hs[i], src) : 0.f;
+            const float Jr = __shfl_sync(0xffffffffu, Jm1, src);
+            const float npr = __shfl_sync(0xffffffffu, npart, src);
+            const bool badr = __shfl_sync(0xffffffffu, bad ? 1 : 0, src) != 0;
+            const int64_t qr = tile * kTile + (warp & 3) * 32 + src;
+            const bool validr = qr < n_qp;
             __syncwarp();
-            stage_kinematics<float, NF>(F[h], kc, cvec, Jm1[h], t, st);
+            stage_kinematics<float, NF>(Fr, kc, cr, Jr, t4, st);
             __syncwarp();
             bool nonfinite = false;
             // spatial form: P and A go to the point's area after its staging, then are
             // pushed forward to tau (written through P) and c (through A)
             constexpr int kStageF = (9 * D + 54 + 18 * NF + 5 + NF + 3) / 4 * 4;
             float *pa = st + kStageF;
-            for (int a = t; a < 9; a += 4) {
+            for (int a = t4; a < 9; a += 4) {
                 float Pa, Arow[9];
                 if (want_A) {
-                    assemble_row<float, NF>(a, st, Hs[h], cvec, Pa, Arow);
+                    assemble_row<float, NF>(a, st, Hr, cr, Pa, Arow);
                 } else {
-                    Pa = assemble_P<float, NF>(a, st, cvec);
+                    Pa = assemble_P<float, NF>(a, st, cr);
 #pragma unroll
                     for (int b = 0; b < 9; ++b) Arow[b] = 0.f;
                 }
@@ -409,54 +499,74 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
                 for (int b = 0; b < 9; ++b) fin = fin && isfinite(Arow[b]);
                 nonfinite |= !fin;
-                const bool nan_out = bad[h] || !fin;
+                const bool nan_out = badr || !fin;
                 if constexpr (SPATIAL) {
                     pa[a] = nan_out ? NAN : Pa;
-                    if (A != nullptr) {
+                    if (want_A) {
 #pragma unroll
                         for (int b = 0; b < 9; ++b) pa[9 + 9 * a + b] = nan_out ? NAN : Arow[b];
                     }
-                } else if (valid[h]) {
-                    P[a * n_qp + q[h]] = nan_out ? NAN : Pa;
-                    if (A != nullptr) {
+                } else if (validr) {
+                    P[a * n_qp + qr] = nan_out ? NAN : Pa;
+                    if (want_A) {
 #pragma unroll
-                        for (int b = 0; b < 9; ++b) A[(9 * a + b) * n_qp + q[h]] = nan_out ? NAN : Arow[b];
+                        for (int b = 0; b < 9; ++b) A[(9 * a + b) * n_qp + qr] = nan_out ? NAN : Arow[b];
                     }
                 }
             }
             if constexpr (SPATIAL) {
                 __syncwarp();
-                const int64_t qo = valid[h] ? q[h] : 0;
-                push_forward_group<float>(st + Stage<D, NF>::F, pa, pa + 9, t, valid[h], P + qo,
-                                          A != nullptr ? A + qo : nullptr, n_qp);
+                const int64_t qo = validr ? qr : 0;
+                push_forward_group<float>(st + Stage<D, NF>::F, pa, pa + 9, t4, validr, P + qo,
+                                          want_A ? A + qo : nullptr, n_qp);
             }
             const unsigned nf_mask = __ballot_sync(0xffffffffu, nonfinite);
             const bool grp_nonfinite = ((nf_mask >> (g * 4)) & 0xFu) != 0u;
-            if (valid[h] && t == 0) {
-                float Psi = npart[h] + kc.kappa * Jm1[h] * Jm1[h];
+            if (validr && t4 == 0) {
+                float Psi = npr + kc.kappa * Jr * Jr;
 #pragma unroll
-                for (int m = 0; m < D; ++m) Psi -= s32[lay.n0 + m] * (K[h][m] - s32[lay.K0 + m]);
-                const bool rep = bad[h] || grp_nonfinite || !isfinite(Psi);
-                if (psi != nullptr) psi[q[h]] = rep ? NAN : Psi;
+                for (int m = 0; m < D; ++m) Psi -= s32[lay.n0 + m] * (Kr[m] - s32[lay.K0 + m]);
+                const bool rep = badr || grp_nonfinite || !isfinite(Psi);
+                if (psi != nullptr) psi[qr] = rep ? NAN : Psi;
                 if (rep && status != nullptr) {
                     atomicAdd(&status[0], 1);
-                    atomicMin(&status[1], (int32_t)(q[h] < INT32_MAX ? q[h] : INT32_MAX));
+                    atomicMin(&status[1], (int32_t)(qr < INT32_MAX ? qr : INT32_MAX));
                 }
             }
+            __syncwarp();
         }
-        __syncwarp();
     }
+    if (aborted) {
+        // an MMA batch did not complete within the bound: report the points this CTA did not
+        // produce, give the batch a last bounded wait, and release tensor memory
+        if (tid == 0) {
+            atomicOr(err, 1);
+            if (status != nullptr) {
+                int64_t missing = 0;
+                for (int64_t t2 = tile; t2 < n_tiles; t2 += gridDim.x) {
+                    const int64_t left = n_qp - t2 * kTile;
+                    missing += left < kTile ? left : kTile;
+                }
+                const int64_t first = tile * kTile;
+                atomicAdd(&status[0], (int32_t)(missing < INT32_MAX ? missing : INT32_MAX));
+                atomicMin(&status[1], (int32_t)(first < INT32_MAX ? first : INT32_MAX));
+            }
+        }
+        mbar_wait_bounded(&s_bar, phase ^ 1u, kWaitTries);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, tmem_cols);
 }
 
 // ------------------------------------------------------------------- host side
 
-static B16Layout b16_layout(int d, int W, int L) {
-    B16Layout l{};
+static TcLayout tc_layout(int d, int W, int L) {
+    TcLayout l{};
     l.d = d;
     l.dp = (d + 3) / 4 * 4;
     l.W = W;
     l.L = L;
-    l.ld = W + 8;
     int o = 0;
     l.W1 = o; o += W * l.dp;
     l.Bk = o; o += (L - 1) * W * l.dp;
@@ -466,56 +576,57 @@ static B16Layout b16_layout(int d, int W, int L) {
     l.n0 = o; o += l.dp;
     l.K0 = o; o += l.dp;
     l.f32_total = (o + 3) / 4 * 4;
-    int p = 0;
-    l.Ab = p; p += (L - 1) * W * l.ld;
-    l.Atb = p; p += (L - 1) * W * l.ld;
-    l.b16_total = (p + 7) / 8 * 8;
+    l.Ab = 0;
+    l.Atb = (L - 1) * W * W * 2;
+    l.b16_bytes = 2 * (L - 1) * W * W * 2;
     return l;
 }
 
-// Builds the bf16-path weight block from the fp32 packed block of the model (device
-// to host copy at creation; kept in m->d_bf16).
+static size_t f32_part_bytes(const TcLayout &l) { return ((size_t)l.f32_total * 4 + 15) / 16 * 16; }
+
+// Builds the bf16-path weight block from the fp32 packed block of the model (device to
+// host copy at creation; kept in m->d_bf16, followed by a 16-byte device error word).
 int prepare_bf16_weights(commet_model *m) {
     const int d = m->d, W = m->W, L = m->L;
     const NetLayout &nl = m->lay;
-    const B16Layout bl = b16_layout(d, W, L);
+    const TcLayout tl = tc_layout(d, W, L);
     float *h = new float[nl.total];
     if (cudaMemcpy(h, m->d_weights, sizeof(float) * nl.total, cudaMemcpyDeviceToHost) != cudaSuccess) {
         delete[] h;
         return COMMET_ERR_CUDA;
     }
     const int dpn = (d + 3) / 4 * 4;
-    const size_t f32_bytes = ((size_t)bl.f32_total * 4 + 15) / 16 * 16;
-    const size_t b16_bytes = ((size_t)bl.b16_total * 2 + 15) / 16 * 16;
-    unsigned char *buf = new unsigned char[f32_bytes + b16_bytes]();
+    const size_t f32_bytes = f32_part_bytes(tl);
+    const size_t total = f32_bytes + (size_t)tl.b16_bytes + 16;
+    unsigned char *buf = new unsigned char[total]();
     float *f = reinterpret_cast<float *>(buf);
-    __nv_bfloat16 *bb = reinterpret_cast<__nv_bfloat16 *>(buf + f32_bytes);
+    unsigned char *bb = buf + f32_bytes;
     for (int j = 0; j < W; ++j)
-        for (int mm = 0; mm < d; ++mm) f[bl.W1 + j * bl.dp + mm] = h[nl.W1r + j * dpn + mm];
+        for (int mm = 0; mm < d; ++mm) f[tl.W1 + j * tl.dp + mm] = h[nl.W1r + j * dpn + mm];
     for (int k = 0; k < L - 1; ++k)
         for (int j = 0; j < W; ++j) {
-            for (int mm = 0; mm < d; ++mm) f[bl.Bk + (k * W + j) * bl.dp + mm] = h[nl.Bt + k * d * W + mm * W + j];
+            for (int mm = 0; mm < d; ++mm) f[tl.Bk + (k * W + j) * tl.dp + mm] = h[nl.Bt + k * d * W + mm * W + j];
             for (int i = 0; i < W; ++i) {
-                const float aji = h[nl.Ar + k * W * W + j * W + i];
-                bb[bl.Ab + (k * W + j) * bl.ld + i] = __float2bfloat16_rn(aji);
-                bb[bl.Atb + (k * W + i) * bl.ld + j] = __float2bfloat16_rn(aji);
+                const __nv_bfloat16 aji = __float2bfloat16_rn(h[nl.Ar + k * W * W + j * W + i]);
+                *reinterpret_cast<__nv_bfloat16 *>(bb + tl.Ab + k * W * W * 2 + cm_byte(j, i, W)) = aji;
+                *reinterpret_cast<__nv_bfloat16 *>(bb + tl.Atb + k * W * W * 2 + cm_byte(i, j, W)) = aji;
             }
         }
-    for (int i = 0; i < L * W; ++i) f[bl.c + i] = h[nl.c + i];
-    for (int j = 0; j < W; ++j) f[bl.a + j] = h[nl.a + j];
+    for (int i = 0; i < L * W; ++i) f[tl.c + i] = h[nl.c + i];
+    for (int j = 0; j < W; ++j) f[tl.a + j] = h[nl.a + j];
     for (int mm = 0; mm < d; ++mm) {
-        f[bl.b + mm] = h[nl.b + mm];
-        f[bl.n0 + mm] = h[nl.n0 + mm];
-        f[bl.K0 + mm] = h[nl.K0 + mm];
+        f[tl.b + mm] = h[nl.b + mm];
+        f[tl.n0 + mm] = h[nl.n0 + mm];
+        f[tl.K0 + mm] = h[nl.K0 + mm];
     }
     delete[] h;
     cudaFree(m->d_bf16);
     m->d_bf16 = nullptr;
     int rc = COMMET_OK;
-    if (cudaMalloc(&m->d_bf16, f32_bytes + b16_bytes) != cudaSuccess ||
-        cudaMemcpy(m->d_bf16, buf, f32_bytes + b16_bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+    if (cudaMalloc(&m->d_bf16, total) != cudaSuccess ||
+        cudaMemcpy(m->d_bf16, buf, total, cudaMemcpyHostToDevice) != cudaSuccess)
         rc = COMMET_ERR_CUDA;
-    m->bf16_bytes = f32_bytes + b16_bytes;
+    m->bf16_bytes = total;
     delete[] buf;
     return rc;
 }
@@ -523,46 +634,57 @@ int prepare_bf16_weights(commet_model *m) {
 template <int NF, int W, bool SPATIAL>
 static int bf16_typed(const commet_model *m, int64_t n_qp, const void *F, void *psi, void *P, void *A,
                       int32_t *status, cudaStream_t s) {
+    constexpr int D = 3 + 2 * NF;
+    const int L = m->L;
+    // tensor memory: D W accumulator columns + L W (F', F'') columns, a power of two >= 32
+    const int need_cols = (D + L) * W;
+    if (need_cols > 512) return COMMET_ERR_UNSUPPORTED;
+    uint32_t cols = 32;
+    while ((int)cols < need_cols) cols <<= 1;
     KinConst<float> kc{};
     kc.kin = m->kp.kin;
     kc.stress_free = m->kp.stress_free;
     kc.kappa = (float)m->kp.kappa;
     for (int f = 0; f < 2; ++f)
         for (int c = 0; c < 3; ++c) kc.fib[f][c] = (float)m->kp.fib[f][c];
-    const B16Layout bl = b16_layout(m->d, W, m->L);
-    const size_t f32_bytes = ((size_t)bl.f32_total * 4 + 15) / 16 * 16;
-    const size_t b16_bytes = ((size_t)bl.b16_total * 2 + 15) / 16 * 16;
-    const int D = 3 + 2 * NF;
+    const TcLayout tl = tc_layout(m->d, W, L);
+    const size_t f32_bytes = f32_part_bytes(tl);
     const int stage = (9 * D + 54 + 18 * NF + 5 + NF + 3) / 4 * 4 + (SPATIAL ? 90 : 0);
-    const int raw_halves = std::max(2 * m->L * W, 2 * stage);
-    const int words = ((raw_halves + 1) / 2 + 31) / 32 * 32 + 4;  // 4-byte words per point
-    const int pstride = 2 * words;                                // halves per point
-    const size_t per_warp = (size_t)kPW * pstride * 2;
-    int dev = 0, smem_max = 0;
+    const int stage_stride = stage | 1;  // odd: the 32 group areas fall on distinct banks
+    const size_t opb = (size_t)kTile * W * 2;
+    const int nred = 1 + D + D * (D + 1) / 2;
+    size_t smem = (size_t)tl.b16_bytes + (1 + D) * opb + f32_bytes + (size_t)kThreads * nred * 4 +
+                  (size_t)64 * stage_stride * 4;
+    int dev = 0, smem_max = 0, smem_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if ((size_t)smem_max < f32_bytes + b16_bytes + per_warp) return COMMET_ERR_UNSUPPORTED;
-    const int warps = (int)std::min<size_t>(8, (smem_max - f32_bytes - b16_bytes) / per_warp);
-    const size_t smem = f32_bytes + b16_bytes + warps * per_warp;
-    auto kern = bf16_update_kernel<NF, W, SPATIAL>;
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    // no more CTAs per SM than tensor memory holds: pad the request so that shared memory
+    // admits at most 512 / cols of them
+    const int ctas_tmem = 512 / (int)cols;
+    const size_t floor_req = (size_t)smem_sm / (ctas_tmem + 1) + 1;
+    smem = std::max(smem, floor_req);
+    if ((size_t)smem_max < smem) return COMMET_ERR_UNSUPPORTED;
+    auto kern = bf16_tc_kernel<NF, W, SPATIAL>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return COMMET_ERR_CUDA;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
-    if (per_sm < 1) per_sm = 1;
-    const int64_t n_tiles = (n_qp + kPW - 1) / kPW;
-    const int64_t want = (n_tiles + warps - 1) / warps;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count() * per_sm));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+    per_sm = std::max(1, std::min(per_sm, ctas_tmem));
+    const int64_t n_tiles = (n_qp + kTile - 1) / kTile;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(n_tiles, (int64_t)sm_count() * per_sm));
     const float *w32 = (const float *)m->d_bf16;
-    const __nv_bfloat16 *w16 = (const __nv_bfloat16 *)((const unsigned char *)m->d_bf16 + f32_bytes);
-    kern<<<grid, warps * 32, smem, s>>>(w32, w16, bl, kc, n_qp, (const float *)F, (float *)psi, (float *)P,
-                                        (float *)A, status, pstride);
+    const unsigned char *w16 = (const unsigned char *)m->d_bf16 + f32_bytes;
+    int *err = (int *)((unsigned char *)m->d_bf16 + f32_bytes + tl.b16_bytes);
+    kern<<<grid, kThreads, smem, s>>>(w32, w16, tl, kc, n_qp, (const float *)F, (float *)psi, (float *)P, (float *)A,
+                                   status, err, cols, stage_stride);
     return cudaGetLastError() == cudaSuccess ? COMMET_OK : COMMET_ERR_CUDA;
 }
 
 template <bool SPATIAL>
 static int bf16_dispatch(const commet_model *m, int64_t n_qp, const void *F, void *psi, void *P, void *A,
                          int32_t *status, cudaStream_t s) {
+    if (n_qp == 0) return COMMET_OK;
     const int nf = m->kp.nf, W = m->W;
     if (nf == 0 && W == 64) return bf16_typed<0, 64, SPATIAL>(m, n_qp, F, psi, P, A, status, s);
     if (nf == 0 && W == 32) return bf16_typed<0, 32, SPATIAL>(m, n_qp, F, psi, P, A, status, s);
