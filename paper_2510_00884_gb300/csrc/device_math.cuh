@@ -44,7 +44,7 @@ __device__ __forceinline__ void act(double y, double &z, double &s, double &t) {
 }
 __device__ __forceinline__ void act(float y, float &z, float &s, float &t) {
     const float e = __expf(-fabsf(y));
-    const float r = __frcp_rn(1.0f + e);
+    const float r = __fdividef(1.0f, 1.0f + e);  // 1 + e in [1, 2]: the approximate reciprocal is within 2 ulp
     z = fmaxf(y, 0.0f) + __logf(1.0f + e);  // absolute error ~1e-7: within the FP32 tolerance
     s = (y >= 0.0f) ? r : e * r;
     t = e * r * r;
@@ -57,7 +57,7 @@ __device__ __forceinline__ void act_value_slope(double y, double &z, double &s) 
 }
 __device__ __forceinline__ void act_value_slope(float y, float &z, float &s) {
     const float e = __expf(-fabsf(y));
-    const float r = __frcp_rn(1.0f + e);
+    const float r = __fdividef(1.0f, 1.0f + e);  // 1 + e in [1, 2]: the approximate reciprocal is within 2 ulp
     z = fmaxf(y, 0.0f) + log1pf(e);
     s = (y >= 0.0f) ? r : e * r;
 }
