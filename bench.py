@@ -620,9 +620,30 @@ def run_ours(args, rank, world, local_rank):
         flops = 2 * (sL - 1) * sW * sW * (2 + spec.d) * run.n_qp
         bound = "tensor"
         peak = float(peaks.get("bf16_tflops", 1900.0))
-        peak_source = f"bf16 dense matmul burst ({peak_src} peaks file); mma.sync m16n8k16 bf16, fp32 accumulate"
-        src = ["bf16_update.cu", "device_math.cuh"]
+        peak_source = (f"bf16 dense matmul burst ({peak_src} peaks file); tcgen05.mma kind::f16, M 128, "
+                       f"fp32 accumulate in tensor memory")
+        src = ["bf16_update.cu", "umma.cuh", "device_math.cuh"]
     achieved = flops / (phase_ms[dom] * 1e-3) / 1e12
+    bounds = None
+    if prec == "bf16" and kname == "const_update_kernel":
+        # the four ceilings of this kernel: tensor (the hidden products above), MUFU (exp,
+        # reciprocal and log per neuron), FP32 (the algorithmic multiply-adds outside the
+        # hidden products) and HBM (F in; psi, P, A out)
+        sec = phase_ms[dom] * 1e-3
+        mufu = 3 * sL * sW * run.n_qp
+        f32_flops = algorithmic_flops_per_qp(spec.d, sW, sL) * run.n_qp - flops
+        per_qp = (9 + 1 + (6 + 21 if args.spatial else 9 + 81)) * 4
+        mufu_peak = 16 * n_sm * mhz * 1e6 / 1e12  # T ops/s: 16 per clock per SM
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        bounds = {
+            "tensor": {"achieved_tflops": achieved, "peak": peak, "frac": achieved / peak},
+            "mufu": {"achieved_tops": mufu / sec / 1e12, "peak": mufu_peak, "frac": mufu / sec / 1e12 / mufu_peak,
+                     "ops_per_qp": 3 * sL * sW},
+            "fp32": {"achieved_tflops": f32_flops / sec / 1e12, "peak": alu_peak_tflops("f32", n_sm, mhz),
+                     "frac": f32_flops / sec / 1e12 / alu_peak_tflops("f32", n_sm, mhz)},
+            "hbm": {"achieved_gbs": per_qp * run.n_qp / sec / 1e9, "peak": hbm,
+                    "frac": per_qp * run.n_qp / sec / 1e9 / hbm, "bytes_per_qp": per_qp},
+        }
     src_hash = kernel_source_hash(src)
     roofline = {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
@@ -631,6 +652,8 @@ def run_ours(args, rank, world, local_rank):
                 "algorithmic_flops_per_launch": flops, "kernel_ms": phase_ms[dom],
                 "frac_at_median_clock": (achieved / peak * mhz / clocks["sm_mhz"]) if clocks.get("sm_mhz") else None,
                 "src_hash": src_hash}
+    if bounds is not None:
+        roofline["bounds"] = bounds
     if kname == "const_update_kernel" and getattr(spec, "inner_name", "micnn") != "micnn":
         # no network: the algorithmic work is the output stream (9 in, 1 + 9 + 81 or
         # 1 + 6 + 21 out per point), so the roofline is HBM
