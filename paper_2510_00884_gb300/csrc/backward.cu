@@ -63,7 +63,8 @@ __host__ __device__ inline BwSlab bw_slab(int d, int W, int L, int NF, int tsize
     b.yd = o; o += L * W;
     b.yb = o; o += W;
     b.ydb = o; o += W;
-    const int stage = 9 * d + 54 + 18 * NF + 5 + NF;
+    // staged kinematics, then G and its precomputed contractions (BwPre below)
+    const int stage = 9 * d + 54 + 18 * NF + 5 + NF + 30 + 9 * NF;
     int raw = o > stage ? o : stage;
     int words = raw * tsize / 4;
     words = (words + 31) / 32 * 32 + 4;
@@ -71,64 +72,121 @@ __host__ __device__ inline BwSlab bw_slab(int d, int W, int L, int NF, int tsize
     return b;
 }
 
-// sum_a G_a S_ab for the structured part S of A (see device_math.cuh), rows b given by
-// the caller; st = staged kinematics.
+// Offsets (units of T) of G = dL/dP and of the contractions of G with the staged
+// kinematics that every row of G : S uses, placed after the staged kinematics.
+template <int D, int NF>
+struct BwPre {
+    static constexpr int G = Stage<D, NF>::size;  // [9]
+    static constexpr int Nh = G + 9;              // [9] (G^T H)_JL at 3 J + L
+    static constexpr int Nf = Nh + 9;             // [9] (G^T F)_JL
+    static constexpr int sc = Nf + 9;             // G : U, G : H, G : F
+    static constexpr int a = sc + 3;              // [NF][3] a_f = F A_f
+    static constexpr int v1 = a + 3 * NF;         // [NF][3] F^T G A_f
+    static constexpr int v23 = v1 + 3 * NF;       // [NF][3] F G^T a_f + B G A_f
+    static constexpr int size = v23 + 3 * NF;
+};
+
+// The group of 4 lanes (lane4) of a point writes G and the contractions above; lanes
+// split the components (a = lane4 + 4 t) and, with two fibres, the fibres, so that the
+// group's FP64 instructions are shared rather than repeated.
 template <typename T, int NF>
-__device__ __forceinline__ T contract_structured(int b, const T *st, const T *G) {
+__device__ __forceinline__ void structured_pre(T *st, const T (&G)[9], const KinConst<T> &kc, int lane4) {
     constexpr int D = 3 + 2 * NF;
     using S = Stage<D, NF>;
-    const int k = b / 3, L = b % 3;
-    const T *F = st + S::F, *H = st + S::H, *U = st + S::U, *X = st + S::X, *Y = st + S::Y, *Bm = st + S::Bm;
-    T GU = 0, GH = 0, GF = 0;
+    using R = BwPre<D, NF>;
+    const T *F = st + S::F, *H = st + S::H, *U = st + S::U, *Bm = st + S::Bm;
+    T *Gs = st + R::G;
 #pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        GU += G[a] * U[a];
-        GH += G[a] * H[a];
-        GF += G[a] * F[a];
+    for (int a = 0; a < 9; ++a)
+        if ((a & 3) == lane4) Gs[a] = G[a];
+    __syncwarp();
+    T gu = 0, gh = 0, gf = 0;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        const int e = lane4 + 4 * t;
+        if (e < 9) {
+            const T g = Gs[e];
+            gu += g * U[e];
+            gh += g * H[e];
+            gf += g * F[e];
+            const int J = e / 3, L = e - 3 * J;
+            T nh = 0, nf = 0;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                nh += Gs[3 * i + J] * H[3 * i + L];
+                nf += Gs[3 * i + J] * F[3 * i + L];
+            }
+            st[R::Nh + e] = nh;
+            st[R::Nf + e] = nf;
+        }
     }
+#pragma unroll
+    for (int msk = 1; msk <= 2; msk <<= 1) {
+        gu += __shfl_xor_sync(0xffffffffu, gu, msk);
+        gh += __shfl_xor_sync(0xffffffffu, gh, msk);
+        gf += __shfl_xor_sync(0xffffffffu, gf, msk);
+    }
+    if (lane4 == 0) {
+        st[R::sc + 0] = gu;
+        st[R::sc + 1] = gh;
+        st[R::sc + 2] = gf;
+    }
+    if constexpr (NF > 0) {
+        // fibre f = lane4 / 2 (lanes 0, 2 write): a = F A, GA = G A, v1 = F^T GA,
+        // w = G^T a, v23 = F w + B GA (B symmetric)
+        const int f = lane4 >> 1;
+        if (f < NF) {
+            const T *A0 = kc.fib[f];
+            T a[3], GA[3], w[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                a[i] = F[3 * i] * A0[0] + F[3 * i + 1] * A0[1] + F[3 * i + 2] * A0[2];
+                GA[i] = Gs[3 * i] * A0[0] + Gs[3 * i + 1] * A0[1] + Gs[3 * i + 2] * A0[2];
+            }
+#pragma unroll
+            for (int J = 0; J < 3; ++J) w[J] = Gs[J] * a[0] + Gs[3 + J] * a[1] + Gs[6 + J] * a[2];
+            if ((lane4 & 1) == 0) {
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    st[R::a + 3 * f + i] = a[i];
+                    st[R::v1 + 3 * f + i] = F[i] * GA[0] + F[3 + i] * GA[1] + F[6 + i] * GA[2];
+                    st[R::v23 + 3 * f + i] = F[3 * i] * w[0] + F[3 * i + 1] * w[1] + F[3 * i + 2] * w[2] +
+                                             Bm[i] * GA[0] + Bm[3 + i] * GA[1] + Bm[6 + i] * GA[2];
+                }
+            }
+        }
+    }
+}
+
+// sum_a G_a S_ab for the structured part S of A (see device_math.cuh) and row b, from
+// the staged kinematics and structured_pre:
+//   (G:U) H_b + (G:H) U_b + beta (G:H) H_b + gamma (G:F) F_b - eta (H G^T H)_b
+//   + zeta (F G^T F)_b + (G X)_b + (Y G)_b
+//   + sum_f 2 c5_f [a_k (F^T G A)_L + A_L (F G^T a + B G A)_k],   b = 3 k + L.
+template <typename T, int NF>
+__device__ __forceinline__ T contract_structured(int b, const T *st, const KinConst<T> &kc) {
+    constexpr int D = 3 + 2 * NF;
+    using S = Stage<D, NF>;
+    using R = BwPre<D, NF>;
+    const int k = b / 3, L = b % 3;
+    const T *F = st + S::F, *H = st + S::H, *U = st + S::U, *X = st + S::X, *Y = st + S::Y;
+    const T *Gs = st + R::G;
+    const T GU = st[R::sc + 0], GH = st[R::sc + 1], GF = st[R::sc + 2];
     const T beta = st[S::sc + 0], gamma = st[S::sc + 1], eta = st[S::sc + 2], zeta = st[S::sc + 3];
     T v = GU * H[b] + GH * U[b] + beta * GH * H[b] + gamma * GF * F[b];
-    // - eta (H G^T H)_kL + zeta (F G^T F)_kL
-    T hgh = 0, fgf = 0;
+    T hgh = 0, fgf = 0, gx = 0, yg = 0;
 #pragma unroll
     for (int J = 0; J < 3; ++J) {
-        T mh = 0, mf = 0;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            mh += G[3 * i + J] * H[3 * i + L];
-            mf += G[3 * i + J] * F[3 * i + L];
-        }
-        hgh += H[3 * k + J] * mh;
-        fgf += F[3 * k + J] * mf;
+        hgh += H[3 * k + J] * st[R::Nh + 3 * J + L];
+        fgf += F[3 * k + J] * st[R::Nf + 3 * J + L];
+        gx += Gs[3 * k + J] * X[3 * J + L];
+        yg += Y[3 * k + J] * Gs[3 * J + L];
     }
-    v += -eta * hgh + zeta * fgf;
-    // (G X)_kL + (Y G)_kL
+    v += -eta * hgh + zeta * fgf + gx + yg;
 #pragma unroll
-    for (int J = 0; J < 3; ++J) v += G[3 * k + J] * X[3 * J + L];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) v += Y[3 * k + i] * G[3 * i + L];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-        const T c5x2 = st[S::sc + 4 + f];
-        const T *aA = st + S::aA + 9 * f, *AA = st + S::AA + 9 * f;
-        // recover a_f and A_f from a (x) A and A (x) A: A_J = sqrt(AA_JJ) signs from AA row
-        // (cheaper: sum over J of aA[kJ] A_J = a_k |A|^2)
-        // Terms: a_k (F^T G A)_L + A_L (F G^T a)_k + (B G A)_k A_L, written with aA and AA:
-        //   a_k (F^T G A)_L      = sum_iJ F_iL G_iJ aA[kJ]
-        //   A_L (F G^T a)_k      = sum_iJ aA[iL] G_iJ F_kJ
-        //   (B G A)_k A_L        = sum_iJ B_ik G_iJ AA[JL]
-        T t1 = 0, t2 = 0, t3 = 0;
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int J = 0; J < 3; ++J) {
-                const T g = G[3 * i + J];
-                t1 += F[3 * i + L] * g * aA[3 * k + J];
-                t2 += aA[3 * i + L] * g * F[3 * k + J];
-                t3 += Bm[3 * i + k] * g * AA[3 * J + L];
-            }
-        v += c5x2 * (t1 + t2 + t3);
-    }
+    for (int f = 0; f < NF; ++f)
+        v += st[S::sc + 4 + f] *
+             (st[R::a + 3 * f + k] * st[R::v1 + 3 * f + L] + kc.fib[f][L] * st[R::v23 + 3 * f + k]);
     return v;
 }
 
@@ -225,17 +283,31 @@ __global__ void __launch_bounds__(WARPS * 32)
             for (int m = 0; m < D; ++m) zero[m] = T(0);
             stage_kinematics<T, NF, true>(F, kc, zero, Jm1, jb, qs);
         }
-        __syncwarp();
         T r[D];
         {
+            // G goes next to the staged g_m (the F slot is free here); lane jb sums the
+            // components a = jb + 4 t, and the group adds the four partial sums
             using S = Stage<D, NF>;
+            T *Gs = qs + S::F;
 #pragma unroll
-            for (int m = 0; m < D; ++m) {
-                T s = T(0);
+            for (int a = 0; a < 9; ++a)
+                if ((a & 3) == jb) Gs[a] = G[a];
+            __syncwarp();
 #pragma unroll
-                for (int a = 0; a < 9; ++a) s += G[a] * qs[S::g + 9 * m + a];
-                r[m] = s;
+            for (int m = 0; m < D; ++m) r[m] = T(0);
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                const int a = jb + 4 * t;
+                if (a < 9) {
+                    const T g = Gs[a];
+#pragma unroll
+                    for (int m = 0; m < D; ++m) r[m] += g * qs[S::g + 9 * m + a];
+                }
             }
+#pragma unroll
+            for (int msk = 1; msk <= 2; msk <<= 1)
+#pragma unroll
+                for (int m = 0; m < D; ++m) r[m] += __shfl_xor_sync(0xffffffffu, r[m], msk);
         }
         // polyconvex layer: g_m above are invariant derivatives; the network sees
         // r_K = phi' r_I, and r_I is kept for the chain rule's second-order term
@@ -402,8 +474,10 @@ __global__ void __launch_bounds__(WARPS * 32)
         __syncwarp();
         if (dFg != nullptr) {
             using S = Stage<D, NF>;
+            structured_pre<T, NF>(qs, G, kc, jb);
+            __syncwarp();
             for (int b = jb; b < 9; b += kG) {
-                T v = contract_structured<T, NF>(b, qs, G);
+                T v = contract_structured<T, NF>(b, qs, kc);
 #pragma unroll
                 for (int n = 0; n < D; ++n) v += Hr[n] * qs[S::g + 9 * n + b];
                 if (valid) dFg[b * n_qp + q] = bad ? T(NAN) : v;
