@@ -3,10 +3,10 @@
 // COMMET_BF16_MLP precision. The network derivatives follow the scheme of the FP64/FP32
 // kernel (forward values, reverse adjoints, forward tangents consumed into the Hessian).
 //
-// One CTA of 256 threads takes a tile of 128 points: point i is lane i of tensor memory
-// and row i of every MMA (M = 128), held by threads i and 128 + i (warps w and w + 4 reach
-// the same TMEM lanes), each taking half of every layer's neurons. Per tile and hidden
-// layer k:
+// One CTA of 128 SPLIT threads takes a tile of 128 points: point i is lane i of tensor
+// memory and row i of every MMA (M = 128), held by threads i + 128 p, p < SPLIT (warps w,
+// w + 4, ... reach the same TMEM lanes), each taking W / SPLIT of every layer's neurons
+// (SPLIT = 2). Per tile and hidden layer k:
 //     values    Y_k      = Z_{k-1} A_k^T                [128 x W] = [128 x W][W x W]
 //     adjoints  Zb_{k-1} = Yb_k A_k                     [128 x W]
 //     tangents  J_k^(m)  = T_{k-1}^(m) A_k^T, m < d,    T = F'(y) (.) J
@@ -16,10 +16,10 @@
 // tcgen05.ld. F'(y) and F''(y) of every layer are kept in the point's TMEM lane as fp16
 // pairs (tcgen05.st), F'' later replaced by the adjoint weight D_k = F''(y) zbar_k. Layer
 // 1 (d inputs), biases and skip terms, activations, the output layer and the Hessian sums
-// run in fp32 in the point's two threads, whose partial sums meet in shared memory. The
+// run in fp32 in the point's threads, whose partial sums meet in shared memory. The
 // kinematics (fp32, J - 1 without cancellation) and the P/A assembly run in groups of 4
-// lanes as in the other kernels, each warp taking 2 rounds of 8 of its 32 points, their
-// data passed by warp shuffles.
+// lanes as in the other kernels, each warp taking 4 / SPLIT rounds of 8 of its 32
+// points, their data passed by warp shuffles.
 //
 // Tensor memory per CTA: d W columns of accumulators (values and adjoints use the first
 // W) plus L W columns of (F', F''/D) pairs: (d + L) W <= 512.
@@ -41,7 +41,6 @@ namespace commet {
 namespace {
 
 constexpr int kTile = 128;           // points per CTA tile = MMA M = TMEM lanes
-constexpr int kThreads = 256;        // two threads per point
 constexpr int kWaitTries = 1 << 22;  // bounded mbarrier polls per MMA batch
 
 // Offsets of the bf16-path weight block: an fp32 part (units of float) followed by a
@@ -182,14 +181,19 @@ __device__ __forceinline__ bool mma_round(uint64_t *bar, uint32_t &phase, Issue 
 
 }  // namespace
 
-template <int NF, int W, bool SPATIAL>
-__global__ void __launch_bounds__(kThreads)
+// Threads per point. 4 (16 warps, at most 128 registers) measured the same as 2 on the
+// d3 W64 L3 network: the kernel is bound by the issue of its per-point scalar work.
+template <int NF> struct TcSplit { static constexpr int value = 2; };
+
+template <int NF, int W, bool SPATIAL, int SPLIT = TcSplit<NF>::value>
+__global__ void __launch_bounds__(kTile * SPLIT, 1)
     bf16_tc_kernel(const float *__restrict__ gw32, const unsigned char *__restrict__ gw16, TcLayout lay,
                    KinConst<float> kc, int64_t n_qp, const float *__restrict__ Fg, float *__restrict__ psi,
                    float *__restrict__ P, float *__restrict__ A, int32_t *__restrict__ status, int *__restrict__ err,
                    uint32_t tmem_cols, int stage_stride) {
     constexpr int D = 3 + 2 * NF, NH = D * (D + 1) / 2;
-    constexpr int WH = W / 2;           // neurons per thread
+    constexpr int kThreads = kTile * SPLIT;
+    constexpr int WH = W / SPLIT;       // neurons per thread
     constexpr int CH = (D > 3 || WH < 16) ? 8 : 16;  // TMEM columns per load / store
     constexpr int NCH = WH / CH;
     constexpr int NRED = 1 + D + NH;    // partial sums a thread hands to its partner
@@ -199,7 +203,7 @@ __global__ void __launch_bounds__(kThreads)
     __shared__ __align__(8) uint64_t s_bar;
 
     // shared memory: [bf16 weights][operand Z][operands T^(0..D-1)][fp32 weights]
-    //                [partial sums NRED x 256][stage areas 64 x stage_stride]
+    //                [partial sums NRED x 128 SPLIT][stage areas 32 SPLIT x stage_stride]
     unsigned char *w16 = smem_raw;
     unsigned char *opZ = w16 + lay.b16_bytes;
     unsigned char *opT = opZ + OPB;
@@ -216,8 +220,8 @@ __global__ void __launch_bounds__(kThreads)
         for (int i = threadIdx.x; i < f32_bytes / 16; i += blockDim.x) dst32[i] = src32[i];
     }
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int row = tid & (kTile - 1), half = tid >> 7;  // point in the tile, neuron half
-    const int j0 = half * WH;
+    const int row = tid & (kTile - 1), part = tid >> 7;  // point in the tile, neuron block
+    const int j0 = part * WH;
     if (warp == 0) {
         tmem_alloc(&s_tmem, tmem_cols);
         tmem_relinquish();
@@ -308,12 +312,12 @@ __global__ void __launch_bounds__(kThreads)
             }
         }
         if (aborted) break;
-        if (half == 0) npart += dot_w<D>(s32 + lay.b, K);
+        if (part == 0) npart += dot_w<D>(s32 + lay.b, K);
 
         // ---- reverse adjoints: zbar_L = a; ybar = F' zbar; D = F'' zbar; zbar_{k-1} = ybar_k A_k
         float dN[D];
         load_w<D>(s32 + lay.b, dN);
-        if (half != 0) {
+        if (part != 0) {
 #pragma unroll
             for (int m = 0; m < D; ++m) dN[m] = 0.f;
         }
@@ -435,7 +439,7 @@ __global__ void __launch_bounds__(kThreads)
             if (aborted) break;
         }
 
-        // ---- the two halves' partial sums: npart, dN, Hs
+        // ---- the point's partial sums over its threads: npart, dN, Hs
         {
             float *mine = red + tid;  // entry i at mine[i * kThreads]
             mine[0] = npart;
@@ -444,12 +448,15 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
             for (int i = 0; i < NH; ++i) mine[(1 + D + i) * kThreads] = Hs[i];
             __syncthreads();
-            const float *other = red + (tid ^ kTile);
-            npart += other[0];
 #pragma unroll
-            for (int m = 0; m < D; ++m) dN[m] += other[(1 + m) * kThreads];
+            for (int p = 1; p < SPLIT; ++p) {
+                const float *other = red + row + ((part + p) % SPLIT) * kTile;
+                npart += other[0];
 #pragma unroll
-            for (int i = 0; i < NH; ++i) Hs[i] += other[(1 + D + i) * kThreads];
+                for (int m = 0; m < D; ++m) dN[m] += other[(1 + m) * kThreads];
+#pragma unroll
+                for (int i = 0; i < NH; ++i) Hs[i] += other[(1 + D + i) * kThreads];
+            }
             __syncthreads();
         }
 
@@ -460,8 +467,9 @@ __global__ void __launch_bounds__(kThreads)
         if constexpr (NF == 0) {
             if (kc.kin == COMMET_KIN_POLYCONVEX) poly_to_invariants<float>(ch, cvec, Hs);
         }
+        constexpr int kRounds = 4 / SPLIT;
 #pragma unroll 1
-        for (int r = 2 * half; r < 2 * half + 2; ++r) {
+        for (int r = kRounds * part; r < kRounds * part + kRounds; ++r) {
             const int src = 8 * r + g;
             float Fr[9], cr[D], Hr[NH], Kr[D];
 #pragma unroll
@@ -653,8 +661,9 @@ static int bf16_typed(const commet_model *m, int64_t n_qp, const void *F, void *
     const int stage_stride = stage | 1;  // odd: the 32 group areas fall on distinct banks
     const size_t opb = (size_t)kTile * W * 2;
     const int nred = 1 + D + D * (D + 1) / 2;
-    size_t smem = (size_t)tl.b16_bytes + (1 + D) * opb + f32_bytes + (size_t)kThreads * nred * 4 +
-                  (size_t)64 * stage_stride * 4;
+    constexpr int threads = kTile * TcSplit<NF>::value;
+    size_t smem = (size_t)tl.b16_bytes + (1 + D) * opb + f32_bytes + (size_t)threads * nred * 4 +
+                  (size_t)(threads / 32) * 8 * stage_stride * 4;
     int dev = 0, smem_max = 0, smem_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -669,14 +678,14 @@ static int bf16_typed(const commet_model *m, int64_t n_qp, const void *F, void *
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return COMMET_ERR_CUDA;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
     per_sm = std::max(1, std::min(per_sm, ctas_tmem));
     const int64_t n_tiles = (n_qp + kTile - 1) / kTile;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(n_tiles, (int64_t)sm_count() * per_sm));
     const float *w32 = (const float *)m->d_bf16;
     const unsigned char *w16 = (const unsigned char *)m->d_bf16 + f32_bytes;
     int *err = (int *)((unsigned char *)m->d_bf16 + f32_bytes + tl.b16_bytes);
-    kern<<<grid, kThreads, smem, s>>>(w32, w16, tl, kc, n_qp, (const float *)F, (float *)psi, (float *)P, (float *)A,
+    kern<<<grid, threads, smem, s>>>(w32, w16, tl, kc, n_qp, (const float *)F, (float *)psi, (float *)P, (float *)A,
                                    status, err, cols, stage_stride);
     return cudaGetLastError() == cudaSuccess ? COMMET_OK : COMMET_ERR_CUDA;
 }
