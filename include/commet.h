@@ -153,6 +153,33 @@ int commet_const_update(const commet_model *m, int64_t n_qp, const void *F, void
                         int32_t *status, void *stream);
 
 /*
+ * Host-buffer form of commet_const_update and, with a mesh, of commet_elem_assemble
+ * (Algorithm 2 with its tables in host memory): the points, or the mesh's elements with
+ * their 8 points each, in chunks of `chunk` (points without a mesh, elements with one).
+ * Chunk c is copied to the device while chunk c - 1 is computed on `stream` and chunk
+ * c - 2 is copied back, so copies and kernels overlap; the results are those of the
+ * device calls on the same inputs, bit for bit.
+ * F, psi, P, A, f_e, K_e are HOST pointers in the layouts of the device calls
+ * (F [9][n_qp], psi [n_qp], P [9][n_qp], A [81][n_qp], f_e [24][n_el], K_e [576][n_el]),
+ * page-locked for the copies to overlap; psi, A, f_e, K_e may be NULL (K_e only with A).
+ * Element type: double for a COMMET_F64 model, float otherwise.
+ * mesh: NULL (update only; f_e and K_e must be NULL) or a mesh with 8 n_el = n_qp.
+ * workspace: device memory of commet_const_update_host_workspace(m, mesh, chunk, A != NULL)
+ * bytes, 256-byte aligned, owned by the caller and not used by anything else until the
+ * call has completed on `stream`.
+ * The call returns once the work is queued; the host outputs are complete when `stream`
+ * reaches that point. Two streams and eight events are created per call and released
+ * when their work is done. No status word: bad points come back as NaN.
+ * Errors: INVALID_ARG (NULL, sizes, alignment, workspace too small), UNSUPPORTED (as the
+ * device calls), CUDA.
+ */
+size_t commet_const_update_host_workspace(const commet_model *m, const commet_mesh *mesh, int64_t chunk,
+                                          int32_t want_A);
+int commet_const_update_host(const commet_model *m, const commet_mesh *mesh, int64_t n_qp, const void *F, void *psi,
+                             void *P, void *A, void *f_e, void *K_e, void *workspace, size_t ws_bytes, int64_t chunk,
+                             void *stream);
+
+/*
  * Constitutive update in spatial form (App. A.1, the paper's own storage): for every qp
  *   tau[:, q] = Kirchhoff stress tau_ij = P_iJ F_jJ in Voigt order (11, 22, 33, 23, 13, 12),
  *   c[:, q]   = spatial stiffness c_ijkl = F_jJ A_iJkL F_lL - delta_ik tau_jl as the 21

@@ -24,6 +24,7 @@ EXPORTED = [
     "commet_const_backward", "commet_target_stress", "commet_status_string", "commet_const_backward_noalloc",
     "commet_mesh_set_dirichlet", "commet_set_dirichlet_values", "commet_apply_dirichlet", "commet_cg_workspace",
     "commet_cg_solve", "commet_add_increment", "commet_norm2", "commet_residual_adjoint", "commet_compute_F_adjoint",
+    "commet_const_update_host_workspace", "commet_const_update_host",
 ]
 
 
@@ -92,6 +93,8 @@ def load() -> C.CDLL:
         "commet_norm2": ([vp, i32, i64, vp, C.POINTER(C.c_double), vp], C.c_int),
         "commet_residual_adjoint": ([vp, i32, vp, vp, vp], C.c_int),
         "commet_compute_F_adjoint": ([vp, i32, vp, vp, vp], C.c_int),
+        "commet_const_update_host_workspace": ([vp, vp, i64, i32], C.c_size_t),
+        "commet_const_update_host": ([vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, C.c_size_t, i64, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

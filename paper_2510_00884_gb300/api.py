@@ -130,6 +130,48 @@ class Model:
             self.handle, n, _ptr(F), _ptr(psi), _ptr(P), _ptr(A), _ptr(st), _stream()))
         return (psi, P, A, st) if status else (psi, P, A)
 
+    def const_update_host(self, F: torch.Tensor, mesh: "Mesh | None" = None, out=None, chunk: int | None = None,
+                          want_A: bool = True, want_psi: bool = True, want_f: bool = True, want_K: bool = True,
+                          workspace: torch.Tensor | None = None):
+        """The update (and, with a mesh, the element integrals) on HOST tensors, pipelined in
+        chunks (points, or elements with a mesh) so that the copies overlap the kernels.
+        F[9, n] is a CPU tensor, ideally pinned; returns CPU tensors
+        (psi[n], P[9, n], A[81, n], f_e[24, n_el], K_e[576, n_el]), entries not wanted (or
+        without a mesh: f_e, K_e) None. ``out`` supplies them (pinned for overlap). Complete
+        when the current stream reaches the end of the call (synchronise before reading)."""
+        if F.device.type != "cpu" or F.dtype != self.dtype or F.dim() != 2 or F.shape[0] != 9 \
+                or not F.is_contiguous():
+            raise ValueError(f"F must be a contiguous CPU tensor [9, n] of {self.dtype}")
+        n = F.shape[1]
+        n_el = mesh.n_el if mesh is not None else 0
+        if mesh is not None and n != 8 * n_el:
+            raise ValueError("F must hold the 8 points of every element of the mesh")
+        if out is None:
+            pin = F.is_pinned()
+
+            def mk(*shape):
+                return torch.empty(*shape, dtype=self.dtype, pin_memory=pin)
+            psi = mk(n) if want_psi else None
+            P, A = mk(9, n), (mk(81, n) if want_A else None)
+            f_e = mk(24, n_el) if (mesh is not None and want_f) else None
+            K_e = mk(576, n_el) if (mesh is not None and want_K and want_A) else None
+        else:
+            psi, P, A, f_e, K_e = out
+        if chunk is None:
+            # every strided host copy then moves rows of at least 128 KB
+            es = 8 if self.dtype == torch.float64 else 4
+            chunk = (131072 // es) if mesh is not None else 131072
+        lib = _lib.load()
+        mh = mesh.handle if mesh is not None else None
+        need = int(lib.commet_const_update_host_workspace(self.handle, mh, chunk, 1 if A is not None else 0))
+        if workspace is None or workspace.numel() < need:
+            workspace = torch.empty(max(need, 1), dtype=torch.uint8, device="cuda")
+        _lib.check("commet_const_update_host", lib.commet_const_update_host(
+            self.handle, mh, n, _ptr(F), _ptr(psi), _ptr(P), _ptr(A), _ptr(f_e), _ptr(K_e), _ptr(workspace),
+            workspace.numel(), chunk, _stream()))
+        self._host_ws = workspace  # keeps the device buffers alive until the next call
+        return psi, P, A, f_e, K_e
+
     def const_update_spatial(self, F: torch.Tensor, want_c: bool = True, want_psi: bool = True,
                              status: bool = False, out=None):
         """psi[n], tau[6, n], c[21, n] (or None) for F[9, n]: Kirchhoff stress and spatial

@@ -430,6 +430,28 @@ int commet_const_update(const commet_model *m, int64_t n_qp, const void *F, void
     return launch_const_update(m, n_qp, F, psi, P, A, status, s, nullptr);
 }
 
+size_t commet_const_update_host_workspace(const commet_model *m, const commet_mesh *mesh, int64_t chunk,
+                                          int32_t want_A) {
+    if (m == nullptr || chunk < 1) return 0;
+    return host_pipeline_workspace(m, mesh, chunk, want_A != 0);
+}
+
+int commet_const_update_host(const commet_model *m, const commet_mesh *mesh, int64_t n_qp, const void *F, void *psi,
+                             void *P, void *A, void *f_e, void *K_e, void *workspace, size_t ws_bytes, int64_t chunk,
+                             void *stream) {
+    if (m == nullptr || n_qp < 0 || chunk < 1) return COMMET_ERR_INVALID_ARG;
+    if (n_qp > 0 && (F == nullptr || P == nullptr)) return COMMET_ERR_INVALID_ARG;
+    if (mesh != nullptr && n_qp != 8 * mesh->n_el) return COMMET_ERR_INVALID_ARG;
+    if (mesh == nullptr && (f_e != nullptr || K_e != nullptr)) return COMMET_ERR_INVALID_ARG;
+    if (A == nullptr && K_e != nullptr) return COMMET_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return COMMET_ERR_INVALID_ARG;
+    if (n_qp == 0) return COMMET_OK;
+    if (workspace == nullptr || ws_bytes < host_pipeline_workspace(m, mesh, chunk, A != nullptr))
+        return COMMET_ERR_INVALID_ARG;
+    return run_host_pipeline(m, mesh, n_qp, F, psi, P, A, f_e, K_e, workspace, ws_bytes, chunk,
+                             reinterpret_cast<cudaStream_t>(stream));
+}
+
 int commet_const_update_spatial(const commet_model *m, int64_t n_qp, const void *F, void *psi, void *tau, void *c,
                                 int32_t *status, void *stream) {
     if (m == nullptr || n_qp < 0) return COMMET_ERR_INVALID_ARG;

@@ -99,6 +99,11 @@ struct commet_mesh {
 
 namespace commet {
 
+// Host-buffer pipeline (host_pipeline.cu): chunked copies in, kernels, copies out.
+size_t host_pipeline_workspace(const commet_model *m, const commet_mesh *mesh, int64_t chunk, bool want_A);
+int run_host_pipeline(const commet_model *m, const commet_mesh *mesh, int64_t n_qp, const void *F, void *psi, void *P,
+                      void *A, void *f_e, void *K_e, void *ws, size_t ws_bytes, int64_t chunk, cudaStream_t s);
+
 // Launchers (return COMMET_* codes). Pointers already validated.
 int launch_const_update(const commet_model *m, int64_t n_qp, const void *F, void *psi, void *P, void *A,
                         int32_t *status, cudaStream_t s, void *dN_out = nullptr);

@@ -94,3 +94,25 @@ def test_c2_full_size_sampled(pkg):
         assert_close(A.index_select(1, it).cpu().numpy().T, A_r, TOL[prec], f"C2 {prec} A")
         del P, A
         torch.cuda.empty_cache()
+
+
+def test_bf16_tensor_memory_budget(pkg):
+    """The tcgen05 kernel keeps d W accumulator columns and L W (F', F'') columns of tensor
+    memory: d3 W64 L5 fills the 512 columns exactly and matches the oracle; L6 would need
+    576 and is refused with UNSUPPORTED."""
+    from paper_2510_00884_gb300 import _lib
+    rng = np.random.Generator(np.random.PCG64(320))
+    spec = wl.make_model(rng, wl.KIN_ISO_SHIFTED, 0, W=64, L=5, kappa=3.0)
+    F = wl.uniaxial_F(rng, 389)
+    Fd = pm_to_cm(F, torch.float32)
+    _, P_r, A_r = oracle.const_update(oracle.OracleModel(spec), cm_to_pm(Fd).astype(np.float64))
+    mb = pkg.Model(spec, "bf16")
+    _, P, A, st = mb.const_update(Fd, status=True)
+    torch.cuda.synchronize()
+    assert int(st[0]) == 0
+    assert_close(cm_to_pm(P), P_r, TOL["bf16"], "bf16 L5 P")
+    assert_close(cm_to_pm(A), A_r, TOL["bf16"], "bf16 L5 A")
+    big = pkg.Model(wl.make_model(rng, wl.KIN_ISO_SHIFTED, 0, W=64, L=6, kappa=3.0), "bf16")
+    with pytest.raises(_lib.CommetError) as ei:
+        big.const_update(Fd)
+    assert ei.value.code == _lib.ERR_UNSUPPORTED
