@@ -70,6 +70,10 @@ def test_host_side_argument_checks(lib):
         _lib.ERR_INVALID_ARG
     assert lib.commet_const_backward(None, 1, None, None, None, None, None, 0, None) == _lib.ERR_INVALID_ARG
     assert lib.commet_model_n_params(None) == -1
+    # host-buffer pipeline: no model, no chunk
+    assert lib.commet_const_update_host(None, None, 8, None, None, None, None, None, None, None, 0, 4,
+                                        None) == _lib.ERR_INVALID_ARG
+    assert lib.commet_const_update_host_workspace(None, None, 4, 1) == 0
 
 
 def test_product_path_does_not_touch_the_oracle():
