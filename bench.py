@@ -857,7 +857,8 @@ def run_sweep(args):
       size   model size (App. D): MICNN on the polyconvex inputs with L in {2, 3, 4} hidden
              layers and W in {2, 4, 8, 16, 32, 64} (W = 2 runs zero-padded to 4), plus the CANN
              and Gent-Thomas laws, at
-             2^21 points per launch, P and A in FP64 and FP32
+             2^21 points per launch, P and A in FP64 and FP32 (and the bf16 tcgen05 MLP for
+             W = 32, 64)
       batch  points per launch (the paper's batch size, Sec. 4.1) from 2^8 to 2^24 for the
              paper's NCM (3 x 16, 675 parameters), FP64 and FP32
     Each case: 3 warm-up launches, then the mean of `steps` launches timed with CUDA events."""
@@ -917,7 +918,7 @@ def run_sweep(args):
             for W in (2, 4, 8, 16, 32, 64):
                 spec = wl.make_model(np.random.Generator(np.random.PCG64(100 * L + W)), wl.KIN_POLYCONVEX, 0,
                                      W=W, L=L, kappa=0.0)
-                for prec in ("f64", "f32"):
+                for prec in ("f64", "f32") + (("bf16",) if W >= 32 else ()):
                     case(spec, f"micnn L{L} W{W}", n_max, prec, F_host)
         for label, spec in (("cann (paper, 4 terms)", wl.make_cann(np.random.Generator(np.random.PCG64(9)))),
                             ("gent-thomas", wl.GentThomasSpec())):
