@@ -315,22 +315,63 @@ int cg_typed(const commet_mesh *mesh, const void *K_vals_v, const void *b_v, voi
                                                            dinv, red);
     cg_start_kernel<<<1, kSolveThreads, 0, s>>>(red, vec_blocks, rtol);
     COMMET_CUDA_TRY(cudaGetLastError());
+    auto iterations = [&](int m, cudaStream_t st) {
+        for (int k = 0; k < m; ++k) {
+            cg_spmv_kernel<T><<<spmv_blocks, kSolveThreads, 0, st>>>(n, mesh->d_rowptr, mesh->d_col, K_vals, p, Ap,
+                                                                     red, counters);
+            cg_update_kernel<T><<<vec_blocks, kSolveThreads, 0, st>>>(n, x, r, z, p, Ap, dinv, red, counters + 1);
+            cg_p_kernel<T><<<vec_blocks, kSolveThreads, 0, st>>>(n, z, p, red);
+        }
+    };
+    // A chunk of kChunk iterations (3 kChunk launches with the same arguments) is captured
+    // once as a CUDA graph and replayed, which removes the per-launch overhead that bounds
+    // the iteration on small meshes. If capture is not available the launches go directly.
+    cudaGraphExec_t chunk_exec = nullptr;
+    if (max_iter >= kChunk) {
+        cudaStream_t cs = nullptr;
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess) {
+            if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                iterations(kChunk, cs);
+                if (cudaStreamEndCapture(cs, &graph) == cudaSuccess && graph != nullptr) {
+                    if (cudaGraphInstantiate(&chunk_exec, graph, 0) != cudaSuccess) chunk_exec = nullptr;
+                    cudaGraphDestroy(graph);
+                }
+            }
+            cudaStreamDestroy(cs);
+        }
+        (void)cudaGetLastError();  // a failed capture leaves the direct launches below
+    }
     double host[S_COUNT];
     int done_iters = 0;
+    int rc = COMMET_OK;
     for (int it0 = 0; it0 < max_iter; it0 += kChunk) {
         const int m = std::min(kChunk, max_iter - it0);
-        for (int k = 0; k < m; ++k) {
-            cg_spmv_kernel<T><<<spmv_blocks, kSolveThreads, 0, s>>>(n, mesh->d_rowptr, mesh->d_col, K_vals, p, Ap,
-                                                                    red, counters);
-            cg_update_kernel<T><<<vec_blocks, kSolveThreads, 0, s>>>(n, x, r, z, p, Ap, dinv, red, counters + 1);
-            cg_p_kernel<T><<<vec_blocks, kSolveThreads, 0, s>>>(n, z, p, red);
+        if (m == kChunk && chunk_exec != nullptr) {
+            if (cudaGraphLaunch(chunk_exec, s) != cudaSuccess) {
+                rc = COMMET_ERR_CUDA;
+                break;
+            }
+        } else {
+            iterations(m, s);
         }
-        COMMET_CUDA_TRY(cudaGetLastError());
-        COMMET_CUDA_TRY(cudaMemcpyAsync(host, red, sizeof(host), cudaMemcpyDeviceToHost, s));
-        COMMET_CUDA_TRY(cudaStreamSynchronize(s));
+        if (cudaGetLastError() != cudaSuccess) {
+            rc = COMMET_ERR_CUDA;
+            break;
+        }
+        if (cudaMemcpyAsync(host, red, sizeof(host), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            rc = COMMET_ERR_CUDA;
+            break;
+        }
         done_iters = (int)host[S_ITERS];
         if (host[S_DONE] != 0.0) break;
     }
+    if (chunk_exec != nullptr) {
+        cudaStreamSynchronize(s);
+        cudaGraphExecDestroy(chunk_exec);
+    }
+    if (rc != COMMET_OK) return rc;
     if (iters) *iters = done_iters;
     if (rel_res) *rel_res = host[S_BB] > 0.0 ? std::sqrt(host[S_RR] / host[S_BB]) : 0.0;
     return COMMET_OK;
