@@ -30,12 +30,13 @@
 
 #include "device_math.cuh"
 #include "internal.h"
+#include "qp_body.cuh"
 
 namespace commet {
 
 namespace {
 
-constexpr int kG = 4, kQPW = 8;
+// kG (lanes per point) and kQPW (points per warp) come from qp_body.cuh
 
 // Warps per CTA (8 points each: the CTA tile): 4 in FP64, 8 in FP32; 64-wide networks,
 // whose weights, accumulators and slabs would not fit, run half as many.
@@ -51,19 +52,21 @@ struct BwSlab {
     int K, r, z, zd, zdL, s, t, yd, yb, ydb, size;
 };
 
+__host__ __device__ inline int bw_round4(int x) { return (x + 3) / 4 * 4; }
+
 __host__ __device__ inline BwSlab bw_slab(int d, int W, int L, int NF, int tsize) {
     BwSlab b{};
-    int o = 0;
-    b.K = o; o += d;
-    b.r = o; o += d;
-    b.z = o; o += (L - 1) * W;
-    b.zd = o; o += (L - 1) * W;
-    b.zdL = o; o += W;
-    b.s = o; o += L * W;
-    b.t = o; o += L * W;
-    b.yd = o; o += L * W;
-    b.yb = o; o += W;
-    b.ydb = o; o += W;
+    int o = 0;  // every array starts on a 4-element boundary (128-bit shared loads)
+    b.K = o; o = bw_round4(o + d);
+    b.r = o; o = bw_round4(o + d);
+    b.z = o; o = bw_round4(o + (L - 1) * W);
+    b.zd = o; o = bw_round4(o + (L - 1) * W);
+    b.zdL = o; o = bw_round4(o + W);
+    b.s = o; o = bw_round4(o + L * W);
+    b.t = o; o = bw_round4(o + L * W);
+    b.yd = o; o = bw_round4(o + L * W);
+    b.yb = o; o = bw_round4(o + W);
+    b.ydb = o; o = bw_round4(o + W);
     // staged kinematics, then G and its precomputed contractions (BwPre below)
     const int stage = 9 * d + 54 + 18 * NF + 5 + NF + 30 + 9 * NF;
     int raw = o > stage ? o : stage;
@@ -365,72 +368,80 @@ __global__ void __launch_bounds__(WARPS * 32)
         __syncwarp();
 
         // ---- forward: values and tangents along r
+        constexpr int V = 16 / (int)sizeof(T);  // elements per 128-bit shared load
         for (int k = 1; k <= L; ++k) {
             T y[NJ], yd[NJ];
+            ldv<NJ>(sw + lay.c + (k - 1) * W + j0, y);
 #pragma unroll
-            for (int jj = 0; jj < NJ; ++jj) {
-                y[jj] = sw[lay.c + (k - 1) * W + j0 + jj];
-                yd[jj] = T(0);
-            }
+            for (int jj = 0; jj < NJ; ++jj) yd[jj] = T(0);
             if (k == 1) {
 #pragma unroll
                 for (int m = 0; m < D; ++m) {
-                    const T *wr = sw + lay.W1t + m * W + j0;
+                    T w[NJ];
+                    ldv<NJ>(sw + lay.W1t + m * W + j0, w);
 #pragma unroll
                     for (int jj = 0; jj < NJ; ++jj) {
-                        y[jj] += wr[jj] * K[m];
-                        yd[jj] += wr[jj] * r[m];
+                        y[jj] += w[jj] * K[m];
+                        yd[jj] += w[jj] * r[m];
                     }
                 }
             } else {
                 const T *zin = qs + sl.z + (k - 2) * W, *zdin = qs + sl.zd + (k - 2) * W;
                 const T *At = sw + lay.At + (k - 2) * W * W + j0;
-#pragma unroll 4
-                for (int i = 0; i < W; ++i) {
-                    const T zi = zin[i], zdi = zdin[i];
+#pragma unroll 2
+                for (int i = 0; i < W; i += V) {
+                    T zv[V], zdv[V];
+                    ldv<V>(zin + i, zv);
+                    ldv<V>(zdin + i, zdv);
 #pragma unroll
-                    for (int jj = 0; jj < NJ; ++jj) {
-                        y[jj] += At[i * W + jj] * zi;
-                        yd[jj] += At[i * W + jj] * zdi;
+                    for (int u = 0; u < V; ++u) {
+                        T w[NJ];
+                        ldv<NJ>(At + (i + u) * W, w);
+#pragma unroll
+                        for (int jj = 0; jj < NJ; ++jj) {
+                            y[jj] += w[jj] * zv[u];
+                            yd[jj] += w[jj] * zdv[u];
+                        }
                     }
                 }
                 const T *Bt = sw + lay.Bt + (k - 2) * D * W + j0;
 #pragma unroll
-                for (int m = 0; m < D; ++m)
+                for (int m = 0; m < D; ++m) {
+                    T w[NJ];
+                    ldv<NJ>(Bt + m * W, w);
 #pragma unroll
                     for (int jj = 0; jj < NJ; ++jj) {
-                        y[jj] += Bt[m * W + jj] * K[m];
-                        yd[jj] += Bt[m * W + jj] * r[m];
+                        y[jj] += w[jj] * K[m];
+                        yd[jj] += w[jj] * r[m];
                     }
+                }
             }
+            T zv[NJ], sv[NJ], tv[NJ], zdv[NJ];
 #pragma unroll
             for (int jj = 0; jj < NJ; ++jj) {
-                const int j = j0 + jj;
-                T z, s, t;
                 if constexpr (sizeof(T) == 8)
-                    act_tab(y[jj], z, s, t, sw + lay.tab);
+                    act_tab(y[jj], zv[jj], sv[jj], tv[jj], sw + lay.tab);
                 else
-                    act(y[jj], z, s, t);
-                qs[sl.s + (k - 1) * W + j] = s;
-                qs[sl.t + (k - 1) * W + j] = t;
-                qs[sl.yd + (k - 1) * W + j] = yd[jj];
-                if (k < L) {
-                    qs[sl.z + (k - 1) * W + j] = z;
-                    qs[sl.zd + (k - 1) * W + j] = s * yd[jj];
-                } else {
-                    qs[sl.zdL + j] = s * yd[jj];
-                }
+                    act(y[jj], zv[jj], sv[jj], tv[jj]);
+                zdv[jj] = sv[jj] * yd[jj];
+            }
+            stv<NJ>(qs + sl.s + (k - 1) * W + j0, sv);
+            stv<NJ>(qs + sl.t + (k - 1) * W + j0, tv);
+            stv<NJ>(qs + sl.yd + (k - 1) * W + j0, yd);
+            if (k < L) {
+                stv<NJ>(qs + sl.z + (k - 1) * W + j0, zv);
+                stv<NJ>(qs + sl.zd + (k - 1) * W + j0, zdv);
+            } else {
+                stv<NJ>(qs + sl.zdL + j0, zdv);
             }
             __syncwarp();
         }
 
         // ---- reverse over the tangent computation
         T zb[NJ], zdb[NJ];
+        ldv<NJ>(sw + lay.a + j0, zdb);
 #pragma unroll
-        for (int jj = 0; jj < NJ; ++jj) {
-            zb[jj] = T(0);
-            zdb[jj] = sw[lay.a + j0 + jj];
-        }
+        for (int jj = 0; jj < NJ; ++jj) zb[jj] = T(0);
         T Hr[D], dN[D];
 #pragma unroll
         for (int m = 0; m < D; ++m) {
@@ -439,18 +450,27 @@ __global__ void __launch_bounds__(WARPS * 32)
         }
         for (int k = L; k >= 1; --k) {
             const T *Bt = (k == 1) ? (sw + lay.W1t + j0) : (sw + lay.Bt + (k - 2) * D * W + j0);
+            {
+                T sv[NJ], tv[NJ], ydv[NJ], ybv[NJ], ydbv[NJ];
+                ldv<NJ>(qs + sl.s + (k - 1) * W + j0, sv);
+                ldv<NJ>(qs + sl.t + (k - 1) * W + j0, tv);
+                ldv<NJ>(qs + sl.yd + (k - 1) * W + j0, ydv);
 #pragma unroll
-            for (int jj = 0; jj < NJ; ++jj) {
-                const int j = j0 + jj;
-                const T s = qs[sl.s + (k - 1) * W + j], t = qs[sl.t + (k - 1) * W + j];
-                const T ydb = s * zdb[jj];
-                const T yb = s * zb[jj] + t * qs[sl.yd + (k - 1) * W + j] * zdb[jj];
-                qs[sl.yb + j] = yb;
-                qs[sl.ydb + j] = ydb;
+                for (int jj = 0; jj < NJ; ++jj) {
+                    ydbv[jj] = sv[jj] * zdb[jj];
+                    ybv[jj] = sv[jj] * zb[jj] + tv[jj] * ydv[jj] * zdb[jj];
+                }
+                stv<NJ>(qs + sl.yb + j0, ybv);
+                stv<NJ>(qs + sl.ydb + j0, ydbv);
 #pragma unroll
                 for (int m = 0; m < D; ++m) {
-                    Hr[m] += Bt[m * W + jj] * yb;
-                    dN[m] += Bt[m * W + jj] * ydb;
+                    T w[NJ];
+                    ldv<NJ>(Bt + m * W, w);
+#pragma unroll
+                    for (int jj = 0; jj < NJ; ++jj) {
+                        Hr[m] += w[jj] * ybv[jj];
+                        dN[m] += w[jj] * ydbv[jj];
+                    }
                 }
             }
             __syncthreads();
@@ -471,13 +491,20 @@ __global__ void __launch_bounds__(WARPS * 32)
                     zb[ii] = T(0);
                     zdb[ii] = T(0);
                 }
-#pragma unroll 4
-                for (int j = 0; j < W; ++j) {
-                    const T ybj = qs[sl.yb + j], ydbj = qs[sl.ydb + j];
+#pragma unroll 2
+                for (int j = 0; j < W; j += V) {
+                    T ybv[V], ydbv[V];
+                    ldv<V>(qs + sl.yb + j, ybv);
+                    ldv<V>(qs + sl.ydb + j, ydbv);
 #pragma unroll
-                    for (int ii = 0; ii < NJ; ++ii) {
-                        zb[ii] += Ar[j * W + ii] * ybj;
-                        zdb[ii] += Ar[j * W + ii] * ydbj;
+                    for (int u = 0; u < V; ++u) {
+                        T w[NJ];
+                        ldv<NJ>(Ar + (j + u) * W, w);
+#pragma unroll
+                        for (int ii = 0; ii < NJ; ++ii) {
+                            zb[ii] += w[ii] * ybv[u];
+                            zdb[ii] += w[ii] * ydbv[u];
+                        }
                     }
                 }
             }
