@@ -194,25 +194,10 @@ __device__ __forceinline__ T contract_structured(int b, const T *st, const KinCo
     return v;
 }
 
-// acc[e] += sum_q U1[q][row(e)] V1[q][col(e)] + U2[q][row] V2[q][col] over the tile,
-// e = row * cols + col; entries owned by threads tid, tid + nthr, ...
-template <typename T>
-__device__ __forceinline__ void tile_outer(T *acc, int rows, int cols, const T *base, int qstride, int u1, int v1,
-                                           int u2, int v2, int Q) {
-    const int n = rows * cols;
-    for (int e = threadIdx.x; e < n; e += blockDim.x) {
-        const int j = e / cols, i = e - j * cols;
-        T s = T(0);
-        for (int q = 0; q < Q; ++q) {
-            const T *p = base + (size_t)q * qstride;
-            s += p[u1 + j] * p[v1 + i];
-            if (u2 >= 0) s += p[u2 + j] * p[v2 + i];
-        }
-        acc[e] += s;
-    }
-}
-
-// The square W x W case of tile_outer (W even, both products present) in 2 x 2 register
+// Weight-gradient sums over the CTA tile's Q points (slab stride qstride):
+//   acc[row * cols + col] += sum_q U1[q][row] V1[q][col] + U2[q][row] V2[q][col],
+// with the U, V vectors at offsets u1, v1, u2, v2 of each point's slab, in register blocks.
+// The square W x W case (W even) in 2 x 2 register
 // blocks: per point, four paired loads feed eight multiply-adds where the scalar form needs
 // four loads for two. Slab offsets and the slab stride are even, so the pairs are aligned.
 template <typename T>
@@ -247,6 +232,31 @@ __device__ __forceinline__ void tile_outer_sq(T *acc, int W, const T *base, int 
     }
 }
 
+// The W x d blocks (rows W even, both products present) with rows in pairs: per point,
+// two paired row loads and two column loads feed four multiply-adds.
+template <typename T>
+__device__ __forceinline__ void tile_outer_rows2(T *acc, int rows, int cols, const T *base, int qstride, int u1,
+                                                 int v1, int u2, int v2, int Q) {
+    using T2 = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
+    const int nb = (rows >> 1) * cols;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        const int jb = b / cols, i = b - jb * cols, j0 = 2 * jb;
+        T s0 = T(0), s1 = T(0);
+        for (int q = 0; q < Q; ++q) {
+            const T *p = base + (size_t)q * qstride;
+            const T2 a = *reinterpret_cast<const T2 *>(p + u1 + j0);
+            const T2 a2 = *reinterpret_cast<const T2 *>(p + u2 + j0);
+            const T c = p[v1 + i], c2 = p[v2 + i];
+            s0 += a.x * c;
+            s1 += a.y * c;
+            s0 += a2.x * c2;
+            s1 += a2.y * c2;
+        }
+        acc[j0 * cols + i] += s0;
+        acc[(j0 + 1) * cols + i] += s1;
+    }
+}
+
 // acc[j] += sum_q U[q][j]
 template <typename T>
 __device__ __forceinline__ void tile_sum(T *acc, int n, const T *base, int qstride, int u, int Q) {
@@ -266,6 +276,8 @@ __global__ void __launch_bounds__(WARPS * 32)
                           T *__restrict__ partial, int np_pad, BwSlab sl) {
     constexpr int D = 3 + 2 * NF, NJ = W / kG;
     constexpr int Q = WARPS * kQPW;  // points per CTA tile
+    static_assert(BwPre<D, NF>::size == 9 * D + 54 + 18 * NF + 5 + NF + 30 + 9 * NF,
+                  "bw_slab reserves the staged kinematics and BwPre");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sw = reinterpret_cast<T *>(smem_raw);
     const int wbytes = (lay.total * (int)sizeof(T) + 15) / 16 * 16;
@@ -477,12 +489,12 @@ __global__ void __launch_bounds__(WARPS * 32)
             // tile reductions of this layer's weight gradients
             const T *base = slabs;
             if (k == 1) {
-                tile_outer<T>(acc + oW1, W, D, base, sl.size, sl.yb, sl.K, sl.ydb, sl.r, Q);
+                tile_outer_rows2<T>(acc + oW1, W, D, base, sl.size, sl.yb, sl.K, sl.ydb, sl.r, Q);
                 tile_sum<T>(acc + oc1, W, base, sl.size, sl.yb, Q);
             } else {
                 const int o = oL + (k - 2) * lsz;
                 tile_outer_sq<T>(acc + o, W, base, sl.size, sl.yb, sl.z + (k - 2) * W, sl.ydb, sl.zd + (k - 2) * W, Q);
-                tile_outer<T>(acc + o + W * W, W, D, base, sl.size, sl.yb, sl.K, sl.ydb, sl.r, Q);
+                tile_outer_rows2<T>(acc + o + W * W, W, D, base, sl.size, sl.yb, sl.K, sl.ydb, sl.r, Q);
                 tile_sum<T>(acc + o + W * W + W * D, W, base, sl.size, sl.yb, Q);
                 // zbar_{k-1} = A_k^T ybar_k, zdotbar_{k-1} = A_k^T ydotbar_k for own neurons
                 const T *Ar = sw + lay.Ar + (k - 2) * W * W + j0;
