@@ -489,9 +489,13 @@ __device__ __forceinline__ void assemble_row(int a, const T *st, const T *Hs, co
 #pragma unroll
             for (int n = 0; n < D; ++n) s += u[n] * st[S::g + 9 * n + b];
             const T Hb = st[S::H + b];
-            s += Ua * Hb + Ha * st[S::U + b] + beta * Ha * Hb + gamma * Fa * st[S::F + b];
+            s += Ua * Hb;
+            s += Ha * st[S::U + b];
+            s += (beta * Ha) * Hb;
+            s += (gamma * Fa) * st[S::F + b];
             const T FiL = st[S::F + 3 * i + L], FkJ = st[S::F + 3 * k + J_];
-            s += -eta * st[S::H + 3 * i + L] * st[S::H + 3 * k + J_] + zeta * FiL * FkJ;
+            s += (-eta * st[S::H + 3 * i + L]) * st[S::H + 3 * k + J_];
+            s += (zeta * FiL) * FkJ;
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
                 const T c5x2 = st[S::sc + 4 + f];
@@ -517,9 +521,14 @@ __device__ __forceinline__ T assemble_entry(int a, int b, const T *st, const T *
     for (int n = 0; n < D; ++n) s += ust[a * DP + n] * st[S::g + 9 * n + b];
     const T Ha = st[S::H + a], Hb = st[S::H + b], Fa = st[S::F + a], Fb = st[S::F + b];
     const T beta = st[S::sc + 0], gamma = st[S::sc + 1], eta = st[S::sc + 2], zeta = st[S::sc + 3];
-    s += st[S::U + a] * Hb + Ha * st[S::U + b] + beta * Ha * Hb + gamma * Fa * Fb;
+    // one fused multiply-add per product term
+    s += st[S::U + a] * Hb;
+    s += Ha * st[S::U + b];
+    s += (beta * Ha) * Hb;
+    s += (gamma * Fa) * Fb;
     const T FiL = st[S::F + 3 * i + L], FkJ = st[S::F + 3 * k + J_];
-    s += -eta * st[S::H + 3 * i + L] * st[S::H + 3 * k + J_] + zeta * FiL * FkJ;
+    s += (-eta * st[S::H + 3 * i + L]) * st[S::H + 3 * k + J_];
+    s += (zeta * FiL) * FkJ;
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
         const T c5x2 = st[S::sc + 4 + f];

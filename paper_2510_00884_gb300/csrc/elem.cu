@@ -129,7 +129,11 @@ __global__ void __launch_bounds__(128)
         const T *Pq = &s_pa[le][0];
         const T *Aq = &s_pa[le][9];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) f[i] += Pq[3 * i] * wg[0] + Pq[3 * i + 1] * wg[1] + Pq[3 * i + 2] * wg[2];
+        for (int i = 0; i < 3; ++i) {
+            f[i] += Pq[3 * i] * wg[0];
+            f[i] += Pq[3 * i + 1] * wg[1];
+            f[i] += Pq[3 * i + 2] * wg[2];
+        }
         if (want_K) {
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
@@ -144,7 +148,12 @@ __global__ void __launch_bounds__(128)
                 for (int K = 0; K < 8; ++K) {
                     const T g0 = s_g[le][q][K][0], g1 = s_g[le][q][K][1], g2 = s_g[le][q][K][2];
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) Kr[i][K][k] += T3[k][0] * g0 + T3[k][1] * g1 + T3[k][2] * g2;
+                    for (int k = 0; k < 3; ++k) {
+                        // one fused multiply-add per product, accumulated in place
+                        Kr[i][K][k] += T3[k][0] * g0;
+                        Kr[i][K][k] += T3[k][1] * g1;
+                        Kr[i][K][k] += T3[k][2] * g2;
+                    }
                 }
             }
         }
@@ -261,9 +270,11 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
         for (int J = 0; J < 3; ++J) wg[J] = w * s_g[le][q][I][J];
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
-            f[i] += s_p[(3 * i) * kTmaQP + col] * wg[0] + s_p[(3 * i + 1) * kTmaQP + col] * wg[1] +
-                    s_p[(3 * i + 2) * kTmaQP + col] * wg[2];
+        for (int i = 0; i < 3; ++i) {
+            f[i] += s_p[(3 * i) * kTmaQP + col] * wg[0];
+            f[i] += s_p[(3 * i + 1) * kTmaQP + col] * wg[1];
+            f[i] += s_p[(3 * i + 2) * kTmaQP + col] * wg[2];
+        }
         if (want_K) {
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
@@ -279,7 +290,12 @@ __global__ void __launch_bounds__(128)
                 for (int K = 0; K < 8; ++K) {
                     const T g0 = s_g[le][q][K][0], g1 = s_g[le][q][K][1], g2 = s_g[le][q][K][2];
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) Kr[i][K][k] += T3[k][0] * g0 + T3[k][1] * g1 + T3[k][2] * g2;
+                    for (int k = 0; k < 3; ++k) {
+                        // one fused multiply-add per product, accumulated in place
+                        Kr[i][K][k] += T3[k][0] * g0;
+                        Kr[i][K][k] += T3[k][1] * g1;
+                        Kr[i][K][k] += T3[k][2] * g2;
+                    }
                 }
             }
         }

@@ -149,7 +149,9 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 384)
             const T *Aq = Pq + 9;
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                f[i] += Pq[3 * i] * wg0 + Pq[3 * i + 1] * wg1 + Pq[3 * i + 2] * wg2;
+                f[i] += Pq[3 * i] * wg0;
+                f[i] += Pq[3 * i + 1] * wg1;
+                f[i] += Pq[3 * i + 2] * wg2;
                 T T3[3][3];
 #pragma unroll
                 for (int k = 0; k < 3; ++k)
@@ -162,7 +164,11 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 384)
                     const int K = 2 * jb + kk;
                     const T g0 = gq[3 * K], g1 = gq[3 * K + 1], g2 = gq[3 * K + 2];
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) Kr[i][kk][k] += T3[k][0] * g0 + T3[k][1] * g1 + T3[k][2] * g2;
+                    for (int k = 0; k < 3; ++k) {
+                        Kr[i][kk][k] += T3[k][0] * g0;
+                        Kr[i][kk][k] += T3[k][1] * g1;
+                        Kr[i][kk][k] += T3[k][2] * g2;
+                    }
                 }
             }
         }

@@ -121,7 +121,11 @@ __global__ void __launch_bounds__(128)
         // eq. r-quad: f_I,i += w tau_ij grad phi_I,j
 #pragma unroll
         for (int i = 0; i < 3; ++i)
-            f[i] += tq[voigt_of(i, 0)] * wg[0] + tq[voigt_of(i, 1)] * wg[1] + tq[voigt_of(i, 2)] * wg[2];
+        {
+            f[i] += tq[voigt_of(i, 0)] * wg[0];
+            f[i] += tq[voigt_of(i, 1)] * wg[1];
+            f[i] += tq[voigt_of(i, 2)] * wg[2];
+        }
         if (want_K) {
             // eq. k-quad: K_(I,i)(K,k) += w grad phi_I,m (delta_ik tau_ml + c_imkl) grad phi_K,l
 #pragma unroll
@@ -144,7 +148,12 @@ __global__ void __launch_bounds__(128)
                 for (int K = 0; K < 8; ++K) {
                     const T g0 = s_gx[le][K][0], g1 = s_gx[le][K][1], g2 = s_gx[le][K][2];
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) Kr[i][K][k] += T3[k][0] * g0 + T3[k][1] * g1 + T3[k][2] * g2;
+                    for (int k = 0; k < 3; ++k) {
+                        // one fused multiply-add per product, accumulated in place
+                        Kr[i][K][k] += T3[k][0] * g0;
+                        Kr[i][K][k] += T3[k][1] * g1;
+                        Kr[i][K][k] += T3[k][2] * g2;
+                    }
                 }
             }
         }
