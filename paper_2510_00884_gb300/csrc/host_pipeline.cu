@@ -1,11 +1,9 @@
 // Host-buffer form of the constitutive update and the element integrals (Algorithm 2 with
 // the tables in host memory): the points, or the elements with their 8 points each, go
 // through the GPU in chunks. Chunk c is copied in on one stream while chunk c - 1 is
-// computed and chunk c - 2 is copied out on a third, with two device buffers taking
-// turns, so that the host-device copies hide behind the kernels (or the kernels behind
-// the copies, whichever is longer). Consecutive chunks compute on two alternating
-// streams, so that the next chunk's kernels fill the SMs that one chunk's last wave
-// leaves idle.
+// computed on the caller's stream and chunk c - 2 is copied out on a third, with two
+// device buffers taking turns, so that the host-device copies hide behind the kernels
+// (or the kernels behind the copies, whichever is longer).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -57,14 +55,12 @@ int copy_rows(void *dst, size_t dpitch, const void *src, size_t spitch, size_t w
 }
 
 struct Streams {
-    cudaStream_t in = nullptr, out = nullptr, comp[2] = {nullptr, nullptr};
+    cudaStream_t in = nullptr, out = nullptr;
     cudaEvent_t start = nullptr, end = nullptr, ev_in[2] = {}, ev_done[2] = {}, ev_free[2] = {};
     bool ok = true;
     Streams() {
         ok = cudaStreamCreateWithFlags(&in, cudaStreamNonBlocking) == cudaSuccess &&
-             cudaStreamCreateWithFlags(&out, cudaStreamNonBlocking) == cudaSuccess &&
-             cudaStreamCreateWithFlags(&comp[0], cudaStreamNonBlocking) == cudaSuccess &&
-             cudaStreamCreateWithFlags(&comp[1], cudaStreamNonBlocking) == cudaSuccess;
+             cudaStreamCreateWithFlags(&out, cudaStreamNonBlocking) == cudaSuccess;
         cudaEvent_t *all[] = {&start, &end, &ev_in[0], &ev_in[1], &ev_done[0], &ev_done[1], &ev_free[0], &ev_free[1]};
         for (cudaEvent_t *e : all) ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
     }
@@ -75,8 +71,6 @@ struct Streams {
             if (e) cudaEventDestroy(e);
         if (in) cudaStreamDestroy(in);
         if (out) cudaStreamDestroy(out);
-        for (cudaStream_t c : comp)
-            if (c) cudaStreamDestroy(c);
     }
 };
 
@@ -107,8 +101,6 @@ int run_host_pipeline(const commet_model *m, const commet_mesh *mesh, int64_t n_
     COMMET_CUDA_TRY(cudaEventRecord(st.start, s));
     COMMET_CUDA_TRY(cudaStreamWaitEvent(st.in, st.start, 0));
     COMMET_CUDA_TRY(cudaStreamWaitEvent(st.out, st.start, 0));
-    COMMET_CUDA_TRY(cudaStreamWaitEvent(st.comp[0], st.start, 0));
-    COMMET_CUDA_TRY(cudaStreamWaitEvent(st.comp[1], st.start, 0));
     int rc = COMMET_OK;
     for (int64_t c = 0; c < n_chunks && rc == COMMET_OK; ++c) {
         const int b = (int)(c & 1);
@@ -122,21 +114,20 @@ int run_host_pipeline(const commet_model *m, const commet_mesh *mesh, int64_t n_
                        cudaMemcpyHostToDevice, st.in);
         if (rc != COMMET_OK) break;
         COMMET_CUDA_TRY(cudaEventRecord(st.ev_in[b], st.in));
-        // kernels on the chunk's compute stream (the buffer's parity)
-        cudaStream_t cs = st.comp[b];
-        COMMET_CUDA_TRY(cudaStreamWaitEvent(cs, st.ev_in[b], 0));
+        // kernels on the caller's stream
+        COMMET_CUDA_TRY(cudaStreamWaitEvent(s, st.ev_in[b], 0));
         rc = commet_const_update(m, nq, buf + lay.F, psi ? buf + lay.psi : nullptr, buf + lay.P,
-                                 want_A ? buf + lay.A : nullptr, nullptr, cs);
+                                 want_A ? buf + lay.A : nullptr, nullptr, s);
         if (rc != COMMET_OK) break;
         if (mesh && (f_e != nullptr || K_e != nullptr)) {
             commet_mesh view = *mesh;  // the chunk's elements: same nodes, a window of conn
             view.n_el = nu;
             view.d_conn = mesh->d_conn + 8 * u0;
             rc = launch_elem_assemble(&view, prec_elem, buf + lay.P, want_A ? buf + lay.A : nullptr,
-                                      f_e ? buf + lay.fe : nullptr, K_e ? buf + lay.Ke : nullptr, nullptr, nullptr, cs);
+                                      f_e ? buf + lay.fe : nullptr, K_e ? buf + lay.Ke : nullptr, nullptr, nullptr, s);
             if (rc != COMMET_OK) break;
         }
-        COMMET_CUDA_TRY(cudaEventRecord(st.ev_done[b], cs));
+        COMMET_CUDA_TRY(cudaEventRecord(st.ev_done[b], s));
         // out: the chunk's results
         COMMET_CUDA_TRY(cudaStreamWaitEvent(st.out, st.ev_done[b], 0));
         unsigned char *ho = nullptr;
