@@ -161,3 +161,22 @@ def test_solver_argument_checks(pkg):
     Kv = torch.zeros(gm.nnz, dtype=torch.float64, device="cuda")
     with pytest.raises(_lib.CommetError):
         gm.cg_solve(Kv, b, max_iter=0)
+
+
+@pytest.mark.parametrize("max_iter", [16, 21, 40])
+def test_cg_graph_chunks_and_tail(pkg, max_iter):
+    """The solve replays chunks of 16 iterations as a CUDA graph and launches the rest
+    directly: stopped by max_iter (16 = one replayed chunk, 21 = one chunk and 5 direct
+    iterations, 40 = two chunks and 8), it runs exactly max_iter iterations and lands where
+    the oracle's PCG does after the same number."""
+    mesh, gm, m, u, r, Kv, dofs, _ = assembled(pkg, n=5, seed=3)
+    gm.set_dirichlet(dofs)
+    gm.apply_dirichlet(r, Kv)
+    rowptr, col = gm.csr()
+    x, it, res = gm.cg_solve(Kv, r, "f64", rtol=1e-30, max_iter=max_iter)
+    assert it == max_iter
+    x_r, it_r, res_r = solver.pcg_jacobi(rowptr, col, Kv.cpu().numpy(), r.cpu().numpy(), 1e-30, max_iter)
+    assert it_r == max_iter
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(xg - x_r) <= 1e-9 * np.linalg.norm(x_r)
+    assert abs(res - res_r) <= 1e-6 * res_r
