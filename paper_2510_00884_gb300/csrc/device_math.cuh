@@ -288,8 +288,8 @@ struct Stage {
 // components a = lane4, lane4 + 4, lane4 + 8 of every 9-component quantity, so that all
 // lanes run the same instructions (GB300 bills a divergent branch's FP64 instructions to
 // every lane of the warp). Scalars and the fibre vectors a = F A, v = C A, F v are formed
-// in every lane. c[] = dN/dK - n0; Jm1 = J - 1 from det_minus_one. With G_ONLY, only the
-// kinematic gradients g_m are staged.
+// in every lane. c[] = dN/dK - n0; Jm1 = J - 1 from det_minus_one. With G_ONLY, only what
+// P needs is staged: the kinematic gradients g_m, F, F^{-T} and 2 kappa (J - 1) J.
 template <typename T, int NF, bool G_ONLY = false>
 __device__ __forceinline__ void stage_kinematics(const T *F, const KinConst<T> &kc, const T *c, T Jm1, int lane4,
                                                  T *st) {
@@ -340,10 +340,10 @@ __device__ __forceinline__ void stage_kinematics(const T *F, const KinConst<T> &
                 st[S::g + 9 * (3 + f) + a] = T(2) * af[f][p] * A0[q];
                 st[S::g + 9 * (3 + NF + f) + a] = T(2) * (af[f][p] * vf[f][q] + Fvf[f][p] * A0[q]);
             }
+            st[S::F + a] = Fa;
+            st[S::H + a] = Ha;
             if (!G_ONLY) {
                 const T Bpq = F[3 * p] * F[3 * q] + F[3 * p + 1] * F[3 * q + 1] + F[3 * p + 2] * F[3 * q + 2];
-                st[S::F + a] = Fa;
-                st[S::H + a] = Ha;
                 st[S::U + a] = c1 * jm23 * p1 * T(2) * Fa + c2 * jm43 * p2 * gI2;
                 st[S::Bm + a] = Bpq;
                 T X = (p == q ? x0 : T(0)) - T(2) * c2 * jm43 * C[a];
@@ -362,6 +362,7 @@ __device__ __forceinline__ void stage_kinematics(const T *F, const KinConst<T> &
             }
         }
     }
+    if (G_ONLY && lane4 == 0) st[S::sc + 4 + NF] = k2 * Jm1 * J;
     if (!G_ONLY && lane4 == 0) {
         st[S::sc + 0] = c1 * jm23 * p1 * p1 * I1 + c2 * jm43 * p2 * p2 * I2 + c3 * J + k2 * J * J + k2 * Jm1 * J;
         st[S::sc + 1] = T(4) * c2 * jm43;

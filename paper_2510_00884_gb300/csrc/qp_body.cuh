@@ -140,8 +140,10 @@ __device__ __forceinline__ void qp_group_finish(const T *n0s, const T *K0s, cons
         npart += shfl_xor(npart, msk);
 #pragma unroll
         for (int m = 0; m < D; ++m) dN[m] += shfl_xor(dN[m], msk);
+        if (want_A) {  // the Hessian is zero and unused when only P is wanted
 #pragma unroll
-        for (int h = 0; h < NH; ++h) Hs[h] += shfl_xor(Hs[h], msk);
+            for (int h = 0; h < NH; ++h) Hs[h] += shfl_xor(Hs[h], msk);
+        }
     }
     if (dNq != nullptr && valid && jb == 0) {
 #pragma unroll
@@ -165,7 +167,10 @@ __device__ __forceinline__ void qp_group_finish(const T *n0s, const T *K0s, cons
     if constexpr (NF == 0) {
         if (kc.kin == COMMET_KIN_POLYCONVEX) poly_to_invariants<T>(ch, cvec, Hs);
     }
-    stage_kinematics<T, NF>(F, kc, cvec, Jm1, jb, qs);
+    if (want_A)
+        stage_kinematics<T, NF>(F, kc, cvec, Jm1, jb, qs);
+    else
+        stage_kinematics<T, NF, true>(F, kc, cvec, Jm1, jb, qs);  // what P (and tau) need
     using S = Stage<D, NF>;
     constexpr int UOFF = (S::size + 3) / 4 * 4;  // u_a = sum_m g_m[a] N_mn : [9][DP]
     constexpr int HOFF = UOFF + 9 * DP;          // d2N/dK2, full: [D][DP]
@@ -314,6 +319,7 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
         kin_scalars<T, NF>(F, kc, K, Jm1, &ch);
     }
 
+    const bool want_A = (Aq != nullptr);  // P alone needs neither F'' nor the tangents
     // ---- forward values
     constexpr int V = 16 / (int)sizeof(T);  // elements per 128-bit shared load
     T npart = T(0);
@@ -361,7 +367,7 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
                 act(y[jj], zv[jj], sv[jj], tv[jj]);
         }
         stv<NJ>(sd + (k - 1) * W + j0, sv);
-        stv<NJ>(sd + (L + k - 1) * W + j0, tv);
+        if (want_A) stv<NJ>(sd + (L + k - 1) * W + j0, tv);
         if (k < L) {
             stv<NJ>(wk + (k & 1) * W + j0, zv);
         } else {
@@ -384,16 +390,18 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
     T *yb = wk;
     {
         const T *Bt = (L == 1) ? (sw + lay.W1t + j0) : (sw + lay.Bt + (L - 2) * D * W + j0);
-        T av[NJ], sv[NJ], tv[NJ], ybar[NJ];
+        T av[NJ], sv[NJ], ybar[NJ];
         ldv<NJ>(sw + lay.a + j0, av);
         ldv<NJ>(sd + (L - 1) * W + j0, sv);
-        ldv<NJ>(sd + (2 * L - 1) * W + j0, tv);
 #pragma unroll
-        for (int jj = 0; jj < NJ; ++jj) {
-            ybar[jj] = sv[jj] * av[jj];
-            tv[jj] *= av[jj];
+        for (int jj = 0; jj < NJ; ++jj) ybar[jj] = sv[jj] * av[jj];
+        if (want_A) {  // D_L = F''(y_L) zbar_L for the Hessian
+            T tv[NJ];
+            ldv<NJ>(sd + (2 * L - 1) * W + j0, tv);
+#pragma unroll
+            for (int jj = 0; jj < NJ; ++jj) tv[jj] *= av[jj];
+            stv<NJ>(sd + (2 * L - 1) * W + j0, tv);
         }
-        stv<NJ>(sd + (2 * L - 1) * W + j0, tv);
         stv<NJ>(yb + j0, ybar);
 #pragma unroll
         for (int m = 0; m < D; ++m) {
@@ -423,15 +431,17 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
         }
         __syncwarp();
         const T *Bt = (k - 1 == 1) ? (sw + lay.W1t + j0) : (sw + lay.Bt + (k - 3) * D * W + j0);
-        T sv[NJ], tv[NJ], ybar[NJ];
+        T sv[NJ], ybar[NJ];
         ldv<NJ>(sd + (k - 2) * W + j0, sv);
-        ldv<NJ>(sd + (L + k - 2) * W + j0, tv);
 #pragma unroll
-        for (int ii = 0; ii < NJ; ++ii) {
-            ybar[ii] = sv[ii] * zb[ii];
-            tv[ii] *= zb[ii];
+        for (int ii = 0; ii < NJ; ++ii) ybar[ii] = sv[ii] * zb[ii];
+        if (want_A) {
+            T tv[NJ];
+            ldv<NJ>(sd + (L + k - 2) * W + j0, tv);
+#pragma unroll
+            for (int ii = 0; ii < NJ; ++ii) tv[ii] *= zb[ii];
+            stv<NJ>(sd + (L + k - 2) * W + j0, tv);
         }
-        stv<NJ>(sd + (L + k - 2) * W + j0, tv);
         stv<NJ>(yb + j0, ybar);
 #pragma unroll
         for (int m = 0; m < D; ++m) {
@@ -444,7 +454,6 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
     }
 
     // ---- forward tangents and Hessian (only when A is wanted: P needs dN/dK alone)
-    const bool want_A = (Aq != nullptr);
     T Hs[NH];
 #pragma unroll
     for (int h = 0; h < NH; ++h) Hs[h] = T(0);

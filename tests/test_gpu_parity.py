@@ -271,7 +271,8 @@ def test_c1_full_size_sampled(pkg, prec):
 
 @pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
 def test_stress_only_path(pkg, prec):
-    """Without A the kernels skip the tangent pass; P and psi must not change."""
+    """Without A the kernels skip the tangent pass and stage only what P needs; P agrees
+    with the full path to rounding and with the oracle at the tolerance, psi exactly."""
     rng = np.random.Generator(np.random.PCG64(51))
     spec = wl.make_model(rng, wl.KIN_RAW, 2, W=32, L=3, kappa=1.0)
     F = wl.random_F(rng, 3001, 0.15)
@@ -281,7 +282,10 @@ def test_stress_only_path(pkg, prec):
     psi2, P2, A2 = m.const_update(Fd, want_A=False)
     assert A2 is None
     torch.cuda.synchronize()
-    assert torch.equal(P1, P2) or (P1 - P2).abs().max().item() <= 1e-14 * P1.abs().max().item()
+    # the stress-only path stages only what P needs, in a separately compiled copy of the
+    # staging: the two agree to rounding (FP64 1e-14, FP32 a few ulp)
+    same_tol = 1e-14 if prec == "f64" else 1e-6
+    assert torch.equal(P1, P2) or (P1 - P2).abs().max().item() <= same_tol * P1.abs().max().item()
     assert torch.equal(psi1, psi2)
     _, P_r, _ = oracle.const_update(oracle.OracleModel(spec), cm_to_pm(Fd).astype(np.float64))
     assert_close(cm_to_pm(P2), P_r, TOL[prec], f"stress only {prec}")

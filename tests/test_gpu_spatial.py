@@ -82,7 +82,12 @@ def test_spatial_stress_only_and_edges(pkg, prec):
     tt, cc = cm_to_pm(tau), cm_to_pm(c)
     assert np.all(np.isnan(tt[5])) and np.all(np.isnan(cc[5])) and np.isnan(psi[5].item())
     good = np.arange(37) != 5
-    assert np.array_equal(cm_to_pm(tau_s)[good], tt[good])
+    # the stress-only form stages only what tau needs (a separately compiled staging):
+    # equal to rounding
+    ts = cm_to_pm(tau_s)[good]
+    same_tol = 1e-14 if prec == "f64" else 1e-6
+    assert np.abs(ts - tt[good]).max() <= same_tol * np.abs(tt[good]).max()
+    assert np.isnan(cm_to_pm(tau_s)[5]).all()
     Fin = cm_to_pm(Fd).astype(np.float64)[good]
     _, P_r, A_r = oracle.const_update(oracle.OracleModel(spec), Fin)
     tau_r, c_r = oracle.push_forward(Fin, P_r, A_r)
