@@ -48,7 +48,10 @@ extern "C" {
 /* ---- precisions ---- */
 #define COMMET_F64 0      /* everything in double */
 #define COMMET_F32 1      /* everything in float */
-#define COMMET_BF16_MLP 2 /* hidden W x W layers on bf16 tensor cores (fp32 accumulate), rest fp32 */
+#define COMMET_BF16_MLP 2 /* hidden W x W layers as tcgen05 MMAs on the fifth-generation tensor cores
+                             (bf16 operands, fp32 accumulators in tensor memory, 128 points per MMA
+                             tile), the rest in fp32; needs (d + L) W <= 512 tensor-memory columns,
+                             else UNSUPPORTED at the compute call */
 
 /* ---- kinematic layers (Sec. 2.2 eq. comp-se; App. A.2) ---- */
 #define COMMET_KIN_ISO_SHIFTED 0 /* K = (Ibar1 - 3, Ibar2 - 3, J - 1), d = 3, no fibres */
@@ -148,6 +151,8 @@ int64_t commet_model_n_params(const commet_model *m);
  * A   [81][n_qp] out, or NULL (stress only).
  * status: device int32[2] or NULL (see top of file).
  * n_qp == 0 is a no-op returning COMMET_OK. Pointers must be 16-byte aligned.
+ * With A == NULL the tangent pass is skipped (stress only); P agrees with the full
+ * call's to rounding.
  */
 int commet_const_update(const commet_model *m, int64_t n_qp, const void *F, void *psi, void *P, void *A,
                         int32_t *status, void *stream);
