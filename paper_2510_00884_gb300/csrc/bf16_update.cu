@@ -244,13 +244,23 @@ __global__ void __launch_bounds__(kTile * SPLIT, 1)
 
     const int64_t n_tiles = (n_qp + kTile - 1) / kTile;
     int64_t tile = blockIdx.x;
+    // F of the next tile is loaded while the current one is in the network passes
+    float Fn[9];
+    auto load_F = [&](int64_t t, float (&dst)[9]) {
+        const int64_t qq = t * kTile + row;
+        const bool v = t < n_tiles && qq < n_qp;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) dst[c] = v ? Fg[c * n_qp + qq] : ((c % 4) == 0 ? 1.f : 0.f);
+    };
+    load_F(tile, Fn);
     for (; tile < n_tiles; tile += gridDim.x) {
         const int64_t q = tile * kTile + row;
         const bool valid = q < n_qp;
         float F[9], K[D], Jm1;
         PolyChain<float> ch;
 #pragma unroll
-        for (int c = 0; c < 9; ++c) F[c] = valid ? Fg[c * n_qp + q] : ((c % 4) == 0 ? 1.f : 0.f);
+        for (int c = 0; c < 9; ++c) F[c] = Fn[c];
+        load_F(tile + gridDim.x, Fn);
         bool bad = !kin_scalars_f32<NF>(F, kc, K, Jm1, &ch);
         if (bad) {
 #pragma unroll
