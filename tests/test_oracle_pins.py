@@ -494,9 +494,13 @@ def test_p11_p12_paper_sizes():
 
 # ---------------------------------------------------------------------- P13
 
-def test_p13_backward_central_differences():
-    rng = np.random.Generator(np.random.PCG64(14))
-    spec = wl.make_model(rng, wl.KIN_RAW, 2, W=4, L=3, kappa=3.0, bias_std=0.1)
+@pytest.mark.parametrize("kin,nf", [(wl.KIN_RAW, 2), (wl.KIN_ISO_SHIFTED, 0), (wl.KIN_POLYCONVEX, 0)])
+def test_p13_backward_central_differences(kin, nf):
+    """dL/dtheta and dL/dF of L = sum_q G_q : P_q(F_q; theta) against central differences,
+    on every kinematic layer: raw with fibres, the shifted isochoric inputs, and the
+    polyconvex layer of App. C, whose chain rule adds the phi'' term to dL/dF."""
+    rng = np.random.Generator(np.random.PCG64(14 + kin))
+    spec = wl.make_model(rng, kin, nf, W=4, L=3, kappa=3.0, bias_std=0.1)
     m = oracle.OracleModel(spec)
     F = rand_F(rng, 6)
     G = rng.normal(size=F.shape)
