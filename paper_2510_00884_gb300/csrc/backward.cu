@@ -46,8 +46,9 @@ struct BwConf {
     static constexpr int min_warps = warps / 2;
 };
 
-// Per-point slab (elements of T): K[d], r[d], z_k/zdot_k (k = 1..L-1), zdot_L, and per
-// layer s_k, t_k, ydot_k; then ybar, ydotbar of the current layer; padded.
+// Per-point slab (elements of T): K[d] then 1, r[d] then 0 (the bias column of the W x d
+// weight-gradient sums), z_k/zdot_k (k = 1..L-1), zdot_L, and per layer s_k, t_k, ydot_k;
+// then ybar, ydotbar of the current layer; padded.
 struct BwSlab {
     int K, r, z, zd, zdL, s, t, yd, yb, ydb, size;
 };
@@ -57,8 +58,8 @@ __host__ __device__ inline int bw_round4(int x) { return (x + 3) / 4 * 4; }
 __host__ __device__ inline BwSlab bw_slab(int d, int W, int L, int NF, int tsize) {
     BwSlab b{};
     int o = 0;  // every array starts on a 4-element boundary (128-bit shared loads)
-    b.K = o; o = bw_round4(o + d);
-    b.r = o; o = bw_round4(o + d);
+    b.K = o; o = bw_round4(o + d + 1);
+    b.r = o; o = bw_round4(o + d + 1);
     b.z = o; o = bw_round4(o + (L - 1) * W);
     b.zd = o; o = bw_round4(o + (L - 1) * W);
     b.zdL = o; o = bw_round4(o + W);
@@ -233,14 +234,18 @@ __device__ __forceinline__ void tile_outer_sq(T *acc, int W, const T *base, int 
 }
 
 // The W x d blocks (rows W even, both products present) with rows in pairs: per point,
-// two paired row loads and two column loads feed four multiply-adds.
+// two paired row loads and two column loads feed four multiply-adds. Column `cols` is the
+// bias: the slabs hold 1 after V1 and 0 after V2, so it sums U1 alone (x * 1 + y * 0 adds
+// exactly x), into acc[rows * cols + row]. The W x d block and the bias vector are
+// adjacent in the parameter order, and the extra column fills threads that the W x d
+// blocks alone leave idle.
 template <typename T>
 __device__ __forceinline__ void tile_outer_rows2(T *acc, int rows, int cols, const T *base, int qstride, int u1,
                                                  int v1, int u2, int v2, int Q) {
     using T2 = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
-    const int nb = (rows >> 1) * cols;
+    const int nc = cols + 1, nb = (rows >> 1) * nc;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        const int jb = b / cols, i = b - jb * cols, j0 = 2 * jb;
+        const int jb = b / nc, i = b - jb * nc, j0 = 2 * jb;
         T s0 = T(0), s1 = T(0);
         for (int q = 0; q < Q; ++q) {
             const T *p = base + (size_t)q * qstride;
@@ -252,15 +257,19 @@ __device__ __forceinline__ void tile_outer_rows2(T *acc, int rows, int cols, con
             s0 += a2.x * c2;
             s1 += a2.y * c2;
         }
-        acc[j0 * cols + i] += s0;
-        acc[(j0 + 1) * cols + i] += s1;
+        T *r0 = (i < cols) ? acc + j0 * cols + i : acc + rows * cols + j0;
+        T *r1 = (i < cols) ? r0 + cols : r0 + 1;
+        *r0 += s0;
+        *r1 += s1;
     }
 }
 
-// acc[j] += sum_q U[q][j]
+// acc[j] += sum_q U[q][j], on the threads from t0 on (independent sums start on
+// different warps, so that they run side by side)
 template <typename T>
-__device__ __forceinline__ void tile_sum(T *acc, int n, const T *base, int qstride, int u, int Q) {
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+__device__ __forceinline__ void tile_sum(T *acc, int n, const T *base, int qstride, int u, int Q, int t0) {
+    const int nt = (int)blockDim.x - t0;
+    for (int j = (int)threadIdx.x - t0; j >= 0 && j < n; j += nt) {
         T s = T(0);
         for (int q = 0; q < Q; ++q) s += base[(size_t)q * qstride + u + j];
         acc[j] += s;
@@ -376,6 +385,8 @@ __global__ void __launch_bounds__(WARPS * 32)
                 qs[sl.K + m] = K[m];
                 qs[sl.r + m] = r[m];
             }
+            qs[sl.K + D] = T(1);  // the bias column of tile_outer_rows2
+            qs[sl.r + D] = T(0);
         }
         __syncwarp();
 
@@ -489,13 +500,13 @@ __global__ void __launch_bounds__(WARPS * 32)
             // tile reductions of this layer's weight gradients
             const T *base = slabs;
             if (k == 1) {
+                // W1 and c_1 (adjacent: oc1 = oW1 + W D)
                 tile_outer_rows2<T>(acc + oW1, W, D, base, sl.size, sl.yb, sl.K, sl.ydb, sl.r, Q);
-                tile_sum<T>(acc + oc1, W, base, sl.size, sl.yb, Q);
             } else {
                 const int o = oL + (k - 2) * lsz;
                 tile_outer_sq<T>(acc + o, W, base, sl.size, sl.yb, sl.z + (k - 2) * W, sl.ydb, sl.zd + (k - 2) * W, Q);
+                // B_k and c_k
                 tile_outer_rows2<T>(acc + o + W * W, W, D, base, sl.size, sl.yb, sl.K, sl.ydb, sl.r, Q);
-                tile_sum<T>(acc + o + W * W + W * D, W, base, sl.size, sl.yb, Q);
                 // zbar_{k-1} = A_k^T ybar_k, zdotbar_{k-1} = A_k^T ydotbar_k for own neurons
                 const T *Ar = sw + lay.Ar + (k - 2) * W * W + j0;
 #pragma unroll
@@ -522,8 +533,8 @@ __global__ void __launch_bounds__(WARPS * 32)
             }
             __syncthreads();
         }
-        tile_sum<T>(acc + oa, W, slabs, sl.size, sl.zdL, Q);
-        tile_sum<T>(acc + ob, D, slabs, sl.size, sl.r, Q);
+        tile_sum<T>(acc + oa, W, slabs, sl.size, sl.zdL, Q, 0);
+        tile_sum<T>(acc + ob, D, slabs, sl.size, sl.r, Q, blockDim.x > 32 ? 32 : 0);
 
         // ---- dL/dF = sum_n (Hr)_n g_n + G : S (structured part)
 #pragma unroll
