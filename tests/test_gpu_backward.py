@@ -74,6 +74,44 @@ def test_backward_vs_oracle(pkg, case, prec):
     assert e.max() < tol_th, e
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("nf", [0, 2])
+def test_backward_w64_half_tile(pkg, nf, prec):
+    """64-wide two-layer networks: their weights, gradient accumulators and point slabs
+    fit in shared memory only at half the CTA tile, which the launch falls back to; the
+    result matches the oracle like every other width (a ragged 1,001 points, biases set)."""
+    rng = np.random.Generator(np.random.PCG64(400 + nf))
+    kin = wl.KIN_RAW if nf else wl.KIN_ISO_SHIFTED
+    spec = wl.make_model(rng, kin, nf, W=64, L=2, kappa=2.0, bias_std=0.1)
+    F = wl.random_F(rng, 1001, 0.15)
+    G = rng.normal(size=F.shape)
+    m = pkg.Model(spec, prec)
+    Fd, Gd = pm_to_cm(F, DT[prec]), pm_to_cm(G, DT[prec])
+    dF, dth = m.backward(Fd, Gd)
+    Fin, Gin = cm_to_pm(Fd).astype(np.float64), cm_to_pm(Gd).astype(np.float64)
+    dF_r, dth_r = oracle.const_backward(oracle.OracleModel(spec), Fin, Gin)
+    assert_close(cm_to_pm(dF), dF_r, TOL[prec], f"W64 dF {prec}")
+    e = blocks_rel(dth.cpu().numpy().astype(np.float64), dth_r, spec, oracle_dtheta_abs(spec, Fin, Gin))
+    assert e.max() < (1e-12 if prec == "f64" else 1e-4), e
+
+
+def test_backward_w64_three_layers_unsupported(pkg):
+    """A 64-wide three-layer network does not fit even at half the tile: refused with
+    UNSUPPORTED before any launch, outputs untouched."""
+    from paper_2510_00884_gb300 import _lib
+    rng = np.random.Generator(np.random.PCG64(402))
+    spec = wl.make_model(rng, wl.KIN_ISO_SHIFTED, 0, W=64, L=3, kappa=1.0)
+    m = pkg.Model(spec, "f64")
+    F = pm_to_cm(wl.random_F(rng, 100, 0.1), torch.float64)
+    dF = torch.full_like(F, 7.0)
+    dth = torch.full((m.n_params,), 7.0, dtype=torch.float64, device="cuda")
+    with pytest.raises(_lib.CommetError) as ei:
+        m.backward(F, torch.zeros_like(F), out=(dF, dth))
+    assert ei.value.code == _lib.ERR_UNSUPPORTED
+    torch.cuda.synchronize()
+    assert bool((dF == 7.0).all()) and bool((dth == 7.0).all())
+
+
 def test_backward_c3_loss_central_differences(pkg):
     """C3 loss sum_q |P(F; theta) - P_target|^2 on 64 points: GPU dL/dtheta and dL/dF
     against central differences (h = 1e-6) of the GPU FP64 forward."""
