@@ -323,6 +323,15 @@ int commet_norm2(const commet_mesh *mesh, int32_t precision, int64_t n, const vo
  * Recomputes the forward per qp; stores no activations. dL_dF may be NULL.
  * workspace: device scratch of commet_const_backward_workspace() bytes, 256-byte aligned.
  * Deterministic: the same inputs give bitwise the same dL_dtheta.
+ * F, dL_dP, dL_dF in the model's precision, [9][n_qp], 16-byte aligned; dL_dtheta
+ * [n_params] is OVERWRITTEN (zeroed when n_qp = 0). A point with a non-finite F or G or
+ * J <= 0 gets NaN in dL_dF and adds nothing to dL_dtheta.
+ * Errors: INVALID_ARG (null, misaligned or short workspace); UNSUPPORTED for the bf16
+ * precision, the closed-form and KAN inner functions, stress-free models (the shift n0
+ * depends on theta), 64-wide networks with one fibre, and networks whose weights,
+ * gradient accumulators and per-point slabs do not fit in shared memory even at half the
+ * tile (64-wide with three or more layers). Nothing is launched when INVALID_ARG or
+ * UNSUPPORTED is returned.
  */
 size_t commet_const_backward_workspace(const commet_model *m, int64_t n_qp);
 int commet_const_backward(const commet_model *m, int64_t n_qp, const void *F, const void *dL_dP, void *dL_dF,
