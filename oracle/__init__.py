@@ -73,7 +73,7 @@ def _load():
         _lib.oracle_scatter_csr.restype = C.c_int64
         _lib.oracle_n_params.argtypes = [C.c_int, C.c_int, C.c_int]
         _lib.oracle_n_params.restype = C.c_int64
-        _lib.oracle_const_backward.argtypes = [P(_Model), i64, d, d, d, d]
+        _lib.oracle_const_backward.argtypes = [P(_Model), i64, d, d, d, d, d]
         _lib.oracle_const_backward.restype = C.c_int
     return _lib
 
@@ -304,15 +304,20 @@ def n_params(d: int, W: int, L: int) -> int:
     return int(_load().oracle_n_params(d, W, L))
 
 
-def const_backward(model: OracleModel, F: np.ndarray, G: np.ndarray):
-    """dL/dF[n][9] and dL/dtheta[n_params] for upstream G = dL/dP [n][9]."""
+def const_backward(model: OracleModel, F: np.ndarray, G: np.ndarray, want_abs: bool = False):
+    """dL/dF[n][9] and dL/dtheta[n_params] for upstream G = dL/dP [n][9]. With ``want_abs``
+    also sum_q |dL/dtheta of point q| per entry: the magnitude the floating-point sum over
+    points is rounded against. Points run on all OpenMP threads in contiguous blocks whose
+    sums are added in thread order."""
     lib = _load()
     F = _c64(F).reshape(-1, 9)
     G = _c64(G).reshape(-1, 9)
     n = F.shape[0]
     dF = np.empty((n, 9))
-    dth = np.empty(n_params(model.d, model.W, model.L))
-    rc = lib.oracle_const_backward(C.byref(model.s), n, _dp(F), _dp(G), _dp(dF), _dp(dth))
+    npar = n_params(model.d, model.W, model.L)
+    dth = np.empty(npar)
+    dabs = np.empty(npar) if want_abs else None
+    rc = lib.oracle_const_backward(C.byref(model.s), n, _dp(F), _dp(G), _dp(dF), _dp(dth), _dp(dabs))
     if rc != 0:
         raise RuntimeError(f"oracle_const_backward rc={rc}")
-    return dF, dth
+    return (dF, dth, dabs) if want_abs else (dF, dth)

@@ -36,6 +36,9 @@
  * none is "parity unpinned".
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stddef.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -988,115 +991,165 @@ int64_t oracle_n_params(int d, int W, int L) {
  *   dL/dtheta  = sum_q d/dtheta [ sum_m r_m dN/dK_m ],  r_m = G : dK_m/dF
  * The inner term s = grad_K N . r is propagated forward as a tangent
  * (zdot = F'(y) ydot, ydot = A zdot + B r) and then differentiated in reverse
- * with respect to every weight; qp are summed in index order.
+ * with respect to every weight. Every entry of theta receives exactly one term
+ * t_q per point. The points are split into contiguous blocks, one per OpenMP
+ * thread in thread order; each block sums its t_q in index order and the block
+ * sums are then added in thread order (with one thread: index order).
+ * dLdtheta_abs (nullable) receives sum_q |t_q| per entry, the magnitude a
+ * floating-point sum of the t_q is rounded against.
  * The volumetric penalty does not depend on theta. MICNN inner only; the
  * stress-free shift is not supported here (returns -2).
  */
-int oracle_const_backward(const oracle_model *m, int64_t n_qp, const double *F, const double *G, double *dLdF,
-                          double *dLdtheta) {
+static void backward_point(const oracle_model *m, const double *Fq, const double *Gq, double *dLdF_q, double *t,
+                           double *y, double *z, double *yd, double *zd, double *zb, double *zdb, double *yb,
+                           double *ydb) {
     const int d = m->d, W = m->W, L = m->L;
-    if (m->inner != OR_INNER_MICNN) return -1;
-    if (m->stress_free) return -2;
-    const int64_t np = oracle_n_params(d, W, L);
-    for (int64_t i = 0; i < np; ++i) dLdtheta[i] = 0.0;
-    /* offsets */
     int64_t off_W1 = 0, off_c1 = (int64_t)W * d;
     int64_t off_layer = off_c1 + W; /* start of layer 2 block */
     int64_t layer_sz = (int64_t)W * W + (int64_t)W * d + W;
     int64_t off_a = off_layer + (int64_t)(L - 1) * layer_sz, off_b = off_a + W;
-
-    double *y = (double *)malloc(sizeof(double) * L * W), *z = (double *)malloc(sizeof(double) * (L + 1) * OR_MAXW);
-    double *yd = (double *)malloc(sizeof(double) * L * W), *zd = (double *)malloc(sizeof(double) * (L + 1) * OR_MAXW);
-    double *zb = (double *)malloc(sizeof(double) * OR_MAXW), *zdb = (double *)malloc(sizeof(double) * OR_MAXW);
-    double *yb = (double *)malloc(sizeof(double) * OR_MAXW), *ydb = (double *)malloc(sizeof(double) * OR_MAXW);
-    for (int64_t q = 0; q < n_qp; ++q) {
-        const double *Fq = &F[9 * q], *Gq = &G[9 * q];
-        double psi, P[9], A[81];
-        qp_update(m, NULL, Fq, &psi, P, A);
-        if (dLdF)
-            for (int b = 0; b < 9; ++b) {
-                double s = 0.0;
-                for (int a = 0; a < 9; ++a) s += Gq[a] * A[a * 9 + b];
-                dLdF[9 * q + b] = s;
-            }
-        double K[OR_MAXD], dK[OR_MAXD * 9], d2K[OR_MAXD * 81], r[OR_MAXD];
-        oracle_kinematics(m, Fq, K, dK, d2K);
-        for (int i = 0; i < d; ++i) {
+    double psi, P[9], A[81];
+    qp_update(m, NULL, Fq, &psi, P, A);
+    if (dLdF_q)
+        for (int b = 0; b < 9; ++b) {
             double s = 0.0;
-            for (int a = 0; a < 9; ++a) s += Gq[a] * dK[9 * i + a];
-            r[i] = s;
+            for (int a = 0; a < 9; ++a) s += Gq[a] * A[a * 9 + b];
+            dLdF_q[b] = s;
         }
-        /* forward: values and tangents along r; z[0] = K, zd[0] = r */
-        for (int i = 0; i < d; ++i) {
-            z[i] = K[i];
-            zd[i] = r[i];
-        }
-        for (int k = 1; k <= L; ++k) {
-            int nin = (k == 1) ? d : W;
-            const double *A_ = (k == 1) ? m->W1 : &m->Ak[(size_t)(k - 2) * W * W];
-            const double *B_ = (k == 1) ? NULL : &m->Bk[(size_t)(k - 2) * W * d];
-            const double *c_ = m->c ? &m->c[(size_t)(k - 1) * W] : NULL;
-            const double *zin = &z[(k - 1) * OR_MAXW], *zdin = &zd[(k - 1) * OR_MAXW];
-            for (int j = 0; j < W; ++j) {
-                double s = c_ ? c_[j] : 0.0, t = 0.0;
-                for (int i = 0; i < nin; ++i) {
-                    s += A_[j * nin + i] * zin[i];
-                    t += A_[j * nin + i] * zdin[i];
-                }
-                if (B_)
-                    for (int i = 0; i < d; ++i) {
-                        s += B_[j * d + i] * K[i];
-                        t += B_[j * d + i] * r[i];
-                    }
-                y[(k - 1) * W + j] = s;
-                yd[(k - 1) * W + j] = t;
-                z[k * OR_MAXW + j] = softplus(s);
-                zd[k * OR_MAXW + j] = logistic(s) * t;
-            }
-        }
-        /* s = a . zd[L] + b . r ; reverse */
+    double K[OR_MAXD], dK[OR_MAXD * 9], d2K[OR_MAXD * 81], r[OR_MAXD];
+    oracle_kinematics(m, Fq, K, dK, d2K);
+    for (int i = 0; i < d; ++i) {
+        double s = 0.0;
+        for (int a = 0; a < 9; ++a) s += Gq[a] * dK[9 * i + a];
+        r[i] = s;
+    }
+    /* forward: values and tangents along r; z[0] = K, zd[0] = r */
+    for (int i = 0; i < d; ++i) {
+        z[i] = K[i];
+        zd[i] = r[i];
+    }
+    for (int k = 1; k <= L; ++k) {
+        int nin = (k == 1) ? d : W;
+        const double *A_ = (k == 1) ? m->W1 : &m->Ak[(size_t)(k - 2) * W * W];
+        const double *B_ = (k == 1) ? NULL : &m->Bk[(size_t)(k - 2) * W * d];
+        const double *c_ = m->c ? &m->c[(size_t)(k - 1) * W] : NULL;
+        const double *zin = &z[(k - 1) * OR_MAXW], *zdin = &zd[(k - 1) * OR_MAXW];
         for (int j = 0; j < W; ++j) {
-            dLdtheta[off_a + j] += zd[L * OR_MAXW + j];
-            zb[j] = 0.0;
-            zdb[j] = m->a[j];
-        }
-        for (int i = 0; i < d; ++i) dLdtheta[off_b + i] += r[i];
-        for (int k = L; k >= 1; --k) {
-            int nin = (k == 1) ? d : W;
-            const double *A_ = (k == 1) ? m->W1 : &m->Ak[(size_t)(k - 2) * W * W];
-            const double *zin = &z[(k - 1) * OR_MAXW], *zdin = &zd[(k - 1) * OR_MAXW];
-            for (int j = 0; j < W; ++j) {
-                double yy = y[(k - 1) * W + j], s1 = logistic(yy), s2 = s1 * (1.0 - s1);
-                ydb[j] = s1 * zdb[j];
-                yb[j] = s1 * zb[j] + s2 * yd[(k - 1) * W + j] * zdb[j];
+            double s = c_ ? c_[j] : 0.0, tt = 0.0;
+            for (int i = 0; i < nin; ++i) {
+                s += A_[j * nin + i] * zin[i];
+                tt += A_[j * nin + i] * zdin[i];
             }
-            int64_t oA = (k == 1) ? off_W1 : off_layer + (int64_t)(k - 2) * layer_sz;
-            int64_t oB = oA + (int64_t)W * W, oc = (k == 1) ? off_c1 : oB + (int64_t)W * d;
-            for (int j = 0; j < W; ++j) {
-                for (int i = 0; i < nin; ++i) dLdtheta[oA + (int64_t)j * nin + i] += yb[j] * zin[i] + ydb[j] * zdin[i];
-                if (k > 1)
-                    for (int i = 0; i < d; ++i) dLdtheta[oB + (int64_t)j * d + i] += yb[j] * K[i] + ydb[j] * r[i];
-                dLdtheta[oc + j] += yb[j];
-            }
-            if (k > 1)
-                for (int i = 0; i < nin; ++i) {
-                    double s = 0.0, t = 0.0;
-                    for (int j = 0; j < W; ++j) {
-                        s += A_[j * nin + i] * yb[j];
-                        t += A_[j * nin + i] * ydb[j];
-                    }
-                    zb[i] = s;
-                    zdb[i] = t;
+            if (B_)
+                for (int i = 0; i < d; ++i) {
+                    s += B_[j * d + i] * K[i];
+                    tt += B_[j * d + i] * r[i];
                 }
+            y[(k - 1) * W + j] = s;
+            yd[(k - 1) * W + j] = tt;
+            z[k * OR_MAXW + j] = softplus(s);
+            zd[k * OR_MAXW + j] = logistic(s) * tt;
         }
     }
-    free(y);
-    free(z);
-    free(yd);
-    free(zd);
-    free(zb);
-    free(zdb);
-    free(yb);
-    free(ydb);
-    return 0;
+    /* s = a . zd[L] + b . r ; reverse. Every entry of t is assigned once. */
+    for (int j = 0; j < W; ++j) {
+        t[off_a + j] = zd[L * OR_MAXW + j];
+        zb[j] = 0.0;
+        zdb[j] = m->a[j];
+    }
+    for (int i = 0; i < d; ++i) t[off_b + i] = r[i];
+    for (int k = L; k >= 1; --k) {
+        int nin = (k == 1) ? d : W;
+        const double *A_ = (k == 1) ? m->W1 : &m->Ak[(size_t)(k - 2) * W * W];
+        const double *zin = &z[(k - 1) * OR_MAXW], *zdin = &zd[(k - 1) * OR_MAXW];
+        for (int j = 0; j < W; ++j) {
+            double yy = y[(k - 1) * W + j], s1 = logistic(yy), s2 = s1 * (1.0 - s1);
+            ydb[j] = s1 * zdb[j];
+            yb[j] = s1 * zb[j] + s2 * yd[(k - 1) * W + j] * zdb[j];
+        }
+        int64_t oA = (k == 1) ? off_W1 : off_layer + (int64_t)(k - 2) * layer_sz;
+        int64_t oB = oA + (int64_t)W * W, oc = (k == 1) ? off_c1 : oB + (int64_t)W * d;
+        for (int j = 0; j < W; ++j) {
+            for (int i = 0; i < nin; ++i) t[oA + (int64_t)j * nin + i] = yb[j] * zin[i] + ydb[j] * zdin[i];
+            if (k > 1)
+                for (int i = 0; i < d; ++i) t[oB + (int64_t)j * d + i] = yb[j] * K[i] + ydb[j] * r[i];
+            t[oc + j] = yb[j];
+        }
+        if (k > 1)
+            for (int i = 0; i < nin; ++i) {
+                double s = 0.0, tt = 0.0;
+                for (int j = 0; j < W; ++j) {
+                    s += A_[j * nin + i] * yb[j];
+                    tt += A_[j * nin + i] * ydb[j];
+                }
+                zb[i] = s;
+                zdb[i] = tt;
+            }
+    }
+}
+
+int oracle_const_backward(const oracle_model *m, int64_t n_qp, const double *F, const double *G, double *dLdF,
+                          double *dLdtheta, double *dLdtheta_abs) {
+    const int d = m->d, W = m->W, L = m->L;
+    if (m->inner != OR_INNER_MICNN) return -1;
+    if (m->stress_free) return -2;
+    const int64_t np = oracle_n_params(d, W, L);
+    int nthr = 1;
+#ifdef _OPENMP
+    nthr = omp_get_max_threads();
+#endif
+    /* per-thread block sums (and magnitude sums), zero for threads that get no points */
+    double *part = (double *)calloc((size_t)nthr * np * 2, sizeof(double));
+    if (!part) return -3;
+    int fail = 0;
+#pragma omp parallel
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *y = (double *)malloc(sizeof(double) * L * W);
+        double *z = (double *)malloc(sizeof(double) * (L + 1) * OR_MAXW);
+        double *yd = (double *)malloc(sizeof(double) * L * W);
+        double *zd = (double *)malloc(sizeof(double) * (L + 1) * OR_MAXW);
+        double *zb = (double *)malloc(sizeof(double) * OR_MAXW), *zdb = (double *)malloc(sizeof(double) * OR_MAXW);
+        double *yb = (double *)malloc(sizeof(double) * OR_MAXW), *ydb = (double *)malloc(sizeof(double) * OR_MAXW);
+        double *t = (double *)malloc(sizeof(double) * np);
+        int ok = y && z && yd && zd && zb && zdb && yb && ydb && t;
+        if (!ok) {
+#pragma omp atomic write
+            fail = 1;
+        }
+        double *sum = &part[(size_t)tid * np * 2], *mag = sum + np;
+        /* static schedule: thread tid gets one contiguous block of points, blocks in thread order */
+#pragma omp for schedule(static)
+        for (int64_t q = 0; q < n_qp; ++q) {
+            if (!ok) continue;
+            backward_point(m, &F[9 * q], &G[9 * q], dLdF ? &dLdF[9 * q] : NULL, t, y, z, yd, zd, zb, zdb, yb, ydb);
+            for (int64_t i = 0; i < np; ++i) {
+                sum[i] += t[i];
+                mag[i] += fabs(t[i]);
+            }
+        }
+        free(y);
+        free(z);
+        free(yd);
+        free(zd);
+        free(zb);
+        free(zdb);
+        free(yb);
+        free(ydb);
+        free(t);
+    }
+    for (int64_t i = 0; i < np; ++i) {
+        double s = 0.0, a = 0.0;
+        for (int th = 0; th < nthr; ++th) {
+            s += part[(size_t)th * np * 2 + i];
+            a += part[(size_t)th * np * 2 + np + i];
+        }
+        dLdtheta[i] = s;
+        if (dLdtheta_abs) dLdtheta_abs[i] = a;
+    }
+    free(part);
+    return fail ? -3 : 0;
 }
