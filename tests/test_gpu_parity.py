@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import workload as wl
-from tests.parity import TOL, assert_close, cm_to_pm, pm_to_cm
+from tests.parity import TOL, assembly_scales, assert_close, cm_to_pm, csr_rows_rel_err, pm_to_cm, rel_err
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -205,11 +205,15 @@ def test_elem_assemble_and_csr_scatter(pkg, prec):
     rowptr, col = gm.csr()
     Kv_r, missing = oracle.scatter_csr(mesh, K_r, rowptr, col)
     assert missing == 0
-    tol = TOL[prec] * 10  # sums of up to 8 element contributions
+    # per node and per CSR row against the magnitudes of their element terms (the bound
+    # derived in tests/parity.py), at the path's per-point tolerance
+    s_r, s_K = assembly_scales(mesh, P_in, A_in, rowptr, col)
     rr = r.cpu().numpy().astype(np.float64)
-    assert np.abs(rr - r_r).max() <= tol * np.abs(r_r).max()
+    e_r = rel_err(rr.reshape(-1, 3), r_r.reshape(-1, 3), s_r.reshape(-1, 3))
+    assert e_r.max() < TOL[prec], (e_r.max(), int(e_r.argmax()))
     kk = Kv.cpu().numpy().astype(np.float64)
-    assert np.abs(kk - Kv_r).max() <= tol * np.abs(Kv_r).max()
+    e_K = csr_rows_rel_err(kk, Kv_r, s_K, rowptr)
+    assert e_K.max() < TOL[prec], (e_K.max(), int(e_K.argmax()))
 
 
 def test_target_stress(pkg):
@@ -381,7 +385,8 @@ def test_padded_widths(pkg, case, prec):
         assert W > 32 and e.code == _lib.ERR_UNSUPPORTED
         return
     Fin, Gin = cm_to_pm(Fd).astype(np.float64), cm_to_pm(Gd).astype(np.float64)
-    dF_r, dth_r = oracle.const_backward(oracle.OracleModel(spec), Fin, Gin)
+    dF_r, dth_r, dth_abs = oracle.const_backward(oracle.OracleModel(spec), Fin, Gin, want_abs=True)
     assert_close(cm_to_pm(dF), dF_r, TOL[prec], "padded dF")
-    scale = np.abs(dth_r).max()
-    assert np.abs(dth.cpu().numpy() - dth_r).max() <= (1e-11 if prec == "f64" else 1e-4) * scale
+    # each entry of dtheta is a sum over points: against sum_q |dtheta_q| of that entry
+    e = np.abs(dth.cpu().numpy().astype(np.float64) - dth_r) / np.maximum(dth_abs, 1e-300)
+    assert e.max() < (1e-12 if prec == "f64" else 1e-4), (e.max(), int(e.argmax()))
