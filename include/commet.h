@@ -173,10 +173,15 @@ int commet_const_update(const commet_model *m, int64_t n_qp, const void *F, void
  * bytes, 256-byte aligned, owned by the caller and not used by anything else until the
  * call has completed on `stream`.
  * The call returns once the work is queued; the host outputs are complete when `stream`
- * reaches that point. Two streams and eight events are created per call and released
- * when their work is done. No status word: bad points come back as NaN.
+ * reaches that point. The copies run on two side streams (with nine events) that the
+ * model handle creates with the model, on its device, and releases with it; a call
+ * creates and allocates nothing. Calls on one model from several host threads are
+ * ordered by a lock while they queue their work. On every return, error or not,
+ * `stream` waits for every copy the call queued, so once `stream` reaches that point
+ * nothing of the call still reads the workspace or F or writes the host outputs.
+ * No status word: bad points come back as NaN.
  * Errors: INVALID_ARG (NULL, sizes, alignment, workspace too small), UNSUPPORTED (as the
- * device calls), CUDA.
+ * device calls), CUDA. The model must belong to the current device.
  */
 size_t commet_const_update_host_workspace(const commet_model *m, const commet_mesh *mesh, int64_t chunk,
                                           int32_t want_A);
@@ -351,6 +356,10 @@ int commet_const_backward(const commet_model *m, int64_t n_qp, const void *F, co
  *  - Returns COMMET_ERR_UNSUPPORTED, launching nothing, when the call would need more
  *    scratch than COMMET_NOALLOC_SCRATCH_BYTES (commet_const_backward_workspace() tells
  *    the need; FP64 d7 W32 L3 needs about 7 MB, W64 networks do not fit).
+ *  - The looked-up address is kept per device ordinal for the life of the process. A
+ *    device reset (cudaDeviceReset, or anything else that destroys the primary context)
+ *    can move the array, so after one this entry point must not be called again until the
+ *    library has been unloaded and loaded anew.
  */
 #define COMMET_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)
 int commet_const_backward_noalloc(const commet_model *m, int64_t n_qp, const void *F, const void *dL_dP,

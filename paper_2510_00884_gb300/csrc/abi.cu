@@ -208,6 +208,7 @@ int create_closed_form(const commet_model_desc *desc, int32_t precision, commet_
     }
     int rc = (precision == COMMET_F64) ? upload<double>(h, &m->d_weights) : upload<float>(h, &m->d_weights);
     if (rc == COMMET_OK) rc = stress_free_shift(m);
+    if (rc == COMMET_OK) rc = pipeline_res_create(m);
     if (rc != COMMET_OK) {
         commet_model_destroy(m);
         return rc;
@@ -395,6 +396,11 @@ int commet_model_create(const commet_model_desc *desc, int32_t precision, commet
             return rc;
         }
     }
+    rc = pipeline_res_create(m);
+    if (rc != COMMET_OK) {
+        commet_model_destroy(m);
+        return rc;
+    }
     *out = m;
     return COMMET_OK;
 }
@@ -405,6 +411,7 @@ int commet_model_destroy(commet_model *m) {
     cudaFree(m->d_theta64);
     cudaFree(m->d_bf16);
     cudaFree(m->d_theta_map);
+    pipeline_res_destroy(m);
     delete m;
     return COMMET_OK;
 }

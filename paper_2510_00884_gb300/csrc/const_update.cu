@@ -1,6 +1,7 @@
 // Material-form constitutive update entry: P [9][n], A [81][n] per point.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <climits>
 #include <cstdint>
 
@@ -18,13 +19,19 @@ int launch_status_init(int32_t *status, cudaStream_t s) {
     return cudaGetLastError() == cudaSuccess ? COMMET_OK : COMMET_ERR_CUDA;
 }
 
+namespace {
+constexpr int kMaxDevices = 64;
+std::atomic<int> g_sm_count[kMaxDevices];  // 0 = not looked up yet
+}  // namespace
+
 int sm_count() {
-    static int n = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+    int n = dev < kMaxDevices ? g_sm_count[dev].load(std::memory_order_relaxed) : 0;
     if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+        // a racing first lookup on the same device stores the same value
+        if (dev < kMaxDevices) g_sm_count[dev].store(n, std::memory_order_relaxed);
     }
     return n;
 }

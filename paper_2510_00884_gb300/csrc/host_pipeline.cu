@@ -8,6 +8,8 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
+#include <new>
 
 #include "internal.h"
 
@@ -54,32 +56,46 @@ int copy_rows(void *dst, size_t dpitch, const void *src, size_t spitch, size_t w
                                                                                           : COMMET_ERR_CUDA;
 }
 
-struct Streams {
-    cudaStream_t in = nullptr, out = nullptr;
-    cudaEvent_t start = nullptr, end = nullptr, ev_in[2] = {}, ev_done[2] = {}, ev_free[2] = {};
-    bool ok = true;
-    Streams() {
-        ok = cudaStreamCreateWithFlags(&in, cudaStreamNonBlocking) == cudaSuccess &&
-             cudaStreamCreateWithFlags(&out, cudaStreamNonBlocking) == cudaSuccess;
-        cudaEvent_t *all[] = {&start, &end, &ev_in[0], &ev_in[1], &ev_done[0], &ev_done[1], &ev_free[0], &ev_free[1]};
-        for (cudaEvent_t *e : all) ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
-    }
-    // resources are released once the work queued on them has completed
-    ~Streams() {
-        cudaEvent_t all[] = {start, end, ev_in[0], ev_in[1], ev_done[0], ev_done[1], ev_free[0], ev_free[1]};
-        for (cudaEvent_t e : all)
-            if (e) cudaEventDestroy(e);
-        if (in) cudaStreamDestroy(in);
-        if (out) cudaStreamDestroy(out);
-    }
-};
-
 }  // namespace
+
+int pipeline_res_create(commet_model *m) {
+    PipelineRes *r = new (std::nothrow) PipelineRes();
+    if (r == nullptr) return COMMET_ERR_CUDA;
+    m->pipe = r;
+    bool ok = cudaStreamCreateWithFlags(&r->in, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&r->out, cudaStreamNonBlocking) == cudaSuccess;
+    cudaEvent_t *all[] = {&r->start, &r->end_in, &r->end_out, &r->ev_in[0], &r->ev_in[1],
+                          &r->ev_done[0], &r->ev_done[1], &r->ev_free[0], &r->ev_free[1]};
+    for (cudaEvent_t *e : all) ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+    return ok ? COMMET_OK : COMMET_ERR_CUDA;
+}
+
+// Streams and events are released once the work queued on them has completed.
+void pipeline_res_destroy(commet_model *m) {
+    PipelineRes *r = m->pipe;
+    if (r == nullptr) return;
+    cudaEvent_t all[] = {r->start, r->end_in, r->end_out, r->ev_in[0], r->ev_in[1],
+                         r->ev_done[0], r->ev_done[1], r->ev_free[0], r->ev_free[1]};
+    for (cudaEvent_t e : all)
+        if (e) cudaEventDestroy(e);
+    if (r->in) cudaStreamDestroy(r->in);
+    if (r->out) cudaStreamDestroy(r->out);
+    delete r;
+    m->pipe = nullptr;
+}
 
 size_t host_pipeline_workspace(const commet_model *m, const commet_mesh *mesh, int64_t chunk, bool want_A) {
     const int64_t npts = mesh ? 8 * chunk : chunk, ne = mesh ? chunk : 0;
     return 2 * chunk_layout(elem_size(m), npts, ne, want_A).bytes;
 }
+
+// Stops the chunk loop with COMMET_ERR_CUDA when a runtime call fails; the join after the
+// loop still runs.
+#define PIPE_TRY(expr)                        \
+    if ((expr) != cudaSuccess) {              \
+        rc = COMMET_ERR_CUDA;                 \
+        break;                                \
+    }
 
 int run_host_pipeline(const commet_model *m, const commet_mesh *mesh, int64_t n_qp, const void *F, void *psi, void *P,
                       void *A, void *f_e, void *K_e, void *ws, size_t ws_bytes, int64_t chunk, cudaStream_t s) {
@@ -92,8 +108,9 @@ int run_host_pipeline(const commet_model *m, const commet_mesh *mesh, int64_t n_
     const int64_t units = mesh ? n_el : n_qp;
     const int64_t n_chunks = (units + chunk - 1) / chunk;
     if (n_chunks == 0) return COMMET_OK;
-    Streams st;
-    if (!st.ok) return COMMET_ERR_CUDA;
+    if (m->pipe == nullptr) return COMMET_ERR_CUDA;
+    PipelineRes &st = *m->pipe;
+    std::lock_guard<std::mutex> lock(st.mu);
     unsigned char *base = static_cast<unsigned char *>(ws);
     const int prec_elem = m->precision == COMMET_F64 ? COMMET_F64 : COMMET_F32;
     // the side streams start after the work already queued on the caller's stream (an
@@ -109,13 +126,13 @@ int run_host_pipeline(const commet_model *m, const commet_mesh *mesh, int64_t n_
         const int64_t q0 = mesh ? 8 * u0 : u0, nq = mesh ? 8 * nu : nu;
         const size_t qpitch = es * n_qp, cw = es * nq;
         // in: F of the chunk, after chunk c - 2 has left this buffer
-        if (c >= 2) COMMET_CUDA_TRY(cudaStreamWaitEvent(st.in, st.ev_free[b], 0));
+        if (c >= 2) PIPE_TRY(cudaStreamWaitEvent(st.in, st.ev_free[b], 0));
         rc = copy_rows(buf + lay.F, cw, static_cast<const unsigned char *>(F) + es * q0, qpitch, cw, 9,
                        cudaMemcpyHostToDevice, st.in);
         if (rc != COMMET_OK) break;
-        COMMET_CUDA_TRY(cudaEventRecord(st.ev_in[b], st.in));
+        PIPE_TRY(cudaEventRecord(st.ev_in[b], st.in));
         // kernels on the caller's stream
-        COMMET_CUDA_TRY(cudaStreamWaitEvent(s, st.ev_in[b], 0));
+        PIPE_TRY(cudaStreamWaitEvent(s, st.ev_in[b], 0));
         rc = commet_const_update(m, nq, buf + lay.F, psi ? buf + lay.psi : nullptr, buf + lay.P,
                                  want_A ? buf + lay.A : nullptr, nullptr, s);
         if (rc != COMMET_OK) break;
@@ -127,15 +144,12 @@ int run_host_pipeline(const commet_model *m, const commet_mesh *mesh, int64_t n_
                                       f_e ? buf + lay.fe : nullptr, K_e ? buf + lay.Ke : nullptr, nullptr, nullptr, s);
             if (rc != COMMET_OK) break;
         }
-        COMMET_CUDA_TRY(cudaEventRecord(st.ev_done[b], s));
+        PIPE_TRY(cudaEventRecord(st.ev_done[b], s));
         // out: the chunk's results
-        COMMET_CUDA_TRY(cudaStreamWaitEvent(st.out, st.ev_done[b], 0));
-        unsigned char *ho = nullptr;
-        if (psi) {
-            ho = static_cast<unsigned char *>(psi) + es * q0;
-            if (cudaMemcpyAsync(ho, buf + lay.psi, cw, cudaMemcpyDeviceToHost, st.out) != cudaSuccess)
-                return COMMET_ERR_CUDA;
-        }
+        PIPE_TRY(cudaStreamWaitEvent(st.out, st.ev_done[b], 0));
+        if (psi)
+            PIPE_TRY(cudaMemcpyAsync(static_cast<unsigned char *>(psi) + es * q0, buf + lay.psi, cw,
+                                     cudaMemcpyDeviceToHost, st.out));
         rc = copy_rows(static_cast<unsigned char *>(P) + es * q0, qpitch, buf + lay.P, cw, cw, 9,
                        cudaMemcpyDeviceToHost, st.out);
         if (rc == COMMET_OK && want_A)
@@ -148,12 +162,18 @@ int run_host_pipeline(const commet_model *m, const commet_mesh *mesh, int64_t n_
             rc = copy_rows(static_cast<unsigned char *>(K_e) + es * u0, es * n_el, buf + lay.Ke, es * nu, es * nu, 576,
                            cudaMemcpyDeviceToHost, st.out);
         if (rc != COMMET_OK) break;
-        COMMET_CUDA_TRY(cudaEventRecord(st.ev_free[b], st.out));
+        PIPE_TRY(cudaEventRecord(st.ev_free[b], st.out));
     }
-    // the caller's stream completes when the last results have reached the host
-    COMMET_CUDA_TRY(cudaEventRecord(st.end, st.out));
-    COMMET_CUDA_TRY(cudaStreamWaitEvent(s, st.end, 0));
+    // Join, on every path: the caller's stream completes only when every copy queued on
+    // either side stream has finished, so that on return (error or not) nothing still
+    // reads the workspace or the host inputs, or writes the host outputs, behind the
+    // caller's back.
+    const bool j1 = cudaEventRecord(st.end_in, st.in) == cudaSuccess && cudaStreamWaitEvent(s, st.end_in, 0) == cudaSuccess;
+    const bool j2 = cudaEventRecord(st.end_out, st.out) == cudaSuccess && cudaStreamWaitEvent(s, st.end_out, 0) == cudaSuccess;
+    if (rc == COMMET_OK && !(j1 && j2)) rc = COMMET_ERR_CUDA;
     return rc;
 }
+
+#undef PIPE_TRY
 
 }  // namespace commet

@@ -6,6 +6,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 
 #include "../../include/commet.h"
 
@@ -48,6 +49,17 @@ struct KinParams {
     int stress_free;
 };
 
+// Side streams and events of the host-buffer pipeline (host_pipeline.cu), created with the
+// model on its device and released with it, so that a pipeline call creates nothing. The
+// mutex orders the enqueueing of concurrent calls on one model: each call records and
+// waits on these events before the next call records them again.
+struct PipelineRes {
+    cudaStream_t in = nullptr, out = nullptr;
+    cudaEvent_t start = nullptr, end_in = nullptr, end_out = nullptr;
+    cudaEvent_t ev_in[2] = {}, ev_done[2] = {}, ev_free[2] = {};
+    std::mutex mu;
+};
+
 }  // namespace commet
 
 struct commet_model {
@@ -64,6 +76,7 @@ struct commet_model {
     void *d_theta64 = nullptr;     // flat theta (double) for reference
     void *d_bf16 = nullptr;        // hidden-layer weights in bf16 fragments (BF16_MLP only)
     size_t bf16_bytes = 0;
+    commet::PipelineRes *pipe = nullptr;  // host-buffer pipeline streams and events
     int device = 0;
 };
 
@@ -100,6 +113,8 @@ struct commet_mesh {
 namespace commet {
 
 // Host-buffer pipeline (host_pipeline.cu): chunked copies in, kernels, copies out.
+int pipeline_res_create(commet_model *m);   // on the current device, at model creation
+void pipeline_res_destroy(commet_model *m);
 size_t host_pipeline_workspace(const commet_model *m, const commet_mesh *mesh, int64_t chunk, bool want_A);
 int run_host_pipeline(const commet_model *m, const commet_mesh *mesh, int64_t n_qp, const void *F, void *psi, void *P,
                       void *A, void *f_e, void *K_e, void *ws, size_t ws_bytes, int64_t chunk, cudaStream_t s);
@@ -145,6 +160,7 @@ int launch_const_backward(const commet_model *m, int64_t n_qp, const void *F, co
 // Host-side mesh graph construction (mesh_host.cpp).
 int build_csr_and_colouring(int64_t n_nodes, int64_t n_el, const int32_t *conn, commet_mesh *mesh);
 
+// SM count of the current device (cached per device ordinal).
 int sm_count();
 
 }  // namespace commet

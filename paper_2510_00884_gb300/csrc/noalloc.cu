@@ -13,6 +13,9 @@
 // array's name as a device address (in host code it names a host-side stand-in), so the
 // first call on each device, with that device current, looks the address up with
 // cudaGetSymbolAddress and caches it; make that first call before any stream capture.
+// The cache is keyed by device ordinal only: a device reset, which can load the module
+// at a new address, voids it, and the entry point must not be used after one until the
+// library is loaded anew.
 // All calls share the one array and it keeps the last call's contents; the kernel
 // writes every scratch word before reading it, so nothing has to start at zero. Calls
 // whose kernels overlap on the GPU (other streams, other host threads) race on the
