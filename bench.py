@@ -96,6 +96,43 @@ def alu_peak_tflops(kind: str, n_sm: int, mhz: float) -> float:
     return n_sm * per_clk * 2 * mhz * 1e6 / 1e12
 
 
+def load_alu_peaks():
+    """Measured FP64 / FP32 FMA rates and MUFU rates of this GPU from the committed probe
+    summary (profiles/alu_peaks.json), or None."""
+    p = os.path.join(ROOT, "profiles", "alu_peaks.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        return json.load(f)
+
+
+def alu_peak(kind: str, n_sm: int, mhz: float):
+    """(peak TFLOP/s, source) for an FP64 or FP32 kernel: the measured FMA rate when the
+    probe summary is present, else the unit-count figure."""
+    ap = load_alu_peaks()
+    key = "f64_tflops" if kind == "f64" else "f32_tflops"
+    derived = alu_peak_tflops(kind, n_sm, mhz)
+    if ap and key in ap:
+        return float(ap[key]), (f"measured {'DFMA' if kind == 'f64' else 'FFMA'} rate {ap[key]:.3g} TFLOP/s "
+                                f"(profiles/alu_peaks.json, {ap.get('profile', '')}); unit-count figure "
+                                f"{derived:.4g} at {mhz:.0f} MHz")
+    return derived, (f"derived: {n_sm} SMs x {'2 DFMA' if kind == 'f64' else '128 FFMA'}/clk x 2 flop x "
+                     f"{mhz:.0f} MHz (max SM clock)")
+
+
+def mufu_peak_tops(n_sm: int, mhz: float):
+    """Peak rate (T ops/s) of the softplus's MUFU mix, one ex2, one rcp and one lg2 per
+    neuron: 3 / (1/r_ex2 + 1/r_rcp + 1/r_lg2) per SM per clock from the measured rates
+    (else 16 per clock for each), and its source."""
+    ap = load_alu_peaks()
+    r = (ap or {}).get("mufu_per_sm_clk") or {}
+    ex2, rcp, lg2 = float(r.get("ex2", 16.0)), float(r.get("rcp", 16.0)), float(r.get("lg2", 16.0))
+    per_clk = 3.0 / (1.0 / ex2 + 1.0 / rcp + 1.0 / lg2)
+    src = (f"measured MUFU ex2 {ex2:.3g}, rcp {rcp:.3g}, lg2 {lg2:.3g} per SM per clock (profiles/alu_peaks.json): "
+           f"{per_clk:.3g} per clock for the mix" if r else "assumed 16 per SM per clock")
+    return per_clk * n_sm * mhz * 1e6 / 1e12, src
+
+
 def kernel_source_hash(files) -> str:
     h = hashlib.sha256()
     for f in files:
@@ -227,41 +264,98 @@ def oracle_residual_loss_gradient(oracle, m, sub, u, free):
     return oracle.compute_F_adjoint(sub, dF), dth
 
 
-def cpu_sample_rate(w, n_el_sample: int):
-    """Oracle throughput on the first n_el_sample elements (qp/s and elements/s through
-    update + element assembly), or on the first n_el_sample / 2 points of the backward
-    workload (its oracle runs on one core)."""
+def special_points(F: np.ndarray, cap: int = 4096):
+    """Indices of the points with |J - 1| < 1e-3 and of those with J < 0.8 (at most `cap`
+    of each, evenly spread), where the cancellation in J - 1 and the strong compression
+    test the reduced precisions."""
+    J = np.linalg.det(F.reshape(-1, 3, 3))
+    out = {}
+    for key, sel in (("J_near_1", np.abs(J - 1.0) < 1e-3), ("J_below_0.8", J < 0.8)):
+        idx = np.nonzero(sel)[0]
+        if idx.size > cap:
+            idx = idx[np.linspace(0, idx.size - 1, cap).astype(np.int64)]
+        out[key] = idx
+    return out
+
+
+def cpu_baseline_leg(w, n_el_sample: int, with_elements: bool = True, spatial: bool = False):
+    """The FP64 oracle on the host cores, timed on a fixed strided sample of the workload:
+    every k-th element with its 8 points (update + element assembly), or every point of
+    the backward workload (stress + loss + backward over all points). Besides the rate it
+    returns the oracle's outputs on the sample, and (untimed) on the points of
+    `special_points`, which the bench line's per-output error statement compares the GPU
+    outputs with."""
     import oracle
     oracle.build()
     spec = w["model"]
     m = oracle.OracleModel(spec)
-    if "mesh" not in w:  # c3: the backward (the oracle's backward runs on one core)
-        n = min(n_el_sample // 2, w["F"].shape[0])
-        F = w["F"][:n]
+    res = {"outputs": {}, "special": {}}
+    if "mesh" not in w:  # c3: the backward over every point (its gradient sums all of them)
+        n = w["F"].shape[0]
+        F = w["F"]
         tgt = oracle.OracleModel(None, inner=oracle.INNER_HGO, kin=1, fibres=spec.fibres, **w["target"])
         t0 = time.perf_counter()
         _, Pt, _ = oracle.const_update(tgt, F, want_A=False)
         _, P, _ = oracle.const_update(m, F, want_A=False)
-        oracle.const_backward(m, F, 2.0 * (P - Pt))
+        dF, dth, dth_abs = oracle.const_backward(m, F, 2.0 * (P - Pt), want_abs=True)
         secs = time.perf_counter() - t0
-        return n / secs, None, secs, f"first {n} points, FP64 stress + loss + backward"
+        res.update(qps=n / secs, eps=None, secs=secs, what=f"all {n} points, FP64 stress + loss + backward",
+                   idx_qp=np.arange(n), idx_el=None)
+        res["outputs"] = {"dL/dF": dF, "dL/dtheta": dth, "dL/dtheta_abs": dth_abs}
+        return res
     mesh = w["mesh"]
-    if "free" in w:  # the residual-loss gradient (its backward runs on one core)
+    if "free" in w:  # the residual-loss gradient chain on a prefix of the mesh
         el = np.arange(min(n_el_sample // 16, mesh.n_el))
         sub = wl_sub(mesh, el)
         t0 = time.perf_counter()
         oracle_residual_loss_gradient(oracle, m, sub, w["u"], w["free"])
         secs = time.perf_counter() - t0
-        return 8 * el.size / secs, el.size / secs, secs, \
-            f"first {el.size} elements and their {8 * el.size} points, FP64 residual-loss gradient chain"
-    el = np.arange(min(n_el_sample, mesh.n_el))
-    F = w["F"][: 8 * el.size] if "F" in w else oracle.compute_F(wl_sub(mesh, el), w["u"])
+        res.update(qps=8 * el.size / secs, eps=el.size / secs, secs=secs,
+                   what=f"first {el.size} elements and their {8 * el.size} points, FP64 residual-loss gradient chain",
+                   idx_qp=None, idx_el=None)
+        return res
+    n_s = min(n_el_sample, mesh.n_el)
+    el = np.linspace(0, mesh.n_el - 1, n_s).astype(np.int64) if n_s < mesh.n_el else np.arange(mesh.n_el)
+    qp = (8 * el[:, None] + np.arange(8)).ravel()
+    F = w["F"][qp] if "F" in w else oracle.compute_F(wl_sub(mesh, el), w["u"])
     t0 = time.perf_counter()
-    _, P, A = oracle.const_update(m, F)
-    oracle.elem_assemble(mesh, P, A, el=el)
+    psi, P, A = oracle.const_update(m, F)
+    if with_elements:
+        f_e, K_e = oracle.elem_assemble(mesh, P, A, el=el)
     secs = time.perf_counter() - t0
-    return 8 * el.size / secs, el.size / secs, secs, \
-        f"first {el.size} elements and their {8 * el.size} points, FP64 update + element assembly"
+    stride = f"every {mesh.n_el // n_s}th element" if n_s < mesh.n_el else "every element"
+    res.update(qps=8 * el.size / secs, eps=el.size / secs if with_elements else None, secs=secs,
+               what=f"{stride} ({el.size} elements, {8 * el.size} points), FP64 update"
+                    + (" + element assembly" if with_elements else ""),
+               idx_qp=qp, idx_el=el if with_elements else None)
+    res["outputs"] = {"psi": psi, "P": P, "A": A, "F": F}
+    if with_elements:
+        res["outputs"].update(f_e=f_e, K_e=K_e.reshape(-1, 576))
+    if spatial:
+        # the push-forward of the oracle's P and A (App. A.1) on the first 65,536 sampled points
+        ns = min(65536, F.shape[0])
+        tau, c = oracle.push_forward(F[:ns], P[:ns], A[:ns])
+        res["outputs"].update(tau=tau, c=c, n_spatial=ns)
+    if "F" in w:
+        for key, idx in special_points(w["F"]).items():
+            if idx.size:
+                sp_psi, sp_P, sp_A = oracle.const_update(m, w["F"][idx])
+                res["special"][key] = {"idx_qp": idx, "psi": sp_psi, "P": sp_P, "A": sp_A, "F": w["F"][idx]}
+    return res
+
+
+def z16_errors(gpu_pm: np.ndarray, ref_pm: np.ndarray) -> dict:
+    """Per-point (or per-element) relative error |X_gpu - X_ref|_F / max(|X_ref|_F,
+    1e-3 RMS |X_ref|_F) over a sample: its maximum, 99th percentile and median."""
+    g = np.asarray(gpu_pm, dtype=np.float64).reshape(gpu_pm.shape[0], -1)
+    r = np.asarray(ref_pm, dtype=np.float64).reshape(ref_pm.shape[0], -1)
+    nr = np.linalg.norm(r, axis=1)
+    floor = 1e-3 * np.sqrt(np.mean(nr ** 2)) if nr.size else 0.0
+    e = np.linalg.norm(g - r, axis=1) / np.maximum(np.maximum(nr, floor), 1e-300)
+    if not e.size:
+        return {"n": 0}
+    return {"n": int(e.size), "max": float(e.max()), "p99": float(np.percentile(e, 99)),
+            "median": float(np.median(e))}
 
 
 # --------------------------------------------------------------- our kernels
@@ -481,6 +575,59 @@ def launches_per_step(run) -> int:
     return n
 
 
+def error_statement(run, leg, torch) -> dict | None:
+    """Error of the step's outputs against the FP64 oracle per output, on the CPU-baseline
+    sample (the oracle's outputs on the FP64 inputs, so the reduced precisions' rounding
+    of F is part of their error): the per-point measure of z16_errors for psi, P, A (or
+    tau, c) and per element for f_e, K_e; separately on the points with |J - 1| < 1e-3 and
+    with J < 0.8; for the backward, dL/dF per point and dL/dtheta per parameter block
+    against the sum of the magnitudes of its per-point terms."""
+    out = leg.get("outputs") or {}
+    if not out:
+        return None
+
+    def cols(t, idx):
+        it = torch.from_numpy(np.asarray(idx, dtype=np.int64)).to(t.device)
+        return t.index_select(1, it).double().cpu().numpy().T
+
+    res = {"against": "FP64 oracle on the FP64 inputs", "measure": "per point |X - X_ref|_F / max(|X_ref|_F, "
+           "1e-3 RMS|X_ref|_F): max, p99, median over the sample", "sample": leg["what"]}
+    if run.name == "c3":
+        res["dL/dF"] = z16_errors(run.dF.double().cpu().numpy().T, out["dL/dF"])
+        spec = run.spec
+        d, W, L = spec.d, spec.W, spec.L
+        sizes = [W * d, W] + [W * W, W * d, W] * (L - 1) + [W, d]
+        g, r, a = run.dth.double().cpu().numpy(), out["dL/dtheta"], out["dL/dtheta_abs"]
+        blk, o = [], 0
+        for n in sizes:
+            blk.append(float(np.linalg.norm(g[o:o + n] - r[o:o + n]) / max(np.linalg.norm(a[o:o + n]), 1e-300)))
+            o += n
+        res["dL/dtheta"] = {"blocks": len(blk), "max_block": max(blk),
+                            "measure": "per block |dtheta - ref|_2 / |sum_q |dtheta_q||_2",
+                            "rel_l2": float(np.linalg.norm(g - r) / np.linalg.norm(r))}
+        return res
+    iq = leg["idx_qp"]
+    if run.spatial:
+        ns = out.get("n_spatial", 0)
+        if ns:
+            res["tau"] = z16_errors(cols(run.P, iq[:ns]), out["tau"])
+            res["c"] = z16_errors(cols(run.A, iq[:ns]), out["c"])
+            res["spatial_points"] = int(ns)
+        res["psi"] = z16_errors(cols(run.psi[None, :], iq), out["psi"][:, None])
+    else:
+        res["psi"] = z16_errors(cols(run.psi[None, :], iq), out["psi"][:, None])
+        res["P"] = z16_errors(cols(run.P, iq), out["P"])
+        res["A"] = z16_errors(cols(run.A, iq), out["A"])
+    if "f_e" in out and leg.get("idx_el") is not None:
+        res["f_e"] = z16_errors(cols(run.f_e, leg["idx_el"]), out["f_e"])
+        res["K_e"] = z16_errors(cols(run.K_e, leg["idx_el"]), out["K_e"])
+    if not run.spatial:
+        for key, sp in leg.get("special", {}).items():
+            res[key] = {"n": int(sp["idx_qp"].size), "P": z16_errors(cols(run.P, sp["idx_qp"]), sp["P"]),
+                        "A": z16_errors(cols(run.A, sp["idx_qp"]), sp["A"])}
+    return res
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2510_00884_gb300 as pkg
@@ -626,10 +773,8 @@ def run_ours(args, rank, world, local_rank):
     else:
         flops = 2 * ELEM_MACS * run.n_el
         units, src = run.n_el, ["spatial.cu" if kname == "elem_spatial_kernel" else "elem.cu", "hex8.cuh"]
-    peak = alu_peak_tflops(alu, n_sm, mhz)
+    peak, peak_source = alu_peak(alu, n_sm, mhz)
     bound = "alu"
-    peak_source = (f"derived: {n_sm} SMs x {'2 DFMA' if alu == 'f64' else '128 FFMA'}/clk x 2 flop x "
-                   f"{mhz:.0f} MHz (max SM clock; {peak_src} peaks file)")
     if prec == "bf16" and kname == "const_update_kernel":
         # the hidden W x W products run on the tensor cores: values, adjoints and the d
         # tangent channels of every hidden layer, 2 (L-1) W^2 (2 + d) flops per point
@@ -649,14 +794,15 @@ def run_ours(args, rank, world, local_rank):
         mufu = 3 * sL * sW * run.n_qp
         f32_flops = algorithmic_flops_per_qp(spec.d, sW, sL) * run.n_qp - flops
         per_qp = (9 + 1 + (6 + 21 if args.spatial else 9 + 81)) * 4
-        mufu_peak = 16 * n_sm * mhz * 1e6 / 1e12  # T ops/s: 16 per clock per SM
+        mufu_peak, mufu_src = mufu_peak_tops(n_sm, mhz)
+        f32_peak, f32_src = alu_peak("f32", n_sm, mhz)
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         bounds = {
             "tensor": {"achieved_tflops": achieved, "peak": peak, "frac": achieved / peak},
             "mufu": {"achieved_tops": mufu / sec / 1e12, "peak": mufu_peak, "frac": mufu / sec / 1e12 / mufu_peak,
-                     "ops_per_qp": 3 * sL * sW},
-            "fp32": {"achieved_tflops": f32_flops / sec / 1e12, "peak": alu_peak_tflops("f32", n_sm, mhz),
-                     "frac": f32_flops / sec / 1e12 / alu_peak_tflops("f32", n_sm, mhz)},
+                     "ops_per_qp": 3 * sL * sW, "peak_source": mufu_src},
+            "fp32": {"achieved_tflops": f32_flops / sec / 1e12, "peak": f32_peak,
+                     "frac": f32_flops / sec / 1e12 / f32_peak, "peak_source": f32_src},
             "hbm": {"achieved_gbs": per_qp * run.n_qp / sec / 1e9, "peak": hbm,
                     "frac": per_qp * run.n_qp / sec / 1e9 / hbm, "bytes_per_qp": per_qp},
         }
@@ -692,10 +838,12 @@ def run_ours(args, rank, world, local_rank):
                                    "achieved_tflops": run.n_el * 2 * ELEM_MACS / (el_ms * 1e-3) / 1e12}
 
     cpu = None
+    errors = None
     if not args.no_cpu_baseline and world == 1:
-        qps_cpu, eps_cpu, secs, what = cpu_sample_rate(w, args.cpu_sample_el)
-        cpu = {"value": qps_cpu, "unit": "qp/s", "cores": os.cpu_count() or 1, "kind": "oracle",
-               "sample": f"{what} of {w['name']}, {secs:.1f} s", "elements_per_s": eps_cpu}
+        leg = cpu_baseline_leg(w, args.cpu_sample_el, with_elements=hasattr(run, "f_e"), spatial=args.spatial)
+        cpu = {"value": leg["qps"], "unit": "qp/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+               "sample": f"{leg['what']} of {w['name']}, {leg['secs']:.1f} s", "elements_per_s": leg["eps"]}
+        errors = error_statement(run, leg, torch)
 
     cfg = {"workload": w["name"], "n_qp": run.n_qp, "n_el": run.n_el, "network": (f"d{spec.d} W{sW} L{sL}" if getattr(spec, "inner_name", "micnn") == "micnn"
                                            else f"{spec.inner_name} d{spec.d}"),
@@ -707,6 +855,7 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": prec, "data": "synthetic (seeded; random non-negative MICNN weights)",
         "elements_per_s": eps, "phases_ms": phases, "config": cfg, "roofline": roofline, "cpu_baseline": cpu,
         "e2e": e2e, "gpu_launches": n_steps * launches_per_step(run), "clocks": clocks,
+        "errors": errors,
     }
     if fp64_base is not None:
         res["fp64_unfused_gpu" if name == "c4" else "fp64_gpu"] = fp64_base
@@ -901,7 +1050,7 @@ def run_sweep(args):
                "qp_per_s": n / (ms * 1e-3), "n_params": m.n_params}
         if getattr(spec, "inner_name", "micnn") == "micnn":
             fl = algorithmic_flops_per_qp(spec.d, spec.W, spec.L) * n / (ms * 1e-3) / 1e12
-            pk = alu_peak_tflops("f64" if prec == "f64" else "f32", n_sm, mhz)
+            pk = alu_peak("f64" if prec == "f64" else "f32", n_sm, mhz)[0]
             rec.update({"bound": "alu", "achieved_tflops": fl, "frac": fl / pk})
         else:
             es = 8 if prec == "f64" else 4
