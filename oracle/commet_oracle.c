@@ -324,6 +324,13 @@ static double logistic(double y) {
     double e = exp(y);
     return e / (1.0 + e);
 }
+/* F''(y) = logistic(y) (1 - logistic(y)), written as e / (1 + e)^2 with e = exp(-|y|): the
+ * same function without the cancellation of 1 - logistic(y) once logistic(y) -> 1 (large y),
+ * where the product form keeps only a few correct digits of a tiny value */
+static double softplus_dd(double y) {
+    double e = exp(-fabs(y)), u = 1.0 + e;
+    return e / (u * u);
+}
 
 /*
  * MICNN value, gradient and Hessian in one pass, following Algorithm 4:
@@ -369,7 +376,7 @@ static void micnn_alg4(const oracle_model *m, const double *K, double *N, double
         }
         for (int j = 0; j < W; ++j) {
             double s1 = logistic(y[j]);
-            double s2 = s1 * (1.0 - s1);
+            double s2 = softplus_dd(y[j]);
             for (int p = 0; p < d; ++p)
                 for (int q = 0; q < d; ++q)
                     d2z[(j * OR_MAXD + p) * OR_MAXD + q] =
@@ -1063,7 +1070,7 @@ static void backward_point(const oracle_model *m, const double *Fq, const double
         const double *A_ = (k == 1) ? m->W1 : &m->Ak[(size_t)(k - 2) * W * W];
         const double *zin = &z[(k - 1) * OR_MAXW], *zdin = &zd[(k - 1) * OR_MAXW];
         for (int j = 0; j < W; ++j) {
-            double yy = y[(k - 1) * W + j], s1 = logistic(yy), s2 = s1 * (1.0 - s1);
+            double yy = y[(k - 1) * W + j], s1 = logistic(yy), s2 = softplus_dd(yy);
             ydb[j] = s1 * zdb[j];
             yb[j] = s1 * zb[j] + s2 * yd[(k - 1) * W + j] * zdb[j];
         }
