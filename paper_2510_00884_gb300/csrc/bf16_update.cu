@@ -48,8 +48,8 @@ constexpr int kWaitTries = 1 << 22;  // bounded mbarrier polls per MMA batch
 // (rows i, K = j) in the core-matrix layout, W * W * 2 bytes each.
 struct TcLayout {
     int d, dp, W, L;
-    int W1, Bk, c, a, b, n0, K0, f32_total;  // float offsets
-    int Ab, Atb, b16_bytes;                   // byte offsets from the start of the bf16 part
+    int W1t, Bkt, c, a, b, n0, K0, f32_total;  // float offsets; W1t [d][W], Bkt [L-1][d][W]
+    int Ab, Atb, b16_bytes;                     // byte offsets from the start of the bf16 part
 };
 
 // J - 1 = det(I + H) - 1 = tr H + (principal 2x2 minors of H) + det H, H = F - I:
@@ -122,6 +122,44 @@ __device__ __forceinline__ void store_row8(unsigned char *op, int r, int j0, con
     *reinterpret_cast<uint4 *>(op + cm_byte(r, j0, W)) = u;
 }
 
+// ---- neuron pairs in packed FP32 (fma/mul/add.rn.f32x2: two lanes per instruction)
+__device__ __forceinline__ float2 bc2(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float mufu_ex2(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float mufu_rcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float mufu_lg2(float x) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+// Softplus of two pre-activations: z = log(1 + e^y), s = z' = logistic(y), t = z'' =
+// e / (1 + e)^2 with e = exp(-|y|) = 2^(-|y| log2 e), all from three MUFU operations per
+// neuron (2^x, 1/x, log2 x); 1 + e lies in (1, 2], where the approximate reciprocal and
+// logarithm are within a few ulp, far inside the bf16 path's tolerance.
+__device__ __forceinline__ void act2(float2 y, float2 &z, float2 &s, float2 &t) {
+    constexpr float kLog2e = 1.4426950408889634f, kLn2 = 0.6931471805599453f;
+    const float2 m = __fmul2_rn(make_float2(-fabsf(y.x), -fabsf(y.y)), bc2(kLog2e));
+    const float2 e = make_float2(mufu_ex2(m.x), mufu_ex2(m.y));
+    const float2 u = __fadd2_rn(e, bc2(1.f));
+    const float2 r = make_float2(mufu_rcp(u.x), mufu_rcp(u.y));
+    const float2 lg = make_float2(mufu_lg2(u.x), mufu_lg2(u.y));
+    z = __ffma2_rn(lg, bc2(kLn2), make_float2(fmaxf(y.x, 0.f), fmaxf(y.y, 0.f)));
+    const float2 er = __fmul2_rn(e, r);
+    s = make_float2(y.x >= 0.f ? r.x : er.x, y.y >= 0.f ? r.y : er.y);
+    t = __fmul2_rn(er, r);
+}
+
+// Pair h (0: neurons 0, 1; 1: neurons 2, 3) of a quad of neurons loaded as one float4.
+__device__ __forceinline__ float2 qh(const float4 &q, int h) { return h ? make_float2(q.z, q.w) : make_float2(q.x, q.y); }
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+
 // sum_m w[m] K[m] with w 16-byte aligned in shared memory (broadcast loads).
 template <int D>
 __device__ __forceinline__ float dot_w(const float *w, const float *K) {
@@ -135,17 +173,6 @@ __device__ __forceinline__ float dot_w(const float *w, const float *K) {
         if (m0 + 3 < D) s += v.w * K[m0 + 3];
     }
     return s;
-}
-template <int D>
-__device__ __forceinline__ void load_w(const float *w, float *o) {
-#pragma unroll
-    for (int m0 = 0; m0 < D; m0 += 4) {
-        const float4 v = *reinterpret_cast<const float4 *>(w + m0);
-        o[m0] = v.x;
-        if (m0 + 1 < D) o[m0 + 1] = v.y;
-        if (m0 + 2 < D) o[m0 + 2] = v.z;
-        if (m0 + 3 < D) o[m0 + 3] = v.w;
-    }
 }
 
 // One GEMM D[128 x W] = Op[128 x W] * Bw[W x W]^T (Bw rows = output columns), K = W.
@@ -254,8 +281,6 @@ __global__ void __launch_bounds__(kTile * SPLIT, 1)
     };
     load_F(tile, Fn);
     for (; tile < n_tiles; tile += gridDim.x) {
-        const int64_t q = tile * kTile + row;
-        const bool valid = q < n_qp;
         float F[9], K[D], Jm1;
         PolyChain<float> ch;
 #pragma unroll
@@ -268,21 +293,36 @@ __global__ void __launch_bounds__(kTile * SPLIT, 1)
             kin_scalars_f32<NF>(F, kc, K, Jm1, &ch);
         }
 
-        // ---- forward values; layer 1 in fp32
-        float npart = 0.f;
+        // ---- forward values; layer 1 in fp32. Neurons go in pairs (packed FP32); tensor
+        // memory holds, for the pair (j, j + 1), half2(s_j, s_j+1) in column j and
+        // half2(t_j, t_j+1) in column j + 1 (t later replaced by D = t zbar).
+        float2 np2 = make_float2(0.f, 0.f);
 #pragma unroll 1
         for (int c = 0; c < NCH; ++c) {
             float zz[CH];
             uint32_t sv[CH];
 #pragma unroll
-            for (int u = 0; u < CH; ++u) {
+            for (int u = 0; u < CH; u += 4) {  // a quad of neurons: two pairs, 128-bit loads
                 const int j = j0 + c * CH + u;
-                const float y = s32[lay.c + j] + dot_w<D>(s32 + lay.W1 + j * lay.dp, K);
-                float z, s, tt;
-                act(y, z, s, tt);
-                sv[u] = pack_half2(s, tt);
-                zz[u] = z;
-                if (L == 1) npart += s32[lay.a + j] * z;
+                const float4 cq = ld4(s32 + lay.c + j);
+                const float4 aq = (L == 1) ? ld4(s32 + lay.a + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+                float4 wq[D];
+#pragma unroll
+                for (int m = 0; m < D; ++m) wq[m] = ld4(s32 + lay.W1t + m * W + j);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int uu = u + 2 * h;
+                    float2 y2 = qh(cq, h);
+#pragma unroll
+                    for (int m = 0; m < D; ++m) y2 = __ffma2_rn(qh(wq[m], h), bc2(K[m]), y2);
+                    float2 z2, s2, t2;
+                    act2(y2, z2, s2, t2);
+                    sv[uu] = pack_half2(s2.x, s2.y);
+                    sv[uu + 1] = pack_half2(t2.x, t2.y);
+                    zz[uu] = z2.x;
+                    zz[uu + 1] = z2.y;
+                    if (L == 1) np2 = __ffma2_rn(qh(aq, h), z2, np2);
+                }
             }
             tmem_st<CH>(tl + col_st + j0 + c * CH, sv);
             if (L > 1) {
@@ -297,7 +337,7 @@ __global__ void __launch_bounds__(kTile * SPLIT, 1)
                 break;
             }
             const float *ck = s32 + lay.c + (k - 1) * W;
-            const float *Bk = s32 + lay.Bk + (k - 2) * W * lay.dp;
+            const float *Bk = s32 + lay.Bkt + (k - 2) * D * W;
 #pragma unroll 1
             for (int c = 0; c < NCH; ++c) {
                 uint32_t acc[CH], sv[CH];
@@ -305,14 +345,28 @@ __global__ void __launch_bounds__(kTile * SPLIT, 1)
                 tmem_ld<CH>(tl + j0 + c * CH, acc);
                 tmem_wait_ld();
 #pragma unroll
-                for (int u = 0; u < CH; ++u) {
+                for (int u = 0; u < CH; u += 4) {
                     const int j = j0 + c * CH + u;
-                    const float y = __uint_as_float(acc[u]) + ck[j] + dot_w<D>(Bk + j * lay.dp, K);
-                    float z, s, tt;
-                    act(y, z, s, tt);
-                    sv[u] = pack_half2(s, tt);
-                    zz[u] = z;
-                    if (k == L) npart += s32[lay.a + j] * z;
+                    const float4 cq = ld4(ck + j);
+                    const float4 aq = (k == L) ? ld4(s32 + lay.a + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    float4 bq[D];
+#pragma unroll
+                    for (int m = 0; m < D; ++m) bq[m] = ld4(Bk + m * W + j);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int uu = u + 2 * h;
+                        float2 y2 = __fadd2_rn(make_float2(__uint_as_float(acc[uu]), __uint_as_float(acc[uu + 1])),
+                                               qh(cq, h));
+#pragma unroll
+                        for (int m = 0; m < D; ++m) y2 = __ffma2_rn(qh(bq[m], h), bc2(K[m]), y2);
+                        float2 z2, s2, t2;
+                        act2(y2, z2, s2, t2);
+                        sv[uu] = pack_half2(s2.x, s2.y);
+                        sv[uu + 1] = pack_half2(t2.x, t2.y);
+                        zz[uu] = z2.x;
+                        zz[uu + 1] = z2.y;
+                        if (k == L) np2 = __ffma2_rn(qh(aq, h), z2, np2);
+                    }
                 }
                 tmem_st<CH>(tl + col_st + (k - 1) * W + j0 + c * CH, sv);
                 if (k < L) {
@@ -322,14 +376,16 @@ __global__ void __launch_bounds__(kTile * SPLIT, 1)
             }
         }
         if (aborted) break;
+        float npart = np2.x + np2.y;
         if (part == 0) npart += dot_w<D>(s32 + lay.b, K);
 
         // ---- reverse adjoints: zbar_L = a; ybar = F' zbar; D = F'' zbar; zbar_{k-1} = ybar_k A_k
-        float dN[D];
-        load_w<D>(s32 + lay.b, dN);
-        if (part != 0) {
+        // two accumulator sets (even and odd pair of a quad) shorten the dependency chains
+        float2 dN2[2][D];
 #pragma unroll
-            for (int m = 0; m < D; ++m) dN[m] = 0.f;
+        for (int m = 0; m < D; ++m) {
+            dN2[0][m] = make_float2(part == 0 ? s32[lay.b + m] : 0.f, 0.f);
+            dN2[1][m] = make_float2(0.f, 0.f);
         }
         tmem_wait_st();  // layer L's (F', F'') pairs are read back below
         for (int k = L; k >= 1; --k) {
@@ -340,7 +396,7 @@ __global__ void __launch_bounds__(kTile * SPLIT, 1)
                     break;
                 }
             }
-            const float *Bw = (k == 1) ? (s32 + lay.W1) : (s32 + lay.Bk + (k - 2) * W * lay.dp);
+            const float *Bw = (k == 1) ? (s32 + lay.W1t) : (s32 + lay.Bkt + (k - 2) * D * W);
 #pragma unroll 1
             for (int c = 0; c < NCH; ++c) {
                 uint32_t sv[CH], acc[CH];
@@ -349,17 +405,26 @@ __global__ void __launch_bounds__(kTile * SPLIT, 1)
                 if (k < L) tmem_ld<CH>(tl + j0 + c * CH, acc);
                 tmem_wait_ld();
 #pragma unroll
-                for (int u = 0; u < CH; ++u) {
+                for (int u = 0; u < CH; u += 4) {
                     const int j = j0 + c * CH + u;
-                    const float zb = (k < L) ? __uint_as_float(acc[u]) : s32[lay.a + j];
-                    const float2 s_t = unpack_half2(sv[u]);
-                    const float yb = s_t.x * zb;
-                    sv[u] = pack_half2(s_t.x, s_t.y * zb);
-                    float w[D];
-                    load_w<D>(Bw + j * lay.dp, w);
+                    const float4 aq = (k < L) ? make_float4(0.f, 0.f, 0.f, 0.f) : ld4(s32 + lay.a + j);
+                    float4 bq[D];
 #pragma unroll
-                    for (int m = 0; m < D; ++m) dN[m] += w[m] * yb;
-                    yv[u] = yb;
+                    for (int m = 0; m < D; ++m) bq[m] = ld4(Bw + m * W + j);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int uu = u + 2 * h;
+                        const float2 zb2 = (k < L) ? make_float2(__uint_as_float(acc[uu]), __uint_as_float(acc[uu + 1]))
+                                                   : qh(aq, h);
+                        const float2 s2 = unpack_half2(sv[uu]), t2 = unpack_half2(sv[uu + 1]);
+                        const float2 yb2 = __fmul2_rn(s2, zb2);
+                        const float2 d2 = __fmul2_rn(t2, zb2);
+                        sv[uu + 1] = pack_half2(d2.x, d2.y);
+#pragma unroll
+                        for (int m = 0; m < D; ++m) dN2[h][m] = __ffma2_rn(qh(bq[m], h), yb2, dN2[h][m]);
+                        yv[uu] = yb2.x;
+                        yv[uu + 1] = yb2.y;
+                    }
                 }
                 tmem_st<CH>(tl + col_st + (k - 1) * W + j0 + c * CH, sv);
                 if (k >= 2) {
@@ -369,11 +434,18 @@ __global__ void __launch_bounds__(kTile * SPLIT, 1)
             }
         }
         if (aborted) break;
-
-        // ---- forward tangents and the Hessian H = sum_k J_k^T diag(D_k) J_k
-        float Hs[NH];
+        float dN[D];
 #pragma unroll
-        for (int i = 0; i < NH; ++i) Hs[i] = 0.f;
+        for (int m = 0; m < D; ++m) dN[m] = (dN2[0][m].x + dN2[0][m].y) + (dN2[1][m].x + dN2[1][m].y);
+
+        // ---- forward tangents and the Hessian H = sum_k J_k^T diag(D_k) J_k, on neuron
+        // pairs: H2 holds the even and the odd neurons' partial sums
+        constexpr int NHA = D == 3 ? 2 : 1;  // Hessian accumulator sets (registers allow two for d = 3)
+        float2 H2[NHA][NH];
+#pragma unroll
+        for (int a2 = 0; a2 < NHA; ++a2)
+#pragma unroll
+            for (int i = 0; i < NH; ++i) H2[a2][i] = make_float2(0.f, 0.f);
         if (want_A) {
             tmem_wait_st();
 #pragma unroll 1
@@ -383,17 +455,27 @@ __global__ void __launch_bounds__(kTile * SPLIT, 1)
                 tmem_ld<CH>(tl + col_st + j0 + c * CH, sv);
                 tmem_wait_ld();
 #pragma unroll
-                for (int u = 0; u < CH; ++u) {
+                for (int u = 0; u < CH; u += 4) {
                     const int j = j0 + c * CH + u;
-                    const float2 s_d = unpack_half2(sv[u]);
-                    float w[D];
-                    load_w<D>(s32 + lay.W1 + j * lay.dp, w);
+                    float4 wq[D];
 #pragma unroll
-                    for (int m = 0; m < D; ++m) {
-                        const float dm = s_d.y * w[m];
+                    for (int m = 0; m < D; ++m) wq[m] = ld4(s32 + lay.W1t + m * W + j);
 #pragma unroll
-                        for (int n = 0; n <= m; ++n) Hs[m * (m + 1) / 2 + n] += dm * w[n];
-                        tv[m][u] = s_d.x * w[m];
+                    for (int h = 0; h < 2; ++h) {
+                        const int uu = u + 2 * h;
+                        float2(&Hh)[NH] = H2[h % NHA];
+                        const float2 s2 = unpack_half2(sv[uu]), d2 = unpack_half2(sv[uu + 1]);
+#pragma unroll
+                        for (int m = 0; m < D; ++m) {
+                            const float2 wm = qh(wq[m], h);
+                            const float2 dm = __fmul2_rn(d2, wm);
+#pragma unroll
+                            for (int n = 0; n <= m; ++n)
+                                Hh[m * (m + 1) / 2 + n] = __ffma2_rn(dm, qh(wq[n], h), Hh[m * (m + 1) / 2 + n]);
+                            const float2 t2 = __fmul2_rn(s2, wm);
+                            tv[m][uu] = t2.x;
+                            tv[m][uu + 1] = t2.y;
+                        }
                     }
                 }
                 if (L > 1) {
@@ -413,7 +495,7 @@ __global__ void __launch_bounds__(kTile * SPLIT, 1)
                     aborted = true;
                     break;
                 }
-                const float *Bk = s32 + lay.Bk + (k - 2) * W * lay.dp;
+                const float *Bk = s32 + lay.Bkt + (k - 2) * D * W;
 #pragma unroll 1
                 for (int c = 0; c < NCH; ++c) {
                     uint32_t jv[D][CH], sv[CH];
@@ -423,19 +505,31 @@ __global__ void __launch_bounds__(kTile * SPLIT, 1)
                     tmem_wait_ld();
                     float tv[D][CH];
 #pragma unroll
-                    for (int u = 0; u < CH; ++u) {
+                    for (int u = 0; u < CH; u += 4) {
                         const int j = j0 + c * CH + u;
-                        const float2 s_d = unpack_half2(sv[u]);
-                        float Jm[D];
-                        load_w<D>(Bk + j * lay.dp, Jm);
+                        float4 bq[D];
 #pragma unroll
-                        for (int m = 0; m < D; ++m) Jm[m] += __uint_as_float(jv[m][u]);
+                        for (int m = 0; m < D; ++m) bq[m] = ld4(Bk + m * W + j);
 #pragma unroll
-                        for (int m = 0; m < D; ++m) {
-                            const float dm = s_d.y * Jm[m];
+                        for (int h = 0; h < 2; ++h) {
+                            const int uu = u + 2 * h;
+                            float2(&Hh)[NH] = H2[h % NHA];
+                            const float2 s2 = unpack_half2(sv[uu]), d2 = unpack_half2(sv[uu + 1]);
+                            float2 Jm[D];
 #pragma unroll
-                            for (int n = 0; n <= m; ++n) Hs[m * (m + 1) / 2 + n] += dm * Jm[n];
-                            tv[m][u] = s_d.x * Jm[m];
+                            for (int m = 0; m < D; ++m)
+                                Jm[m] = __fadd2_rn(make_float2(__uint_as_float(jv[m][uu]), __uint_as_float(jv[m][uu + 1])),
+                                                   qh(bq[m], h));
+#pragma unroll
+                            for (int m = 0; m < D; ++m) {
+                                const float2 dm = __fmul2_rn(d2, Jm[m]);
+#pragma unroll
+                                for (int n = 0; n <= m; ++n)
+                                    Hh[m * (m + 1) / 2 + n] = __ffma2_rn(dm, Jm[n], Hh[m * (m + 1) / 2 + n]);
+                                const float2 t2 = __fmul2_rn(s2, Jm[m]);
+                                tv[m][uu] = t2.x;
+                                tv[m][uu + 1] = t2.y;
+                            }
                         }
                     }
                     if (k < L) {
@@ -447,6 +541,12 @@ __global__ void __launch_bounds__(kTile * SPLIT, 1)
                 }
             }
             if (aborted) break;
+        }
+        float Hs[NH];
+#pragma unroll
+        for (int i = 0; i < NH; ++i) {
+            Hs[i] = H2[0][i].x + H2[0][i].y;
+            if constexpr (NHA > 1) Hs[i] += H2[NHA - 1][i].x + H2[NHA - 1][i].y;
         }
 
         // ---- the point's partial sums over its threads: npart, dN, Hs
@@ -586,8 +686,10 @@ static TcLayout tc_layout(int d, int W, int L) {
     l.W = W;
     l.L = L;
     int o = 0;
-    l.W1 = o; o += W * l.dp;
-    l.Bk = o; o += (L - 1) * W * l.dp;
+    // W1 and B_k transposed: row m holds input m's weights of all W neurons, so that the
+    // weights of neighbouring neurons (a packed pair, a 128-bit load) are adjacent
+    l.W1t = o; o += d * W;
+    l.Bkt = o; o += (L - 1) * d * W;
     l.c = o; o += L * W;
     l.a = o; o += W;
     l.b = o; o += l.dp;
@@ -620,10 +722,10 @@ int prepare_bf16_weights(commet_model *m) {
     float *f = reinterpret_cast<float *>(buf);
     unsigned char *bb = buf + f32_bytes;
     for (int j = 0; j < W; ++j)
-        for (int mm = 0; mm < d; ++mm) f[tl.W1 + j * tl.dp + mm] = h[nl.W1r + j * dpn + mm];
+        for (int mm = 0; mm < d; ++mm) f[tl.W1t + mm * W + j] = h[nl.W1r + j * dpn + mm];
     for (int k = 0; k < L - 1; ++k)
         for (int j = 0; j < W; ++j) {
-            for (int mm = 0; mm < d; ++mm) f[tl.Bk + (k * W + j) * tl.dp + mm] = h[nl.Bt + k * d * W + mm * W + j];
+            for (int mm = 0; mm < d; ++mm) f[tl.Bkt + (k * d + mm) * W + j] = h[nl.Bt + k * d * W + mm * W + j];
             for (int i = 0; i < W; ++i) {
                 const __nv_bfloat16 aji = __float2bfloat16_rn(h[nl.Ar + k * W * W + j * W + i]);
                 *reinterpret_cast<__nv_bfloat16 *>(bb + tl.Ab + k * W * W * 2 + cm_byte(j, i, W)) = aji;
