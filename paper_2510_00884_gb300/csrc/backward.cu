@@ -44,6 +44,7 @@ template <typename T>
 struct BwConf {
     static constexpr int warps = sizeof(T) == 8 ? 4 : 8;
     static constexpr int min_warps = warps / 2;
+    static constexpr int least_warps = sizeof(T) == 8 ? 1 : 2;  // smallest tile of any launch
 };
 
 // Per-point slab (elements of T): K[d] then 1, r[d] then 0 (the bias column of the W x d
@@ -278,7 +279,12 @@ __device__ __forceinline__ void tile_sum(T *acc, int n, const T *base, int qstri
 
 }  // namespace
 
-template <typename T, int NF, int W, int WARPS>
+// GACC: the network is too large for its weights, the parameter-gradient accumulators
+// and the point slabs to share the shared memory (64-wide networks with three or more
+// layers). The CTA then accumulates straight into its own slice of the workspace (each
+// entry still owned by one fixed thread, so the sums keep their order) and reads the
+// row-major A_k of the reverse pass from global memory (through L1).
+template <typename T, int NF, int W, int WARPS, bool GACC = false>
 __global__ void __launch_bounds__(WARPS * 32)
     const_backward_kernel(const T *__restrict__ gw, NetLayout lay, KinConst<T> kc, int64_t n_qp,
                           const T *__restrict__ Fg, const T *__restrict__ Gg, T *__restrict__ dFg,
@@ -289,15 +295,18 @@ __global__ void __launch_bounds__(WARPS * 32)
                   "bw_slab reserves the staged kinematics and BwPre");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sw = reinterpret_cast<T *>(smem_raw);
-    const int wbytes = (lay.total * (int)sizeof(T) + 15) / 16 * 16;
+    const int wcount = GACC ? lay.Ar : lay.total;  // A_k row-major is the last block
+    const int wbytes = (wcount * (int)sizeof(T) + 15) / 16 * 16;
     {
         const int n16 = wbytes / 16;
         const int4 *src = reinterpret_cast<const int4 *>(gw);
         int4 *dst = reinterpret_cast<int4 *>(sw);
         for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = src[i];
     }
-    T *acc = sw + wbytes / (int)sizeof(T);  // [np_pad] parameter-gradient accumulators
-    T *slabs = acc + np_pad;
+    const T *arw = GACC ? gw + lay.Ar : sw + lay.Ar;
+    // [np_pad] parameter-gradient accumulators: shared memory, or this CTA's workspace slice
+    T *acc = GACC ? partial + (size_t)blockIdx.x * np_pad : sw + wbytes / (int)sizeof(T);
+    T *slabs = GACC ? sw + wbytes / (int)sizeof(T) : acc + np_pad;
     for (int i = threadIdx.x; i < np_pad; i += blockDim.x) acc[i] = T(0);
     __syncthreads();
 
@@ -508,7 +517,7 @@ __global__ void __launch_bounds__(WARPS * 32)
                 // B_k and c_k
                 tile_outer_rows2<T>(acc + o + W * W, W, D, base, sl.size, sl.yb, sl.K, sl.ydb, sl.r, Q);
                 // zbar_{k-1} = A_k^T ybar_k, zdotbar_{k-1} = A_k^T ydotbar_k for own neurons
-                const T *Ar = sw + lay.Ar + (k - 2) * W * W + j0;
+                const T *Ar = arw + (k - 2) * W * W + j0;
 #pragma unroll
                 for (int ii = 0; ii < NJ; ++ii) {
                     zb[ii] = T(0);
@@ -571,9 +580,11 @@ __global__ void __launch_bounds__(WARPS * 32)
         }
         __syncthreads();
     }
-    // write this CTA's partial sums
-    T *dst = partial + (size_t)blockIdx.x * np_pad;
-    for (int i = threadIdx.x; i < np_pad; i += blockDim.x) dst[i] = acc[i];
+    // write this CTA's partial sums (GACC: already in place)
+    if constexpr (!GACC) {
+        T *dst = partial + (size_t)blockIdx.x * np_pad;
+        for (int i = threadIdx.x; i < np_pad; i += blockDim.x) dst[i] = acc[i];
+    }
 }
 
 // Sums the per-CTA partials of parameter p in CTA order; with a map (padded networks) the
@@ -603,12 +614,12 @@ size_t backward_workspace_bytes(const commet_model *m, int64_t n_qp) {
     if (m->inner != COMMET_INNER_MICNN) return 0;
     const size_t es = m->precision == COMMET_F64 ? 8 : 4;
     // sized for the smallest tile any launch may use (the largest grid)
-    const int Q = (m->precision == COMMET_F64 ? BwConf<double>::min_warps : BwConf<float>::min_warps) * kQPW;
+    const int Q = (m->precision == COMMET_F64 ? BwConf<double>::least_warps : BwConf<float>::least_warps) * kQPW;
     const size_t bytes = (size_t)bw_grid(m, n_qp, Q) * np_padded(m) * es;
     return (bytes + 255) / 256 * 256;
 }
 
-template <typename T, int NF, int W, int WARPS>
+template <typename T, int NF, int W, int WARPS, bool GACC = false>
 static int bw_launch(const commet_model *m, int64_t n_qp, const void *F, const void *G, void *dF, void *dth,
                      void *ws, cudaStream_t s) {
     KinConst<T> kc{};
@@ -621,13 +632,13 @@ static int bw_launch(const commet_model *m, int64_t n_qp, const void *F, const v
     const BwSlab sl = bw_slab(D, W, m->L, NF, (int)sizeof(T));
     const int Q = WARPS * kQPW;
     const int np_pad = np_padded(m);
-    const size_t wbytes = ((size_t)m->lay.total * sizeof(T) + 15) / 16 * 16;
-    const size_t smem = wbytes + (size_t)np_pad * sizeof(T) + (size_t)Q * sl.size * sizeof(T);
+    const size_t wbytes = ((size_t)(GACC ? m->lay.Ar : m->lay.total) * sizeof(T) + 15) / 16 * 16;
+    const size_t smem = wbytes + (GACC ? 0 : (size_t)np_pad * sizeof(T)) + (size_t)Q * sl.size * sizeof(T);
     int dev = 0, smem_max = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (smem > (size_t)smem_max) return COMMET_ERR_UNSUPPORTED;
-    auto kern = const_backward_kernel<T, NF, W, WARPS>;
+    auto kern = const_backward_kernel<T, NF, W, WARPS, GACC>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return COMMET_ERR_CUDA;
     const int grid = bw_grid(m, n_qp, Q);
@@ -643,9 +654,16 @@ static int bw_launch(const commet_model *m, int64_t n_qp, const void *F, const v
 template <typename T, int NF, int W>
 static int bw_typed(const commet_model *m, int64_t n_qp, const void *F, const void *G, void *dF, void *dth,
                     void *ws, cudaStream_t s) {
-    const int rc = bw_launch<T, NF, W, BwConf<T>::warps>(m, n_qp, F, G, dF, dth, ws, s);
+    int rc = bw_launch<T, NF, W, BwConf<T>::warps>(m, n_qp, F, G, dF, dth, ws, s);
     if constexpr (W == 64) {
-        if (rc == COMMET_ERR_UNSUPPORTED) return bw_launch<T, NF, W, BwConf<T>::min_warps>(m, n_qp, F, G, dF, dth, ws, s);
+        // half the tile; then accumulators in the workspace and A_k row-major from global
+        // memory, at the full, half and (FP64) quarter tile
+        if (rc == COMMET_ERR_UNSUPPORTED) rc = bw_launch<T, NF, W, BwConf<T>::min_warps>(m, n_qp, F, G, dF, dth, ws, s);
+        if (rc == COMMET_ERR_UNSUPPORTED) rc = bw_launch<T, NF, W, BwConf<T>::warps, true>(m, n_qp, F, G, dF, dth, ws, s);
+        if (rc == COMMET_ERR_UNSUPPORTED)
+            rc = bw_launch<T, NF, W, BwConf<T>::min_warps, true>(m, n_qp, F, G, dF, dth, ws, s);
+        if (rc == COMMET_ERR_UNSUPPORTED && BwConf<T>::least_warps < BwConf<T>::min_warps)
+            rc = bw_launch<T, NF, W, BwConf<T>::least_warps, true>(m, n_qp, F, G, dF, dth, ws, s);
     }
     return rc;
 }
