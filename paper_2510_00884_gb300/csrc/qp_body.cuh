@@ -120,6 +120,37 @@ __device__ __forceinline__ void stv(T *p, const T *r) {
     }
 }
 
+// One input neuron's contribution to a lane's block of the layer tangent:
+//   acc[cc][m] += (w[cc] * scale) * v[m]      (scaled: k = 2, s_1 folded into the weight)
+//   acc[cc][m] +=  w[cc] * v[m]               (otherwise)
+// FP32 with 8 output neurons per lane runs on output pairs, one fma.rn.f32x2 (two FMAs,
+// one issue slot, the same correctly rounded result per lane) per pair and input entry.
+// Measured on d7 W32 L3 (4.24 -> 3.73 ms on 2^21 points); with 4 outputs per lane the
+// scalar form was the faster one, so it is kept there and in FP64.
+template <typename T, int NC, int D>
+__device__ __forceinline__ void tangent_step(T (&acc)[NC][D], const T *w, const T *v, T scale, bool scaled = true) {
+    if constexpr (sizeof(T) == 4 && NC >= 8 && NC % 2 == 0) {
+#pragma unroll
+        for (int p = 0; p < NC / 2; ++p) {
+            float2 w2 = make_float2(w[2 * p], w[2 * p + 1]);
+            if (scaled) w2 = __fmul2_rn(w2, make_float2(scale, scale));
+#pragma unroll
+            for (int m = 0; m < D; ++m) {
+                const float2 r = __ffma2_rn(w2, make_float2(v[m], v[m]), make_float2(acc[2 * p][m], acc[2 * p + 1][m]));
+                acc[2 * p][m] = r.x;
+                acc[2 * p + 1][m] = r.y;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int cc = 0; cc < NC; ++cc) {
+            const T ws = scaled ? w[cc] * scale : w[cc];
+#pragma unroll
+            for (int m = 0; m < D; ++m) acc[cc][m] += ws * v[m];
+        }
+    }
+}
+
 // Second half of a point's update, shared by every inner function: the 4-lane group
 // reduction of the partial sums (npart, dN, Hs: N, dN/dK and the packed lower triangle
 // of d2N/dK2, each lane holding its share), the polyconvex chain rule, the kinematic
@@ -499,12 +530,7 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
                             T w1[DP], w[NC];
                             ldv<DP>(sw + lay.W1r + (i + u) * DP, w1);
                             ldv<NC>(At + (i + u) * W + c0, w);
-#pragma unroll
-                            for (int cc = 0; cc < NC; ++cc) {
-                                const T ws = w[cc] * s1[u];
-#pragma unroll
-                                for (int m = 0; m < D; ++m) acc[cc][m] += ws * w1[m];
-                            }
+                            tangent_step<T, NC, D>(acc, w, w1, s1[u]);
                         }
                     }
                 } else {
@@ -513,10 +539,7 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
                         T sv[DP], w[NC];
                         ldv<DP>(sin + i * DP, sv);
                         ldv<NC>(At + i * W + c0, w);
-#pragma unroll
-                        for (int cc = 0; cc < NC; ++cc)
-#pragma unroll
-                            for (int m = 0; m < D; ++m) acc[cc][m] += w[cc] * sv[m];
+                        tangent_step<T, NC, D>(acc, w, sv, T(1), false);
                     }
                 }
                 T Dv[NC], sjv[NC];
