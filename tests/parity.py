@@ -167,3 +167,20 @@ def csr_rows_rel_err(gpu_vals, ref_vals, scale_vals, rowptr, rows=None):
     d2 = np.add.reduceat((g - r) ** 2, starts)
     s2 = np.add.reduceat(s ** 2, starts)
     return np.sqrt(d2) / np.maximum(np.sqrt(s2), 1e-300)
+
+
+def blocks_rel(g, r, spec, scale=None):
+    """Relative error of each parameter block (W1, c1, A_k, B_k, c_k, a, b). dL/dtheta is
+    a sum over points, so the error is measured against the sum of the magnitudes of the
+    per-point terms (``scale`` = sum_q |dtheta_q|, the usual bound of a floating-point
+    sum) when it is given: a block whose terms cancel has a small result but no smaller
+    rounding error."""
+    d, W, L = spec.d, spec.W, spec.L
+    sizes = [W * d, W] + [W * W, W * d, W] * (L - 1) + [W, d]
+    sc = r if scale is None else scale
+    out, o = [], 0
+    for n in sizes:
+        a, b = g[o:o + n], r[o:o + n]
+        out.append(np.linalg.norm(a - b) / max(np.linalg.norm(sc[o:o + n]), 1e-300))
+        o += n
+    return np.array(out)

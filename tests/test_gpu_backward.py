@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 import workload as wl
-from tests.parity import TOL, assert_close, cm_to_pm, pm_to_cm
+from tests.parity import TOL, assert_close, blocks_rel, cm_to_pm, pm_to_cm
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -18,23 +18,6 @@ def pkg():
     import paper_2510_00884_gb300 as p
     p.build()
     return p
-
-
-def blocks_rel(g, r, spec, scale=None):
-    """Relative error of each parameter block (W1, c1, A_k, B_k, c_k, a, b). dL/dtheta is
-    a sum over points, so the error is measured against the sum of the magnitudes of the
-    per-point terms (``scale`` = sum_q |dtheta_q|, the usual bound of a floating-point
-    sum) when it is given: a block whose terms cancel has a small result but no smaller
-    rounding error."""
-    d, W, L = spec.d, spec.W, spec.L
-    sizes = [W * d, W] + [W * W, W * d, W] * (L - 1) + [W, d]
-    sc = r if scale is None else scale
-    out, o = [], 0
-    for n in sizes:
-        a, b = g[o:o + n], r[o:o + n]
-        out.append(np.linalg.norm(a - b) / max(np.linalg.norm(sc[o:o + n]), 1e-300))
-        o += n
-    return np.array(out)
 
 
 def oracle_dtheta_abs(spec, F, G):

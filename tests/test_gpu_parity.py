@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import workload as wl
-from tests.parity import TOL, assembly_scales, assert_close, cm_to_pm, csr_rows_rel_err, pm_to_cm, rel_err
+from tests.parity import TOL, assembly_scales, assert_close, blocks_rel, cm_to_pm, csr_rows_rel_err, pm_to_cm, rel_err
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -119,15 +119,79 @@ def test_stress_free_reference_state(pkg):
 
 # ------------------------------------------------------------------- edge cases
 
-def test_empty_and_tiny(pkg):
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_empty_and_tiny(pkg, prec):
+    """No points, and 1, 2, 8, 9 points (a part of one warp's 8-point tile and one more),
+    for the update and for the backward: the backward of no points returns a zero
+    dL/dtheta, and of one point the oracle's."""
     rng = np.random.Generator(np.random.PCG64(6))
     spec = wl.make_model(rng, wl.KIN_RAW, 2, W=32, L=3, kappa=0.0)
-    m = pkg.Model(spec, "f64")
-    F0 = torch.empty(9, 0, dtype=torch.float64, device="cuda")
+    m = pkg.Model(spec, prec)
+    F0 = torch.empty(9, 0, dtype=DT[prec], device="cuda")
     psi, P, A = m.const_update(F0)
     assert P.shape == (9, 0)
     for n in (1, 2, 8, 9):
-        check_update(pkg, spec, wl.random_F(rng, n, 0.15), "f64", f"n={n}")
+        check_update(pkg, spec, wl.random_F(rng, n, 0.15), prec, f"n={n}")
+    dF0 = torch.empty(9, 0, dtype=DT[prec], device="cuda")
+    dth0 = torch.full((m.n_params,), 7.0, dtype=DT[prec], device="cuda")
+    m.backward(F0, torch.empty_like(F0), out=(dF0, dth0))
+    torch.cuda.synchronize()
+    assert bool((dth0 == 0).all())
+    for n in (1, 9):
+        F = wl.random_F(rng, n, 0.15)
+        G = rng.normal(size=F.shape)
+        Fd, Gd = pm_to_cm(F, DT[prec]), pm_to_cm(G, DT[prec])
+        dF, dth = m.backward(Fd, Gd)
+        Fin, Gin = cm_to_pm(Fd).astype(np.float64), cm_to_pm(Gd).astype(np.float64)
+        dF_r, dth_r, dth_abs = oracle.const_backward(oracle.OracleModel(spec), Fin, Gin, want_abs=True)
+        assert_close(cm_to_pm(dF), dF_r, TOL[prec], f"backward n={n} dF")
+        e = blocks_rel(dth.cpu().numpy().astype(np.float64), dth_r, spec, dth_abs)
+        assert e.max() < (1e-12 if prec == "f64" else 1e-4), (n, e)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_single_element_mesh(pkg, prec):
+    """The smallest mesh, one distorted hex8 element: F from u, the element integrals, the
+    global r and the CSR K (one 24 x 24 block) and the fused Newton kernel, against the
+    oracle; every CSR row against the magnitudes of its terms (R14)."""
+    mesh = wl.structured_mesh(1, 1, 1, lengths=(0.9, 1.1, 0.7))
+    rng = np.random.Generator(np.random.PCG64(61))
+    X = mesh.X + 0.05 * rng.uniform(-1, 1, size=mesh.X.shape)
+    mesh = wl.Mesh(X=X, conn=mesh.conn, n=mesh.n)
+    spec = wl.make_model(rng, wl.KIN_RAW, 2, W=32, L=3, kappa=1.0)
+    gm = pkg.Mesh(mesh.X, mesh.conn, want_csr=True)
+    rowptr, col = gm.csr()
+    assert rowptr[-1] == 24 * 24
+    dt = DT[prec]
+    u = torch.from_numpy(np.ascontiguousarray((0.03 * rng.normal(size=mesh.X.shape)).T)).to(dt).cuda()
+    u_in = u.double().cpu().numpy().T
+    F = gm.compute_F(u, prec)
+    assert_close(cm_to_pm(F), oracle.compute_F(mesh, u_in), TOL[prec], "1-element F")
+    m = pkg.Model(spec, prec)
+    _, P, A = m.const_update(F)
+    P_in, A_in = cm_to_pm(P).astype(np.float64), cm_to_pm(A).astype(np.float64)
+    f_e, K_e, r, Kv = gm.elem_assemble(P, A, prec, want_r=True, want_Kcsr=True)
+    f_r, K_r = oracle.elem_assemble(mesh, P_in, A_in)
+    assert_close(cm_to_pm(f_e), f_r, TOL[prec], "1-element f_e")
+    assert_close(cm_to_pm(K_e), K_r.reshape(-1, 576), TOL[prec], "1-element K_e")
+    r_r = oracle.scatter_residual(mesh, f_r)
+    Kv_r, missing = oracle.scatter_csr(mesh, K_r, rowptr, col)
+    assert missing == 0
+    s_r, s_K = assembly_scales(mesh, P_in, A_in, rowptr, col)
+    assert rel_err(r.double().cpu().numpy().reshape(-1, 3), r_r.reshape(-1, 3), s_r.reshape(-1, 3)).max() < TOL[prec]
+    assert csr_rows_rel_err(Kv.double().cpu().numpy(), Kv_r, s_K, rowptr).max() < TOL[prec]
+    # fused: u -> r, CSR K in one pass, against the oracle chain from the same u
+    r2, Kv2, st = pkg.newton_assemble(m, gm, u, status=True)
+    torch.cuda.synchronize()
+    assert int(st[0]) == 0
+    F_o = oracle.compute_F(mesh, u_in)
+    _, P_o, A_o = oracle.const_update(oracle.OracleModel(spec), F_o)
+    f_o, K_o = oracle.elem_assemble(mesh, P_o, A_o)
+    Kv_o, _ = oracle.scatter_csr(mesh, K_o, rowptr, col)
+    s_r2, s_K2 = assembly_scales(mesh, P_o, A_o, rowptr, col)
+    r_o = oracle.scatter_residual(mesh, f_o)
+    assert rel_err(r2.double().cpu().numpy().reshape(-1, 3), r_o.reshape(-1, 3), s_r2.reshape(-1, 3)).max() < TOL[prec]
+    assert csr_rows_rel_err(Kv2.double().cpu().numpy(), Kv_o, s_K2, rowptr).max() < TOL[prec]
 
 
 def test_bad_points_are_reported(pkg):
