@@ -314,7 +314,7 @@ def const_backward(model: OracleModel, F: np.ndarray, G: np.ndarray, want_abs: b
     G = _c64(G).reshape(-1, 9)
     n = F.shape[0]
     dF = np.empty((n, 9))
-    npar = n_params(model.d, model.W, model.L)
+    npar = model.cw.size if model.cw is not None else n_params(model.d, model.W, model.L)
     dth = np.empty(npar)
     dabs = np.empty(npar) if want_abs else None
     rc = lib.oracle_const_backward(C.byref(model.s), n, _dp(F), _dp(G), _dp(dF), _dp(dth), _dp(dabs))

@@ -28,7 +28,7 @@
  *   f_int and K_e per element ........................ Eq. r-quad, k-quad (material form)
  *   Kirchhoff stress, spatial stiffness (Voigt) ...... App. A.1 (push-forward of P, A)
  *   f_int and K_e from tau, c ........................ Eq. r-quad, k-quad (spatial form)
- *   backward dL/dF, dL/dtheta ........................ chain rule on G : P(F; theta)
+ *   backward dL/dF, dL/dtheta (MICNN, CANN) .......... chain rule on G : P(F; theta)
  *   adjoints of r-quad and of the trial F ............. transposes for a residual loss (eq. loss)
  *
  * Parity status: every function here is pinned by the CPU tests (closed forms,
@@ -1004,8 +1004,8 @@ int64_t oracle_n_params(int d, int W, int L) {
  * sums are then added in thread order (with one thread: index order).
  * dLdtheta_abs (nullable) receives sum_q |t_q| per entry, the magnitude a
  * floating-point sum of the t_q is rounded against.
- * The volumetric penalty does not depend on theta. MICNN inner only; the
- * stress-free shift is not supported here (returns -2).
+ * The volumetric penalty does not depend on theta. MICNN and CANN inner functions
+ * (any other returns -1); the stress-free shift is not supported here (returns -2).
  */
 static void backward_point(const oracle_model *m, const double *Fq, const double *Gq, double *dLdF_q, double *t,
                            double *y, double *z, double *yd, double *zd, double *zb, double *zdb, double *yb,
@@ -1095,12 +1095,75 @@ static void backward_point(const oracle_model *m, const double *Fq, const double
     }
 }
 
+/*
+ * The same backward for the CANN inner function (eq. cann-def), theta = the weights
+ * w[d][n][2] = (w1, w2) per input m and term k. With r_m = G : dK_m/dF, the inner term
+ * s = sum_m r_m dN/dK_m and dN/dK_m = sum_k w2 f2'(f1(f0(K_m)); w1) f1'(f0(K_m)) f0'(K_m):
+ *   ds/dw2_mk = r_m f2' f1' f0',   ds/dw1_mk = r_m w2 (d f2'/d w1) f1' f0',
+ * with f2' and d f2'/d w1 of the menu of eq. cann-fs written out:
+ *   w1 y:           f2' = w1,              d f2'/d w1 = 1
+ *   exp(w1 y) - 1:  f2' = w1 exp(w1 y),    d f2'/d w1 = exp(w1 y) (1 + w1 y)
+ *   -ln(1 - w1 y):  f2' = w1 / (1 - w1 y), d f2'/d w1 = 1 / (1 - w1 y)^2
+ */
+static void cann_backward_point(const oracle_model *m, const double *Fq, const double *Gq, double *dLdF_q,
+                                double *t) {
+    const int d = m->d, n = m->cann_n;
+    double psi, P[9], A[81];
+    qp_update(m, NULL, Fq, &psi, P, A);
+    if (dLdF_q)
+        for (int b = 0; b < 9; ++b) {
+            double s = 0.0;
+            for (int a = 0; a < 9; ++a) s += Gq[a] * A[a * 9 + b];
+            dLdF_q[b] = s;
+        }
+    double K[OR_MAXD], dK[OR_MAXD * 9], d2K[OR_MAXD * 81];
+    oracle_kinematics(m, Fq, K, dK, d2K);
+    for (int mm = 0; mm < d; ++mm) {
+        double r = 0.0;
+        for (int a = 0; a < 9; ++a) r += Gq[a] * dK[9 * mm + a];
+        const double x = K[mm];
+        for (int k = 0; k < n; ++k) {
+            const int *kind = &m->cann_kind[3 * k];
+            const double w1 = m->cann_w[(mm * n + k) * 2], w2 = m->cann_w[(mm * n + k) * 2 + 1];
+            double f0, f0d;
+            if (kind[0] == OR_F0_MACAULAY) {
+                f0 = x > 0.0 ? x : 0.0;
+                f0d = 0.5 * (1.0 + (x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0)));
+            } else if (kind[0] == OR_F0_ABS) {
+                f0 = fabs(x);
+                f0d = x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0);
+            } else {
+                f0 = x;
+                f0d = 1.0;
+            }
+            const int p = kind[1];
+            const double f1 = pow(f0, p), f1d = p * pow(f0, p - 1);
+            double f2d, f2d_w1;
+            if (kind[2] == OR_F2_EXP) {
+                const double e = exp(w1 * f1);
+                f2d = w1 * e;
+                f2d_w1 = e * (1.0 + w1 * f1);
+            } else if (kind[2] == OR_F2_LOG) {
+                const double q = 1.0 - w1 * f1;
+                f2d = w1 / q;
+                f2d_w1 = 1.0 / (q * q);
+            } else {
+                f2d = w1;
+                f2d_w1 = 1.0;
+            }
+            t[(mm * n + k) * 2] = r * w2 * f2d_w1 * f1d * f0d;
+            t[(mm * n + k) * 2 + 1] = r * f2d * f1d * f0d;
+        }
+    }
+}
+
 int oracle_const_backward(const oracle_model *m, int64_t n_qp, const double *F, const double *G, double *dLdF,
                           double *dLdtheta, double *dLdtheta_abs) {
     const int d = m->d, W = m->W, L = m->L;
-    if (m->inner != OR_INNER_MICNN) return -1;
+    const int cann = m->inner == OR_INNER_CANN;
+    if (m->inner != OR_INNER_MICNN && !cann) return -1;
     if (m->stress_free) return -2;
-    const int64_t np = oracle_n_params(d, W, L);
+    const int64_t np = cann ? (int64_t)2 * d * m->cann_n : oracle_n_params(d, W, L);
     int nthr = 1;
 #ifdef _OPENMP
     nthr = omp_get_max_threads();
@@ -1132,7 +1195,11 @@ int oracle_const_backward(const oracle_model *m, int64_t n_qp, const double *F, 
 #pragma omp for schedule(static)
         for (int64_t q = 0; q < n_qp; ++q) {
             if (!ok) continue;
-            backward_point(m, &F[9 * q], &G[9 * q], dLdF ? &dLdF[9 * q] : NULL, t, y, z, yd, zd, zb, zdb, yb, ydb);
+            if (cann)
+                cann_backward_point(m, &F[9 * q], &G[9 * q], dLdF ? &dLdF[9 * q] : NULL, t);
+            else
+                backward_point(m, &F[9 * q], &G[9 * q], dLdF ? &dLdF[9 * q] : NULL, t, y, z, yd, zd, zb, zdb, yb,
+                               ydb);
             for (int64_t i = 0; i < np; ++i) {
                 sum[i] += t[i];
                 mag[i] += fabs(t[i]);

@@ -713,6 +713,39 @@ def test_cann_exact_derivatives(kin, nf):
         assert rel(A[q], A_h) < 1e-12
 
 
+@pytest.mark.parametrize("kin,nf", [(wl.KIN_POLYCONVEX, 0), (wl.KIN_RAW, 2), (wl.KIN_ISO_SHIFTED, 0)])
+def test_cann_backward_central_differences(kin, nf):
+    """dL/dw and dL/dF of L = sum_q G_q : P_q(F_q; w) for the CANN of eq. cann-def, every
+    f0/f1/f2 entry of eq. cann-fs, against central differences in each weight and each F
+    entry; and, since P is linear in the w2 weights, sum w2 dL/dw2 = L with kappa = 0."""
+    import dataclasses
+    rng = np.random.Generator(np.random.PCG64(43 + kin))
+    spec = wl.make_cann(rng, kin, nf, kinds=ALL_KINDS, kappa=0.0, std=0.02 if kin == wl.KIN_RAW else 0.2)
+    m = oracle.OracleModel(spec)
+    F = rand_F(rng, 5, 0.25)
+    G = rng.normal(size=F.shape)
+    dF, dth = oracle.const_backward(m, F, G)
+    theta = spec.theta()
+    assert dth.size == theta.size == 2 * spec.d * spec.n
+
+    def L_of(th, FF):
+        mm = oracle.OracleModel(dataclasses.replace(spec, w=th.reshape(spec.w.shape)))
+        _, P, _ = oracle.const_update(mm, FF, want_A=False)
+        return float(np.sum(G * P))
+    h = 1e-6
+    fd = np.array([(L_of(theta + h * e, F) - L_of(theta - h * e, F)) / (2 * h) for e in np.eye(theta.size)])
+    assert rel(dth, fd) < 1e-7
+    fdF = np.zeros_like(F)
+    for q in range(F.shape[0]):
+        for a in range(9):
+            Fp, Fm = F.copy(), F.copy()
+            Fp[q, a] += h
+            Fm[q, a] -= h
+            fdF[q, a] = (L_of(theta, Fp) - L_of(theta, Fm)) / (2 * h)
+    assert rel(dF, fdF) < 1e-7
+    assert abs(np.sum(theta[1::2] * dth[1::2]) - L_of(theta, F)) < 1e-12 * np.abs(dth).sum()
+
+
 def test_cann_reduces_to_neo_hookean():
     """One linear term w2 w1 (Ibar1 - 3) with w1 w2 = mu / 2 is the textbook Neo-Hookean."""
     mu, kappa = 1.7, 10.0
