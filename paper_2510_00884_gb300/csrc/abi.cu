@@ -42,7 +42,7 @@ NetLayout make_layout(int d, int W, int L, bool with_tab) {
     l.tab = 0;
     if (with_tab) {
         l.tab = o;
-        o = round4(o + kActTab);
+        o = round4(o + actdf::kSlots);
     }
     // the reverse pass's row-major copy of A_k comes last: networks whose block does not
     // fit in shared memory beside the point slabs read it from global memory (L1) instead
@@ -357,22 +357,10 @@ int commet_model_create(const commet_model_desc *desc, int32_t precision, commet
     for (int j = 0; j < W; ++j) h[l.a + j] = desc->a_out[j];
     for (int mm = 0; mm < d; ++mm) h[l.b + mm] = desc->b_out[mm];
     if (l.tab > 0) {
-        // tables of the FP64 activation (device_math.cuh act_tab): 2^(j/64) and
-        // log(1 + k/128) as double-double pairs, 1/(1 + k/128), from extended precision
-        for (int j = 0; j < 64; ++j) {
-            const long double v = exp2l((long double)j / 64.0L);
-            const double hi = (double)v;
-            h[l.tab + 2 * j] = hi;
-            h[l.tab + 2 * j + 1] = (double)(v - (long double)hi);
-        }
-        for (int k = 0; k <= 128; ++k) {
-            const long double F = 1.0L + (long double)k / 128.0L;
-            const long double v = logl(F);
-            const double hi = (double)v;
-            h[l.tab + 128 + 3 * k] = hi;
-            h[l.tab + 128 + 3 * k + 1] = (double)(v - (long double)hi);
-            h[l.tab + 128 + 3 * k + 2] = (double)(1.0L / F);
-        }
+        // float-pair tables of the FP64 activation (act_df.cuh), one pair per 8-byte slot
+        std::vector<actdf::f2> tab(actdf::kSlots);
+        actdf::make_table(tab.data());
+        for (int i = 0; i < actdf::kSlots; ++i) std::memcpy(&h[l.tab + i], &tab[i], sizeof(double));
     }
 
     int rc;

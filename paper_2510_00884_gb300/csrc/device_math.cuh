@@ -21,6 +21,7 @@
 #include <cstdint>
 
 #include "../../include/commet.h"
+#include "act_df.cuh"
 
 namespace commet {
 
@@ -62,66 +63,9 @@ __device__ __forceinline__ void act_value_slope(float y, float &z, float &s) {
     s = (y >= 0.0f) ? r : e * r;
 }
 
-// FP64 softplus triple from tables in shared memory, after the table-driven methods
-// of P. T. P. Tang (exp: ACM TOMS 15(2) 1989; log: ACM TOMS 16(4) 1990). GB300 runs
-// FP64 at 1/64 of FP32 and charges every warp-level FP64 instruction in full, so the
-// libm exp/log1p/division sequence (about 68 FP64 slots per neuron) dominated the
-// FP64 update; this form needs about 38.
-//  e = exp(-|y|):  -|y| = (64 m + j) ln2/64 + r, |r| <= ln2/128,
-//                  e = 2^m (T_j + T_j p(r)), p(r) = expm1(r) to degree 6, T_j = 2^(j/64)
-//  u = 1 + e rounded, c = e - (u - 1) its exact error (u in [1, 2])
-//  log1p(e) = log F_k + log1p(rr) + c / u,  F_k = 1 + k/128 nearest u, rr = (u - F_k)/F_k,
-//             |rr| <= 1/256, log1p(rr) to degree 6
-//  1/(1+e)  = (1/F_k) (1 - rr + rr^2 - ... + rr^6) (1 - c/u)
-// Table layout (doubles): [0, 128) = (T_hi, T_lo) for j = 0..63;
-// [128, 128 + 3*129) = (logF_hi, logF_lo, 1/F) for k = 0..128.
-constexpr int kActTab = 128 + 3 * 129;
-
+// FP64 softplus triple from float-pair tables in shared memory: act_df.cuh
 __device__ __forceinline__ void act_tab(double y, double &z, double &s, double &t, const double *tab) {
-    const double x = fmax(-fabs(y), -700.0);
-    const double SH = 6755399441055744.0;  // 1.5 * 2^52: rounds to an integer in the low bits
-    const double tt = fma(x, 92.33248261689366, SH);  // x * 64 / ln2
-    const double kd = tt - SH;
-    const int k = __double2loint(tt);
-    const int j = k & 63, m = k >> 6;
-    double r = fma(-kd, 0.010830424696249145, x);
-    r = fma(-kd, 3.623510646634843e-19, r);
-    double q = fma(r, 1.0 / 720.0, 1.0 / 120.0);
-    q = fma(r, q, 1.0 / 24.0);
-    q = fma(r, q, 1.0 / 6.0);
-    q = fma(r, q, 0.5);
-    const double p = fma(r * r, q, r);
-    const double Thi = tab[2 * j], Tlo = tab[2 * j + 1];
-    double e = fma(Thi, p, Tlo) + Thi;
-    e = __hiloint2double(__double2hiint(e) + (m << 20), __double2loint(e));
-    // log1p(e) and 1/(1+e)
-    const double u = 1.0 + e;
-    const double c = e - (u - 1.0);
-    const int hw = __double2hiint(u);
-    const int kk = (hw >= 0x40000000) ? 128 : (((hw & 0xFFFFF) + (1 << 12)) >> 13);
-    const double *lt = tab + 128 + 3 * kk;
-    const double F = 1.0 + kk * 0.0078125;
-    const double invF = lt[2];
-    const double rr = (u - F) * invF;
-    double g = fma(rr, -1.0 / 6.0, 0.2);
-    g = fma(rr, g, -0.25);
-    g = fma(rr, g, 1.0 / 3.0);
-    g = fma(rr, g, -0.5);
-    g = fma(rr, g, 1.0);
-    const double lrr = rr * g;                       // log1p(rr)
-    const double cu = c * invF;                      // c / u to first order
-    const double lg = lt[0] + (lt[1] + (lrr + cu));  // log1p(e)
-    double h = fma(rr, 1.0, -1.0);                   // series 1 - rr + rr^2 - ... + rr^6
-    h = fma(rr, h, 1.0);
-    h = fma(rr, h, -1.0);
-    h = fma(rr, h, 1.0);
-    h = fma(rr, h, -1.0);
-    h = fma(rr, h, 1.0);
-    const double inv_u = invF * h;
-    const double rinv = fma(-cu, inv_u, inv_u);      // 1/(u + c)
-    z = fmax(y, 0.0) + lg;
-    s = (y >= 0.0) ? rinv : e * rinv;
-    t = e * rinv * rinv;
+    actdf::softplus3(y, z, s, t, reinterpret_cast<const actdf::f2 *>(tab));
 }
 
 __device__ __forceinline__ double dev_rcbrt(double x) { return rcbrt(x); }

@@ -31,7 +31,7 @@ struct NetLayout {
     int b;    // [d]
     int n0;   // [d] stress-free shift (zeros when off)
     int K0;   // [d] K at F = I
-    int tab;  // FP64 models: activation tables (kActTab doubles); 0 otherwise
+    int tab;  // FP64 models: activation tables (actdf::kSlots float pairs); 0 otherwise
     // CANN (inner == COMMET_INNER_CANN): cn terms, weights cw [d][cn][2], kinds ck [cn][3]
     int inner, cn, cw, ck;
     // ICKAN: kR layers, B-spline degree kdeg, kG intervals; offsets of the widths [kR + 1]
