@@ -1048,7 +1048,19 @@ def run_sweep(args):
             return
         rec = {"sweep": args.sweep, "case": label, "precision": prec, "n_qp": n, "ms": ms,
                "qp_per_s": n / (ms * 1e-3), "n_params": m.n_params}
-        if getattr(spec, "inner_name", "micnn") == "micnn":
+        if getattr(spec, "inner_name", "micnn") == "micnn" and prec == "bf16":
+            # hidden products on the tensor cores against the bf16 matmul peak (headline),
+            # with the MUFU and FP32 ceilings of the rest, as in the single-workload line
+            sec = ms * 1e-3
+            tc = 2 * (spec.L - 1) * spec.W * spec.W * (2 + spec.d) * n
+            rest = algorithmic_flops_per_qp(spec.d, spec.W, spec.L) * n - tc
+            tpk = float(peaks.get("bf16_tflops", 1900.0))
+            mpk = mufu_peak_tops(n_sm, mhz)[0]
+            fpk = alu_peak("f32", n_sm, mhz)[0]
+            mufu = 3 * spec.L * spec.W * n / sec / 1e12
+            rec.update({"bound": "tensor", "achieved_tflops": tc / sec / 1e12, "frac": tc / sec / 1e12 / tpk,
+                        "mufu_frac": mufu / mpk, "fp32_frac": rest / sec / 1e12 / fpk})
+        elif getattr(spec, "inner_name", "micnn") == "micnn":
             fl = algorithmic_flops_per_qp(spec.d, spec.W, spec.L) * n / (ms * 1e-3) / 1e12
             pk = alu_peak("f64" if prec == "f64" else "f32", n_sm, mhz)[0]
             rec.update({"bound": "alu", "achieved_tflops": fl, "frac": fl / pk})

@@ -32,7 +32,6 @@ NetLayout make_layout(int d, int W, int L, bool with_tab) {
     int o = 0;
     l.W1t = o; o = round4(o + d * W);
     l.W1r = o; o = round4(o + W * dp);
-    l.At = o; o = round4(o + (L - 1) * W * W);
     l.Bt = o; o = round4(o + (L - 1) * d * W);
     l.c = o; o = round4(o + L * W);
     l.a = o; o = round4(o + W);
@@ -44,8 +43,10 @@ NetLayout make_layout(int d, int W, int L, bool with_tab) {
         l.tab = o;
         o = round4(o + actdf::kSlots);
     }
-    // the reverse pass's row-major copy of A_k comes last: networks whose block does not
-    // fit in shared memory beside the point slabs read it from global memory (L1) instead
+    // the hidden weights come last, A_k transposed (forward values and tangents) and then
+    // A_k row-major (reverse pass): networks whose weights crowd the point slabs out of
+    // shared memory read one or both of these blocks from global memory (L1/L2) instead
+    l.At = o; o = round4(o + (L - 1) * W * W);
     l.Ar = o; o = round4(o + (L - 1) * W * W);
     l.total = o;
     return l;

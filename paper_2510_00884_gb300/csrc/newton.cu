@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 384)
         T psi_val;
         bool report;
         T *pa = ea + kEPA + 90 * qi;
-        qp_group_update<T, NF, W>(sw, lay, sw + lay.Ar, kc, qs, qi, jb, F, true, pa, 1, pa + 9, 1, nullptr, 0, psi_val,
+        qp_group_update<T, NF, W>(sw, lay, sw + lay.At, sw + lay.Ar, kc, qs, qi, jb, F, true, pa, 1, pa + 9, 1, nullptr, 0, psi_val,
                                   report);
         if (report && jb == 0 && status != nullptr) {
             const int64_t q = 8 * e + qi;

@@ -321,6 +321,8 @@ __device__ __forceinline__ void qp_group_finish(const T *n0s, const T *K0s, cons
 }
 
 // One point on its 4-lane group (all 32 lanes of the warp call this together).
+//  at     the transposed A_k block (lay.At of the packed weights), in shared memory or,
+//         for networks too large for it, in global memory
 //  ar     the row-major A_k block (lay.Ar of the packed weights), in shared memory or,
 //         for networks too large for it, in global memory
 //  F      the point's deformation gradient (replaced by I when it is not admissible)
@@ -332,7 +334,8 @@ __device__ __forceinline__ void qp_group_finish(const T *n0s, const T *K0s, cons
 //                      (J <= 0, non-finite input or result); valid in every lane
 template <typename T, int NF, int W>
 __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const NetLayout &lay,
-                                                const T *__restrict__ ar, const KinConst<T> &kc, T *qs, int qi, int jb, T (&F)[9],
+                                                const T *__restrict__ at, const T *__restrict__ ar,
+                                                const KinConst<T> &kc, T *qs, int qi, int jb, T (&F)[9],
                                                 bool valid, T *Pq, int64_t pst, T *Aq, int64_t ast, T *dNq,
                                                 int64_t dst, T &psi_val, bool &report) {
     using Cf = CUConf<T, NF, W>;
@@ -367,7 +370,7 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
             }
         } else {
             const T *zin = wk + ((k - 1) & 1) * W;
-            const T *At = sw + lay.At + (k - 2) * W * W + j0;
+            const T *At = at + (k - 2) * W * W + j0;
 #pragma unroll 2
             for (int i = 0; i < W; i += V) {
                 T zv[V];
@@ -505,7 +508,7 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
             }
         }
         for (int k = 2; k <= L; ++k) {
-            const T *At = sw + lay.At + (k - 2) * W * W + j0;
+            const T *At = at + (k - 2) * W * W + j0;
             const T *Bt = sw + lay.Bt + (k - 2) * D * W + j0;
             const T *sin = wk + ((k - 1) & 1) * W * DP;
             T *sout = wk + (k & 1) * W * DP;

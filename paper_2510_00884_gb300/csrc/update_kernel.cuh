@@ -29,9 +29,11 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 384)
     using Cf = CUConf<T, NF, W>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sw = reinterpret_cast<T *>(smem_raw);
-    // the packed weights up to wcount elements go to shared memory; A_k row-major (the
-    // last block) is read from global memory when wcount stops before it
+    // the packed weights up to wcount elements go to shared memory; the hidden weights
+    // A_k transposed and A_k row-major (the last two blocks) are read from global memory
+    // when wcount stops before them
     const int wbytes = (wcount * (int)sizeof(T) + 15) / 16 * 16;
+    const T *at = (wcount > lay.At) ? sw + lay.At : gw + lay.At;
     const T *ar = (wcount >= lay.total) ? sw + lay.Ar : gw + lay.Ar;
     {
         const int n16 = wbytes / 16;
@@ -58,12 +60,12 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 384)
         if constexpr (SPATIAL) {
             // P and A of the point go to its slab, then are pushed forward to tau (P) and c (A)
             T *pa = qs + qp_stage_end(Cf::D, NF);
-            qp_group_update<T, NF, W>(sw, lay, ar, kc, qs, qi, jb, F, valid, pa, 1, A ? pa + 9 : nullptr, 1, nullptr, 0,
+            qp_group_update<T, NF, W>(sw, lay, at, ar, kc, qs, qi, jb, F, valid, pa, 1, A ? pa + 9 : nullptr, 1, nullptr, 0,
                                       psi_val, report);
             __syncwarp();
             push_forward_group<T>(qs + Stage<Cf::D, NF>::F, pa, pa + 9, jb, valid, P + qo, A ? A + qo : nullptr, n_qp);
         } else {
-            qp_group_update<T, NF, W>(sw, lay, ar, kc, qs, qi, jb, F, valid, P + qo, n_qp, A ? A + qo : nullptr, n_qp,
+            qp_group_update<T, NF, W>(sw, lay, at, ar, kc, qs, qi, jb, F, valid, P + qo, n_qp, A ? A + qo : nullptr, n_qp,
                                       dN_out ? dN_out + qo : nullptr, n_qp, psi_val, report);
         }
         if (valid && jb == 0) {
@@ -94,19 +96,25 @@ static int launch_typed(const commet_model *m, int64_t n_qp, const void *F, void
     int smem_max = 0;
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int max_threads = sizeof(T) == 8 ? 256 : 384;
-    // all weights in shared memory, unless leaving A_k row-major (the last block) in global
-    // memory lets more warps fit beside the point slabs
+    // all weights in shared memory, unless leaving A_k row-major, or both hidden blocks
+    // (A_k transposed and row-major, the last two), in global memory lets more warps fit
+    // beside the point slabs; FP64 warps are worth most in multiples of four, one per
+    // scheduler, each of which has its own share of the FP64 pipe
     auto fit = [&](size_t wb) -> int {
         return wb + per_warp > (size_t)smem_max
                    ? 0
                    : (int)std::min<size_t>((size_t)max_threads / 32, (smem_max - wb) / per_warp);
     };
-    const size_t wb_all = ((size_t)m->lay.total * sizeof(T) + 15) / 16 * 16;
-    const size_t wb_noar = ((size_t)m->lay.Ar * sizeof(T) + 15) / 16 * 16;
-    const bool ar_global = fit(wb_noar) > fit(wb_all);
-    const int wcount = ar_global ? m->lay.Ar : m->lay.total;
-    const size_t wbytes = ar_global ? wb_noar : wb_all;
-    const int warps = fit(wbytes);
+    int wcount = m->lay.total;
+    int warps = fit(((size_t)m->lay.total * sizeof(T) + 15) / 16 * 16);
+    for (const int wc : {m->lay.Ar, m->lay.At}) {
+        const int w = fit(((size_t)wc * sizeof(T) + 15) / 16 * 16);
+        if (w > warps) {
+            warps = w;
+            wcount = wc;
+        }
+    }
+    const size_t wbytes = ((size_t)wcount * sizeof(T) + 15) / 16 * 16;
     if (warps < 1) return COMMET_ERR_UNSUPPORTED;
     const size_t smem = wbytes + warps * per_warp;
     auto kern = const_update_kernel<T, NF, W, SPATIAL>;

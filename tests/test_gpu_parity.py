@@ -96,6 +96,10 @@ CASES = [
     # the narrow networks of the paper's model-size study (App. D)
     (wl.KIN_POLYCONVEX, 0, 4, 2, 0.0, False, False, 1001),
     (wl.KIN_ISO_SHIFTED, 0, 8, 4, 5.0, True, False, 2049),
+    # the widest, deepest networks of the study (W64 L4, the paper's largest): the hidden
+    # weights crowd the point slabs out of shared memory and are read from global memory
+    (wl.KIN_ISO_SHIFTED, 0, 64, 4, 3.0, True, False, 1537),
+    (wl.KIN_RAW, 2, 64, 4, 1.0, False, False, 1029),
 ]
 
 
