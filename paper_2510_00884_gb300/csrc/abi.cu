@@ -43,10 +43,16 @@ NetLayout make_layout(int d, int W, int L, bool with_tab) {
         l.tab = o;
         o = round4(o + actdf::kSlots);
     }
-    // the hidden weights come last, A_k transposed (forward values and tangents) and then
-    // A_k row-major (reverse pass): networks whose weights crowd the point slabs out of
-    // shared memory read one or both of these blocks from global memory (L1/L2) instead
+    // the hidden weights come last: A_k transposed (forward values and tangents), the
+    // FP64 layer-2 tangent weights M and A_k row-major (reverse pass); networks whose
+    // weights crowd the point slabs out of shared memory read the last one, two or three
+    // of these blocks from global memory (L1/L2) instead
     l.At = o; o = round4(o + (L - 1) * W * W);
+    l.M = 0;
+    if (with_tab && L >= 2) {
+        l.M = o;
+        o = round4(o + W * W * dp);
+    }
     l.Ar = o; o = round4(o + (L - 1) * W * W);
     l.total = o;
     return l;
@@ -357,6 +363,13 @@ int commet_model_create(const commet_model_desc *desc, int32_t precision, commet
         for (int j = 0; j < W; ++j) h[l.c + k * W + j] = desc->c ? desc->c[k * W + j] : 0.0;
     for (int j = 0; j < W; ++j) h[l.a + j] = desc->a_out[j];
     for (int mm = 0; mm < d; ++mm) h[l.b + mm] = desc->b_out[mm];
+    if (l.M > 0) {
+        // M[i][c][m] = A_2[c][i] W1[i][m] (rows of A_2 are the layer's output neurons)
+        for (int i = 0; i < W; ++i)
+            for (int c = 0; c < W; ++c)
+                for (int mm = 0; mm < d; ++mm)
+                    h[l.M + ((size_t)i * W + c) * dp + mm] = desc->A[(size_t)c * W + i] * desc->W1[i * d + mm];
+    }
     if (l.tab > 0) {
         // float-pair tables of the FP64 activation (act_df.cuh), one pair per 8-byte slot
         std::vector<actdf::f2> tab(actdf::kSlots);

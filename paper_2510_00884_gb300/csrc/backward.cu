@@ -295,15 +295,21 @@ __global__ void __launch_bounds__(WARPS * 32)
                   "bw_slab reserves the staged kinematics and BwPre");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sw = reinterpret_cast<T *>(smem_raw);
-    const int wcount = GACC ? lay.Ar : lay.total;  // A_k row-major is the last block
+    // the packed weights go to shared memory except the update's layer-2 tangent weights M
+    // (A_k row-major, the last block, moves down by its size) and, with GACC, A_k
+    // row-major, read from global memory
+    const int msz = lay.M ? lay.Ar - lay.M : 0;
+    const int wcount = (GACC ? lay.Ar : lay.total) - msz;
     const int wbytes = (wcount * (int)sizeof(T) + 15) / 16 * 16;
     {
         const int n16 = wbytes / 16;
+        const int cut16 = msz ? lay.M * (int)sizeof(T) / 16 : n16;
+        const int skip16 = msz * (int)sizeof(T) / 16;
         const int4 *src = reinterpret_cast<const int4 *>(gw);
         int4 *dst = reinterpret_cast<int4 *>(sw);
-        for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = src[i];
+        for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = src[i < cut16 ? i : i + skip16];
     }
-    const T *arw = GACC ? gw + lay.Ar : sw + lay.Ar;
+    const T *arw = GACC ? gw + lay.Ar : sw + lay.Ar - msz;
     // [np_pad] parameter-gradient accumulators: shared memory, or this CTA's workspace slice
     T *acc = GACC ? partial + (size_t)blockIdx.x * np_pad : sw + wbytes / (int)sizeof(T);
     T *slabs = GACC ? sw + wbytes / (int)sizeof(T) : acc + np_pad;
@@ -632,7 +638,8 @@ static int bw_launch(const commet_model *m, int64_t n_qp, const void *F, const v
     const BwSlab sl = bw_slab(D, W, m->L, NF, (int)sizeof(T));
     const int Q = WARPS * kQPW;
     const int np_pad = np_padded(m);
-    const size_t wbytes = ((size_t)(GACC ? m->lay.Ar : m->lay.total) * sizeof(T) + 15) / 16 * 16;
+    const int msz = m->lay.M ? m->lay.Ar - m->lay.M : 0;  // M is not used here (global memory)
+    const size_t wbytes = ((size_t)((GACC ? m->lay.Ar : m->lay.total) - msz) * sizeof(T) + 15) / 16 * 16;
     const size_t smem = wbytes + (GACC ? 0 : (size_t)np_pad * sizeof(T)) + (size_t)Q * sl.size * sizeof(T);
     int dev = 0, smem_max = 0;
     cudaGetDevice(&dev);

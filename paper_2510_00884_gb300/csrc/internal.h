@@ -23,9 +23,12 @@ struct NetLayout {
     int d, W, L;
     int W1t;  // [d][W]       W1 transposed (forward: contiguous over neurons)
     int W1r;  // [W][dp]      W1 row-major, rows padded to dp (tangent seed)
-    int At;   // [L-1][W][W]  A_k transposed: At[i][j] = A_k[j][i]
-    int Ar;   // [L-1][W][W]  A_k row-major (reverse pass); the last block
     int Bt;   // [L-1][d][W]  B_k transposed
+    int At;   // [L-1][W][W]  A_k transposed: At[i][j] = A_k[j][i]
+    int M;    // FP64 models with L >= 2: [W][W][dp] M[i][c][m] = A_2[c][i] W1[i][m], the first
+              // hidden tangent's weight product (the layer-2 tangent is then sum_i s_1[i] M[i]);
+              // 0 otherwise. At, M and Ar are the last three blocks, in this order
+    int Ar;   // [L-1][W][W]  A_k row-major (reverse pass); the last block
     int c;    // [L][W]
     int a;    // [W]
     int b;    // [d]

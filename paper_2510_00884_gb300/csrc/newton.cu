@@ -76,12 +76,17 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 384)
                   int32_t *__restrict__ status, int qstride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sw = reinterpret_cast<T *>(smem_raw);
-    const int wbytes = (lay.total * (int)sizeof(T) + 15) / 16 * 16;
+    // every packed block but the layer-2 tangent weights M goes to shared memory (this
+    // kernel folds s_1 into A_2 instead); A_k row-major, the last block, moves down by M
+    const int msz = lay.M ? lay.Ar - lay.M : 0;
+    const int wbytes = ((lay.total - msz) * (int)sizeof(T) + 15) / 16 * 16;
     {
         const int n16 = wbytes / 16;
+        const int cut16 = msz ? lay.M * (int)sizeof(T) / 16 : n16;
+        const int skip16 = msz * (int)sizeof(T) / 16;
         const int4 *src = reinterpret_cast<const int4 *>(gw);
         int4 *dst = reinterpret_cast<int4 *>(sw);
-        for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = src[i];
+        for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = src[i < cut16 ? i : i + skip16];
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -122,7 +127,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 384)
         T psi_val;
         bool report;
         T *pa = ea + kEPA + 90 * qi;
-        qp_group_update<T, NF, W>(sw, lay, sw + lay.At, sw + lay.Ar, kc, qs, qi, jb, F, true, pa, 1, pa + 9, 1, nullptr, 0, psi_val,
+        qp_group_update<T, NF, W>(sw, lay, nullptr, sw + lay.At, sw + lay.Ar - msz, kc, qs, qi, jb, F, true, pa, 1, pa + 9, 1, nullptr, 0, psi_val,
                                   report);
         if (report && jb == 0 && status != nullptr) {
             const int64_t q = 8 * e + qi;
@@ -202,7 +207,8 @@ static int newton_typed(const commet_model *m, const commet_mesh *mesh, const vo
     for (int f = 0; f < 2; ++f)
         for (int c = 0; c < 3; ++c) kc.fib[f][c] = (T)m->kp.fib[f][c];
     const int qstride = qp_slab_elems<T>(Cf::D, W, m->L, NF);
-    const size_t wbytes = ((size_t)m->lay.total * sizeof(T) + 15) / 16 * 16;
+    const int msz = m->lay.M ? m->lay.Ar - m->lay.M : 0;  // M stays in global memory (unused here)
+    const size_t wbytes = ((size_t)(m->lay.total - msz) * sizeof(T) + 15) / 16 * 16;
     const size_t per_warp = ((size_t)kQPW * qstride + (kEArea + 3) / 4 * 4) * sizeof(T);
     int dev = 0, smem_max = 0;
     cudaGetDevice(&dev);

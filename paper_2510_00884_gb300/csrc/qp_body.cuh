@@ -321,6 +321,8 @@ __device__ __forceinline__ void qp_group_finish(const T *n0s, const T *K0s, cons
 }
 
 // One point on its 4-lane group (all 32 lanes of the warp call this together).
+//  mt     the layer-2 tangent weights M (lay.M), in shared or global memory, or null: the
+//         layer-2 tangent then folds s_1 into A_2 (one multiply per neuron pair)
 //  at     the transposed A_k block (lay.At of the packed weights), in shared memory or,
 //         for networks too large for it, in global memory
 //  ar     the row-major A_k block (lay.Ar of the packed weights), in shared memory or,
@@ -334,8 +336,9 @@ __device__ __forceinline__ void qp_group_finish(const T *n0s, const T *K0s, cons
 //                      (J <= 0, non-finite input or result); valid in every lane
 template <typename T, int NF, int W>
 __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const NetLayout &lay,
-                                                const T *__restrict__ at, const T *__restrict__ ar,
-                                                const KinConst<T> &kc, T *qs, int qi, int jb, T (&F)[9],
+                                                const T *__restrict__ mt, const T *__restrict__ at,
+                                                const T *__restrict__ ar, const KinConst<T> &kc, T *qs, int qi,
+                                                int jb, T (&F)[9],
                                                 bool valid, T *Pq, int64_t pst, T *Aq, int64_t ast, T *dNq,
                                                 int64_t dst, T &psi_val, bool &report) {
     using Cf = CUConf<T, NF, W>;
@@ -522,7 +525,19 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
 #pragma unroll
                     for (int cc = 0; cc < NC; ++cc) acc[cc][m] = w[cc];
                 }
-                if (k == 2) {
+                if (k == 2 && mt != nullptr) {
+                    // J_2 = B_2 + sum_i s_1[i] M[i]: one multiply-add per entry
+#pragma unroll 2
+                    for (int i = 0; i < W; ++i) {
+                        const T s1 = sd[i];
+                        T mv[NC * DP];
+                        ldv<NC * DP>(mt + ((size_t)i * W + j0 + c0) * DP, mv);
+#pragma unroll
+                        for (int cc = 0; cc < NC; ++cc)
+#pragma unroll
+                            for (int m = 0; m < D; ++m) acc[cc][m] += s1 * mv[cc * DP + m];
+                    }
+                } else if (k == 2) {
 #pragma unroll 1
                     for (int i = 0; i < W; i += V) {
                         T s1[V];

@@ -30,10 +30,11 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 384)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sw = reinterpret_cast<T *>(smem_raw);
     // the packed weights up to wcount elements go to shared memory; the hidden weights
-    // A_k transposed and A_k row-major (the last two blocks) are read from global memory
-    // when wcount stops before them
+    // (the last blocks: A_k transposed, M, A_k row-major) are read from global memory when
+    // wcount stops before them
     const int wbytes = (wcount * (int)sizeof(T) + 15) / 16 * 16;
     const T *at = (wcount > lay.At) ? sw + lay.At : gw + lay.At;
+    const T *mt = (lay.M == 0) ? nullptr : ((wcount > lay.M) ? sw + lay.M : gw + lay.M);
     const T *ar = (wcount >= lay.total) ? sw + lay.Ar : gw + lay.Ar;
     {
         const int n16 = wbytes / 16;
@@ -60,12 +61,12 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 384)
         if constexpr (SPATIAL) {
             // P and A of the point go to its slab, then are pushed forward to tau (P) and c (A)
             T *pa = qs + qp_stage_end(Cf::D, NF);
-            qp_group_update<T, NF, W>(sw, lay, at, ar, kc, qs, qi, jb, F, valid, pa, 1, A ? pa + 9 : nullptr, 1, nullptr, 0,
+            qp_group_update<T, NF, W>(sw, lay, mt, at, ar, kc, qs, qi, jb, F, valid, pa, 1, A ? pa + 9 : nullptr, 1, nullptr, 0,
                                       psi_val, report);
             __syncwarp();
             push_forward_group<T>(qs + Stage<Cf::D, NF>::F, pa, pa + 9, jb, valid, P + qo, A ? A + qo : nullptr, n_qp);
         } else {
-            qp_group_update<T, NF, W>(sw, lay, at, ar, kc, qs, qi, jb, F, valid, P + qo, n_qp, A ? A + qo : nullptr, n_qp,
+            qp_group_update<T, NF, W>(sw, lay, mt, at, ar, kc, qs, qi, jb, F, valid, P + qo, n_qp, A ? A + qo : nullptr, n_qp,
                                       dN_out ? dN_out + qo : nullptr, n_qp, psi_val, report);
         }
         if (valid && jb == 0) {
@@ -96,8 +97,8 @@ static int launch_typed(const commet_model *m, int64_t n_qp, const void *F, void
     int smem_max = 0;
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int max_threads = sizeof(T) == 8 ? 256 : 384;
-    // all weights in shared memory, unless leaving A_k row-major, or both hidden blocks
-    // (A_k transposed and row-major, the last two), in global memory lets more warps fit
+    // all weights in shared memory, unless leaving A_k row-major, or the last two or three
+    // blocks (A_k transposed, M, A_k row-major), in global memory lets more warps fit
     // beside the point slabs; FP64 warps are worth most in multiples of four, one per
     // scheduler, each of which has its own share of the FP64 pipe
     auto fit = [&](size_t wb) -> int {
@@ -107,7 +108,7 @@ static int launch_typed(const commet_model *m, int64_t n_qp, const void *F, void
     };
     int wcount = m->lay.total;
     int warps = fit(((size_t)m->lay.total * sizeof(T) + 15) / 16 * 16);
-    for (const int wc : {m->lay.Ar, m->lay.At}) {
+    for (const int wc : {m->lay.Ar, m->lay.M > 0 ? m->lay.M : m->lay.Ar, m->lay.At}) {
         const int w = fit(((size_t)wc * sizeof(T) + 15) / 16 * 16);
         if (w > warps) {
             warps = w;
