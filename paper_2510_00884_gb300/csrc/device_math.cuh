@@ -68,7 +68,25 @@ __device__ __forceinline__ void act_tab(double y, double &z, double &s, double &
     actdf::softplus3(y, z, s, t, reinterpret_cast<const actdf::f2 *>(tab));
 }
 
-__device__ __forceinline__ double dev_rcbrt(double x) { return rcbrt(x); }
+// x^(-1/3) for x > 0: an FP32 seed 2^(-log2(x)/3) from the MUFU (relative error about
+// 2^-21) and two Newton steps y <- y + y (1 - x y^3)/3 in FP64 (2^-42, then rounding
+// level): 10 FP64 operations, where libm's rcbrt costs several times that on the FP64
+// pipe. Arguments outside [2^-126, 2^120) take libm's rcbrt.
+__device__ __forceinline__ double dev_rcbrt(double x) {
+    const int hi = __double2hiint(x);
+    if (hi < 0x38100000 || hi >= 0x47700000) return rcbrt(x);
+    // truncated FP32 copy of x (exponent rebiased from 1023 to 127); the seed converted to
+    // double exactly with integer operations
+    const float xf = __int_as_float((int)((unsigned)(hi - 0x38000000) << 3));
+    double y = actdf::f_to_d(__expf(-0.33333334f * __logf(xf)));
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const double y3 = y * y * y;
+        const double r = fma(-x, y3, 1.0);
+        y = fma(y * (1.0 / 3.0), r, y);
+    }
+    return y;
+}
 __device__ __forceinline__ float dev_rcbrt(float x) { return rcbrtf(x); }
 __device__ __forceinline__ bool dev_finite(double x) { return isfinite(x); }
 __device__ __forceinline__ bool dev_finite(float x) { return isfinite(x); }
@@ -250,7 +268,7 @@ __device__ __forceinline__ void stage_kinematics(const T *F, const KinConst<T> &
     const T I2 = T(0.5) * (I1 * I1 - trC2);
     const T r3 = dev_rcbrt(J);
     const T jm23 = r3 * r3, jm43 = jm23 * jm23;
-    const T iJ = T(1) / J;
+    const T iJ = jm23 * r3;  // 1/J = (J^(-1/3))^3
     const T p1 = T(-2) / T(3), p2 = T(-4) / T(3);
     const T c1 = c[0], c2 = c[1], c3 = c[2];
     const T k2 = T(2) * kc.kappa;
@@ -454,34 +472,64 @@ __device__ __forceinline__ void assemble_row(int a, const T *st, const T *Hs, co
 }
 
 
-// Entry (a, b) of A: the rank-one network part from the row vectors
-// u_a = sum_m g_m[a] d2N/dK_m dK (staged at ust[a * DP ...]) plus the structured part.
+// FP64 A assembly with the structured terms' scalars folded into per-point vectors, so
+// that each term of an entry is one fused multiply-add (GB300 bills every FP64 warp
+// instruction 16 SM clocks): lane4 writes components a = lane4, lane4 + 4, lane4 + 8 of
+//   V = U + (beta/2) H, G = gamma F, E = -eta H, Z = zeta F,
+//   XY[3i + J] = X[3J + J] + Y[3i + i]      (the two Kronecker terms of a diagonal entry)
+//   per fibre f: aA'_f = 2 c5f aA_f, Bm'_f = 2 c5f Bm
+// at pre[0, 9, 18, 27, 36] and pre[45 + 18 f], pre[54 + 18 f]. Then
+//   A_ab = d_ik d_JL XY + d_ik (1 - d_JL) X_JL + (1 - d_ik) d_JL Y_ik + u_a . g_b
+//        + V_a H_b + H_a V_b + G_a F_b + E_iL H_kJ + Z_iL F_kJ
+//        + sum_f (F_iL aA'_f,kJ + aA'_f,iL F_kJ + Bm'_f,ik AA_f,JL),
+// the same sum as assemble_entry with D + 5 + 3 NF FP64 operations instead of D + 12 + 4 NF.
+template <typename T, int NF>
+__device__ __forceinline__ void prescale_structured(const T *st, int lane4, T *pre) {
+    constexpr int D = 3 + 2 * NF;
+    using S = Stage<D, NF>;
+    const T hb = T(0.5) * st[S::sc + 0], gamma = st[S::sc + 1], meta = -st[S::sc + 2], zeta = st[S::sc + 3];
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        const int a = lane4 + 4 * t;
+        if (a < 9) {
+            const int i = a / 3, J_ = a - 3 * i;
+            const T Ha = st[S::H + a], Fa = st[S::F + a];
+            pre[a] = hb * Ha + st[S::U + a];
+            pre[9 + a] = gamma * Fa;
+            pre[18 + a] = meta * Ha;
+            pre[27 + a] = zeta * Fa;
+            pre[36 + a] = st[S::X + 4 * J_] + st[S::Y + 4 * i];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const T c5x2 = st[S::sc + 4 + f];
+                pre[45 + 18 * f + a] = c5x2 * st[S::aA + 9 * f + a];
+                pre[54 + 18 * f + a] = c5x2 * st[S::Bm + a];
+            }
+        }
+    }
+}
+
 template <typename T, int NF, int DP>
-__device__ __forceinline__ T assemble_entry(int a, int b, const T *st, const T *ust) {
+__device__ __forceinline__ T assemble_entry_pre(int a, int b, const T *st, const T *ust, const T *pre) {
     constexpr int D = 3 + 2 * NF;
     using S = Stage<D, NF>;
     const int i = a / 3, J_ = a - 3 * i, k = b / 3, L = b - 3 * k;
-    T s = T(0);
+    const int iL = 3 * i + L, kJ = 3 * k + J_;
+    T s = (i == k) ? ((J_ == L) ? pre[36 + a] : st[S::X + 3 * J_ + L]) : ((J_ == L) ? st[S::Y + 3 * i + k] : T(0));
 #pragma unroll
     for (int n = 0; n < D; ++n) s += ust[a * DP + n] * st[S::g + 9 * n + b];
-    const T Ha = st[S::H + a], Hb = st[S::H + b], Fa = st[S::F + a], Fb = st[S::F + b];
-    const T beta = st[S::sc + 0], gamma = st[S::sc + 1], eta = st[S::sc + 2], zeta = st[S::sc + 3];
-    // one fused multiply-add per product term
-    s += st[S::U + a] * Hb;
-    s += Ha * st[S::U + b];
-    s += (beta * Ha) * Hb;
-    s += (gamma * Fa) * Fb;
-    const T FiL = st[S::F + 3 * i + L], FkJ = st[S::F + 3 * k + J_];
-    s += (-eta * st[S::H + 3 * i + L]) * st[S::H + 3 * k + J_];
-    s += (zeta * FiL) * FkJ;
+    s += pre[a] * st[S::H + b];
+    s += st[S::H + a] * pre[b];
+    s += pre[9 + a] * st[S::F + b];
+    s += pre[18 + iL] * st[S::H + kJ];
+    const T FiL = st[S::F + iL], FkJ = st[S::F + kJ];
+    s += pre[27 + iL] * FkJ;
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-        const T c5x2 = st[S::sc + 4 + f];
-        s += c5x2 * (FiL * st[S::aA + 9 * f + 3 * k + J_] + st[S::aA + 9 * f + 3 * i + L] * FkJ +
-                     st[S::Bm + 3 * i + k] * st[S::AA + 9 * f + 3 * J_ + L]);
+        s += FiL * pre[45 + 18 * f + kJ];
+        s += pre[45 + 18 * f + iL] * FkJ;
+        s += pre[54 + 18 * f + 3 * i + k] * st[S::AA + 9 * f + 3 * J_ + L];
     }
-    s += (i == k) ? st[S::X + 3 * J_ + L] : T(0);
-    s += (J_ == L) ? st[S::Y + 3 * i + k] : T(0);
     return s;
 }
 

@@ -47,6 +47,11 @@ __host__ __device__ inline int qp_stage_end(int D, int NF) {
     return (9 * D + 54 + 18 * NF + 5 + NF + 3) / 4 * 4 + 9 * DP + D * DP;
 }
 
+// FP64 only: the per-point prescaled vectors of A's structured terms (see
+// prescale_structured), right after the staging area; in the spatial kernels the same
+// room later holds the point's P and A (every A entry is formed before any is stored).
+__host__ __device__ inline int qp_pre_elems(int NF) { return (45 + 18 * NF + 3) / 4 * 4; }
+
 // Per-qp slab size in elements of T for the given network (host and device agree);
 // with `spatial`, room for P and A after the staging area; `net` elements at least.
 template <typename T>
@@ -56,7 +61,9 @@ __host__ __device__ inline int qp_slab_elems(int D, int W, int L, int NF, bool s
     int work = 2 * W;
     if (nbuf * W * DP > work) work = nbuf * W * DP;
     int raw = 2 * L * W + work;
-    const int stage = qp_stage_end(D, NF) + (spatial ? 90 : 0);
+    int after = spatial ? 90 : 0;
+    if (sizeof(T) == 8 && qp_pre_elems(NF) > after) after = qp_pre_elems(NF);
+    const int stage = qp_stage_end(D, NF) + after;
     if (stage > raw) raw = stage;
     if (net > raw) raw = net;  // per-point network area of the non-MLP inner functions
     int words = raw * (int)sizeof(T) / 4;
@@ -270,6 +277,8 @@ __device__ __forceinline__ void qp_group_finish(const T *n0s, const T *K0s, cons
                     if (n < D) qs[UOFF + a * DP + n] = acc;
                 }
             }
+            T *pre = qs + qp_stage_end(D, NF);
+            prescale_structured<T, NF>(qs, jb, pre);
             __syncwarp();
 #pragma unroll
             for (int t = 0; t < 12; ++t) {
@@ -277,7 +286,7 @@ __device__ __forceinline__ void qp_group_finish(const T *n0s, const T *K0s, cons
                 if (e < 45) {
                     int a, b;
                     upper_index(e, a, b);
-                    Av[t] = assemble_entry<T, NF, DP>(a, b, qs, qs + UOFF);
+                    Av[t] = assemble_entry_pre<T, NF, DP>(a, b, qs, qs + UOFF, pre);
                 }
             }
         }
