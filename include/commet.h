@@ -325,6 +325,8 @@ int commet_norm2(const commet_mesh *mesh, int32_t precision, int64_t n, const vo
  *   dL_dF[:, q]   = sum_iJ G_iJ A_iJkL            (A of the forward at F_q)
  *   dL_dtheta[p]  = sum_q d/dtheta_p [ G_q : P_q ]  (all network parameters, order as
  *                   commet_model_n_params), summed over q in a fixed order
+ * For a CANN model (eq. cann-def) theta is its weights in the order of cann_w,
+ * [d][n][2] = (w1, w2) per input and term (App. C's calibration of the CANN).
  * Recomputes the forward per qp; stores no activations. dL_dF may be NULL.
  * workspace: device scratch of commet_const_backward_workspace() bytes, 256-byte aligned.
  * Deterministic: the same inputs give bitwise the same dL_dtheta.
@@ -332,7 +334,7 @@ int commet_norm2(const commet_mesh *mesh, int32_t precision, int64_t n, const vo
  * [n_params] is OVERWRITTEN (zeroed when n_qp = 0). A point with a non-finite F or G or
  * J <= 0 gets NaN in dL_dF and adds nothing to dL_dtheta.
  * Errors: INVALID_ARG (null, misaligned or short workspace); UNSUPPORTED for the bf16
- * precision, the closed-form and KAN inner functions, stress-free models (the shift n0
+ * precision, the Gent-Thomas and KAN inner functions, stress-free models (the shift n0
  * depends on theta), 64-wide networks with one fibre, and networks whose weights,
  * gradient accumulators and per-point slabs do not fit in shared memory even at half the
  * tile (64-wide with three or more layers). Nothing is launched when INVALID_ARG or
@@ -355,7 +357,8 @@ int commet_const_backward(const commet_model *m, int64_t n_qp, const void *F, co
  *    be serialised by the caller. Nothing in it needs to be zero before a call.
  *  - Returns COMMET_ERR_UNSUPPORTED, launching nothing, when the call would need more
  *    scratch than COMMET_NOALLOC_SCRATCH_BYTES (commet_const_backward_workspace() tells
- *    the need; FP64 d7 W32 L3 needs about 7 MB, W64 networks do not fit).
+ *    the need; FP64 d7 W32 L3 needs about 7 MB, W64 networks do not fit), and for models
+ *    other than the MICNN (the CANN's backward takes a workspace).
  *  - The looked-up address is kept per device ordinal for the life of the process. A
  *    device reset (cudaDeviceReset, or anything else that destroys the primary context)
  *    can move the array, so after one this entry point must not be called again until the

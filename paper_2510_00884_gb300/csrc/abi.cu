@@ -727,8 +727,10 @@ size_t commet_const_backward_workspace(const commet_model *m, int64_t n_qp) {
 
 int commet_const_backward(const commet_model *m, int64_t n_qp, const void *F, const void *dL_dP, void *dL_dF,
                           void *dL_dtheta, void *workspace, size_t ws_bytes, void *stream) {
-    if (m == nullptr || n_qp < 0 || dL_dtheta == nullptr) return COMMET_ERR_INVALID_ARG;
-    if (m->inner != COMMET_INNER_MICNN) return COMMET_ERR_UNSUPPORTED;
+    if (m == nullptr || n_qp < 0) return COMMET_ERR_INVALID_ARG;
+    // inner functions without a backward first: Gent-Thomas has no parameters (no dL_dtheta)
+    if (m->inner != COMMET_INNER_MICNN && m->inner != COMMET_INNER_CANN) return COMMET_ERR_UNSUPPORTED;
+    if (dL_dtheta == nullptr) return COMMET_ERR_INVALID_ARG;
     if (n_qp > 0 && (F == nullptr || dL_dP == nullptr)) return COMMET_ERR_INVALID_ARG;
     if (!aligned16(F) || !aligned16(dL_dP) || !aligned16(dL_dF) || !aligned16(dL_dtheta)) return COMMET_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return COMMET_ERR_INVALID_ARG;

@@ -28,6 +28,7 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "closed_form.cuh"
 #include "device_math.cuh"
 #include "internal.h"
 #include "qp_body.cuh"
@@ -615,8 +616,150 @@ static int bw_grid(const commet_model *m, int64_t n_qp, int Q) {
 static int64_t np_net(const commet_model *m) { return m->n_params_net > 0 ? m->n_params_net : m->n_params; }
 static int np_padded(const commet_model *m) { return (int)((np_net(m) + 3) / 4 * 4); }
 
+// Backward of the CANN (eq. cann-def), theta = its weights (w1, w2) per input m and term k:
+// with r_m = G : dK_m/dF (times phi'_m on the polyconvex layer, whose staged gradients are
+// those of the invariants),
+//   dL/dF = G : A,   dL/dw2_mk = sum_q r_m f2' f1' f0',   dL/dw1_mk = sum_q r_m w2 (d f2'/d w1) f1' f0'.
+// Per point (4 lanes, 8 points per warp) the forward of the closed-form update leaves P and
+// A in the point's slab; the lanes contract A with G by columns, then take the D n terms
+// round-robin. Each term's gradient is summed over the warp's 8 points by shuffles and
+// added to the warp's accumulators in shared memory (one lane per term); the CTA's sum over
+// its warps, in warp order, goes to the workspace, reduced over CTAs by reduce_partials_kernel.
+constexpr int kCannBwWarps = 8;
+
+template <typename T, int NF>
+__global__ void __launch_bounds__(kCannBwWarps * 32)
+    cann_backward_kernel(const T *__restrict__ gw, NetLayout lay, KinConst<T> kc, int64_t n_qp,
+                         const T *__restrict__ Fg, const T *__restrict__ Gg, T *__restrict__ dFg,
+                         T *__restrict__ partial, int np_pad, int qstride) {
+    constexpr int D = 3 + 2 * NF, NH = D * (D + 1) / 2;
+    using S = Stage<D, NF>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sw = reinterpret_cast<T *>(smem_raw);
+    const int wbytes = (lay.total * (int)sizeof(T) + 15) / 16 * 16;
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(gw);
+        int4 *dst = reinterpret_cast<int4 *>(sw);
+        for (int i = threadIdx.x; i < wbytes / 16; i += blockDim.x) dst[i] = src[i];
+    }
+    T *acc = sw + wbytes / (int)sizeof(T);  // [kCannBwWarps][np_pad]
+    T *slabs = acc + kCannBwWarps * np_pad;
+    for (int i = threadIdx.x; i < kCannBwWarps * np_pad; i += blockDim.x) acc[i] = T(0);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int qi = lane >> 2, jb = lane & 3;
+    T *qs = slabs + (size_t)(warp * kQPW + qi) * qstride;
+    T *wacc = acc + warp * np_pad;
+    const int n = lay.cn, nt = D * n;
+    const int64_t n_tiles = (n_qp + kQPW - 1) / kQPW;
+    const int64_t n_gwarps = (int64_t)gridDim.x * kCannBwWarps;
+
+    for (int64_t tile = (int64_t)blockIdx.x * kCannBwWarps + warp; tile < n_tiles; tile += n_gwarps) {
+        const int64_t q = tile * kQPW + qi;
+        const bool valid = q < n_qp;
+        T F[9], G[9];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+            F[c] = valid ? Fg[c * n_qp + q] : ((c % 4) == 0 ? T(1) : T(0));
+            G[c] = valid ? Gg[c * n_qp + q] : T(0);
+        }
+        T K[D], Jm1;
+        PolyChain<T> ch;
+        bool bad = !kin_scalars_k64<T, NF>(F, kc, K, Jm1, ch);
+#pragma unroll
+        for (int c = 0; c < 9; ++c) bad = bad || !dev_finite(G[c]);
+        if (bad) {
+#pragma unroll
+            for (int c = 0; c < 9; ++c) {
+                F[c] = (c % 4) == 0 ? T(1) : T(0);
+                G[c] = T(0);
+            }
+            kin_scalars_k64<T, NF>(F, kc, K, Jm1, ch);
+        }
+        T npart = T(0), dN[D], Hs[NH];
+#pragma unroll
+        for (int m = 0; m < D; ++m) dN[m] = T(0);
+#pragma unroll
+        for (int h = 0; h < NH; ++h) Hs[h] = T(0);
+        cann_point<T, D>(sw, lay, K, jb, npart, dN, Hs);
+        T *pa = qs + qp_stage_end(D, NF);  // the point's P (9) and A (81)
+        T psi_val;
+        bool report;
+        qp_group_finish<T, NF>(sw + lay.n0, sw + lay.K0, kc, qs, qi, jb, F, K, Jm1, ch, bad, valid, npart, dN, Hs,
+                               true, pa, 1, pa + 9, 1, nullptr, 0, psi_val, report);
+        __syncwarp();
+        // a point outside the energy's domain (reported by the forward) is treated as J <= 0
+        const bool drop = report || !valid;
+        // dL/dF by columns b = jb, jb + 4, jb + 8
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const int b = jb + kG * t;
+            if (b < 9) {
+                T v = T(0);
+#pragma unroll
+                for (int a = 0; a < 9; ++a) v += G[a] * pa[9 + 9 * a + b];
+                if (valid && dFg != nullptr) dFg[b * n_qp + q] = report ? T(NAN) : v;
+            }
+        }
+        // r_m = G : dK_m/dF from the staged kinematic gradients
+        T r[D];
+#pragma unroll
+        for (int m = 0; m < D; ++m) {
+            T v = T(0);
+#pragma unroll
+            for (int a = 0; a < 9; ++a) v += G[a] * qs[S::g + 9 * m + a];
+            r[m] = v;
+        }
+        if constexpr (NF == 0) {
+            if (kc.kin == COMMET_KIN_POLYCONVEX) {
+#pragma unroll
+                for (int m = 0; m < 3; ++m) r[m] *= ch.d1[m];
+            }
+        }
+        for (int t0 = 0; t0 < nt; t0 += kG) {
+            const int t = t0 + jb;
+            T g1 = T(0), g2 = T(0);
+            if (t < nt && !drop) {
+                const int m = t / n, k = t - m * n;
+                T x = T(0), rm = T(0);
+#pragma unroll
+                for (int mm = 0; mm < D; ++mm) {
+                    x = (mm == m) ? K[mm] : x;
+                    rm = (mm == m) ? r[mm] : rm;
+                }
+                cann_term_wgrad<T>(x, (int)sw[lay.ck + 3 * k], (int)sw[lay.ck + 3 * k + 1], (int)sw[lay.ck + 3 * k + 2],
+                                   sw[lay.cw + 2 * t], sw[lay.cw + 2 * t + 1], g1, g2);
+                g1 *= rm;
+                g2 *= rm;
+            }
+            // the same term over the warp's 8 points (lanes with the same jb)
+#pragma unroll
+            for (int msk = 4; msk <= 16; msk <<= 1) {
+                g1 += shfl_xor(g1, msk);
+                g2 += shfl_xor(g2, msk);
+            }
+            if (qi == 0 && t < nt) {
+                wacc[2 * t] += g1;
+                wacc[2 * t + 1] += g2;
+            }
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < np_pad; p += blockDim.x) {
+        T v = T(0);
+        for (int w = 0; w < kCannBwWarps; ++w) v += acc[w * np_pad + p];
+        partial[(size_t)blockIdx.x * np_pad + p] = v;
+    }
+}
+
 size_t backward_workspace_bytes(const commet_model *m, int64_t n_qp) {
     if (m->precision != COMMET_F64 && m->precision != COMMET_F32) return 0;
+    if (m->inner == COMMET_INNER_CANN) {
+        const size_t es = m->precision == COMMET_F64 ? 8 : 4;
+        const size_t bytes = (size_t)bw_grid(m, n_qp, kCannBwWarps * kQPW) * np_padded(m) * es;
+        return (bytes + 255) / 256 * 256;
+    }
     if (m->inner != COMMET_INNER_MICNN) return 0;
     const size_t es = m->precision == COMMET_F64 ? 8 : 4;
     // sized for the smallest tile any launch may use (the largest grid)
@@ -695,13 +838,58 @@ static int bw_dispatch(const commet_model *m, int64_t n_qp, const void *F, const
     return COMMET_ERR_UNSUPPORTED;
 }
 
+template <typename T, int NF>
+static int cann_bw_launch(const commet_model *m, int64_t n_qp, const void *F, const void *G, void *dF, void *dth,
+                          void *ws, cudaStream_t s) {
+    constexpr int D = 3 + 2 * NF;
+    KinConst<T> kc{};
+    kc.kin = m->kp.kin;
+    kc.stress_free = m->kp.stress_free;
+    kc.kappa = (T)m->kp.kappa;
+    for (int f = 0; f < 2; ++f)
+        for (int c = 0; c < 3; ++c) kc.fib[f][c] = (T)m->kp.fib[f][c];
+    const int qstride = qp_slab_elems<T>(D, 0, 0, NF, true);  // room for P and A after the staging
+    const int np_pad = np_padded(m);
+    const size_t wbytes = ((size_t)m->lay.total * sizeof(T) + 15) / 16 * 16;
+    const size_t smem = wbytes + (size_t)kCannBwWarps * np_pad * sizeof(T) +
+                        (size_t)kCannBwWarps * kQPW * qstride * sizeof(T);
+    int dev = 0, smem_max = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (smem > (size_t)smem_max) return COMMET_ERR_UNSUPPORTED;
+    auto kern = cann_backward_kernel<T, NF>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return COMMET_ERR_CUDA;
+    const int grid = bw_grid(m, n_qp, kCannBwWarps * kQPW);
+    kern<<<grid, kCannBwWarps * 32, smem, s>>>((const T *)m->d_weights, m->lay, kc, n_qp, (const T *)F, (const T *)G,
+                                                (T *)dF, (T *)ws, np_pad, qstride);
+    if (cudaGetLastError() != cudaSuccess) return COMMET_ERR_CUDA;
+    const int np = (int)np_net(m);
+    reduce_partials_kernel<T><<<(np + 255) / 256, 256, 0, s>>>((const T *)ws, grid, np, np_pad, (T *)dth, nullptr);
+    return cudaGetLastError() == cudaSuccess ? COMMET_OK : COMMET_ERR_CUDA;
+}
+
+template <typename T>
+static int cann_bw_dispatch(const commet_model *m, int64_t n_qp, const void *F, const void *G, void *dF, void *dth,
+                            void *ws, cudaStream_t s) {
+    if (m->kp.nf == 0) return cann_bw_launch<T, 0>(m, n_qp, F, G, dF, dth, ws, s);
+    if (m->kp.nf == 1) return cann_bw_launch<T, 1>(m, n_qp, F, G, dF, dth, ws, s);
+    if (m->kp.nf == 2) return cann_bw_launch<T, 2>(m, n_qp, F, G, dF, dth, ws, s);
+    return COMMET_ERR_UNSUPPORTED;
+}
+
 int launch_const_backward(const commet_model *m, int64_t n_qp, const void *F, const void *G, void *dF, void *dth,
                           void *ws, size_t ws_bytes, cudaStream_t s) {
     (void)ws_bytes;
-    if (m->inner != COMMET_INNER_MICNN) return COMMET_ERR_UNSUPPORTED;
+    if (m->inner != COMMET_INNER_MICNN && m->inner != COMMET_INNER_CANN) return COMMET_ERR_UNSUPPORTED;
     if (n_qp == 0) {
         const size_t es = m->precision == COMMET_F64 ? 8 : 4;
         return cudaMemsetAsync(dth, 0, es * m->n_params, s) == cudaSuccess ? COMMET_OK : COMMET_ERR_CUDA;
+    }
+    if (m->inner == COMMET_INNER_CANN) {
+        if (m->precision == COMMET_F64) return cann_bw_dispatch<double>(m, n_qp, F, G, dF, dth, ws, s);
+        if (m->precision == COMMET_F32) return cann_bw_dispatch<float>(m, n_qp, F, G, dF, dth, ws, s);
+        return COMMET_ERR_UNSUPPORTED;
     }
     if (m->precision == COMMET_F64) return bw_dispatch<double>(m, n_qp, F, G, dF, dth, ws, s);
     if (m->precision == COMMET_F32) return bw_dispatch<float>(m, n_qp, F, G, dF, dth, ws, s);

@@ -74,6 +74,69 @@ __device__ __forceinline__ void cann_term(T x, int f0, int p, int f2, T w1, T w2
     h = w2 * (fdd * yd * yd + fd * ydd) * ad * ad;
 }
 
+// Derivatives of one CANN term's dv/dx = w2 f2'(f1(f0(x)); w1) f1'(f0(x)) f0'(x) with
+// respect to its weights (the backward's parameter gradients): g2 = d/dw2 = f2' f1' f0',
+// g1 = d/dw1 = w2 (d f2'/d w1) f1' f0', with d f2'/d w1 = 1 (w1 y), exp(w1 y) (1 + w1 y)
+// (exp(w1 y) - 1) and 1/(1 - w1 y)^2 (-ln(1 - w1 y)).
+template <typename T>
+__device__ __forceinline__ void cann_term_wgrad(T x, int f0, int p, int f2, T w1, T w2, T &g1, T &g2) {
+    T a, ad;
+    if (f0 == COMMET_CANN_F0_MACAULAY) {
+        a = x > T(0) ? x : T(0);
+        ad = x > T(0) ? T(1) : (x < T(0) ? T(0) : T(0.5));
+    } else if (f0 == COMMET_CANN_F0_ABS) {
+        a = x < T(0) ? -x : x;
+        ad = x > T(0) ? T(1) : (x < T(0) ? T(-1) : T(0));
+    } else {
+        a = x;
+        ad = T(1);
+    }
+    const T y = p == 1 ? a : (p == 2 ? a * a : a * a * a);
+    const T yd = p == 1 ? T(1) : (p == 2 ? T(2) * a : T(3) * a * a);
+    T fd, fdw;
+    if (f2 == COMMET_CANN_F2_EXP) {
+        const T e = dev_exp(w1 * y);
+        fd = w1 * e;
+        fdw = e * (T(1) + w1 * y);
+    } else if (f2 == COMMET_CANN_F2_LOG) {
+        const T qi = T(1) / (T(1) - w1 * y);
+        fd = w1 * qi;
+        fdw = qi * qi;
+    } else {
+        fd = w1;
+        fdw = T(1);
+    }
+    const T c = yd * ad;
+    g2 = fd * c;
+    g1 = w2 * fdw * c;
+}
+
+// The CANN's N, dN/dK and diagonal Hessian at K for one point: the D n terms (input m,
+// term k) go round-robin over the point's 4 lanes, each lane holding partial sums.
+template <typename T, int D>
+__device__ __forceinline__ void cann_point(const T *sw, const NetLayout &lay, const T *K, int jb, T &npart, T *dN,
+                                           T *Hs) {
+    const int n = lay.cn, nt = D * n;
+    for (int t0 = 0; t0 < nt; t0 += kG) {
+        const int t = t0 + jb;
+        if (t < nt) {
+            const int m = t / n, k = t - m * n;
+            T x = T(0);
+#pragma unroll
+            for (int mm = 0; mm < D; ++mm) x = (mm == m) ? K[mm] : x;
+            T v, g, h;
+            cann_term<T>(x, (int)sw[lay.ck + 3 * k], (int)sw[lay.ck + 3 * k + 1], (int)sw[lay.ck + 3 * k + 2],
+                         sw[lay.cw + 2 * t], sw[lay.cw + 2 * t + 1], v, g, h);
+            npart += v;
+#pragma unroll
+            for (int mm = 0; mm < D; ++mm) {
+                dN[mm] += (mm == m) ? g : T(0);
+                Hs[mm * (mm + 1) / 2 + mm] += (mm == m) ? h : T(0);
+            }
+        }
+    }
+}
+
 // K in FP64 whatever T is. The CANN's polynomial terms make dN/dK proportional to K,
 // and a shifted invariant such as Ibar2 - 3 formed in FP32 carries an absolute error of
 // a few ulp(3) ~ 1e-6, a large relative error when K is small; with FP64 kinematic
@@ -291,26 +354,7 @@ __global__ void __launch_bounds__(256)
         if constexpr (INNER == COMMET_INNER_ICKAN) {
             kan_point<T, 3 + 2 * NF, KD>(sw, lay, K, qs, jb, npart, dN, Hs);
         } else if constexpr (INNER == COMMET_INNER_CANN) {
-            // the D n terms (input m, term k) go round-robin over the group's 4 lanes
-            const int n = lay.cn, nt = D * n;
-            for (int t0 = 0; t0 < nt; t0 += kG) {
-                const int t = t0 + jb;
-                if (t < nt) {
-                    const int m = t / n, k = t - m * n;
-                    T x = T(0);
-#pragma unroll
-                    for (int mm = 0; mm < D; ++mm) x = (mm == m) ? K[mm] : x;
-                    T v, g, h;
-                    cann_term<T>(x, (int)sw[lay.ck + 3 * k], (int)sw[lay.ck + 3 * k + 1], (int)sw[lay.ck + 3 * k + 2],
-                                 sw[lay.cw + 2 * t], sw[lay.cw + 2 * t + 1], v, g, h);
-                    npart += v;
-#pragma unroll
-                    for (int mm = 0; mm < D; ++mm) {
-                        dN[mm] += (mm == m) ? g : T(0);
-                        Hs[mm * (mm + 1) / 2 + mm] += (mm == m) ? h : T(0);
-                    }
-                }
-            }
+            cann_point<T, D>(sw, lay, K, jb, npart, dN, Hs);
         } else {
             // eq. gt on raw (Ibar1, Ibar2, J); J - 1 from det_minus_one
             if (jb == 0) {

@@ -112,8 +112,13 @@ def test_unsupported_paths(pkg):
     assert ei.value.code == _lib.ERR_UNSUPPORTED
     m = pkg.Model(spec, "f64")
     F = torch.eye(3, dtype=torch.float64).reshape(9, 1).repeat(1, 8).cuda().contiguous()
+    # the closed-form Gent-Thomas energy has no parameters to differentiate: no backward
     with pytest.raises(_lib.CommetError) as ei:
-        m.backward(F, torch.zeros_like(F))
+        pkg.Model(SPECS["gent_thomas"], "f64").backward(F, torch.zeros_like(F))
+    assert ei.value.code == _lib.ERR_UNSUPPORTED
+    # nor a stress-free CANN (its shift n0 depends on the weights)
+    with pytest.raises(_lib.CommetError) as ei:
+        pkg.Model(SPECS["cann_all_iso_shift"], "f64").backward(F, torch.zeros_like(F))
     assert ei.value.code == _lib.ERR_UNSUPPORTED
     mesh = wl.structured_mesh(1)
     gm = pkg.Mesh(mesh.X, mesh.conn, want_csr=True)
@@ -158,3 +163,73 @@ def test_full_size_sampled(pkg, name):
     idx = torch.from_numpy(qp).cuda()
     assert_close(cm_to_pm(P[:, idx]), P_r, 1e-12, f"{name} P")
     assert_close(cm_to_pm(A[:, idx]), A_r, 1e-12, f"{name} A")
+
+
+# ------------------------------------------------------------ backward of the CANN
+
+BW_SPECS = {
+    "cann_paper_poly": SPECS["cann_paper_poly"],
+    "cann_all_raw2": SPECS["cann_all_raw2"],
+    "cann_all_raw1": SPECS["cann_all_raw1"],
+    "cann_all_iso": dataclasses.replace(SPECS["cann_all_iso_shift"], stress_free=False),
+}
+
+
+def cann_backward_check(pkg, spec, F, G, prec, what):
+    """dL/dF per point at the path's tolerance; dL/dw per weight against the sum of the
+    per-point terms' magnitudes (a floating-point sum's bound), 1e-12 in FP64 and 1e-4 in
+    FP32, against the oracle on the same (rounded) inputs."""
+    m = pkg.Model(spec, prec)
+    Fd, Gd = pm_to_cm(F, DT[prec]), pm_to_cm(G, DT[prec])
+    dF, dth = m.backward(Fd, Gd)
+    dF2, dth2 = m.backward(Fd, Gd)
+    torch.cuda.synchronize()
+    assert torch.equal(dth, dth2) and torch.equal(dF, dF2), "backward not deterministic"
+    Fin, Gin = cm_to_pm(Fd).astype(np.float64), cm_to_pm(Gd).astype(np.float64)
+    dF_r, dth_r, dth_abs = oracle.const_backward(oracle.OracleModel(spec), Fin, Gin, want_abs=True)
+    assert dth.numel() == dth_r.size == 2 * spec.d * spec.n
+    assert_close(cm_to_pm(dF), dF_r, TOL[prec], f"{what} dL/dF")
+    e = np.abs(dth.cpu().numpy().astype(np.float64) - dth_r) / np.maximum(dth_abs, 1e-300)
+    assert e.max() < (1e-12 if prec == "f64" else 1e-4), f"{what} dL/dw {e.max():.3e}"
+    return dF, dth
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("name", list(BW_SPECS))
+@pytest.mark.parametrize("n", [3001, 9])
+def test_cann_backward_vs_oracle(pkg, name, prec, n):
+    """Backward of the CANN (eq. cann-def): dL/dF = G : A and dL/dw for every menu entry of
+    eq. cann-fs on the polyconvex, raw-with-fibres and shifted isochoric layers; 3001 points
+    span many CTA tiles with a ragged last one, 9 points one partial tile."""
+    rng = np.random.Generator(np.random.PCG64(620 + n))
+    F = wl.random_F(rng, n, 0.15)
+    G = rng.normal(size=F.shape)
+    cann_backward_check(pkg, BW_SPECS[name], F, G, prec, f"{name} {prec} n={n}")
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_cann_backward_edge_cases(pkg, prec):
+    """No points (dL/dw zeroed), one point, and a batch with one inadmissible point (J < 0):
+    NaN in its dL/dF, nothing from it in dL/dw (compared with the oracle on the others)."""
+    spec = BW_SPECS["cann_all_raw2"]
+    m = pkg.Model(spec, prec)
+    empty = torch.empty(9, 0, dtype=DT[prec], device="cuda")
+    dF0, dth0 = m.backward(empty, empty)
+    torch.cuda.synchronize()
+    assert dth0.numel() == 2 * spec.d * spec.n and bool((dth0 == 0).all())
+    rng = np.random.Generator(np.random.PCG64(631))
+    F1 = wl.random_F(rng, 1, 0.15)
+    cann_backward_check(pkg, spec, F1, rng.normal(size=F1.shape), prec, f"one point {prec}")
+    F = wl.random_F(rng, 77, 0.15)
+    G = rng.normal(size=F.shape)
+    F[5] = np.diag([-1.0, 1.0, 1.0]).ravel()  # J = -1
+    dF, dth = m.backward(pm_to_cm(F, DT[prec]), pm_to_cm(G, DT[prec]))
+    torch.cuda.synchronize()
+    dFh = cm_to_pm(dF)
+    assert np.isnan(dFh[5]).all() and np.isfinite(np.delete(dFh, 5, axis=0)).all()
+    keep = np.delete(np.arange(77), 5)
+    Fin = cm_to_pm(pm_to_cm(F, DT[prec])).astype(np.float64)[keep]
+    Gin = cm_to_pm(pm_to_cm(G, DT[prec])).astype(np.float64)[keep]
+    _, dth_r, dth_abs = oracle.const_backward(oracle.OracleModel(spec), Fin, Gin, want_abs=True)
+    e = np.abs(dth.cpu().numpy().astype(np.float64) - dth_r) / np.maximum(dth_abs, 1e-300)
+    assert e.max() < (1e-12 if prec == "f64" else 1e-4), e.max()
