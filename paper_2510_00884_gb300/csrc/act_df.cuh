@@ -3,19 +3,19 @@
 // GB300 executes FP64 at 1/63 of the FP32 rate and bills each warp-level FP64
 // instruction 16 SM clocks, while an FP64-bound kernel leaves most of its issue slots
 // and the FP32/integer pipes idle. So the activation of the FP64 path keeps only the
-// argument reduction (two FP64 FMAs) and the final rounding of each output to double
-// (one FP64 add per output) on the FP64 pipe; everything else runs in double-float
-// arithmetic: an unevaluated sum hi + lo of two FP32 numbers, about 48 significant
-// bits (T. J. Dekker, Numer. Math. 18, 1971: the exact sum and product transforms used
-// below; the product's error term comes from one FP32 FMA).
+// final rounding of each output to double (one FP64 add per output, four per neuron) on
+// the FP64 pipe; everything else runs in double-float arithmetic: an unevaluated sum
+// hi + lo of two FP32 numbers, about 48 significant bits (T. J. Dekker, Numer. Math. 18,
+// 1971, and D. E. Knuth, TAOCP vol. 2: the exact sum and product transforms used below;
+// the product's error term comes from one FP32 FMA).
 //
 // With x = -|y| (clamped at -700) and e = exp(x):
 //   z  = max(y, 0) + log1p(e)
 //   s  = z'  = 1/(1+e) for y >= 0, e/(1+e) for y < 0
 //   t  = z'' = e/(1+e)^2
 // Steps (table-driven, after P. T. P. Tang, ACM TOMS 15(2) 1989 and 16(4) 1990):
-//   x = (128 m + j) ln2/128 + r, |r| <= ln2/256 (k = 128 m + j from an FP32 product,
-//       r by two FP64 FMAs against a split ln2/128),
+//   x = (128 m + j) ln2/128 + r, |r| <= ln2/256 (k = 128 m + j from an FP32 product;
+//       r from |y| cut exactly into three floats and ln2/128 split in three, k C1 exact),
 //   e = 2^m * T_j * (1 + expm1(r)), T_j = 2^(j/128) as a float pair, expm1 to degree 5;
 //   k' = round(256 e), F = 1 + k'/256, rr = (e - k'/256)/F (the difference is exact),
 //   log1p(e) = log F + log1p(rr),  1/(1+e) = (1/F) / (1 + rr),  |rr| <= 1/512,
@@ -130,25 +130,11 @@ ACTDF_FN double hilo(int32_t hi, int32_t lo) {
     return d;
 #endif
 }
-ACTDF_FN int clz32(uint32_t x) {
-#if defined(__CUDA_ARCH__)
-    return __clz((int)x);
-#else
-    return x ? __builtin_clz(x) : 32;
-#endif
-}
 ACTDF_FN double dadd(double a, double b) {
 #if defined(__CUDA_ARCH__)
     return __dadd_rn(a, b);
 #else
     return a + b;
-#endif
-}
-ACTDF_FN double dfma(double a, double b, double c) {
-#if defined(__CUDA_ARCH__)
-    return __fma_rn(a, b, c);
-#else
-    return std::fma(a, b, c);
 #endif
 }
 
@@ -178,21 +164,18 @@ ACTDF_FN double f_to_d(float f) {
 // round hi + lo to double: the one FP64 operation per output
 ACTDF_FN double df_to_d(f2 a) { return dadd(f_to_d(a.h), f_to_d(a.l)); }
 
-// -(double)n for 0 <= n < 2^31, exactly, with integer operations
-ACTDF_FN double neg_int_to_d(int32_t n) {
-    const uint32_t u = (uint32_t)n;
-    const int lz = clz32(u);
-    const uint32_t mant = (lz < 31) ? (u << (lz + 1)) : 0u;  // fraction bits after the leading one
-    const int32_t hi = (int32_t)(0x80000000u | ((uint32_t)(1023 + 31 - lz) << 20) | (mant >> 12));
-    const int32_t lo = (int32_t)(mant << 20);
-    return (u == 0u) ? 0.0 : hilo(hi, lo);
+// s + e = a + b exactly, any order of magnitude (Knuth)
+ACTDF_FN f2 two_sum(float a, float b) {
+    const float s = fadd(a, b);
+    const float bb = fsub(s, a);
+    return {s, fadd(fsub(a, fsub(s, bb)), fsub(b, bb))};
 }
 
-// split ln2/128 = C1 + C2: C1 with 29 significant bits (k * C1 exact for |k| < 2^24),
-// C2 the rest rounded to double (their sum is within 1e-29 of ln2/128); 128/ln2 for the
-// FP32 product that picks k
-constexpr double kC1 = 0x1.62e42ffp-8;
-constexpr double kC2 = -0x1.718432a1b0e26p-42;
+// ln2/128 = C1 + C2 + C3 + O(1e-20): C1 with 7 significant bits (k C1 exact in FP32 for
+// k < 2^17, all k here), C2 and C3 floats; 128/ln2 for the FP32 product that picks k
+constexpr float kC1 = 0x1.64p-8f;
+constexpr float kC2 = -0x1.1bd01p-16f;
+constexpr float kC3 = -0x1.718432p-42f;
 constexpr float kInvC = 0x1.715476p+7f;
 constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: adding it rounds to an integer in the low bits
 
@@ -206,31 +189,29 @@ ACTDF_FN void softplus3(double y, double &z, double &s, double &t, const f2 *tab
         aH = 0x4085E000;
         aL = 0;
     }
-    const double x = hilo(aH | (int32_t)0x80000000, aL);  // -|y|
-    // k = round(x * 128/ln2) from a truncated FP32 copy of |y| (0 below 2^-126)
-    const float af = (aH >= 0x38100000) ? i_as_f((int32_t)((uint32_t)(aH - 0x38000000) << 3)) : 0.0f;
-    const float kf = ffma(-af, kInvC, kMagic);
-    const int32_t k = f_as_i(kf) - 0x4B400000;  // k <= 0
-    const double kd = neg_int_to_d(-k);
-    double r = dfma(kd, -kC1, x);  // exact: k * C1 is exact and r1 is near x
-    r = dfma(kd, -kC2, r);
+    // |y| = a1 + a2 + a3 exactly: its 53-bit mantissa cut into 24, 23 and 6 bits, each an
+    // exact float (built with integer operations; a part below 2^-126 is zero, which
+    // changes r by less than 2^-100)
+    const int32_t E = aH >> 20;
+    const float a1 = (E >= 897) ? i_as_f((int32_t)(((uint32_t)(aH - 0x38000000) << 3) | ((uint32_t)aL >> 29))) : 0.0f;
+    const float a2 = (E >= 943) ? fmul(fsub(i_as_f(0x4B000000 | (int32_t)(((uint32_t)aL >> 6) & 0x7fffffu)), 8388608.0f),
+                                       i_as_f((E - 942) << 23))
+                                : 0.0f;
+    const float a3 = (E >= 949) ? fmul(fsub(i_as_f(0x4B000000 | (aL & 63)), 8388608.0f), i_as_f((E - 948) << 23)) : 0.0f;
+    // kn = round(|y| 128/ln2) >= 0 and r = kn ln2/128 - |y|, so that -|y| = k ln2/128 + r
+    // with k = -kn: kn C1 - a1 is exact, kn C2 exact as a float pair, the sums exact up to
+    // the last one (|r| <= ln2/256 + 2^-14, about 2^-50 absolute in the end)
+    const float knm = ffma(a1, kInvC, kMagic);
+    const int32_t k = 0x4B400000 - f_as_i(knm);  // k = -kn <= 0
+    const float knf = fsub(knm, kMagic);
+    const float t1 = ffma(knf, kC1, -a1);
+    const float ph = fmul(knf, kC2), pe = ffma(knf, kC2, -ph);
+    const f2 u1 = two_sum(t1, ph);
+    const f2 u2 = two_sum(u1.h, -a2);
+    const float rest = fsub(fadd(fadd(fadd(u1.l, u2.l), pe), fmul(knf, kC3)), a3);
+    const f2 rr2 = fast_two_sum(u2.h, rest);
     const int32_t j = k & (kExpN - 1);
     const int32_t m = k >> 7;
-    // r as a float pair by truncating its mantissa (r = 0 and |r| < 2^-60 give 0)
-    f2 rr2{0.0f, 0.0f};
-    {
-        const int32_t rH = d_hi(r), rL = d_lo(r);
-        const int32_t E = (rH >> 20) & 0x7ff;
-        if (E >= 1023 - 60) {
-            const int32_t sg = rH & (int32_t)0x80000000;
-            const uint32_t top = ((uint32_t)((rH & 0x7fffffff) - 0x38000000) << 3) | ((uint32_t)rL >> 29);
-            const float hi = i_as_f((int32_t)top | sg);
-            const uint32_t n23 = ((uint32_t)rL >> 6) & 0x7fffffu;
-            float lo = fmul(fsub(i_as_f(0x4B000000 | (int32_t)n23), 8388608.0f), i_as_f((E - 942) << 23));
-            lo = sg ? -lo : lo;
-            rr2 = {hi, lo};
-        }
-    }
     const float rh = rr2.h, rl = rr2.l;
     // expm1(r) = r + r^2/2 + r^3/6 + r^4/24 + r^5/120
     const float sqh = fmul(rh, rh);
