@@ -257,8 +257,7 @@ __device__ __forceinline__ void stage_kinematics(const T *F, const KinConst<T> &
                                                  T *st) {
     constexpr int D = 3 + 2 * NF;
     using S = Stage<D, NF>;
-    T cof[9], Jc, C[9];
-    cof_det(F, cof, Jc);
+    T C[9];
     right_cg(F, C);
     const T J = T(1) + Jm1;
     const T I1 = C[0] + C[4] + C[8];
@@ -290,12 +289,16 @@ __device__ __forceinline__ void stage_kinematics(const T *F, const KinConst<T> &
         const int a = lane4 + 4 * t;
         if (a < 9) {
             const int p = a / 3, q = a - 3 * p;  // a = 3 p + q
-            const T Fa = F[a], Ha = cof[a] * iJ;
+            // this lane's cofactor entry only (the lanes share one instruction stream)
+            const int pa1 = p == 2 ? 0 : p + 1, pa2 = p == 0 ? 2 : p - 1;
+            const int qa1 = q == 2 ? 0 : q + 1, qa2 = q == 0 ? 2 : q - 1;
+            const T cofa = F[3 * pa1 + qa1] * F[3 * pa2 + qa2] - F[3 * pa1 + qa2] * F[3 * pa2 + qa1];
+            const T Fa = F[a], Ha = cofa * iJ;
             const T FC = F[3 * p] * C[q] + F[3 * p + 1] * C[3 + q] + F[3 * p + 2] * C[6 + q];
             const T gI2 = T(2) * (I1 * Fa - FC);  // raw dI2/dF = 2 (I1 F - F C)
             st[S::g + a] = jm23 * (T(2) * Fa + p1 * I1 * Ha);
             st[S::g + 9 + a] = jm43 * (gI2 + p2 * I2 * Ha);
-            st[S::g + 18 + a] = cof[a];
+            st[S::g + 18 + a] = cofa;
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
                 const T *A0 = kc.fib[f];
