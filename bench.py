@@ -77,6 +77,9 @@ def backward_flops_per_qp(d: int, W: int, L: int) -> int:
 # of K_e, A contracted with the node's gradient (9 entries x 3) and then with every
 # column's gradient (24 entries x 3), plus 3 for f_e: 24 x (27 + 72 + 3) per point, 8 points.
 ELEM_MACS = 8 * 24 * (27 + 72 + 3)
+# With a major-symmetric A (the update's own tangent), the upper node blocks only: per
+# point the 24 rows' A contraction and f (27 + 3) and the 36 upper 3 x 3 blocks (27 each).
+ELEM_MACS_SYM = 8 * (24 * (27 + 3) + 36 * 27)
 PUSH_FORWARD_MACS = 21 * 15 + 6 * 3  # per point: c = F A F - delta tau (21 entries), tau = P F^T (6)
 
 
@@ -402,7 +405,7 @@ class Run:
                         self.F, self.P, self.A, mp, out=(self.f_e, self.K_e, None, None))))
                 else:
                     self.phases.append(("elem_assemble_kernel", lambda: self.gmesh.elem_assemble(
-                        self.P, self.A, mp, out=(self.f_e, self.K_e, None, None))))
+                        self.P, self.A, mp, out=(self.f_e, self.K_e, None, None), symmetric=True)))
             else:
                 self.n_el = 0
             self.input_dev = {"F": self.F}
@@ -425,7 +428,7 @@ class Run:
                            ("const_update_kernel",
                             lambda: self.model.const_update(self.Fb, out=(self.psi, self.P, self.A))),
                            ("elem_assemble_kernel", lambda: self.gmesh.elem_assemble(
-                               self.P, self.A, mp, out=(self.f_e, self.K_e, None, None)))]
+                               self.P, self.A, mp, out=(self.f_e, self.K_e, None, None), symmetric=True))]
             self.input_dev = {"u": self.u}
         elif name == "c3":
             F_host = np.ascontiguousarray(w["F"].T)
@@ -543,7 +546,7 @@ def fp64_unfused_baseline(run, pkg, torch, dev, reps=2):
     def once():
         run.gmesh.compute_F(u, "f64", out=F)
         m64.const_update(F, want_psi=False, out=(None, P, A))
-        run.gmesh.elem_assemble(P, A, "f64", want_f=False, want_K=False, out=(None, None, r, Kv))
+        run.gmesh.elem_assemble(P, A, "f64", want_f=False, want_K=False, out=(None, None, r, Kv), symmetric=True)
     once()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -771,7 +774,9 @@ def run_ours(args, rank, world, local_rank):
         flops = (algorithmic_flops_per_qp(spec.d, sW, sL) * 8 + 2 * ELEM_MACS) * run.n_el
         units, src = run.n_el, ["newton.cu", "qp_body.cuh", "device_math.cuh"]
     else:
-        flops = 2 * ELEM_MACS * run.n_el
+        # the FP64 material form runs the symmetric element kernel (the update's own tangent)
+        sym = kname == "elem_assemble_kernel" and prec == "f64"
+        flops = 2 * (ELEM_MACS_SYM if sym else ELEM_MACS) * run.n_el
         units, src = run.n_el, ["spatial.cu" if kname == "elem_spatial_kernel" else "elem.cu", "hex8.cuh"]
     peak, peak_source = alu_peak(alu, n_sm, mhz)
     bound = "alu"
@@ -835,7 +840,8 @@ def run_ours(args, rank, world, local_rank):
         roofline["elem_kernel"] = {"kernel": ek, "ms": el_ms, "bytes_per_el": (8 * per_qp + 600) * es,
                                    "achieved_gbs": run.n_el * (8 * per_qp + 600) * es / (el_ms * 1e-3) / 1e9,
                                    "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)),
-                                   "achieved_tflops": run.n_el * 2 * ELEM_MACS / (el_ms * 1e-3) / 1e12}
+                                   "achieved_tflops": run.n_el * 2 * (ELEM_MACS if args.spatial or prec != "f64"
+                                                                      else ELEM_MACS_SYM) / (el_ms * 1e-3) / 1e12}
 
     cpu = None
     errors = None

@@ -168,7 +168,9 @@ int commet_const_update(const commet_model *m, int64_t n_qp, const void *F, void
  * (F [9][n_qp], psi [n_qp], P [9][n_qp], A [81][n_qp], f_e [24][n_el], K_e [576][n_el]),
  * page-locked for the copies to overlap; psi, A, f_e, K_e may be NULL (K_e only with A).
  * Element type: double for a COMMET_F64 model, float otherwise.
- * mesh: NULL (update only; f_e and K_e must be NULL) or a mesh with 8 n_el = n_qp.
+ * mesh: NULL (update only; f_e and K_e must be NULL) or a mesh with 8 n_el = n_qp. The
+ * element integrals are those of commet_elem_assemble_symmetric: A is the update's own
+ * tangent, the Hessian of an energy, so major symmetric.
  * workspace: device memory of commet_const_update_host_workspace(m, mesh, chunk, A != NULL)
  * bytes, 256-byte aligned, owned by the caller and not used by anything else until the
  * call has completed on `stream`.
@@ -242,6 +244,19 @@ int commet_compute_F(const commet_mesh *mesh, int32_t precision, const void *u, 
  */
 int commet_elem_assemble(const commet_mesh *mesh, int32_t precision, const void *P, const void *A, void *f_e,
                          void *K_e, void *r, void *K_vals, void *stream);
+
+/*
+ * The same element integrals for a major-symmetric A (A_iJkL = A_kLiJ: the tangent of every
+ * hyperelastic energy, eq. nncm-chain, and so every A that commet_const_update writes).
+ * K_e is then symmetric, and it is formed from its upper node blocks (36 of 64, each node
+ * pair once) and written whole, its other blocks as transposes: in FP64 about a quarter
+ * fewer multiply-adds. The result for a non-symmetric A is K_e of its symmetrised upper
+ * blocks, not eq. k-quad: call commet_elem_assemble for such an A. Arguments, outputs,
+ * scatter and errors as commet_elem_assemble; the FP32 form without scatter is the same
+ * kernel as there (bound by memory, not by arithmetic).
+ */
+int commet_elem_assemble_symmetric(const commet_mesh *mesh, int32_t precision, const void *P, const void *A,
+                                   void *f_e, void *K_e, void *r, void *K_vals, void *stream);
 
 /*
  * Element integrals in the spatial form of eq. r-quad and k-quad:

@@ -20,7 +20,8 @@ EXPORTED = [
     "commet_model_create", "commet_model_destroy", "commet_model_n_params", "commet_const_update",
     "commet_const_update_spatial", "commet_elem_assemble_spatial",
     "commet_mesh_create", "commet_mesh_destroy", "commet_mesh_info", "commet_mesh_csr", "commet_compute_F",
-    "commet_elem_assemble", "commet_newton_assemble", "commet_const_backward_workspace",
+    "commet_elem_assemble", "commet_elem_assemble_symmetric", "commet_newton_assemble",
+    "commet_const_backward_workspace",
     "commet_const_backward", "commet_target_stress", "commet_status_string", "commet_const_backward_noalloc",
     "commet_mesh_set_dirichlet", "commet_set_dirichlet_values", "commet_apply_dirichlet", "commet_cg_workspace",
     "commet_cg_solve", "commet_add_increment", "commet_norm2", "commet_residual_adjoint", "commet_compute_F_adjoint",
@@ -74,6 +75,7 @@ def load() -> C.CDLL:
         "commet_mesh_csr": ([vp, C.POINTER(i64), C.POINTER(i32)], C.c_int),
         "commet_compute_F": ([vp, i32, vp, vp, vp], C.c_int),
         "commet_elem_assemble": ([vp, i32, vp, vp, vp, vp, vp, vp, vp], C.c_int),
+        "commet_elem_assemble_symmetric": ([vp, i32, vp, vp, vp, vp, vp, vp, vp], C.c_int),
         "commet_const_update_spatial": ([vp, i64, vp, vp, vp, vp, vp, vp], C.c_int),
         "commet_elem_assemble_spatial": ([vp, i32, vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
         "commet_newton_assemble": ([vp, vp, vp, vp, vp, vp, vp], C.c_int),

@@ -252,8 +252,9 @@ class Mesh:
 
     def elem_assemble(self, P: torch.Tensor, A: torch.Tensor | None, precision: str = "f64",
                       want_f: bool = True, want_K: bool = True, want_r: bool = False, want_Kcsr: bool = False,
-                      out=None):
-        """(f_e[24, n_el], K_e[576, n_el], r[3 n_nodes], K_vals[nnz]); entries not wanted are None."""
+                      out=None, symmetric: bool = False):
+        """(f_e[24, n_el], K_e[576, n_el], r[3 n_nodes], K_vals[nnz]); entries not wanted are None.
+        ``symmetric``: A is major symmetric (the update's own tangent), K_e from its upper blocks."""
         dt = _DTYPE[precision]
         n_qp = 8 * self.n_el
         _check_dev(P, dt, shape=(9, n_qp), name="P")
@@ -267,7 +268,8 @@ class Mesh:
             Kv = torch.empty(self.nnz, dtype=dt, device=dev) if want_Kcsr else None
         else:
             f_e, K_e, r, Kv = out
-        _lib.check("commet_elem_assemble", _lib.load().commet_elem_assemble(
+        name = "commet_elem_assemble_symmetric" if symmetric else "commet_elem_assemble"
+        _lib.check(name, getattr(_lib.load(), name)(
             self.handle, _PREC[precision], _ptr(P), _ptr(A), _ptr(f_e), _ptr(K_e), _ptr(r), _ptr(Kv), _stream()))
         return f_e, K_e, r, Kv
 
@@ -400,7 +402,7 @@ class Assembler:
             g.compute_F(u, m.precision, out=self.F)
             m.const_update(self.F, out=(self.psi, self.P, self.A))
             g.elem_assemble(self.P, self.A, m.precision, want_f=False, want_K=False, want_r=True, want_Kcsr=True,
-                            out=(None, None, self.r, self.Kv))
+                            out=(None, None, self.r, self.Kv), symmetric=True)  # the update's own tangent
         return self.r, self.Kv
 
 

@@ -676,6 +676,19 @@ int commet_elem_assemble(const commet_mesh *mesh, int32_t precision, const void 
                                 reinterpret_cast<cudaStream_t>(stream));
 }
 
+int commet_elem_assemble_symmetric(const commet_mesh *mesh, int32_t precision, const void *P, const void *A,
+                                   void *f_e, void *K_e, void *r, void *K_vals, void *stream) {
+    if (mesh == nullptr || (precision != COMMET_F64 && precision != COMMET_F32 && precision != COMMET_BF16_MLP))
+        return COMMET_ERR_INVALID_ARG;
+    if (mesh->n_el > 0 && P == nullptr) return COMMET_ERR_INVALID_ARG;
+    if (A == nullptr && (K_e != nullptr || K_vals != nullptr)) return COMMET_ERR_INVALID_ARG;
+    if ((r != nullptr || K_vals != nullptr) && mesh->h_rowptr == nullptr) return COMMET_ERR_NO_CSR;
+    if (!aligned16(P) || !aligned16(A) || !aligned16(f_e) || !aligned16(K_e) || !aligned16(r) || !aligned16(K_vals))
+        return COMMET_ERR_INVALID_ARG;
+    return launch_elem_assemble(mesh, precision == COMMET_F64 ? COMMET_F64 : COMMET_F32, P, A, f_e, K_e, r, K_vals,
+                                reinterpret_cast<cudaStream_t>(stream), true);
+}
+
 int commet_elem_assemble_spatial(const commet_mesh *mesh, int32_t precision, const void *F, const void *tau,
                                  const void *c, void *f_e, void *K_e, void *r, void *K_vals, void *stream) {
     if (mesh == nullptr || (precision != COMMET_F64 && precision != COMMET_F32 && precision != COMMET_BF16_MLP))

@@ -121,6 +121,19 @@ __device__ __forceinline__ void right_cg(const T *F, T *C) {
         }
 }
 
+// I2 = (tr^2 C - tr C^2)/2 as the sum of the principal 2x2 minors of the symmetric C:
+// six operations instead of eleven
+template <typename T>
+__device__ __forceinline__ T second_invariant(const T *C) {
+    T s = C[0] * C[4];
+    s += C[0] * C[8];
+    s += C[4] * C[8];
+    s -= C[1] * C[1];
+    s -= C[2] * C[2];
+    s -= C[5] * C[5];
+    return s;
+}
+
 // B = F F^T (full 3x3)
 template <typename T>
 __device__ __forceinline__ void left_cg(const T *F, T *B) {
@@ -201,10 +214,7 @@ __device__ __forceinline__ bool kin_scalars(const T *F, const KinConst<T> &kc, T
     T C[9];
     right_cg(F, C);
     const T I1 = C[0] + C[4] + C[8];
-    T trC2 = 0;
-#pragma unroll
-    for (int a = 0; a < 9; ++a) trC2 += C[a] * C[a];
-    const T I2 = T(0.5) * (I1 * I1 - trC2);
+    const T I2 = second_invariant(C);
     const bool ok = (J > T(0)) && dev_finite(Jm1) && dev_finite(I1);
     const T r3 = dev_rcbrt(ok ? J : T(1));
     const T jm23 = r3 * r3;
@@ -261,10 +271,7 @@ __device__ __forceinline__ void stage_kinematics(const T *F, const KinConst<T> &
     right_cg(F, C);
     const T J = T(1) + Jm1;
     const T I1 = C[0] + C[4] + C[8];
-    T trC2 = 0;
-#pragma unroll
-    for (int a = 0; a < 9; ++a) trC2 += C[a] * C[a];
-    const T I2 = T(0.5) * (I1 * I1 - trC2);
+    const T I2 = second_invariant(C);
     const T r3 = dev_rcbrt(J);
     const T jm23 = r3 * r3, jm43 = jm23 * jm23;
     const T iJ = jm23 * r3;  // 1/J = (J^(-1/3))^3

@@ -69,7 +69,11 @@ int launch_compute_F(const commet_mesh *mesh, int precision, const void *u, void
 // are staged in shared memory and read by its 8 lanes.
 constexpr int kElPerCta = 16;
 
-template <typename T, bool SCATTER>
+// SYM (a major-symmetric A, A_iJkL = A_kLiJ, as every hyperelastic tangent): K_e is
+// symmetric, and lane I forms only the blocks (I, K) with K = I, I + 1, I + 2, I + 3 and,
+// for I < 4, I + 4 (mod 8): each unordered node pair once, at most 5 blocks per lane
+// instead of 8; every block other than (I, I) is also written transposed as (K, I).
+template <typename T, bool SCATTER, bool SYM = false>
 __global__ void __launch_bounds__(128)
     elem_assemble_kernel(int64_t n_el, const int32_t *__restrict__ el_list, int64_t n_list,
                          const int32_t *__restrict__ conn, const double *__restrict__ X, const T *__restrict__ P,
@@ -101,12 +105,13 @@ __global__ void __launch_bounds__(128)
             for (int a = 0; a < 3; ++a) s_g[le][I][K][a] = gX[K][a];
         s_w[le][I] = w;
     }
+    constexpr int NB = SYM ? 5 : 8;  // blocks per lane: slot b is node K = (I + b) mod 8 (SYM) or b
     T f[3] = {T(0), T(0), T(0)};
-    T Kr[3][8][3];
+    T Kr[3][NB][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int K = 0; K < 8; ++K)
+        for (int K = 0; K < NB; ++K)
 #pragma unroll
             for (int k = 0; k < 3; ++k) Kr[i][K][k] = T(0);
     const bool want_K = (A != nullptr);
@@ -145,14 +150,16 @@ __global__ void __launch_bounds__(128)
                         T3[k][L] = wg[0] * Aq[(3 * i) * 9 + 3 * k + L] + wg[1] * Aq[(3 * i + 1) * 9 + 3 * k + L] +
                                    wg[2] * Aq[(3 * i + 2) * 9 + 3 * k + L];
 #pragma unroll
-                for (int K = 0; K < 8; ++K) {
+                for (int b = 0; b < NB; ++b) {
+                    if (SYM && b == 4 && I >= 4) continue;
+                    const int K = SYM ? ((I + b) & 7) : b;
                     const T g0 = s_g[le][q][K][0], g1 = s_g[le][q][K][1], g2 = s_g[le][q][K][2];
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
                         // one fused multiply-add per product, accumulated in place
-                        Kr[i][K][k] += T3[k][0] * g0;
-                        Kr[i][K][k] += T3[k][1] * g1;
-                        Kr[i][K][k] += T3[k][2] * g2;
+                        Kr[i][b][k] += T3[k][0] * g0;
+                        Kr[i][b][k] += T3[k][1] * g1;
+                        Kr[i][b][k] += T3[k][2] * g2;
                     }
                 }
             }
@@ -165,11 +172,17 @@ __global__ void __launch_bounds__(128)
     }
     if (K_e != nullptr && want_K) {
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
+        for (int b = 0; b < NB; ++b) {
+            if (SYM && b == 4 && I >= 4) continue;
+            const int K = SYM ? ((I + b) & 7) : b;
 #pragma unroll
-            for (int K = 0; K < 8; ++K)
+            for (int i = 0; i < 3; ++i)
 #pragma unroll
-                for (int k = 0; k < 3; ++k) K_e[((3 * I + i) * 24 + 3 * K + k) * n_el + e] = Kr[i][K][k];
+                for (int k = 0; k < 3; ++k) {
+                    K_e[((3 * I + i) * 24 + 3 * K + k) * n_el + e] = Kr[i][b][k];
+                    if (SYM && b > 0) K_e[((3 * K + k) * 24 + 3 * I + i) * n_el + e] = Kr[i][b][k];
+                }
+        }
     }
     if (SCATTER) {
         const int64_t gI = conn[8 * e + I];
@@ -180,12 +193,24 @@ __global__ void __launch_bounds__(128)
         if (K_vals != nullptr && want_K) {
             const int64_t rl = rowlen[gI];
 #pragma unroll
-            for (int K = 0; K < 8; ++K) {
+            for (int b = 0; b < NB; ++b) {
+                if (SYM && b == 4 && I >= 4) continue;
+                const int K = SYM ? ((I + b) & 7) : b;
                 const int64_t base = emap[(8 * e + I) * 8 + K];
 #pragma unroll
                 for (int i = 0; i < 3; ++i)
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) K_vals[base + i * rl + k] += Kr[i][K][k];
+                    for (int k = 0; k < 3; ++k) K_vals[base + i * rl + k] += Kr[i][b][k];
+                if (SYM && b > 0) {
+                    // the transposed block into the rows of node K (no other element of this
+                    // colour touches them)
+                    const int64_t base2 = emap[(8 * e + K) * 8 + I];
+                    const int64_t rl2 = rowlen[conn[8 * e + K]];
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) K_vals[base2 + k * rl2 + i] += Kr[i][b][k];
+                }
             }
         }
     }
@@ -364,7 +389,7 @@ static int launch_elem_tma(const commet_mesh *mesh, const void *P, const void *A
     return cudaGetLastError() == cudaSuccess ? COMMET_OK : COMMET_ERR_CUDA;
 }
 
-template <typename T>
+template <typename T, bool SYM>
 static int elem_typed(const commet_mesh *mesh, const void *P, const void *A, void *f_e, void *K_e, void *r,
                       void *K_vals, cudaStream_t s) {
     const int64_t n_el = mesh->n_el;
@@ -372,11 +397,12 @@ static int elem_typed(const commet_mesh *mesh, const void *P, const void *A, voi
     const bool scatter = (r != nullptr) || (K_vals != nullptr);
     if (!scatter) {
         if constexpr (sizeof(T) == 4) {
+            // HBM-bound: the full contraction costs no more than the symmetric one
             const int rc = launch_elem_tma<T>(mesh, P, A, f_e, K_e, s);
             if (rc != COMMET_ERR_UNSUPPORTED) return rc;
         }
         const int64_t blocks = (n_el + kElPerCta - 1) / kElPerCta;
-        elem_assemble_kernel<T, false><<<(unsigned)blocks, 128, 0, s>>>(
+        elem_assemble_kernel<T, false, SYM><<<(unsigned)blocks, 128, 0, s>>>(
             n_el, nullptr, n_el, mesh->d_conn, mesh->d_X, (const T *)P, (const T *)A, (T *)f_e, (T *)K_e, nullptr,
             nullptr, nullptr, nullptr);
         return cudaGetLastError() == cudaSuccess ? COMMET_OK : COMMET_ERR_CUDA;
@@ -387,7 +413,7 @@ static int elem_typed(const commet_mesh *mesh, const void *P, const void *A, voi
         const int64_t off = mesh->colour_off[c], cnt = mesh->colour_off[c + 1] - off;
         if (cnt == 0) continue;
         const int64_t blocks = (cnt + kElPerCta - 1) / kElPerCta;
-        elem_assemble_kernel<T, true><<<(unsigned)blocks, 128, 0, s>>>(
+        elem_assemble_kernel<T, true, SYM><<<(unsigned)blocks, 128, 0, s>>>(
             n_el, mesh->d_colour_el + off, cnt, mesh->d_conn, mesh->d_X, (const T *)P, (const T *)A, (T *)f_e,
             (T *)K_e, (T *)r, (T *)K_vals, mesh->d_emap, mesh->d_rowlen);
         if (cudaGetLastError() != cudaSuccess) return COMMET_ERR_CUDA;
@@ -503,9 +529,13 @@ int launch_assembly_adjoints(const commet_mesh *mesh, int precision, const void 
 }
 
 int launch_elem_assemble(const commet_mesh *mesh, int precision, const void *P, const void *A, void *f_e,
-                         void *K_e, void *r, void *K_vals, cudaStream_t s) {
-    if (precision == COMMET_F64) return elem_typed<double>(mesh, P, A, f_e, K_e, r, K_vals, s);
-    return elem_typed<float>(mesh, P, A, f_e, K_e, r, K_vals, s);
+                         void *K_e, void *r, void *K_vals, cudaStream_t s, bool symmetric) {
+    if (symmetric) {
+        if (precision == COMMET_F64) return elem_typed<double, true>(mesh, P, A, f_e, K_e, r, K_vals, s);
+        return elem_typed<float, true>(mesh, P, A, f_e, K_e, r, K_vals, s);
+    }
+    if (precision == COMMET_F64) return elem_typed<double, false>(mesh, P, A, f_e, K_e, r, K_vals, s);
+    return elem_typed<float, false>(mesh, P, A, f_e, K_e, r, K_vals, s);
 }
 
 }  // namespace commet

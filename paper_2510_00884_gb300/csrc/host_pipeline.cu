@@ -140,8 +140,10 @@ int run_host_pipeline(const commet_model *m, const commet_mesh *mesh, int64_t n_
             commet_mesh view = *mesh;  // the chunk's elements: same nodes, a window of conn
             view.n_el = nu;
             view.d_conn = mesh->d_conn + 8 * u0;
+            // A is the update's own tangent, the Hessian of an energy: major symmetric
             rc = launch_elem_assemble(&view, prec_elem, buf + lay.P, want_A ? buf + lay.A : nullptr,
-                                      f_e ? buf + lay.fe : nullptr, K_e ? buf + lay.Ke : nullptr, nullptr, nullptr, s);
+                                      f_e ? buf + lay.fe : nullptr, K_e ? buf + lay.Ke : nullptr, nullptr, nullptr, s,
+                                      true);
             if (rc != COMMET_OK) break;
         }
         PIPE_TRY(cudaEventRecord(st.ev_done[b], s));

@@ -151,8 +151,9 @@ int launch_status_init(int32_t *status, cudaStream_t s);
 int launch_target_stress(int precision, int64_t n_qp, const void *F, int nf, const double *fib, double mu,
                          double k1, double k2, double kappa, void *P, cudaStream_t s);
 int launch_compute_F(const commet_mesh *mesh, int precision, const void *u, void *F, cudaStream_t s);
+// symmetric: A is major symmetric (every hyperelastic tangent); K_e from its upper blocks
 int launch_elem_assemble(const commet_mesh *mesh, int precision, const void *P, const void *A, void *f_e,
-                         void *K_e, void *r, void *K_vals, cudaStream_t s);
+                         void *K_e, void *r, void *K_vals, cudaStream_t s, bool symmetric = false);
 int launch_newton_assemble(const commet_model *m, const commet_mesh *mesh, const void *u, void *r, void *K_vals,
                            int32_t *status, cudaStream_t s);
 int prepare_bf16_weights(commet_model *m);

@@ -42,7 +42,8 @@ def test_with_mesh_matches_device_calls(pkg, prec, chunk):
     gm = pkg.Mesh(mesh.X, mesh.conn)
     F = pm_to_cm(wl.random_F(rng, 8 * mesh.n_el, 0.15), DT[prec])
     psi, P, A = m.const_update(F)
-    f_e, K_e, _, _ = gm.elem_assemble(P, A, "f64" if prec == "f64" else "f32")
+    # the pipeline assembles the update's own (major-symmetric) tangent by its upper blocks
+    f_e, K_e, _, _ = gm.elem_assemble(P, A, "f64" if prec == "f64" else "f32", symmetric=True)
     Fh = F.cpu().pin_memory()
     out = m.const_update_host(Fh, gm, chunk=chunk)
     torch.cuda.synchronize()

@@ -284,6 +284,48 @@ def test_elem_assemble_and_csr_scatter(pkg, prec):
     assert e_K.max() < TOL[prec], (e_K.max(), int(e_K.argmax()))
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("n", [(5, 4, 3), (1, 1, 1), (3, 1, 2)])
+def test_elem_assemble_symmetric(pkg, prec, n):
+    """commet_elem_assemble_symmetric (upper node blocks of K_e for a major-symmetric A):
+    on distorted meshes (ragged last CTA of 16 elements, a single element), f_e, K_e, r and
+    the CSR values against the oracle's full eq. r-quad / k-quad on the same P and A (the
+    update's own tangent), and K_e exactly symmetric."""
+    mesh = wl.structured_mesh(*n, lengths=(1.0, 0.8, 0.6))
+    rng = np.random.Generator(np.random.PCG64(19 + sum(n)))
+    X = mesh.X + 0.02 * rng.uniform(-1, 1, size=mesh.X.shape)
+    mesh = wl.Mesh(X=X, conn=mesh.conn, n=mesh.n)
+    spec = wl.make_model(rng, wl.KIN_RAW, 2, W=32, L=3, kappa=1.0)
+    gm = pkg.Mesh(mesh.X, mesh.conn, want_csr=True)
+    dt = DT[prec]
+    u = torch.from_numpy(np.ascontiguousarray((0.01 * rng.normal(size=mesh.X.shape)).T)).to(dt).cuda()
+    F = gm.compute_F(u, prec)
+    _, P, A = pkg.Model(spec, prec).const_update(F)
+    P_in, A_in = cm_to_pm(P).astype(np.float64), cm_to_pm(A).astype(np.float64)
+    f_e, K_e, r, Kv = gm.elem_assemble(P, A, prec, want_r=True, want_Kcsr=True, symmetric=True)
+    f_e2, K_e2, _, _ = gm.elem_assemble(P, A, prec, symmetric=True)
+    f_r, K_r = oracle.elem_assemble(mesh, P_in, A_in)
+    for fe, Ke, what in ((f_e, K_e, "scatter launch"), (f_e2, K_e2, "plain launch")):
+        assert_close(cm_to_pm(fe), f_r, TOL[prec], f"f_e {what}")
+        assert_close(cm_to_pm(Ke), K_r.reshape(-1, 576), TOL[prec], f"K_e {what}")
+    # the off-diagonal node blocks are written as exact transposes (the diagonal ones are
+    # formed whole, symmetric to rounding)
+    Kh = cm_to_pm(K_e).reshape(-1, 8, 3, 8, 3)
+    for I in range(8):
+        for K in range(8):
+            if I != K:
+                assert np.array_equal(Kh[:, I, :, K, :], np.transpose(Kh[:, K, :, I, :], (0, 2, 1))), (I, K)
+    r_r = oracle.scatter_residual(mesh, f_r)
+    rowptr, col = gm.csr()
+    Kv_r, missing = oracle.scatter_csr(mesh, K_r, rowptr, col)
+    assert missing == 0
+    s_r, s_K = assembly_scales(mesh, P_in, A_in, rowptr, col)
+    e_r = rel_err(r.cpu().numpy().astype(np.float64).reshape(-1, 3), r_r.reshape(-1, 3), s_r.reshape(-1, 3))
+    assert e_r.max() < TOL[prec], (e_r.max(), int(e_r.argmax()))
+    e_K = csr_rows_rel_err(Kv.cpu().numpy().astype(np.float64), Kv_r, s_K, rowptr)
+    assert e_K.max() < TOL[prec], (e_K.max(), int(e_K.argmax()))
+
+
 def test_target_stress(pkg):
     rng = np.random.Generator(np.random.PCG64(10))
     F = wl.random_F(rng, 3001, 0.15)
