@@ -269,6 +269,10 @@ __device__ __forceinline__ void stage_kinematics(const T *F, const KinConst<T> &
     using S = Stage<D, NF>;
     T C[9];
     right_cg(F, C);
+    // FP32 (bound by latency, not by FP64 instructions) forms the cofactor matrix in
+    // straight-line code; FP64 lanes form only their own entries below
+    T cof[9], Jc;
+    if constexpr (sizeof(T) != 8) cof_det(F, cof, Jc);
     const T J = T(1) + Jm1;
     const T I1 = C[0] + C[4] + C[8];
     const T I2 = second_invariant(C);
@@ -296,10 +300,15 @@ __device__ __forceinline__ void stage_kinematics(const T *F, const KinConst<T> &
         const int a = lane4 + 4 * t;
         if (a < 9) {
             const int p = a / 3, q = a - 3 * p;  // a = 3 p + q
-            // this lane's cofactor entry only (the lanes share one instruction stream)
-            const int pa1 = p == 2 ? 0 : p + 1, pa2 = p == 0 ? 2 : p - 1;
-            const int qa1 = q == 2 ? 0 : q + 1, qa2 = q == 0 ? 2 : q - 1;
-            const T cofa = F[3 * pa1 + qa1] * F[3 * pa2 + qa2] - F[3 * pa1 + qa2] * F[3 * pa2 + qa1];
+            // FP64: this lane's cofactor entry only (the lanes share one instruction stream)
+            T cofa;
+            if constexpr (sizeof(T) == 8) {
+                const int pa1 = p == 2 ? 0 : p + 1, pa2 = p == 0 ? 2 : p - 1;
+                const int qa1 = q == 2 ? 0 : q + 1, qa2 = q == 0 ? 2 : q - 1;
+                cofa = F[3 * pa1 + qa1] * F[3 * pa2 + qa2] - F[3 * pa1 + qa2] * F[3 * pa2 + qa1];
+            } else {
+                cofa = cof[a];
+            }
             const T Fa = F[a], Ha = cofa * iJ;
             const T FC = F[3 * p] * C[q] + F[3 * p + 1] * C[3 + q] + F[3 * p + 2] * C[6 + q];
             const T gI2 = T(2) * (I1 * Fa - FC);  // raw dI2/dF = 2 (I1 F - F C)

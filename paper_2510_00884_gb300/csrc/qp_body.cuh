@@ -382,7 +382,7 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
             }
         } else {
             const T *zin = wk + ((k - 1) & 1) * W;
-            const T *At = at + (k - 2) * W * W + j0;
+            const T *At = (sizeof(T) == 8 ? at : sw + lay.At) + (k - 2) * W * W + j0;
 #pragma unroll 2
             for (int i = 0; i < W; i += V) {
                 T zv[V];
@@ -520,7 +520,7 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
             }
         }
         for (int k = 2; k <= L; ++k) {
-            const T *At = at + (k - 2) * W * W + j0;
+            const T *At = (sizeof(T) == 8 ? at : sw + lay.At) + (k - 2) * W * W + j0;
             const T *Bt = sw + lay.Bt + (k - 2) * D * W + j0;
             const T *sin = wk + ((k - 1) & 1) * W * DP;
             T *sout = wk + (k & 1) * W * DP;
@@ -534,7 +534,9 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
 #pragma unroll
                     for (int cc = 0; cc < NC; ++cc) acc[cc][m] = w[cc];
                 }
-                if (k == 2 && mt != nullptr) {
+                bool use_m = false;
+                if constexpr (sizeof(T) == 8) use_m = (k == 2 && mt != nullptr);
+                if (use_m) {
                     // J_2 = B_2 + sum_i s_1[i] M[i]: one multiply-add per entry
 #pragma unroll 2
                     for (int i = 0; i < W; ++i) {

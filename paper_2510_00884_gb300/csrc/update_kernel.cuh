@@ -108,7 +108,8 @@ static int launch_typed(const commet_model *m, int64_t n_qp, const void *F, void
     };
     int wcount = m->lay.total;
     int warps = fit(((size_t)m->lay.total * sizeof(T) + 15) / 16 * 16);
-    for (const int wc : {m->lay.Ar, m->lay.M > 0 ? m->lay.M : m->lay.Ar, m->lay.At}) {
+    // (FP32 is bound by latency: A_k transposed stays in shared memory there)
+    for (const int wc : {m->lay.Ar, m->lay.M > 0 ? m->lay.M : m->lay.Ar, sizeof(T) == 8 ? m->lay.At : m->lay.Ar}) {
         const int w = fit(((size_t)wc * sizeof(T) + 15) / 16 * 16);
         if (w > warps) {
             warps = w;
