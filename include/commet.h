@@ -347,7 +347,9 @@ int commet_norm2(const commet_mesh *mesh, int32_t precision, int64_t n, const vo
  * Deterministic: the same inputs give bitwise the same dL_dtheta.
  * F, dL_dP, dL_dF in the model's precision, [9][n_qp], 16-byte aligned; dL_dtheta
  * [n_params] is OVERWRITTEN (zeroed when n_qp = 0). A point with a non-finite F or G or
- * J <= 0 gets NaN in dL_dF and adds nothing to dL_dtheta.
+ * J <= 0 gets NaN in dL_dF and adds nothing to dL_dtheta; for a CANN model so does a
+ * point whose dL_dF or weight-gradient terms leave the precision's number range (its
+ * exponential terms at large stretches, in FP32 mostly).
  * Errors: INVALID_ARG (null, misaligned or short workspace); UNSUPPORTED for the bf16
  * precision, the Gent-Thomas and KAN inner functions, stress-free models (the shift n0
  * depends on theta), 64-wide networks with one fibre, and networks whose weights,

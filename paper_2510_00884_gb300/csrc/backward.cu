@@ -688,18 +688,19 @@ __global__ void __launch_bounds__(kCannBwWarps * 32)
         qp_group_finish<T, NF>(sw + lay.n0, sw + lay.K0, kc, qs, qi, jb, F, K, Jm1, ch, bad, valid, npart, dN, Hs,
                                true, pa, 1, pa + 9, 1, nullptr, 0, psi_val, report);
         __syncwarp();
-        // a point outside the energy's domain (reported by the forward) is treated as J <= 0
-        const bool drop = report || !valid;
         // dL/dF by columns b = jb, jb + 4, jb + 8
+        T dfv[3];
+        bool fin = true;
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
             const int b = jb + kG * t;
+            T v = T(0);
             if (b < 9) {
-                T v = T(0);
 #pragma unroll
                 for (int a = 0; a < 9; ++a) v += G[a] * pa[9 + 9 * a + b];
-                if (valid && dFg != nullptr) dFg[b * n_qp + q] = report ? T(NAN) : v;
             }
+            dfv[t] = v;
+            fin = fin && dev_finite(v);
         }
         // r_m = G : dK_m/dF from the staged kinematic gradients
         T r[D];
@@ -716,22 +717,41 @@ __global__ void __launch_bounds__(kCannBwWarps * 32)
                 for (int m = 0; m < 3; ++m) r[m] *= ch.d1[m];
             }
         }
+        // the point's weight-gradient terms, d n of them round-robin over its 4 lanes
+        auto term = [&](int t, T &g1, T &g2) {
+            const int m = t / n, k = t - m * n;
+            T x = T(0), rm = T(0);
+#pragma unroll
+            for (int mm = 0; mm < D; ++mm) {
+                x = (mm == m) ? K[mm] : x;
+                rm = (mm == m) ? r[mm] : rm;
+            }
+            cann_term_wgrad<T>(x, (int)sw[lay.ck + 3 * k], (int)sw[lay.ck + 3 * k + 1], (int)sw[lay.ck + 3 * k + 2],
+                               sw[lay.cw + 2 * t], sw[lay.cw + 2 * t + 1], g1, g2);
+            g1 *= rm;
+            g2 *= rm;
+        };
+        for (int t0 = 0; t0 < nt; t0 += kG) {
+            if (t0 + jb < nt) {
+                T g1, g2;
+                term(t0 + jb, g1, g2);
+                fin = fin && dev_finite(g1) && dev_finite(g2);
+            }
+        }
+        // a point outside the energy's domain (reported by the forward) or whose dL/dF or
+        // gradient terms leave the number range (the CANN's exponentials, mostly in FP32)
+        // is treated as J <= 0: NaN in dL/dF, nothing in dL/dw
+        const unsigned nonfin = __ballot_sync(0xffffffffu, !fin);
+        const bool drop = report || !valid || ((nonfin >> (qi * 4)) & 0xFu) != 0u;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const int b = jb + kG * t;
+            if (b < 9 && valid && dFg != nullptr) dFg[b * n_qp + q] = drop ? T(NAN) : dfv[t];
+        }
         for (int t0 = 0; t0 < nt; t0 += kG) {
             const int t = t0 + jb;
             T g1 = T(0), g2 = T(0);
-            if (t < nt && !drop) {
-                const int m = t / n, k = t - m * n;
-                T x = T(0), rm = T(0);
-#pragma unroll
-                for (int mm = 0; mm < D; ++mm) {
-                    x = (mm == m) ? K[mm] : x;
-                    rm = (mm == m) ? r[mm] : rm;
-                }
-                cann_term_wgrad<T>(x, (int)sw[lay.ck + 3 * k], (int)sw[lay.ck + 3 * k + 1], (int)sw[lay.ck + 3 * k + 2],
-                                   sw[lay.cw + 2 * t], sw[lay.cw + 2 * t + 1], g1, g2);
-                g1 *= rm;
-                g2 *= rm;
-            }
+            if (t < nt && !drop) term(t, g1, g2);
             // the same term over the warp's 8 points (lanes with the same jb)
 #pragma unroll
             for (int msk = 4; msk <= 16; msk <<= 1) {

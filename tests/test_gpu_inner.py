@@ -233,3 +233,33 @@ def test_cann_backward_edge_cases(pkg, prec):
     _, dth_r, dth_abs = oracle.const_backward(oracle.OracleModel(spec), Fin, Gin, want_abs=True)
     e = np.abs(dth.cpu().numpy().astype(np.float64) - dth_r) / np.maximum(dth_abs, 1e-300)
     assert e.max() < (1e-12 if prec == "f64" else 1e-4), e.max()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_cann_backward_out_of_range_point(pkg, prec):
+    """On the paper's CANN (no logarithmic terms, so every F with J > 0 is in the energy's
+    domain) F = diag(5, 1/2, 1/2) takes the exponential terms to psi ~ 1e63, A ~ 2e68 and
+    dL/dw ~ 5e68: finite in FP64, where the point is kept and matches the oracle, but past
+    the FP32 range, where it gets NaN in dL/dF and adds nothing to dL/dw (the other points'
+    sum then matches the oracle over them alone)."""
+    spec = BW_SPECS["cann_paper_poly"]
+    m = pkg.Model(spec, prec)
+    rng = np.random.Generator(np.random.PCG64(632))
+    F = wl.random_F(rng, 100, 0.15)
+    G = rng.normal(size=F.shape)
+    F[37] = np.diag([5.0, 0.5, 0.5]).ravel()
+    dF, dth = m.backward(pm_to_cm(F, DT[prec]), pm_to_cm(G, DT[prec]))
+    torch.cuda.synchronize()
+    dFh = cm_to_pm(dF)
+    keep = np.arange(100) if prec == "f64" else np.delete(np.arange(100), 37)
+    if prec == "f32":
+        assert np.isnan(dFh[37]).all()
+    assert np.isfinite(dFh[keep]).all()
+    Fin = cm_to_pm(pm_to_cm(F, DT[prec])).astype(np.float64)[keep]
+    Gin = cm_to_pm(pm_to_cm(G, DT[prec])).astype(np.float64)[keep]
+    dF_r, dth_r, dth_abs = oracle.const_backward(oracle.OracleModel(spec), Fin, Gin, want_abs=True)
+    tol = 1e-12 if prec == "f64" else 1e-4
+    e = np.abs(dth.cpu().numpy().astype(np.float64) - dth_r) / np.maximum(dth_abs, 1e-300)
+    assert e.max() < tol, e.max()
+    ef = np.linalg.norm(dFh[keep] - dF_r, axis=1) / np.maximum(np.linalg.norm(dF_r, axis=1), 1e-300)
+    assert ef.max() < (1e-11 if prec == "f64" else 1e-3), ef.max()

@@ -455,14 +455,17 @@ def workload_c2(n: int = 128, seed: int = 2):
     return dict(name=f"c2_uniaxial_{n}cube_d3w64l3", model=model, mesh=mesh, F=F)
 
 
-def workload_c3(n_qp: int = 1 << 20, seed: int = 3):
+def workload_c3(n_qp: int = 1 << 20, seed: int = 3, inner: str = "micnn"):
     """Differentiation: the C1 network (seed 1 weights), n_qp points F = I + 0.15 N(0,1)
-    drawn from seed 3; target model Neo-Hookean plus fibres (mu 1, k1 2, k2 0.5, kappa 10)."""
-    model = workload_c1(n=1)["model"]
+    drawn from seed 3; target model Neo-Hookean plus fibres (mu 1, k1 2, k2 0.5, kappa 10).
+    inner = "cann": the same loss for the paper's CANN (App. C, the weights of
+    workload_cann) on the same points; its target has no fibres (Neo-Hookean, kappa 10)."""
+    model = workload_c1(n=1)["model"] if inner == "micnn" else workload_cann(n=1)["model"]
     rng = np.random.Generator(np.random.PCG64(seed))
     F = random_F(rng, n_qp, 0.15)
     target = dict(mu=1.0, k1=2.0, k2=0.5, kappa=10.0)
-    return dict(name=f"c3_backward_{n_qp}qp_d7w32l3", model=model, F=F, target=target)
+    tag = "d7w32l3" if inner == "micnn" else "cann_polyconvex_4terms"
+    return dict(name=f"c3_backward_{n_qp}qp_{tag}", model=model, F=F, target=target)
 
 
 def workload_residual(n: int = 64, seed: int = 9):
