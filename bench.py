@@ -788,7 +788,8 @@ def run_ours(args, rank, world, local_rank):
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
     spec = run.spec
     sW, sL = getattr(spec, "W", 0), getattr(spec, "L", 0)
-    net = f"d{spec.d}w{sW}l{sL}"
+    inner_name = getattr(spec, "inner_name", "micnn")
+    net = f"d{spec.d}w{sW}l{sL}" if inner_name == "micnn" else f"{inner_name}_d{spec.d}"
     dom = int(np.argmax(phase_ms))
     kname = run.phases[dom][0]
     alu = "f64" if prec == "f64" else "f32"
@@ -797,10 +798,10 @@ def run_ours(args, rank, world, local_rank):
         flops = per_qp * run.n_qp
         units = run.n_qp
         src = ["spatial.cu" if args.spatial else "const_update.cu", "update_kernel.cuh", "qp_body.cuh",
-               "device_math.cuh"]
+               "device_math.cuh"] + ([] if inner_name == "micnn" else ["closed_form.cuh"])
     elif kname == "const_backward_kernel":
         flops = backward_flops_per_qp(spec.d, sW, sL) * run.n_qp
-        units, src = run.n_qp, ["backward.cu", "device_math.cuh"]
+        units, src = run.n_qp, ["backward.cu", "qp_body.cuh", "device_math.cuh", "closed_form.cuh"]
     elif kname == "newton_kernel":
         flops = (algorithmic_flops_per_qp(spec.d, sW, sL) * 8 + 2 * ELEM_MACS) * run.n_el
         units, src = run.n_el, ["newton.cu", "qp_body.cuh", "device_math.cuh"]
@@ -860,7 +861,8 @@ def run_ours(args, rank, world, local_rank):
         bts = per_qp * run.n_qp / (phase_ms[dom] * 1e-3) / 1e9
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         roofline = {"bound": "hbm", "kernel": kname, "achieved": bts, "peak": hbm, "unit": "GB/s",
-                    "frac": bts / hbm, "traffic": None, "bytes_per_qp": per_qp,
+                    "frac": bts / hbm, "traffic": ncu_traffic(kname, net, prec, src_hash, units),
+                    "bytes_per_qp": per_qp, "src_hash": src_hash,
                     "peak_source": f"measured HBM copy ({peak_src} peaks file)", "kernel_ms": phase_ms[dom]}
     if kname == "const_backward_kernel" and getattr(spec, "inner_name", "micnn") != "micnn":
         # the CANN's backward: a few dozen operations per point around the forward's
@@ -870,7 +872,8 @@ def run_ours(args, rank, world, local_rank):
         bts = per_qp * run.n_qp / (phase_ms[dom] * 1e-3) / 1e9
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         roofline = {"bound": "hbm", "kernel": kname, "achieved": bts, "peak": hbm, "unit": "GB/s",
-                    "frac": bts / hbm, "traffic": None, "bytes_per_qp": per_qp,
+                    "frac": bts / hbm, "traffic": ncu_traffic(kname, net, prec, src_hash, units),
+                    "bytes_per_qp": per_qp, "src_hash": src_hash,
                     "peak_source": f"measured HBM copy ({peak_src} peaks file)", "kernel_ms": phase_ms[dom]}
     phases = {n_: ms for (n_, _), ms in zip(run.phases, phase_ms)}
     ek = "elem_spatial_kernel" if args.spatial else "elem_assemble_kernel"

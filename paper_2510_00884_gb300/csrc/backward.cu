@@ -731,7 +731,20 @@ __global__ void __launch_bounds__(kCannBwWarps * 32)
             g1 *= rm;
             g2 *= rm;
         };
-        for (int t0 = 0; t0 < nt; t0 += kG) {
+        // FP64: the lane's first kTermRegs terms stay in registers for the sums below (their
+        // exponentials cost FP64 work); any further ones, and all FP32 ones, are evaluated
+        // again there
+        constexpr int kTermRegs = sizeof(T) == 8 ? 4 : 0;
+        T c1[kTermRegs > 0 ? kTermRegs : 1], c2[kTermRegs > 0 ? kTermRegs : 1];
+#pragma unroll
+        for (int i = 0; i < kTermRegs; ++i) {
+            c1[i] = c2[i] = T(0);
+            if (jb + kG * i < nt) {
+                term(jb + kG * i, c1[i], c2[i]);
+                fin = fin && dev_finite(c1[i]) && dev_finite(c2[i]);
+            }
+        }
+        for (int t0 = kG * kTermRegs; t0 < nt; t0 += kG) {
             if (t0 + jb < nt) {
                 T g1, g2;
                 term(t0 + jb, g1, g2);
@@ -749,9 +762,18 @@ __global__ void __launch_bounds__(kCannBwWarps * 32)
             if (b < 9 && valid && dFg != nullptr) dFg[b * n_qp + q] = drop ? T(NAN) : dfv[t];
         }
         for (int t0 = 0; t0 < nt; t0 += kG) {
-            const int t = t0 + jb;
+            const int t = t0 + jb, i = t0 / kG;
             T g1 = T(0), g2 = T(0);
-            if (t < nt && !drop) term(t, g1, g2);
+            if (kTermRegs > 0 && i < kTermRegs) {
+#pragma unroll
+                for (int r2 = 0; r2 < kTermRegs; ++r2) {
+                    g1 = (r2 == i) ? c1[r2] : g1;
+                    g2 = (r2 == i) ? c2[r2] : g2;
+                }
+                if (drop) g1 = g2 = T(0);
+            } else if (t < nt && !drop) {
+                term(t, g1, g2);
+            }
             // the same term over the warp's 8 points (lanes with the same jb)
 #pragma unroll
             for (int msk = 4; msk <= 16; msk <<= 1) {
