@@ -627,8 +627,15 @@ static int np_padded(const commet_model *m) { return (int)((np_net(m) + 3) / 4 *
 // its warps, in warp order, goes to the workspace, reduced over CTAs by reduce_partials_kernel.
 constexpr int kCannBwWarps = 8;
 
+// Whether the CANN backward forms the kinematic scalars in batches (kin_batch): not in
+// FP64 with fibres, whose point slabs leave no room for the records.
 template <typename T, int NF>
-__global__ void __launch_bounds__(kCannBwWarps * 32)
+__host__ __device__ constexpr bool cann_bw_batches() {
+    return sizeof(T) == 4 || NF == 0;
+}
+
+template <typename T, int NF>
+__global__ void __launch_bounds__(kCannBwWarps * 32, (sizeof(T) == 4 && NF == 0) ? 2 : 1)
     cann_backward_kernel(const T *__restrict__ gw, NetLayout lay, KinConst<T> kc, int64_t n_qp,
                          const T *__restrict__ Fg, const T *__restrict__ Gg, T *__restrict__ dFg,
                          T *__restrict__ partial, int np_pad, int qstride) {
@@ -653,8 +660,17 @@ __global__ void __launch_bounds__(kCannBwWarps * 32)
     const int n = lay.cn, nt = D * n;
     const int64_t n_tiles = (n_qp + kQPW - 1) / kQPW;
     const int64_t n_gwarps = (int64_t)gridDim.x * kCannBwWarps;
+    // the warp's kinematic records after the point slabs (FP64 with fibres: no room beside
+    // its slabs, the scalars are formed per point)
+    constexpr bool kBatch = cann_bw_batches<T, NF>();
+    T *rec = slabs + (size_t)kCannBwWarps * kQPW * qstride + (size_t)warp * kinrec_size<NF>() * 32;
 
-    for (int64_t tile = (int64_t)blockIdx.x * kCannBwWarps + warp; tile < n_tiles; tile += n_gwarps) {
+    for (int64_t tile0 = (int64_t)blockIdx.x * kCannBwWarps + warp; tile0 < n_tiles; tile0 += kKinTiles * n_gwarps) {
+      if constexpr (kBatch) kin_batch<T, NF, true>(Fg, Gg, n_qp, tile0, n_gwarps, n_tiles, kc, rec, lane);
+      __syncwarp();
+      for (int sub = 0; sub < kKinTiles; ++sub) {
+        const int64_t tile = tile0 + sub * n_gwarps;
+        if (tile >= n_tiles) break;
         const int64_t q = tile * kQPW + qi;
         const bool valid = q < n_qp;
         T F[9], G[9];
@@ -665,16 +681,21 @@ __global__ void __launch_bounds__(kCannBwWarps * 32)
         }
         T K[D], Jm1;
         PolyChain<T> ch;
-        bool bad = !kin_scalars_k64<T, NF>(F, kc, K, Jm1, ch);
+        bool bad;
+        if constexpr (kBatch) {
+            bad = kin_read<T, NF>(rec, sub * kQPW + qi, K, Jm1, ch);
+        } else {
+            bad = !kin_scalars_k64<T, NF>(F, kc, K, Jm1, ch);
 #pragma unroll
-        for (int c = 0; c < 9; ++c) bad = bad || !dev_finite(G[c]);
+            for (int c = 0; c < 9; ++c) bad = bad || !dev_finite(G[c]);
+        }
         if (bad) {
 #pragma unroll
             for (int c = 0; c < 9; ++c) {
                 F[c] = (c % 4) == 0 ? T(1) : T(0);
                 G[c] = T(0);
             }
-            kin_scalars_k64<T, NF>(F, kc, K, Jm1, ch);
+            if constexpr (!kBatch) kin_scalars_k64<T, NF>(F, kc, K, Jm1, ch);
         }
         T npart = T(0), dN[D], Hs[NH];
 #pragma unroll
@@ -786,6 +807,7 @@ __global__ void __launch_bounds__(kCannBwWarps * 32)
             }
         }
         __syncwarp();
+      }
     }
     __syncthreads();
     for (int p = threadIdx.x; p < np_pad; p += blockDim.x) {
@@ -894,7 +916,8 @@ static int cann_bw_launch(const commet_model *m, int64_t n_qp, const void *F, co
     const int np_pad = np_padded(m);
     const size_t wbytes = ((size_t)m->lay.total * sizeof(T) + 15) / 16 * 16;
     const size_t smem = wbytes + (size_t)kCannBwWarps * np_pad * sizeof(T) +
-                        (size_t)kCannBwWarps * kQPW * qstride * sizeof(T);
+                        (size_t)kCannBwWarps * (kQPW * qstride + (cann_bw_batches<T, NF>() ? kinrec_size<NF>() * 32 : 0)) *
+                            sizeof(T);
     int dev = 0, smem_max = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

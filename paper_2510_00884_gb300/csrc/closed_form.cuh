@@ -172,6 +172,69 @@ __device__ __forceinline__ bool kin_scalars_k64(const T (&F)[9], const KinConst<
     }
 }
 
+// Kinematic scalars of a warp's next kKinTiles tiles (kKinTiles x kQPW = 32 points), one
+// point per lane. In the per-point code the four lanes of a point's group would each form
+// the same FP64 scalars, and GB300 bills an FP64 warp instruction to all 32 lanes whatever
+// the mask: formed here, once per point, they take a quarter of the FP64 instructions.
+// Lane l takes point l % kQPW of tile tile0 + (l / kQPW) tstep and writes, component-major
+// at rec[c * 32 + l]: K[D], J - 1, phi'[3], phi''[3] and 1 where F (or, WITH_G, G = dL/dP)
+// was inadmissible and the scalars are those of F = I (0 otherwise).
+constexpr int kKinTiles = 32 / kQPW;
+template <int NF>
+__host__ __device__ constexpr int kinrec_size() {
+    return 3 + 2 * NF + 8;
+}
+
+template <typename T, int NF, bool WITH_G>
+__device__ __forceinline__ void kin_batch(const T *__restrict__ Fg, const T *__restrict__ Gg, int64_t n_qp,
+                                          int64_t tile0, int64_t tstep, int64_t n_tiles, const KinConst<T> &kc,
+                                          T *rec, int lane) {
+    constexpr int D = 3 + 2 * NF;
+    const int64_t tile = tile0 + (int64_t)(lane / kQPW) * tstep;
+    const int64_t q = tile * kQPW + (lane % kQPW);
+    const bool valid = tile < n_tiles && q < n_qp;
+    T F[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) F[c] = valid ? Fg[c * n_qp + q] : ((c % 4) == 0 ? T(1) : T(0));
+    bool gbad = false;
+    if constexpr (WITH_G) {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) gbad = gbad || (valid && !dev_finite(Gg[c * n_qp + q]));
+    }
+    T K[D], Jm1;
+    PolyChain<T> ch{};
+    const bool bad = !kin_scalars_k64<T, NF>(F, kc, K, Jm1, ch) || gbad;
+    if (bad) {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) F[c] = (c % 4) == 0 ? T(1) : T(0);
+        kin_scalars_k64<T, NF>(F, kc, K, Jm1, ch);
+    }
+#pragma unroll
+    for (int m = 0; m < D; ++m) rec[m * 32 + lane] = K[m];
+    rec[D * 32 + lane] = Jm1;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        rec[(D + 1 + m) * 32 + lane] = ch.d1[m];
+        rec[(D + 4 + m) * 32 + lane] = ch.d2[m];
+    }
+    rec[(D + 7) * 32 + lane] = bad ? T(1) : T(0);
+}
+
+// The record of point r (0..31) of the last kin_batch; returns whether F = I was used.
+template <typename T, int NF>
+__device__ __forceinline__ bool kin_read(const T *rec, int r, T *K, T &Jm1, PolyChain<T> &ch) {
+    constexpr int D = 3 + 2 * NF;
+#pragma unroll
+    for (int m = 0; m < D; ++m) K[m] = rec[m * 32 + r];
+    Jm1 = rec[D * 32 + r];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        ch.d1[m] = rec[(D + 1 + m) * 32 + r];
+        ch.d2[m] = rec[(D + 4 + m) * 32 + r];
+    }
+    return rec[(D + 7) * 32 + r] != T(0);
+}
+
 // One weighted B-spline phi = w psi of an ICKAN layer (App. B) at x, with phi' and phi'':
 // degree KD on uniform knots t_m = lo + (m - KD) h. In knot units x sits in span m with
 // offset u; the KD + 1 non-zero basis functions follow from de Boor's triangle on uniform
@@ -313,7 +376,7 @@ template <typename T, int NF, int INNER, bool SPATIAL, int KD = 3>
 __global__ void __launch_bounds__(256)
     closed_update_kernel(const T *__restrict__ gw, NetLayout lay, KinConst<T> kc, int64_t n_qp,
                          const T *__restrict__ Fg, T *__restrict__ psi, T *__restrict__ P, T *__restrict__ A,
-                         int32_t *__restrict__ status, T *__restrict__ dN_out, int qstride) {
+                         int32_t *__restrict__ status, T *__restrict__ dN_out, int qstride, bool batch) {
     constexpr int D = 3 + 2 * NF, NH = D * (D + 1) / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sw = reinterpret_cast<T *>(smem_raw);
@@ -330,8 +393,18 @@ __global__ void __launch_bounds__(256)
     const int64_t n_tiles = (n_qp + kQPW - 1) / kQPW;
     const int64_t n_gwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const bool want_A = (A != nullptr);
+    // the warp's kinematic records after the point slabs (batch: when they fit in shared
+    // memory; otherwise the scalars are formed per point)
+    T *rec = sw + wbytes / (int)sizeof(T) + (size_t)(blockDim.x >> 5) * kQPW * qstride +
+             (size_t)warp * kinrec_size<NF>() * 32;
 
-    for (int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; tile < n_tiles; tile += n_gwarps) {
+    for (int64_t tile0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; tile0 < n_tiles;
+         tile0 += kKinTiles * n_gwarps) {
+      if (batch) kin_batch<T, NF, false>(Fg, nullptr, n_qp, tile0, n_gwarps, n_tiles, kc, rec, lane);
+      __syncwarp();
+      for (int sub = 0; sub < kKinTiles; ++sub) {
+        const int64_t tile = tile0 + sub * n_gwarps;
+        if (tile >= n_tiles) break;
         const int64_t q = tile * kQPW + qi;
         const bool valid = q < n_qp;
         const int64_t qo = valid ? q : 0;
@@ -340,11 +413,12 @@ __global__ void __launch_bounds__(256)
         for (int c = 0; c < 9; ++c) F[c] = valid ? Fg[c * n_qp + q] : ((c % 4) == 0 ? T(1) : T(0));
         T K[D], Jm1;
         PolyChain<T> ch;
-        const bool bad = !kin_scalars_k64<T, NF>(F, kc, K, Jm1, ch);
+        const bool bad = batch ? kin_read<T, NF>(rec, sub * kQPW + qi, K, Jm1, ch)
+                               : !kin_scalars_k64<T, NF>(F, kc, K, Jm1, ch);
         if (bad) {
 #pragma unroll
             for (int c = 0; c < 9; ++c) F[c] = (c % 4) == 0 ? T(1) : T(0);
-            kin_scalars_k64<T, NF>(F, kc, K, Jm1, ch);
+            if (!batch) kin_scalars_k64<T, NF>(F, kc, K, Jm1, ch);
         }
         T npart = T(0), dN[D], Hs[NH];
 #pragma unroll
@@ -389,6 +463,7 @@ __global__ void __launch_bounds__(256)
             }
         }
         __syncwarp();
+      }
     }
 }
 
@@ -406,7 +481,13 @@ static int launch_closed(const commet_model *m, int64_t n_qp, const void *F, voi
     const int qstride = qp_slab_elems<T>(D, 0, 0, NF, SPATIAL, net);
     const size_t wbytes = ((size_t)m->lay.total * sizeof(T) + 15) / 16 * 16;
     const int warps = 8;
-    const size_t smem = wbytes + (size_t)warps * kQPW * qstride * sizeof(T);
+    const size_t smem_pt = wbytes + (size_t)warps * kQPW * qstride * sizeof(T);
+    const size_t smem_b = smem_pt + (size_t)warps * kinrec_size<NF>() * 32 * sizeof(T);
+    int dev = 0, smem_max = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const bool batch = smem_b <= (size_t)smem_max;  // kinematic records beside the slabs
+    const size_t smem = batch ? smem_b : smem_pt;
     auto kern = closed_update_kernel<T, NF, INNER, SPATIAL, KD>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return COMMET_ERR_CUDA;
@@ -417,7 +498,7 @@ static int launch_closed(const commet_model *m, int64_t n_qp, const void *F, voi
     const int64_t want = (n_tiles + warps - 1) / warps;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count() * per_sm));
     kern<<<grid, warps * 32, smem, s>>>((const T *)m->d_weights, m->lay, kc, n_qp, (const T *)F, (T *)psi, (T *)P,
-                                        (T *)A, status, (T *)dN_out, qstride);
+                                        (T *)A, status, (T *)dN_out, qstride, batch);
     return cudaGetLastError() == cudaSuccess ? COMMET_OK : COMMET_ERR_CUDA;
 }
 
