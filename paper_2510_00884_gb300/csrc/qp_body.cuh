@@ -127,6 +127,104 @@ __device__ __forceinline__ void stv(T *p, const T *r) {
     }
 }
 
+// K in FP64 whatever T is. The CANN's polynomial terms make dN/dK proportional to K,
+// and a shifted invariant such as Ibar2 - 3 formed in FP32 carries an absolute error of
+// a few ulp(3) ~ 1e-6, a large relative error when K is small; with FP64 kinematic
+// scalars the FP32 path keeps its 1e-5 bound. (A network's dN/dK varies slowly with K,
+// so the network kernels form K in T.)
+template <typename T, int NF>
+__device__ __forceinline__ bool kin_scalars_k64(const T (&F)[9], const KinConst<T> &kc, T *K, T &Jm1,
+                                                PolyChain<T> &ch) {
+    if constexpr (sizeof(T) == 8) {
+        return kin_scalars<T, NF>(F, kc, K, Jm1, &ch);
+    } else {
+        constexpr int D = 3 + 2 * NF;
+        KinConst<double> kd{};
+        kd.kin = kc.kin;
+        kd.stress_free = kc.stress_free;
+        kd.kappa = (double)kc.kappa;
+        for (int f = 0; f < 2; ++f)
+            for (int c = 0; c < 3; ++c) kd.fib[f][c] = (double)kc.fib[f][c];
+        double Fd[9], Kd[D], Jd;
+        PolyChain<double> chd;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) Fd[c] = (double)F[c];
+        const bool ok = kin_scalars<double, NF>(Fd, kd, Kd, Jd, &chd);
+#pragma unroll
+        for (int m = 0; m < D; ++m) K[m] = (T)Kd[m];
+        Jm1 = (T)Jd;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            ch.d1[m] = (T)chd.d1[m];
+            ch.d2[m] = (T)chd.d2[m];
+        }
+        return ok;
+    }
+}
+
+// Kinematic scalars of a warp's next kKinTiles tiles (kKinTiles x kQPW = 32 points), one
+// point per lane. In the per-point code the four lanes of a point's group would each form
+// the same FP64 scalars, and GB300 bills an FP64 warp instruction to all 32 lanes whatever
+// the mask: formed here, once per point, they take a quarter of the FP64 instructions.
+// Lane l takes point l % kQPW of tile tile0 + (l / kQPW) tstep and writes, component-major
+// at rec[c * 32 + l]: K[D], J - 1, phi'[3], phi''[3] and 1 where F (or, WITH_G, G = dL/dP)
+// was inadmissible and the scalars are those of F = I (0 otherwise).
+constexpr int kKinTiles = 32 / kQPW;
+template <int NF>
+__host__ __device__ constexpr int kinrec_size() {
+    return 3 + 2 * NF + 8;
+}
+
+template <typename T, int NF, bool WITH_G>
+__device__ __forceinline__ void kin_batch(const T *__restrict__ Fg, const T *__restrict__ Gg, int64_t n_qp,
+                                          int64_t tile0, int64_t tstep, int64_t n_tiles, const KinConst<T> &kc,
+                                          T *rec, int lane) {
+    constexpr int D = 3 + 2 * NF;
+    const int64_t tile = tile0 + (int64_t)(lane / kQPW) * tstep;
+    const int64_t q = tile * kQPW + (lane % kQPW);
+    const bool valid = tile < n_tiles && q < n_qp;
+    T F[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) F[c] = valid ? Fg[c * n_qp + q] : ((c % 4) == 0 ? T(1) : T(0));
+    bool gbad = false;
+    if constexpr (WITH_G) {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) gbad = gbad || (valid && !dev_finite(Gg[c * n_qp + q]));
+    }
+    T K[D], Jm1;
+    PolyChain<T> ch{};
+    const bool bad = !kin_scalars_k64<T, NF>(F, kc, K, Jm1, ch) || gbad;
+    if (bad) {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) F[c] = (c % 4) == 0 ? T(1) : T(0);
+        kin_scalars_k64<T, NF>(F, kc, K, Jm1, ch);
+    }
+#pragma unroll
+    for (int m = 0; m < D; ++m) rec[m * 32 + lane] = K[m];
+    rec[D * 32 + lane] = Jm1;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        rec[(D + 1 + m) * 32 + lane] = ch.d1[m];
+        rec[(D + 4 + m) * 32 + lane] = ch.d2[m];
+    }
+    rec[(D + 7) * 32 + lane] = bad ? T(1) : T(0);
+}
+
+// The record of point r (0..31) of the last kin_batch; returns whether F = I was used.
+template <typename T, int NF>
+__device__ __forceinline__ bool kin_read(const T *rec, int r, T *K, T &Jm1, PolyChain<T> &ch) {
+    constexpr int D = 3 + 2 * NF;
+#pragma unroll
+    for (int m = 0; m < D; ++m) K[m] = rec[m * 32 + r];
+    Jm1 = rec[D * 32 + r];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        ch.d1[m] = rec[(D + 1 + m) * 32 + r];
+        ch.d2[m] = rec[(D + 4 + m) * 32 + r];
+    }
+    return rec[(D + 7) * 32 + r] != T(0);
+}
+
 // One input neuron's contribution to a lane's block of the layer tangent:
 //   acc[cc][m] += (w[cc] * scale) * v[m]      (scaled: k = 2, s_1 folded into the weight)
 //   acc[cc][m] +=  w[cc] * v[m]               (otherwise)
@@ -349,7 +447,8 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
                                                 const T *__restrict__ ar, const KinConst<T> &kc, T *qs, int qi,
                                                 int jb, T (&F)[9],
                                                 bool valid, T *Pq, int64_t pst, T *Aq, int64_t ast, T *dNq,
-                                                int64_t dst, T &psi_val, bool &report) {
+                                                int64_t dst, T &psi_val, bool &report, const T *krec = nullptr,
+                                                int kr = 0) {
     using Cf = CUConf<T, NF, W>;
     constexpr int D = Cf::D, DP = Cf::DP, NH = Cf::NH, NJ = Cf::NJ, NC = Cf::NC;
     const int L = lay.L;
@@ -358,11 +457,13 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
     const int j0 = jb * NJ;
     T K[D], Jm1;
     PolyChain<T> ch;
-    bool bad = !kin_scalars<T, NF>(F, kc, K, Jm1, &ch);
+    // the kinematic scalars: from the warp's batch record krec[.. kr ..] (kin_batch, FP64),
+    // else formed here
+    bool bad = krec != nullptr ? kin_read<T, NF>(krec, kr, K, Jm1, ch) : !kin_scalars<T, NF>(F, kc, K, Jm1, &ch);
     if (bad) {
 #pragma unroll
         for (int cpt = 0; cpt < 9; ++cpt) F[cpt] = (cpt % 4) == 0 ? T(1) : T(0);
-        kin_scalars<T, NF>(F, kc, K, Jm1, &ch);
+        if (krec == nullptr) kin_scalars<T, NF>(F, kc, K, Jm1, &ch);
     }
 
     const bool want_A = (Aq != nullptr);  // P alone needs neither F'' nor the tangents

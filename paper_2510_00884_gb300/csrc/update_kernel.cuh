@@ -25,7 +25,7 @@ template <typename T, int NF, int W, bool SPATIAL>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 384)
     const_update_kernel(const T *__restrict__ gw, NetLayout lay, KinConst<T> kc, int64_t n_qp,
                         const T *__restrict__ Fg, T *__restrict__ psi, T *__restrict__ P, T *__restrict__ A,
-                        int32_t *__restrict__ status, T *__restrict__ dN_out, int qstride, int wcount) {
+                        int32_t *__restrict__ status, T *__restrict__ dN_out, int qstride, int wcount, bool batch) {
     using Cf = CUConf<T, NF, W>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sw = reinterpret_cast<T *>(smem_raw);
@@ -48,8 +48,21 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 384)
     T *qs = sw + wbytes / (int)sizeof(T) + (size_t)(warp * kQPW + qi) * qstride;
     const int64_t n_tiles = (n_qp + kQPW - 1) / kQPW;
     const int64_t n_gwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    // FP64 with batch: the kinematic scalars of the warp's next kKinTiles tiles, one point
+    // per lane (kin_batch), in the warp's records after the point slabs
+    T *rec = sw + wbytes / (int)sizeof(T) + (size_t)(blockDim.x >> 5) * kQPW * qstride +
+             (size_t)warp * kinrec_size<NF>() * 32;
+    const bool use_rec = sizeof(T) == 8 && batch;
 
-    for (int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; tile < n_tiles; tile += n_gwarps) {
+    for (int64_t tile0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; tile0 < n_tiles;
+         tile0 += kKinTiles * n_gwarps) {
+      if (use_rec) kin_batch<T, NF, false>(Fg, nullptr, n_qp, tile0, n_gwarps, n_tiles, kc, rec, lane);
+      __syncwarp();
+      for (int sub = 0; sub < kKinTiles; ++sub) {
+        const int64_t tile = tile0 + sub * n_gwarps;
+        if (tile >= n_tiles) break;
+        const T *krec = use_rec ? rec : nullptr;
+        const int kr = sub * kQPW + qi;
         const int64_t q = tile * kQPW + qi;
         const bool valid = q < n_qp;
         T F[9];
@@ -62,12 +75,12 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 384)
             // P and A of the point go to its slab, then are pushed forward to tau (P) and c (A)
             T *pa = qs + qp_stage_end(Cf::D, NF);
             qp_group_update<T, NF, W>(sw, lay, mt, at, ar, kc, qs, qi, jb, F, valid, pa, 1, A ? pa + 9 : nullptr, 1, nullptr, 0,
-                                      psi_val, report);
+                                      psi_val, report, krec, kr);
             __syncwarp();
             push_forward_group<T>(qs + Stage<Cf::D, NF>::F, pa, pa + 9, jb, valid, P + qo, A ? A + qo : nullptr, n_qp);
         } else {
             qp_group_update<T, NF, W>(sw, lay, mt, at, ar, kc, qs, qi, jb, F, valid, P + qo, n_qp, A ? A + qo : nullptr, n_qp,
-                                      dN_out ? dN_out + qo : nullptr, n_qp, psi_val, report);
+                                      dN_out ? dN_out + qo : nullptr, n_qp, psi_val, report, krec, kr);
         }
         if (valid && jb == 0) {
             if (psi != nullptr) psi[q] = psi_val;
@@ -77,6 +90,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 384)
             }
         }
         __syncwarp();
+      }
     }
 }
 
@@ -118,7 +132,10 @@ static int launch_typed(const commet_model *m, int64_t n_qp, const void *F, void
     }
     const size_t wbytes = ((size_t)wcount * sizeof(T) + 15) / 16 * 16;
     if (warps < 1) return COMMET_ERR_UNSUPPORTED;
-    const size_t smem = wbytes + warps * per_warp;
+    // FP64: the batched kinematic scalars' records, where they fit beside the same warps
+    const size_t rec_bytes = (size_t)kinrec_size<NF>() * 32 * sizeof(T);
+    const bool batch = sizeof(T) == 8 && wbytes + warps * (per_warp + rec_bytes) <= (size_t)smem_max;
+    const size_t smem = wbytes + warps * (per_warp + (batch ? rec_bytes : 0));
     auto kern = const_update_kernel<T, NF, W, SPATIAL>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return COMMET_ERR_CUDA;
@@ -129,7 +146,7 @@ static int launch_typed(const commet_model *m, int64_t n_qp, const void *F, void
     const int64_t want = (n_tiles + warps - 1) / warps;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count() * per_sm));
     kern<<<grid, warps * 32, smem, s>>>((const T *)m->d_weights, m->lay, kc, n_qp, (const T *)F, (T *)psi, (T *)P,
-                                        (T *)A, status, (T *)dN_out, qstride, wcount);
+                                        (T *)A, status, (T *)dN_out, qstride, wcount, batch);
     return cudaGetLastError() == cudaSuccess ? COMMET_OK : COMMET_ERR_CUDA;
 }
 
