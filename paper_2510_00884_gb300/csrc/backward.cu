@@ -289,7 +289,7 @@ template <typename T, int NF, int W, int WARPS, bool GACC = false>
 __global__ void __launch_bounds__(WARPS * 32)
     const_backward_kernel(const T *__restrict__ gw, NetLayout lay, KinConst<T> kc, int64_t n_qp,
                           const T *__restrict__ Fg, const T *__restrict__ Gg, T *__restrict__ dFg,
-                          T *__restrict__ partial, int np_pad, BwSlab sl) {
+                          T *__restrict__ partial, int np_pad, BwSlab sl, bool batch) {
     constexpr int D = 3 + 2 * NF, NJ = W / kG;
     constexpr int Q = WARPS * kQPW;  // points per CTA tile
     static_assert(BwPre<D, NF>::size == 9 * D + 54 + 18 * NF + 5 + NF + 30 + 9 * NF,
@@ -329,7 +329,16 @@ __global__ void __launch_bounds__(WARPS * 32)
     const int oa = oL + (L - 1) * lsz, ob = oa + W;
 
     const int64_t n_tiles = (n_qp + Q - 1) / Q;
-    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    // FP64 with batch: the kinematic scalars of the warp's points in the CTA's next
+    // kKinTiles tiles, one point per lane (kin_batch), in the warp's records after the slabs
+    const bool use_rec = sizeof(T) == 8 && batch;
+    T *rec = slabs + (size_t)Q * sl.size + (size_t)warp * kinrec_size<NF>() * 32;
+    for (int64_t tile0 = blockIdx.x; tile0 < n_tiles; tile0 += (int64_t)kKinTiles * gridDim.x) {
+      if (use_rec) kin_batch<T, NF, true>(Fg, Gg, n_qp, tile0, gridDim.x, n_tiles, kc, rec, lane, Q, warp * kQPW);
+      __syncwarp();
+      for (int sub = 0; sub < kKinTiles; ++sub) {
+        const int64_t tile = tile0 + (int64_t)sub * gridDim.x;
+        if (tile >= n_tiles) break;
         const int64_t q = tile * Q + ql;
         const bool valid = q < n_qp;
         T F[9], G[9];
@@ -340,16 +349,21 @@ __global__ void __launch_bounds__(WARPS * 32)
         }
         T K[D], Jm1;
         PolyChain<T> ch;
-        bool bad = !kin_scalars<T, NF>(F, kc, K, Jm1, &ch);
+        bool bad;
+        if (use_rec) {
+            bad = kin_read<T, NF>(rec, sub * kQPW + qi, K, Jm1, ch);
+        } else {
+            bad = !kin_scalars<T, NF>(F, kc, K, Jm1, &ch);
 #pragma unroll
-        for (int c = 0; c < 9; ++c) bad = bad || !dev_finite(G[c]);
+            for (int c = 0; c < 9; ++c) bad = bad || !dev_finite(G[c]);
+        }
         if (bad) {
 #pragma unroll
             for (int c = 0; c < 9; ++c) {
                 F[c] = (c % 4) == 0 ? T(1) : T(0);
                 G[c] = T(0);
             }
-            kin_scalars<T, NF>(F, kc, K, Jm1, &ch);
+            if (!use_rec) kin_scalars<T, NF>(F, kc, K, Jm1, &ch);
         }
         const bool poly = NF == 0 && kc.kin == COMMET_KIN_POLYCONVEX;
         // r_m = G : g_m; the 4 lanes stage g (part 1, 2) and read it back
@@ -586,6 +600,7 @@ __global__ void __launch_bounds__(WARPS * 32)
             }
         }
         __syncthreads();
+      }
     }
     // write this CTA's partial sums (GACC: already in place)
     if constexpr (!GACC) {
@@ -847,17 +862,21 @@ static int bw_launch(const commet_model *m, int64_t n_qp, const void *F, const v
     const int np_pad = np_padded(m);
     const int msz = m->lay.M ? m->lay.Ar - m->lay.M : 0;  // M is not used here (global memory)
     const size_t wbytes = ((size_t)((GACC ? m->lay.Ar : m->lay.total) - msz) * sizeof(T) + 15) / 16 * 16;
-    const size_t smem = wbytes + (GACC ? 0 : (size_t)np_pad * sizeof(T)) + (size_t)Q * sl.size * sizeof(T);
+    const size_t smem0 = wbytes + (GACC ? 0 : (size_t)np_pad * sizeof(T)) + (size_t)Q * sl.size * sizeof(T);
     int dev = 0, smem_max = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (smem > (size_t)smem_max) return COMMET_ERR_UNSUPPORTED;
+    if (smem0 > (size_t)smem_max) return COMMET_ERR_UNSUPPORTED;
+    // FP64: the batched kinematic scalars' records, where they fit beside the slabs
+    const size_t rec_bytes = (size_t)WARPS * kinrec_size<NF>() * 32 * sizeof(T);
+    const bool batch = sizeof(T) == 8 && smem0 + rec_bytes <= (size_t)smem_max;
+    const size_t smem = smem0 + (batch ? rec_bytes : 0);
     auto kern = const_backward_kernel<T, NF, W, WARPS, GACC>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return COMMET_ERR_CUDA;
     const int grid = bw_grid(m, n_qp, Q);
     kern<<<grid, WARPS * 32, smem, s>>>((const T *)m->d_weights, m->lay, kc, n_qp, (const T *)F,
-                                                   (const T *)G, (T *)dF, (T *)ws, np_pad, sl);
+                                                   (const T *)G, (T *)dF, (T *)ws, np_pad, sl, batch);
     if (cudaGetLastError() != cudaSuccess) return COMMET_ERR_CUDA;
     const int np = (int)np_net(m);
     reduce_partials_kernel<T><<<(np + 255) / 256, 256, 0, s>>>((const T *)ws, grid, np, np_pad, (T *)dth,

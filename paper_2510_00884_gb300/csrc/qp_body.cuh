@@ -166,7 +166,8 @@ __device__ __forceinline__ bool kin_scalars_k64(const T (&F)[9], const KinConst<
 // point per lane. In the per-point code the four lanes of a point's group would each form
 // the same FP64 scalars, and GB300 bills an FP64 warp instruction to all 32 lanes whatever
 // the mask: formed here, once per point, they take a quarter of the FP64 instructions.
-// Lane l takes point l % kQPW of tile tile0 + (l / kQPW) tstep and writes, component-major
+// Lane l takes point off + l % kQPW of tile tile0 + (l / kQPW) tstep (tiles of tile_pts
+// points: kQPW for a warp's own tiles, the CTA's for a CTA tile) and writes, component-major
 // at rec[c * 32 + l]: K[D], J - 1, phi'[3], phi''[3] and 1 where F (or, WITH_G, G = dL/dP)
 // was inadmissible and the scalars are those of F = I (0 otherwise).
 constexpr int kKinTiles = 32 / kQPW;
@@ -178,10 +179,10 @@ __host__ __device__ constexpr int kinrec_size() {
 template <typename T, int NF, bool WITH_G>
 __device__ __forceinline__ void kin_batch(const T *__restrict__ Fg, const T *__restrict__ Gg, int64_t n_qp,
                                           int64_t tile0, int64_t tstep, int64_t n_tiles, const KinConst<T> &kc,
-                                          T *rec, int lane) {
+                                          T *rec, int lane, int tile_pts = kQPW, int off = 0) {
     constexpr int D = 3 + 2 * NF;
     const int64_t tile = tile0 + (int64_t)(lane / kQPW) * tstep;
-    const int64_t q = tile * kQPW + (lane % kQPW);
+    const int64_t q = tile * tile_pts + off + (lane % kQPW);
     const bool valid = tile < n_tiles && q < n_qp;
     T F[9];
 #pragma unroll
