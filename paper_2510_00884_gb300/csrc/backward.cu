@@ -678,10 +678,11 @@ __global__ void __launch_bounds__(kCannBwWarps * 32, (sizeof(T) == 4 && NF == 0)
     // the warp's kinematic records after the point slabs (FP64 with fibres: no room beside
     // its slabs, the scalars are formed per point)
     constexpr bool kBatch = cann_bw_batches<T, NF>();
-    T *rec = slabs + (size_t)kCannBwWarps * kQPW * qstride + (size_t)warp * kinrec_size<NF>() * 32;
+    constexpr bool kPre = kBatch && sizeof(T) == 8;  // FP64 records also hold the staging's scalars
+    T *rec = slabs + (size_t)kCannBwWarps * kQPW * qstride + (size_t)warp * kinrec_size<NF, kPre>() * 32;
 
     for (int64_t tile0 = (int64_t)blockIdx.x * kCannBwWarps + warp; tile0 < n_tiles; tile0 += kKinTiles * n_gwarps) {
-      if constexpr (kBatch) kin_batch<T, NF, true>(Fg, Gg, n_qp, tile0, n_gwarps, n_tiles, kc, rec, lane);
+      if constexpr (kBatch) kin_batch<T, NF, true, kPre>(Fg, Gg, n_qp, tile0, n_gwarps, n_tiles, kc, rec, lane);
       __syncwarp();
       for (int sub = 0; sub < kKinTiles; ++sub) {
         const int64_t tile = tile0 + sub * n_gwarps;
@@ -722,7 +723,8 @@ __global__ void __launch_bounds__(kCannBwWarps * 32, (sizeof(T) == 4 && NF == 0)
         T psi_val;
         bool report;
         qp_group_finish<T, NF>(sw + lay.n0, sw + lay.K0, kc, qs, qi, jb, F, K, Jm1, ch, bad, valid, npart, dN, Hs,
-                               true, pa, 1, pa + 9, 1, nullptr, 0, psi_val, report);
+                               true, pa, 1, pa + 9, 1, nullptr, 0, psi_val, report,
+                               kPre ? kin_pre<T, NF>(rec, sub * kQPW + qi) : nullptr);
         __syncwarp();
         // dL/dF by columns b = jb, jb + 4, jb + 8
         T dfv[3];
@@ -935,7 +937,7 @@ static int cann_bw_launch(const commet_model *m, int64_t n_qp, const void *F, co
     const int np_pad = np_padded(m);
     const size_t wbytes = ((size_t)m->lay.total * sizeof(T) + 15) / 16 * 16;
     const size_t smem = wbytes + (size_t)kCannBwWarps * np_pad * sizeof(T) +
-                        (size_t)kCannBwWarps * (kQPW * qstride + (cann_bw_batches<T, NF>() ? kinrec_size<NF>() * 32 : 0)) *
+                        (size_t)kCannBwWarps * (kQPW * qstride + (cann_bw_batches<T, NF>() ? kinrec_size<NF, cann_bw_batches<T, NF>() && sizeof(T) == 8>() * 32 : 0)) *
                             sizeof(T);
     int dev = 0, smem_max = 0;
     cudaGetDevice(&dev);

@@ -298,11 +298,11 @@ __global__ void __launch_bounds__(256)
     // the warp's kinematic records after the point slabs (batch: when they fit in shared
     // memory; otherwise the scalars are formed per point)
     T *rec = sw + wbytes / (int)sizeof(T) + (size_t)(blockDim.x >> 5) * kQPW * qstride +
-             (size_t)warp * kinrec_size<NF>() * 32;
+             (size_t)warp * kinrec_size<NF, sizeof(T) == 8>() * 32;
 
     for (int64_t tile0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; tile0 < n_tiles;
          tile0 += kKinTiles * n_gwarps) {
-      if (batch) kin_batch<T, NF, false>(Fg, nullptr, n_qp, tile0, n_gwarps, n_tiles, kc, rec, lane);
+      if (batch) kin_batch<T, NF, false, sizeof(T) == 8>(Fg, nullptr, n_qp, tile0, n_gwarps, n_tiles, kc, rec, lane);
       __syncwarp();
       for (int sub = 0; sub < kKinTiles; ++sub) {
         const int64_t tile = tile0 + sub * n_gwarps;
@@ -345,17 +345,18 @@ __global__ void __launch_bounds__(256)
         }
         T psi_val;
         bool report;
+        const T *pre = (sizeof(T) == 8 && batch) ? kin_pre<T, NF>(rec, sub * kQPW + qi) : nullptr;
         if constexpr (SPATIAL) {
             T *pa = qs + qp_stage_end(D, NF);
             qp_group_finish<T, NF>(sw + lay.n0, sw + lay.K0, kc, qs, qi, jb, F, K, Jm1, ch, bad, valid, npart, dN, Hs,
-                                   want_A, pa, 1, want_A ? pa + 9 : nullptr, 1, nullptr, 0, psi_val, report);
+                                   want_A, pa, 1, want_A ? pa + 9 : nullptr, 1, nullptr, 0, psi_val, report, pre);
             __syncwarp();
             push_forward_group<T>(qs + Stage<D, NF>::F, pa, pa + 9, jb, valid, P + qo, want_A ? A + qo : nullptr,
                                   n_qp);
         } else {
             qp_group_finish<T, NF>(sw + lay.n0, sw + lay.K0, kc, qs, qi, jb, F, K, Jm1, ch, bad, valid, npart, dN, Hs,
                                    want_A, P + qo, n_qp, want_A ? A + qo : nullptr, n_qp,
-                                   dN_out ? dN_out + qo : nullptr, n_qp, psi_val, report);
+                                   dN_out ? dN_out + qo : nullptr, n_qp, psi_val, report, pre);
         }
         if (valid && jb == 0) {
             if (psi != nullptr) psi[q] = psi_val;
@@ -384,7 +385,7 @@ static int launch_closed(const commet_model *m, int64_t n_qp, const void *F, voi
     const size_t wbytes = ((size_t)m->lay.total * sizeof(T) + 15) / 16 * 16;
     const int warps = 8;
     const size_t smem_pt = wbytes + (size_t)warps * kQPW * qstride * sizeof(T);
-    const size_t smem_b = smem_pt + (size_t)warps * kinrec_size<NF>() * 32 * sizeof(T);
+    const size_t smem_b = smem_pt + (size_t)warps * kinrec_size<NF, sizeof(T) == 8>() * 32 * sizeof(T);
     int dev = 0, smem_max = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

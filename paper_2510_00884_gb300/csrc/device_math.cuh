@@ -262,21 +262,32 @@ struct Stage {
 // every lane of the warp). Scalars and the fibre vectors a = F A, v = C A, F v are formed
 // in every lane. c[] = dN/dK - n0; Jm1 = J - 1 from det_minus_one. With G_ONLY, only what
 // P needs is staged: the kinematic gradients g_m, F, F^{-T} and 2 kappa (J - 1) J.
+// pre (FP64, optional): C[9], I1, I2 and J^(-1/3) of this F already formed, at stride 32
+// (a batch record, see kin_batch), instead of forming them in every lane.
 template <typename T, int NF, bool G_ONLY = false>
 __device__ __forceinline__ void stage_kinematics(const T *F, const KinConst<T> &kc, const T *c, T Jm1, int lane4,
-                                                 T *st) {
+                                                 T *st, const T *pre = nullptr) {
     constexpr int D = 3 + 2 * NF;
     using S = Stage<D, NF>;
     T C[9];
-    right_cg(F, C);
     // FP32 (bound by latency, not by FP64 instructions) forms the cofactor matrix in
     // straight-line code; FP64 lanes form only their own entries below
     T cof[9], Jc;
     if constexpr (sizeof(T) != 8) cof_det(F, cof, Jc);
     const T J = T(1) + Jm1;
-    const T I1 = C[0] + C[4] + C[8];
-    const T I2 = second_invariant(C);
-    const T r3 = dev_rcbrt(J);
+    T I1, I2, r3;
+    if (pre != nullptr) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) C[i] = pre[i * 32];
+        I1 = pre[9 * 32];
+        I2 = pre[10 * 32];
+        r3 = pre[11 * 32];
+    } else {
+        right_cg(F, C);
+        I1 = C[0] + C[4] + C[8];
+        I2 = second_invariant(C);
+        r3 = dev_rcbrt(J);
+    }
     const T jm23 = r3 * r3, jm43 = jm23 * jm23;
     const T iJ = jm23 * r3;  // 1/J = (J^(-1/3))^3
     const T p1 = T(-2) / T(3), p2 = T(-4) / T(3);

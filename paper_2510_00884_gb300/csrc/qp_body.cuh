@@ -166,17 +166,18 @@ __device__ __forceinline__ bool kin_scalars_k64(const T (&F)[9], const KinConst<
 // point per lane. In the per-point code the four lanes of a point's group would each form
 // the same FP64 scalars, and GB300 bills an FP64 warp instruction to all 32 lanes whatever
 // the mask: formed here, once per point, they take a quarter of the FP64 instructions.
-// Lane l takes point off + l % kQPW of tile tile0 + (l / kQPW) tstep (tiles of tile_pts
+// With PRE (FP64) the record also holds, after those, C[9], I1, I2 and J^(-1/3) of the
+// same F for stage_kinematics. Lane l takes point off + l % kQPW of tile tile0 + (l / kQPW) tstep (tiles of tile_pts
 // points: kQPW for a warp's own tiles, the CTA's for a CTA tile) and writes, component-major
 // at rec[c * 32 + l]: K[D], J - 1, phi'[3], phi''[3] and 1 where F (or, WITH_G, G = dL/dP)
 // was inadmissible and the scalars are those of F = I (0 otherwise).
 constexpr int kKinTiles = 32 / kQPW;
-template <int NF>
+template <int NF, bool PRE = false>
 __host__ __device__ constexpr int kinrec_size() {
-    return 3 + 2 * NF + 8;
+    return 3 + 2 * NF + 8 + (PRE ? 12 : 0);
 }
 
-template <typename T, int NF, bool WITH_G>
+template <typename T, int NF, bool WITH_G, bool PRE = false>
 __device__ __forceinline__ void kin_batch(const T *__restrict__ Fg, const T *__restrict__ Gg, int64_t n_qp,
                                           int64_t tile0, int64_t tstep, int64_t n_tiles, const KinConst<T> &kc,
                                           T *rec, int lane, int tile_pts = kQPW, int off = 0) {
@@ -209,6 +210,22 @@ __device__ __forceinline__ void kin_batch(const T *__restrict__ Fg, const T *__r
         rec[(D + 4 + m) * 32 + lane] = ch.d2[m];
     }
     rec[(D + 7) * 32 + lane] = bad ? T(1) : T(0);
+    if constexpr (PRE) {
+        // as stage_kinematics forms them (the same F, replaced by I where bad)
+        T C[9];
+        right_cg(F, C);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) rec[(D + 8 + i) * 32 + lane] = C[i];
+        rec[(D + 17) * 32 + lane] = C[0] + C[4] + C[8];
+        rec[(D + 18) * 32 + lane] = second_invariant(C);
+        rec[(D + 19) * 32 + lane] = dev_rcbrt(T(1) + Jm1);
+    }
+}
+
+// Where point r's stage_kinematics values sit in a PRE record (stride 32).
+template <typename T, int NF>
+__device__ __forceinline__ const T *kin_pre(const T *rec, int r) {
+    return rec + (3 + 2 * NF + 8) * 32 + r;
 }
 
 // The record of point r (0..31) of the last kin_batch; returns whether F = I was used.
@@ -269,7 +286,8 @@ __device__ __forceinline__ void qp_group_finish(const T *n0s, const T *K0s, cons
                                                 int jb, const T (&F)[9], const T *K, T Jm1,
                                                 const PolyChain<T> &ch, bool bad, bool valid, T npart, T *dN,
                                                 T *Hs, bool want_A, T *Pq, int64_t pst, T *Aq, int64_t ast,
-                                                T *dNq, int64_t dst, T &psi_val, bool &report) {
+                                                T *dNq, int64_t dst, T &psi_val, bool &report,
+                                                const T *pre = nullptr) {
     constexpr int D = 3 + 2 * NF, DP = (D + 3) / 4 * 4, NH = D * (D + 1) / 2;
     // ---- reduce the group's partial sums
 #pragma unroll
@@ -305,9 +323,9 @@ __device__ __forceinline__ void qp_group_finish(const T *n0s, const T *K0s, cons
         if (kc.kin == COMMET_KIN_POLYCONVEX) poly_to_invariants<T>(ch, cvec, Hs);
     }
     if (want_A)
-        stage_kinematics<T, NF>(F, kc, cvec, Jm1, jb, qs);
+        stage_kinematics<T, NF>(F, kc, cvec, Jm1, jb, qs, pre);
     else
-        stage_kinematics<T, NF, true>(F, kc, cvec, Jm1, jb, qs);  // what P (and tau) need
+        stage_kinematics<T, NF, true>(F, kc, cvec, Jm1, jb, qs, pre);  // what P (and tau) need
     using S = Stage<D, NF>;
     constexpr int UOFF = (S::size + 3) / 4 * 4;  // u_a = sum_m g_m[a] N_mn : [9][DP]
     constexpr int HOFF = UOFF + 9 * DP;          // d2N/dK2, full: [D][DP]
@@ -696,8 +714,10 @@ __device__ __forceinline__ void qp_group_update(const T *__restrict__ sw, const 
         }
     }  // want_A
 
+    // an FP64 batch record (PRE) also holds the staging's C, I1, I2 and J^(-1/3)
+    const T *pre = (sizeof(T) == 8 && krec != nullptr) ? kin_pre<T, NF>(krec, kr) : nullptr;
     qp_group_finish<T, NF>(sw + lay.n0, sw + lay.K0, kc, qs, qi, jb, F, K, Jm1, ch, bad, valid, npart, dN, Hs,
-                           want_A, Pq, pst, Aq, ast, dNq, dst, psi_val, report);
+                           want_A, Pq, pst, Aq, ast, dNq, dst, psi_val, report, pre);
 }
 
 }  // namespace commet

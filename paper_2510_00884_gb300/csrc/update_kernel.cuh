@@ -51,12 +51,12 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 384)
     // FP64 with batch: the kinematic scalars of the warp's next kKinTiles tiles, one point
     // per lane (kin_batch), in the warp's records after the point slabs
     T *rec = sw + wbytes / (int)sizeof(T) + (size_t)(blockDim.x >> 5) * kQPW * qstride +
-             (size_t)warp * kinrec_size<NF>() * 32;
+             (size_t)warp * kinrec_size<NF, true>() * 32;
     const bool use_rec = sizeof(T) == 8 && batch;
 
     for (int64_t tile0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; tile0 < n_tiles;
          tile0 += kKinTiles * n_gwarps) {
-      if (use_rec) kin_batch<T, NF, false>(Fg, nullptr, n_qp, tile0, n_gwarps, n_tiles, kc, rec, lane);
+      if (use_rec) kin_batch<T, NF, false, true>(Fg, nullptr, n_qp, tile0, n_gwarps, n_tiles, kc, rec, lane);
       __syncwarp();
       for (int sub = 0; sub < kKinTiles; ++sub) {
         const int64_t tile = tile0 + sub * n_gwarps;
@@ -133,7 +133,7 @@ static int launch_typed(const commet_model *m, int64_t n_qp, const void *F, void
     const size_t wbytes = ((size_t)wcount * sizeof(T) + 15) / 16 * 16;
     if (warps < 1) return COMMET_ERR_UNSUPPORTED;
     // FP64: the batched kinematic scalars' records, where they fit beside the same warps
-    const size_t rec_bytes = (size_t)kinrec_size<NF>() * 32 * sizeof(T);
+    const size_t rec_bytes = (size_t)kinrec_size<NF, true>() * 32 * sizeof(T);
     const bool batch = sizeof(T) == 8 && wbytes + warps * (per_warp + rec_bytes) <= (size_t)smem_max;
     const size_t smem = wbytes + warps * (per_warp + (batch ? rec_bytes : 0));
     auto kern = const_update_kernel<T, NF, W, SPATIAL>;
