@@ -334,273 +334,274 @@ __global__ void __launch_bounds__(WARPS * 32)
     const bool use_rec = sizeof(T) == 8 && batch;
     T *rec = slabs + (size_t)Q * sl.size + (size_t)warp * kinrec_size<NF>() * 32;
     for (int64_t tile0 = blockIdx.x; tile0 < n_tiles; tile0 += (int64_t)kKinTiles * gridDim.x) {
-      if (use_rec) kin_batch<T, NF, true>(Fg, Gg, n_qp, tile0, gridDim.x, n_tiles, kc, rec, lane, Q, warp * kQPW);
-      __syncwarp();
-      for (int sub = 0; sub < kKinTiles; ++sub) {
-        const int64_t tile = tile0 + (int64_t)sub * gridDim.x;
-        if (tile >= n_tiles) break;
-        const int64_t q = tile * Q + ql;
-        const bool valid = q < n_qp;
-        T F[9], G[9];
-#pragma unroll
-        for (int c = 0; c < 9; ++c) {
-            F[c] = valid ? Fg[c * n_qp + q] : ((c % 4) == 0 ? T(1) : T(0));
-            G[c] = valid ? Gg[c * n_qp + q] : T(0);
-        }
-        T K[D], Jm1;
-        PolyChain<T> ch;
-        bool bad;
-        if (use_rec) {
-            bad = kin_read<T, NF>(rec, sub * kQPW + qi, K, Jm1, ch);
-        } else {
-            bad = !kin_scalars<T, NF>(F, kc, K, Jm1, &ch);
-#pragma unroll
-            for (int c = 0; c < 9; ++c) bad = bad || !dev_finite(G[c]);
-        }
-        if (bad) {
+        if (use_rec) kin_batch<T, NF, true>(Fg, Gg, n_qp, tile0, gridDim.x, n_tiles, kc, rec, lane, Q, warp * kQPW);
+        __syncwarp();
+        for (int sub = 0; sub < kKinTiles; ++sub) {
+            const int64_t tile = tile0 + (int64_t)sub * gridDim.x;
+            if (tile >= n_tiles) break;
+            const int64_t q = tile * Q + ql;
+            const bool valid = q < n_qp;
+            T F[9], G[9];
 #pragma unroll
             for (int c = 0; c < 9; ++c) {
-                F[c] = (c % 4) == 0 ? T(1) : T(0);
-                G[c] = T(0);
+                F[c] = valid ? Fg[c * n_qp + q] : ((c % 4) == 0 ? T(1) : T(0));
+                G[c] = valid ? Gg[c * n_qp + q] : T(0);
             }
-            if (!use_rec) kin_scalars<T, NF>(F, kc, K, Jm1, &ch);
-        }
-        const bool poly = NF == 0 && kc.kin == COMMET_KIN_POLYCONVEX;
-        // r_m = G : g_m; the 4 lanes stage g (part 1, 2) and read it back
-        {
-            T zero[D];
+            T K[D], Jm1;
+            PolyChain<T> ch;
+            bool bad;
+            if (use_rec) {
+                bad = kin_read<T, NF>(rec, sub * kQPW + qi, K, Jm1, ch);
+            } else {
+                bad = !kin_scalars<T, NF>(F, kc, K, Jm1, &ch);
 #pragma unroll
-            for (int m = 0; m < D; ++m) zero[m] = T(0);
-            stage_kinematics<T, NF, true>(F, kc, zero, Jm1, jb, qs);
-        }
-        T r[D];
-        {
-            // G goes next to the staged g_m (the F slot is free here); lane jb sums the
-            // components a = jb + 4 t, and the group adds the four partial sums
-            using S = Stage<D, NF>;
-            T *Gs = qs + S::F;
+                for (int c = 0; c < 9; ++c) bad = bad || !dev_finite(G[c]);
+            }
+            if (bad) {
 #pragma unroll
-            for (int a = 0; a < 9; ++a)
-                if ((a & 3) == jb) Gs[a] = G[a];
-            __syncwarp();
-#pragma unroll
-            for (int m = 0; m < D; ++m) r[m] = T(0);
-#pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                const int a = jb + 4 * t;
-                if (a < 9) {
-                    const T g = Gs[a];
-#pragma unroll
-                    for (int m = 0; m < D; ++m) r[m] += g * qs[S::g + 9 * m + a];
+                for (int c = 0; c < 9; ++c) {
+                    F[c] = (c % 4) == 0 ? T(1) : T(0);
+                    G[c] = T(0);
                 }
+                if (!use_rec) kin_scalars<T, NF>(F, kc, K, Jm1, &ch);
             }
+            const bool poly = NF == 0 && kc.kin == COMMET_KIN_POLYCONVEX;
+            // r_m = G : g_m; the 4 lanes stage g (part 1, 2) and read it back
+            {
+                T zero[D];
+#pragma unroll
+                for (int m = 0; m < D; ++m) zero[m] = T(0);
+                stage_kinematics<T, NF, true>(F, kc, zero, Jm1, jb, qs);
+            }
+            T r[D];
+            {
+                // G goes next to the staged g_m (the F slot is free here); lane jb sums the
+                // components a = jb + 4 t, and the group adds the four partial sums
+                using S = Stage<D, NF>;
+                T *Gs = qs + S::F;
+#pragma unroll
+                for (int a = 0; a < 9; ++a)
+                    if ((a & 3) == jb) Gs[a] = G[a];
+                __syncwarp();
+#pragma unroll
+                for (int m = 0; m < D; ++m) r[m] = T(0);
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    const int a = jb + 4 * t;
+                    if (a < 9) {
+                        const T g = Gs[a];
+#pragma unroll
+                        for (int m = 0; m < D; ++m) r[m] += g * qs[S::g + 9 * m + a];
+                    }
+                }
+#pragma unroll
+                for (int msk = 1; msk <= 2; msk <<= 1)
+#pragma unroll
+                    for (int m = 0; m < D; ++m) r[m] += __shfl_xor_sync(0xffffffffu, r[m], msk);
+            }
+            // polyconvex layer: g_m above are invariant derivatives; the network sees
+            // r_K = phi' r_I, and r_I is kept for the chain rule's second-order term
+            T rI[D];
+#pragma unroll
+            for (int m = 0; m < D; ++m) rI[m] = r[m];
+            if (poly) {
+#pragma unroll
+                for (int m = 0; m < 3; ++m) r[m] *= ch.d1[m];
+            }
+            __syncwarp();
+            if (jb == 0) {
+#pragma unroll
+                for (int m = 0; m < D; ++m) {
+                    qs[sl.K + m] = K[m];
+                    qs[sl.r + m] = r[m];
+                }
+                qs[sl.K + D] = T(1);  // the bias column of tile_outer_rows2
+                qs[sl.r + D] = T(0);
+            }
+            __syncwarp();
+
+            // ---- forward: values and tangents along r
+            constexpr int V = 16 / (int)sizeof(T);  // elements per 128-bit shared load
+            for (int k = 1; k <= L; ++k) {
+                T y[NJ], yd[NJ];
+                ldv<NJ>(sw + lay.c + (k - 1) * W + j0, y);
+#pragma unroll
+                for (int jj = 0; jj < NJ; ++jj) yd[jj] = T(0);
+                if (k == 1) {
+#pragma unroll
+                    for (int m = 0; m < D; ++m) {
+                        T w[NJ];
+                        ldv<NJ>(sw + lay.W1t + m * W + j0, w);
+#pragma unroll
+                        for (int jj = 0; jj < NJ; ++jj) {
+                            y[jj] += w[jj] * K[m];
+                            yd[jj] += w[jj] * r[m];
+                        }
+                    }
+                } else {
+                    const T *zin = qs + sl.z + (k - 2) * W, *zdin = qs + sl.zd + (k - 2) * W;
+                    const T *At = sw + lay.At + (k - 2) * W * W + j0;
+#pragma unroll 2
+                    for (int i = 0; i < W; i += V) {
+                        T zv[V], zdv[V];
+                        ldv<V>(zin + i, zv);
+                        ldv<V>(zdin + i, zdv);
+#pragma unroll
+                        for (int u = 0; u < V; ++u) {
+                            T w[NJ];
+                            ldv<NJ>(At + (i + u) * W, w);
+#pragma unroll
+                            for (int jj = 0; jj < NJ; ++jj) {
+                                y[jj] += w[jj] * zv[u];
+                                yd[jj] += w[jj] * zdv[u];
+                            }
+                        }
+                    }
+                    const T *Bt = sw + lay.Bt + (k - 2) * D * W + j0;
+#pragma unroll
+                    for (int m = 0; m < D; ++m) {
+                        T w[NJ];
+                        ldv<NJ>(Bt + m * W, w);
+#pragma unroll
+                        for (int jj = 0; jj < NJ; ++jj) {
+                            y[jj] += w[jj] * K[m];
+                            yd[jj] += w[jj] * r[m];
+                        }
+                    }
+                }
+                T zv[NJ], sv[NJ], tv[NJ], zdv[NJ];
+#pragma unroll
+                for (int jj = 0; jj < NJ; ++jj) {
+                    if constexpr (sizeof(T) == 8)
+                        act_tab(y[jj], zv[jj], sv[jj], tv[jj], sw + lay.tab);
+                    else
+                        act(y[jj], zv[jj], sv[jj], tv[jj]);
+                    zdv[jj] = sv[jj] * yd[jj];
+                }
+                stv<NJ>(qs + sl.s + (k - 1) * W + j0, sv);
+                stv<NJ>(qs + sl.t + (k - 1) * W + j0, tv);
+                stv<NJ>(qs + sl.yd + (k - 1) * W + j0, yd);
+                if (k < L) {
+                    stv<NJ>(qs + sl.z + (k - 1) * W + j0, zv);
+                    stv<NJ>(qs + sl.zd + (k - 1) * W + j0, zdv);
+                } else {
+                    stv<NJ>(qs + sl.zdL + j0, zdv);
+                }
+                __syncwarp();
+            }
+
+            // ---- reverse over the tangent computation
+            T zb[NJ], zdb[NJ];
+            ldv<NJ>(sw + lay.a + j0, zdb);
+#pragma unroll
+            for (int jj = 0; jj < NJ; ++jj) zb[jj] = T(0);
+            T Hr[D], dN[D];
+#pragma unroll
+            for (int m = 0; m < D; ++m) {
+                Hr[m] = T(0);
+                dN[m] = (jb == 0) ? sw[lay.b + m] : T(0);
+            }
+            for (int k = L; k >= 1; --k) {
+                const T *Bt = (k == 1) ? (sw + lay.W1t + j0) : (sw + lay.Bt + (k - 2) * D * W + j0);
+                {
+                    T sv[NJ], tv[NJ], ydv[NJ], ybv[NJ], ydbv[NJ];
+                    ldv<NJ>(qs + sl.s + (k - 1) * W + j0, sv);
+                    ldv<NJ>(qs + sl.t + (k - 1) * W + j0, tv);
+                    ldv<NJ>(qs + sl.yd + (k - 1) * W + j0, ydv);
+#pragma unroll
+                    for (int jj = 0; jj < NJ; ++jj) {
+                        ydbv[jj] = sv[jj] * zdb[jj];
+                        ybv[jj] = sv[jj] * zb[jj] + tv[jj] * ydv[jj] * zdb[jj];
+                    }
+                    stv<NJ>(qs + sl.yb + j0, ybv);
+                    stv<NJ>(qs + sl.ydb + j0, ydbv);
+#pragma unroll
+                    for (int m = 0; m < D; ++m) {
+                        T w[NJ];
+                        ldv<NJ>(Bt + m * W, w);
+#pragma unroll
+                        for (int jj = 0; jj < NJ; ++jj) {
+                            Hr[m] += w[jj] * ybv[jj];
+                            dN[m] += w[jj] * ydbv[jj];
+                        }
+                    }
+                }
+                __syncthreads();
+                // tile reductions of this layer's weight gradients
+                const T *base = slabs;
+                if (k == 1) {
+                    // W1 and c_1 (adjacent: oc1 = oW1 + W D)
+                    tile_outer_rows2<T>(acc + oW1, W, D, base, sl.size, sl.yb, sl.K, sl.ydb, sl.r, Q);
+                } else {
+                    const int o = oL + (k - 2) * lsz;
+                    tile_outer_sq<T>(acc + o, W, base, sl.size, sl.yb, sl.z + (k - 2) * W, sl.ydb,
+                                     sl.zd + (k - 2) * W, Q);
+                    // B_k and c_k
+                    tile_outer_rows2<T>(acc + o + W * W, W, D, base, sl.size, sl.yb, sl.K, sl.ydb, sl.r, Q);
+                    // zbar_{k-1} = A_k^T ybar_k, zdotbar_{k-1} = A_k^T ydotbar_k for own neurons
+                    const T *Ar = arw + (k - 2) * W * W + j0;
+#pragma unroll
+                    for (int ii = 0; ii < NJ; ++ii) {
+                        zb[ii] = T(0);
+                        zdb[ii] = T(0);
+                    }
+#pragma unroll 2
+                    for (int j = 0; j < W; j += V) {
+                        T ybv[V], ydbv[V];
+                        ldv<V>(qs + sl.yb + j, ybv);
+                        ldv<V>(qs + sl.ydb + j, ydbv);
+#pragma unroll
+                        for (int u = 0; u < V; ++u) {
+                            T w[NJ];
+                            ldv<NJ>(Ar + (j + u) * W, w);
+#pragma unroll
+                            for (int ii = 0; ii < NJ; ++ii) {
+                                zb[ii] += w[ii] * ybv[u];
+                                zdb[ii] += w[ii] * ydbv[u];
+                            }
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+            tile_sum<T>(acc + oa, W, slabs, sl.size, sl.zdL, Q, 0);
+            tile_sum<T>(acc + ob, D, slabs, sl.size, sl.r, Q, blockDim.x > 32 ? 32 : 0);
+
+            // ---- dL/dF = sum_n (Hr)_n g_n + G : S (structured part)
 #pragma unroll
             for (int msk = 1; msk <= 2; msk <<= 1)
 #pragma unroll
-                for (int m = 0; m < D; ++m) r[m] += __shfl_xor_sync(0xffffffffu, r[m], msk);
-        }
-        // polyconvex layer: g_m above are invariant derivatives; the network sees
-        // r_K = phi' r_I, and r_I is kept for the chain rule's second-order term
-        T rI[D];
-#pragma unroll
-        for (int m = 0; m < D; ++m) rI[m] = r[m];
-        if (poly) {
-#pragma unroll
-            for (int m = 0; m < 3; ++m) r[m] *= ch.d1[m];
-        }
-        __syncwarp();
-        if (jb == 0) {
-#pragma unroll
-            for (int m = 0; m < D; ++m) {
-                qs[sl.K + m] = K[m];
-                qs[sl.r + m] = r[m];
-            }
-            qs[sl.K + D] = T(1);  // the bias column of tile_outer_rows2
-            qs[sl.r + D] = T(0);
-        }
-        __syncwarp();
-
-        // ---- forward: values and tangents along r
-        constexpr int V = 16 / (int)sizeof(T);  // elements per 128-bit shared load
-        for (int k = 1; k <= L; ++k) {
-            T y[NJ], yd[NJ];
-            ldv<NJ>(sw + lay.c + (k - 1) * W + j0, y);
-#pragma unroll
-            for (int jj = 0; jj < NJ; ++jj) yd[jj] = T(0);
-            if (k == 1) {
-#pragma unroll
                 for (int m = 0; m < D; ++m) {
-                    T w[NJ];
-                    ldv<NJ>(sw + lay.W1t + m * W + j0, w);
-#pragma unroll
-                    for (int jj = 0; jj < NJ; ++jj) {
-                        y[jj] += w[jj] * K[m];
-                        yd[jj] += w[jj] * r[m];
-                    }
+                    Hr[m] += __shfl_xor_sync(0xffffffffu, Hr[m], msk);
+                    dN[m] += __shfl_xor_sync(0xffffffffu, dN[m], msk);
                 }
-            } else {
-                const T *zin = qs + sl.z + (k - 2) * W, *zdin = qs + sl.zd + (k - 2) * W;
-                const T *At = sw + lay.At + (k - 2) * W * W + j0;
-#pragma unroll 2
-                for (int i = 0; i < W; i += V) {
-                    T zv[V], zdv[V];
-                    ldv<V>(zin + i, zv);
-                    ldv<V>(zdin + i, zdv);
+            __syncthreads();  // slabs are reused as staging below
+            T cvec[D];
 #pragma unroll
-                    for (int u = 0; u < V; ++u) {
-                        T w[NJ];
-                        ldv<NJ>(At + (i + u) * W, w);
+            for (int m = 0; m < D; ++m) cvec[m] = dN[m] - sw[lay.n0 + m];
+            if (poly) {
+                // (d2Psi/dI2) r_I = phi' (N r_K) + phi'' c r_I;  dPsi/dI = phi' c
 #pragma unroll
-                        for (int jj = 0; jj < NJ; ++jj) {
-                            y[jj] += w[jj] * zv[u];
-                            yd[jj] += w[jj] * zdv[u];
-                        }
-                    }
-                }
-                const T *Bt = sw + lay.Bt + (k - 2) * D * W + j0;
-#pragma unroll
-                for (int m = 0; m < D; ++m) {
-                    T w[NJ];
-                    ldv<NJ>(Bt + m * W, w);
-#pragma unroll
-                    for (int jj = 0; jj < NJ; ++jj) {
-                        y[jj] += w[jj] * K[m];
-                        yd[jj] += w[jj] * r[m];
-                    }
+                for (int m = 0; m < 3; ++m) {
+                    Hr[m] = ch.d1[m] * Hr[m] + ch.d2[m] * cvec[m] * rI[m];
+                    cvec[m] *= ch.d1[m];
                 }
             }
-            T zv[NJ], sv[NJ], tv[NJ], zdv[NJ];
-#pragma unroll
-            for (int jj = 0; jj < NJ; ++jj) {
-                if constexpr (sizeof(T) == 8)
-                    act_tab(y[jj], zv[jj], sv[jj], tv[jj], sw + lay.tab);
-                else
-                    act(y[jj], zv[jj], sv[jj], tv[jj]);
-                zdv[jj] = sv[jj] * yd[jj];
-            }
-            stv<NJ>(qs + sl.s + (k - 1) * W + j0, sv);
-            stv<NJ>(qs + sl.t + (k - 1) * W + j0, tv);
-            stv<NJ>(qs + sl.yd + (k - 1) * W + j0, yd);
-            if (k < L) {
-                stv<NJ>(qs + sl.z + (k - 1) * W + j0, zv);
-                stv<NJ>(qs + sl.zd + (k - 1) * W + j0, zdv);
-            } else {
-                stv<NJ>(qs + sl.zdL + j0, zdv);
-            }
+            stage_kinematics<T, NF>(F, kc, cvec, Jm1, jb, qs);
             __syncwarp();
-        }
-
-        // ---- reverse over the tangent computation
-        T zb[NJ], zdb[NJ];
-        ldv<NJ>(sw + lay.a + j0, zdb);
+            if (dFg != nullptr) {
+                using S = Stage<D, NF>;
+                structured_pre<T, NF>(qs, G, kc, jb);
+                __syncwarp();
+                for (int b = jb; b < 9; b += kG) {
+                    T v = contract_structured<T, NF>(b, qs, kc);
 #pragma unroll
-        for (int jj = 0; jj < NJ; ++jj) zb[jj] = T(0);
-        T Hr[D], dN[D];
-#pragma unroll
-        for (int m = 0; m < D; ++m) {
-            Hr[m] = T(0);
-            dN[m] = (jb == 0) ? sw[lay.b + m] : T(0);
-        }
-        for (int k = L; k >= 1; --k) {
-            const T *Bt = (k == 1) ? (sw + lay.W1t + j0) : (sw + lay.Bt + (k - 2) * D * W + j0);
-            {
-                T sv[NJ], tv[NJ], ydv[NJ], ybv[NJ], ydbv[NJ];
-                ldv<NJ>(qs + sl.s + (k - 1) * W + j0, sv);
-                ldv<NJ>(qs + sl.t + (k - 1) * W + j0, tv);
-                ldv<NJ>(qs + sl.yd + (k - 1) * W + j0, ydv);
-#pragma unroll
-                for (int jj = 0; jj < NJ; ++jj) {
-                    ydbv[jj] = sv[jj] * zdb[jj];
-                    ybv[jj] = sv[jj] * zb[jj] + tv[jj] * ydv[jj] * zdb[jj];
-                }
-                stv<NJ>(qs + sl.yb + j0, ybv);
-                stv<NJ>(qs + sl.ydb + j0, ydbv);
-#pragma unroll
-                for (int m = 0; m < D; ++m) {
-                    T w[NJ];
-                    ldv<NJ>(Bt + m * W, w);
-#pragma unroll
-                    for (int jj = 0; jj < NJ; ++jj) {
-                        Hr[m] += w[jj] * ybv[jj];
-                        dN[m] += w[jj] * ydbv[jj];
-                    }
-                }
-            }
-            __syncthreads();
-            // tile reductions of this layer's weight gradients
-            const T *base = slabs;
-            if (k == 1) {
-                // W1 and c_1 (adjacent: oc1 = oW1 + W D)
-                tile_outer_rows2<T>(acc + oW1, W, D, base, sl.size, sl.yb, sl.K, sl.ydb, sl.r, Q);
-            } else {
-                const int o = oL + (k - 2) * lsz;
-                tile_outer_sq<T>(acc + o, W, base, sl.size, sl.yb, sl.z + (k - 2) * W, sl.ydb, sl.zd + (k - 2) * W, Q);
-                // B_k and c_k
-                tile_outer_rows2<T>(acc + o + W * W, W, D, base, sl.size, sl.yb, sl.K, sl.ydb, sl.r, Q);
-                // zbar_{k-1} = A_k^T ybar_k, zdotbar_{k-1} = A_k^T ydotbar_k for own neurons
-                const T *Ar = arw + (k - 2) * W * W + j0;
-#pragma unroll
-                for (int ii = 0; ii < NJ; ++ii) {
-                    zb[ii] = T(0);
-                    zdb[ii] = T(0);
-                }
-#pragma unroll 2
-                for (int j = 0; j < W; j += V) {
-                    T ybv[V], ydbv[V];
-                    ldv<V>(qs + sl.yb + j, ybv);
-                    ldv<V>(qs + sl.ydb + j, ydbv);
-#pragma unroll
-                    for (int u = 0; u < V; ++u) {
-                        T w[NJ];
-                        ldv<NJ>(Ar + (j + u) * W, w);
-#pragma unroll
-                        for (int ii = 0; ii < NJ; ++ii) {
-                            zb[ii] += w[ii] * ybv[u];
-                            zdb[ii] += w[ii] * ydbv[u];
-                        }
-                    }
+                    for (int n = 0; n < D; ++n) v += Hr[n] * qs[S::g + 9 * n + b];
+                    if (valid) dFg[b * n_qp + q] = bad ? T(NAN) : v;
                 }
             }
             __syncthreads();
         }
-        tile_sum<T>(acc + oa, W, slabs, sl.size, sl.zdL, Q, 0);
-        tile_sum<T>(acc + ob, D, slabs, sl.size, sl.r, Q, blockDim.x > 32 ? 32 : 0);
-
-        // ---- dL/dF = sum_n (Hr)_n g_n + G : S (structured part)
-#pragma unroll
-        for (int msk = 1; msk <= 2; msk <<= 1)
-#pragma unroll
-            for (int m = 0; m < D; ++m) {
-                Hr[m] += __shfl_xor_sync(0xffffffffu, Hr[m], msk);
-                dN[m] += __shfl_xor_sync(0xffffffffu, dN[m], msk);
-            }
-        __syncthreads();  // slabs are reused as staging below
-        T cvec[D];
-#pragma unroll
-        for (int m = 0; m < D; ++m) cvec[m] = dN[m] - sw[lay.n0 + m];
-        if (poly) {
-            // (d2Psi/dI2) r_I = phi' (N r_K) + phi'' c r_I;  dPsi/dI = phi' c
-#pragma unroll
-            for (int m = 0; m < 3; ++m) {
-                Hr[m] = ch.d1[m] * Hr[m] + ch.d2[m] * cvec[m] * rI[m];
-                cvec[m] *= ch.d1[m];
-            }
-        }
-        stage_kinematics<T, NF>(F, kc, cvec, Jm1, jb, qs);
-        __syncwarp();
-        if (dFg != nullptr) {
-            using S = Stage<D, NF>;
-            structured_pre<T, NF>(qs, G, kc, jb);
-            __syncwarp();
-            for (int b = jb; b < 9; b += kG) {
-                T v = contract_structured<T, NF>(b, qs, kc);
-#pragma unroll
-                for (int n = 0; n < D; ++n) v += Hr[n] * qs[S::g + 9 * n + b];
-                if (valid) dFg[b * n_qp + q] = bad ? T(NAN) : v;
-            }
-        }
-        __syncthreads();
-      }
     }
     // write this CTA's partial sums (GACC: already in place)
     if constexpr (!GACC) {
@@ -682,149 +683,149 @@ __global__ void __launch_bounds__(kCannBwWarps * 32, (sizeof(T) == 4 && NF == 0)
     T *rec = slabs + (size_t)kCannBwWarps * kQPW * qstride + (size_t)warp * kinrec_size<NF, kPre>() * 32;
 
     for (int64_t tile0 = (int64_t)blockIdx.x * kCannBwWarps + warp; tile0 < n_tiles; tile0 += kKinTiles * n_gwarps) {
-      if constexpr (kBatch) kin_batch<T, NF, true, kPre>(Fg, Gg, n_qp, tile0, n_gwarps, n_tiles, kc, rec, lane);
-      __syncwarp();
-      for (int sub = 0; sub < kKinTiles; ++sub) {
-        const int64_t tile = tile0 + sub * n_gwarps;
-        if (tile >= n_tiles) break;
-        const int64_t q = tile * kQPW + qi;
-        const bool valid = q < n_qp;
-        T F[9], G[9];
-#pragma unroll
-        for (int c = 0; c < 9; ++c) {
-            F[c] = valid ? Fg[c * n_qp + q] : ((c % 4) == 0 ? T(1) : T(0));
-            G[c] = valid ? Gg[c * n_qp + q] : T(0);
-        }
-        T K[D], Jm1;
-        PolyChain<T> ch;
-        bool bad;
-        if constexpr (kBatch) {
-            bad = kin_read<T, NF>(rec, sub * kQPW + qi, K, Jm1, ch);
-        } else {
-            bad = !kin_scalars_k64<T, NF>(F, kc, K, Jm1, ch);
-#pragma unroll
-            for (int c = 0; c < 9; ++c) bad = bad || !dev_finite(G[c]);
-        }
-        if (bad) {
+        if constexpr (kBatch) kin_batch<T, NF, true, kPre>(Fg, Gg, n_qp, tile0, n_gwarps, n_tiles, kc, rec, lane);
+        __syncwarp();
+        for (int sub = 0; sub < kKinTiles; ++sub) {
+            const int64_t tile = tile0 + sub * n_gwarps;
+            if (tile >= n_tiles) break;
+            const int64_t q = tile * kQPW + qi;
+            const bool valid = q < n_qp;
+            T F[9], G[9];
 #pragma unroll
             for (int c = 0; c < 9; ++c) {
-                F[c] = (c % 4) == 0 ? T(1) : T(0);
-                G[c] = T(0);
+                F[c] = valid ? Fg[c * n_qp + q] : ((c % 4) == 0 ? T(1) : T(0));
+                G[c] = valid ? Gg[c * n_qp + q] : T(0);
             }
-            if constexpr (!kBatch) kin_scalars_k64<T, NF>(F, kc, K, Jm1, ch);
-        }
-        T npart = T(0), dN[D], Hs[NH];
+            T K[D], Jm1;
+            PolyChain<T> ch;
+            bool bad;
+            if constexpr (kBatch) {
+                bad = kin_read<T, NF>(rec, sub * kQPW + qi, K, Jm1, ch);
+            } else {
+                bad = !kin_scalars_k64<T, NF>(F, kc, K, Jm1, ch);
 #pragma unroll
-        for (int m = 0; m < D; ++m) dN[m] = T(0);
-#pragma unroll
-        for (int h = 0; h < NH; ++h) Hs[h] = T(0);
-        cann_point<T, D>(sw, lay, K, jb, npart, dN, Hs);
-        T *pa = qs + qp_stage_end(D, NF);  // the point's P (9) and A (81)
-        T psi_val;
-        bool report;
-        qp_group_finish<T, NF>(sw + lay.n0, sw + lay.K0, kc, qs, qi, jb, F, K, Jm1, ch, bad, valid, npart, dN, Hs,
-                               true, pa, 1, pa + 9, 1, nullptr, 0, psi_val, report,
-                               kPre ? kin_pre<T, NF>(rec, sub * kQPW + qi) : nullptr);
-        __syncwarp();
-        // dL/dF by columns b = jb, jb + 4, jb + 8
-        T dfv[3];
-        bool fin = true;
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            const int b = jb + kG * t;
-            T v = T(0);
-            if (b < 9) {
-#pragma unroll
-                for (int a = 0; a < 9; ++a) v += G[a] * pa[9 + 9 * a + b];
+                for (int c = 0; c < 9; ++c) bad = bad || !dev_finite(G[c]);
             }
-            dfv[t] = v;
-            fin = fin && dev_finite(v);
-        }
-        // r_m = G : dK_m/dF from the staged kinematic gradients
-        T r[D];
+            if (bad) {
 #pragma unroll
-        for (int m = 0; m < D; ++m) {
-            T v = T(0);
-#pragma unroll
-            for (int a = 0; a < 9; ++a) v += G[a] * qs[S::g + 9 * m + a];
-            r[m] = v;
-        }
-        if constexpr (NF == 0) {
-            if (kc.kin == COMMET_KIN_POLYCONVEX) {
-#pragma unroll
-                for (int m = 0; m < 3; ++m) r[m] *= ch.d1[m];
-            }
-        }
-        // the point's weight-gradient terms, d n of them round-robin over its 4 lanes
-        auto term = [&](int t, T &g1, T &g2) {
-            const int m = t / n, k = t - m * n;
-            T x = T(0), rm = T(0);
-#pragma unroll
-            for (int mm = 0; mm < D; ++mm) {
-                x = (mm == m) ? K[mm] : x;
-                rm = (mm == m) ? r[mm] : rm;
-            }
-            cann_term_wgrad<T>(x, (int)sw[lay.ck + 3 * k], (int)sw[lay.ck + 3 * k + 1], (int)sw[lay.ck + 3 * k + 2],
-                               sw[lay.cw + 2 * t], sw[lay.cw + 2 * t + 1], g1, g2);
-            g1 *= rm;
-            g2 *= rm;
-        };
-        // FP64: the lane's first kTermRegs terms stay in registers for the sums below (their
-        // exponentials cost FP64 work); any further ones, and all FP32 ones, are evaluated
-        // again there
-        constexpr int kTermRegs = sizeof(T) == 8 ? 4 : 0;
-        T c1[kTermRegs > 0 ? kTermRegs : 1], c2[kTermRegs > 0 ? kTermRegs : 1];
-#pragma unroll
-        for (int i = 0; i < kTermRegs; ++i) {
-            c1[i] = c2[i] = T(0);
-            if (jb + kG * i < nt) {
-                term(jb + kG * i, c1[i], c2[i]);
-                fin = fin && dev_finite(c1[i]) && dev_finite(c2[i]);
-            }
-        }
-        for (int t0 = kG * kTermRegs; t0 < nt; t0 += kG) {
-            if (t0 + jb < nt) {
-                T g1, g2;
-                term(t0 + jb, g1, g2);
-                fin = fin && dev_finite(g1) && dev_finite(g2);
-            }
-        }
-        // a point outside the energy's domain (reported by the forward) or whose dL/dF or
-        // gradient terms leave the number range (the CANN's exponentials, mostly in FP32)
-        // is treated as J <= 0: NaN in dL/dF, nothing in dL/dw
-        const unsigned nonfin = __ballot_sync(0xffffffffu, !fin);
-        const bool drop = report || !valid || ((nonfin >> (qi * 4)) & 0xFu) != 0u;
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            const int b = jb + kG * t;
-            if (b < 9 && valid && dFg != nullptr) dFg[b * n_qp + q] = drop ? T(NAN) : dfv[t];
-        }
-        for (int t0 = 0; t0 < nt; t0 += kG) {
-            const int t = t0 + jb, i = t0 / kG;
-            T g1 = T(0), g2 = T(0);
-            if (kTermRegs > 0 && i < kTermRegs) {
-#pragma unroll
-                for (int r2 = 0; r2 < kTermRegs; ++r2) {
-                    g1 = (r2 == i) ? c1[r2] : g1;
-                    g2 = (r2 == i) ? c2[r2] : g2;
+                for (int c = 0; c < 9; ++c) {
+                    F[c] = (c % 4) == 0 ? T(1) : T(0);
+                    G[c] = T(0);
                 }
-                if (drop) g1 = g2 = T(0);
-            } else if (t < nt && !drop) {
-                term(t, g1, g2);
+                if constexpr (!kBatch) kin_scalars_k64<T, NF>(F, kc, K, Jm1, ch);
             }
-            // the same term over the warp's 8 points (lanes with the same jb)
+            T npart = T(0), dN[D], Hs[NH];
 #pragma unroll
-            for (int msk = 4; msk <= 16; msk <<= 1) {
-                g1 += shfl_xor(g1, msk);
-                g2 += shfl_xor(g2, msk);
+            for (int m = 0; m < D; ++m) dN[m] = T(0);
+#pragma unroll
+            for (int h = 0; h < NH; ++h) Hs[h] = T(0);
+            cann_point<T, D>(sw, lay, K, jb, npart, dN, Hs);
+            T *pa = qs + qp_stage_end(D, NF);  // the point's P (9) and A (81)
+            T psi_val;
+            bool report;
+            qp_group_finish<T, NF>(sw + lay.n0, sw + lay.K0, kc, qs, qi, jb, F, K, Jm1, ch, bad, valid, npart, dN, Hs,
+                                   true, pa, 1, pa + 9, 1, nullptr, 0, psi_val, report,
+                                   kPre ? kin_pre<T, NF>(rec, sub * kQPW + qi) : nullptr);
+            __syncwarp();
+            // dL/dF by columns b = jb, jb + 4, jb + 8
+            T dfv[3];
+            bool fin = true;
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                const int b = jb + kG * t;
+                T v = T(0);
+                if (b < 9) {
+#pragma unroll
+                    for (int a = 0; a < 9; ++a) v += G[a] * pa[9 + 9 * a + b];
+                }
+                dfv[t] = v;
+                fin = fin && dev_finite(v);
             }
-            if (qi == 0 && t < nt) {
-                wacc[2 * t] += g1;
-                wacc[2 * t + 1] += g2;
+            // r_m = G : dK_m/dF from the staged kinematic gradients
+            T r[D];
+#pragma unroll
+            for (int m = 0; m < D; ++m) {
+                T v = T(0);
+#pragma unroll
+                for (int a = 0; a < 9; ++a) v += G[a] * qs[S::g + 9 * m + a];
+                r[m] = v;
             }
+            if constexpr (NF == 0) {
+                if (kc.kin == COMMET_KIN_POLYCONVEX) {
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) r[m] *= ch.d1[m];
+                }
+            }
+            // the point's weight-gradient terms, d n of them round-robin over its 4 lanes
+            auto term = [&](int t, T &g1, T &g2) {
+                const int m = t / n, k = t - m * n;
+                T x = T(0), rm = T(0);
+#pragma unroll
+                for (int mm = 0; mm < D; ++mm) {
+                    x = (mm == m) ? K[mm] : x;
+                    rm = (mm == m) ? r[mm] : rm;
+                }
+                cann_term_wgrad<T>(x, (int)sw[lay.ck + 3 * k], (int)sw[lay.ck + 3 * k + 1], (int)sw[lay.ck + 3 * k + 2],
+                                   sw[lay.cw + 2 * t], sw[lay.cw + 2 * t + 1], g1, g2);
+                g1 *= rm;
+                g2 *= rm;
+            };
+            // FP64: the lane's first kTermRegs terms stay in registers for the sums below (their
+            // exponentials cost FP64 work); any further ones, and all FP32 ones, are evaluated
+            // again there
+            constexpr int kTermRegs = sizeof(T) == 8 ? 4 : 0;
+            T c1[kTermRegs > 0 ? kTermRegs : 1], c2[kTermRegs > 0 ? kTermRegs : 1];
+#pragma unroll
+            for (int i = 0; i < kTermRegs; ++i) {
+                c1[i] = c2[i] = T(0);
+                if (jb + kG * i < nt) {
+                    term(jb + kG * i, c1[i], c2[i]);
+                    fin = fin && dev_finite(c1[i]) && dev_finite(c2[i]);
+                }
+            }
+            for (int t0 = kG * kTermRegs; t0 < nt; t0 += kG) {
+                if (t0 + jb < nt) {
+                    T g1, g2;
+                    term(t0 + jb, g1, g2);
+                    fin = fin && dev_finite(g1) && dev_finite(g2);
+                }
+            }
+            // a point outside the energy's domain (reported by the forward) or whose dL/dF or
+            // gradient terms leave the number range (the CANN's exponentials, mostly in FP32)
+            // is treated as J <= 0: NaN in dL/dF, nothing in dL/dw
+            const unsigned nonfin = __ballot_sync(0xffffffffu, !fin);
+            const bool drop = report || !valid || ((nonfin >> (qi * 4)) & 0xFu) != 0u;
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                const int b = jb + kG * t;
+                if (b < 9 && valid && dFg != nullptr) dFg[b * n_qp + q] = drop ? T(NAN) : dfv[t];
+            }
+            for (int t0 = 0; t0 < nt; t0 += kG) {
+                const int t = t0 + jb, i = t0 / kG;
+                T g1 = T(0), g2 = T(0);
+                if (kTermRegs > 0 && i < kTermRegs) {
+#pragma unroll
+                    for (int r2 = 0; r2 < kTermRegs; ++r2) {
+                        g1 = (r2 == i) ? c1[r2] : g1;
+                        g2 = (r2 == i) ? c2[r2] : g2;
+                    }
+                    if (drop) g1 = g2 = T(0);
+                } else if (t < nt && !drop) {
+                    term(t, g1, g2);
+                }
+                // the same term over the warp's 8 points (lanes with the same jb)
+#pragma unroll
+                for (int msk = 4; msk <= 16; msk <<= 1) {
+                    g1 += shfl_xor(g1, msk);
+                    g2 += shfl_xor(g2, msk);
+                }
+                if (qi == 0 && t < nt) {
+                    wacc[2 * t] += g1;
+                    wacc[2 * t + 1] += g2;
+                }
+            }
+            __syncwarp();
         }
-        __syncwarp();
-      }
     }
     __syncthreads();
     for (int p = threadIdx.x; p < np_pad; p += blockDim.x) {
@@ -936,9 +937,12 @@ static int cann_bw_launch(const commet_model *m, int64_t n_qp, const void *F, co
     const int qstride = qp_slab_elems<T>(D, 0, 0, NF, true);  // room for P and A after the staging
     const int np_pad = np_padded(m);
     const size_t wbytes = ((size_t)m->lay.total * sizeof(T) + 15) / 16 * 16;
+    // the point slabs, then (where the scalars are batched) the kinematic records, FP64
+    // with the staging's scalars
+    constexpr bool batch = cann_bw_batches<T, NF>();
+    constexpr int rec = batch ? kinrec_size<NF, batch && sizeof(T) == 8>() * 32 : 0;
     const size_t smem = wbytes + (size_t)kCannBwWarps * np_pad * sizeof(T) +
-                        (size_t)kCannBwWarps * (kQPW * qstride + (cann_bw_batches<T, NF>() ? kinrec_size<NF, cann_bw_batches<T, NF>() && sizeof(T) == 8>() * 32 : 0)) *
-                            sizeof(T);
+                        (size_t)kCannBwWarps * (kQPW * qstride + rec) * sizeof(T);
     int dev = 0, smem_max = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

@@ -302,71 +302,72 @@ __global__ void __launch_bounds__(256)
 
     for (int64_t tile0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; tile0 < n_tiles;
          tile0 += kKinTiles * n_gwarps) {
-      if (batch) kin_batch<T, NF, false, sizeof(T) == 8>(Fg, nullptr, n_qp, tile0, n_gwarps, n_tiles, kc, rec, lane);
-      __syncwarp();
-      for (int sub = 0; sub < kKinTiles; ++sub) {
-        const int64_t tile = tile0 + sub * n_gwarps;
-        if (tile >= n_tiles) break;
-        const int64_t q = tile * kQPW + qi;
-        const bool valid = q < n_qp;
-        const int64_t qo = valid ? q : 0;
-        T F[9];
-#pragma unroll
-        for (int c = 0; c < 9; ++c) F[c] = valid ? Fg[c * n_qp + q] : ((c % 4) == 0 ? T(1) : T(0));
-        T K[D], Jm1;
-        PolyChain<T> ch;
-        const bool bad = batch ? kin_read<T, NF>(rec, sub * kQPW + qi, K, Jm1, ch)
-                               : !kin_scalars_k64<T, NF>(F, kc, K, Jm1, ch);
-        if (bad) {
-#pragma unroll
-            for (int c = 0; c < 9; ++c) F[c] = (c % 4) == 0 ? T(1) : T(0);
-            if (!batch) kin_scalars_k64<T, NF>(F, kc, K, Jm1, ch);
-        }
-        T npart = T(0), dN[D], Hs[NH];
-#pragma unroll
-        for (int m = 0; m < D; ++m) dN[m] = T(0);
-#pragma unroll
-        for (int h = 0; h < NH; ++h) Hs[h] = T(0);
-        if constexpr (INNER == COMMET_INNER_ICKAN) {
-            kan_point<T, 3 + 2 * NF, KD>(sw, lay, K, qs, jb, npart, dN, Hs);
-        } else if constexpr (INNER == COMMET_INNER_CANN) {
-            cann_point<T, D>(sw, lay, K, jb, npart, dN, Hs);
-        } else {
-            // eq. gt on raw (Ibar1, Ibar2, J); J - 1 from det_minus_one
-            if (jb == 0) {
-                const T r2 = T(1) / K[1];
-                npart = T(0.5) * (K[0] - T(3)) + dev_log(K[1] * T(1.0 / 3.0)) + Jm1 * Jm1;
-                dN[0] = T(0.5);
-                dN[1] = r2;
-                dN[2] = T(2) * Jm1;
-                Hs[2] = -r2 * r2;
-                Hs[5] = T(2);
-            }
-        }
-        T psi_val;
-        bool report;
-        const T *pre = (sizeof(T) == 8 && batch) ? kin_pre<T, NF>(rec, sub * kQPW + qi) : nullptr;
-        if constexpr (SPATIAL) {
-            T *pa = qs + qp_stage_end(D, NF);
-            qp_group_finish<T, NF>(sw + lay.n0, sw + lay.K0, kc, qs, qi, jb, F, K, Jm1, ch, bad, valid, npart, dN, Hs,
-                                   want_A, pa, 1, want_A ? pa + 9 : nullptr, 1, nullptr, 0, psi_val, report, pre);
-            __syncwarp();
-            push_forward_group<T>(qs + Stage<D, NF>::F, pa, pa + 9, jb, valid, P + qo, want_A ? A + qo : nullptr,
-                                  n_qp);
-        } else {
-            qp_group_finish<T, NF>(sw + lay.n0, sw + lay.K0, kc, qs, qi, jb, F, K, Jm1, ch, bad, valid, npart, dN, Hs,
-                                   want_A, P + qo, n_qp, want_A ? A + qo : nullptr, n_qp,
-                                   dN_out ? dN_out + qo : nullptr, n_qp, psi_val, report, pre);
-        }
-        if (valid && jb == 0) {
-            if (psi != nullptr) psi[q] = psi_val;
-            if (report && status != nullptr) {
-                atomicAdd(&status[0], 1);
-                atomicMin(&status[1], (int32_t)(q < INT32_MAX ? q : INT32_MAX));
-            }
-        }
+        if (batch) kin_batch<T, NF, false, sizeof(T) == 8>(Fg, nullptr, n_qp, tile0, n_gwarps, n_tiles, kc, rec, lane);
         __syncwarp();
-      }
+        for (int sub = 0; sub < kKinTiles; ++sub) {
+            const int64_t tile = tile0 + sub * n_gwarps;
+            if (tile >= n_tiles) break;
+            const int64_t q = tile * kQPW + qi;
+            const bool valid = q < n_qp;
+            const int64_t qo = valid ? q : 0;
+            T F[9];
+#pragma unroll
+            for (int c = 0; c < 9; ++c) F[c] = valid ? Fg[c * n_qp + q] : ((c % 4) == 0 ? T(1) : T(0));
+            T K[D], Jm1;
+            PolyChain<T> ch;
+            const bool bad = batch ? kin_read<T, NF>(rec, sub * kQPW + qi, K, Jm1, ch)
+                                   : !kin_scalars_k64<T, NF>(F, kc, K, Jm1, ch);
+            if (bad) {
+#pragma unroll
+                for (int c = 0; c < 9; ++c) F[c] = (c % 4) == 0 ? T(1) : T(0);
+                if (!batch) kin_scalars_k64<T, NF>(F, kc, K, Jm1, ch);
+            }
+            T npart = T(0), dN[D], Hs[NH];
+#pragma unroll
+            for (int m = 0; m < D; ++m) dN[m] = T(0);
+#pragma unroll
+            for (int h = 0; h < NH; ++h) Hs[h] = T(0);
+            if constexpr (INNER == COMMET_INNER_ICKAN) {
+                kan_point<T, 3 + 2 * NF, KD>(sw, lay, K, qs, jb, npart, dN, Hs);
+            } else if constexpr (INNER == COMMET_INNER_CANN) {
+                cann_point<T, D>(sw, lay, K, jb, npart, dN, Hs);
+            } else {
+                // eq. gt on raw (Ibar1, Ibar2, J); J - 1 from det_minus_one
+                if (jb == 0) {
+                    const T r2 = T(1) / K[1];
+                    npart = T(0.5) * (K[0] - T(3)) + dev_log(K[1] * T(1.0 / 3.0)) + Jm1 * Jm1;
+                    dN[0] = T(0.5);
+                    dN[1] = r2;
+                    dN[2] = T(2) * Jm1;
+                    Hs[2] = -r2 * r2;
+                    Hs[5] = T(2);
+                }
+            }
+            T psi_val;
+            bool report;
+            const T *pre = (sizeof(T) == 8 && batch) ? kin_pre<T, NF>(rec, sub * kQPW + qi) : nullptr;
+            if constexpr (SPATIAL) {
+                T *pa = qs + qp_stage_end(D, NF);
+                qp_group_finish<T, NF>(sw + lay.n0, sw + lay.K0, kc, qs, qi, jb, F, K, Jm1, ch, bad, valid, npart, dN,
+                                       Hs, want_A, pa, 1, want_A ? pa + 9 : nullptr, 1, nullptr, 0, psi_val, report,
+                                       pre);
+                __syncwarp();
+                push_forward_group<T>(qs + Stage<D, NF>::F, pa, pa + 9, jb, valid, P + qo, want_A ? A + qo : nullptr,
+                                      n_qp);
+            } else {
+                qp_group_finish<T, NF>(sw + lay.n0, sw + lay.K0, kc, qs, qi, jb, F, K, Jm1, ch, bad, valid, npart, dN,
+                                       Hs, want_A, P + qo, n_qp, want_A ? A + qo : nullptr, n_qp,
+                                       dN_out ? dN_out + qo : nullptr, n_qp, psi_val, report, pre);
+            }
+            if (valid && jb == 0) {
+                if (psi != nullptr) psi[q] = psi_val;
+                if (report && status != nullptr) {
+                    atomicAdd(&status[0], 1);
+                    atomicMin(&status[1], (int32_t)(q < INT32_MAX ? q : INT32_MAX));
+                }
+            }
+            __syncwarp();
+        }
     }
 }
 

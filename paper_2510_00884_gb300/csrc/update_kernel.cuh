@@ -56,41 +56,43 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 384)
 
     for (int64_t tile0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; tile0 < n_tiles;
          tile0 += kKinTiles * n_gwarps) {
-      if (use_rec) kin_batch<T, NF, false, true>(Fg, nullptr, n_qp, tile0, n_gwarps, n_tiles, kc, rec, lane);
-      __syncwarp();
-      for (int sub = 0; sub < kKinTiles; ++sub) {
-        const int64_t tile = tile0 + sub * n_gwarps;
-        if (tile >= n_tiles) break;
-        const T *krec = use_rec ? rec : nullptr;
-        const int kr = sub * kQPW + qi;
-        const int64_t q = tile * kQPW + qi;
-        const bool valid = q < n_qp;
-        T F[9];
-#pragma unroll
-        for (int cpt = 0; cpt < 9; ++cpt) F[cpt] = valid ? Fg[cpt * n_qp + q] : ((cpt % 4) == 0 ? T(1) : T(0));
-        const int64_t qo = valid ? q : 0;
-        T psi_val;
-        bool report;
-        if constexpr (SPATIAL) {
-            // P and A of the point go to its slab, then are pushed forward to tau (P) and c (A)
-            T *pa = qs + qp_stage_end(Cf::D, NF);
-            qp_group_update<T, NF, W>(sw, lay, mt, at, ar, kc, qs, qi, jb, F, valid, pa, 1, A ? pa + 9 : nullptr, 1, nullptr, 0,
-                                      psi_val, report, krec, kr);
-            __syncwarp();
-            push_forward_group<T>(qs + Stage<Cf::D, NF>::F, pa, pa + 9, jb, valid, P + qo, A ? A + qo : nullptr, n_qp);
-        } else {
-            qp_group_update<T, NF, W>(sw, lay, mt, at, ar, kc, qs, qi, jb, F, valid, P + qo, n_qp, A ? A + qo : nullptr, n_qp,
-                                      dN_out ? dN_out + qo : nullptr, n_qp, psi_val, report, krec, kr);
-        }
-        if (valid && jb == 0) {
-            if (psi != nullptr) psi[q] = psi_val;
-            if (report && status != nullptr) {
-                atomicAdd(&status[0], 1);
-                atomicMin(&status[1], (int32_t)(q < INT32_MAX ? q : INT32_MAX));
-            }
-        }
+        if (use_rec) kin_batch<T, NF, false, true>(Fg, nullptr, n_qp, tile0, n_gwarps, n_tiles, kc, rec, lane);
         __syncwarp();
-      }
+        for (int sub = 0; sub < kKinTiles; ++sub) {
+            const int64_t tile = tile0 + sub * n_gwarps;
+            if (tile >= n_tiles) break;
+            const T *krec = use_rec ? rec : nullptr;
+            const int kr = sub * kQPW + qi;
+            const int64_t q = tile * kQPW + qi;
+            const bool valid = q < n_qp;
+            T F[9];
+#pragma unroll
+            for (int cpt = 0; cpt < 9; ++cpt) F[cpt] = valid ? Fg[cpt * n_qp + q] : ((cpt % 4) == 0 ? T(1) : T(0));
+            const int64_t qo = valid ? q : 0;
+            T psi_val;
+            bool report;
+            if constexpr (SPATIAL) {
+                // P and A of the point go to its slab, then are pushed forward to tau (P) and c (A)
+                T *pa = qs + qp_stage_end(Cf::D, NF);
+                qp_group_update<T, NF, W>(sw, lay, mt, at, ar, kc, qs, qi, jb, F, valid, pa, 1,
+                                          A ? pa + 9 : nullptr, 1, nullptr, 0, psi_val, report, krec, kr);
+                __syncwarp();
+                push_forward_group<T>(qs + Stage<Cf::D, NF>::F, pa, pa + 9, jb, valid, P + qo,
+                                      A ? A + qo : nullptr, n_qp);
+            } else {
+                qp_group_update<T, NF, W>(sw, lay, mt, at, ar, kc, qs, qi, jb, F, valid, P + qo, n_qp,
+                                          A ? A + qo : nullptr, n_qp, dN_out ? dN_out + qo : nullptr, n_qp, psi_val,
+                                          report, krec, kr);
+            }
+            if (valid && jb == 0) {
+                if (psi != nullptr) psi[q] = psi_val;
+                if (report && status != nullptr) {
+                    atomicAdd(&status[0], 1);
+                    atomicMin(&status[1], (int32_t)(q < INT32_MAX ? q : INT32_MAX));
+                }
+            }
+            __syncwarp();
+        }
     }
 }
 
