@@ -285,11 +285,19 @@ __device__ __forceinline__ void tile_sum(T *acc, int n, const T *base, int qstri
 // layers). The CTA then accumulates straight into its own slice of the workspace (each
 // entry still owned by one fixed thread, so the sums keep their order) and reads the
 // row-major A_k of the reverse pass from global memory (through L1).
+// Resident CTAs per SM the register allocation plans for: two (FP64, whose CTAs of at most
+// 128 threads then keep up to 255 registers, their shared memory allowing no more than two;
+// FP32 networks without fibres up to 32 wide, at most 128 registers), one elsewhere.
+template <typename T, int NF, int W>
+struct BwMinBlocks {
+    static constexpr int value = (sizeof(T) == 8 || (NF == 0 && W <= 32)) ? 2 : 1;
+};
+
 template <typename T, int NF, int W, int WARPS, bool GACC = false>
-__global__ void __launch_bounds__(WARPS * 32)
+__global__ void __launch_bounds__(WARPS * 32, (BwMinBlocks<T, NF, W>::value))
     const_backward_kernel(const T *__restrict__ gw, NetLayout lay, KinConst<T> kc, int64_t n_qp,
                           const T *__restrict__ Fg, const T *__restrict__ Gg, T *__restrict__ dFg,
-                          T *__restrict__ partial, int np_pad, BwSlab sl, bool batch) {
+                          T *__restrict__ partial, int np_pad, BwSlab sl, int batch) {
     constexpr int D = 3 + 2 * NF, NJ = W / kG;
     constexpr int Q = WARPS * kQPW;  // points per CTA tile
     static_assert(BwPre<D, NF>::size == 9 * D + 54 + 18 * NF + 5 + NF + 30 + 9 * NF,
@@ -330,11 +338,18 @@ __global__ void __launch_bounds__(WARPS * 32)
 
     const int64_t n_tiles = (n_qp + Q - 1) / Q;
     // FP64 with batch: the kinematic scalars of the warp's points in the CTA's next
-    // kKinTiles tiles, one point per lane (kin_batch), in the warp's records after the slabs
-    const bool use_rec = sizeof(T) == 8 && batch;
-    T *rec = slabs + (size_t)Q * sl.size + (size_t)warp * kinrec_size<NF>() * 32;
+    // kKinTiles tiles, one point per lane (kin_batch), in the warp's records after the slabs;
+    // batch 2: with the staging's scalars too (PRE records), 1: without
+    const bool use_rec = sizeof(T) == 8 && batch > 0;
+    const int rsize = batch == 2 ? kinrec_size<NF, true>() : kinrec_size<NF>();
+    T *rec = slabs + (size_t)Q * sl.size + (size_t)warp * rsize * 32;
     for (int64_t tile0 = blockIdx.x; tile0 < n_tiles; tile0 += (int64_t)kKinTiles * gridDim.x) {
-        if (use_rec) kin_batch<T, NF, true>(Fg, Gg, n_qp, tile0, gridDim.x, n_tiles, kc, rec, lane, Q, warp * kQPW);
+        if (use_rec) {
+            if (batch == 2)
+                kin_batch<T, NF, true, true>(Fg, Gg, n_qp, tile0, gridDim.x, n_tiles, kc, rec, lane, Q, warp * kQPW);
+            else
+                kin_batch<T, NF, true>(Fg, Gg, n_qp, tile0, gridDim.x, n_tiles, kc, rec, lane, Q, warp * kQPW);
+        }
         __syncwarp();
         for (int sub = 0; sub < kKinTiles; ++sub) {
             const int64_t tile = tile0 + (int64_t)sub * gridDim.x;
@@ -365,13 +380,15 @@ __global__ void __launch_bounds__(WARPS * 32)
                 }
                 if (!use_rec) kin_scalars<T, NF>(F, kc, K, Jm1, &ch);
             }
+            // the staging's C, I1, I2, J^(-1/3) from a PRE record
+            const T *pre = (sizeof(T) == 8 && batch == 2) ? kin_pre<T, NF>(rec, sub * kQPW + qi) : nullptr;
             const bool poly = NF == 0 && kc.kin == COMMET_KIN_POLYCONVEX;
             // r_m = G : g_m; the 4 lanes stage g (part 1, 2) and read it back
             {
                 T zero[D];
 #pragma unroll
                 for (int m = 0; m < D; ++m) zero[m] = T(0);
-                stage_kinematics<T, NF, true>(F, kc, zero, Jm1, jb, qs);
+                stage_kinematics<T, NF, true>(F, kc, zero, Jm1, jb, qs, pre);
             }
             T r[D];
             {
@@ -587,7 +604,7 @@ __global__ void __launch_bounds__(WARPS * 32)
                     cvec[m] *= ch.d1[m];
                 }
             }
-            stage_kinematics<T, NF>(F, kc, cvec, Jm1, jb, qs);
+            stage_kinematics<T, NF>(F, kc, cvec, Jm1, jb, qs, pre);
             __syncwarp();
             if (dFg != nullptr) {
                 using S = Stage<D, NF>;
@@ -871,9 +888,13 @@ static int bw_launch(const commet_model *m, int64_t n_qp, const void *F, const v
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (smem0 > (size_t)smem_max) return COMMET_ERR_UNSUPPORTED;
     // FP64: the batched kinematic scalars' records, where they fit beside the slabs
-    const size_t rec_bytes = (size_t)WARPS * kinrec_size<NF>() * 32 * sizeof(T);
-    const bool batch = sizeof(T) == 8 && smem0 + rec_bytes <= (size_t)smem_max;
-    const size_t smem = smem0 + (batch ? rec_bytes : 0);
+    const size_t rec_long = (size_t)WARPS * kinrec_size<NF, true>() * 32 * sizeof(T);
+    const size_t rec_short = (size_t)WARPS * kinrec_size<NF>() * 32 * sizeof(T);
+    const int batch = sizeof(T) != 8                            ? 0
+                      : smem0 + rec_long <= (size_t)smem_max  ? 2
+                      : smem0 + rec_short <= (size_t)smem_max ? 1
+                                                              : 0;
+    const size_t smem = smem0 + (batch == 2 ? rec_long : batch == 1 ? rec_short : 0);
     auto kern = const_backward_kernel<T, NF, W, WARPS, GACC>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return COMMET_ERR_CUDA;

@@ -172,16 +172,28 @@ __device__ __forceinline__ bool kin_scalars_k64(const T (&F)[9], const KinConst<
 // at rec[c * 32 + l]: K[D], J - 1, phi'[3], phi''[3] and 1 where F (or, WITH_G, G = dL/dP)
 // was inadmissible and the scalars are those of F = I (0 otherwise).
 constexpr int kKinTiles = 32 / kQPW;
+
+// Record layout (component-major, stride 32): K[D] at 0, J - 1 at D, then phi'[3] and
+// phi''[3] (the polyconvex layer: networks without fibres only), the replaced-input flag,
+// and with PRE the staging's C[9], I1, I2, J^(-1/3).
+template <int NF>
+__host__ __device__ constexpr int kinrec_chain() {
+    return 3 + 2 * NF + 1;
+}
+template <int NF>
+__host__ __device__ constexpr int kinrec_flag() {
+    return kinrec_chain<NF>() + (NF == 0 ? 6 : 0);
+}
 template <int NF, bool PRE = false>
 __host__ __device__ constexpr int kinrec_size() {
-    return 3 + 2 * NF + 8 + (PRE ? 12 : 0);
+    return kinrec_flag<NF>() + 1 + (PRE ? 12 : 0);
 }
 
 template <typename T, int NF, bool WITH_G, bool PRE = false>
 __device__ __forceinline__ void kin_batch(const T *__restrict__ Fg, const T *__restrict__ Gg, int64_t n_qp,
                                           int64_t tile0, int64_t tstep, int64_t n_tiles, const KinConst<T> &kc,
                                           T *rec, int lane, int tile_pts = kQPW, int off = 0) {
-    constexpr int D = 3 + 2 * NF;
+    constexpr int D = 3 + 2 * NF, oc = kinrec_chain<NF>(), of = kinrec_flag<NF>();
     const int64_t tile = tile0 + (int64_t)(lane / kQPW) * tstep;
     const int64_t q = tile * tile_pts + off + (lane % kQPW);
     const bool valid = tile < n_tiles && q < n_qp;
@@ -204,43 +216,46 @@ __device__ __forceinline__ void kin_batch(const T *__restrict__ Fg, const T *__r
 #pragma unroll
     for (int m = 0; m < D; ++m) rec[m * 32 + lane] = K[m];
     rec[D * 32 + lane] = Jm1;
+    if constexpr (NF == 0) {
 #pragma unroll
-    for (int m = 0; m < 3; ++m) {
-        rec[(D + 1 + m) * 32 + lane] = ch.d1[m];
-        rec[(D + 4 + m) * 32 + lane] = ch.d2[m];
+        for (int m = 0; m < 3; ++m) {
+            rec[(oc + m) * 32 + lane] = ch.d1[m];
+            rec[(oc + 3 + m) * 32 + lane] = ch.d2[m];
+        }
     }
-    rec[(D + 7) * 32 + lane] = bad ? T(1) : T(0);
+    rec[of * 32 + lane] = bad ? T(1) : T(0);
     if constexpr (PRE) {
         // as stage_kinematics forms them (the same F, replaced by I where bad)
         T C[9];
         right_cg(F, C);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) rec[(D + 8 + i) * 32 + lane] = C[i];
-        rec[(D + 17) * 32 + lane] = C[0] + C[4] + C[8];
-        rec[(D + 18) * 32 + lane] = second_invariant(C);
-        rec[(D + 19) * 32 + lane] = dev_rcbrt(T(1) + Jm1);
+        for (int i = 0; i < 9; ++i) rec[(of + 1 + i) * 32 + lane] = C[i];
+        rec[(of + 10) * 32 + lane] = C[0] + C[4] + C[8];
+        rec[(of + 11) * 32 + lane] = second_invariant(C);
+        rec[(of + 12) * 32 + lane] = dev_rcbrt(T(1) + Jm1);
     }
 }
 
 // Where point r's stage_kinematics values sit in a PRE record (stride 32).
 template <typename T, int NF>
 __device__ __forceinline__ const T *kin_pre(const T *rec, int r) {
-    return rec + (3 + 2 * NF + 8) * 32 + r;
+    return rec + (kinrec_flag<NF>() + 1) * 32 + r;
 }
 
 // The record of point r (0..31) of the last kin_batch; returns whether F = I was used.
+// (phi', phi'' are zero for networks with fibres, which have no polyconvex layer.)
 template <typename T, int NF>
 __device__ __forceinline__ bool kin_read(const T *rec, int r, T *K, T &Jm1, PolyChain<T> &ch) {
-    constexpr int D = 3 + 2 * NF;
+    constexpr int D = 3 + 2 * NF, oc = kinrec_chain<NF>();
 #pragma unroll
     for (int m = 0; m < D; ++m) K[m] = rec[m * 32 + r];
     Jm1 = rec[D * 32 + r];
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-        ch.d1[m] = rec[(D + 1 + m) * 32 + r];
-        ch.d2[m] = rec[(D + 4 + m) * 32 + r];
+        ch.d1[m] = NF == 0 ? rec[(oc + m) * 32 + r] : T(0);
+        ch.d2[m] = NF == 0 ? rec[(oc + 3 + m) * 32 + r] : T(0);
     }
-    return rec[(D + 7) * 32 + r] != T(0);
+    return rec[kinrec_flag<NF>() * 32 + r] != T(0);
 }
 
 // One input neuron's contribution to a lane's block of the layer tangent:
