@@ -21,6 +21,14 @@ namespace commet {
 
 int sm_count();
 
+// Instantiations that batch the kinematic scalars where the records fit: FP64 networks
+// without fibres or at most 16 wide (the two-fibre 32- and 64-wide ones have no room for
+// the records beside their warps' slabs, and carry no code for them).
+template <typename T, int NF, int W>
+constexpr bool update_batches() {
+    return sizeof(T) == 8 && (NF == 0 || W <= 16);
+}
+
 template <typename T, int NF, int W, bool SPATIAL>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 384)
     const_update_kernel(const T *__restrict__ gw, NetLayout lay, KinConst<T> kc, int64_t n_qp,
@@ -52,7 +60,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 384)
     // per lane (kin_batch), in the warp's records after the point slabs
     T *rec = sw + wbytes / (int)sizeof(T) + (size_t)(blockDim.x >> 5) * kQPW * qstride +
              (size_t)warp * kinrec_size<NF, true>() * 32;
-    const bool use_rec = sizeof(T) == 8 && batch;
+    const bool use_rec = update_batches<T, NF, W>() && batch;
 
     for (int64_t tile0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; tile0 < n_tiles;
          tile0 += kKinTiles * n_gwarps) {
@@ -136,7 +144,7 @@ static int launch_typed(const commet_model *m, int64_t n_qp, const void *F, void
     if (warps < 1) return COMMET_ERR_UNSUPPORTED;
     // FP64: the batched kinematic scalars' records, where they fit beside the same warps
     const size_t rec_bytes = (size_t)kinrec_size<NF, true>() * 32 * sizeof(T);
-    const bool batch = sizeof(T) == 8 && wbytes + warps * (per_warp + rec_bytes) <= (size_t)smem_max;
+    const bool batch = update_batches<T, NF, W>() && wbytes + warps * (per_warp + rec_bytes) <= (size_t)smem_max;
     const size_t smem = wbytes + warps * (per_warp + (batch ? rec_bytes : 0));
     auto kern = const_update_kernel<T, NF, W, SPATIAL>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
